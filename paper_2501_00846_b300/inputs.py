@@ -1,0 +1,183 @@
+"""Seeded synthetic inputs: initial phase fields, velocity fields and named workloads.
+
+This module holds no step arithmetic of the method.  It only builds initial conditions and
+parameter sets, in FP64 numpy, so that the CUDA path and the CPU oracle read identical bytes.
+
+Phase convention: phi = 1 is the heavy (liquid) phase, phi = 0 the light (gas) phase; the
+interface sits at phi = 1/2.  Initial profiles use the equilibrium interface of the
+conservative Allen-Cahn equation (Section "Allen-Cahn equation for interface tracking"), read
+as phi = 1/2 + 1/2 tanh(2 d / W) with d the signed Euclidean distance to the interface (the
+printed profile uses an L1 distance without the factor 2; with the factor 2 the profile is the
+exact zero of the chemical potential with beta = 12 sigma/W, kappa = 3 sigma W/2 and of the
+sharpening flux with kappa_AC = 4 D/W).
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+
+
+def _grid(nx, ny, nz):
+    z, y, x = np.meshgrid(np.arange(nz, dtype=np.float64), np.arange(ny, dtype=np.float64),
+                          np.arange(nx, dtype=np.float64), indexing="ij")
+    return x, y, z
+
+
+def _min_image(d, n, periodic):
+    if not periodic:
+        return d
+    return d - n * np.round(d / n)
+
+
+def sphere_phi(nx, ny, nz, center, radius, width, inside=1.0, periodic=(True, True, True)):
+    """tanh sphere: phi -> inside at the centre, 1 - inside far away."""
+    x, y, z = _grid(nx, ny, nz)
+    dx = _min_image(x - center[0], nx, periodic[0])
+    dy = _min_image(y - center[1], ny, periodic[1])
+    dz = _min_image(z - center[2], nz, periodic[2])
+    r = np.sqrt(dx * dx + dy * dy + dz * dz)
+    prof = 0.5 + 0.5 * np.tanh(2.0 * (radius - r) / width)
+    return prof if inside == 1.0 else 1.0 - prof
+
+
+def cylinder_phi(nx, ny, nz, center, radius, width, inside=1.0):
+    """tanh cylinder along z (a 2D droplet when nz is small)."""
+    x, y, _ = _grid(nx, ny, nz)
+    dx = _min_image(x - center[0], nx, True)
+    dy = _min_image(y - center[1], ny, True)
+    r = np.sqrt(dx * dx + dy * dy)
+    prof = 0.5 + 0.5 * np.tanh(2.0 * (radius - r) / width)
+    return prof if inside == 1.0 else 1.0 - prof
+
+
+def slab_phi(nx, ny, nz, z_lo, z_hi, width):
+    """Heavy slab between two planar interfaces normal to z (at z_lo and z_hi)."""
+    _, _, z = _grid(nx, ny, nz)
+    return 0.5 + 0.5 * np.tanh(2.0 * np.minimum(z - z_lo, z_hi - z) / width)
+
+
+def layer_phi(nx, ny, nz, z_if, width, heavy_below=True):
+    """One planar interface normal to z at z_if."""
+    _, _, z = _grid(nx, ny, nz)
+    s = (z_if - z) if heavy_below else (z - z_if)
+    return 0.5 + 0.5 * np.tanh(2.0 * s / width)
+
+
+def fourier_velocity(nx, ny, nz, modes=8, amplitude=0.01, seed=1234):
+    """Smooth random periodic velocity: `modes` random Fourier modes with wave numbers 1..2 per
+    axis, random phases and directions, scaled so that max |u| = amplitude.  FP64."""
+    rng = np.random.default_rng(seed)
+    x, y, z = _grid(nx, ny, nz)
+    u = np.zeros((3, nz, ny, nx))
+    for _ in range(modes):
+        k = rng.integers(-2, 3, size=3)
+        if not k.any():
+            k[0] = 1
+        kv = 2.0 * math.pi * k / np.array([nx, ny, nz], dtype=np.float64)
+        ph = rng.uniform(0.0, 2.0 * math.pi)
+        amp = rng.normal(size=3)
+        arg = kv[0] * x + kv[1] * y + kv[2] * z + ph
+        s = np.sin(arg)
+        for a in range(3):
+            u[a] += amp[a] * s
+    m = np.sqrt((u ** 2).sum(axis=0)).max()
+    return u * (amplitude / m)
+
+
+def wall_damp(u, nz):
+    """Multiply a velocity field by sin(pi (z+1/2)/nz) so it vanishes at z walls."""
+    z = np.arange(nz, dtype=np.float64)
+    d = np.sin(math.pi * (z + 0.5) / nz)
+    return u * d[None, :, None, None]
+
+
+@dataclasses.dataclass
+class Workload:
+    """A named physical configuration (lattice units)."""
+    name: str
+    nx: int
+    ny: int
+    nz: int
+    wall_z: int
+    rho_l: float
+    rho_g: float
+    mu_l: float
+    mu_g: float
+    sigma: float
+    width: float
+    mobility: float
+    gravity: tuple
+    rho_ref: float
+    body: tuple
+    kind: str                  # "droplet" or "bubble"
+    center: tuple
+    radius: float
+    noise: float = 0.0         # amplitude of the seeded Fourier velocity
+    seed: int = 1234
+
+    @property
+    def n(self):
+        return self.nx * self.ny * self.nz
+
+    def phi0(self):
+        if self.kind == "droplet":
+            return sphere_phi(self.nx, self.ny, self.nz, self.center, self.radius, self.width,
+                              inside=1.0, periodic=(True, True, not self.wall_z))
+        if self.kind == "bubble":
+            return sphere_phi(self.nx, self.ny, self.nz, self.center, self.radius, self.width,
+                              inside=0.0, periodic=(True, True, not self.wall_z))
+        raise ValueError(self.kind)
+
+    def u0(self):
+        if self.noise == 0.0:
+            return np.zeros((3, self.nz, self.ny, self.nx))
+        u = fourier_velocity(self.nx, self.ny, self.nz, amplitude=self.noise, seed=self.seed)
+        return wall_damp(u, self.nz) if self.wall_z else u
+
+    def params(self) -> dict:
+        return dict(nx=self.nx, ny=self.ny, nz=self.nz, wall_z=self.wall_z, rho_l=self.rho_l,
+                    rho_g=self.rho_g, mu_l=self.mu_l, mu_g=self.mu_g, sigma=self.sigma,
+                    width=self.width, mobility=self.mobility, gravity=tuple(self.gravity),
+                    rho_ref=self.rho_ref, body=tuple(self.body))
+
+
+def static_droplet(L=48, radius=None, noise=0.0, seed=1234, sigma=0.01):
+    """Static droplet: periodic L^3, sphere R (default L/4) centred, W = 4, density ratio 10,
+    viscosity ratio 10 (nu_L = nu_G = 0.1, tau = 0.8), sigma = 0.01, D = 0.1, fluid at rest."""
+    R = L / 4.0 if radius is None else radius
+    c = (L - 1) / 2.0
+    return Workload(name=f"static_droplet_{L}^3", nx=L, ny=L, nz=L, wall_z=0,
+                    rho_l=1.0, rho_g=0.1, mu_l=0.1, mu_g=0.01, sigma=sigma, width=4.0,
+                    mobility=0.1, gravity=(0.0, 0.0, 0.0), rho_ref=1.0, body=(0.0, 0.0, 0.0),
+                    kind="droplet", center=(c, c, c), radius=R, noise=noise, seed=seed)
+
+
+def rising_bubble_params(Eo=10.0, Mo=1e-4, R=16.0, sqrt_gR=0.04, rho_l=1.0, rho_ratio=1000.0,
+                         mu_ratio=100.0):
+    """Gravity, surface tension and viscosities for a rising bubble from Eo and Mo.
+
+    Eo = rho_L g R^2 / sigma and Ga = sqrt(g R) R / nu_L (Section "Rising bubble"); the Morton
+    number is read as Mo = Eo^3 / Ga^4 = g mu_L^4 / (rho_L sigma^3).  The velocity scale
+    sqrt(g R) is chosen, which fixes g."""
+    g = sqrt_gR ** 2 / R
+    sigma = g * rho_l * R * R / Eo
+    Ga = (Eo ** 3 / Mo) ** 0.25
+    nu_l = sqrt_gR * R / Ga
+    mu_l = rho_l * nu_l
+    return dict(g=g, sigma=sigma, Ga=Ga, nu_l=nu_l, mu_l=mu_l, mu_g=mu_l / mu_ratio,
+                rho_g=rho_l / rho_ratio)
+
+
+def rising_bubble(nx=128, ny=128, nz=256, R=16.0, zc=40.0, Eo=10.0, Mo=1e-4, rho_ratio=1000.0,
+                  mu_ratio=100.0, width=4.0, mobility=0.1):
+    """Rising bubble: walls on z, periodic x, y; gas bubble of radius R at (nx/2, ny/2, zc);
+    density ratio 1000, viscosity ratio 100; gravity from Eo and Mo; buoyancy acts on the
+    light phase only (rho_ref = rho_L)."""
+    p = rising_bubble_params(Eo=Eo, Mo=Mo, R=R, rho_ratio=rho_ratio, mu_ratio=mu_ratio)
+    return Workload(name=f"rising_bubble_{nx}x{ny}x{nz}", nx=nx, ny=ny, nz=nz, wall_z=1,
+                    rho_l=1.0, rho_g=p["rho_g"], mu_l=p["mu_l"], mu_g=p["mu_g"], sigma=p["sigma"],
+                    width=width, mobility=mobility, gravity=(0.0, 0.0, -p["g"]), rho_ref=1.0,
+                    body=(0.0, 0.0, 0.0), kind="bubble", center=(nx / 2.0, ny / 2.0, zc),
+                    radius=R)
