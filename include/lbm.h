@@ -1,0 +1,173 @@
+/*
+ * C ABI of the B300-native coupled lattice Boltzmann + conservative Allen–Cahn solver
+ * (arXiv 2501.00846, "Thread-safe multiphase lattice Boltzmann model for droplet and bubble
+ * dynamics at high density and viscosity contrasts").
+ *
+ * One context owns one box of nx*ny*nz nodes on the current CUDA device.  Every entry point
+ * takes plain pointers and sizes; no C++ or PyTorch type crosses this boundary.  All device
+ * work is enqueued on the context's stream (lbm_params.stream, or a stream the library creates
+ * when that is NULL).
+ *
+ * Lattice: D3Q27, cs^2 = 1/3, dx = dt = 1.  Velocity index i = 9 (cz+1) + 3 (cy+1) + (cx+1)
+ * for c_i = (cx, cy, cz) in {-1,0,1}^3; the opposite of i is 26 - i; the rest velocity is 13.
+ *
+ * Array layouts (all FP32, structure of arrays, x fastest):
+ *   scalar field   s[(z*ny + y)*nx + x]                     N = nx*ny*nz floats
+ *   vector field   v[a*N + (z*ny + y)*nx + x], a = 0,1,2   3N floats
+ *   populations    g[i*N + (z*ny + y)*nx + x], i = 0..26   27N floats
+ *
+ * Phase convention: phi = 1 is the heavy (liquid) phase of density rho_l, phi = 0 the light
+ * (gas) phase of density rho_g; rho = rho_l phi + (1 - phi) rho_g (paper Section "Model
+ * extension for high-density and viscosity contrasts").
+ *
+ * State after step n: (g^n, phi^n, ubar^n).  g^n_i(x) is the post-collision population at its
+ * origin node, phi^n the phase field that collision used, ubar^n the velocity it produced.
+ * p* = sum_i g_i and p = p* rho cs^2 (Eq. eqts and the relation that follows Eq. press_corr).
+ *
+ * Errors: every function returns LBM_OK or a negative lbm_status; lbm_last_error() gives a
+ * one-line message for the calling thread's last failure.  On error no output is written
+ * except where stated.  Functions never abort the process and never trap the GPU.
+ */
+#ifndef LBM_H
+#define LBM_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lbm_ctx lbm_ctx;
+
+typedef enum {
+    LBM_OK = 0,
+    LBM_ERR_ARG = -1,        /* invalid argument or parameter set */
+    LBM_ERR_OOM = -2,        /* device allocation failed; nothing leaked */
+    LBM_ERR_CUDA = -3,       /* a CUDA call failed; see lbm_last_error() */
+    LBM_ERR_NONFINITE = -4,  /* the state holds NaN/Inf (observables still filled) */
+    LBM_ERR_TIMEOUT = -5,    /* a bounded device wait expired */
+    LBM_ERR_STATE = -6       /* call out of order (e.g. lbm_step before lbm_init_fields) */
+} lbm_status;
+
+typedef enum {
+    LBM_FP32 = 0,            /* populations stored as FP32 */
+    LBM_BF16 = 1,            /* populations stored as BF16 deviations (not built: LBM_ERR_ARG) */
+    LBM_FP16 = 2             /* populations stored as FP16 deviations (not built: LBM_ERR_ARG) */
+} lbm_storage;
+
+/*
+ * Parameters, lattice units.  Plain old data; set struct_size = sizeof(lbm_params).
+ * Validation in lbm_create (LBM_ERR_ARG on failure):
+ *   nx, ny, nz >= 4, ny, nz <= 65535 and nx*ny*nz < 2^31;
+ *   rho_l, rho_g, mu_l, mu_g, width > 0; sigma >= 0; 0 <= mobility < 9/26 (FTCS limit of the
+ *   27-point Laplacian: mobility * 52/9 < 2); forces finite.
+ */
+typedef struct {
+    size_t struct_size;
+    int nx, ny, nz;
+    int wall_z;           /* 0: periodic in z.  1: no-slip walls at z = -1/2 and z = nz - 1/2
+                             (halfway bounce-back; phase field mirrored, neutral wetting) */
+    double rho_l, rho_g;  /* densities of the phi = 1 and phi = 0 phases */
+    double mu_l, mu_g;    /* dynamic viscosities; mu(phi) = mu_g + phi (mu_l - mu_g),
+                             nu = mu / rho, tau = nu / cs^2 + 1/2 (the paper gives no
+                             interpolation law; this linear law in phi is the one applied) */
+    double sigma;         /* surface tension: beta = 12 sigma/width, kappa = 3 sigma width/2 */
+    double width;         /* interface width delta (W) */
+    double mobility;      /* Allen–Cahn diffusivity D; sharpening kappa_AC = 4 D / width */
+    double gravity[3];    /* gravitational acceleration; buoyancy force (rho - rho_ref) g */
+    double rho_ref;       /* reference density; rho_l applies gravity to the light phase only */
+    double body[3];       /* uniform body-force density (e.g. a driven channel) */
+    int storage;          /* lbm_storage */
+    void *stream;         /* cudaStream_t to enqueue on; NULL: the library creates its own */
+} lbm_params;
+
+/* Integral diagnostics, accumulated in FP64 on the device (all doubles). */
+typedef struct {
+    double step;              /* steps taken since lbm_init_fields / lbm_set_state */
+    double sum_phi;           /* sum phi */
+    double mass;              /* sum rho */
+    double sum_pstar;         /* sum p* */
+    double momentum[3];       /* sum rho ubar */
+    double centroid_liq[3];   /* sum phi x / sum phi */
+    double centroid_gas[3];   /* sum (1-phi) x / sum (1-phi) */
+    double vel_liq[3];        /* sum phi ubar / sum phi */
+    double vel_gas[3];        /* sum (1-phi) ubar / sum (1-phi) */
+    double p_liq, p_gas;      /* mean p over nodes with phi > 0.999 / phi < 0.001 (NaN if none) */
+    double n_liq, n_gas;      /* node counts of those two sets */
+    double umax;              /* max |ubar| */
+    double phi_min, phi_max;  /* extrema of phi (overshoot outside [0,1] is not clamped) */
+    double n_nonfinite;       /* count of nodes with a non-finite phi, ubar or p* */
+} lbm_obs;
+
+/* Create a context: validates *params, allocates every device buffer (two FP32 copies of
+ * g, phi, ubar: 2 x 31 floats per node, plus scratch).  The caller owns *out and releases it
+ * with lbm_destroy.  On error *out = NULL and nothing is leaked. */
+lbm_status lbm_create(const lbm_params *params, lbm_ctx **out);
+
+/* Set the initial state (the paper's loop starts from equilibrium populations):
+ *   g = f^eq(p*0, u0) (Eq. eqts), phi = phi0, ubar = u0, step counter = 0.
+ * phi: N floats; u: 3N floats; pstar: N floats or NULL for p*0 = 0.
+ * on_device = 0: host pointers (copied, then the stream is synchronised); 1: device pointers
+ * on the context's device (copied on the context's stream).  The library never keeps the
+ * caller's pointers. */
+lbm_status lbm_init_fields(lbm_ctx *ctx, const float *phi, const float *u, const float *pstar,
+                           int on_device);
+
+/* Advance nsteps >= 0 time steps.  One step is the coupled update of the paper's step list
+ * (Section "Implementation of the hybrid LB-finite difference implementation"): Allen–Cahn
+ * FTCS update of phi, pull streaming (each node writes only itself), moments, surface-tension /
+ * pressure / viscous / body forces, velocity, pre-regularisation and the third-order
+ * regularised collision (Eqs. lbe to guoforce, press_corr, visc_corr).
+ * Asynchronous on the context's stream; no host synchronisation.  LBM_ERR_STATE before
+ * lbm_init_fields.  No NaN check (lbm_observables reports non-finite values). */
+lbm_status lbm_step(lbm_ctx *ctx, int nsteps);
+
+/* FP64 reductions over the current state into *out (see lbm_obs).  Synchronises the stream.
+ * Returns LBM_ERR_NONFINITE when out->n_nonfinite > 0; *out is filled in that case too. */
+lbm_status lbm_observables(lbm_ctx *ctx, lbm_obs *out);
+
+/* Copy out phi (N floats), ubar (3N floats) and p = p* rho cs^2 (N floats).  Any of the three
+ * pointers may be NULL.  on_device as in lbm_init_fields.  Synchronises the stream. */
+lbm_status lbm_read_fields(lbm_ctx *ctx, float *phi, float *u, float *p, int on_device);
+
+/* Checkpoint / resume of the raw state: g (27N floats), phi (N), ubar (3N).  A state written
+ * by lbm_get_state and restored by lbm_set_state continues bit-identically.  lbm_set_state
+ * sets the step counter to `step`.  Both synchronise the stream. */
+lbm_status lbm_get_state(lbm_ctx *ctx, float *g, float *phi, float *u, int on_device);
+lbm_status lbm_set_state(lbm_ctx *ctx, const float *g, const float *phi, const float *u,
+                         long long step, int on_device);
+
+/* Block the host until the context's stream is idle. */
+lbm_status lbm_synchronize(lbm_ctx *ctx);
+
+/* Number of nodes N and steps taken; 0 for NULL. */
+long long lbm_num_nodes(const lbm_ctx *ctx);
+long long lbm_step_count(const lbm_ctx *ctx);
+
+/* Select the step kernel: 0 = one fused kernel per step (default), 1 = the unfused
+ * three-kernel path (Allen–Cahn flux, Allen–Cahn update, lattice Boltzmann) kept for
+ * cross-checks.  LBM_ERR_ARG for other values. */
+lbm_status lbm_set_path(lbm_ctx *ctx, int path);
+
+/* Fused-kernel tuning: z planes marched by one CTA; 0 restores the library's default for the
+ * grid.  Results are bit-identical for every value (the halo planes each CTA recomputes use the
+ * same arithmetic as their owners).  LBM_ERR_ARG for negative values. */
+lbm_status lbm_set_chunk(lbm_ctx *ctx, int z_chunk);
+
+/* Free every resource of ctx; NULL-safe.  Waits for the context's stream first. */
+void lbm_destroy(lbm_ctx *ctx);
+
+/* Static description of a status code; never NULL. */
+const char *lbm_status_string(lbm_status s);
+
+/* Message of the calling thread's last failure ("" if none). */
+const char *lbm_last_error(void);
+
+/* ABI version of this header (incremented on incompatible changes). */
+int lbm_abi_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBM_H */

@@ -1,0 +1,357 @@
+// C ABI (include/lbm.h): context management, validation, buffer ownership and dispatch.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <new>
+
+#include <cuda_runtime.h>
+
+#include "lbm.h"
+#include "tslb_internal.h"
+
+namespace {
+
+thread_local char g_last_error[512] = "";
+
+lbm_status fail(lbm_status s, const char *fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_last_error, sizeof g_last_error, fmt, ap);
+    va_end(ap);
+    return s;
+}
+
+#define CUDA_TRY(call)                                                                           \
+    do {                                                                                         \
+        cudaError_t e_ = (call);                                                                 \
+        if (e_ != cudaSuccess)                                                                   \
+            return fail(LBM_ERR_CUDA, "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_),     \
+                        __FILE__, __LINE__);                                                     \
+    } while (0)
+
+}  // namespace
+
+struct lbm_ctx {
+    lbm_params prm;
+    tslb::Grid G;
+    tslb::Phys P;
+    float *g[2] = {nullptr, nullptr};
+    float *phi[2] = {nullptr, nullptr};
+    float *u[2] = {nullptr, nullptr};
+    float *flux = nullptr;            // 3N, unfused path only
+    double *partials = nullptr;       // observables pass-1 records
+    double *result = nullptr;         // observables pass-2 record (device)
+    double *h_result = nullptr;       // pinned host copy
+    int nblocks = 0;
+    int cur = 0;                      // index of the buffers holding S^n
+    long long step = 0;
+    bool initialized = false;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int path = 0;
+    int chunk = 0;
+};
+
+namespace {
+
+void free_ctx(lbm_ctx *c)
+{
+    if (!c) return;
+    for (int b = 0; b < 2; ++b) {
+        cudaFree(c->g[b]);
+        cudaFree(c->phi[b]);
+        cudaFree(c->u[b]);
+    }
+    cudaFree(c->flux);
+    cudaFree(c->partials);
+    cudaFree(c->result);
+    if (c->h_result) cudaFreeHost(c->h_result);
+    if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+    delete c;
+}
+
+lbm_status validate(const lbm_params *p)
+{
+    if (!p) return fail(LBM_ERR_ARG, "params is NULL");
+    if (p->struct_size != sizeof(lbm_params))
+        return fail(LBM_ERR_ARG, "params.struct_size = %zu, expected %zu", p->struct_size, sizeof(lbm_params));
+    if (p->nx < 4 || p->ny < 4 || p->nz < 4) return fail(LBM_ERR_ARG, "nx, ny, nz must be >= 4");
+    const long long n = (long long)p->nx * p->ny * p->nz;
+    if (n >= (1LL << 31)) return fail(LBM_ERR_ARG, "nx*ny*nz must be < 2^31");
+    if (p->ny > 65535 || p->nz > 65535) return fail(LBM_ERR_ARG, "ny, nz must be <= 65535");
+    if (p->wall_z != 0 && p->wall_z != 1) return fail(LBM_ERR_ARG, "wall_z must be 0 or 1");
+    if (!(p->rho_l > 0) || !(p->rho_g > 0)) return fail(LBM_ERR_ARG, "densities must be > 0");
+    if (!(p->mu_l > 0) || !(p->mu_g > 0)) return fail(LBM_ERR_ARG, "viscosities must be > 0");
+    if (!(p->width > 0)) return fail(LBM_ERR_ARG, "interface width must be > 0");
+    if (!(p->sigma >= 0) || !isfinite(p->sigma)) return fail(LBM_ERR_ARG, "sigma must be finite and >= 0");
+    if (!(p->mobility >= 0) || !(p->mobility * 52.0 / 9.0 < 2.0))
+        return fail(LBM_ERR_ARG, "mobility must satisfy 0 <= D < 9/26 (FTCS limit)");
+    for (int a = 0; a < 3; ++a)
+        if (!isfinite(p->gravity[a]) || !isfinite(p->body[a])) return fail(LBM_ERR_ARG, "forces must be finite");
+    if (!isfinite(p->rho_ref)) return fail(LBM_ERR_ARG, "rho_ref must be finite");
+    if (p->storage != LBM_FP32)
+        return fail(LBM_ERR_ARG, "storage %d is not built in this library (only LBM_FP32)", p->storage);
+    return LBM_OK;
+}
+
+void make_consts(lbm_ctx *c)
+{
+    const lbm_params &p = c->prm;
+    c->G.nx = p.nx;
+    c->G.ny = p.ny;
+    c->G.nz = p.nz;
+    c->G.nxy = p.nx * p.ny;
+    c->G.N = p.nx * p.ny * p.nz;
+    c->G.wall = p.wall_z;
+    c->P.rho_g = (float)p.rho_g;
+    c->P.drho = (float)(p.rho_l - p.rho_g);
+    c->P.mu_g = (float)p.mu_g;
+    c->P.dmu = (float)(p.mu_l - p.mu_g);
+    c->P.beta4 = (float)(4.0 * 12.0 * p.sigma / p.width);
+    c->P.kappa = (float)(1.5 * p.sigma * p.width);
+    c->P.mob = (float)p.mobility;
+    c->P.kac = (float)(4.0 * p.mobility / p.width);
+    for (int a = 0; a < 3; ++a) {
+        c->P.grav[a] = (float)p.gravity[a];
+        c->P.body[a] = (float)p.body[a];
+    }
+    c->P.rho_ref = (float)p.rho_ref;
+}
+
+cudaMemcpyKind kind_in(int on_device) { return on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice; }
+cudaMemcpyKind kind_out(int on_device) { return on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost; }
+
+}  // namespace
+
+extern "C" {
+
+int lbm_abi_version(void) { return 1; }
+
+const char *lbm_last_error(void) { return g_last_error; }
+
+const char *lbm_status_string(lbm_status s)
+{
+    switch (s) {
+    case LBM_OK: return "ok";
+    case LBM_ERR_ARG: return "invalid argument";
+    case LBM_ERR_OOM: return "device out of memory";
+    case LBM_ERR_CUDA: return "CUDA error";
+    case LBM_ERR_NONFINITE: return "non-finite values in the state";
+    case LBM_ERR_TIMEOUT: return "bounded device wait expired";
+    case LBM_ERR_STATE: return "call out of order";
+    }
+    return "unknown status";
+}
+
+lbm_status lbm_create(const lbm_params *params, lbm_ctx **out)
+{
+    if (!out) return fail(LBM_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    lbm_status st = validate(params);
+    if (st != LBM_OK) return st;
+
+    lbm_ctx *c = new (std::nothrow) lbm_ctx;
+    if (!c) return fail(LBM_ERR_OOM, "host allocation failed");
+    c->prm = *params;
+    make_consts(c);
+    const size_t N = (size_t)c->G.N;
+
+    if (params->stream) {
+        c->stream = (cudaStream_t)params->stream;
+    } else {
+        cudaError_t e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) {
+            free_ctx(c);
+            return fail(LBM_ERR_CUDA, "cudaStreamCreate failed: %s", cudaGetErrorString(e));
+        }
+        c->own_stream = true;
+    }
+
+    c->nblocks = tslb::observables_blocks(c->G);
+    struct {
+        void **p;
+        size_t bytes;
+    } allocs[] = {
+        {(void **)&c->g[0], 27 * N * sizeof(float)}, {(void **)&c->g[1], 27 * N * sizeof(float)},
+        {(void **)&c->phi[0], N * sizeof(float)},    {(void **)&c->phi[1], N * sizeof(float)},
+        {(void **)&c->u[0], 3 * N * sizeof(float)},  {(void **)&c->u[1], 3 * N * sizeof(float)},
+        {(void **)&c->flux, 3 * N * sizeof(float)},
+        {(void **)&c->partials, (size_t)c->nblocks * tslb::kObsFields * sizeof(double)},
+        {(void **)&c->result, tslb::kObsFields * sizeof(double)},
+    };
+    for (auto &a : allocs) {
+        cudaError_t e = cudaMalloc(a.p, a.bytes);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            free_ctx(c);
+            return fail(e == cudaErrorMemoryAllocation ? LBM_ERR_OOM : LBM_ERR_CUDA, "cudaMalloc(%zu) failed: %s",
+                        a.bytes, cudaGetErrorString(e));
+        }
+    }
+    cudaError_t e = cudaMallocHost(&c->h_result, tslb::kObsFields * sizeof(double));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        free_ctx(c);
+        return fail(LBM_ERR_OOM, "cudaMallocHost failed: %s", cudaGetErrorString(e));
+    }
+    *out = c;
+    return LBM_OK;
+}
+
+void lbm_destroy(lbm_ctx *ctx)
+{
+    if (!ctx) return;
+    cudaStreamSynchronize(ctx->stream);
+    free_ctx(ctx);
+}
+
+long long lbm_num_nodes(const lbm_ctx *ctx) { return ctx ? (long long)ctx->G.N : 0; }
+long long lbm_step_count(const lbm_ctx *ctx) { return ctx ? ctx->step : 0; }
+
+lbm_status lbm_set_path(lbm_ctx *ctx, int path)
+{
+    if (!ctx) return fail(LBM_ERR_ARG, "context is NULL");
+    if (path != 0 && path != 1) return fail(LBM_ERR_ARG, "path must be 0 (fused) or 1 (unfused)");
+    ctx->path = path;
+    return LBM_OK;
+}
+
+lbm_status lbm_set_chunk(lbm_ctx *ctx, int z_chunk)
+{
+    if (!ctx) return fail(LBM_ERR_ARG, "context is NULL");
+    if (z_chunk < 0) return fail(LBM_ERR_ARG, "z_chunk must be >= 0");
+    ctx->chunk = z_chunk;
+    return LBM_OK;
+}
+
+lbm_status lbm_init_fields(lbm_ctx *ctx, const float *phi, const float *u, const float *pstar, int on_device)
+{
+    if (!ctx) return fail(LBM_ERR_ARG, "context is NULL");
+    if (!phi || !u) return fail(LBM_ERR_ARG, "phi and u are required");
+    const size_t N = (size_t)ctx->G.N;
+    const int c = ctx->cur;
+    CUDA_TRY(cudaMemcpyAsync(ctx->phi[c], phi, N * sizeof(float), kind_in(on_device), ctx->stream));
+    CUDA_TRY(cudaMemcpyAsync(ctx->u[c], u, 3 * N * sizeof(float), kind_in(on_device), ctx->stream));
+    const float *ps = nullptr;
+    if (pstar) {   // stage p*0 in the idle population buffer
+        CUDA_TRY(cudaMemcpyAsync(ctx->g[1 - c], pstar, N * sizeof(float), kind_in(on_device), ctx->stream));
+        ps = ctx->g[1 - c];
+    }
+    CUDA_TRY(tslb::launch_init(ctx->G, ps, ctx->u[c], ctx->g[c], ctx->stream));
+    if (!on_device) CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+    ctx->step = 0;
+    ctx->initialized = true;
+    return LBM_OK;
+}
+
+lbm_status lbm_step(lbm_ctx *ctx, int nsteps)
+{
+    if (!ctx) return fail(LBM_ERR_ARG, "context is NULL");
+    if (nsteps < 0) return fail(LBM_ERR_ARG, "nsteps must be >= 0");
+    if (!ctx->initialized) return fail(LBM_ERR_STATE, "lbm_step before lbm_init_fields");
+    for (int s = 0; s < nsteps; ++s) {
+        const int a = ctx->cur, b = 1 - ctx->cur;
+        tslb::StepArgs args{ctx->g[a], ctx->g[b], ctx->phi[a], ctx->phi[b], ctx->u[a], ctx->u[b], ctx->flux};
+        cudaError_t e = ctx->path == 0 ? tslb::launch_step_fused(ctx->G, ctx->P, args, ctx->chunk, ctx->stream)
+                                       : tslb::launch_step_unfused(ctx->G, ctx->P, args, ctx->stream);
+        if (e != cudaSuccess) return fail(LBM_ERR_CUDA, "step launch failed: %s", cudaGetErrorString(e));
+        ctx->cur = b;
+        ++ctx->step;
+    }
+    return LBM_OK;
+}
+
+lbm_status lbm_synchronize(lbm_ctx *ctx)
+{
+    if (!ctx) return fail(LBM_ERR_ARG, "context is NULL");
+    CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+    return LBM_OK;
+}
+
+lbm_status lbm_observables(lbm_ctx *ctx, lbm_obs *out)
+{
+    if (!ctx) return fail(LBM_ERR_ARG, "context is NULL");
+    if (!out) return fail(LBM_ERR_ARG, "out is NULL");
+    if (!ctx->initialized) return fail(LBM_ERR_STATE, "lbm_observables before lbm_init_fields");
+    const int c = ctx->cur;
+    CUDA_TRY(tslb::launch_observables(ctx->G, ctx->P, ctx->g[c], ctx->phi[c], ctx->u[c], ctx->partials, ctx->nblocks,
+                                      ctx->result, ctx->stream));
+    CUDA_TRY(cudaMemcpyAsync(ctx->h_result, ctx->result, tslb::kObsFields * sizeof(double), cudaMemcpyDeviceToHost,
+                             ctx->stream));
+    CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+    const double *r = ctx->h_result;
+    memset(out, 0, sizeof *out);
+    out->step = (double)ctx->step;
+    out->sum_phi = r[0];
+    out->mass = r[1];
+    out->sum_pstar = r[2];
+    for (int a = 0; a < 3; ++a) {
+        out->momentum[a] = r[3 + a];
+        out->centroid_liq[a] = r[6 + a] / r[0];
+        out->centroid_gas[a] = r[9 + a] / r[26];
+        out->vel_liq[a] = r[12 + a] / r[0];
+        out->vel_gas[a] = r[15 + a] / r[26];
+    }
+    out->n_liq = r[19];
+    out->n_gas = r[21];
+    out->p_liq = r[19] > 0 ? r[18] / r[19] : NAN;
+    out->p_gas = r[21] > 0 ? r[20] / r[21] : NAN;
+    out->umax = r[22];
+    out->phi_min = r[23];
+    out->phi_max = r[24];
+    out->n_nonfinite = r[25];
+    if (out->n_nonfinite > 0) return fail(LBM_ERR_NONFINITE, "%.0f non-finite nodes", out->n_nonfinite);
+    return LBM_OK;
+}
+
+lbm_status lbm_read_fields(lbm_ctx *ctx, float *phi, float *u, float *p, int on_device)
+{
+    if (!ctx) return fail(LBM_ERR_ARG, "context is NULL");
+    if (!ctx->initialized) return fail(LBM_ERR_STATE, "lbm_read_fields before lbm_init_fields");
+    const size_t N = (size_t)ctx->G.N;
+    const int c = ctx->cur;
+    if (phi) CUDA_TRY(cudaMemcpyAsync(phi, ctx->phi[c], N * sizeof(float), kind_out(on_device), ctx->stream));
+    if (u) CUDA_TRY(cudaMemcpyAsync(u, ctx->u[c], 3 * N * sizeof(float), kind_out(on_device), ctx->stream));
+    if (p) {   // compute p into the idle population buffer, then copy
+        float *tmp = ctx->g[1 - c];
+        CUDA_TRY(tslb::launch_pressure(ctx->G, ctx->P, ctx->g[c], ctx->phi[c], tmp, ctx->stream));
+        CUDA_TRY(cudaMemcpyAsync(p, tmp, N * sizeof(float), kind_out(on_device), ctx->stream));
+    }
+    CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+    return LBM_OK;
+}
+
+lbm_status lbm_get_state(lbm_ctx *ctx, float *g, float *phi, float *u, int on_device)
+{
+    if (!ctx) return fail(LBM_ERR_ARG, "context is NULL");
+    if (!ctx->initialized) return fail(LBM_ERR_STATE, "lbm_get_state before lbm_init_fields");
+    const size_t N = (size_t)ctx->G.N;
+    const int c = ctx->cur;
+    if (g) CUDA_TRY(cudaMemcpyAsync(g, ctx->g[c], 27 * N * sizeof(float), kind_out(on_device), ctx->stream));
+    if (phi) CUDA_TRY(cudaMemcpyAsync(phi, ctx->phi[c], N * sizeof(float), kind_out(on_device), ctx->stream));
+    if (u) CUDA_TRY(cudaMemcpyAsync(u, ctx->u[c], 3 * N * sizeof(float), kind_out(on_device), ctx->stream));
+    CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+    return LBM_OK;
+}
+
+lbm_status lbm_set_state(lbm_ctx *ctx, const float *g, const float *phi, const float *u, long long step,
+                         int on_device)
+{
+    if (!ctx) return fail(LBM_ERR_ARG, "context is NULL");
+    if (!g || !phi || !u) return fail(LBM_ERR_ARG, "g, phi and u are required");
+    if (step < 0) return fail(LBM_ERR_ARG, "step must be >= 0");
+    const size_t N = (size_t)ctx->G.N;
+    const int c = ctx->cur;
+    CUDA_TRY(cudaMemcpyAsync(ctx->g[c], g, 27 * N * sizeof(float), kind_in(on_device), ctx->stream));
+    CUDA_TRY(cudaMemcpyAsync(ctx->phi[c], phi, N * sizeof(float), kind_in(on_device), ctx->stream));
+    CUDA_TRY(cudaMemcpyAsync(ctx->u[c], u, 3 * N * sizeof(float), kind_in(on_device), ctx->stream));
+    CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+    ctx->step = step;
+    ctx->initialized = true;
+    return LBM_OK;
+}
+
+}  // extern "C"

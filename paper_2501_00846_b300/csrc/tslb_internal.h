@@ -1,0 +1,40 @@
+// Internal launch interface shared by the translation units of the library (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "tslb_device.cuh"
+
+namespace tslb {
+
+struct StepArgs {
+    const float *g_in;
+    float *g_out;
+    const float *phi_in;
+    float *phi_out;
+    const float *u_in;
+    float *u_out;
+    float *flux;           // 3N scratch of the unfused path (Allen–Cahn flux); unused by the fused path
+};
+
+// One step S^n -> S^{n+1}.
+cudaError_t launch_step_unfused(const Grid &G, const Phys &P, const StepArgs &a, cudaStream_t s);
+cudaError_t launch_step_fused(const Grid &G, const Phys &P, const StepArgs &a, int tz, cudaStream_t s);
+
+// Default z-chunk of the fused kernel for a grid.
+int fused_default_chunk(const Grid &G);
+
+// g = f^eq(p*, u); pstar may be nullptr (p* = 0).
+cudaError_t launch_init(const Grid &G, const float *pstar, const float *u, float *g, cudaStream_t s);
+
+// p = (sum_i g_i) rho cs^2.
+cudaError_t launch_pressure(const Grid &G, const Phys &P, const float *g, const float *phi, float *p,
+                            cudaStream_t s);
+
+// FP64 reductions: number of doubles in one partial record, and the two-pass reduction.
+constexpr int kObsFields = 32;
+int observables_blocks(const Grid &G);
+cudaError_t launch_observables(const Grid &G, const Phys &P, const float *g, const float *phi, const float *u,
+                               double *partials, int nblocks, double *result, cudaStream_t s);
+
+}  // namespace tslb
