@@ -1,0 +1,331 @@
+#!/usr/bin/env python
+"""Benchmark of the coupled TSLB + Allen-Cahn step on B300 (one JSON line on rank 0).
+
+Workload (default): the rising bubble, 128 x 128 x 256 nodes, walls on z, periodic x and y,
+gas bubble R = 16 at z = 40, density ratio 1000, viscosity ratio 100, gravity from Eo = 10 and
+Mo = 1e-4, W = 4; synthetic seeded inputs.  A step is one time step of the whole box (one fused
+kernel launch).  The state (1.04 GB of FP32 populations and fields per copy) is far larger than
+the 126 MB L2, so consecutive steps stream from HBM and no flush is needed.
+
+  value  MLUPS = nodes * K / device time of K steps (CUDA events on the solver's stream),
+         summed over ranks (each rank runs its own replica: weak scaling).
+  e2e    the same metric through the public API from pinned host buffers: init from host,
+         K steps, observables and a read-back of phi, u, p to host, all inside the timed region.
+  roofline  dominant kernel (the fused step): algorithmic 248 B per node update (read 27 g +
+         phi + 3 u, write the same) over its mean launch duration, against the measured HBM peak.
+  cpu_baseline  the FP64 oracle (plain C, OpenMP) on the host cores, on a bounded sample.
+
+--impl reference runs the FP64 CPU oracle as the reference arm (rank 0 only).
+"""
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+BYTES_PER_LUP = 248          # FP32: (27 + 1 + 3) floats read + the same written
+FALLBACK_HBM_GBS = 6400.0
+METRIC = "MLUPS & % HBM peak: coupled LBM+Allen-Cahn step, FP32 vs BF16 store"
+KERNEL_SOURCES = ["paper_2501_00846_b300/csrc/step_fused.cu", "paper_2501_00846_b300/csrc/tslb_device.cuh",
+                  "paper_2501_00846_b300/csrc/tslb_internal.h"]
+
+
+def workload(name):
+    from paper_2501_00846_b300 import inputs
+    if name == "rising_bubble":
+        return inputs.rising_bubble()
+    if name.startswith("droplet"):
+        L = int(name[len("droplet"):])
+        return inputs.static_droplet(L=L)
+    raise SystemExit(f"unknown workload {name}")
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for rel in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, rel), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def measured_traffic(wl_name, nodes):
+    """DRAM bytes per launch of the fused kernel from the committed ncu summary, if its source
+    hash matches the current kernel sources (else None)."""
+    path = os.path.join(ROOT, "profiles", f"fused_step_{wl_name}.txt")
+    if not os.path.exists(path):
+        return None
+    kv = {}
+    for line in open(path):
+        if ":" in line and not line.startswith("#"):
+            k, v = line.split(":", 1)
+            kv[k.strip()] = v.strip()
+    if kv.get("source_sha256") != kernel_source_hash():
+        return None
+    try:
+        b = float(kv["dram_bytes_per_launch"])
+        n = float(kv["nodes"])
+    except (KeyError, ValueError):
+        return None
+    return b * nodes / n
+
+
+def hbm_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+    FIELDS = ("clocks.sm,clocks.max.sm,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.out = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "50"], stdout=self.out, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+            return
+        t0 = time.time()
+        while time.time() - t0 < 5 and os.path.getsize(self.out.name) == 0:
+            time.sleep(0.05)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.1)
+        self.proc.terminate()
+        self.proc.wait()
+        rows = []
+        with open(self.out.name) as fh:
+            for line in fh:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) == 6:
+                    rows.append(parts)
+        os.unlink(self.out.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[0]) for r in rows if r[0].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[2 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": float(rows[0][1]) if rows[0][1].replace(".", "").isdigit() else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def oracle_sample(seconds, max_steps=None):
+    """Time the FP64 oracle on a rising-bubble sub-box (same parameters and per-node arithmetic
+    as the benchmark workload) for about `seconds`; returns (MLUPS, description, threads)."""
+    import oracle
+    from paper_2501_00846_b300 import inputs
+    L = 16
+    wl = inputs.rising_bubble(nx=L, ny=L, nz=2 * L, R=L / 4, zc=L / 2)
+    P = oracle.Params(**wl.params())
+    s = oracle.init(P, wl.phi0(), wl.u0())
+    t0 = time.perf_counter()
+    s = oracle.run(P, s, 2)
+    per_node = (time.perf_counter() - t0) / (2 * P.n)
+    # choose the sub-box so that one step takes ~seconds/8, at least 16^2 x 32 nodes
+    target_nodes = max(P.n, min(128 * 128 * 256, seconds / 8 / per_node))
+    L = max(16, int((target_nodes / 2) ** (1 / 3)) // 4 * 4)
+    wl = inputs.rising_bubble(nx=L, ny=L, nz=2 * L, R=L / 4, zc=L / 2)
+    P = oracle.Params(**wl.params())
+    s = oracle.init(P, wl.phi0(), wl.u0())
+    steps = 0
+    t0 = time.perf_counter()
+    while time.perf_counter() - t0 < seconds and (max_steps is None or steps < max_steps):
+        s = oracle.step(P, s)
+        steps += 1
+    dt = time.perf_counter() - t0
+    desc = (f"oracle on a {L}x{L}x{2 * L} rising-bubble sub-box with the benchmark's parameters, "
+            f"{steps} steps in {dt:.1f} s")
+    return P.n * steps / dt / 1e6, desc, oracle.get_threads()
+
+
+def run_reference(args):
+    """Reference arm: the FP64 CPU oracle, each step on a bounded sub-box of the workload."""
+    import oracle
+    from paper_2501_00846_b300 import inputs
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    budget = 150.0
+    # calibrate the per-node cost, then size the sub-box so warmup + steps fit the budget
+    wl = inputs.rising_bubble(nx=16, ny=16, nz=32, R=4.0, zc=8.0)
+    P = oracle.Params(**wl.params())
+    s = oracle.init(P, wl.phi0(), wl.u0())
+    t0 = time.perf_counter()
+    oracle.run(P, s, 2)
+    per_node = (time.perf_counter() - t0) / (2 * P.n)
+    nodes = budget / max(1, args.steps + args.warmup) / per_node
+    L = int(max(4, min(128, (nodes / 2) ** (1 / 3))))
+    wl = inputs.rising_bubble(nx=L, ny=L, nz=2 * L, R=max(1.5, L / 4), zc=L / 2)
+    P = oracle.Params(**wl.params())
+    s = oracle.init(P, wl.phi0(), wl.u0())
+    s = oracle.run(P, s, args.warmup)
+    t0 = time.perf_counter()
+    s = oracle.run(P, s, args.steps)
+    dt = time.perf_counter() - t0
+    value = P.n * args.steps / dt / 1e6
+    desc = f"each step: one oracle step of a {L}x{L}x{2 * L} rising-bubble sub-box with the workload's parameters"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": workload(args.workload).name, "sample": desc},
+        "cpu_baseline": {"value": value, "unit": "MLUPS", "cores": oracle.get_threads(), "kind": "oracle",
+                         "sample": desc},
+        "e2e": {"value": value, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="b300", choices=["b300", "reference"])
+    ap.add_argument("--workload", default="rising_bubble")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        raise SystemExit("--warmup must be >= 3")
+
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_2501_00846_b300 import solver
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+
+    wl = workload(args.workload)
+    N = wl.n
+    stream = torch.cuda.current_stream()
+    s = solver.Solver(stream=stream, **wl.params())
+    phi0 = np.ascontiguousarray(wl.phi0(), np.float32)
+    u0 = np.ascontiguousarray(wl.u0(), np.float32)
+    s.init_fields(phi0, u0)
+    s.step(args.warmup)
+    torch.cuda.synchronize()
+
+    # ---- device-timed region: K steps, one fused kernel each --------------------------------
+    sampler = ClockSampler(local)
+    sampler.start()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    s.step(args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clocks = sampler.stop()
+    ms = e0.elapsed_time(e1)
+    t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    obs = s.observables(allow_nonfinite=True)
+
+    # ---- end to end through the public API from pinned host buffers --------------------------
+    phi_h = torch.from_numpy(phi0.reshape(-1)).pin_memory().numpy()
+    u_h = torch.from_numpy(u0.reshape(-1)).pin_memory().numpy()
+    outs = [torch.empty(n, dtype=torch.float32).pin_memory().numpy() for n in (N, 3 * N, N)]
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    s.init_fields(phi_h, u_h)
+    s.step(args.steps)
+    obs_e2e = s.observables(allow_nonfinite=True)
+    s.read_fields(*outs)
+    e2e_s = time.perf_counter() - t0
+    te = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
+    if world > 1:
+        dist.all_reduce(te, op=dist.ReduceOp.MAX)
+    e2e_s = float(te.item())
+    s.close()
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return 0
+
+    value = world * N * args.steps / (ms_max * 1e-3) / 1e6
+    launch_s = ms * 1e-3 / args.steps
+    achieved = BYTES_PER_LUP * N / launch_s / 1e9
+    peak, peak_src = hbm_peak()
+    traffic = measured_traffic(args.workload, N)
+    line = {
+        "metric": METRIC,
+        "value": value,
+        "unit": "MLUPS",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": ms_max / args.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": wl.name, "nodes": N, "store": "fp32",
+                   "l2": "state 1.04 GB per copy >> 126 MB L2: inputs larger than L2, no flush",
+                   "parallelism": f"replicas x{world}", "sum_phi_after": obs["sum_phi"],
+                   "nonfinite_after": obs["n_nonfinite"]},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic,
+                     "kernel": "fused_step_kernel", "bytes_per_lup": BYTES_PER_LUP,
+                     "peak_source": f"{peak_src} hbm_gbs"},
+        "e2e": {"value": world * N * args.steps / e2e_s / 1e6, "unit": "MLUPS",
+                "h2d_bytes_per_step": 4 * 4 * N / args.steps,
+                "d2h_bytes_per_step": (5 * 4 * N + 8 * 64) / args.steps,
+                "includes": "init_fields from pinned host, K steps, observables, read_fields to pinned host"},
+        "gpu_launches": args.steps,
+        "clocks": clocks,
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        v, desc, cores = oracle_sample(args.cpu_seconds)
+        line["cpu_baseline"] = {"value": v, "unit": "MLUPS", "cores": cores, "kind": "oracle", "sample": desc}
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,247 @@
+"""Thin ctypes binding over the C ABI of include/lbm.h (argument marshalling only).
+
+Every step of the method runs in the CUDA library ``libtslb_b300.so``; this module only converts
+arguments.  Host arrays are numpy float32; device arrays are torch CUDA float32 tensors (torch
+provides device memory and the stream, nothing else).  There is no CPU fallback: if the library
+is missing, ``load()`` raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libtslb_b300.so")
+
+LBM_OK = 0
+STATUS = {0: "LBM_OK", -1: "LBM_ERR_ARG", -2: "LBM_ERR_OOM", -3: "LBM_ERR_CUDA",
+          -4: "LBM_ERR_NONFINITE", -5: "LBM_ERR_TIMEOUT", -6: "LBM_ERR_STATE"}
+
+
+class LbmParams(ctypes.Structure):
+    _fields_ = [
+        ("struct_size", ctypes.c_size_t),
+        ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+        ("wall_z", ctypes.c_int),
+        ("rho_l", ctypes.c_double), ("rho_g", ctypes.c_double),
+        ("mu_l", ctypes.c_double), ("mu_g", ctypes.c_double),
+        ("sigma", ctypes.c_double), ("width", ctypes.c_double), ("mobility", ctypes.c_double),
+        ("gravity", ctypes.c_double * 3),
+        ("rho_ref", ctypes.c_double),
+        ("body", ctypes.c_double * 3),
+        ("storage", ctypes.c_int),
+        ("stream", ctypes.c_void_p),
+    ]
+
+
+class LbmObs(ctypes.Structure):
+    _fields_ = [
+        ("step", ctypes.c_double), ("sum_phi", ctypes.c_double), ("mass", ctypes.c_double),
+        ("sum_pstar", ctypes.c_double),
+        ("momentum", ctypes.c_double * 3),
+        ("centroid_liq", ctypes.c_double * 3), ("centroid_gas", ctypes.c_double * 3),
+        ("vel_liq", ctypes.c_double * 3), ("vel_gas", ctypes.c_double * 3),
+        ("p_liq", ctypes.c_double), ("p_gas", ctypes.c_double),
+        ("n_liq", ctypes.c_double), ("n_gas", ctypes.c_double),
+        ("umax", ctypes.c_double), ("phi_min", ctypes.c_double), ("phi_max", ctypes.c_double),
+        ("n_nonfinite", ctypes.c_double),
+    ]
+
+    def as_dict(self) -> dict:
+        out = {}
+        for name, _ in self._fields_:
+            v = getattr(self, name)
+            out[name] = list(v) if isinstance(v, ctypes.Array) else float(v)
+        return out
+
+
+class LbmError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load the CUDA library (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"CUDA library {path} is missing: build it with paper_2501_00846_b300.build.build()")
+    L = ctypes.CDLL(path)
+    vp, i, ll = ctypes.c_void_p, ctypes.c_int, ctypes.c_longlong
+    fp = ctypes.c_void_p
+    sigs = {
+        "lbm_create": ([ctypes.POINTER(LbmParams), ctypes.POINTER(vp)], i),
+        "lbm_init_fields": ([vp, fp, fp, fp, i], i),
+        "lbm_step": ([vp, i], i),
+        "lbm_observables": ([vp, ctypes.POINTER(LbmObs)], i),
+        "lbm_read_fields": ([vp, fp, fp, fp, i], i),
+        "lbm_get_state": ([vp, fp, fp, fp, i], i),
+        "lbm_set_state": ([vp, fp, fp, fp, ll, i], i),
+        "lbm_synchronize": ([vp], i),
+        "lbm_num_nodes": ([vp], ll),
+        "lbm_step_count": ([vp], ll),
+        "lbm_set_path": ([vp, i], i),
+        "lbm_set_chunk": ([vp, i], i),
+        "lbm_destroy": ([vp], None),
+        "lbm_status_string": ([i], ctypes.c_char_p),
+        "lbm_last_error": ([], ctypes.c_char_p),
+        "lbm_abi_version": ([], i),
+    }
+    for name, (args, res) in sigs.items():
+        fn = getattr(L, name)
+        fn.argtypes = args
+        fn.restype = res
+    _lib = L
+    return L
+
+
+def _check(status: int):
+    if status != LBM_OK:
+        raise LbmError(status, load().lbm_last_error().decode())
+
+
+def make_params(nx, ny, nz, wall_z=0, rho_l=1.0, rho_g=0.1, mu_l=0.1, mu_g=0.01, sigma=0.01,
+                width=4.0, mobility=0.1, gravity=(0.0, 0.0, 0.0), rho_ref=1.0,
+                body=(0.0, 0.0, 0.0), storage=0, stream=None) -> LbmParams:
+    p = LbmParams()
+    p.struct_size = ctypes.sizeof(LbmParams)
+    p.nx, p.ny, p.nz, p.wall_z = int(nx), int(ny), int(nz), int(wall_z)
+    p.rho_l, p.rho_g, p.mu_l, p.mu_g = rho_l, rho_g, mu_l, mu_g
+    p.sigma, p.width, p.mobility = sigma, width, mobility
+    p.gravity[:] = [float(v) for v in gravity]
+    p.rho_ref = rho_ref
+    p.body[:] = [float(v) for v in body]
+    p.storage = int(storage)
+    p.stream = stream
+    return p
+
+
+def _ptr(a, n: int, writable: bool):
+    """(pointer, on_device) of a float32 numpy array or torch CUDA tensor with n elements."""
+    if a is None:
+        return None, None
+    if isinstance(a, np.ndarray):
+        if a.dtype != np.float32 or not a.flags.c_contiguous or a.size != n:
+            raise ValueError(f"expected a C-contiguous float32 array of {n} elements")
+        if writable and not a.flags.writeable:
+            raise ValueError("output array is read-only")
+        return a.ctypes.data, 0
+    import torch
+    if not isinstance(a, torch.Tensor) or not a.is_cuda or a.dtype != torch.float32 \
+            or not a.is_contiguous() or a.numel() != n:
+        raise ValueError(f"expected a contiguous float32 CUDA tensor of {n} elements")
+    return a.data_ptr(), 1
+
+
+class Solver:
+    """One box on the current CUDA device, driven through the C ABI.
+
+    ``stream``: a ``torch.cuda.Stream`` (default: torch's current stream at construction)."""
+
+    def __init__(self, stream=None, **params):
+        import torch
+        L = load()
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        self.params = make_params(stream=stream.cuda_stream, **params)
+        self._ctx = ctypes.c_void_p()
+        _check(L.lbm_create(ctypes.byref(self.params), ctypes.byref(self._ctx)))
+        self.shape = (self.params.nz, self.params.ny, self.params.nx)
+        self.n = int(L.lbm_num_nodes(self._ctx))
+
+    # -- lifecycle --------------------------------------------------------------------------
+    def close(self):
+        if getattr(self, "_ctx", None) and self._ctx.value:
+            load().lbm_destroy(self._ctx)
+            self._ctx = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # -- calls ------------------------------------------------------------------------------
+    def init_fields(self, phi, u, pstar=None):
+        pp, d1 = _ptr(phi, self.n, False)
+        up, d2 = _ptr(u, 3 * self.n, False)
+        sp, d3 = _ptr(pstar, self.n, False)
+        on_dev = {d for d in (d1, d2, d3) if d is not None}
+        if len(on_dev) != 1:
+            raise ValueError("inputs must all be host arrays or all device tensors")
+        _check(load().lbm_init_fields(self._ctx, pp, up, sp, on_dev.pop()))
+
+    def step(self, nsteps: int = 1):
+        _check(load().lbm_step(self._ctx, int(nsteps)))
+
+    def synchronize(self):
+        _check(load().lbm_synchronize(self._ctx))
+
+    def set_path(self, path: int):
+        _check(load().lbm_set_path(self._ctx, int(path)))
+
+    def set_chunk(self, z_chunk: int):
+        _check(load().lbm_set_chunk(self._ctx, int(z_chunk)))
+
+    @property
+    def step_count(self) -> int:
+        return int(load().lbm_step_count(self._ctx))
+
+    def observables(self, allow_nonfinite: bool = False) -> dict:
+        o = LbmObs()
+        st = load().lbm_observables(self._ctx, ctypes.byref(o))
+        if st == -4 and allow_nonfinite:
+            return o.as_dict()
+        _check(st)
+        return o.as_dict()
+
+    def read_fields(self, phi=None, u=None, p=None):
+        """Fill the given outputs (numpy or CUDA tensors); with no argument return host copies
+        (phi[nz,ny,nx], u[3,nz,ny,nx], p[nz,ny,nx])."""
+        if phi is None and u is None and p is None:
+            phi = np.empty(self.shape, np.float32)
+            u = np.empty((3,) + self.shape, np.float32)
+            p = np.empty(self.shape, np.float32)
+        ptrs = [_ptr(phi, self.n, True), _ptr(u, 3 * self.n, True), _ptr(p, self.n, True)]
+        on_dev = {d for _, d in ptrs if d is not None}
+        if len(on_dev) != 1:
+            raise ValueError("outputs must all be host arrays or all device tensors")
+        _check(load().lbm_read_fields(self._ctx, ptrs[0][0], ptrs[1][0], ptrs[2][0], on_dev.pop()))
+        return phi, u, p
+
+    def get_state(self):
+        g = np.empty((27,) + self.shape, np.float32)
+        phi = np.empty(self.shape, np.float32)
+        u = np.empty((3,) + self.shape, np.float32)
+        _check(load().lbm_get_state(self._ctx, g.ctypes.data, phi.ctypes.data, u.ctypes.data, 0))
+        return g, phi, u
+
+    def set_state(self, g, phi, u, step: int = 0):
+        gp, d1 = _ptr(g, 27 * self.n, False)
+        pp, d2 = _ptr(phi, self.n, False)
+        up, d3 = _ptr(u, 3 * self.n, False)
+        on_dev = {d1, d2, d3}
+        if len(on_dev) != 1:
+            raise ValueError("inputs must all be host arrays or all device tensors")
+        _check(load().lbm_set_state(self._ctx, gp, pp, up, int(step), on_dev.pop()))
+
+
+def from_workload(wl, stream=None) -> Solver:
+    """Solver for an inputs.Workload, initialised with its seeded phi0/u0 (FP64 -> FP32)."""
+    s = Solver(stream=stream, **wl.params())
+    s.init_fields(np.ascontiguousarray(wl.phi0(), np.float32), np.ascontiguousarray(wl.u0(), np.float32))
+    return s

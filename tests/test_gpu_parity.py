@@ -1,0 +1,262 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 CPU oracle on the same seeded
+inputs.  Both sides start from identical FP32 bytes (phi0, u0 rounded to float32, then widened
+to FP64 for the oracle).
+
+Tolerances (after the stated number of steps, FP32 on the GPU):
+  max |d phi| <= 1e-5;  ||d u||_inf / ||u_oracle||_inf <= 1e-4;  ||d p||_inf / ||p_oracle||_inf <= 1e-4
+and integral observables within 0.5% on long runs.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2501_00846_b300 import inputs, solver
+
+pytestmark = pytest.mark.gpu
+
+TOL_PHI, TOL_U, TOL_P = 1e-5, 1e-4, 1e-4
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    torch.cuda.set_device(0)
+    solver.load()
+
+
+def _f32(a):
+    return np.ascontiguousarray(a, dtype=np.float32)
+
+
+def _gpu_run(wl, nsteps, path=0, chunk=0, phi0=None, u0=None):
+    phi0 = wl.phi0() if phi0 is None else phi0
+    u0 = wl.u0() if u0 is None else u0
+    with solver.Solver(**wl.params()) as s:
+        s.set_path(path)
+        s.set_chunk(chunk)
+        s.init_fields(_f32(phi0), _f32(u0))
+        s.step(nsteps)
+        phi, u, p = s.read_fields()
+        g, _, _ = s.get_state()
+        obs = s.observables()
+    return phi, u, p, g, obs
+
+
+def _oracle_run(wl, nsteps, phi0=None, u0=None):
+    phi0 = wl.phi0() if phi0 is None else phi0
+    u0 = wl.u0() if u0 is None else u0
+    P = oracle.Params(**wl.params())
+    s = oracle.run(P, oracle.init(P, _f32(phi0).astype(np.float64), _f32(u0).astype(np.float64)), nsteps)
+    return P, s
+
+
+def _compare(gpu, P, ref):
+    phi, u, p = gpu[:3]
+    pref = oracle.pressure(P, ref)
+    dphi = float(np.abs(phi - ref.phi).max())
+    du = float(np.abs(u - ref.u).max() / np.abs(ref.u).max())
+    dp = float(np.abs(p - pref).max() / np.abs(pref).max())
+    return dphi, du, dp
+
+
+def _assert_parity(gpu, P, ref, label):
+    dphi, du, dp = _compare(gpu, P, ref)
+    print(f"{label}: max|dphi| {dphi:.3e}  rel du {du:.3e}  rel dp {dp:.3e}")
+    assert dphi <= TOL_PHI, (label, dphi)
+    assert du <= TOL_U, (label, du)
+    assert dp <= TOL_P, (label, dp)
+
+
+# -- the 48^3 static droplet (density ratio 10, viscosity ratio 10), seeded velocity noise ---------
+
+@pytest.fixture(scope="module")
+def droplet48():
+    wl = inputs.static_droplet(L=48, radius=12.0, noise=0.01, seed=1234)
+    P, ref = _oracle_run(wl, 100)
+    return wl, P, ref
+
+
+@pytest.mark.parametrize("path", [0, 1], ids=["fused", "unfused"])
+def test_droplet48_100_steps(droplet48, path):
+    wl, P, ref = droplet48
+    gpu = _gpu_run(wl, 100, path=path)
+    _assert_parity(gpu, P, ref, f"droplet48 path={path}")
+    # populations too (same velocity ordering on both sides)
+    assert np.abs(gpu[3] - ref.g).max() <= 1e-4 * np.abs(ref.g).max()
+
+
+def test_droplet48_observables(droplet48):
+    wl, P, ref = droplet48
+    phi, u, p, g, obs = _gpu_run(wl, 100)
+    o = oracle.observables(P, ref)
+    assert abs(obs["sum_phi"] / o["sum_phi"] - 1) < 1e-6
+    assert abs(obs["mass"] / o["mass"] - 1) < 1e-6
+    for a in range(3):
+        assert abs(obs["centroid_liq"][a] - o["centroid_liq"][a]) < 1e-4
+    assert abs(obs["umax"] / o["umax"] - 1) < 1e-4
+    # the device reduction equals FP64 sums of the device's own fields
+    phi64 = phi.astype(np.float64)
+    rho = P.rho_l * phi64 + (1 - phi64) * P.rho_g
+    assert math.isclose(obs["sum_phi"], phi64.sum(), rel_tol=1e-12)
+    assert math.isclose(obs["mass"], rho.sum(), rel_tol=1e-12)
+    assert math.isclose(obs["sum_pstar"], g.astype(np.float64).sum(), rel_tol=1e-9, abs_tol=1e-9)
+    for a in range(3):
+        assert math.isclose(obs["momentum"][a], (rho * u[a]).sum(), rel_tol=1e-9, abs_tol=1e-12)
+
+
+def test_droplet48_at_rest_200_steps():
+    """The configuration as stated (fluid at rest, 200 steps): only spurious currents move."""
+    wl = inputs.static_droplet(L=48, radius=12.0)
+    P, ref = _oracle_run(wl, 200)
+    gpu = _gpu_run(wl, 200)
+    dphi, du, dp = _compare(gpu, P, ref)
+    print(f"droplet48 at rest: max|dphi| {dphi:.3e} rel du {du:.3e} rel dp {dp:.3e} "
+          f"(umax {np.abs(ref.u).max():.2e})")
+    assert dphi <= TOL_PHI and dp <= TOL_P
+    assert du <= TOL_U
+
+
+# -- ragged sizes, walls, density ratio 1000 --------------------------------------------------
+
+def _ragged_bubble():
+    wl = inputs.rising_bubble(nx=37, ny=21, nz=19, R=5.0, zc=8.0)
+    wl.noise, wl.seed = 0.005, 99
+    return wl
+
+
+@pytest.mark.parametrize("path", [0, 1], ids=["fused", "unfused"])
+def test_ragged_walled_bubble_ratio1000(path):
+    wl = _ragged_bubble()
+    P, ref = _oracle_run(wl, 60)
+    gpu = _gpu_run(wl, 60, path=path)
+    _assert_parity(gpu, P, ref, f"ragged walled bubble path={path}")
+
+
+def test_ragged_periodic_droplet_across_boundary():
+    wl = inputs.static_droplet(L=24, radius=7.0, noise=0.02, seed=5)
+    wl.nx, wl.ny, wl.nz = 45, 13, 27
+    wl.center = (2.0, 11.5, 25.0)            # wraps around all three periodic boundaries
+    P, ref = _oracle_run(wl, 80)
+    gpu = _gpu_run(wl, 80)
+    _assert_parity(gpu, P, ref, "ragged periodic droplet")
+
+
+def test_minimum_box():
+    wl = inputs.static_droplet(L=4, radius=1.5, noise=0.01, seed=3)
+    P, ref = _oracle_run(wl, 10)
+    _assert_parity(_gpu_run(wl, 10), P, ref, "4^3 box")
+    wl = inputs.rising_bubble(nx=4, ny=5, nz=4, R=1.5, zc=2.0)
+    P, ref = _oracle_run(wl, 10)
+    _assert_parity(_gpu_run(wl, 10), P, ref, "4x5x4 walled box")
+
+
+# -- determinism and invariances of the fused kernel -------------------------------------------
+
+def test_chunk_size_does_not_change_results():
+    wl = _ragged_bubble()
+    ref = _gpu_run(wl, 25, chunk=0)
+    for chunk in (1, 3, 7, 64):
+        out = _gpu_run(wl, 25, chunk=chunk)
+        for a, b in zip(ref[:4], out[:4]):
+            assert np.array_equal(a, b), chunk
+
+
+def test_checkpoint_resume_bit_exact():
+    wl = inputs.static_droplet(L=32, radius=8.0, noise=0.01, seed=11)
+    with solver.Solver(**wl.params()) as s:
+        s.init_fields(_f32(wl.phi0()), _f32(wl.u0()))
+        s.step(10)
+        state = s.get_state()
+        s.step(15)
+        a = s.get_state()
+        s.set_state(*state, step=10)
+        assert s.step_count == 10
+        s.step(15)
+        b = s.get_state()
+        assert s.step_count == 25
+    for x, y in zip(a, b):
+        assert np.array_equal(x, y)
+
+
+def test_device_pointers_match_host_pointers():
+    import torch
+    wl = inputs.static_droplet(L=20, radius=5.0, noise=0.01, seed=2)
+    phi0, u0 = _f32(wl.phi0()), _f32(wl.u0())
+    host = _gpu_run(wl, 5)
+    with solver.Solver(**wl.params()) as s:
+        s.init_fields(torch.from_numpy(phi0).cuda().reshape(-1), torch.from_numpy(u0).cuda().reshape(-1))
+        s.step(5)
+        out = [torch.empty(n, device="cuda") for n in (s.n, 3 * s.n, s.n)]
+        s.read_fields(*out)
+        torch.cuda.synchronize()
+    for a, b in zip(host[:3], out):
+        assert np.array_equal(a.reshape(-1), b.cpu().numpy())
+
+
+# -- error paths ----------------------------------------------------------------------------------
+
+def test_step_before_init_and_nonfinite_detection():
+    wl = inputs.static_droplet(L=16, radius=4.0)
+    with solver.Solver(**wl.params()) as s:
+        with pytest.raises(solver.LbmError) as e:
+            s.step(1)
+        assert e.value.status == -6
+        phi0 = _f32(wl.phi0())
+        phi0[3, 4, 5] = np.nan
+        s.init_fields(phi0, _f32(wl.u0()))
+        s.step(2)
+        with pytest.raises(solver.LbmError) as e:
+            s.observables()
+        assert e.value.status == -4
+        o = s.observables(allow_nonfinite=True)
+        assert o["n_nonfinite"] > 0
+
+
+# -- the benchmark workload at full size, in the benchmark's launch configuration --------------
+
+def test_rising_bubble_full_size_two_steps():
+    wl = inputs.rising_bubble()          # 128 x 128 x 256, walls on z, ratios 1000 / 100
+    P, ref = _oracle_run(wl, 2)
+    gpu = _gpu_run(wl, 2)
+    dphi, du, dp = _compare(gpu, P, ref)
+    print(f"rising bubble 128x128x256, 2 steps: {dphi:.3e} {du:.3e} {dp:.3e}")
+    assert dphi <= TOL_PHI
+    # at rest after two steps velocities are ~1e-6: compare against the velocity scale sqrt(gR)
+    assert np.abs(gpu[1] - ref.u).max() <= TOL_U * 0.04
+    assert dp <= TOL_P
+
+
+# -- long runs: integral observables within 0.5% ---------------------------------------------------
+
+def test_long_run_small_rising_bubble_observables():
+    wl = inputs.rising_bubble(nx=24, ny=24, nz=96, R=5.0, zc=14.0, Eo=10.0, Mo=1e-2, rho_ratio=100.0,
+                              mu_ratio=10.0)
+    nsteps = 800
+    P, ref = _oracle_run(wl, nsteps)
+    gpu = _gpu_run(wl, nsteps)
+    o, obs = oracle.observables(P, ref), gpu[4]
+    rise_o = o["centroid_gas"][2] - 14.0
+    rise_g = obs["centroid_gas"][2] - 14.0
+    print(f"bubble rise oracle {rise_o:.5f} gpu {rise_g:.5f}; vel {o['vel_gas'][2]:.3e} {obs['vel_gas'][2]:.3e}")
+    assert rise_o > 0.1
+    assert abs(rise_g / rise_o - 1) < 5e-3
+    assert abs(obs["vel_gas"][2] / o["vel_gas"][2] - 1) < 5e-3
+    assert abs(obs["mass"] / o["mass"] - 1) < 5e-3
+    assert abs(obs["sum_phi"] / o["sum_phi"] - 1) < 5e-3
+
+
+def test_laplace_law_on_gpu():
+    """Static droplet, 48^3, R = 12: p_in - p_out -> 2 sigma / R_eff (closed form)."""
+    wl = inputs.static_droplet(L=48, radius=12.0)
+    with solver.Solver(**wl.params()) as s:
+        s.init_fields(_f32(wl.phi0()), _f32(wl.u0()))
+        s.step(4000)
+        o = s.observables()
+    reff = (3 * o["sum_phi"] / (4 * math.pi)) ** (1 / 3)
+    ratio = (o["p_liq"] - o["p_gas"]) / (2 * wl.sigma / reff)
+    print(f"Laplace 48^3 R=12: dp ratio {ratio:.4f}, umax {o['umax']:.2e}")
+    assert abs(ratio - 1) < 0.05
