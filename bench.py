@@ -235,7 +235,8 @@ def main():
     s = solver.Solver(stream=stream, **wl.params())
     phi0 = np.ascontiguousarray(wl.phi0(), np.float32)
     u0 = np.ascontiguousarray(wl.u0(), np.float32)
-    s.init_fields(phi0, u0)
+    ps0 = np.ascontiguousarray(wl.pstar0(), np.float32)
+    s.init_fields(phi0, u0, ps0)
     s.step(args.warmup)
     torch.cuda.synchronize()
 
@@ -264,12 +265,13 @@ def main():
     # ---- end to end through the public API from pinned host buffers --------------------------
     phi_h = torch.from_numpy(phi0.reshape(-1)).pin_memory().numpy()
     u_h = torch.from_numpy(u0.reshape(-1)).pin_memory().numpy()
+    ps_h = torch.from_numpy(ps0.reshape(-1)).pin_memory().numpy()
     outs = [torch.empty(n, dtype=torch.float32).pin_memory().numpy() for n in (N, 3 * N, N)]
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    s.init_fields(phi_h, u_h)
+    s.init_fields(phi_h, u_h, ps_h)
     s.step(args.steps)
     obs_e2e = s.observables(allow_nonfinite=True)
     s.read_fields(*outs)
@@ -312,7 +314,7 @@ def main():
                      "kernel": "fused_step_kernel", "bytes_per_lup": BYTES_PER_LUP,
                      "peak_source": f"{peak_src} hbm_gbs"},
         "e2e": {"value": world * N * args.steps / e2e_s / 1e6, "unit": "MLUPS",
-                "h2d_bytes_per_step": 4 * 4 * N / args.steps,
+                "h2d_bytes_per_step": 5 * 4 * N / args.steps,
                 "d2h_bytes_per_step": (5 * 4 * N + 8 * 64) / args.steps,
                 "includes": "init_fields from pinned host, K steps, observables, read_fields to pinned host"},
         "gpu_launches": args.steps,

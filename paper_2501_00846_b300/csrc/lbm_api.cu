@@ -277,7 +277,7 @@ lbm_status lbm_observables(lbm_ctx *ctx, lbm_obs *out)
     if (!out) return fail(LBM_ERR_ARG, "out is NULL");
     if (!ctx->initialized) return fail(LBM_ERR_STATE, "lbm_observables before lbm_init_fields");
     const int c = ctx->cur;
-    CUDA_TRY(tslb::launch_observables(ctx->G, ctx->P, ctx->g[c], ctx->phi[c], ctx->u[c], ctx->partials, ctx->nblocks,
+    CUDA_TRY(tslb::launch_observables(ctx->G, ctx->prm.rho_l, ctx->prm.rho_g, ctx->g[c], ctx->phi[c], ctx->u[c], ctx->partials, ctx->nblocks,
                                       ctx->result, ctx->stream));
     CUDA_TRY(cudaMemcpyAsync(ctx->h_result, ctx->result, tslb::kObsFields * sizeof(double), cudaMemcpyDeviceToHost,
                              ctx->stream));

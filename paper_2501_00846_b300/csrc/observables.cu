@@ -31,7 +31,8 @@ __device__ __forceinline__ double combine(int f, double a, double b)
 
 constexpr int kThreads = 256;
 
-__global__ void __launch_bounds__(kThreads) obs_partial_kernel(Grid G, Phys P, const float *__restrict__ g,
+__global__ void __launch_bounds__(kThreads) obs_partial_kernel(Grid G, double rho_g, double drho,
+                                                               const float *__restrict__ g,
                                                                const float *__restrict__ phi,
                                                                const float *__restrict__ u,
                                                                double *__restrict__ partials)
@@ -57,7 +58,7 @@ __global__ void __launch_bounds__(kThreads) obs_partial_kernel(Grid G, Phys P, c
             r[F_NONFIN] += 1.0;
             continue;
         }
-        const double rho = (double)P.rho_g + ph * (double)P.drho;
+        const double rho = rho_g + ph * drho;
         const double gas = 1.0 - ph;
         r[F_SUM_PHI] += ph;
         r[F_SUM_GAS] += gas;
@@ -123,10 +124,10 @@ int observables_blocks(const Grid &G)
     return (int)(need < 148 * 8 ? need : 148 * 8);
 }
 
-cudaError_t launch_observables(const Grid &G, const Phys &P, const float *g, const float *phi, const float *u,
-                               double *partials, int nblocks, double *result, cudaStream_t s)
+cudaError_t launch_observables(const Grid &G, double rho_l, double rho_g, const float *g, const float *phi,
+                               const float *u, double *partials, int nblocks, double *result, cudaStream_t s)
 {
-    obs_partial_kernel<<<nblocks, kThreads, 0, s>>>(G, P, g, phi, u, partials);
+    obs_partial_kernel<<<nblocks, kThreads, 0, s>>>(G, rho_g, rho_l - rho_g, g, phi, u, partials);
     obs_final_kernel<<<1, 32, 0, s>>>(partials, nblocks, result);
     return cudaGetLastError();
 }

@@ -156,14 +156,8 @@ __global__ void __launch_bounds__(NT, 2) fused_step_kernel(Grid G, Phys P, StepA
                     float psi[27];
 #pragma unroll
                     for (int i = 0; i < 27; ++i) psi[i] = ph[cz(i) + 1][c3 + cy(i) * R3X + cx(i)];
-                    float gx = 0.f, gy = 0.f, gz = 0.f;
-#pragma unroll
-                    for (int i = 0; i < 27; ++i) {
-                        const float w3 = 3.0f * wgt(i);
-                        if (cx(i)) gx = fmaf(cx(i) * w3, psi[i], gx);
-                        if (cy(i)) gy = fmaf(cy(i) * w3, psi[i], gy);
-                        if (cz(i)) gz = fmaf(cz(i) * w3, psi[i], gz);
-                    }
+                    float gx, gy, gz;
+                    grad27(psi, gx, gy, gz);
                     const float inv = rsqrtf(fmaxf(gx * gx + gy * gy + gz * gz, kNormalEps * kNormalEps));
                     const float p = psi[13];
                     const float sh = P.kac * p * (1.0f - p) * inv;
@@ -187,7 +181,7 @@ __global__ void __launch_bounds__(NT, 2) fused_step_kernel(Grid G, Phys P, StepA
                     const int ry = t / R1X, rx = t - ry * R1X;
                     const int c2 = (ry + 1) * R2X + rx + 1;
                     const int c3 = (ry + 2) * R3X + rx + 2;
-                    float div = 0.f, lap = 0.f;
+                    float div = 0.f;
 #pragma unroll
                     for (int i = 0; i < 27; ++i) {
                         if (i == 13) continue;
@@ -196,10 +190,12 @@ __global__ void __launch_bounds__(NT, 2) fused_step_kernel(Grid G, Phys P, StepA
                         if (cx(i)) div = fmaf(cx(i) * w3, wp[0], div);
                         if (cy(i)) div = fmaf(cy(i) * w3, wp[N2], div);
                         if (cz(i)) div = fmaf(cz(i) * w3, wp[2 * N2], div);
-                        lap = fmaf(6.0f * wgt(i), ph[cz(i) + 1][c3 + cy(i) * R3X + cx(i)], lap);
                     }
-                    const float p0 = ph[1][c3];
-                    lap = fmaf(-38.0f / 9.0f, p0, lap);
+                    float psi[27];
+#pragma unroll
+                    for (int i = 0; i < 27; ++i) psi[i] = ph[cz(i) + 1][c3 + cy(i) * R3X + cx(i)];
+                    const float p0 = psi[13];
+                    const float lap = lap27(psi);
                     dst[t] = p0 - div + P.mob * lap;
                 }
             }

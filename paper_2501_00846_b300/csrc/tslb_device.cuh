@@ -43,22 +43,36 @@ constexpr float kNormalEps = 1e-9f;
 
 // Isotropic gradient and Laplacian of a scalar on the 27-point stencil (paper Section "Model
 // extension", finite-difference formulas; Laplacian read as (2/cs^2) sum_{i!=0} w_i (psi_i - psi_0)).
-// psi[i] holds psi(x + c_i).
-__device__ __forceinline__ void grad_lap27(const float (&psi)[27], float &gx, float &gy, float &gz, float &lap)
+// psi[i] holds psi(x + c_i).  Evaluated over opposite pairs (c, -c) from differences:
+//   grad = 3 sum_pairs w c (psi_c - psi_-c),   lap = 6 sum_pairs w ((psi_c - psi_0) + (psi_-c - psi_0))
+// The differences psi_c - psi_0 are exact in FP32 for neighbouring values of a smooth field, so the
+// Laplacian carries no cancellation error of the size of psi itself.
+__device__ __forceinline__ void grad27(const float (&psi)[27], float &gx, float &gy, float &gz)
 {
     gx = gy = gz = 0.0f;
+#pragma unroll
+    for (int i = 0; i < 13; ++i) {
+        const float a = psi[i] - psi[26 - i];
+        const float w3 = 3.0f * wgt(i);
+        if (cx(i)) gx = fmaf(cx(i) * w3, a, gx);
+        if (cy(i)) gy = fmaf(cy(i) * w3, a, gy);
+        if (cz(i)) gz = fmaf(cz(i) * w3, a, gz);
+    }
+}
+
+__device__ __forceinline__ float lap27(const float (&psi)[27])
+{
+    const float p0 = psi[13];
     float l = 0.0f;
 #pragma unroll
-    for (int i = 0; i < 27; ++i) {
-        if (i == 13) continue;
-        const float w3 = 3.0f * wgt(i);
-        if (cx(i)) gx = fmaf(cx(i) * w3, psi[i], gx);
-        if (cy(i)) gy = fmaf(cy(i) * w3, psi[i], gy);
-        if (cz(i)) gz = fmaf(cz(i) * w3, psi[i], gz);
-        l = fmaf(6.0f * wgt(i), psi[i], l);
-    }
-    // sum_{i != 0} 6 w_i = 6 (1 - 8/27) = 38/9
-    lap = fmaf(-38.0f / 9.0f, psi[13], l);
+    for (int i = 0; i < 13; ++i) l = fmaf(6.0f * wgt(i), (psi[i] - p0) + (psi[26 - i] - p0), l);
+    return l;
+}
+
+__device__ __forceinline__ void grad_lap27(const float (&psi)[27], float &gx, float &gy, float &gz, float &lap)
+{
+    grad27(psi, gx, gy, gz);
+    lap = lap27(psi);
 }
 
 // Macroscopic update and third-order regularised collision of one node.

@@ -34,7 +34,8 @@ cudaError_t launch_pressure(const Grid &G, const Phys &P, const float *g, const 
 // FP64 reductions: number of doubles in one partial record, and the two-pass reduction.
 constexpr int kObsFields = 32;
 int observables_blocks(const Grid &G);
-cudaError_t launch_observables(const Grid &G, const Phys &P, const float *g, const float *phi, const float *u,
-                               double *partials, int nblocks, double *result, cudaStream_t s);
+// rho_l, rho_g in FP64 so the mass sum uses the exact parameter values.
+cudaError_t launch_observables(const Grid &G, double rho_l, double rho_g, const float *g, const float *phi,
+                               const float *u, double *partials, int nblocks, double *result, cudaStream_t s);
 
 }  // namespace tslb

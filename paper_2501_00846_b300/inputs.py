@@ -116,6 +116,7 @@ class Workload:
     radius: float
     noise: float = 0.0         # amplitude of the seeded Fourier velocity
     seed: int = 1234
+    balanced_p0: bool = True   # start from pstar0() (Laplace + hydrostatic) instead of p* = 0
 
     @property
     def n(self):
@@ -135,6 +136,35 @@ class Workload:
             return np.zeros((3, self.nz, self.ny, self.nx))
         u = fourier_velocity(self.nx, self.ny, self.nz, amplitude=self.noise, seed=self.seed)
         return wall_damp(u, self.nz) if self.wall_z else u
+
+    def inside(self):
+        """Indicator of the dispersed phase: phi for a droplet, 1 - phi for a bubble."""
+        phi = self.phi0()
+        return phi if self.kind == "droplet" else 1.0 - phi
+
+    def pressure0(self):
+        """Initial pressure p0 of the undeformed dispersed sphere in mechanical balance: the
+        Laplace jump 2 sigma / R inside it, plus the hydrostatic head of the body force
+        (rho - rho_ref) g in each phase, taken about the sphere's centre."""
+        chi = self.inside()
+        x, y, z = _grid(self.nx, self.ny, self.nz)
+        per = (True, True, not self.wall_z)
+        r = [_min_image(c - c0, n, pp) for c, c0, n, pp in
+             zip((x, y, z), self.center, (self.nx, self.ny, self.nz), per)]
+        head = sum(self.gravity[a] * r[a] for a in range(3))
+        rho_in, rho_out = (self.rho_l, self.rho_g) if self.kind == "droplet" else (self.rho_g, self.rho_l)
+        return (2.0 * self.sigma / self.radius) * chi + ((rho_in - self.rho_ref) * chi
+                                                         + (rho_out - self.rho_ref) * (1.0 - chi)) * head
+
+    def pstar0(self):
+        """Initial non-dimensional pressure p*0 = p0 / (rho cs^2), with rho interpolated in phi."""
+        phi = self.phi0()
+        rho = self.rho_l * phi + (1.0 - phi) * self.rho_g
+        return 3.0 * self.pressure0() / rho
+
+    def pstar_init(self):
+        """p*0 handed to the initialisation: pstar0() or None (p* = 0)."""
+        return self.pstar0() if self.balanced_p0 else None
 
     def params(self) -> dict:
         return dict(nx=self.nx, ny=self.ny, nz=self.nz, wall_z=self.wall_z, rho_l=self.rho_l,

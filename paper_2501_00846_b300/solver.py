@@ -241,7 +241,9 @@ class Solver:
 
 
 def from_workload(wl, stream=None) -> Solver:
-    """Solver for an inputs.Workload, initialised with its seeded phi0/u0 (FP64 -> FP32)."""
+    """Solver for an inputs.Workload, initialised with its seeded phi0, u0 and p*0 (FP64 -> FP32)."""
     s = Solver(stream=stream, **wl.params())
-    s.init_fields(np.ascontiguousarray(wl.phi0(), np.float32), np.ascontiguousarray(wl.u0(), np.float32))
+    ps = wl.pstar_init()
+    s.init_fields(np.ascontiguousarray(wl.phi0(), np.float32), np.ascontiguousarray(wl.u0(), np.float32),
+                  None if ps is None else np.ascontiguousarray(ps, np.float32))
     return s

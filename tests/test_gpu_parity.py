@@ -32,13 +32,18 @@ def _f32(a):
     return np.ascontiguousarray(a, dtype=np.float32)
 
 
+def _pstar0(wl):
+    ps = wl.pstar_init()
+    return None if ps is None else _f32(ps)
+
+
 def _gpu_run(wl, nsteps, path=0, chunk=0, phi0=None, u0=None):
     phi0 = wl.phi0() if phi0 is None else phi0
     u0 = wl.u0() if u0 is None else u0
     with solver.Solver(**wl.params()) as s:
         s.set_path(path)
         s.set_chunk(chunk)
-        s.init_fields(_f32(phi0), _f32(u0))
+        s.init_fields(_f32(phi0), _f32(u0), _pstar0(wl))
         s.step(nsteps)
         phi, u, p = s.read_fields()
         g, _, _ = s.get_state()
@@ -50,7 +55,9 @@ def _oracle_run(wl, nsteps, phi0=None, u0=None):
     phi0 = wl.phi0() if phi0 is None else phi0
     u0 = wl.u0() if u0 is None else u0
     P = oracle.Params(**wl.params())
-    s = oracle.run(P, oracle.init(P, _f32(phi0).astype(np.float64), _f32(u0).astype(np.float64)), nsteps)
+    ps = _pstar0(wl)
+    s = oracle.run(P, oracle.init(P, _f32(phi0).astype(np.float64), _f32(u0).astype(np.float64),
+                                  None if ps is None else ps.astype(np.float64)), nsteps)
     return P, s
 
 
@@ -137,9 +144,9 @@ def test_ragged_walled_bubble_ratio1000(path):
 
 
 def test_ragged_periodic_droplet_across_boundary():
-    wl = inputs.static_droplet(L=24, radius=7.0, noise=0.02, seed=5)
-    wl.nx, wl.ny, wl.nz = 45, 13, 27
-    wl.center = (2.0, 11.5, 25.0)            # wraps around all three periodic boundaries
+    wl = inputs.static_droplet(L=24, radius=6.0, noise=0.01, seed=5)
+    wl.nx, wl.ny, wl.nz = 45, 29, 27
+    wl.center = (2.0, 27.5, 25.0)            # wraps around all three periodic boundaries
     P, ref = _oracle_run(wl, 80)
     gpu = _gpu_run(wl, 80)
     _assert_parity(gpu, P, ref, "ragged periodic droplet")
@@ -149,7 +156,8 @@ def test_minimum_box():
     wl = inputs.static_droplet(L=4, radius=1.5, noise=0.01, seed=3)
     P, ref = _oracle_run(wl, 10)
     _assert_parity(_gpu_run(wl, 10), P, ref, "4^3 box")
-    wl = inputs.rising_bubble(nx=4, ny=5, nz=4, R=1.5, zc=2.0)
+    wl = inputs.static_droplet(L=4, radius=1.5, noise=0.01, seed=3)
+    wl.ny, wl.wall_z, wl.gravity = 5, 1, (0.0, 0.0, -1e-5)
     P, ref = _oracle_run(wl, 10)
     _assert_parity(_gpu_run(wl, 10), P, ref, "4x5x4 walled box")
 
@@ -168,7 +176,7 @@ def test_chunk_size_does_not_change_results():
 def test_checkpoint_resume_bit_exact():
     wl = inputs.static_droplet(L=32, radius=8.0, noise=0.01, seed=11)
     with solver.Solver(**wl.params()) as s:
-        s.init_fields(_f32(wl.phi0()), _f32(wl.u0()))
+        s.init_fields(_f32(wl.phi0()), _f32(wl.u0()), _pstar0(wl))
         s.step(10)
         state = s.get_state()
         s.step(15)
@@ -187,8 +195,9 @@ def test_device_pointers_match_host_pointers():
     wl = inputs.static_droplet(L=20, radius=5.0, noise=0.01, seed=2)
     phi0, u0 = _f32(wl.phi0()), _f32(wl.u0())
     host = _gpu_run(wl, 5)
+    ps = torch.from_numpy(_pstar0(wl)).cuda().reshape(-1)
     with solver.Solver(**wl.params()) as s:
-        s.init_fields(torch.from_numpy(phi0).cuda().reshape(-1), torch.from_numpy(u0).cuda().reshape(-1))
+        s.init_fields(torch.from_numpy(phi0).cuda().reshape(-1), torch.from_numpy(u0).cuda().reshape(-1), ps)
         s.step(5)
         out = [torch.empty(n, device="cuda") for n in (s.n, 3 * s.n, s.n)]
         s.read_fields(*out)
@@ -253,7 +262,7 @@ def test_laplace_law_on_gpu():
     """Static droplet, 48^3, R = 12: p_in - p_out -> 2 sigma / R_eff (closed form)."""
     wl = inputs.static_droplet(L=48, radius=12.0)
     with solver.Solver(**wl.params()) as s:
-        s.init_fields(_f32(wl.phi0()), _f32(wl.u0()))
+        s.init_fields(_f32(wl.phi0()), _f32(wl.u0()), _pstar0(wl))
         s.step(4000)
         o = s.observables()
     reff = (3 * o["sum_phi"] / (4 * math.pi)) ** (1 / 3)
