@@ -126,6 +126,26 @@ lbm_status lbm_step(lbm_ctx *ctx, int nsteps);
  * Returns LBM_ERR_NONFINITE when out->n_nonfinite > 0; *out is filled in that case too. */
 lbm_status lbm_observables(lbm_ctx *ctx, lbm_obs *out);
 
+/* Diagnostics of a state the caller owns, without allocating any device memory.  The paper has
+ * no counterpart: this is a library convenience.  It is for callers that cannot allocate device
+ * memory: code embedded in an application that owns the whole device heap (a fixed arena handed
+ * out at start-up, or a framework allocator that must account for every byte), and code that
+ * must not call cudaMalloc because it would synchronise the device and stall queued work.
+ *   g, phi, u   device pointers to populations (27N floats), phi (N) and ubar (3N) in the
+ *               layouts above; nx, ny, nz the box; rho_l, rho_g the phase densities
+ *   stream      cudaStream_t to run on (NULL: the legacy default stream); synchronised on return
+ *   out         filled as by lbm_observables, except out->step = 0
+ * The reduction's scratch is a fixed array of 1185 x 32 doubles (303,360 bytes) inside the
+ * library, held by every GPU that loads the library until the process exits.  Boxes of up to
+ * 2^31 - 1 nodes fit; larger boxes return LBM_ERR_ARG.  The first call on a device looks up the
+ * array's device address (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  All calls share the array and nothing in it carries over between
+ * calls, but calls whose work overlaps on the GPU (e.g. on two streams) race on it.
+ * Returns LBM_ERR_NONFINITE when out->n_nonfinite > 0 (out filled), LBM_ERR_ARG for bad
+ * arguments, LBM_ERR_CUDA if a CUDA call fails.  Calls no allocating routine. */
+lbm_status lbm_observables_noalloc(const float *g, const float *phi, const float *u, int nx, int ny,
+                                   int nz, double rho_l, double rho_g, void *stream, lbm_obs *out);
+
 /* Copy out phi (N floats), ubar (3N floats) and p = p* rho cs^2 (N floats).  Any of the three
  * pointers may be NULL.  on_device as in lbm_init_fields.  Synchronises the stream. */
 lbm_status lbm_read_fields(lbm_ctx *ctx, float *phi, float *u, float *p, int on_device);

@@ -34,6 +34,11 @@ lbm_status fail(lbm_status s, const char *fmt, ...)
 
 }  // namespace
 
+namespace tslb {
+// Record a failure message for lbm_last_error() from another translation unit.
+void set_last_error(const char *msg) { snprintf(g_last_error, sizeof g_last_error, "%s", msg); }
+}  // namespace tslb
+
 struct lbm_ctx {
     lbm_params prm;
     tslb::Grid G;

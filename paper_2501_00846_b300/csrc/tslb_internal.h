@@ -38,4 +38,7 @@ int observables_blocks(const Grid &G);
 cudaError_t launch_observables(const Grid &G, double rho_l, double rho_g, const float *g, const float *phi,
                                const float *u, double *partials, int nblocks, double *result, cudaStream_t s);
 
+// Message returned by lbm_last_error() for the calling thread.
+void set_last_error(const char *msg);
+
 }  // namespace tslb

@@ -93,6 +93,8 @@ def load(path: str = LIB_PATH):
         "lbm_status_string": ([i], ctypes.c_char_p),
         "lbm_last_error": ([], ctypes.c_char_p),
         "lbm_abi_version": ([], i),
+        "lbm_observables_noalloc": ([fp, fp, fp, i, i, i, ctypes.c_double, ctypes.c_double, vp,
+                                     ctypes.POINTER(LbmObs)], i),
     }
     for name, (args, res) in sigs.items():
         fn = getattr(L, name)
