@@ -34,8 +34,13 @@ sys.path.insert(0, ROOT)
 BYTES_PER_LUP = 248          # FP32: (27 + 1 + 3) floats read + the same written
 FALLBACK_HBM_GBS = 6400.0
 METRIC = "MLUPS & % HBM peak: coupled LBM+Allen-Cahn step, FP32 vs BF16 store"
-KERNEL_SOURCES = ["paper_2501_00846_b300/csrc/step_fused.cu", "paper_2501_00846_b300/csrc/tslb_device.cuh",
-                  "paper_2501_00846_b300/csrc/tslb_internal.h"]
+# sources that define each step kernel's device code (the profile of a kernel is reused only while
+# these files are unchanged)
+KERNEL_SOURCES = {
+    "fused_step_kernel": ["paper_2501_00846_b300/csrc/step_fused.cu", "paper_2501_00846_b300/csrc/tslb_device.cuh"],
+    "fused2_kernel": ["paper_2501_00846_b300/csrc/step_fused2.cu", "paper_2501_00846_b300/csrc/tslb_device.cuh"],
+}
+KERNEL_NAMES = {0: "fused2_kernel", 1: "ac_flux+ac_update+lbm", 2: "fused_step_kernel"}
 
 
 def workload(name):
@@ -48,18 +53,21 @@ def workload(name):
     raise SystemExit(f"unknown workload {name}")
 
 
-def kernel_source_hash():
+def kernel_source_hash(kernel):
     h = hashlib.sha256()
-    for rel in KERNEL_SOURCES:
+    for rel in KERNEL_SOURCES[kernel]:
         with open(os.path.join(ROOT, rel), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()
 
 
-def measured_traffic(wl_name, nodes):
-    """DRAM bytes per launch of the fused kernel from the committed ncu summary, if its source
-    hash matches the current kernel sources (else None)."""
-    path = os.path.join(ROOT, "profiles", f"fused_step_{wl_name}.txt")
+def measured_traffic(kernel, wl_name, nodes):
+    """DRAM bytes per launch of a step kernel from the committed ncu summary
+    profiles/<kernel>_<workload>.txt, if its source hash matches the current kernel sources
+    (else None)."""
+    if kernel not in KERNEL_SOURCES:
+        return None
+    path = os.path.join(ROOT, "profiles", f"{kernel}_{wl_name}.txt")
     if not os.path.exists(path):
         return None
     kv = {}
@@ -67,7 +75,7 @@ def measured_traffic(wl_name, nodes):
         if ":" in line and not line.startswith("#"):
             k, v = line.split(":", 1)
             kv[k.strip()] = v.strip()
-    if kv.get("source_sha256") != kernel_source_hash():
+    if kv.get("source_sha256") != kernel_source_hash(kernel):
         return None
     try:
         b = float(kv["dram_bytes_per_launch"])
@@ -207,6 +215,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="b300", choices=["b300", "reference"])
     ap.add_argument("--workload", default="rising_bubble")
+    ap.add_argument("--path", type=int, default=0,
+                    help="step kernel: 0 fused separable (default), 1 unfused, 2 fused windowed")
+    ap.add_argument("--split", type=int, default=0, help="work split of the fused kernel (0 = default)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
@@ -233,6 +244,8 @@ def main():
     N = wl.n
     stream = torch.cuda.current_stream()
     s = solver.Solver(stream=stream, **wl.params())
+    s.set_path(args.path)
+    s.set_split(args.split)
     phi0 = np.ascontiguousarray(wl.phi0(), np.float32)
     u0 = np.ascontiguousarray(wl.u0(), np.float32)
     ps0 = np.ascontiguousarray(wl.pstar0(), np.float32)
@@ -291,7 +304,8 @@ def main():
     launch_s = ms * 1e-3 / args.steps
     achieved = BYTES_PER_LUP * N / launch_s / 1e9
     peak, peak_src = hbm_peak()
-    traffic = measured_traffic(args.workload, N)
+    kernel = KERNEL_NAMES[args.path]
+    traffic = measured_traffic(kernel, args.workload, N)
     line = {
         "metric": METRIC,
         "value": value,
@@ -305,19 +319,20 @@ def main():
         "vs_baseline": None,
         "dtype": "f32",
         "data": "synthetic",
-        "config": {"workload": wl.name, "nodes": N, "store": "fp32",
+        "config": {"workload": wl.name, "nodes": N, "store": "fp32", "path": args.path, "split": args.split,
                    "l2": "state 1.04 GB per copy >> 126 MB L2: inputs larger than L2, no flush",
                    "parallelism": f"replicas x{world}", "sum_phi_after": obs["sum_phi"],
                    "nonfinite_after": obs["n_nonfinite"]},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
-                     "kernel": "fused_step_kernel", "bytes_per_lup": BYTES_PER_LUP,
+                     "kernel": kernel,
+                     "bytes_per_lup": BYTES_PER_LUP,
                      "peak_source": f"{peak_src} hbm_gbs"},
         "e2e": {"value": world * N * args.steps / e2e_s / 1e6, "unit": "MLUPS",
                 "h2d_bytes_per_step": 5 * 4 * N / args.steps,
                 "d2h_bytes_per_step": (5 * 4 * N + 8 * 64) / args.steps,
                 "includes": "init_fields from pinned host, K steps, observables, read_fields to pinned host"},
-        "gpu_launches": args.steps,
+        "gpu_launches": args.steps * (3 if args.path == 1 else 1),
         "clocks": clocks,
     }
     if world == 1 and not args.no_cpu_baseline:

@@ -164,15 +164,19 @@ lbm_status lbm_synchronize(lbm_ctx *ctx);
 long long lbm_num_nodes(const lbm_ctx *ctx);
 long long lbm_step_count(const lbm_ctx *ctx);
 
-/* Select the step kernel: 0 = one fused kernel per step (default), 1 = the unfused
- * three-kernel path (Allen–Cahn flux, Allen–Cahn update, lattice Boltzmann) kept for
- * cross-checks.  LBM_ERR_ARG for other values. */
+/* Select the step kernel (all three compute the same step; they differ in data movement):
+ *   0  fused, separable stencils, persistent CTAs (default, fastest)
+ *   1  unfused: Allen–Cahn flux, Allen–Cahn update and lattice Boltzmann as three kernels
+ *   2  fused, 27-point shared-memory stencils over a z-marching window
+ * LBM_ERR_ARG for other values. */
 lbm_status lbm_set_path(lbm_ctx *ctx, int path);
 
-/* Fused-kernel tuning: z planes marched by one CTA; 0 restores the library's default for the
- * grid.  Results are bit-identical for every value (the halo planes each CTA recomputes use the
- * same arithmetic as their owners).  LBM_ERR_ARG for negative values. */
-lbm_status lbm_set_chunk(lbm_ctx *ctx, int z_chunk);
+/* Work split of the fused kernels: for path 0 the number of CTAs the (column, plane) range is
+ * divided among; for path 2 the z planes marched by one CTA.  0 restores the library's default
+ * (path 0: one CTA per resident slot of the GPU).  Results are bit-identical for every value:
+ * the halo points each CTA recomputes use the same arithmetic as their owners.  LBM_ERR_ARG
+ * for negative values. */
+lbm_status lbm_set_split(lbm_ctx *ctx, int split);
 
 /* Free every resource of ctx; NULL-safe.  Waits for the context's stream first. */
 void lbm_destroy(lbm_ctx *ctx);

@@ -57,7 +57,7 @@ struct lbm_ctx {
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     int path = 0;
-    int chunk = 0;
+    int split = 0;
 };
 
 namespace {
@@ -219,16 +219,17 @@ long long lbm_step_count(const lbm_ctx *ctx) { return ctx ? ctx->step : 0; }
 lbm_status lbm_set_path(lbm_ctx *ctx, int path)
 {
     if (!ctx) return fail(LBM_ERR_ARG, "context is NULL");
-    if (path != 0 && path != 1) return fail(LBM_ERR_ARG, "path must be 0 (fused) or 1 (unfused)");
+    if (path < 0 || path > 2)
+        return fail(LBM_ERR_ARG, "path must be 0 (fused, separable), 1 (unfused) or 2 (fused, windowed)");
     ctx->path = path;
     return LBM_OK;
 }
 
-lbm_status lbm_set_chunk(lbm_ctx *ctx, int z_chunk)
+lbm_status lbm_set_split(lbm_ctx *ctx, int split)
 {
     if (!ctx) return fail(LBM_ERR_ARG, "context is NULL");
-    if (z_chunk < 0) return fail(LBM_ERR_ARG, "z_chunk must be >= 0");
-    ctx->chunk = z_chunk;
+    if (split < 0) return fail(LBM_ERR_ARG, "split must be >= 0");
+    ctx->split = split;
     return LBM_OK;
 }
 
@@ -260,8 +261,9 @@ lbm_status lbm_step(lbm_ctx *ctx, int nsteps)
     for (int s = 0; s < nsteps; ++s) {
         const int a = ctx->cur, b = 1 - ctx->cur;
         tslb::StepArgs args{ctx->g[a], ctx->g[b], ctx->phi[a], ctx->phi[b], ctx->u[a], ctx->u[b], ctx->flux};
-        cudaError_t e = ctx->path == 0 ? tslb::launch_step_fused(ctx->G, ctx->P, args, ctx->chunk, ctx->stream)
-                                       : tslb::launch_step_unfused(ctx->G, ctx->P, args, ctx->stream);
+        cudaError_t e = ctx->path == 0   ? tslb::launch_step_fused2(ctx->G, ctx->P, args, ctx->split, ctx->stream)
+                         : ctx->path == 2 ? tslb::launch_step_fused(ctx->G, ctx->P, args, ctx->split, ctx->stream)
+                                          : tslb::launch_step_unfused(ctx->G, ctx->P, args, ctx->stream);
         if (e != cudaSuccess) return fail(LBM_ERR_CUDA, "step launch failed: %s", cudaGetErrorString(e));
         ctx->cur = b;
         ++ctx->step;

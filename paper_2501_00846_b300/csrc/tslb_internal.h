@@ -21,6 +21,9 @@ struct StepArgs {
 cudaError_t launch_step_unfused(const Grid &G, const Phys &P, const StepArgs &a, cudaStream_t s);
 cudaError_t launch_step_fused(const Grid &G, const Phys &P, const StepArgs &a, int tz, cudaStream_t s);
 
+// Separable-stencil fused step with persistent CTAs; ctas <= 0 selects one CTA per resident slot.
+cudaError_t launch_step_fused2(const Grid &G, const Phys &P, const StepArgs &a, int ctas, cudaStream_t s);
+
 // Default z-chunk of the fused kernel for a grid.
 int fused_default_chunk(const Grid &G);
 

@@ -88,7 +88,7 @@ def load(path: str = LIB_PATH):
         "lbm_num_nodes": ([vp], ll),
         "lbm_step_count": ([vp], ll),
         "lbm_set_path": ([vp, i], i),
-        "lbm_set_chunk": ([vp, i], i),
+        "lbm_set_split": ([vp, i], i),
         "lbm_destroy": ([vp], None),
         "lbm_status_string": ([i], ctypes.c_char_p),
         "lbm_last_error": ([], ctypes.c_char_p),
@@ -196,8 +196,9 @@ class Solver:
     def set_path(self, path: int):
         _check(load().lbm_set_path(self._ctx, int(path)))
 
-    def set_chunk(self, z_chunk: int):
-        _check(load().lbm_set_chunk(self._ctx, int(z_chunk)))
+    def set_split(self, split: int):
+        """CTA count (path 0) or z planes per CTA (path 2); 0 = default."""
+        _check(load().lbm_set_split(self._ctx, int(split)))
 
     @property
     def step_count(self) -> int:

@@ -22,7 +22,7 @@ def _golden(name):
 def test_rising_bubble_parameters_match_hand_derivation():
     ref = _golden("rising_bubble_params.txt")
     wl = inputs.rising_bubble()
-    p = inputs.rising_bubble_params()
+    p = inputs.rising_bubble_params(sqrt_gR=0.02)
     assert math.isclose(-wl.gravity[2], ref["g"], rel_tol=1e-12)
     assert math.isclose(wl.sigma, ref["sigma"], rel_tol=1e-12)
     assert math.isclose(p["Ga"], ref["Ga"], rel_tol=1e-5)
