@@ -46,6 +46,9 @@
  *   R11 body force (rho - rho_ref) g + G_body.
  *   R13 z walls: halfway bounce-back for populations; scalar fields mirrored about the wall;
  *       vector fields mirrored with their z component negated.
+ *   R15 the sharpening weight phi (1 - phi) is taken as max(phi (1 - phi), 0): the paper's phi
+ *       lives in [0, 1]; outside it the weight would turn the sharpening flux around exactly
+ *       where phi has an extremum and the normal is undefined.
  */
 #include <math.h>
 #include <stdlib.h>
@@ -396,7 +399,7 @@ void oracle_force_node(const oracle_params *P, const double f[Q], double phi, co
 /* ------------------------------------------------------------------------------------------ */
 /* Allen–Cahn FTCS update (interface-tracking item of the step list, readings R4, R5, R13):     */
 /*   phi^{n+1} = phi^n - div(ubar phi^n) + D lap(phi^n) - kappa_AC div(phi^n (1-phi^n) n^n)   */
-/*   kappa_AC = 4 D / delta,  n = grad(phi) / max(|grad(phi)|, 1e-12).                         */
+/*   kappa_AC = 4 D / delta,  n = grad(phi) / max(|grad(phi)|, 1e-12),  phi(1-phi) >= 0 (R15).  */
 /* ------------------------------------------------------------------------------------------ */
 void oracle_ac_update(const oracle_params *P, const double *phi, const double *ubar, double *phi_new)
 {
@@ -416,7 +419,7 @@ void oracle_ac_update(const oracle_params *P, const double *phi, const double *u
                 double den = mag > 1e-12 ? mag : 1e-12;
                 double p = phi[k];
                 for (int a = 0; a < 3; ++a)
-                    V[a * N + k] = ubar[a * N + k] * p + kac * p * (1.0 - p) * g[a] / den;
+                    V[a * N + k] = ubar[a * N + k] * p + kac * fmax(p * (1.0 - p), 0.0) * g[a] / den;
             }
 
     #pragma omp parallel for collapse(2) schedule(static)

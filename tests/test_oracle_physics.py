@@ -177,3 +177,17 @@ def test_droplet_translation():
     assert abs(dx / (U * steps) - 1) < 0.02
     assert abs(o["centroid_liq"][1] - o0["centroid_liq"][1]) < 1e-6
     assert abs(o["vel_liq"][0] / U - 1) < 0.02
+
+
+def test_sharpening_weight_vanishes_outside_unit_interval():
+    """Reading R15: outside [0, 1] the sharpening weight phi (1 - phi) is zero, so at rest the
+    Allen-Cahn update there reduces to FTCS diffusion phi + D lap(phi); inside (0, 1) it is not."""
+    rng = np.random.default_rng(17)
+    P = oracle.Params(8, 7, 6, mobility=0.1)
+    above = 1.0 + 1e-3 * rng.random(P.shape)
+    zero_u = np.zeros((3,) + P.shape)
+    np.testing.assert_allclose(oracle.ac_update(P, above, zero_u), above + 0.1 * oracle.lap(P, above), atol=1e-15)
+    below = -1e-3 * rng.random(P.shape)
+    np.testing.assert_allclose(oracle.ac_update(P, below, zero_u), below + 0.1 * oracle.lap(P, below), atol=1e-15)
+    inside = 0.5 + 0.1 * rng.random(P.shape)
+    assert np.abs(oracle.ac_update(P, inside, zero_u) - (inside + 0.1 * oracle.lap(P, inside))).max() > 1e-4
