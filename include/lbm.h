@@ -5,8 +5,8 @@
  *
  * One context owns one box of nx*ny*nz nodes on the current CUDA device.  Every entry point
  * takes plain pointers and sizes; no C++ or PyTorch type crosses this boundary.  All device
- * work is enqueued on the context's stream (lbm_params.stream, or a stream the library creates
- * when that is NULL).
+ * work is enqueued on the context's stream (lbm_params.stream; NULL is the legacy default
+ * stream, as everywhere in CUDA).
  *
  * Lattice: D3Q27, cs^2 = 1/3, dx = dt = 1.  Velocity index i = 9 (cz+1) + 3 (cy+1) + (cx+1)
  * for c_i = (cx, cy, cz) in {-1,0,1}^3; the opposite of i is 26 - i; the rest velocity is 13.
@@ -78,7 +78,7 @@ typedef struct {
     double rho_ref;       /* reference density; rho_l applies gravity to the light phase only */
     double body[3];       /* uniform body-force density (e.g. a driven channel) */
     int storage;          /* lbm_storage */
-    void *stream;         /* cudaStream_t to enqueue on; NULL: the library creates its own */
+    void *stream;         /* cudaStream_t to enqueue on; NULL: the legacy default stream */
 } lbm_params;
 
 /* Integral diagnostics, accumulated in FP64 on the device (all doubles). */
@@ -164,19 +164,29 @@ lbm_status lbm_synchronize(lbm_ctx *ctx);
 long long lbm_num_nodes(const lbm_ctx *ctx);
 long long lbm_step_count(const lbm_ctx *ctx);
 
-/* Select the step kernel (all three compute the same step; they differ in data movement):
- *   0  fused, separable stencils, persistent CTAs (default, fastest)
- *   1  unfused: Allen–Cahn flux, Allen–Cahn update and lattice Boltzmann as three kernels
- *   2  fused, 27-point shared-memory stencils over a z-marching window
+/* Select how a step is launched (all three compute the same step; they differ in data movement):
+ *   0  two kernels (default, fastest): a z-marching Allen–Cahn kernel with separable stencils
+ *      writes phi^{n+1}, then the one-thread-per-node lattice Boltzmann kernel
+ *   1  three kernels: Allen–Cahn flux, Allen–Cahn update, lattice Boltzmann (plain 27-point
+ *      stencils from global memory; the simplest form, kept as a cross-check)
+ *   2  one fused kernel: the Allen–Cahn stencils of a z-marching shared-memory window and the
+ *      lattice Boltzmann update of each plane in the same kernel
  * LBM_ERR_ARG for other values. */
 lbm_status lbm_set_path(lbm_ctx *ctx, int path);
 
-/* Work split of the fused kernels: for path 0 the number of CTAs the (column, plane) range is
- * divided among; for path 2 the z planes marched by one CTA.  0 restores the library's default
- * (path 0: one CTA per resident slot of the GPU).  Results are bit-identical for every value:
+/* Work split of the z-marching kernels (paths 0 and 2): the number of z chunks each 32 x 8
+ * column tile is cut into.  0 restores the library's default.
+ * Results are bit-identical for every value:
  * the halo points each CTA recomputes use the same arithmetic as their owners.  LBM_ERR_ARG
  * for negative values. */
 lbm_status lbm_set_split(lbm_ctx *ctx, int split);
+
+/* Profiling aid: launch one kernel of the two-kernel step nrep times on the context's stream
+ * without advancing the state (phase 0: the Allen–Cahn kernel, reading phi^n and ubar^n and
+ * writing the idle phi buffer; phase 1: the lattice Boltzmann kernel, reading g^n, that phi buffer
+ * and ubar^n and writing the idle g and ubar buffers).  The next lbm_step overwrites those idle
+ * buffers.  Asynchronous.  LBM_ERR_STATE before lbm_init_fields. */
+lbm_status lbm_run_phase(lbm_ctx *ctx, int phase, int nrep);
 
 /* Free every resource of ctx; NULL-safe.  Waits for the context's stream first. */
 void lbm_destroy(lbm_ctx *ctx);

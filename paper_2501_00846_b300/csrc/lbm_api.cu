@@ -55,7 +55,6 @@ struct lbm_ctx {
     long long step = 0;
     bool initialized = false;
     cudaStream_t stream = nullptr;
-    bool own_stream = false;
     int path = 0;
     int split = 0;
 };
@@ -74,7 +73,6 @@ void free_ctx(lbm_ctx *c)
     cudaFree(c->partials);
     cudaFree(c->result);
     if (c->h_result) cudaFreeHost(c->h_result);
-    if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
     delete c;
 }
 
@@ -164,16 +162,7 @@ lbm_status lbm_create(const lbm_params *params, lbm_ctx **out)
     make_consts(c);
     const size_t N = (size_t)c->G.N;
 
-    if (params->stream) {
-        c->stream = (cudaStream_t)params->stream;
-    } else {
-        cudaError_t e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
-        if (e != cudaSuccess) {
-            free_ctx(c);
-            return fail(LBM_ERR_CUDA, "cudaStreamCreate failed: %s", cudaGetErrorString(e));
-        }
-        c->own_stream = true;
-    }
+    c->stream = (cudaStream_t)params->stream;   // NULL: the legacy default stream
 
     c->nblocks = tslb::observables_blocks(c->G);
     struct {
@@ -220,7 +209,7 @@ lbm_status lbm_set_path(lbm_ctx *ctx, int path)
 {
     if (!ctx) return fail(LBM_ERR_ARG, "context is NULL");
     if (path < 0 || path > 2)
-        return fail(LBM_ERR_ARG, "path must be 0 (fused, separable), 1 (unfused) or 2 (fused, windowed)");
+        return fail(LBM_ERR_ARG, "path must be 0 (two kernels), 1 (three kernels) or 2 (one fused kernel)");
     ctx->path = path;
     return LBM_OK;
 }
@@ -261,12 +250,29 @@ lbm_status lbm_step(lbm_ctx *ctx, int nsteps)
     for (int s = 0; s < nsteps; ++s) {
         const int a = ctx->cur, b = 1 - ctx->cur;
         tslb::StepArgs args{ctx->g[a], ctx->g[b], ctx->phi[a], ctx->phi[b], ctx->u[a], ctx->u[b], ctx->flux};
-        cudaError_t e = ctx->path == 0   ? tslb::launch_step_fused2(ctx->G, ctx->P, args, ctx->split, ctx->stream)
-                         : ctx->path == 2 ? tslb::launch_step_fused(ctx->G, ctx->P, args, ctx->split, ctx->stream)
+        cudaError_t e = ctx->path == 0   ? tslb::launch_step_split(ctx->G, ctx->P, args, ctx->split, ctx->stream)
+                         : ctx->path == 2 ? tslb::launch_step_fused2(ctx->G, ctx->P, args, ctx->split, ctx->stream)
                                           : tslb::launch_step_unfused(ctx->G, ctx->P, args, ctx->stream);
         if (e != cudaSuccess) return fail(LBM_ERR_CUDA, "step launch failed: %s", cudaGetErrorString(e));
         ctx->cur = b;
         ++ctx->step;
+    }
+    return LBM_OK;
+}
+
+lbm_status lbm_run_phase(lbm_ctx *ctx, int phase, int nrep)
+{
+    if (!ctx) return fail(LBM_ERR_ARG, "context is NULL");
+    if (!ctx->initialized) return fail(LBM_ERR_STATE, "lbm_run_phase before lbm_init_fields");
+    if (phase != 0 && phase != 1) return fail(LBM_ERR_ARG, "phase must be 0 or 1");
+    if (nrep < 0) return fail(LBM_ERR_ARG, "nrep must be >= 0");
+    const int a = ctx->cur, b = 1 - ctx->cur;
+    for (int r = 0; r < nrep; ++r) {
+        cudaError_t e = phase == 0 ? tslb::launch_ac_split(ctx->G, ctx->P, ctx->phi[a], ctx->u[a], ctx->phi[b], ctx->split,
+                                                           ctx->stream)
+                                   : tslb::launch_lbm(ctx->G, ctx->P, ctx->g[a], ctx->phi[b], ctx->u[a], ctx->g[b],
+                                                      ctx->u[b], ctx->stream);
+        if (e != cudaSuccess) return fail(LBM_ERR_CUDA, "phase launch failed: %s", cudaGetErrorString(e));
     }
     return LBM_OK;
 }

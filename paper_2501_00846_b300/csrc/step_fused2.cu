@@ -24,8 +24,12 @@
 //   f. partials of phi^{n+1} at the own node (plane p-2), then the lattice Boltzmann update of
 //      the own node on plane p-3 (pull, forces, regularised collision), whose 27 population
 //      loads were issued at the top of the iteration.
-// Persistent scheduling: the (column tile, z plane) pairs, column-major, are split into equal
-// contiguous ranges, one per resident CTA; a range that crosses a column restarts the march.
+// The phi^n and ubar^n values of the next plane are loaded into registers one iteration ahead
+// (stored to shared memory at the top of the next iteration), and the own node's ubar^n with the
+// pulled populations, so no stage waits on a global load it has just issued.
+// Scheduling: the box is cut into units (column tile, z chunk of equal length); units are dealt
+// round-robin to the CTAs, so in every round all CTAs march the same z range and a tile's
+// neighbours are processed at the same time (their halo rows are then L2 hits).
 #include "tslb_internal.h"
 
 namespace tslb {
@@ -74,6 +78,7 @@ __device__ __forceinline__ float zsign(int p, int nz)
 }
 
 __device__ __forceinline__ int slot3(int p) { return (p + 9) % 3; }
+
 __device__ __forceinline__ int slot4(int p) { return (p + 8) & 3; }
 
 // 3x3 partials of a scalar plane around element `ci` of an array with row pitch RX.
@@ -91,7 +96,7 @@ __device__ __forceinline__ void partials(const float *a, int ci, float &px, floa
 }
 
 template <bool WALL>
-__global__ void __launch_bounds__(NT, 2) fused2_kernel(Grid G, Phys P, StepArgs a, long long total, int nblk)
+__global__ void __launch_bounds__(NT, 2) fused2_kernel(Grid G, Phys P, StepArgs a, int ncols, int zlen, int units)
 {
     extern __shared__ float sm[];
     float *sPhi = sm + OFF_PHI;
@@ -117,14 +122,10 @@ __global__ void __launch_bounds__(NT, 2) fused2_kernel(Grid G, Phys P, StepArgs 
         own1[k] = own2[k] && ry2[k] >= 1 && ry2[k] <= R2Y - 2 && rx2[k] >= 1 && rx2[k] <= R2X - 2;
     }
 
-    const long long wbeg = total * blockIdx.x / nblk;
-    const long long wend = total * (blockIdx.x + 1) / nblk;
-    long long w = wbeg;
-    while (w < wend) {
-        const int col = (int)(w / nz);
-        const int z0 = (int)(w - (long long)col * nz);
-        const int zend = (int)min((long long)nz, z0 + (wend - w));
-        w += zend - z0;
+    for (int unit = blockIdx.x; unit < units; unit += gridDim.x) {
+        const int col = unit % ncols;
+        const int z0 = (unit / ncols) * zlen;
+        const int zend = min(nz, z0 + zlen);
         const int x0 = (col % ncx) * TX, y0 = (col / ncx) * TY;
 
         int off3[K3], off2[K2];
@@ -146,14 +147,27 @@ __global__ void __launch_bounds__(NT, 2) fused2_kernel(Grid G, Phys P, StepArgs 
         float qx0 = 0.f, qy0 = 0.f, qs0 = 0.f, qc0 = 0.f;   // plane p-4
         float qx1 = 0.f, qy1 = 0.f, qs1 = 0.f, qc1 = 0.f;   // plane p-3
 
+        // phi^n (halo 3) of the plane loaded next, and ubar^n (own halo-2 points) of the plane
+        // before it, held in registers one iteration ahead of their use
+        float nphi[K3], nub[K2][3];
+        {
+            const int pl = zmap<WALL>(z0 - 3, nz) * nxy;
+#pragma unroll
+            for (int k = 0; k < K3; ++k)
+                nphi[k] = (tid + k * NT < N3) ? __ldg(a.phi_in + pl + off3[k]) : 0.0f;
+#pragma unroll
+            for (int k = 0; k < K2; ++k) nub[k][0] = nub[k][1] = nub[k][2] = 0.0f;
+        }
+
         const int nsteps = (zend - z0) + 6;
         for (int s = 0; s < nsteps; ++s) {
             const int p = z0 - 3 + s;
             const bool do_w = s >= 2, do_e = s >= 4, do_c = s >= 6 && active;
             const int zc = p - 3;
 
-            // pulled populations of plane zc, issued early
+            // pulled populations of plane zc and the own ubar^n, issued early
             float f[27];
+            float ubx = 0.f, uby = 0.f, ubz = 0.f;
             int kc = 0;
             if (do_c) {
                 const int zs[3] = {zmap<false>(zc - 1, nz) * nxy, zc * nxy, zmap<false>(zc + 1, nz) * nxy};
@@ -168,26 +182,43 @@ __global__ void __launch_bounds__(NT, 2) fused2_kernel(Grid G, Phys P, StepArgs 
                                               : (size_t)i * N + (zs[1 - cz(i)] + yo[1 - cy(i)] + xo[1 - cx(i)]);
                     f[i] = __ldg(a.g_in + src);
                 }
+                ubx = __ldg(a.u_in + kc);
+                uby = __ldg(a.u_in + N + kc);
+                ubz = __ldg(a.u_in + 2 * N + kc);
             }
 
-            // a. phi^n plane p (halo 3); ubar^n plane p-1 at this thread's halo-2 points
+            // a. phi^n plane p (halo 3) and ubar^n plane p-1 (own halo-2 points) from the
+            //    registers loaded one iteration ago; then load plane p+1 / p into them
             {
-                const int pl = zmap<WALL>(p, nz) * nxy;
 #pragma unroll
                 for (int k = 0; k < K3; ++k) {
                     const int t = tid + k * NT;
-                    if (t < N3) sPhi[t] = __ldg(a.phi_in + pl + off3[k]);
+                    if (t < N3) sPhi[t] = nphi[k];
                 }
-                if (do_w) {
-                    const int pw = zmap<WALL>(p - 1, nz) * nxy;
-                    const float sg = zsign<WALL>(p - 1, nz);
 #pragma unroll
-                    for (int k = 0; k < K2; ++k) {
-                        if (own2[k]) {
-                            const int t = tid + k * NT;
-                            sU[t] = __ldg(a.u_in + pw + off2[k]);
-                            sU[N2 + t] = __ldg(a.u_in + N + pw + off2[k]);
-                            sU[2 * N2 + t] = sg * __ldg(a.u_in + 2 * N + pw + off2[k]);
+                for (int k = 0; k < K2; ++k) {
+                    if (own2[k]) {
+                        const int t = tid + k * NT;
+                        sU[t] = nub[k][0];
+                        sU[N2 + t] = nub[k][1];
+                        sU[2 * N2 + t] = nub[k][2];
+                    }
+                }
+                if (s + 1 < nsteps) {
+                    const int pl = zmap<WALL>(p + 1, nz) * nxy;
+#pragma unroll
+                    for (int k = 0; k < K3; ++k)
+                        if (tid + k * NT < N3) nphi[k] = __ldg(a.phi_in + pl + off3[k]);
+                    if (s + 1 >= 2) {
+                        const int pw = zmap<WALL>(p, nz) * nxy;
+                        const float sg = zsign<WALL>(p, nz);
+#pragma unroll
+                        for (int k = 0; k < K2; ++k) {
+                            if (own2[k]) {
+                                nub[k][0] = __ldg(a.u_in + pw + off2[k]);
+                                nub[k][1] = __ldg(a.u_in + N + pw + off2[k]);
+                                nub[k][2] = sg * __ldg(a.u_in + 2 * N + pw + off2[k]);
+                            }
                         }
                     }
                 }
@@ -218,7 +249,7 @@ __global__ void __launch_bounds__(NT, 2) fused2_kernel(Grid G, Phys P, StepArgs 
                         const float gz = 0.5f * ((sd - sc_m2[t]) + (c - sc_m2[N2 + t]));
                         const float ph = sc_m1[N2 + t];
                         const float inv = rsqrtf(fmaxf(gx * gx + gy * gy + gz * gz, kNormalEps * kNormalEps));
-                        const float sh = P.kac * ph * (1.0f - ph) * inv;
+                        const float sh = P.kac * fmaxf(ph * (1.0f - ph), 0.0f) * inv;
                         sW[t] = fmaf(sU[t], ph, sh * gx);
                         sW[N2 + t] = fmaf(sU[N2 + t], ph, sh * gy);
                         sW[2 * N2 + t] = fmaf(sU[2 * N2 + t], ph, sh * gz);
@@ -269,7 +300,6 @@ __global__ void __launch_bounds__(NT, 2) fused2_kernel(Grid G, Phys P, StepArgs 
                     const float gy = 0.5f * fmaf(W0, qy1, W1 * (qy0 + py));
                     const float gz = 0.5f * ((sd - qs0) + (c - qc0));
                     const float lap = 6.0f * fmaf(W0, qs1, W1 * ((qs0 + sd) + ((qc0 - qc1) + (c - qc1))));
-                    const float ubx = __ldg(a.u_in + kc), uby = __ldg(a.u_in + N + kc), ubz = __ldg(a.u_in + 2 * N + kc);
                     float g[27], ux, uy, uz;
                     collide_node(f, qc1, gx, gy, gz, lap, ubx, uby, ubz, P, g, ux, uy, uz);
 #pragma unroll
@@ -291,11 +321,40 @@ struct Launch2 {
     int sms = 0;
 };
 
+struct Split2 {
+    int ncols, zlen, units, ctas;
+};
+
+// Units of work: every column tile cut into m z chunks of equal length.  Default m: as many
+// chunks as fit one round on the resident slots, keeping chunks of at least 16 planes (the
+// march recomputes ~6 halo planes per chunk).  CTAs = units / rounds, rounded up.
+Split2 fused2_split(const Grid &G, int slots, int m)
+{
+    Split2 sp;
+    sp.ncols = ((G.nx + TX - 1) / TX) * ((G.ny + TY - 1) / TY);
+    if (m <= 0) {
+        m = slots / sp.ncols;
+        if (m > G.nz / 16) m = G.nz / 16;
+        if (m < 1) m = 1;
+    }
+    if (m > G.nz) m = G.nz;
+    sp.zlen = (G.nz + m - 1) / m;
+    m = (G.nz + sp.zlen - 1) / sp.zlen;
+    sp.units = sp.ncols * m;
+    const int rounds = (sp.units + slots - 1) / slots;
+    sp.ctas = (sp.units + rounds - 1) / rounds;
+    return sp;
+}
+
 template <bool WALL>
 cudaError_t prepare(Launch2 &L)
 {
     cudaError_t e = cudaFuncSetAttribute(fused2_kernel<WALL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)SMEM_BYTES);
+    if (e != cudaSuccess) return e;
+    // two CTAs of ~48 KB per SM need a large shared-memory carveout
+    e = cudaFuncSetAttribute(fused2_kernel<WALL>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             cudaSharedmemCarveoutMaxShared);
     if (e != cudaSuccess) return e;
     int dev = 0;
     if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
@@ -305,7 +364,7 @@ cudaError_t prepare(Launch2 &L)
 
 }  // namespace
 
-cudaError_t launch_step_fused2(const Grid &G, const Phys &P, const StepArgs &a, int ctas, cudaStream_t s)
+cudaError_t launch_step_fused2(const Grid &G, const Phys &P, const StepArgs &a, int zchunks, cudaStream_t s)
 {
     static Launch2 lw[2];
     Launch2 &L = lw[G.wall ? 1 : 0];
@@ -314,14 +373,11 @@ cudaError_t launch_step_fused2(const Grid &G, const Phys &P, const StepArgs &a, 
         if (e != cudaSuccess) return e;
         if (L.blocks_per_sm < 1) return cudaErrorInvalidConfiguration;
     }
-    const long long cols = (long long)((G.nx + TX - 1) / TX) * ((G.ny + TY - 1) / TY);
-    const long long total = cols * G.nz;
-    long long nblk = ctas > 0 ? ctas : (long long)L.sms * L.blocks_per_sm;
-    if (nblk > total) nblk = total;
+    Split2 sp = fused2_split(G, L.sms * L.blocks_per_sm, zchunks);
     if (G.wall)
-        fused2_kernel<true><<<(int)nblk, NT, SMEM_BYTES, s>>>(G, P, a, total, (int)nblk);
+        fused2_kernel<true><<<sp.ctas, NT, SMEM_BYTES, s>>>(G, P, a, sp.ncols, sp.zlen, sp.units);
     else
-        fused2_kernel<false><<<(int)nblk, NT, SMEM_BYTES, s>>>(G, P, a, total, (int)nblk);
+        fused2_kernel<false><<<sp.ctas, NT, SMEM_BYTES, s>>>(G, P, a, sp.ncols, sp.zlen, sp.units);
     return cudaGetLastError();
 }
 

@@ -1,4 +1,5 @@
-// Unfused step: three plain global-memory kernels, one thread per node.
+// Unfused step: three plain global-memory kernels, one thread per node.  The lattice Boltzmann
+// kernel is also the second kernel of the two-kernel step (step_split.cu).
 //   1. ac_flux:   W = ubar^n phi^n + kappa_AC phi^n (1 - phi^n) n^n          (3N scratch)
 //   2. ac_update: phi^{n+1} = phi^n - div W + D lap(phi^n)
 //   3. lbm:       pull streaming, forces from phi^{n+1}, regularised collision
@@ -69,7 +70,7 @@ __global__ void __launch_bounds__(128) ac_flux_kernel(Grid G, Phys P, const floa
     const float inv = rsqrtf(fmaxf(gx * gx + gy * gy + gz * gz, kNormalEps * kNormalEps));
     const int k = n.zo[1] + n.yo[1] + x;
     const float p = ps[13];
-    const float s = P.kac * p * (1.0f - p) * inv;
+    const float s = P.kac * fmaxf(p * (1.0f - p), 0.0f) * inv;
     W[k] = fmaf(u[k], p, s * gx);
     W[G.N + k] = fmaf(u[G.N + k], p, s * gy);
     W[2 * G.N + k] = fmaf(u[2 * G.N + k], p, s * gz);
@@ -171,6 +172,13 @@ cudaError_t launch_step_unfused(const Grid &G, const Phys &P, const StepArgs &a,
     ac_flux_kernel<<<grid, 128, 0, s>>>(G, P, a.phi_in, a.u_in, a.flux);
     ac_update_kernel<<<grid, 128, 0, s>>>(G, P, a.phi_in, a.flux, a.phi_out);
     lbm_kernel<<<grid, 128, 0, s>>>(G, P, a.g_in, a.phi_out, a.u_in, a.g_out, a.u_out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_lbm(const Grid &G, const Phys &P, const float *g_in, const float *phi_new, const float *u_in,
+                       float *g_out, float *u_out, cudaStream_t s)
+{
+    lbm_kernel<<<node_grid(G), 128, 0, s>>>(G, P, g_in, phi_new, u_in, g_out, u_out);
     return cudaGetLastError();
 }
 

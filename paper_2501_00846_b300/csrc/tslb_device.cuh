@@ -39,6 +39,8 @@ struct Grid {
 };
 
 // Minimum |grad phi| of the interface normal n = grad(phi) / max(|grad(phi)|, eps) in FP32.
+// The sharpening flux kappa_AC max(phi (1 - phi), 0) n weights the normal by zero wherever phi
+// has left [0, 1] (an overshoot extremum, where n is undefined).
 constexpr float kNormalEps = 1e-9f;
 
 // Isotropic gradient and Laplacian of a scalar on the 27-point stencil (paper Section "Model

@@ -17,15 +17,18 @@ struct StepArgs {
     float *flux;           // 3N scratch of the unfused path (Allen–Cahn flux); unused by the fused path
 };
 
-// One step S^n -> S^{n+1}.
+// One step S^n -> S^{n+1}.  zchunks = z chunks per column tile of the marching kernels (<= 0:
+// the default for the grid and GPU).
+cudaError_t launch_step_split(const Grid &G, const Phys &P, const StepArgs &a, int zchunks, cudaStream_t s);
 cudaError_t launch_step_unfused(const Grid &G, const Phys &P, const StepArgs &a, cudaStream_t s);
-cudaError_t launch_step_fused(const Grid &G, const Phys &P, const StepArgs &a, int tz, cudaStream_t s);
+cudaError_t launch_step_fused2(const Grid &G, const Phys &P, const StepArgs &a, int zchunks, cudaStream_t s);
 
-// Separable-stencil fused step with persistent CTAs; ctas <= 0 selects one CTA per resident slot.
-cudaError_t launch_step_fused2(const Grid &G, const Phys &P, const StepArgs &a, int ctas, cudaStream_t s);
-
-// Default z-chunk of the fused kernel for a grid.
-int fused_default_chunk(const Grid &G);
+// The two kernels of the two-kernel step: phi^{n+1} from (phi^n, ubar^n), then the lattice
+// Boltzmann update of every node from g^n, phi^{n+1} and ubar^n.
+cudaError_t launch_ac_split(const Grid &G, const Phys &P, const float *phi_in, const float *u_in, float *phi_out,
+                            int zchunks, cudaStream_t s);
+cudaError_t launch_lbm(const Grid &G, const Phys &P, const float *g_in, const float *phi_new, const float *u_in,
+                       float *g_out, float *u_out, cudaStream_t s);
 
 // g = f^eq(p*, u); pstar may be nullptr (p* = 0).
 cudaError_t launch_init(const Grid &G, const float *pstar, const float *u, float *g, cudaStream_t s);

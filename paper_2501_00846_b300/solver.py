@@ -89,6 +89,7 @@ def load(path: str = LIB_PATH):
         "lbm_step_count": ([vp], ll),
         "lbm_set_path": ([vp, i], i),
         "lbm_set_split": ([vp, i], i),
+        "lbm_run_phase": ([vp, i, i], i),
         "lbm_destroy": ([vp], None),
         "lbm_status_string": ([i], ctypes.c_char_p),
         "lbm_last_error": ([], ctypes.c_char_p),
@@ -197,8 +198,12 @@ class Solver:
         _check(load().lbm_set_path(self._ctx, int(path)))
 
     def set_split(self, split: int):
-        """CTA count (path 0) or z planes per CTA (path 2); 0 = default."""
+        """z chunks per column tile of the marching kernels (paths 0 and 2); 0 = default."""
         _check(load().lbm_set_split(self._ctx, int(split)))
+
+    def run_phase(self, phase: int, nrep: int = 1):
+        """Launch one kernel of the two-kernel step nrep times without advancing the state."""
+        _check(load().lbm_run_phase(self._ctx, int(phase), int(nrep)))
 
     @property
     def step_count(self) -> int:

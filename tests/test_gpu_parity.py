@@ -88,7 +88,7 @@ def droplet48():
 
 
 PATHS = [0, 1, 2]
-PATH_IDS = ["fused", "unfused", "windowed"]
+PATH_IDS = ["two_kernel", "three_kernel", "fused"]
 
 
 @pytest.mark.parametrize("path", PATHS, ids=PATH_IDS)
@@ -127,14 +127,13 @@ def droplet48_rest():
     return wl, P, ref100, ref200
 
 
-@pytest.mark.parametrize("path", [0, 2], ids=["fused", "windowed"])
+@pytest.mark.parametrize("path", [0, 2], ids=["two_kernel", "fused"])
 def test_droplet48_at_rest(droplet48_rest, path):
-    """The configuration as stated (fluid at rest): only spurious currents move (max|u| ~ 1e-4).
-    After 100 steps all three tolerances hold.  After the configuration's 200 steps phi and p
-    still meet theirs; the velocity, which is pure spurious current there, is bounded by 2e-4 of
-    its maximum: its driver, the chemical potential, is the near-cancelling difference of two
-    terms of size ~6e-3, so FP32 rounding of phi alone (~3e-8) moves it by ~1e-8, the size of
-    the velocity error seen (~9e-9 against max|u| ~ 9e-5)."""
+    """The configuration as stated (fluid at rest, checked after 100 and after 200 steps): only
+    spurious currents move (max|u| ~ 9e-5), so the velocity tolerance is the strictest here.
+    Before the sharpening weight was read as max(phi(1-phi), 0) (reading R15) an overshoot of phi
+    above 1 at the droplet centre, where the normal is undefined, made FP32 and FP64 differ by
+    1e-4 in phi."""
     wl, P, ref100, ref200 = droplet48_rest
     with solver.Solver(**wl.params()) as s:
         s.set_path(path)
@@ -148,7 +147,7 @@ def test_droplet48_at_rest(droplet48_rest, path):
     print(f"droplet48 at rest, 200 steps, path={path}: max|dphi| {dphi:.3e} rel du {du:.3e} rel dp {dp:.3e} "
           f"(umax {np.abs(ref200.u).max():.2e})")
     assert dphi <= TOL_PHI and dp <= TOL_P
-    assert du <= 2 * TOL_U
+    assert du <= TOL_U
 
 
 # -- ragged sizes, walls, density ratio 1000 --------------------------------------------------
@@ -167,7 +166,7 @@ def test_ragged_walled_bubble_ratio1000(path):
     _assert_parity(gpu, P, ref, f"ragged walled bubble path={path}")
 
 
-@pytest.mark.parametrize("path", [0, 2], ids=["fused", "windowed"])
+@pytest.mark.parametrize("path", [0, 2], ids=["two_kernel", "fused"])
 def test_ragged_periodic_droplet_across_boundary(path):
     wl = inputs.static_droplet(L=24, radius=6.0, noise=0.01, seed=5)
     wl.nx, wl.ny, wl.nz = 45, 29, 27
@@ -177,7 +176,7 @@ def test_ragged_periodic_droplet_across_boundary(path):
     _assert_parity(gpu, P, ref, f"ragged periodic droplet path={path}")
 
 
-@pytest.mark.parametrize("path", [0, 2], ids=["fused", "windowed"])
+@pytest.mark.parametrize("path", [0, 2], ids=["two_kernel", "fused"])
 def test_minimum_box(path):
     wl = inputs.static_droplet(L=4, radius=1.5, noise=0.01, seed=3)
     P, ref = _oracle_run(wl, 10)
@@ -190,9 +189,9 @@ def test_minimum_box(path):
 
 # -- determinism and invariances of the fused kernel -------------------------------------------
 
-@pytest.mark.parametrize("path", [0, 2], ids=["fused", "windowed"])
+@pytest.mark.parametrize("path", [0, 2], ids=["two_kernel", "fused"])
 def test_work_split_does_not_change_results(path):
-    """The CTA count (path 0) or the z chunk (path 2) changes only how the planes are split among
+    """The number of z chunks per column tile changes only how the planes are split among
     CTAs; halo planes are recomputed with identical arithmetic, so results are bit-identical."""
     wl = _ragged_bubble()
     ref = _gpu_run(wl, 25, path=path, chunk=0)
@@ -235,6 +234,34 @@ def test_device_pointers_match_host_pointers():
         assert np.array_equal(a.reshape(-1), b.cpu().numpy())
 
 
+@pytest.mark.parametrize("kind", ["default", "created"])
+def test_kernels_run_on_the_callers_stream(kind):
+    """Every kernel is enqueued on the stream given at creation (NULL = the legacy default stream):
+    CUDA events recorded on that stream around the steps span their whole device time."""
+    import time
+    import torch
+    st = torch.cuda.default_stream() if kind == "default" else torch.cuda.Stream()
+    wl = inputs.static_droplet(L=128, radius=32.0)
+    with torch.cuda.stream(st):
+        s = solver.Solver(stream=st, **wl.params())
+        try:
+            s.init_fields(_f32(wl.phi0()), _f32(wl.u0()), _pstar0(wl))
+            s.step(5)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            t0 = time.perf_counter()
+            e0.record(st)
+            s.step(60)
+            e1.record(st)
+            torch.cuda.synchronize()
+            wall = time.perf_counter() - t0
+            ev = e0.elapsed_time(e1) * 1e-3
+        finally:
+            s.close()
+    print(f"stream {kind}: event {ev * 1e3:.2f} ms, wall {wall * 1e3:.2f} ms")
+    assert ev > 0.7 * wall
+
+
 # -- error paths ----------------------------------------------------------------------------------
 
 def test_step_before_init_and_nonfinite_detection():
@@ -263,7 +290,7 @@ def bubble_full():
     return wl, P, ref
 
 
-@pytest.mark.parametrize("path", [0, 2], ids=["fused", "windowed"])
+@pytest.mark.parametrize("path", [0, 2], ids=["two_kernel", "fused"])
 def test_rising_bubble_full_size_two_steps(bubble_full, path):
     wl, P, ref = bubble_full
     gpu = _gpu_run(wl, 2, path=path)
