@@ -51,9 +51,23 @@ typedef enum {
 
 typedef enum {
     LBM_FP32 = 0,            /* populations stored as FP32 */
-    LBM_BF16 = 1,            /* populations stored as BF16 deviations (not built: LBM_ERR_ARG) */
-    LBM_FP16 = 2             /* populations stored as FP16 deviations (not built: LBM_ERR_ARG) */
+    LBM_BF16 = 1,            /* populations stored as BF16 deviations (see below) */
+    LBM_FP16 = 2             /* populations stored as FP16 deviations (see below) */
 } lbm_storage;
+
+/*
+ * 16-bit population storage (LBM_BF16, LBM_FP16).  The paper stores FP32 populations; this is a
+ * bandwidth option of the library.  Per node it stores, instead of g_i, the deviation from the
+ * equilibrium of the node's own p* and velocity u (Eq. eqts), per unit weight,
+ *     h_i = (g_i - f^eq_i(p*, u)) / w_i       (27 x 16 bit; FP16 holds 2^12 h_i),
+ * and P = p* - sum_i w_i h_i(rounded) in FP32; u is the velocity stored with the node anyway.
+ * The populations that streaming rebuilds, w_i P + f^eq_i(0, u) + w_i h_i, then sum to the
+ * collision's p* exactly (no drift of sum p* from rounding), and only the non-equilibrium part,
+ * orders of magnitude below p* and u, is rounded to 16 bits.  Arithmetic stays FP32.
+ * 148 bytes move per node and step instead of 248.  Paths 0 and 1 (lbm_set_path) run it;
+ * lbm_get_state / lbm_set_state convert to and from FP32 g; lbm_read_fields and
+ * lbm_observables report p* = P + sum_i w_i h_i.
+ */
 
 /*
  * Parameters, lattice units.  Plain old data; set struct_size = sizeof(lbm_params).
@@ -99,8 +113,9 @@ typedef struct {
     double n_nonfinite;       /* count of nodes with a non-finite phi, ubar or p* */
 } lbm_obs;
 
-/* Create a context: validates *params, allocates every device buffer (two FP32 copies of
- * g, phi, ubar: 2 x 31 floats per node, plus scratch).  The caller owns *out and releases it
+/* Create a context: validates *params, allocates every device buffer (two copies of g, phi,
+ * ubar: 2 x 31 floats per node with FP32 storage, 2 x (27 halves + 5 floats) with 16-bit
+ * storage, plus scratch).  The caller owns *out and releases it
  * with lbm_destroy.  On error *out = NULL and nothing is leaked. */
 lbm_status lbm_create(const lbm_params *params, lbm_ctx **out);
 
@@ -151,8 +166,10 @@ lbm_status lbm_observables_noalloc(const float *g, const float *phi, const float
 lbm_status lbm_read_fields(lbm_ctx *ctx, float *phi, float *u, float *p, int on_device);
 
 /* Checkpoint / resume of the raw state: g (27N floats), phi (N), ubar (3N).  A state written
- * by lbm_get_state and restored by lbm_set_state continues bit-identically.  lbm_set_state
- * sets the step counter to `step`.  Both synchronise the stream. */
+ * by lbm_get_state and restored by lbm_set_state continues bit-identically with FP32 storage.
+ * With 16-bit storage g is exchanged as FP32 g_i = w_i (h_i + p*): lbm_get_state expands it and
+ * lbm_set_state rounds it back (a round trip is not guaranteed to reproduce the stored h bit
+ * for bit).  lbm_set_state sets the step counter to `step`.  Both synchronise the stream. */
 lbm_status lbm_get_state(lbm_ctx *ctx, float *g, float *phi, float *u, int on_device);
 lbm_status lbm_set_state(lbm_ctx *ctx, const float *g, const float *phi, const float *u,
                          long long step, int on_device);
@@ -171,7 +188,7 @@ long long lbm_step_count(const lbm_ctx *ctx);
  *      stencils from global memory; the simplest form, kept as a cross-check)
  *   2  one fused kernel: the Allen–Cahn stencils of a z-marching shared-memory window and the
  *      lattice Boltzmann update of each plane in the same kernel
- * LBM_ERR_ARG for other values. */
+ * LBM_ERR_ARG for other values, and for path 2 with 16-bit storage. */
 lbm_status lbm_set_path(lbm_ctx *ctx, int path);
 
 /* Work split of the z-marching kernels (paths 0 and 2): the number of z chunks each 32 x 8

@@ -43,7 +43,8 @@ struct lbm_ctx {
     lbm_params prm;
     tslb::Grid G;
     tslb::Phys P;
-    float *g[2] = {nullptr, nullptr};
+    float *g[2] = {nullptr, nullptr};  // populations: FP32 g, or 16-bit h (storage 1 / 2)
+    float *pst[2] = {nullptr, nullptr};  // stored p* of the 16-bit formats (N floats)
     float *phi[2] = {nullptr, nullptr};
     float *u[2] = {nullptr, nullptr};
     float *flux = nullptr;            // 3N, unfused path only
@@ -57,6 +58,7 @@ struct lbm_ctx {
     cudaStream_t stream = nullptr;
     int path = 0;
     int split = 0;
+    int storage = LBM_FP32;
 };
 
 namespace {
@@ -66,6 +68,7 @@ void free_ctx(lbm_ctx *c)
     if (!c) return;
     for (int b = 0; b < 2; ++b) {
         cudaFree(c->g[b]);
+        cudaFree(c->pst[b]);
         cudaFree(c->phi[b]);
         cudaFree(c->u[b]);
     }
@@ -95,8 +98,8 @@ lbm_status validate(const lbm_params *p)
     for (int a = 0; a < 3; ++a)
         if (!isfinite(p->gravity[a]) || !isfinite(p->body[a])) return fail(LBM_ERR_ARG, "forces must be finite");
     if (!isfinite(p->rho_ref)) return fail(LBM_ERR_ARG, "rho_ref must be finite");
-    if (p->storage != LBM_FP32)
-        return fail(LBM_ERR_ARG, "storage %d is not built in this library (only LBM_FP32)", p->storage);
+    if (p->storage != LBM_FP32 && p->storage != LBM_BF16 && p->storage != LBM_FP16)
+        return fail(LBM_ERR_ARG, "storage must be LBM_FP32, LBM_BF16 or LBM_FP16 (got %d)", p->storage);
     return LBM_OK;
 }
 
@@ -163,13 +166,17 @@ lbm_status lbm_create(const lbm_params *params, lbm_ctx **out)
     const size_t N = (size_t)c->G.N;
 
     c->stream = (cudaStream_t)params->stream;   // NULL: the legacy default stream
+    c->storage = params->storage;
+    const size_t esz = c->storage == LBM_FP32 ? sizeof(float) : 2;
+    const size_t pst_bytes = c->storage == LBM_FP32 ? 0 : N * sizeof(float);
 
     c->nblocks = tslb::observables_blocks(c->G);
     struct {
         void **p;
         size_t bytes;
     } allocs[] = {
-        {(void **)&c->g[0], 27 * N * sizeof(float)}, {(void **)&c->g[1], 27 * N * sizeof(float)},
+        {(void **)&c->g[0], 27 * N * esz}, {(void **)&c->g[1], 27 * N * esz},
+        {(void **)&c->pst[0], pst_bytes}, {(void **)&c->pst[1], pst_bytes},
         {(void **)&c->phi[0], N * sizeof(float)},    {(void **)&c->phi[1], N * sizeof(float)},
         {(void **)&c->u[0], 3 * N * sizeof(float)},  {(void **)&c->u[1], 3 * N * sizeof(float)},
         {(void **)&c->flux, 3 * N * sizeof(float)},
@@ -177,6 +184,7 @@ lbm_status lbm_create(const lbm_params *params, lbm_ctx **out)
         {(void **)&c->result, tslb::kObsFields * sizeof(double)},
     };
     for (auto &a : allocs) {
+        if (a.bytes == 0) continue;
         cudaError_t e = cudaMalloc(a.p, a.bytes);
         if (e != cudaSuccess) {
             cudaGetLastError();
@@ -210,6 +218,8 @@ lbm_status lbm_set_path(lbm_ctx *ctx, int path)
     if (!ctx) return fail(LBM_ERR_ARG, "context is NULL");
     if (path < 0 || path > 2)
         return fail(LBM_ERR_ARG, "path must be 0 (two kernels), 1 (three kernels) or 2 (one fused kernel)");
+    if (path == 2 && ctx->storage != LBM_FP32)
+        return fail(LBM_ERR_ARG, "16-bit population storage runs on paths 0 and 1 only");
     ctx->path = path;
     return LBM_OK;
 }
@@ -231,11 +241,14 @@ lbm_status lbm_init_fields(lbm_ctx *ctx, const float *phi, const float *u, const
     CUDA_TRY(cudaMemcpyAsync(ctx->phi[c], phi, N * sizeof(float), kind_in(on_device), ctx->stream));
     CUDA_TRY(cudaMemcpyAsync(ctx->u[c], u, 3 * N * sizeof(float), kind_in(on_device), ctx->stream));
     const float *ps = nullptr;
-    if (pstar) {   // stage p*0 in the idle population buffer
+    if (pstar) {   // stage p*0 in the idle population buffer (at least 54 N bytes)
         CUDA_TRY(cudaMemcpyAsync(ctx->g[1 - c], pstar, N * sizeof(float), kind_in(on_device), ctx->stream));
         ps = ctx->g[1 - c];
     }
-    CUDA_TRY(tslb::launch_init(ctx->G, ps, ctx->u[c], ctx->g[c], ctx->stream));
+    if (ctx->storage == LBM_FP32)
+        CUDA_TRY(tslb::launch_init(ctx->G, ps, ctx->u[c], ctx->g[c], ctx->stream));
+    else
+        CUDA_TRY(tslb::launch_init16(ctx->G, ctx->storage, ps, ctx->g[c], ctx->pst[c], ctx->stream));
     if (!on_device) CUDA_TRY(cudaStreamSynchronize(ctx->stream));
     ctx->step = 0;
     ctx->initialized = true;
@@ -249,7 +262,8 @@ lbm_status lbm_step(lbm_ctx *ctx, int nsteps)
     if (!ctx->initialized) return fail(LBM_ERR_STATE, "lbm_step before lbm_init_fields");
     for (int s = 0; s < nsteps; ++s) {
         const int a = ctx->cur, b = 1 - ctx->cur;
-        tslb::StepArgs args{ctx->g[a], ctx->g[b], ctx->phi[a], ctx->phi[b], ctx->u[a], ctx->u[b], ctx->flux};
+        tslb::StepArgs args{ctx->g[a], ctx->g[b], ctx->phi[a], ctx->phi[b], ctx->u[a], ctx->u[b], ctx->flux,
+                            ctx->storage, ctx->pst[a], ctx->pst[b]};
         cudaError_t e = ctx->path == 0   ? tslb::launch_step_split(ctx->G, ctx->P, args, ctx->split, ctx->stream)
                          : ctx->path == 2 ? tslb::launch_step_fused2(ctx->G, ctx->P, args, ctx->split, ctx->stream)
                                           : tslb::launch_step_unfused(ctx->G, ctx->P, args, ctx->stream);
@@ -270,8 +284,11 @@ lbm_status lbm_run_phase(lbm_ctx *ctx, int phase, int nrep)
     for (int r = 0; r < nrep; ++r) {
         cudaError_t e = phase == 0 ? tslb::launch_ac_split(ctx->G, ctx->P, ctx->phi[a], ctx->u[a], ctx->phi[b], ctx->split,
                                                            ctx->stream)
-                                   : tslb::launch_lbm(ctx->G, ctx->P, ctx->g[a], ctx->phi[b], ctx->u[a], ctx->g[b],
-                                                      ctx->u[b], ctx->stream);
+                         : ctx->storage != LBM_FP32
+                             ? tslb::launch_lbm16(ctx->G, ctx->P, ctx->storage, ctx->g[a], ctx->pst[a], ctx->phi[b],
+                                                  ctx->u[a], ctx->g[b], ctx->pst[b], ctx->u[b], ctx->stream)
+                             : tslb::launch_lbm(ctx->G, ctx->P, 0, ctx->g[a], nullptr, ctx->phi[b], ctx->u[a],
+                                                ctx->g[b], nullptr, ctx->u[b], ctx->stream);
         if (e != cudaSuccess) return fail(LBM_ERR_CUDA, "phase launch failed: %s", cudaGetErrorString(e));
     }
     return LBM_OK;
@@ -290,8 +307,9 @@ lbm_status lbm_observables(lbm_ctx *ctx, lbm_obs *out)
     if (!out) return fail(LBM_ERR_ARG, "out is NULL");
     if (!ctx->initialized) return fail(LBM_ERR_STATE, "lbm_observables before lbm_init_fields");
     const int c = ctx->cur;
-    CUDA_TRY(tslb::launch_observables(ctx->G, ctx->prm.rho_l, ctx->prm.rho_g, ctx->g[c], ctx->phi[c], ctx->u[c], ctx->partials, ctx->nblocks,
-                                      ctx->result, ctx->stream));
+    CUDA_TRY(tslb::launch_observables(ctx->G, ctx->prm.rho_l, ctx->prm.rho_g, ctx->g[c], ctx->phi[c], ctx->u[c],
+                                      ctx->partials, ctx->nblocks, ctx->result, ctx->stream, ctx->storage,
+                                      ctx->pst[c]));
     CUDA_TRY(cudaMemcpyAsync(ctx->h_result, ctx->result, tslb::kObsFields * sizeof(double), cudaMemcpyDeviceToHost,
                              ctx->stream));
     CUDA_TRY(cudaStreamSynchronize(ctx->stream));
@@ -330,7 +348,8 @@ lbm_status lbm_read_fields(lbm_ctx *ctx, float *phi, float *u, float *p, int on_
     if (u) CUDA_TRY(cudaMemcpyAsync(u, ctx->u[c], 3 * N * sizeof(float), kind_out(on_device), ctx->stream));
     if (p) {   // compute p into the idle population buffer, then copy
         float *tmp = ctx->g[1 - c];
-        CUDA_TRY(tslb::launch_pressure(ctx->G, ctx->P, ctx->g[c], ctx->phi[c], tmp, ctx->stream));
+        CUDA_TRY(tslb::launch_pressure(ctx->G, ctx->P, ctx->storage, ctx->g[c], ctx->pst[c], ctx->phi[c], tmp,
+                                       ctx->stream));
         CUDA_TRY(cudaMemcpyAsync(p, tmp, N * sizeof(float), kind_out(on_device), ctx->stream));
     }
     CUDA_TRY(cudaStreamSynchronize(ctx->stream));
@@ -343,7 +362,21 @@ lbm_status lbm_get_state(lbm_ctx *ctx, float *g, float *phi, float *u, int on_de
     if (!ctx->initialized) return fail(LBM_ERR_STATE, "lbm_get_state before lbm_init_fields");
     const size_t N = (size_t)ctx->G.N;
     const int c = ctx->cur;
-    if (g) CUDA_TRY(cudaMemcpyAsync(g, ctx->g[c], 27 * N * sizeof(float), kind_out(on_device), ctx->stream));
+    if (g && ctx->storage == LBM_FP32) {
+        CUDA_TRY(cudaMemcpyAsync(g, ctx->g[c], 27 * N * sizeof(float), kind_out(on_device), ctx->stream));
+    } else if (g && on_device) {   // g_i = w_i (P + f^eq_i(0, u) / w_i + h_i) straight into the caller's buffer
+        CUDA_TRY(tslb::launch_expand16(ctx->G, ctx->storage, ctx->g[c], ctx->pst[c], ctx->u[c], 0, 27, g,
+                                       ctx->stream));
+    } else if (g) {   // expand 13 directions at a time into the idle buffer (54 N bytes), then copy
+        float *tmp = ctx->g[1 - c];
+        for (int i0 = 0; i0 < 27; i0 += 13) {
+            const int ni = i0 + 13 <= 27 ? 13 : 27 - i0;
+            CUDA_TRY(tslb::launch_expand16(ctx->G, ctx->storage, ctx->g[c], ctx->pst[c], ctx->u[c], i0, ni, tmp,
+                                           ctx->stream));
+            CUDA_TRY(cudaMemcpyAsync(g + (size_t)i0 * N, tmp, ni * N * sizeof(float), cudaMemcpyDeviceToHost,
+                                     ctx->stream));
+        }
+    }
     if (phi) CUDA_TRY(cudaMemcpyAsync(phi, ctx->phi[c], N * sizeof(float), kind_out(on_device), ctx->stream));
     if (u) CUDA_TRY(cudaMemcpyAsync(u, ctx->u[c], 3 * N * sizeof(float), kind_out(on_device), ctx->stream));
     CUDA_TRY(cudaStreamSynchronize(ctx->stream));
@@ -358,9 +391,34 @@ lbm_status lbm_set_state(lbm_ctx *ctx, const float *g, const float *phi, const f
     if (step < 0) return fail(LBM_ERR_ARG, "step must be >= 0");
     const size_t N = (size_t)ctx->G.N;
     const int c = ctx->cur;
-    CUDA_TRY(cudaMemcpyAsync(ctx->g[c], g, 27 * N * sizeof(float), kind_in(on_device), ctx->stream));
     CUDA_TRY(cudaMemcpyAsync(ctx->phi[c], phi, N * sizeof(float), kind_in(on_device), ctx->stream));
     CUDA_TRY(cudaMemcpyAsync(ctx->u[c], u, 3 * N * sizeof(float), kind_in(on_device), ctx->stream));
+    if (ctx->storage == LBM_FP32) {
+        CUDA_TRY(cudaMemcpyAsync(ctx->g[c], g, 27 * N * sizeof(float), kind_in(on_device), ctx->stream));
+    } else {
+        // P = sum g (mode 0), then h_i = g_i / w_i - P - f^eq_i(0, u) / w_i and P -= sum w_i h_i
+        // (mode 1 + finish), with u already in place.  Host input is staged 13 directions at a
+        // time in the idle population buffer (54 N bytes); corr uses the flux scratch.
+        float *corr = ctx->flux;
+        CUDA_TRY(cudaMemsetAsync(ctx->pst[c], 0, N * sizeof(float), ctx->stream));
+        CUDA_TRY(cudaMemsetAsync(corr, 0, N * sizeof(float), ctx->stream));
+        for (int mode = 0; mode < 2; ++mode) {
+            if (on_device) {
+                CUDA_TRY(tslb::launch_compress16(ctx->G, ctx->storage, g, ctx->u[c], 0, 27, mode, ctx->g[c],
+                                                 ctx->pst[c], corr, ctx->stream));
+                continue;
+            }
+            float *tmp = ctx->g[1 - c];
+            for (int i0 = 0; i0 < 27; i0 += 13) {
+                const int ni = i0 + 13 <= 27 ? 13 : 27 - i0;
+                CUDA_TRY(cudaMemcpyAsync(tmp, g + (size_t)i0 * N, ni * N * sizeof(float), cudaMemcpyHostToDevice,
+                                         ctx->stream));
+                CUDA_TRY(tslb::launch_compress16(ctx->G, ctx->storage, tmp, ctx->u[c], i0, ni, mode, ctx->g[c],
+                                                 ctx->pst[c], corr, ctx->stream));
+            }
+        }
+        CUDA_TRY(tslb::launch_finish16(ctx->G, corr, ctx->pst[c], ctx->stream));
+    }
     CUDA_TRY(cudaStreamSynchronize(ctx->stream));
     ctx->step = step;
     ctx->initialized = true;

@@ -32,7 +32,8 @@ __device__ __forceinline__ double combine(int f, double a, double b)
 constexpr int kThreads = 256;
 
 __global__ void __launch_bounds__(kThreads) obs_partial_kernel(Grid G, double rho_g, double drho,
-                                                               const float *__restrict__ g,
+                                                               const void *__restrict__ gv, int storage,
+                                                               const float *__restrict__ pst,
                                                                const float *__restrict__ phi,
                                                                const float *__restrict__ u,
                                                                double *__restrict__ partials)
@@ -50,8 +51,16 @@ __global__ void __launch_bounds__(kThreads) obs_partial_kernel(Grid G, double rh
         const int y = rem / G.nx;
         const int x = rem - y * G.nx;
         double ps = 0.0;
+        if (pst) {   // 16-bit formats: p* = P + sum_i w_i h_i
+            float s = pst[k];
 #pragma unroll
-        for (int i = 0; i < 27; ++i) ps += (double)g[i * N + k];
+            for (int i = 0; i < 27; ++i) s = fmaf(wgt(i), load_h16(gv, storage, i * N + k), s);
+            ps = s;
+        } else {
+            const float *g = (const float *)gv;
+#pragma unroll
+            for (int i = 0; i < 27; ++i) ps += (double)g[i * N + k];
+        }
         const double ph = phi[k];
         const double ux = u[k], uy = u[N + k], uz = u[2 * N + k];
         if (!(isfinite(ph) && isfinite(ux) && isfinite(uy) && isfinite(uz) && isfinite(ps))) {
@@ -124,10 +133,11 @@ int observables_blocks(const Grid &G)
     return (int)(need < 148 * 8 ? need : 148 * 8);
 }
 
-cudaError_t launch_observables(const Grid &G, double rho_l, double rho_g, const float *g, const float *phi,
-                               const float *u, double *partials, int nblocks, double *result, cudaStream_t s)
+cudaError_t launch_observables(const Grid &G, double rho_l, double rho_g, const void *g, const float *phi,
+                               const float *u, double *partials, int nblocks, double *result, cudaStream_t s,
+                               int storage, const float *pst)
 {
-    obs_partial_kernel<<<nblocks, kThreads, 0, s>>>(G, rho_g, rho_l - rho_g, g, phi, u, partials);
+    obs_partial_kernel<<<nblocks, kThreads, 0, s>>>(G, rho_g, rho_l - rho_g, g, storage, pst, phi, u, partials);
     obs_final_kernel<<<1, 32, 0, s>>>(partials, nblocks, result);
     return cudaGetLastError();
 }

@@ -10,44 +10,7 @@
 namespace tslb {
 namespace {
 
-// Neighbour coordinates of one node at distance 1: offsets into a scalar array for c = -1, 0, +1
-// along each axis, with x, y periodic and z periodic or mirrored at the walls.
-struct Nbr {
-    int xo[3], yo[3], zo[3];
-    float zsgn[3];   // -1 where the z neighbour is a mirror image (odd z component of vectors)
-};
-
-__device__ __forceinline__ Nbr make_nbr(int x, int y, int z, const Grid &G)
-{
-    Nbr n;
-    n.xo[0] = x == 0 ? G.nx - 1 : x - 1;
-    n.xo[1] = x;
-    n.xo[2] = x == G.nx - 1 ? 0 : x + 1;
-    n.yo[0] = (y == 0 ? G.ny - 1 : y - 1) * G.nx;
-    n.yo[1] = y * G.nx;
-    n.yo[2] = (y == G.ny - 1 ? 0 : y + 1) * G.nx;
-    n.zsgn[0] = n.zsgn[1] = n.zsgn[2] = 1.0f;
-    int zm, zp;
-    if (G.wall) {
-        zm = z == 0 ? 0 : z - 1;
-        zp = z == G.nz - 1 ? G.nz - 1 : z + 1;
-        if (z == 0) n.zsgn[0] = -1.0f;
-        if (z == G.nz - 1) n.zsgn[2] = -1.0f;
-    } else {
-        zm = z == 0 ? G.nz - 1 : z - 1;
-        zp = z == G.nz - 1 ? 0 : z + 1;
-    }
-    n.zo[0] = zm * G.nxy;
-    n.zo[1] = z * G.nxy;
-    n.zo[2] = zp * G.nxy;
-    return n;
-}
-
-__device__ __forceinline__ int nidx(const Nbr &n, int i)
-{
-    return n.zo[cz(i) + 1] + n.yo[cy(i) + 1] + n.xo[cx(i) + 1];
-}
-
+// One thread per node: x from the thread index, y and z from the block index.
 __device__ __forceinline__ bool node_coords(const Grid &G, int &x, int &y, int &z)
 {
     x = blockIdx.x * blockDim.x + threadIdx.x;
@@ -98,9 +61,17 @@ __global__ void __launch_bounds__(128) ac_update_kernel(Grid G, Phys P, const fl
     phi_out[n.zo[1] + n.yo[1] + x] = ps[13] - div + P.mob * lap;
 }
 
-__global__ void __launch_bounds__(128) lbm_kernel(Grid G, Phys P, const float *__restrict__ gin,
-                                                  const float *__restrict__ phi_new, const float *__restrict__ ubar,
-                                                  float *__restrict__ gout, float *__restrict__ uout)
+// Lattice Boltzmann update of one node per thread (pull, forces from phi^{n+1}, regularised
+// collision).  S selects the population format: FP32 g, or a 16-bit deviation from equilibrium
+// h_i with P in FP32 (pin / pout; see the storage formats in tslb_device.cuh).  A 16-bit puller
+// rebuilds g_i(x - c_i) = w_i (P + f^eq_i(0, ubar) / w_i + h_i) from the source node's P, ubar
+// and h; the collision forms h_i = (g_i - f^eq_i(p*, u)) / w_i directly and stores it with
+// P = p* - sum w_i h_i(rounded).
+template <class S>
+__global__ void __launch_bounds__(128) lbm_kernel(Grid G, Phys P, const typename S::T *__restrict__ gin,
+                                                  const float *__restrict__ pin, const float *__restrict__ phi_new,
+                                                  const float *__restrict__ ubar, typename S::T *__restrict__ gout,
+                                                  float *__restrict__ pout, float *__restrict__ uout)
 {
     int x, y, z;
     if (!node_coords(G, x, y, z)) return;
@@ -118,7 +89,17 @@ __global__ void __launch_bounds__(128) lbm_kernel(Grid G, Phys P, const float *_
         bool bounce = false;
         if (cz(i) == 1) bounce = wlo;
         if (cz(i) == -1) bounce = whi;
-        f[i] = bounce ? __ldg(gin + (26 - i) * N + k) : __ldg(gin + i * N + j);
+        const int src = bounce ? k : j;
+        const size_t at = (size_t)(bounce ? 26 - i : i) * N + src;
+        if (S::kShifted) {
+            const float vx = __ldg(ubar + src), vy = __ldg(ubar + N + src), vz = __ldg(ubar + 2 * N + src);
+            const float v2 = vx * vx + vy * vy + vz * vz;
+            const float cu = cdot(i, vx, vy, vz);
+            const float e = eq_shifted(bounce ? -cu : cu, v2);
+            f[i] = wgt(i) * (__ldg(pin + src) + e + S::to_f(gin[at]));
+        } else {
+            f[i] = S::to_f(gin[at]);
+        }
     }
 
     float ps[27];
@@ -127,13 +108,101 @@ __global__ void __launch_bounds__(128) lbm_kernel(Grid G, Phys P, const float *_
     float gx, gy, gz, lap;
     grad_lap27(ps, gx, gy, gz, lap);
 
-    float g[27], ux, uy, uz;
-    collide_node(f, ps[13], gx, gy, gz, lap, ubar[k], ubar[N + k], ubar[2 * N + k], P, g, ux, uy, uz);
+    float g[27], ux, uy, uz, pstar;
+    collide_node<S::kShifted>(f, ps[13], gx, gy, gz, lap, ubar[k], ubar[N + k], ubar[2 * N + k], P, g, ux, uy, uz,
+                              &pstar);
+    if (S::kShifted) {
+        float sum = 0.0f;
 #pragma unroll
-    for (int i = 0; i < 27; ++i) gout[i * N + k] = g[i];
+        for (int i = 0; i < 27; ++i) {
+            const typename S::T h = S::from_f(g[i]);
+            gout[i * N + k] = h;
+            sum = fmaf(wgt(i), S::to_f(h), sum);
+        }
+        pout[k] = pstar - sum;
+    } else {
+#pragma unroll
+        for (int i = 0; i < 27; ++i) gout[i * N + k] = S::from_f(g[i]);
+    }
     uout[k] = ux;
     uout[N + k] = uy;
     uout[2 * N + k] = uz;
+}
+
+// 16-bit formats from equilibrium: h = 0 and P = p*0.
+template <class S>
+__global__ void __launch_bounds__(128) init16_kernel(Grid G, const float *__restrict__ pstar,
+                                                     typename S::T *__restrict__ h, float *__restrict__ pst)
+{
+    int x, y, z;
+    if (!node_coords(G, x, y, z)) return;
+    const size_t N = (size_t)G.N;
+    const int k = (z * G.ny + y) * G.nx + x;
+#pragma unroll
+    for (int i = 0; i < 27; ++i) h[i * N + k] = S::from_f(0.0f);
+    pst[k] = pstar ? pstar[k] : 0.0f;
+}
+
+// g_i = w_i (P + f^eq_i(0, u) / w_i + h_i) for directions [i0, i0 + ni) into g[(i - i0) * N + node]
+template <class S>
+__global__ void __launch_bounds__(128) expand16_kernel(Grid G, const typename S::T *__restrict__ h,
+                                                       const float *__restrict__ pst, const float *__restrict__ u,
+                                                       int i0, int ni, float *__restrict__ g)
+{
+    int x, y, z;
+    if (!node_coords(G, x, y, z)) return;
+    const size_t N = (size_t)G.N;
+    const int k = (z * G.ny + y) * G.nx + x;
+    const float p = pst[k], ux = u[k], uy = u[N + k], uz = u[2 * N + k];
+    const float u2 = ux * ux + uy * uy + uz * uz;
+#pragma unroll
+    for (int i = 0; i < 27; ++i)
+        if (i >= i0 && i < i0 + ni)
+            g[(size_t)(i - i0) * N + k] = wgt(i) * (p + eq_shifted(cdot(i, ux, uy, uz), u2) + S::to_f(h[i * N + k]));
+}
+
+// From FP32 g (directions [i0, i0 + ni) at g[(i - i0) * N + node]) and the node's u: mode 0
+// accumulates p* = sum g into pst (zeroed by the caller); mode 1 writes
+// h_i = g_i / w_i - p* - f^eq_i(0, u) / w_i and accumulates sum w_i h_i(rounded) into corr.
+template <class S>
+__global__ void __launch_bounds__(128) compress16_kernel(Grid G, const float *__restrict__ g,
+                                                         const float *__restrict__ u, int i0, int ni, int mode,
+                                                         typename S::T *__restrict__ h, float *__restrict__ pst,
+                                                         float *__restrict__ corr)
+{
+    int x, y, z;
+    if (!node_coords(G, x, y, z)) return;
+    const size_t N = (size_t)G.N;
+    const int k = (z * G.ny + y) * G.nx + x;
+    if (mode == 0) {
+        float s = pst[k];
+#pragma unroll
+        for (int i = 0; i < 27; ++i)
+            if (i >= i0 && i < i0 + ni) s += g[(size_t)(i - i0) * N + k];
+        pst[k] = s;
+        return;
+    }
+    const float p = pst[k], ux = u[k], uy = u[N + k], uz = u[2 * N + k];
+    const float u2 = ux * ux + uy * uy + uz * uz;
+    float c = corr[k];
+#pragma unroll
+    for (int i = 0; i < 27; ++i) {
+        if (i >= i0 && i < i0 + ni) {
+            const float gi = g[(size_t)(i - i0) * N + k];
+            const typename S::T v = S::from_f(gi / wgt(i) - p - eq_shifted(cdot(i, ux, uy, uz), u2));
+            h[i * N + k] = v;
+            c = fmaf(wgt(i), S::to_f(v), c);
+        }
+    }
+    corr[k] = c;
+}
+
+__global__ void __launch_bounds__(128) finish16_kernel(Grid G, const float *__restrict__ corr, float *__restrict__ pst)
+{
+    int x, y, z;
+    if (!node_coords(G, x, y, z)) return;
+    const int k = (z * G.ny + y) * G.nx + x;
+    pst[k] -= corr[k];
 }
 
 __global__ void __launch_bounds__(128) init_kernel(Grid G, const float *__restrict__ pstar, const float *__restrict__ u,
@@ -149,16 +218,25 @@ __global__ void __launch_bounds__(128) init_kernel(Grid G, const float *__restri
     for (int i = 0; i < 27; ++i) g[i * N + k] = e[i];
 }
 
-__global__ void __launch_bounds__(128) pressure_kernel(Grid G, Phys P, const float *__restrict__ g,
-                                                       const float *__restrict__ phi, float *__restrict__ p)
+// p = p* rho cs^2 with p* = sum_i g_i (FP32 populations; pst null), or P + sum_i w_i h_i
+// (16-bit formats: g holds h, storage 1 / 2)
+__global__ void __launch_bounds__(128) pressure_kernel(Grid G, Phys P, const float *__restrict__ g, int storage,
+                                                       const float *__restrict__ pst, const float *__restrict__ phi,
+                                                       float *__restrict__ p)
 {
     int x, y, z;
     if (!node_coords(G, x, y, z)) return;
     const size_t N = (size_t)G.N;
     const int k = (z * G.ny + y) * G.nx + x;
     float s = 0.0f;
+    if (pst) {   // 16-bit formats: p* = P + sum_i w_i h_i
+        s = pst[k];
 #pragma unroll
-    for (int i = 0; i < 27; ++i) s += g[i * N + k];
+        for (int i = 0; i < 27; ++i) s = fmaf(wgt(i), load_h16(g, storage, i * N + k), s);
+    } else {
+#pragma unroll
+        for (int i = 0; i < 27; ++i) s += g[i * N + k];
+    }
     p[k] = s * fmaf(phi[k], P.drho, P.rho_g) * (1.0f / 3.0f);
 }
 
@@ -171,14 +249,66 @@ cudaError_t launch_step_unfused(const Grid &G, const Phys &P, const StepArgs &a,
     const dim3 grid = node_grid(G);
     ac_flux_kernel<<<grid, 128, 0, s>>>(G, P, a.phi_in, a.u_in, a.flux);
     ac_update_kernel<<<grid, 128, 0, s>>>(G, P, a.phi_in, a.flux, a.phi_out);
-    lbm_kernel<<<grid, 128, 0, s>>>(G, P, a.g_in, a.phi_out, a.u_in, a.g_out, a.u_out);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    return launch_lbm(G, P, a.storage, a.g_in, a.p_in, a.phi_out, a.u_in, a.g_out, a.p_out, a.u_out, s);
+}
+
+cudaError_t launch_lbm(const Grid &G, const Phys &P, int storage, const void *g_in, const float *p_in,
+                       const float *phi_new, const float *u_in, void *g_out, float *p_out, float *u_out, cudaStream_t s)
+{
+    const dim3 grid = node_grid(G);
+    switch (storage) {
+    case 0:
+        lbm_kernel<StoreF32><<<grid, 128, 0, s>>>(G, P, (const float *)g_in, nullptr, phi_new, u_in, (float *)g_out,
+                                                  nullptr, u_out);
+        break;
+    case 1:
+        lbm_kernel<StoreB16><<<grid, 128, 0, s>>>(G, P, (const __nv_bfloat16 *)g_in, p_in, phi_new, u_in,
+                                                  (__nv_bfloat16 *)g_out, p_out, u_out);
+        break;
+    case 2:
+        lbm_kernel<StoreF16><<<grid, 128, 0, s>>>(G, P, (const __half *)g_in, p_in, phi_new, u_in, (__half *)g_out,
+                                                  p_out, u_out);
+        break;
+    default: return cudaErrorInvalidValue;
+    }
     return cudaGetLastError();
 }
 
-cudaError_t launch_lbm(const Grid &G, const Phys &P, const float *g_in, const float *phi_new, const float *u_in,
-                       float *g_out, float *u_out, cudaStream_t s)
+cudaError_t launch_init16(const Grid &G, int storage, const float *pstar, void *h, float *pst, cudaStream_t s)
 {
-    lbm_kernel<<<node_grid(G), 128, 0, s>>>(G, P, g_in, phi_new, u_in, g_out, u_out);
+    if (storage == 1)
+        init16_kernel<StoreB16><<<node_grid(G), 128, 0, s>>>(G, pstar, (__nv_bfloat16 *)h, pst);
+    else
+        init16_kernel<StoreF16><<<node_grid(G), 128, 0, s>>>(G, pstar, (__half *)h, pst);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_expand16(const Grid &G, int storage, const void *h, const float *pst, const float *u, int i0,
+                            int ni, float *g, cudaStream_t s)
+{
+    if (storage == 1)
+        expand16_kernel<StoreB16><<<node_grid(G), 128, 0, s>>>(G, (const __nv_bfloat16 *)h, pst, u, i0, ni, g);
+    else
+        expand16_kernel<StoreF16><<<node_grid(G), 128, 0, s>>>(G, (const __half *)h, pst, u, i0, ni, g);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_compress16(const Grid &G, int storage, const float *g, const float *u, int i0, int ni, int mode,
+                              void *h, float *pst, float *corr, cudaStream_t s)
+{
+    if (storage == 1)
+        compress16_kernel<StoreB16><<<node_grid(G), 128, 0, s>>>(G, g, u, i0, ni, mode, (__nv_bfloat16 *)h, pst,
+                                                                 corr);
+    else
+        compress16_kernel<StoreF16><<<node_grid(G), 128, 0, s>>>(G, g, u, i0, ni, mode, (__half *)h, pst, corr);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_finish16(const Grid &G, const float *corr, float *pst, cudaStream_t s)
+{
+    finish16_kernel<<<node_grid(G), 128, 0, s>>>(G, corr, pst);
     return cudaGetLastError();
 }
 
@@ -188,9 +318,10 @@ cudaError_t launch_init(const Grid &G, const float *pstar, const float *u, float
     return cudaGetLastError();
 }
 
-cudaError_t launch_pressure(const Grid &G, const Phys &P, const float *g, const float *phi, float *p, cudaStream_t s)
+cudaError_t launch_pressure(const Grid &G, const Phys &P, int storage, const void *g, const float *pst,
+                            const float *phi, float *p, cudaStream_t s)
 {
-    pressure_kernel<<<node_grid(G), 128, 0, s>>>(G, P, g, phi, p);
+    pressure_kernel<<<node_grid(G), 128, 0, s>>>(G, P, (const float *)g, storage, pst, phi, p);
     return cudaGetLastError();
 }
 

@@ -5,6 +5,8 @@
 // literal {-1, 0, 1} and the products with it fold into adds.
 #pragma once
 
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -96,9 +98,14 @@ __device__ __forceinline__ void grad_lap27(const float (&psi)[27], float &gx, fl
 //   O = cu (K1 + 4.5 cu^2 + 3 k2 cAc) + c.v,                  K1 = 3 - 4.5 u^2 - k2 trA
 //   k2 = 4.5 (1 - omega),  v = 1.5 a - 2 k2 A u
 // which is the full contraction of the Hermite terms (H3_aaa vanishes on D3Q27).
+// NEQ = true writes, instead of g_i, its deviation from the equilibrium of the node's own p* and u,
+// h_i = (g_i - f^eq_i(p*, u)) / w_i = ((1 - omega) f^neq_i + S_i / 2) / w_i: the same E and O with
+// their equilibrium terms dropped (K0 -> -1.5 u.a - 1.5 (1-omega) trA, K1 -> -k2 trA, no 4.5 cu^2),
+// so the small deviation is formed without cancellation.  ps_out receives p*.
+template <bool NEQ = false>
 __device__ __forceinline__ void collide_node(const float (&f)[27], float phi, float gpx, float gpy, float gpz,
                                              float lap, float ubx, float uby, float ubz, const Phys &P,
-                                             float (&g)[27], float &ux, float &uy, float &uz)
+                                             float (&g)[27], float &ux, float &uy, float &uz, float *ps_out = nullptr)
 {
     // moments over opposite pairs
     float ps = f[13];
@@ -156,15 +163,16 @@ __device__ __forceinline__ void collide_node(const float (&f)[27], float phi, fl
     const float trA = Axx + Ayy + Azz;
     const float u2 = ux * ux + uy * uy + uz * uz;
     const float ua = ux * ax + uy * ay + uz * az;
-    const float K0 = ps - 1.5f * u2 - 1.5f * ua - 1.5f * om1 * trA;
-    const float K1 = 3.0f - 4.5f * u2 - k2 * trA;
+    const float K0 = NEQ ? -1.5f * ua - 1.5f * om1 * trA : ps - 1.5f * u2 - 1.5f * ua - 1.5f * om1 * trA;
+    const float K1 = NEQ ? -k2 * trA : 3.0f - 4.5f * u2 - k2 * trA;
     const float twok2 = 2.0f * k2;
     const float vx = 1.5f * ax - twok2 * (Axx * ux + Axy * uy + Axz * uz);
     const float vy = 1.5f * ay - twok2 * (Axy * ux + Ayy * uy + Ayz * uz);
     const float vz = 1.5f * az - twok2 * (Axz * ux + Ayz * uy + Azz * uz);
     const float A2xy = 2.0f * Axy, A2xz = 2.0f * Axz, A2yz = 2.0f * Ayz;
 
-    g[13] = wgt(13) * K0;
+    if (ps_out) *ps_out = ps;
+    g[13] = NEQ ? K0 : wgt(13) * K0;
 #pragma unroll
     for (int i = 0; i < 13; ++i) {
         float cu = 0.f, ca = 0.f, cv = 0.f, cac = 0.f;
@@ -175,11 +183,29 @@ __device__ __forceinline__ void collide_node(const float (&f)[27], float phi, fl
         if (cx(i) * cz(i)) cac += (cx(i) * cz(i)) * A2xz;
         if (cy(i) * cz(i)) cac += (cy(i) * cz(i)) * A2yz;
         const float hcu = 4.5f * cu;
-        const float E = fmaf(k2, cac, fmaf(hcu, cu + ca, K0));
-        const float O = fmaf(cu, fmaf(k3, cac, fmaf(hcu, cu, K1)), cv);
-        g[i] = wgt(i) * (E + O);
-        g[26 - i] = wgt(i) * (E - O);
+        const float E = NEQ ? fmaf(k2, cac, fmaf(hcu, ca, K0)) : fmaf(k2, cac, fmaf(hcu, cu + ca, K0));
+        const float O = NEQ ? fmaf(cu, fmaf(k3, cac, K1), cv) : fmaf(cu, fmaf(k3, cac, fmaf(hcu, cu, K1)), cv);
+        g[i] = NEQ ? E + O : wgt(i) * (E + O);
+        g[26 - i] = NEQ ? E - O : wgt(i) * (E - O);
     }
+}
+
+// f^eq_i(p*, u) / w_i - p* for a velocity projection cu = c_i . u and u2 = |u|^2 (Eq. eqts):
+// -3/2 u^2 + 3 cu + 9/2 cu^2 + cu (9/2 cu^2 - 9/2 u^2), in the even/odd split E + O that the
+// collision uses; the opposite direction (-cu) gives E - O bit for bit.
+__device__ __forceinline__ float eq_shifted(float cu, float u2)
+{
+    const float E = fmaf(4.5f * cu, cu, -1.5f * u2);
+    const float O = cu * fmaf(4.5f * cu, cu, 3.0f - 4.5f * u2);
+    return E + O;
+}
+
+// p* + f^eq_i(0, u) / w_i from the node quantities A = p* - 1.5 u^2 and B = 3 - 4.5 u^2 (the same
+// polynomial as eq_shifted, with the u^2 terms precomputed once per node)
+__device__ __forceinline__ float eq_from_ab(float cu, float A, float B)
+{
+    const float t = 4.5f * cu * cu;
+    return (A + t) + cu * (t + B);
 }
 
 // Equilibrium populations f^eq_i(p*, u) (Eq. eqts), even/odd form, for initialisation.
@@ -188,7 +214,6 @@ __device__ __forceinline__ void equilibrium(float ps, float ux, float uy, float 
     const float u2 = ux * ux + uy * uy + uz * uz;
     const float K0 = ps - 1.5f * u2;
     const float K1 = 3.0f - 4.5f * u2;
-    g[13] = wgt(13) * K0;
 #pragma unroll
     for (int i = 0; i < 13; ++i) {
         float cu = 0.f;
@@ -200,6 +225,93 @@ __device__ __forceinline__ void equilibrium(float ps, float ux, float uy, float 
         g[i] = wgt(i) * (E + O);
         g[26 - i] = wgt(i) * (E - O);
     }
+    g[13] = wgt(13) * K0;
+}
+
+// c_i . u with the zero components of c_i skipped at compile time
+__device__ __forceinline__ float cdot(int i, float ux, float uy, float uz)
+{
+    float cu = 0.f;
+    if (cx(i)) cu += cx(i) * ux;
+    if (cy(i)) cu += cy(i) * uy;
+    if (cz(i)) cu += cz(i) * uz;
+    return cu;
+}
+
+// Population storage formats.
+//   FP32:  g_i as computed.
+//   BF16 / FP16:  the deviation of g_i from its equilibrium, per unit weight,
+//       h_i = (g_i - f^eq_i(p*, u)) / w_i = ((1 - omega) f^neq_i + S_i / 2) / w_i,
+//     stored as 16-bit kScale * h_i, next to P = p* - sum_i w_i h_i(rounded) in FP32; u is the
+//     velocity stored with the node anyway.  A puller rebuilds
+//       g_i = w_i (P + f^eq_i(0, u) / w_i + h_i),
+//     whose sum over i is the collision's p* exactly.  h is O(velocity gradients and forces),
+//     orders of magnitude below p* and u, so its 16-bit relative error costs little in
+//     absolute terms.  FP16 stores 2^12 h so that values down to ~1e-8 stay normal
+//     (|h| < 16 in any stable run).
+struct StoreF32 {
+    using T = float;
+    static constexpr bool kShifted = false;
+    __device__ static float to_f(float v) { return v; }
+    __device__ static float from_f(float v) { return v; }
+};
+struct StoreF16 {
+    using T = __half;
+    static constexpr bool kShifted = true;
+    // to_f / from_f include the scale 2^12 (exact in binary)
+    __device__ static float to_f(__half v) { return __half2float(v) * (1.0f / 4096.0f); }
+    __device__ static __half from_f(float v) { return __float2half_rn(v * 4096.0f); }
+};
+struct StoreB16 {
+    using T = __nv_bfloat16;
+    static constexpr bool kShifted = true;
+    __device__ static float to_f(__nv_bfloat16 v) { return __bfloat162float(v); }
+    __device__ static __nv_bfloat16 from_f(float v) { return __float2bfloat16_rn(v); }
+};
+
+// h_i of a 16-bit format (storage 1 BF16, 2 FP16) read with a run-time format switch
+__device__ __forceinline__ float load_h16(const void *h, int storage, size_t at)
+{
+    return storage == 1 ? StoreB16::to_f(((const __nv_bfloat16 *)h)[at]) : StoreF16::to_f(((const __half *)h)[at]);
+}
+
+// Neighbours of node (x, y, z) at distance 1: offsets into a scalar array for c = -1, 0, +1 along
+// each axis; periodic wrap in x and y; in z periodic or, with walls, the mirror image about the
+// wall (ghost z = -1 is z = 0, ghost z = nz is z = nz - 1).
+struct Nbr {
+    int xo[3], yo[3], zo[3];
+    float zsgn[3];   // -1 where the z neighbour is a mirror image (odd z component of vectors)
+};
+
+__device__ __forceinline__ Nbr make_nbr(int x, int y, int z, const Grid &G)
+{
+    Nbr n;
+    n.xo[0] = x == 0 ? G.nx - 1 : x - 1;
+    n.xo[1] = x;
+    n.xo[2] = x == G.nx - 1 ? 0 : x + 1;
+    n.yo[0] = (y == 0 ? G.ny - 1 : y - 1) * G.nx;
+    n.yo[1] = y * G.nx;
+    n.yo[2] = (y == G.ny - 1 ? 0 : y + 1) * G.nx;
+    n.zsgn[0] = n.zsgn[1] = n.zsgn[2] = 1.0f;
+    int zm, zp;
+    if (G.wall) {
+        zm = z == 0 ? 0 : z - 1;
+        zp = z == G.nz - 1 ? G.nz - 1 : z + 1;
+        if (z == 0) n.zsgn[0] = -1.0f;
+        if (z == G.nz - 1) n.zsgn[2] = -1.0f;
+    } else {
+        zm = z == 0 ? G.nz - 1 : z - 1;
+        zp = z == G.nz - 1 ? 0 : z + 1;
+    }
+    n.zo[0] = zm * G.nxy;
+    n.zo[1] = z * G.nxy;
+    n.zo[2] = zp * G.nxy;
+    return n;
+}
+
+__device__ __forceinline__ int nidx(const Nbr &n, int i)
+{
+    return n.zo[cz(i) + 1] + n.yo[cy(i) + 1] + n.xo[cx(i) + 1];
 }
 
 }  // namespace tslb

@@ -8,13 +8,16 @@
 namespace tslb {
 
 struct StepArgs {
-    const float *g_in;
+    const float *g_in;       // populations (FP32 g, or 16-bit h for storage 1 / 2)
     float *g_out;
     const float *phi_in;
     float *phi_out;
     const float *u_in;
     float *u_out;
     float *flux;           // 3N scratch of the unfused path (Allen–Cahn flux); unused by the fused path
+    int storage = 0;       // 0 FP32, 1 BF16, 2 FP16 (16-bit formats: two-kernel path only)
+    const float *p_in = nullptr;   // stored p* of the 16-bit formats
+    float *p_out = nullptr;
 };
 
 // One step S^n -> S^{n+1}.  zchunks = z chunks per column tile of the marching kernels (<= 0:
@@ -27,22 +30,43 @@ cudaError_t launch_step_fused2(const Grid &G, const Phys &P, const StepArgs &a, 
 // Boltzmann update of every node from g^n, phi^{n+1} and ubar^n.
 cudaError_t launch_ac_split(const Grid &G, const Phys &P, const float *phi_in, const float *u_in, float *phi_out,
                             int zchunks, cudaStream_t s);
-cudaError_t launch_lbm(const Grid &G, const Phys &P, const float *g_in, const float *phi_new, const float *u_in,
-                       float *g_out, float *u_out, cudaStream_t s);
+// storage: 0 FP32 g; 1 BF16, 2 FP16 h = g / w - p* with p* in p_in / p_out.
+cudaError_t launch_lbm(const Grid &G, const Phys &P, int storage, const void *g_in, const float *p_in,
+                       const float *phi_new, const float *u_in, void *g_out, float *p_out, float *u_out, cudaStream_t s);
+
+// Tiled lattice Boltzmann kernel for the 16-bit formats (storage 1 BF16, 2 FP16), with (P, ubar)
+// and phi^{n+1} staged in shared memory; same arguments as launch_lbm.
+cudaError_t launch_lbm16(const Grid &G, const Phys &P, int storage, const void *h_in, const float *p_in,
+                         const float *phi_new, const float *u_in, void *h_out, float *p_out, float *u_out,
+                         cudaStream_t s);
+
+// 16-bit population formats (h and P; see the storage formats in tslb_device.cuh):
+// initialise from equilibrium (h = 0, P = p*0 or 0), expand to FP32 g (directions [i0, i0+ni)
+// at g[(i-i0)*N + node]), compress FP32 g back (mode 0: P += sum g; mode 1: h and the
+// rounding correction corr += sum w h), and apply the correction P -= corr.
+cudaError_t launch_init16(const Grid &G, int storage, const float *pstar, void *h, float *pst, cudaStream_t s);
+cudaError_t launch_expand16(const Grid &G, int storage, const void *h, const float *pst, const float *u, int i0,
+                            int ni, float *g, cudaStream_t s);
+cudaError_t launch_compress16(const Grid &G, int storage, const float *g, const float *u, int i0, int ni, int mode,
+                              void *h, float *pst, float *corr, cudaStream_t s);
+cudaError_t launch_finish16(const Grid &G, const float *corr, float *pst, cudaStream_t s);
 
 // g = f^eq(p*, u); pstar may be nullptr (p* = 0).
 cudaError_t launch_init(const Grid &G, const float *pstar, const float *u, float *g, cudaStream_t s);
 
-// p = (sum_i g_i) rho cs^2.
-cudaError_t launch_pressure(const Grid &G, const Phys &P, const float *g, const float *phi, float *p,
-                            cudaStream_t s);
+// p = p* rho cs^2 with p* = sum_i g_i (FP32, pst null) or P + sum_i w_i h_i (16-bit formats).
+cudaError_t launch_pressure(const Grid &G, const Phys &P, int storage, const void *g, const float *pst,
+                            const float *phi, float *p, cudaStream_t s);
 
 // FP64 reductions: number of doubles in one partial record, and the two-pass reduction.
 constexpr int kObsFields = 32;
 int observables_blocks(const Grid &G);
 // rho_l, rho_g in FP64 so the mass sum uses the exact parameter values.
-cudaError_t launch_observables(const Grid &G, double rho_l, double rho_g, const float *g, const float *phi,
-                               const float *u, double *partials, int nblocks, double *result, cudaStream_t s);
+// p* is summed from the 27 FP32 population arrays g, or (storage 1 / 2, pst not null) is
+// P + sum_i w_i h_i of a 16-bit format whose h arrays g points to.
+cudaError_t launch_observables(const Grid &G, double rho_l, double rho_g, const void *g, const float *phi,
+                               const float *u, double *partials, int nblocks, double *result, cudaStream_t s,
+                               int storage = 0, const float *pst = nullptr);
 
 // Message returned by lbm_last_error() for the calling thread.
 void set_last_error(const char *msg);

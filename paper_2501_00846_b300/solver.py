@@ -16,6 +16,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libtslb_b300.so")
 
 LBM_OK = 0
+LBM_FP32, LBM_BF16, LBM_FP16 = 0, 1, 2     # lbm_storage: population storage formats
 STATUS = {0: "LBM_OK", -1: "LBM_ERR_ARG", -2: "LBM_ERR_OOM", -3: "LBM_ERR_CUDA",
           -4: "LBM_ERR_NONFINITE", -5: "LBM_ERR_TIMEOUT", -6: "LBM_ERR_STATE"}
 
@@ -248,9 +249,10 @@ class Solver:
         _check(load().lbm_set_state(self._ctx, gp, pp, up, int(step), on_dev.pop()))
 
 
-def from_workload(wl, stream=None) -> Solver:
-    """Solver for an inputs.Workload, initialised with its seeded phi0, u0 and p*0 (FP64 -> FP32)."""
-    s = Solver(stream=stream, **wl.params())
+def from_workload(wl, stream=None, storage: int = LBM_FP32) -> Solver:
+    """Solver for an inputs.Workload, initialised with its seeded phi0, u0 and p*0 (FP64 -> FP32).
+    ``storage``: LBM_FP32, LBM_BF16 or LBM_FP16 population storage."""
+    s = Solver(stream=stream, storage=storage, **wl.params())
     ps = wl.pstar_init()
     s.init_fields(np.ascontiguousarray(wl.phi0(), np.float32), np.ascontiguousarray(wl.u0(), np.float32),
                   None if ps is None else np.ascontiguousarray(ps, np.float32))
