@@ -3,16 +3,21 @@
 
 Workload (default): the rising bubble, 128 x 128 x 256 nodes, walls on z, periodic x and y,
 gas bubble R = 16 at z = 40, density ratio 1000, viscosity ratio 100, gravity from Eo = 10 and
-Mo = 1e-4, W = 4; synthetic seeded inputs.  A step is one time step of the whole box (one fused
-kernel launch).  The state (1.04 GB of FP32 populations and fields per copy) is far larger than
-the 126 MB L2, so consecutive steps stream from HBM and no flush is needed.
+Mo = 1e-4, W = 4; synthetic seeded inputs.  A step is one time step of the whole box: two kernel
+launches by default (the z-marching Allen-Cahn kernel, then the lattice Boltzmann kernel).  The
+state (1.04 GB of FP32 populations and fields per copy, 0.62 GB with 16-bit populations) is far
+larger than the 126 MB L2, so consecutive steps stream from HBM and no flush is needed.
 
   value  MLUPS = nodes * K / device time of K steps (CUDA events on the solver's stream),
          summed over ranks (each rank runs its own replica: weak scaling).
   e2e    the same metric through the public API from pinned host buffers: init from host,
          K steps, observables and a read-back of phi, u, p to host, all inside the timed region.
-  roofline  dominant kernel (the fused step): algorithmic 248 B per node update (read 27 g +
-         phi + 3 u, write the same) over its mean launch duration, against the measured HBM peak.
+  roofline  dominant kernel (the lattice Boltzmann kernel): algorithmic bytes per node update
+         (FP32 244 B: read 27 g + phi + 3 u, write 27 g + 3 u; 16-bit 144 B) over its mean
+         launch duration, against the measured HBM copy peak; step_* the same for the whole step
+         (248 B / 148 B per node update: the state read once and written once).
+  store_compare  the same workload with the other population stores (FP32 / BF16 / FP16),
+         device-timed over min(K, 2000) steps.
   cpu_baseline  the FP64 oracle (plain C, OpenMP) on the host cores, on a bounded sample.
 
 --impl reference runs the FP64 CPU oracle as the reference arm (rank 0 only).
@@ -31,10 +36,15 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-BYTES_PER_LUP = 248          # FP32 step: (27 + 1 + 3) floats read + the same written
+# algorithmic bytes per node update of a whole step: the state read once and written once
+#   FP32:   27 g + phi + 3 ubar floats = 124 B, twice
+#   16-bit: 27 h (2 B) + P + phi + 3 ubar floats = 74 B, twice
+STEP_BYTES = {"fp32": 248, "bf16": 148, "fp16": 148}
 # algorithmic bytes per node of each kernel that can dominate a step
 KERNEL_BYTES = {"lbm_kernel": 244,      # read 27 g + phi^{n+1} + 3 ubar, write 27 g + 3 ubar
-                "fused2_kernel": 248}
+                "fused2_kernel": 248,
+                "lbm16_kernel": 144}    # read 27 h + P + phi^{n+1} + 3 ubar, write 27 h + P + 3 ubar
+STORES = {"fp32": 0, "bf16": 1, "fp16": 2}
 FALLBACK_HBM_GBS = 6400.0
 METRIC = "MLUPS & % HBM peak: coupled LBM+Allen-Cahn step, FP32 vs BF16 store"
 # sources that define each step kernel's device code (the profile of a kernel is reused only while
@@ -42,8 +52,16 @@ METRIC = "MLUPS & % HBM peak: coupled LBM+Allen-Cahn step, FP32 vs BF16 store"
 KERNEL_SOURCES = {
     "lbm_kernel": ["paper_2501_00846_b300/csrc/step_unfused.cu", "paper_2501_00846_b300/csrc/tslb_device.cuh"],
     "fused2_kernel": ["paper_2501_00846_b300/csrc/step_fused2.cu", "paper_2501_00846_b300/csrc/tslb_device.cuh"],
+    "lbm16_kernel": ["paper_2501_00846_b300/csrc/step_lbm16.cu", "paper_2501_00846_b300/csrc/tslb_device.cuh"],
+    "ac_split_kernel": ["paper_2501_00846_b300/csrc/step_split.cu", "paper_2501_00846_b300/csrc/tslb_device.cuh"],
 }
 KERNEL_NAMES = {0: "lbm_kernel", 1: "lbm_kernel", 2: "fused2_kernel"}
+
+
+def kernel_name(path, store):
+    if store != "fp32":
+        return "lbm16_kernel" if path == 0 else "lbm_kernel"
+    return KERNEL_NAMES[path]
 LAUNCHES_PER_STEP = {0: 2, 1: 3, 2: 1}
 
 
@@ -65,13 +83,14 @@ def kernel_source_hash(kernel):
     return h.hexdigest()
 
 
-def measured_traffic(kernel, wl_name, nodes):
+def measured_traffic(kernel, wl_name, nodes, store="fp32"):
     """DRAM bytes per launch of a step kernel from the committed ncu summary
-    profiles/<kernel>_<workload>.txt, if its source hash matches the current kernel sources
-    (else None)."""
+    profiles/<kernel>[_<store>]_<workload>.txt, if its source hash matches the current kernel
+    sources (else None)."""
     if kernel not in KERNEL_SOURCES:
         return None
-    path = os.path.join(ROOT, "profiles", f"{kernel}_{wl_name}.txt")
+    tag = kernel if store == "fp32" else f"{kernel}_{store}"
+    path = os.path.join(ROOT, "profiles", f"{tag}_{wl_name}.txt")
     if not os.path.exists(path):
         return None
     kv = {}
@@ -224,6 +243,9 @@ def main():
     ap.add_argument("--split", type=int, default=0, help="work split of the fused kernel (0 = default)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--store", default="fp32", choices=list(STORES),
+                    help="population storage of the headline line (the others go to store_compare)")
+    ap.add_argument("--no-store-compare", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")
@@ -249,50 +271,70 @@ def main():
     # an explicit stream: the library enqueues every kernel on it and the events are recorded on it
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
-    s = solver.Solver(stream=stream, **wl.params())
-    s.set_path(args.path)
-    s.set_split(args.split)
     phi0 = np.ascontiguousarray(wl.phi0(), np.float32)
     u0 = np.ascontiguousarray(wl.u0(), np.float32)
     ps0 = np.ascontiguousarray(wl.pstar0(), np.float32)
-    s.init_fields(phi0, u0, ps0)
-    s.step(args.warmup)
-    torch.cuda.synchronize()
 
-    # ---- device-timed region: K steps, one fused kernel each --------------------------------
-    sampler = ClockSampler(local)
-    sampler.start()
-    if world > 1:
-        dist.barrier()
-    torch.cuda.synchronize()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    s.step(args.steps)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    if world > 1:
-        dist.barrier()
-    ms = e0.elapsed_time(e1)
-    # the dominant kernel alone, timed the same way on the same stream (paths 0 and 1: the lattice
-    # Boltzmann kernel, launched without advancing the state; path 2: the step is one kernel)
-    kernel_ms = ms / args.steps
-    if args.path in (0, 1):
-        nrep = min(args.steps, 1000)
-        s.run_phase(0, 1)
-        k0 = torch.cuda.Event(enable_timing=True)
-        k1 = torch.cuda.Event(enable_timing=True)
-        k0.record(stream)
-        s.run_phase(1, nrep)
-        k1.record(stream)
+    def device_timed(store, steps, sampler=None):
+        """K steps of one store on the device, CUDA events on the solver's stream; then the
+        dominant kernel alone (paths 0 and 1: the lattice Boltzmann kernel relaunched without
+        advancing the state; path 2: the step is one kernel).  Returns (ms of K steps, ms per
+        dominant-kernel launch, observables after the K steps, the solver)."""
+        s = solver.Solver(stream=stream, storage=STORES[store], **wl.params())
+        s.set_path(args.path)
+        s.set_split(args.split)
+        s.init_fields(phi0, u0, ps0)
+        s.step(args.warmup)
         torch.cuda.synchronize()
-        kernel_ms = k0.elapsed_time(k1) / nrep
+        if sampler is not None:
+            sampler.start()
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        s.step(steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        ms = e0.elapsed_time(e1)
+        kernel_ms = ms / steps
+        if args.path in (0, 1):
+            nrep = min(steps, 1000)
+            s.run_phase(0, 1)
+            k0 = torch.cuda.Event(enable_timing=True)
+            k1 = torch.cuda.Event(enable_timing=True)
+            k0.record(stream)
+            s.run_phase(1, nrep)
+            k1.record(stream)
+            torch.cuda.synchronize()
+            kernel_ms = k0.elapsed_time(k1) / nrep
+        obs = s.observables(allow_nonfinite=True)
+        return ms, kernel_ms, obs, s
+
+    def roofline(store, ms_step, kernel_ms):
+        kernel = kernel_name(args.path, store)
+        kbytes = KERNEL_BYTES[kernel]
+        achieved = kbytes * N / (kernel_ms * 1e-3) / 1e9
+        step_gbs = STEP_BYTES[store] * N / (ms_step * 1e-3) / 1e9
+        return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": measured_traffic(kernel, args.workload, N, store),
+                "kernel": kernel, "kernel_ms": kernel_ms, "bytes_per_lup": kbytes,
+                "step_achieved": step_gbs, "step_frac": step_gbs / peak, "step_bytes_per_lup": STEP_BYTES[store],
+                "peak_source": f"{peak_src} hbm_gbs"}
+
+    peak, peak_src = hbm_peak()
+
+    # ---- device-timed region: K steps of the chosen store -------------------------------------
+    sampler = ClockSampler(local)
+    ms, kernel_ms, obs, s = device_timed(args.store, args.steps, sampler)
     clocks = sampler.stop()
     t = torch.tensor([ms], device="cuda", dtype=torch.float64)
     if world > 1:
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
     ms_max = float(t.item())
-    obs = s.observables(allow_nonfinite=True)
 
     # ---- end to end through the public API from pinned host buffers --------------------------
     phi_h = torch.from_numpy(phi0.reshape(-1)).pin_memory().numpy()
@@ -305,7 +347,7 @@ def main():
     t0 = time.perf_counter()
     s.init_fields(phi_h, u_h, ps_h)
     s.step(args.steps)
-    obs_e2e = s.observables(allow_nonfinite=True)
+    s.observables(allow_nonfinite=True)
     s.read_fields(*outs)
     e2e_s = time.perf_counter() - t0
     te = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
@@ -314,18 +356,26 @@ def main():
     e2e_s = float(te.item())
     s.close()
 
+    # ---- the other population stores on the same workload (device-timed, fewer steps) -------
+    compare = {}
+    if not args.no_store_compare and args.path in (0, 1):
+        kc = min(args.steps, 2000)
+        for store in STORES:
+            if store == args.store:
+                continue
+            cms, ckms, cobs, cs = device_timed(store, kc)
+            cs.close()
+            compare[store] = {"value": world * N * kc / (cms * 1e-3) / 1e6, "unit": "MLUPS", "steps": kc,
+                              "ms_per_step": cms / kc, "roofline": roofline(store, cms / kc, ckms),
+                              "sum_phi_after": cobs["sum_phi"], "nonfinite_after": cobs["n_nonfinite"]}
+
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
         return 0
 
     value = world * N * args.steps / (ms_max * 1e-3) / 1e6
-    kernel = KERNEL_NAMES[args.path]
-    kbytes = KERNEL_BYTES[kernel]
-    achieved = kbytes * N / (kernel_ms * 1e-3) / 1e9
-    step_gbs = BYTES_PER_LUP * N / (ms * 1e-3 / args.steps) / 1e9
-    peak, peak_src = hbm_peak()
-    traffic = measured_traffic(kernel, args.workload, N)
+    dtype = {"fp32": "f32", "bf16": "f32 compute, bf16 store", "fp16": "f32 compute, f16 store"}[args.store]
     line = {
         "metric": METRIC,
         "value": value,
@@ -337,17 +387,13 @@ def main():
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "f32",
+        "dtype": dtype,
         "data": "synthetic",
-        "config": {"workload": wl.name, "nodes": N, "store": "fp32", "path": args.path, "split": args.split,
-                   "l2": "state 1.04 GB per copy >> 126 MB L2: inputs larger than L2, no flush",
+        "config": {"workload": wl.name, "nodes": N, "store": args.store, "path": args.path, "split": args.split,
+                   "l2": "state >= 0.6 GB per copy >> 126 MB L2: inputs larger than L2, no flush",
                    "parallelism": f"replicas x{world}", "sum_phi_after": obs["sum_phi"],
                    "nonfinite_after": obs["n_nonfinite"]},
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": traffic,
-                     "kernel": kernel, "kernel_ms": kernel_ms, "bytes_per_lup": kbytes,
-                     "step_achieved": step_gbs, "step_frac": step_gbs / peak, "step_bytes_per_lup": BYTES_PER_LUP,
-                     "peak_source": f"{peak_src} hbm_gbs"},
+        "roofline": roofline(args.store, ms / args.steps, kernel_ms),
         "e2e": {"value": world * N * args.steps / e2e_s / 1e6, "unit": "MLUPS",
                 "h2d_bytes_per_step": 5 * 4 * N / args.steps,
                 "d2h_bytes_per_step": (5 * 4 * N + 8 * 64) / args.steps,
@@ -355,6 +401,8 @@ def main():
         "gpu_launches": args.steps * LAUNCHES_PER_STEP[args.path],
         "clocks": clocks,
     }
+    if compare:
+        line["store_compare"] = compare
     if world == 1 and not args.no_cpu_baseline:
         v, desc, cores = oracle_sample(args.cpu_seconds)
         line["cpu_baseline"] = {"value": v, "unit": "MLUPS", "cores": cores, "kind": "oracle", "sample": desc}
