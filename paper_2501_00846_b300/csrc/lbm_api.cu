@@ -47,7 +47,8 @@ struct lbm_ctx {
     float *pst[2] = {nullptr, nullptr};  // stored p* of the 16-bit formats (N floats)
     float *phi[2] = {nullptr, nullptr};
     float *u[2] = {nullptr, nullptr};
-    float *flux = nullptr;            // 3N, unfused path only
+    float *flux = nullptr;            // 3N Allen–Cahn flux W of the current state (paths 0, 1)
+    bool w_valid = false;             // flux holds W(phi^n, ubar^n) of the current state
     double *partials = nullptr;       // observables pass-1 records
     double *result = nullptr;         // observables pass-2 record (device)
     double *h_result = nullptr;       // pinned host copy
@@ -249,6 +250,8 @@ lbm_status lbm_init_fields(lbm_ctx *ctx, const float *phi, const float *u, const
         CUDA_TRY(tslb::launch_init(ctx->G, ps, ctx->u[c], ctx->g[c], ctx->stream));
     else
         CUDA_TRY(tslb::launch_init16(ctx->G, ctx->storage, ps, ctx->g[c], ctx->pst[c], ctx->stream));
+    CUDA_TRY(tslb::launch_flux(ctx->G, ctx->P, ctx->phi[c], ctx->u[c], ctx->flux, ctx->stream));
+    ctx->w_valid = true;
     if (!on_device) CUDA_TRY(cudaStreamSynchronize(ctx->stream));
     ctx->step = 0;
     ctx->initialized = true;
@@ -262,12 +265,18 @@ lbm_status lbm_step(lbm_ctx *ctx, int nsteps)
     if (!ctx->initialized) return fail(LBM_ERR_STATE, "lbm_step before lbm_init_fields");
     for (int s = 0; s < nsteps; ++s) {
         const int a = ctx->cur, b = 1 - ctx->cur;
+        if (ctx->path == 0 && !ctx->w_valid) {   // the flux of the current state, once
+            cudaError_t e = tslb::launch_flux(ctx->G, ctx->P, ctx->phi[a], ctx->u[a], ctx->flux, ctx->stream);
+            if (e != cudaSuccess) return fail(LBM_ERR_CUDA, "flux launch failed: %s", cudaGetErrorString(e));
+            ctx->w_valid = true;
+        }
         tslb::StepArgs args{ctx->g[a], ctx->g[b], ctx->phi[a], ctx->phi[b], ctx->u[a], ctx->u[b], ctx->flux,
                             ctx->storage, ctx->pst[a], ctx->pst[b]};
         cudaError_t e = ctx->path == 0   ? tslb::launch_step_split(ctx->G, ctx->P, args, ctx->split, ctx->stream)
                          : ctx->path == 2 ? tslb::launch_step_fused2(ctx->G, ctx->P, args, ctx->split, ctx->stream)
                                           : tslb::launch_step_unfused(ctx->G, ctx->P, args, ctx->stream);
         if (e != cudaSuccess) return fail(LBM_ERR_CUDA, "step launch failed: %s", cudaGetErrorString(e));
+        ctx->w_valid = ctx->path != 2;   // paths 0 and 1 leave W^{n+1} in the flux buffer
         ctx->cur = b;
         ++ctx->step;
     }
@@ -281,14 +290,21 @@ lbm_status lbm_run_phase(lbm_ctx *ctx, int phase, int nrep)
     if (phase != 0 && phase != 1) return fail(LBM_ERR_ARG, "phase must be 0 or 1");
     if (nrep < 0) return fail(LBM_ERR_ARG, "nrep must be >= 0");
     const int a = ctx->cur, b = 1 - ctx->cur;
+    if (phase == 0 && !ctx->w_valid) {
+        CUDA_TRY(tslb::launch_flux(ctx->G, ctx->P, ctx->phi[a], ctx->u[a], ctx->flux, ctx->stream));
+        ctx->w_valid = true;
+    }
+    // phase 1 writes the flux of the idle state: the current state's W is recomputed before the
+    // next use
+    if (phase == 1 && nrep > 0) ctx->w_valid = false;
     for (int r = 0; r < nrep; ++r) {
-        cudaError_t e = phase == 0 ? tslb::launch_ac_split(ctx->G, ctx->P, ctx->phi[a], ctx->u[a], ctx->phi[b], ctx->split,
-                                                           ctx->stream)
+        cudaError_t e = phase == 0 ? tslb::launch_ac_div(ctx->G, ctx->P, ctx->phi[a], ctx->flux, ctx->phi[b], ctx->split,
+                                                         ctx->stream)
                          : ctx->storage != LBM_FP32
                              ? tslb::launch_lbm16(ctx->G, ctx->P, ctx->storage, ctx->g[a], ctx->pst[a], ctx->phi[b],
-                                                  ctx->u[a], ctx->g[b], ctx->pst[b], ctx->u[b], ctx->stream)
+                                                  ctx->u[a], ctx->g[b], ctx->pst[b], ctx->u[b], ctx->flux, ctx->stream)
                              : tslb::launch_lbm(ctx->G, ctx->P, 0, ctx->g[a], nullptr, ctx->phi[b], ctx->u[a],
-                                                ctx->g[b], nullptr, ctx->u[b], ctx->stream);
+                                                ctx->g[b], nullptr, ctx->u[b], ctx->flux, ctx->stream);
         if (e != cudaSuccess) return fail(LBM_ERR_CUDA, "phase launch failed: %s", cudaGetErrorString(e));
     }
     return LBM_OK;
@@ -419,6 +435,8 @@ lbm_status lbm_set_state(lbm_ctx *ctx, const float *g, const float *phi, const f
         }
         CUDA_TRY(tslb::launch_finish16(ctx->G, corr, ctx->pst[c], ctx->stream));
     }
+    CUDA_TRY(tslb::launch_flux(ctx->G, ctx->P, ctx->phi[c], ctx->u[c], ctx->flux, ctx->stream));
+    ctx->w_valid = true;
     CUDA_TRY(cudaStreamSynchronize(ctx->stream));
     ctx->step = step;
     ctx->initialized = true;

@@ -80,7 +80,8 @@ template <class S>
 __global__ void __launch_bounds__(NT) lbm16_kernel(Grid G, Phys P, const typename S::T *__restrict__ hin,
                                                    const float *__restrict__ pin, const float *__restrict__ phi_new,
                                                    const float *__restrict__ ubar, typename S::T *__restrict__ hout,
-                                                   float *__restrict__ pout, float *__restrict__ uout)
+                                                   float *__restrict__ pout, float *__restrict__ uout,
+                                                   float *__restrict__ wout)
 {
     __shared__ float4 sq[HN];    // (A = P - 1.5 |ubar|^2, ubar_x, ubar_y, ubar_z)
     __shared__ float sb[HN];     // B = 3 - 4.5 |ubar|^2
@@ -148,21 +149,28 @@ __global__ void __launch_bounds__(NT) lbm16_kernel(Grid G, Phys P, const typenam
     uout[k] = ux;
     uout[N + k] = uy;
     uout[2 * N + k] = uz;
+    if (wout) {   // Allen–Cahn flux of the new state for the next step
+        float wx, wy, wz;
+        ac_flux(ps[13], gx, gy, gz, ux, uy, uz, P, wx, wy, wz);
+        wout[k] = wx;
+        wout[N + k] = wy;
+        wout[2 * N + k] = wz;
+    }
 }
 
 }  // namespace
 
 cudaError_t launch_lbm16(const Grid &G, const Phys &P, int storage, const void *h_in, const float *p_in,
                          const float *phi_new, const float *u_in, void *h_out, float *p_out, float *u_out,
-                         cudaStream_t s)
+                         float *w_out, cudaStream_t s)
 {
     const dim3 grid((G.nx + TX - 1) / TX, (G.ny + TY - 1) / TY, (G.nz + TZ - 1) / TZ);
     if (storage == 1)
         lbm16_kernel<StoreB16><<<grid, NT, 0, s>>>(G, P, (const __nv_bfloat16 *)h_in, p_in, phi_new, u_in,
-                                                   (__nv_bfloat16 *)h_out, p_out, u_out);
+                                                   (__nv_bfloat16 *)h_out, p_out, u_out, w_out);
     else if (storage == 2)
         lbm16_kernel<StoreF16><<<grid, NT, 0, s>>>(G, P, (const __half *)h_in, p_in, phi_new, u_in,
-                                                   (__half *)h_out, p_out, u_out);
+                                                   (__half *)h_out, p_out, u_out, w_out);
     else
         return cudaErrorInvalidValue;
     return cudaGetLastError();

@@ -71,7 +71,8 @@ template <class S>
 __global__ void __launch_bounds__(128) lbm_kernel(Grid G, Phys P, const typename S::T *__restrict__ gin,
                                                   const float *__restrict__ pin, const float *__restrict__ phi_new,
                                                   const float *__restrict__ ubar, typename S::T *__restrict__ gout,
-                                                  float *__restrict__ pout, float *__restrict__ uout)
+                                                  float *__restrict__ pout, float *__restrict__ uout,
+                                                  float *__restrict__ wout)
 {
     int x, y, z;
     if (!node_coords(G, x, y, z)) return;
@@ -127,6 +128,35 @@ __global__ void __launch_bounds__(128) lbm_kernel(Grid G, Phys P, const typename
     uout[k] = ux;
     uout[N + k] = uy;
     uout[2 * N + k] = uz;
+    if (wout) {   // Allen–Cahn flux of the new state for the next step
+        float wx, wy, wz;
+        ac_flux(ps[13], gx, gy, gz, ux, uy, uz, P, wx, wy, wz);
+        wout[k] = wx;
+        wout[N + k] = wy;
+        wout[2 * N + k] = wz;
+    }
+}
+
+// W = W(phi, ubar) at every node, with the same gradient and flux arithmetic as the lattice
+// Boltzmann kernels (so a restored state continues exactly as an uninterrupted one)
+__global__ void __launch_bounds__(128) flux_kernel(Grid G, Phys P, const float *__restrict__ phi,
+                                                   const float *__restrict__ u, float *__restrict__ w)
+{
+    int x, y, z;
+    if (!node_coords(G, x, y, z)) return;
+    const Nbr n = make_nbr(x, y, z, G);
+    const int k = n.zo[1] + n.yo[1] + x;
+    const size_t N = (size_t)G.N;
+    float ps[27];
+#pragma unroll
+    for (int i = 0; i < 27; ++i) ps[i] = __ldg(phi + nidx(n, i));
+    float gx, gy, gz, lap;
+    grad_lap27(ps, gx, gy, gz, lap);
+    float wx, wy, wz;
+    ac_flux(ps[13], gx, gy, gz, u[k], u[N + k], u[2 * N + k], P, wx, wy, wz);
+    w[k] = wx;
+    w[N + k] = wy;
+    w[2 * N + k] = wz;
 }
 
 // 16-bit formats from equilibrium: h = 0 and P = p*0.
@@ -251,28 +281,36 @@ cudaError_t launch_step_unfused(const Grid &G, const Phys &P, const StepArgs &a,
     ac_update_kernel<<<grid, 128, 0, s>>>(G, P, a.phi_in, a.flux, a.phi_out);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    return launch_lbm(G, P, a.storage, a.g_in, a.p_in, a.phi_out, a.u_in, a.g_out, a.p_out, a.u_out, s);
+    // the scratch flux is consumed: the lattice Boltzmann kernel leaves W^{n+1} in it
+    return launch_lbm(G, P, a.storage, a.g_in, a.p_in, a.phi_out, a.u_in, a.g_out, a.p_out, a.u_out, a.flux, s);
 }
 
 cudaError_t launch_lbm(const Grid &G, const Phys &P, int storage, const void *g_in, const float *p_in,
-                       const float *phi_new, const float *u_in, void *g_out, float *p_out, float *u_out, cudaStream_t s)
+                       const float *phi_new, const float *u_in, void *g_out, float *p_out, float *u_out,
+                       float *w_out, cudaStream_t s)
 {
     const dim3 grid = node_grid(G);
     switch (storage) {
     case 0:
         lbm_kernel<StoreF32><<<grid, 128, 0, s>>>(G, P, (const float *)g_in, nullptr, phi_new, u_in, (float *)g_out,
-                                                  nullptr, u_out);
+                                                  nullptr, u_out, w_out);
         break;
     case 1:
         lbm_kernel<StoreB16><<<grid, 128, 0, s>>>(G, P, (const __nv_bfloat16 *)g_in, p_in, phi_new, u_in,
-                                                  (__nv_bfloat16 *)g_out, p_out, u_out);
+                                                  (__nv_bfloat16 *)g_out, p_out, u_out, w_out);
         break;
     case 2:
         lbm_kernel<StoreF16><<<grid, 128, 0, s>>>(G, P, (const __half *)g_in, p_in, phi_new, u_in, (__half *)g_out,
-                                                  p_out, u_out);
+                                                  p_out, u_out, w_out);
         break;
     default: return cudaErrorInvalidValue;
     }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_flux(const Grid &G, const Phys &P, const float *phi, const float *u, float *w, cudaStream_t s)
+{
+    flux_kernel<<<node_grid(G), 128, 0, s>>>(G, P, phi, u, w);
     return cudaGetLastError();
 }
 

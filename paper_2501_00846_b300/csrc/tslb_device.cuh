@@ -190,6 +190,18 @@ __device__ __forceinline__ void collide_node(const float (&f)[27], float phi, fl
     }
 }
 
+// Allen–Cahn flux W = ubar phi + kappa_AC max(phi (1 - phi), 0) n with the normal
+// n = grad phi / max(|grad phi|, eps) (Allen–Cahn equation; readings R5, R15)
+__device__ __forceinline__ void ac_flux(float ph, float gx, float gy, float gz, float ux, float uy, float uz,
+                                        const Phys &P, float &wx, float &wy, float &wz)
+{
+    const float inv = rsqrtf(fmaxf(gx * gx + gy * gy + gz * gz, kNormalEps * kNormalEps));
+    const float shp = P.kac * fmaxf(ph * (1.0f - ph), 0.0f) * inv;
+    wx = fmaf(ux, ph, shp * gx);
+    wy = fmaf(uy, ph, shp * gy);
+    wz = fmaf(uz, ph, shp * gz);
+}
+
 // f^eq_i(p*, u) / w_i - p* for a velocity projection cu = c_i . u and u2 = |u|^2 (Eq. eqts):
 // -3/2 u^2 + 3 cu + 9/2 cu^2 + cu (9/2 cu^2 - 9/2 u^2), in the even/odd split E + O that the
 // collision uses; the opposite direction (-cu) gives E - O bit for bit.

@@ -14,7 +14,8 @@ struct StepArgs {
     float *phi_out;
     const float *u_in;
     float *u_out;
-    float *flux;           // 3N scratch of the unfused path (Allen–Cahn flux); unused by the fused path
+    float *flux;           // 3N Allen–Cahn flux W: read (W^n) and rewritten (W^{n+1}) by the two-kernel
+                           // step; scratch of the unfused path; unused by the fused path
     int storage = 0;       // 0 FP32, 1 BF16, 2 FP16 (16-bit formats: two-kernel path only)
     const float *p_in = nullptr;   // stored p* of the 16-bit formats
     float *p_out = nullptr;
@@ -26,19 +27,24 @@ cudaError_t launch_step_split(const Grid &G, const Phys &P, const StepArgs &a, i
 cudaError_t launch_step_unfused(const Grid &G, const Phys &P, const StepArgs &a, cudaStream_t s);
 cudaError_t launch_step_fused2(const Grid &G, const Phys &P, const StepArgs &a, int zchunks, cudaStream_t s);
 
-// The two kernels of the two-kernel step: phi^{n+1} from (phi^n, ubar^n), then the lattice
-// Boltzmann update of every node from g^n, phi^{n+1} and ubar^n.
-cudaError_t launch_ac_split(const Grid &G, const Phys &P, const float *phi_in, const float *u_in, float *phi_out,
-                            int zchunks, cudaStream_t s);
-// storage: 0 FP32 g; 1 BF16, 2 FP16 h = g / w - p* with p* in p_in / p_out.
+// The two kernels of the two-kernel step: phi^{n+1} = phi^n - div W^n + D lap phi^n from
+// (phi^n, W^n), then the lattice Boltzmann update of every node from g^n, phi^{n+1} and ubar^n,
+// which also writes W^{n+1} = W(phi^{n+1}, u^{n+1}) into w_out when w_out is not null.
+cudaError_t launch_ac_div(const Grid &G, const Phys &P, const float *phi_in, const float *w, float *phi_out,
+                          int zchunks, cudaStream_t s);
+// storage: 0 FP32 g; 1 BF16, 2 FP16 h (see the storage formats) with P in p_in / p_out.
 cudaError_t launch_lbm(const Grid &G, const Phys &P, int storage, const void *g_in, const float *p_in,
-                       const float *phi_new, const float *u_in, void *g_out, float *p_out, float *u_out, cudaStream_t s);
+                       const float *phi_new, const float *u_in, void *g_out, float *p_out, float *u_out,
+                       float *w_out, cudaStream_t s);
+// W = W(phi, ubar) at every node (the flux the lattice Boltzmann kernels write), for a state set
+// from outside the step (initialisation, restore, after a path that does not keep W).
+cudaError_t launch_flux(const Grid &G, const Phys &P, const float *phi, const float *u, float *w, cudaStream_t s);
 
 // Tiled lattice Boltzmann kernel for the 16-bit formats (storage 1 BF16, 2 FP16), with (P, ubar)
 // and phi^{n+1} staged in shared memory; same arguments as launch_lbm.
 cudaError_t launch_lbm16(const Grid &G, const Phys &P, int storage, const void *h_in, const float *p_in,
                          const float *phi_new, const float *u_in, void *h_out, float *p_out, float *u_out,
-                         cudaStream_t s);
+                         float *w_out, cudaStream_t s);
 
 // 16-bit population formats (h and P; see the storage formats in tslb_device.cuh):
 // initialise from equilibrium (h = 0, P = p*0 or 0), expand to FP32 g (directions [i0, i0+ni)
