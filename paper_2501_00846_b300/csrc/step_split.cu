@@ -17,25 +17,31 @@
 //   Sd = sum_{dx,dy} w1(dx) w1(dy) (phi(x+dx, y+dy) - phi(x, y)),  c = phi(x, y)
 //   div W   = 1/2 [2/3 Q(z) + 1/6 (Q(z-1) + Q(z+1))] + 1/2 [T(z+1) - T(z-1)]
 //   lap phi = 6 [2/3 Sd(z) + 1/6 (Sd(z-1) + Sd(z+1)) + 1/6 ((c(z-1) - c(z)) + (c(z+1) - c(z)))]
-// (the paper's isotropic gradient and, reading R2, Laplacian).  A CTA of 256 threads owns a 32 x 8
-// column tile, one column per thread, and marches a z chunk: per plane it stages (phi, W) of the
-// 34 x 10 halo-1 plane as float4 in shared memory (double-buffered, so one barrier per plane),
-// computes the partials of its column and keeps them in 3-slot register rings (march unrolled by
-// 3).  The next plane is loaded into registers one iteration ahead.  At a wall the ghost plane is
-// the mirror image with W_z negated (R13), so the wall flux vanishes.
+// (the paper's isotropic gradient and, reading R2, Laplacian).  Both in-plane sums factorise once
+// more, over y then x: with the y-sums of one column
+//   Yp = 2/3 phi(y) + 1/6 (phi(y-1) + phi(y+1)),  Yx, Yz likewise for W_x, W_z,
+//   Dy = W_y(y+1) - W_y(y-1),
+// the partials are  Sd = 2/3 Yd(x) + 1/6 (Yd(x-1) + Yd(x+1)) + 1/6 ((c(x-1) - c) + (c(x+1) - c)),
+// with Yd = 1/6 ((phi(y-1) - phi(y)) + (phi(y+1) - phi(y))) (difference form, as FP32 needs),
+// Q = (Yx(x+1) - Yx(x-1)) + 2/3 Dy(x) + 1/6 (Dy(x-1) + Dy(x+1)),  T = 2/3 Yz(x) + 1/6 (Yz(x-1) + Yz(x+1)).
+//
+// One warp owns a column tile of 30 x RY nodes and marches a z chunk with no shared memory and no
+// barrier: lane l holds column x0 - 1 + l (lanes 0 and 31 are the x halo), loads rows y0 - 1 ..
+// y0 + RY of the plane (phi, W) with coalesced loads one plane ahead, forms the y-sums in
+// registers and takes the x-neighbours' sums by warp shuffles.  Plane p (c_p = phi there)
+// contributes to the targets p - 1, p, p + 1 (D is the mobility):
+//   p - 1:  D (Sd + (c_p - c_{p-1})) - Q/12 - T/2      p:  D (4 Sd + (c_{p-1} - c_p)) - Q/3      p + 1:  D Sd - Q/12 + T/2
+// accumulated in two registers per row; target p - 1 is complete after plane p and is stored as
+// c_{p-1} + its sum (the z differences of c in the Laplacian are taken plane to plane, and the
+// large c itself is added last, so Sum phi stays conserved to FP32 round-off).
+// At a wall the ghost plane is the mirror image with W_z negated (R13), so the wall flux
+// vanishes.
 #include "tslb_internal.h"
 
 namespace tslb {
 namespace {
 
-constexpr int TX = 32;
-constexpr int TY = 8;
-constexpr int NT = TX * TY;                     // 256 threads
-constexpr int HX = TX + 2, HY = TY + 2, NH = HX * HY;   // halo-1 plane: 340 points
-constexpr int KH = (NH + NT - 1) / NT;          // staged points per thread (2)
-
 constexpr float W0 = 2.0f / 3.0f, W1 = 1.0f / 6.0f;
-constexpr float WE = W0 * W1, WC = W1 * W1;
 
 __device__ __forceinline__ int wrapc(int v, int n)
 {
@@ -56,109 +62,96 @@ __device__ __forceinline__ float zsign(int p, int nz)
     return (WALL && (p < 0 || p >= nz)) ? -1.0f : 1.0f;
 }
 
-struct DivThread {
-    int off[KH];              // in-plane offsets of the staged points
-    int own;                  // in-plane offset of the own column
-    bool store;               // own column inside the box
-    float4 next[KH];          // (phi, W) of the next plane, loaded one iteration ahead
-    float q[3], t[3], sd[3], c[3];   // rings, slot = plane index mod 3
+constexpr int XO = 30;              // output columns per warp (lanes 1..30)
+constexpr int RY = 4;               // output rows per warp
+constexpr int NROW = RY + 2;        // rows loaded per plane
+constexpr int WPB = 4;              // warps per CTA
+constexpr unsigned FULL = 0xffffffffu;
+
+struct PlaneRows {
+    float phi[NROW], wx[NROW], wy[NROW], wz[NROW];
 };
 
-// One plane of the march: iteration s (phase J = s mod 3) stages plane p = z0 - 1 + s and, from
-// s = 2 on, writes phi^{n+1} of plane p - 1.
-template <bool WALL, int J>
-__device__ __forceinline__ void div_iteration(float4 (&sh)[2][NH], DivThread &th, const Grid &G, const Phys &P,
-                                              const float *__restrict__ phi, const float *__restrict__ w,
-                                              float *__restrict__ phi_out, int z0, int s, int nsteps)
+__device__ __forceinline__ void load_rows(PlaneRows &v, const float *__restrict__ phi, const float *__restrict__ w,
+                                          size_t N, int plane_off, const int (&roff)[NROW], int xg)
 {
-    constexpr int S0 = J, S1 = (J + 2) % 3, S2 = (J + 1) % 3;   // slots of planes p, p-1, p-2
-    const int tid = threadIdx.x;
-    const size_t N = (size_t)G.N;
-    const int p = z0 - 1 + s;
-    float4 *buf = sh[s & 1];
-
 #pragma unroll
-    for (int k = 0; k < KH; ++k)
-        if (tid + k * NT < NH) buf[tid + k * NT] = th.next[k];
-    if (s + 1 < nsteps) {
-        const int pl = zmap<WALL>(p + 1, G.nz) * G.nxy;
-        const float sg = zsign<WALL>(p + 1, G.nz);
-#pragma unroll
-        for (int k = 0; k < KH; ++k)
-            if (tid + k * NT < NH) {
-                const int at = pl + th.off[k];
-                th.next[k] = make_float4(__ldg(phi + at), __ldg(w + at), __ldg(w + N + at), sg * __ldg(w + 2 * N + at));
-            }
-    }
-    __syncthreads();
-
-    const int ty = tid / TX, tx = tid - ty * TX;
-    const int ci = (ty + 1) * HX + tx + 1;
-    const float4 m0 = buf[ci - HX - 1], m1 = buf[ci - HX], m2 = buf[ci - HX + 1];
-    const float4 l0 = buf[ci - 1], cc = buf[ci], l2 = buf[ci + 1];
-    const float4 q0 = buf[ci + HX - 1], q1 = buf[ci + HX], q2 = buf[ci + HX + 1];
-    const float c = cc.x;
-    th.c[S0] = c;
-    th.sd[S0] = fmaf(WE, ((m1.x - c) + (q1.x - c)) + ((l0.x - c) + (l2.x - c)),
-                     WC * (((m0.x - c) + (m2.x - c)) + ((q0.x - c) + (q2.x - c))));
-    th.q[S0] = fmaf(W0, l2.y - l0.y, W1 * ((m2.y - m0.y) + (q2.y - q0.y)))
-             + fmaf(W0, q1.z - m1.z, W1 * ((q0.z - m0.z) + (q2.z - m2.z)));
-    th.t[S0] = fmaf(W0 * W0, cc.w, fmaf(WE, (l0.w + l2.w) + (m1.w + q1.w), WC * ((m0.w + m2.w) + (q0.w + q2.w))));
-
-    if (s >= 2 && th.store) {
-        const float c1 = th.c[S1];
-        const float div = 0.5f * fmaf(W0, th.q[S1], W1 * (th.q[S2] + th.q[S0])) + 0.5f * (th.t[S0] - th.t[S2]);
-        const float lap = 6.0f * fmaf(W0, th.sd[S1], W1 * ((th.sd[S2] + th.sd[S0]) + ((th.c[S2] - c1) + (th.c[S0] - c1))));
-        phi_out[(size_t)(p - 1) * G.nxy + th.own] = c1 - div + P.mob * lap;
+    for (int r = 0; r < NROW; ++r) {
+        const int at = plane_off + roff[r] + xg;
+        v.phi[r] = __ldg(phi + at);
+        v.wx[r] = __ldg(w + at);
+        v.wy[r] = __ldg(w + N + at);
+        v.wz[r] = __ldg(w + 2 * N + at);
     }
 }
 
 template <bool WALL>
-__global__ void __launch_bounds__(NT) ac_div_kernel(Grid G, Phys P, const float *__restrict__ phi,
-                                                    const float *__restrict__ w, float *__restrict__ phi_out,
-                                                    int ncols, int zlen, int units)
+__global__ void __launch_bounds__(WPB * 32) ac_div_kernel(Grid G, Phys P, const float *__restrict__ phi,
+                                                          const float *__restrict__ w, float *__restrict__ phi_out,
+                                                          int ncols, int zlen, int tasks)
 {
-    __shared__ float4 sh[2][NH];
-    DivThread th;
-    const int tid = threadIdx.x;
-    const int nx = G.nx, ny = G.ny, nz = G.nz;
-    const int ncx = (nx + TX - 1) / TX;
+    const int lane = threadIdx.x & 31;
+    const int nx = G.nx, ny = G.ny, nz = G.nz, nxy = G.nxy;
+    const int ncx = (nx + XO - 1) / XO;
     const size_t N = (size_t)G.N;
-    const int ty = tid / TX, tx = tid - ty * TX;
+    const float D = P.mob;
+    const int nwarps = gridDim.x * WPB;
 
-    for (int unit = blockIdx.x; unit < units; unit += gridDim.x) {
-        const int col = unit % ncols;
-        const int z0 = (unit / ncols) * zlen;
+    for (int task = blockIdx.x * WPB + (threadIdx.x >> 5); task < tasks; task += nwarps) {
+        const int col = task % ncols;
+        const int z0 = (task / ncols) * zlen;
         const int zend = min(nz, z0 + zlen);
-        const int x0 = (col % ncx) * TX, y0 = (col / ncx) * TY;
+        const int x0 = (col % ncx) * XO, y0 = (col / ncx) * RY;
+        const int x = x0 - 1 + lane;                       // this lane's column (before wrapping)
+        const int xg = wrapc(x, nx);
+        const bool xout = lane >= 1 && lane <= XO && x < nx;
+        int roff[NROW];
 #pragma unroll
-        for (int k = 0; k < KH; ++k) {
-            const int t = tid + k * NT;
-            const int ry = t / HX, rx = t - ry * HX;
-            th.off[k] = wrapc(y0 - 1 + ry, ny) * nx + wrapc(x0 - 1 + rx, nx);
-        }
-        th.own = min(y0 + ty, ny - 1) * nx + min(x0 + tx, nx - 1);
-        th.store = x0 + tx < nx && y0 + ty < ny;
-        {
-            const int pl = zmap<WALL>(z0 - 1, nz) * G.nxy;
-            const float sg = zsign<WALL>(z0 - 1, nz);
+        for (int r = 0; r < NROW; ++r) roff[r] = wrapc(y0 - 1 + r, ny) * nx;
+
+        float acc1[RY], acc2[RY], cprev[RY];
 #pragma unroll
-            for (int k = 0; k < KH; ++k) {
-                th.next[k] = make_float4(0.f, 0.f, 0.f, 0.f);
-                if (tid + k * NT < NH) {
-                    const int at = pl + th.off[k];
-                    th.next[k] = make_float4(__ldg(phi + at), __ldg(w + at), __ldg(w + N + at),
-                                             sg * __ldg(w + 2 * N + at));
-                }
+        for (int r = 0; r < RY; ++r) acc1[r] = acc2[r] = cprev[r] = 0.0f;
+        PlaneRows cur, nxt;
+        load_rows(cur, phi, w, N, zmap<WALL>(z0 - 1, nz) * nxy, roff, xg);
+        for (int p = z0 - 1; p <= zend; ++p) {
+            if (p + 1 <= zend) load_rows(nxt, phi, w, N, zmap<WALL>(p + 1, nz) * nxy, roff, xg);
+            const float sg = zsign<WALL>(p, nz);
+            const bool store = p - 1 >= z0;
+#pragma unroll
+            for (int r = 0; r < RY; ++r) {
+                // y-sums of this column (phi in difference form against the row's own value)
+                const float c = cur.phi[r + 1];
+                const float yd = W1 * ((cur.phi[r] - c) + (cur.phi[r + 2] - c));
+                const float yx = fmaf(W0, cur.wx[r + 1], W1 * (cur.wx[r] + cur.wx[r + 2]));
+                const float dy = cur.wy[r + 2] - cur.wy[r];
+                const float yz = fmaf(W0, cur.wz[r + 1], W1 * (cur.wz[r] + cur.wz[r + 2]));
+                // the x-neighbours' sums
+                const float cl = __shfl_up_sync(FULL, c, 1), cr = __shfl_down_sync(FULL, c, 1);
+                const float ydl = __shfl_up_sync(FULL, yd, 1), ydr = __shfl_down_sync(FULL, yd, 1);
+                const float yxl = __shfl_up_sync(FULL, yx, 1), yxr = __shfl_down_sync(FULL, yx, 1);
+                const float dyl = __shfl_up_sync(FULL, dy, 1), dyr = __shfl_down_sync(FULL, dy, 1);
+                const float yzl = __shfl_up_sync(FULL, yz, 1), yzr = __shfl_down_sync(FULL, yz, 1);
+                // plane partials: Sd (difference form), Q, T
+                const float sd = fmaf(W0, yd, W1 * ((ydl + ydr) + ((cl - c) + (cr - c))));
+                const float q = (yxr - yxl) + fmaf(W0, dy, W1 * (dyl + dyr));
+                const float t = sg * fmaf(W0, yz, W1 * (yzl + yzr));
+                // contributions of plane p to the targets p - 1, p, p + 1; the z differences of c
+                // are taken between neighbouring planes (cp = c of plane p - 1), and each target's
+                // own c is added last
+                const float cp = cprev[r];
+                const float qs = q * (-1.0f / 12.0f);
+                const float lo = fmaf(D, sd + (c - cp), fmaf(-0.5f, t, qs));
+                const float mid = fmaf(D, fmaf(4.0f, sd, cp - c), q * (-1.0f / 3.0f));
+                const float hi = fmaf(D, sd, fmaf(0.5f, t, qs));
+                const float done = cp + (acc1[r] + lo);                  // phi^{n+1} of plane p - 1
+                if (store && xout && y0 + r < ny) phi_out[(size_t)(p - 1) * nxy + (y0 + r) * nx + x] = done;
+                acc1[r] = acc2[r] + mid;
+                acc2[r] = hi;
+                cprev[r] = c;
             }
+            cur = nxt;
         }
-        const int nsteps = (zend - z0) + 2;
-        for (int s = 0; s < nsteps; s += 3) {
-            div_iteration<WALL, 0>(sh, th, G, P, phi, w, phi_out, z0, s, nsteps);
-            if (s + 1 < nsteps) div_iteration<WALL, 1>(sh, th, G, P, phi, w, phi_out, z0, s + 1, nsteps);
-            if (s + 2 < nsteps) div_iteration<WALL, 2>(sh, th, G, P, phi, w, phi_out, z0, s + 2, nsteps);
-        }
-        __syncthreads();   // the next unit restages both buffers
     }
 }
 
@@ -174,7 +167,7 @@ cudaError_t prepare_ac(LaunchAC &L)
     cudaError_t e;
     if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
     if ((e = cudaDeviceGetAttribute(&L.sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&L.blocks_per_sm, ac_div_kernel<WALL>, NT, 0);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&L.blocks_per_sm, ac_div_kernel<WALL>, WPB * 32, 0);
 }
 
 }  // namespace
@@ -189,25 +182,25 @@ cudaError_t launch_ac_div(const Grid &G, const Phys &P, const float *phi_in, con
         if (e != cudaSuccess) return e;
         if (L.blocks_per_sm < 1) return cudaErrorInvalidConfiguration;
     }
-    const int slots = L.sms * L.blocks_per_sm;
-    const int ncols = ((G.nx + TX - 1) / TX) * ((G.ny + TY - 1) / TY);
-    // default: one unit per resident CTA, chunks of at least 8 planes (2 halo planes per chunk)
+    const int warp_slots = L.sms * L.blocks_per_sm * WPB;
+    const int ncols = ((G.nx + XO - 1) / XO) * ((G.ny + RY - 1) / RY);
+    // default: about one task per resident warp, chunks of at least 16 planes (2 halo planes each)
     int m = zchunks;
     if (m <= 0) {
-        m = slots / ncols;
-        if (m > G.nz / 8) m = G.nz / 8;
+        m = warp_slots / ncols;
+        if (m > G.nz / 16) m = G.nz / 16;
         if (m < 1) m = 1;
     }
     if (m > G.nz) m = G.nz;
     const int zlen = (G.nz + m - 1) / m;
     m = (G.nz + zlen - 1) / zlen;
-    const int units = ncols * m;
-    const int rounds = (units + slots - 1) / slots;
-    const int ctas = (units + rounds - 1) / rounds;
+    const int tasks = ncols * m;
+    const int warps = tasks < warp_slots ? tasks : warp_slots;
+    const int ctas = (warps + WPB - 1) / WPB;
     if (G.wall)
-        ac_div_kernel<true><<<ctas, NT, 0, s>>>(G, P, phi_in, w, phi_out, ncols, zlen, units);
+        ac_div_kernel<true><<<ctas, WPB * 32, 0, s>>>(G, P, phi_in, w, phi_out, ncols, zlen, tasks);
     else
-        ac_div_kernel<false><<<ctas, NT, 0, s>>>(G, P, phi_in, w, phi_out, ncols, zlen, units);
+        ac_div_kernel<false><<<ctas, WPB * 32, 0, s>>>(G, P, phi_in, w, phi_out, ncols, zlen, tasks);
     return cudaGetLastError();
 }
 
