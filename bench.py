@@ -13,9 +13,10 @@ larger than the 126 MB L2, so consecutive steps stream from HBM and no flush is 
   e2e    the same metric through the public API from pinned host buffers: init from host,
          K steps, observables and a read-back of phi, u, p to host, all inside the timed region.
   roofline  dominant kernel (the lattice Boltzmann kernel): algorithmic bytes per node update
-         (FP32 244 B: read 27 g + phi + 3 u, write 27 g + 3 u; 16-bit 144 B) over its mean
-         launch duration, against the measured HBM copy peak; step_* the same for the whole step
-         (248 B / 148 B per node update: the state read once and written once).
+         (FP32 256 B: read 27 g + phi + 3 u, write 27 g + 3 u + the 3-component Allen-Cahn flux;
+         16-bit 156 B) over its mean launch duration, against the measured HBM copy peak; step_*
+         the same for the whole step against the method's state (248 B / 148 B per node update:
+         the state read once and written once; the flux this design carries is not counted).
   store_compare  the same workload with the other population stores (FP32 / BF16 / FP16),
          device-timed over min(K, 2000) steps.
   cpu_baseline  the FP64 oracle (plain C, OpenMP) on the host cores, on a bounded sample.
@@ -36,14 +37,17 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-# algorithmic bytes per node update of a whole step: the state read once and written once
+# algorithmic bytes per node update of a whole step: the method's state read once and written once
 #   FP32:   27 g + phi + 3 ubar floats = 124 B, twice
 #   16-bit: 27 h (2 B) + P + phi + 3 ubar floats = 74 B, twice
+# (the Allen-Cahn flux W that this design carries from the lattice Boltzmann kernel of one step
+# to the Allen-Cahn kernel of the next, 24 B per node, is extra traffic and not counted here)
 STEP_BYTES = {"fp32": 248, "bf16": 148, "fp16": 148}
 # algorithmic bytes per node of each kernel that can dominate a step
-KERNEL_BYTES = {"lbm_kernel": 244,      # read 27 g + phi^{n+1} + 3 ubar, write 27 g + 3 ubar
+KERNEL_BYTES = {"lbm_kernel": 256,      # read 27 g + phi^{n+1} + 3 ubar, write 27 g + 3 ubar + 3 W
                 "fused2_kernel": 248,
-                "lbm16_kernel": 144}    # read 27 h + P + phi^{n+1} + 3 ubar, write 27 h + P + 3 ubar
+                "lbm16_kernel": 156,    # read 27 h + P + phi^{n+1} + 3 ubar, write 27 h + P + 3 ubar + 3 W
+                "ac_div_kernel": 20}    # read phi^n + 3 W^n, write phi^{n+1}
 STORES = {"fp32": 0, "bf16": 1, "fp16": 2}
 FALLBACK_HBM_GBS = 6400.0
 METRIC = "MLUPS & % HBM peak: coupled LBM+Allen-Cahn step, FP32 vs BF16 store"
@@ -53,7 +57,7 @@ KERNEL_SOURCES = {
     "lbm_kernel": ["paper_2501_00846_b300/csrc/step_unfused.cu", "paper_2501_00846_b300/csrc/tslb_device.cuh"],
     "fused2_kernel": ["paper_2501_00846_b300/csrc/step_fused2.cu", "paper_2501_00846_b300/csrc/tslb_device.cuh"],
     "lbm16_kernel": ["paper_2501_00846_b300/csrc/step_lbm16.cu", "paper_2501_00846_b300/csrc/tslb_device.cuh"],
-    "ac_split_kernel": ["paper_2501_00846_b300/csrc/step_split.cu", "paper_2501_00846_b300/csrc/tslb_device.cuh"],
+    "ac_div_kernel": ["paper_2501_00846_b300/csrc/step_split.cu", "paper_2501_00846_b300/csrc/tslb_device.cuh"],
 }
 KERNEL_NAMES = {0: "lbm_kernel", 1: "lbm_kernel", 2: "fused2_kernel"}
 
