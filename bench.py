@@ -19,6 +19,8 @@ larger than the 126 MB L2, so consecutive steps stream from HBM and no flush is 
          the state read once and written once; the flux this design carries is not counted).
   store_compare  the same workload with the other population stores (FP32 / BF16 / FP16),
          device-timed over min(K, 2000) steps.
+  ensemble  the batched ensemble of 256 seeded droplets (32^3 .. 96^3 boxes): autotuned, min(K, 400)
+         steps from CUDA graphs, next to the same boxes advanced one context at a time.
   cpu_baseline  the FP64 oracle (plain C, OpenMP) on the host cores, on a bounded sample.
 
 --impl reference runs the FP64 CPU oracle as the reference arm (rank 0 only).
@@ -235,6 +237,66 @@ def run_reference(args):
     return 0
 
 
+def run_ensemble(args, stream):
+    """The batched ensemble: 256 seeded static droplets in uneven periodic boxes (32^3 .. 96^3,
+    density ratios 10 .. 1000), autotuned, K_e steps replayed from CUDA graphs, device-timed;
+    beside it the same boxes advanced one context at a time (each box's two kernels launched
+    separately), device-timed over fewer steps."""
+    import numpy as np
+    import torch
+    from paper_2501_00846_b300 import inputs, solver
+    wls = inputs.droplet_ensemble()
+    n_nodes = sum(wl.n for wl in wls)
+    ke = min(args.steps, 400)
+    f32 = lambda a: None if a is None else np.ascontiguousarray(a, np.float32)
+    fields = [(f32(wl.phi0()), f32(wl.u0()), f32(wl.pstar_init())) for wl in wls]
+    with torch.cuda.stream(stream):
+        e = solver.Ensemble([wl.params() for wl in wls], stream=stream)
+        for b, (phi0, u0, ps0) in enumerate(fields):
+            e.init_fields(b, phi0, u0, ps0)
+        e.step(2)
+        tun = e.autotune(reps=3)
+        e.step(16)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        e.step(ke)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        bad = sum(e.observables(b, allow_nonfinite=True)["n_nonfinite"] > 0 for b in range(len(wls)))
+        e.close()
+        # the same boxes one context each, every box stepped in turn
+        ku = 20
+        ctxs = []
+        for wl, (phi0, u0, ps0) in zip(wls, fields):
+            c = solver.Solver(stream=stream, **wl.params())
+            c.init_fields(phi0, u0, ps0)
+            ctxs.append(c)
+        for c in ctxs:
+            c.step(2)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(ku):
+            for c in ctxs:
+                c.step(1)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms_u = e0.elapsed_time(e1)
+        for c in ctxs:
+            c.close()
+    value = n_nodes * ke / (ms * 1e-3) / 1e6
+    unbatched = n_nodes * ku / (ms_u * 1e-3) / 1e6
+    return {"workload": "256 static droplets, periodic cubes L in [32, 96], R in [6, L/4], sigma in "
+                        "[0.001, 0.02], density ratio log-uniform in [10, 1000], seed 2501",
+            "nodes": n_nodes, "value": value, "unit": "MLUPS", "steps": ke, "ms_per_step": ms / ke,
+            "launches_per_step": 2, "graph_steps": tun["graph_steps"],
+            "tuning": {k: tun[k] for k in ("lbm_block", "ac_rows", "ac_zlen", "lbm_us", "ac_us")},
+            "unbatched": {"value": unbatched, "unit": "MLUPS", "steps": ku, "ms_per_step": ms_u / ku,
+                          "launches_per_step": 2 * len(wls)},
+            "speedup": value / unbatched, "boxes_nonfinite": int(bad)}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -250,6 +312,7 @@ def main():
     ap.add_argument("--store", default="fp32", choices=list(STORES),
                     help="population storage of the headline line (the others go to store_compare)")
     ap.add_argument("--no-store-compare", action="store_true")
+    ap.add_argument("--no-ensemble", action="store_true", help="skip the 256-droplet batched ensemble")
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")
@@ -373,6 +436,8 @@ def main():
                               "ms_per_step": cms / kc, "roofline": roofline(store, cms / kc, ckms),
                               "sum_phi_after": cobs["sum_phi"], "nonfinite_after": cobs["n_nonfinite"]}
 
+    ensemble = None if args.no_ensemble or rank != 0 else run_ensemble(args, stream)
+
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
@@ -407,6 +472,8 @@ def main():
     }
     if compare:
         line["store_compare"] = compare
+    if ensemble is not None:
+        line["ensemble"] = ensemble
     if world == 1 and not args.no_cpu_baseline:
         v, desc, cores = oracle_sample(args.cpu_seconds)
         line["cpu_baseline"] = {"value": v, "unit": "MLUPS", "cores": cores, "kind": "oracle", "sample": desc}

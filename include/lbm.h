@@ -217,6 +217,65 @@ const char *lbm_last_error(void);
 /* ABI version of this header (incremented on incompatible changes). */
 int lbm_abi_version(void);
 
+/* ---------------------------------------------------------------------------------------------
+ * Batched ensemble: many independent boxes advanced together.  The paper has no counterpart (it
+ * runs one box); this is the library's batching of its step for ensembles of small boxes, which
+ * one at a time cannot fill the GPU.  Every box has its own lbm_params (size, walls, densities,
+ * viscosities, surface tension, mobility, forces; storage must be LBM_FP32) and its own state;
+ * the boxes never interact.  A step advances every box by one time step with two launches for
+ * the whole ensemble: the Allen–Cahn kernel over the (column tile, z chunk) tasks of all boxes,
+ * then the lattice Boltzmann kernel over the node blocks of all boxes.  Each box's arithmetic is
+ * exactly that of lbm_step on a context with the same parameters (bit-identical results), for
+ * every tuning.  Steps are replayed from a captured CUDA graph of graph_steps steps.
+ * ------------------------------------------------------------------------------------------- */
+typedef struct lbm_ens lbm_ens;
+
+/* Launch configuration of the ensemble kernels (lbm_ens_autotune chooses one). */
+typedef struct {
+    int lbm_block;       /* threads per block of the lattice Boltzmann kernel: 64, 128 or 256 */
+    int ac_rows;         /* output rows per warp of the Allen–Cahn kernel: 2 or 4 */
+    int ac_zlen;         /* planes per Allen–Cahn task (z-march depth), >= 1 */
+    int graph_steps;     /* steps per captured CUDA graph: even and >= 2, or 0 for direct launches */
+    double lbm_us;       /* output of lbm_ens_autotune: mean launch time of each kernel with the */
+    double ac_us;        /* chosen configuration, microseconds (0 when not measured) */
+} lbm_tuning;
+
+/* Create an ensemble of nboxes >= 1 boxes; params[b] is validated as in lbm_create (its stream
+ * field is ignored).  stream: the cudaStream_t every ensemble call enqueues on (NULL: the legacy
+ * default stream).  Allocates the packed state of all boxes (two copies of g, phi, ubar and one
+ * flux W: 272 B per node) plus scratch.  The caller owns *out (lbm_ens_destroy).  On error
+ * *out = NULL and nothing is leaked: LBM_ERR_ARG (bad count or box parameters, message names the
+ * box), LBM_ERR_OOM, LBM_ERR_CUDA. */
+lbm_status lbm_ens_create(const lbm_params *params, int nboxes, void *stream, lbm_ens **out);
+void lbm_ens_destroy(lbm_ens *ens);
+
+/* Initial state of box b, as lbm_init_fields (phi: N_b floats, u: 3 N_b, pstar: N_b or NULL). */
+lbm_status lbm_ens_init_fields(lbm_ens *ens, int box, const float *phi, const float *u, const float *pstar,
+                               int on_device);
+
+/* Advance every box by nsteps >= 0 steps (asynchronous on the ensemble's stream).  LBM_ERR_STATE
+ * if any box has not been initialised. */
+lbm_status lbm_ens_step(lbm_ens *ens, int nsteps);
+
+/* Diagnostics and fields of box b, as lbm_observables / lbm_read_fields (synchronising). */
+lbm_status lbm_ens_observables(lbm_ens *ens, int box, lbm_obs *out);
+lbm_status lbm_ens_read_fields(lbm_ens *ens, int box, float *phi, float *u, float *p, int on_device);
+
+/* Launch configuration: get, set (validated; LBM_ERR_ARG for values outside the documented
+ * sets), and autotune: time each candidate (lbm_block in {64, 128, 256}; ac_rows in {2, 4} x
+ * ac_zlen in {8, 16, 32, 64}) over reps >= 1 launches of each kernel on the current state,
+ * without advancing it, keep the fastest, and report it in *out (may be NULL).  The state is
+ * unchanged by autotuning. */
+lbm_status lbm_ens_get_tuning(const lbm_ens *ens, lbm_tuning *out);
+lbm_status lbm_ens_set_tuning(lbm_ens *ens, const lbm_tuning *t);
+lbm_status lbm_ens_autotune(lbm_ens *ens, int reps, lbm_tuning *out);
+
+/* Number of boxes, total nodes, nodes of box b, steps taken; 0 for NULL or a bad index. */
+int lbm_ens_num_boxes(const lbm_ens *ens);
+long long lbm_ens_num_nodes(const lbm_ens *ens);
+long long lbm_ens_box_nodes(const lbm_ens *ens, int box);
+long long lbm_ens_step_count(const lbm_ens *ens);
+
 #ifdef __cplusplus
 }
 #endif

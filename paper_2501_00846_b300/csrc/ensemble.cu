@@ -1,0 +1,595 @@
+// Batched ensemble of independent boxes (lbm_ens_* in include/lbm.h).
+//
+// Small boxes (32^3 ... 96^3) cannot fill 148 SMs one at a time, and a launch per box and kernel
+// costs more than the box's work.  Here the boxes' states are packed one after the other into
+// shared arrays (box b: g[27][N_b], phi[N_b], ubar[3][N_b], W[3][N_b] at node offset off_b), and a
+// step is two launches for the whole ensemble:
+//   1. the Allen–Cahn kernel over a task list that concatenates every box's (column tile, z chunk)
+//      tasks; a warp finds its box by binary search over the boxes' first task and runs
+//      ac_div_task (ac_div.cuh) on it;
+//   2. the lattice Boltzmann kernel over a block list that concatenates every box's node blocks;
+//      a block finds its box the same way and each thread runs lbm_node (lbm_node.cuh) on its node.
+// Both device functions are the ones the one-box kernels use, so every box evolves bit-identically
+// to lbm_step on its own context.  Steps are replayed from a CUDA graph captured once per tuning
+// (graph_steps steps, an even number so the ping-pong buffers return to their start).
+//
+// Tuning (lbm_ens_autotune): threads per lattice Boltzmann block, output rows per Allen–Cahn warp
+// and planes per Allen–Cahn task, timed with CUDA events on launches that do not advance the
+// state (the kernels read the current buffers and write the idle ones; the flux W that the
+// lattice Boltzmann kernel overwrites is recomputed from the current state afterwards, with the
+// same arithmetic).
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <new>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "ac_div.cuh"
+#include "lbm.h"
+#include "lbm_node.cuh"
+#include "tslb_internal.h"
+
+namespace tslb {
+namespace {
+
+struct EnsBox {
+    Grid G;
+    Phys P;
+    long long off;   // first node of the box in the packed arrays
+    int blk0;        // first block of the box in the lattice Boltzmann grid
+    int task0;       // first task of the box in the Allen–Cahn task list
+    int ncols;       // Allen–Cahn column tiles of the box
+    int zlen;        // planes per Allen–Cahn task of the box
+};
+
+constexpr int AC_WPB = 4;   // warps per Allen–Cahn CTA
+
+// The last box whose first block (FIELD 0) or first task (FIELD 1) is <= v; box 0 starts at 0.
+template <int FIELD>
+__device__ __forceinline__ int find_box(const EnsBox *__restrict__ boxes, int nb, int v)
+{
+    int lo = 0, hi = nb - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        const int start = FIELD == 0 ? boxes[mid].blk0 : boxes[mid].task0;
+        if (start <= v)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return lo;
+}
+
+__global__ void __launch_bounds__(256, 3) ens_lbm_kernel(const EnsBox *__restrict__ boxes, int nb,
+                                                      const float *__restrict__ g_in, const float *__restrict__ phi_new,
+                                                      const float *__restrict__ u_in, float *__restrict__ g_out,
+                                                      float *__restrict__ u_out, float *__restrict__ w_out)
+{
+    const int b = find_box<0>(boxes, nb, blockIdx.x);
+    const Grid G = boxes[b].G;
+    const int node = (blockIdx.x - boxes[b].blk0) * blockDim.x + threadIdx.x;
+    if (node >= G.N) return;
+    const Phys P = boxes[b].P;
+    const size_t o = (size_t)boxes[b].off;
+    const int z = node / G.nxy;
+    const int rem = node - z * G.nxy;
+    const int y = rem / G.nx;
+    const int x = rem - y * G.nx;
+    lbm_node<StoreF32>(G, P, g_in + 27 * o, nullptr, phi_new + o, u_in + 3 * o, g_out + 27 * o, nullptr,
+                       u_out + 3 * o, w_out + 3 * o, x, y, z);
+}
+
+template <int RY>
+__global__ void __launch_bounds__(AC_WPB * 32) ens_ac_kernel(const EnsBox *__restrict__ boxes, int nb, int ntasks,
+                                                             const float *__restrict__ phi,
+                                                             const float *__restrict__ w, float *__restrict__ phi_out)
+{
+    const int nwarps = gridDim.x * AC_WPB;
+    for (int task = blockIdx.x * AC_WPB + (threadIdx.x >> 5); task < ntasks; task += nwarps) {
+        const int b = find_box<1>(boxes, nb, task);
+        const Grid G = boxes[b].G;
+        const Phys P = boxes[b].P;
+        const size_t o = (size_t)boxes[b].off;
+        const int local = task - boxes[b].task0;
+        const int ncols = boxes[b].ncols, zlen = boxes[b].zlen;
+        const int col = local % ncols;
+        const int z0 = (local / ncols) * zlen;
+        const int zend = min(G.nz, z0 + zlen);
+        if (G.wall)   // uniform across the warp
+            ac_div_task<true, RY>(G, P, phi + o, w + 3 * o, phi_out + o, col, z0, zend);
+        else
+            ac_div_task<false, RY>(G, P, phi + o, w + 3 * o, phi_out + o, col, z0, zend);
+    }
+}
+
+lbm_status ens_fail(lbm_status s, const char *fmt, ...)
+{
+    char msg[384];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(msg, sizeof msg, fmt, ap);
+    va_end(ap);
+    set_last_error(msg);
+    return s;
+}
+
+}  // namespace
+}  // namespace tslb
+
+using tslb::ens_fail;
+using tslb::EnsBox;
+
+#define ENS_TRY(call)                                                                              \
+    do {                                                                                           \
+        cudaError_t e_ = (call);                                                                   \
+        if (e_ != cudaSuccess)                                                                     \
+            return ens_fail(LBM_ERR_CUDA, "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_),   \
+                            __FILE__, __LINE__);                                                   \
+    } while (0)
+
+struct lbm_ens {
+    int nb = 0;
+    std::vector<lbm_params> prm;
+    std::vector<EnsBox> box;          // host copy of the box table
+    EnsBox *box_d = nullptr;          // device copy
+    long long ntot = 0;
+    float *g[2] = {nullptr, nullptr};
+    float *phi[2] = {nullptr, nullptr};
+    float *u[2] = {nullptr, nullptr};
+    float *w = nullptr;               // Allen–Cahn flux of the current state, all boxes
+    double *partials = nullptr;       // observables scratch (largest box)
+    double *result = nullptr;
+    double *h_result = nullptr;
+    std::vector<char> ready;          // box initialised
+    int cur = 0;
+    long long step = 0;
+    cudaStream_t stream = nullptr;    // the caller's stream (NULL: legacy default)
+    cudaStream_t cap = nullptr;       // private stream used only to capture the step graph
+    lbm_tuning tun{};
+    int sms = 0;
+    int ac_bps[2] = {0, 0};           // resident Allen–Cahn CTAs per SM, ac_rows 2 and 4
+    int lbm_blocks = 0, ac_tasks = 0, ac_ctas = 0;
+    cudaGraphExec_t exec = nullptr;   // graph_steps steps from cur = 0
+};
+
+namespace {
+
+void free_ens(lbm_ens *e)
+{
+    if (!e) return;
+    if (e->exec) cudaGraphExecDestroy(e->exec);
+    for (int b = 0; b < 2; ++b) {
+        cudaFree(e->g[b]);
+        cudaFree(e->phi[b]);
+        cudaFree(e->u[b]);
+    }
+    cudaFree(e->w);
+    cudaFree(e->box_d);
+    cudaFree(e->partials);
+    cudaFree(e->result);
+    if (e->h_result) cudaFreeHost(e->h_result);
+    if (e->cap) cudaStreamDestroy(e->cap);
+    delete e;
+}
+
+bool tuning_valid(const lbm_tuning &t)
+{
+    return (t.lbm_block == 64 || t.lbm_block == 128 || t.lbm_block == 256) && (t.ac_rows == 2 || t.ac_rows == 4) &&
+           t.ac_zlen >= 1 && (t.graph_steps == 0 || (t.graph_steps >= 2 && t.graph_steps % 2 == 0));
+}
+
+// Box table for the current tuning: block and task ranges of every box, uploaded to the device.
+lbm_status build_tables(lbm_ens *e)
+{
+    long long blk = 0, task = 0;
+    const int ry = e->tun.ac_rows;
+    for (int b = 0; b < e->nb; ++b) {
+        EnsBox &B = e->box[b];
+        const int zlen = e->tun.ac_zlen < B.G.nz ? e->tun.ac_zlen : B.G.nz;
+        const int m = (B.G.nz + zlen - 1) / zlen;
+        B.blk0 = (int)blk;
+        B.task0 = (int)task;
+        B.ncols = ((B.G.nx + tslb::AC_XO - 1) / tslb::AC_XO) * ((B.G.ny + ry - 1) / ry);
+        B.zlen = zlen;
+        blk += (B.G.N + e->tun.lbm_block - 1) / e->tun.lbm_block;
+        task += (long long)B.ncols * m;
+    }
+    if (blk >= (1LL << 31) || task >= (1LL << 31))
+        return ens_fail(LBM_ERR_ARG, "ensemble too large for one launch (%lld blocks, %lld tasks)", blk, task);
+    e->lbm_blocks = (int)blk;
+    e->ac_tasks = (int)task;
+    const long long warp_slots = (long long)e->sms * e->ac_bps[ry == 2 ? 0 : 1] * tslb::AC_WPB;
+    const long long warps = task < warp_slots ? task : warp_slots;
+    e->ac_ctas = (int)((warps + tslb::AC_WPB - 1) / tslb::AC_WPB);
+    ENS_TRY(cudaMemcpyAsync(e->box_d, e->box.data(), e->nb * sizeof(EnsBox), cudaMemcpyHostToDevice, e->stream));
+    ENS_TRY(cudaStreamSynchronize(e->stream));
+    if (e->exec) {
+        cudaGraphExecDestroy(e->exec);
+        e->exec = nullptr;
+    }
+    return LBM_OK;
+}
+
+cudaError_t ens_launch_ac(lbm_ens *e, int a, cudaStream_t s)
+{
+    if (e->tun.ac_rows == 2)
+        tslb::ens_ac_kernel<2><<<e->ac_ctas, tslb::AC_WPB * 32, 0, s>>>(e->box_d, e->nb, e->ac_tasks, e->phi[a], e->w,
+                                                                         e->phi[1 - a]);
+    else
+        tslb::ens_ac_kernel<4><<<e->ac_ctas, tslb::AC_WPB * 32, 0, s>>>(e->box_d, e->nb, e->ac_tasks, e->phi[a], e->w,
+                                                                         e->phi[1 - a]);
+    return cudaGetLastError();
+}
+
+cudaError_t ens_launch_lbm(lbm_ens *e, int a, cudaStream_t s)
+{
+    tslb::ens_lbm_kernel<<<e->lbm_blocks, e->tun.lbm_block, 0, s>>>(e->box_d, e->nb, e->g[a], e->phi[1 - a], e->u[a],
+                                                                      e->g[1 - a], e->u[1 - a], e->w);
+    return cudaGetLastError();
+}
+
+// One step from buffers a to 1 - a.
+cudaError_t ens_launch_step(lbm_ens *e, int a, cudaStream_t s)
+{
+    cudaError_t err = ens_launch_ac(e, a, s);
+    if (err != cudaSuccess) return err;
+    return ens_launch_lbm(e, a, s);
+}
+
+// Capture graph_steps steps starting from buffers 0 on the private stream.
+lbm_status build_graph(lbm_ens *e)
+{
+    cudaGraph_t graph = nullptr;
+    ENS_TRY(cudaStreamBeginCapture(e->cap, cudaStreamCaptureModeThreadLocal));
+    cudaError_t err = cudaSuccess;
+    for (int k = 0; k < e->tun.graph_steps && err == cudaSuccess; ++k) err = ens_launch_step(e, k & 1, e->cap);
+    cudaError_t end = cudaStreamEndCapture(e->cap, &graph);
+    if (err != cudaSuccess || end != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        return ens_fail(LBM_ERR_CUDA, "graph capture failed: %s",
+                        cudaGetErrorString(err != cudaSuccess ? err : end));
+    }
+    err = cudaGraphInstantiate(&e->exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (err != cudaSuccess) {
+        e->exec = nullptr;
+        return ens_fail(LBM_ERR_CUDA, "graph instantiation failed: %s", cudaGetErrorString(err));
+    }
+    return LBM_OK;
+}
+
+// W of the current state of every box (after a launch that overwrote it)
+lbm_status recompute_flux(lbm_ens *e)
+{
+    const int c = e->cur;
+    for (int b = 0; b < e->nb; ++b) {
+        const EnsBox &B = e->box[b];
+        const size_t o = (size_t)B.off;
+        ENS_TRY(tslb::launch_flux(B.G, B.P, e->phi[c] + o, e->u[c] + 3 * o, e->w + 3 * o, e->stream));
+    }
+    return LBM_OK;
+}
+
+bool all_ready(const lbm_ens *e)
+{
+    for (char r : e->ready)
+        if (!r) return false;
+    return true;
+}
+
+}  // namespace
+
+extern "C" {
+
+lbm_status lbm_ens_create(const lbm_params *params, int nboxes, void *stream, lbm_ens **out)
+{
+    if (!out) return ens_fail(LBM_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (!params) return ens_fail(LBM_ERR_ARG, "params is NULL");
+    if (nboxes < 1) return ens_fail(LBM_ERR_ARG, "nboxes must be >= 1");
+    for (int b = 0; b < nboxes; ++b) {
+        lbm_status st = tslb::check_params(&params[b]);
+        if (st != LBM_OK) {
+            char msg[512];
+            snprintf(msg, sizeof msg, "box %d: %s", b, lbm_last_error());
+            tslb::set_last_error(msg);
+            return st;
+        }
+        if (params[b].storage != LBM_FP32) return ens_fail(LBM_ERR_ARG, "box %d: ensembles use LBM_FP32 storage", b);
+    }
+    lbm_ens *e = new (std::nothrow) lbm_ens;
+    if (!e) return ens_fail(LBM_ERR_OOM, "host allocation failed");
+    e->nb = nboxes;
+    e->stream = (cudaStream_t)stream;
+    e->prm.assign(params, params + nboxes);
+    e->box.resize(nboxes);
+    e->ready.assign(nboxes, 0);
+    int max_obs = 1;
+    for (int b = 0; b < nboxes; ++b) {
+        EnsBox &B = e->box[b];
+        memset(&B, 0, sizeof B);
+        tslb::params_to_consts(params[b], B.G, B.P);
+        B.off = e->ntot;
+        e->ntot += B.G.N;
+        const int ob = tslb::observables_blocks(B.G);
+        if (ob > max_obs) max_obs = ob;
+    }
+    e->tun.lbm_block = 128;
+    e->tun.ac_rows = 4;
+    e->tun.ac_zlen = 32;
+    e->tun.graph_steps = 16;
+    const size_t N = (size_t)e->ntot;
+    struct {
+        void **p;
+        size_t bytes;
+    } allocs[] = {
+        {(void **)&e->g[0], 27 * N * sizeof(float)}, {(void **)&e->g[1], 27 * N * sizeof(float)},
+        {(void **)&e->phi[0], N * sizeof(float)},    {(void **)&e->phi[1], N * sizeof(float)},
+        {(void **)&e->u[0], 3 * N * sizeof(float)},  {(void **)&e->u[1], 3 * N * sizeof(float)},
+        {(void **)&e->w, 3 * N * sizeof(float)},     {(void **)&e->box_d, nboxes * sizeof(EnsBox)},
+        {(void **)&e->partials, (size_t)max_obs * tslb::kObsFields * sizeof(double)},
+        {(void **)&e->result, tslb::kObsFields * sizeof(double)},
+    };
+    for (auto &a : allocs) {
+        cudaError_t err = cudaMalloc(a.p, a.bytes);
+        if (err != cudaSuccess) {
+            cudaGetLastError();
+            free_ens(e);
+            return ens_fail(err == cudaErrorMemoryAllocation ? LBM_ERR_OOM : LBM_ERR_CUDA, "cudaMalloc(%zu) failed: %s",
+                            a.bytes, cudaGetErrorString(err));
+        }
+    }
+    cudaError_t err = cudaMallocHost(&e->h_result, tslb::kObsFields * sizeof(double));
+    if (err == cudaSuccess) err = cudaStreamCreateWithFlags(&e->cap, cudaStreamNonBlocking);
+    int dev = 0;
+    if (err == cudaSuccess) err = cudaGetDevice(&dev);
+    if (err == cudaSuccess) err = cudaDeviceGetAttribute(&e->sms, cudaDevAttrMultiProcessorCount, dev);
+    if (err == cudaSuccess)
+        err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&e->ac_bps[0], tslb::ens_ac_kernel<2>, tslb::AC_WPB * 32, 0);
+    if (err == cudaSuccess)
+        err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&e->ac_bps[1], tslb::ens_ac_kernel<4>, tslb::AC_WPB * 32, 0);
+    if (err != cudaSuccess) {
+        cudaGetLastError();
+        free_ens(e);
+        return ens_fail(LBM_ERR_CUDA, "ensemble setup failed: %s", cudaGetErrorString(err));
+    }
+    if (e->ac_bps[0] < 1 || e->ac_bps[1] < 1) {
+        free_ens(e);
+        return ens_fail(LBM_ERR_CUDA, "Allen-Cahn ensemble kernel does not fit an SM");
+    }
+    lbm_status st = build_tables(e);
+    if (st != LBM_OK) {
+        free_ens(e);
+        return st;
+    }
+    *out = e;
+    return LBM_OK;
+}
+
+void lbm_ens_destroy(lbm_ens *ens)
+{
+    if (!ens) return;
+    cudaStreamSynchronize(ens->stream);
+    free_ens(ens);
+}
+
+int lbm_ens_num_boxes(const lbm_ens *ens) { return ens ? ens->nb : 0; }
+long long lbm_ens_num_nodes(const lbm_ens *ens) { return ens ? ens->ntot : 0; }
+long long lbm_ens_box_nodes(const lbm_ens *ens, int box)
+{
+    return (ens && box >= 0 && box < ens->nb) ? (long long)ens->box[box].G.N : 0;
+}
+long long lbm_ens_step_count(const lbm_ens *ens) { return ens ? ens->step : 0; }
+
+lbm_status lbm_ens_init_fields(lbm_ens *ens, int box, const float *phi, const float *u, const float *pstar,
+                               int on_device)
+{
+    if (!ens) return ens_fail(LBM_ERR_ARG, "ensemble is NULL");
+    if (box < 0 || box >= ens->nb) return ens_fail(LBM_ERR_ARG, "box %d out of range [0, %d)", box, ens->nb);
+    if (!phi || !u) return ens_fail(LBM_ERR_ARG, "phi and u are required");
+    const EnsBox &B = ens->box[box];
+    const size_t n = (size_t)B.G.N, o = (size_t)B.off;
+    const int c = ens->cur;
+    const cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    ENS_TRY(cudaMemcpyAsync(ens->phi[c] + o, phi, n * sizeof(float), k, ens->stream));
+    ENS_TRY(cudaMemcpyAsync(ens->u[c] + 3 * o, u, 3 * n * sizeof(float), k, ens->stream));
+    const float *ps = nullptr;
+    if (pstar) {   // stage p*0 in the box's idle population slice
+        ENS_TRY(cudaMemcpyAsync(ens->g[1 - c] + 27 * o, pstar, n * sizeof(float), k, ens->stream));
+        ps = ens->g[1 - c] + 27 * o;
+    }
+    ENS_TRY(tslb::launch_init(B.G, ps, ens->u[c] + 3 * o, ens->g[c] + 27 * o, ens->stream));
+    ENS_TRY(tslb::launch_flux(B.G, B.P, ens->phi[c] + o, ens->u[c] + 3 * o, ens->w + 3 * o, ens->stream));
+    if (!on_device) ENS_TRY(cudaStreamSynchronize(ens->stream));
+    ens->ready[box] = 1;
+    return LBM_OK;
+}
+
+lbm_status lbm_ens_step(lbm_ens *ens, int nsteps)
+{
+    if (!ens) return ens_fail(LBM_ERR_ARG, "ensemble is NULL");
+    if (nsteps < 0) return ens_fail(LBM_ERR_ARG, "nsteps must be >= 0");
+    if (!all_ready(ens)) return ens_fail(LBM_ERR_STATE, "lbm_ens_step before every box was initialised");
+    const int K = ens->tun.graph_steps;
+    while (nsteps > 0) {
+        if (K >= 2 && ens->cur == 0 && nsteps >= K) {
+            if (!ens->exec) {
+                lbm_status st = build_graph(ens);
+                if (st != LBM_OK) return st;
+            }
+            ENS_TRY(cudaGraphLaunch(ens->exec, ens->stream));
+            nsteps -= K;
+            ens->step += K;
+        } else {
+            ENS_TRY(ens_launch_step(ens, ens->cur, ens->stream));
+            ens->cur ^= 1;
+            --nsteps;
+            ++ens->step;
+        }
+    }
+    return LBM_OK;
+}
+
+lbm_status lbm_ens_observables(lbm_ens *ens, int box, lbm_obs *out)
+{
+    if (!ens) return ens_fail(LBM_ERR_ARG, "ensemble is NULL");
+    if (box < 0 || box >= ens->nb) return ens_fail(LBM_ERR_ARG, "box %d out of range [0, %d)", box, ens->nb);
+    if (!out) return ens_fail(LBM_ERR_ARG, "out is NULL");
+    if (!ens->ready[box]) return ens_fail(LBM_ERR_STATE, "box %d is not initialised", box);
+    const EnsBox &B = ens->box[box];
+    const lbm_params &p = ens->prm[box];
+    const size_t o = (size_t)B.off;
+    const int c = ens->cur;
+    ENS_TRY(tslb::launch_observables(B.G, p.rho_l, p.rho_g, ens->g[c] + 27 * o, ens->phi[c] + o, ens->u[c] + 3 * o,
+                                     ens->partials, tslb::observables_blocks(B.G), ens->result, ens->stream));
+    ENS_TRY(cudaMemcpyAsync(ens->h_result, ens->result, tslb::kObsFields * sizeof(double), cudaMemcpyDeviceToHost,
+                            ens->stream));
+    ENS_TRY(cudaStreamSynchronize(ens->stream));
+    const double *r = ens->h_result;
+    memset(out, 0, sizeof *out);
+    out->step = (double)ens->step;
+    out->sum_phi = r[0];
+    out->mass = r[1];
+    out->sum_pstar = r[2];
+    for (int a = 0; a < 3; ++a) {
+        out->momentum[a] = r[3 + a];
+        out->centroid_liq[a] = r[6 + a] / r[0];
+        out->centroid_gas[a] = r[9 + a] / r[26];
+        out->vel_liq[a] = r[12 + a] / r[0];
+        out->vel_gas[a] = r[15 + a] / r[26];
+    }
+    out->n_liq = r[19];
+    out->n_gas = r[21];
+    out->p_liq = r[19] > 0 ? r[18] / r[19] : NAN;
+    out->p_gas = r[21] > 0 ? r[20] / r[21] : NAN;
+    out->umax = r[22];
+    out->phi_min = r[23];
+    out->phi_max = r[24];
+    out->n_nonfinite = r[25];
+    if (out->n_nonfinite > 0) return ens_fail(LBM_ERR_NONFINITE, "box %d: %.0f non-finite nodes", box, out->n_nonfinite);
+    return LBM_OK;
+}
+
+lbm_status lbm_ens_read_fields(lbm_ens *ens, int box, float *phi, float *u, float *p, int on_device)
+{
+    if (!ens) return ens_fail(LBM_ERR_ARG, "ensemble is NULL");
+    if (box < 0 || box >= ens->nb) return ens_fail(LBM_ERR_ARG, "box %d out of range [0, %d)", box, ens->nb);
+    if (!ens->ready[box]) return ens_fail(LBM_ERR_STATE, "box %d is not initialised", box);
+    const EnsBox &B = ens->box[box];
+    const size_t n = (size_t)B.G.N, o = (size_t)B.off;
+    const int c = ens->cur;
+    const cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    if (phi) ENS_TRY(cudaMemcpyAsync(phi, ens->phi[c] + o, n * sizeof(float), k, ens->stream));
+    if (u) ENS_TRY(cudaMemcpyAsync(u, ens->u[c] + 3 * o, 3 * n * sizeof(float), k, ens->stream));
+    if (p) {   // p into the box's idle population slice, then copy
+        float *tmp = ens->g[1 - c] + 27 * o;
+        ENS_TRY(tslb::launch_pressure(B.G, B.P, 0, ens->g[c] + 27 * o, nullptr, ens->phi[c] + o, tmp, ens->stream));
+        ENS_TRY(cudaMemcpyAsync(p, tmp, n * sizeof(float), k, ens->stream));
+    }
+    ENS_TRY(cudaStreamSynchronize(ens->stream));
+    return LBM_OK;
+}
+
+lbm_status lbm_ens_get_tuning(const lbm_ens *ens, lbm_tuning *out)
+{
+    if (!ens || !out) return ens_fail(LBM_ERR_ARG, "ensemble and out are required");
+    *out = ens->tun;
+    return LBM_OK;
+}
+
+lbm_status lbm_ens_set_tuning(lbm_ens *ens, const lbm_tuning *t)
+{
+    if (!ens || !t) return ens_fail(LBM_ERR_ARG, "ensemble and tuning are required");
+    if (!tuning_valid(*t))
+        return ens_fail(LBM_ERR_ARG, "tuning out of range (lbm_block %d, ac_rows %d, ac_zlen %d, graph_steps %d)",
+                        t->lbm_block, t->ac_rows, t->ac_zlen, t->graph_steps);
+    ens->tun = *t;
+    return build_tables(ens);
+}
+
+lbm_status lbm_ens_autotune(lbm_ens *ens, int reps, lbm_tuning *out)
+{
+    if (!ens) return ens_fail(LBM_ERR_ARG, "ensemble is NULL");
+    if (reps < 1) return ens_fail(LBM_ERR_ARG, "reps must be >= 1");
+    if (!all_ready(ens)) return ens_fail(LBM_ERR_STATE, "lbm_ens_autotune before every box was initialised");
+    cudaEvent_t t0, t1;
+    ENS_TRY(cudaEventCreate(&t0));
+    cudaError_t err = cudaEventCreate(&t1);
+    if (err != cudaSuccess) {
+        cudaEventDestroy(t0);
+        return ens_fail(LBM_ERR_CUDA, "cudaEventCreate: %s", cudaGetErrorString(err));
+    }
+    lbm_tuning best = ens->tun;
+    lbm_status st = LBM_OK;
+    const int a = ens->cur;
+    // Allen–Cahn kernel: reads phi and W of the current state, writes the idle phi
+    double best_ac = 1e30;
+    const int rows[2] = {2, 4};
+    const int zlens[4] = {8, 16, 32, 64};
+    for (int ri = 0; ri < 2 && st == LBM_OK; ++ri)
+        for (int zi = 0; zi < 4 && st == LBM_OK; ++zi) {
+            ens->tun.ac_rows = rows[ri];
+            ens->tun.ac_zlen = zlens[zi];
+            if ((st = build_tables(ens)) != LBM_OK) break;
+            err = ens_launch_ac(ens, a, ens->stream);
+            if (err == cudaSuccess) err = cudaEventRecord(t0, ens->stream);
+            for (int r = 0; r < reps && err == cudaSuccess; ++r) err = ens_launch_ac(ens, a, ens->stream);
+            if (err == cudaSuccess) err = cudaEventRecord(t1, ens->stream);
+            if (err == cudaSuccess) err = cudaEventSynchronize(t1);
+            float ms = 0.f;
+            if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, t0, t1);
+            if (err != cudaSuccess) {
+                st = ens_fail(LBM_ERR_CUDA, "autotune (Allen-Cahn): %s", cudaGetErrorString(err));
+                break;
+            }
+            const double us = 1e3 * ms / reps;
+            if (us < best_ac) {
+                best_ac = us;
+                best.ac_rows = rows[ri];
+                best.ac_zlen = zlens[zi];
+            }
+        }
+    // lattice Boltzmann kernel: reads g, ubar of the current state and the idle phi just written;
+    // writes the idle g, ubar and W (W of the current state is recomputed below)
+    double best_lbm = 1e30;
+    const int blocks[3] = {64, 128, 256};
+    for (int bi = 0; bi < 3 && st == LBM_OK; ++bi) {
+        ens->tun.lbm_block = blocks[bi];
+        if ((st = build_tables(ens)) != LBM_OK) break;
+        err = ens_launch_lbm(ens, a, ens->stream);
+        if (err == cudaSuccess) err = cudaEventRecord(t0, ens->stream);
+        for (int r = 0; r < reps && err == cudaSuccess; ++r) err = ens_launch_lbm(ens, a, ens->stream);
+        if (err == cudaSuccess) err = cudaEventRecord(t1, ens->stream);
+        if (err == cudaSuccess) err = cudaEventSynchronize(t1);
+        float ms = 0.f;
+        if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, t0, t1);
+        if (err != cudaSuccess) {
+            st = ens_fail(LBM_ERR_CUDA, "autotune (lattice Boltzmann): %s", cudaGetErrorString(err));
+            break;
+        }
+        const double us = 1e3 * ms / reps;
+        if (us < best_lbm) {
+            best_lbm = us;
+            best.lbm_block = blocks[bi];
+        }
+    }
+    cudaEventDestroy(t0);
+    cudaEventDestroy(t1);
+    best.lbm_us = best_lbm < 1e30 ? best_lbm : 0.0;
+    best.ac_us = best_ac < 1e30 ? best_ac : 0.0;
+    ens->tun = best;
+    lbm_status st2 = build_tables(ens);
+    lbm_status st3 = recompute_flux(ens);
+    if (st == LBM_OK) st = st2 != LBM_OK ? st2 : st3;
+    if (st == LBM_OK) {
+        ENS_TRY(cudaStreamSynchronize(ens->stream));
+        if (out) *out = ens->tun;
+    }
+    return st;
+}
+
+}  // extern "C"

@@ -37,6 +37,31 @@ lbm_status fail(lbm_status s, const char *fmt, ...)
 namespace tslb {
 // Record a failure message for lbm_last_error() from another translation unit.
 void set_last_error(const char *msg) { snprintf(g_last_error, sizeof g_last_error, "%s", msg); }
+
+// Grid and FP32 kernel constants of a parameter set (beta = 12 sigma / W, kappa = 3 sigma W / 2,
+// kappa_AC = 4 D / W; Section "Phase-field model").
+void params_to_consts(const lbm_params &p, Grid &G, Phys &P)
+{
+    G.nx = p.nx;
+    G.ny = p.ny;
+    G.nz = p.nz;
+    G.nxy = p.nx * p.ny;
+    G.N = p.nx * p.ny * p.nz;
+    G.wall = p.wall_z;
+    P.rho_g = (float)p.rho_g;
+    P.drho = (float)(p.rho_l - p.rho_g);
+    P.mu_g = (float)p.mu_g;
+    P.dmu = (float)(p.mu_l - p.mu_g);
+    P.beta4 = (float)(4.0 * 12.0 * p.sigma / p.width);
+    P.kappa = (float)(1.5 * p.sigma * p.width);
+    P.mob = (float)p.mobility;
+    P.kac = (float)(4.0 * p.mobility / p.width);
+    for (int a = 0; a < 3; ++a) {
+        P.grav[a] = (float)p.gravity[a];
+        P.body[a] = (float)p.body[a];
+    }
+    P.rho_ref = (float)p.rho_ref;
+}
 }  // namespace tslb
 
 struct lbm_ctx {
@@ -104,29 +129,15 @@ lbm_status validate(const lbm_params *p)
     return LBM_OK;
 }
 
-void make_consts(lbm_ctx *c)
-{
-    const lbm_params &p = c->prm;
-    c->G.nx = p.nx;
-    c->G.ny = p.ny;
-    c->G.nz = p.nz;
-    c->G.nxy = p.nx * p.ny;
-    c->G.N = p.nx * p.ny * p.nz;
-    c->G.wall = p.wall_z;
-    c->P.rho_g = (float)p.rho_g;
-    c->P.drho = (float)(p.rho_l - p.rho_g);
-    c->P.mu_g = (float)p.mu_g;
-    c->P.dmu = (float)(p.mu_l - p.mu_g);
-    c->P.beta4 = (float)(4.0 * 12.0 * p.sigma / p.width);
-    c->P.kappa = (float)(1.5 * p.sigma * p.width);
-    c->P.mob = (float)p.mobility;
-    c->P.kac = (float)(4.0 * p.mobility / p.width);
-    for (int a = 0; a < 3; ++a) {
-        c->P.grav[a] = (float)p.gravity[a];
-        c->P.body[a] = (float)p.body[a];
-    }
-    c->P.rho_ref = (float)p.rho_ref;
-}
+void make_consts(lbm_ctx *c) { tslb::params_to_consts(c->prm, c->G, c->P); }
+
+}  // namespace
+
+namespace tslb {
+lbm_status check_params(const lbm_params *p) { return validate(p); }
+}  // namespace tslb
+
+namespace {
 
 cudaMemcpyKind kind_in(int on_device) { return on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice; }
 cudaMemcpyKind kind_out(int on_device) { return on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost; }

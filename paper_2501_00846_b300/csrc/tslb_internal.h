@@ -3,6 +3,7 @@
 
 #include <cuda_runtime.h>
 
+#include "lbm.h"
 #include "tslb_device.cuh"
 
 namespace tslb {
@@ -76,5 +77,10 @@ cudaError_t launch_observables(const Grid &G, double rho_l, double rho_g, const 
 
 // Message returned by lbm_last_error() for the calling thread.
 void set_last_error(const char *msg);
+
+// Parameter validation of lbm_create (sets the thread's last error) and the kernel constants of
+// a parameter set; shared by the one-box context and the ensemble.
+lbm_status check_params(const lbm_params *p);
+void params_to_consts(const lbm_params &p, Grid &G, Phys &P);
 
 }  // namespace tslb

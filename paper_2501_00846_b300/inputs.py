@@ -216,3 +216,31 @@ def rising_bubble(nx=128, ny=128, nz=256, R=16.0, zc=40.0, Eo=10.0, Mo=1e-4, rho
                     width=width, mobility=mobility, gravity=(0.0, 0.0, -p["g"]), rho_ref=1.0,
                     body=(0.0, 0.0, 0.0), kind="bubble", center=(nx / 2.0, ny / 2.0, zc),
                     radius=R)
+
+
+def droplet_ensemble(n=256, seed=2501, L_min=32, L_max=96, v_max=0.02):
+    """Ensemble of independent static-droplet boxes with seeded, uneven sizes and properties.
+
+    Box b: periodic cube of side L ~ U{L_min .. L_max}; droplet radius R ~ U[6, L/4] at the centre;
+    sigma ~ U[0.001, 0.02]; density ratio rho_L/rho_G log-uniform in [10, 1000] (rho_L = 1); equal
+    kinematic viscosity nu = 0.1 in both phases (tau = 0.8; the dynamic viscosity ratio equals the
+    density ratio); W = 4, D = 0.1; a seeded Fourier velocity field of amplitude ~ U[0, v_max].
+    Every draw comes from numpy default_rng(seed), in box order.  L_min >= 24 (R >= 6 needs
+    L/4 >= 6)."""
+    if L_min < 24 or L_max < L_min:
+        raise ValueError("droplet_ensemble needs 24 <= L_min <= L_max")
+    rng = np.random.default_rng(seed)
+    out = []
+    for b in range(n):
+        L = int(rng.integers(L_min, L_max + 1))
+        R = float(rng.uniform(6.0, L / 4.0))
+        sigma = float(rng.uniform(0.001, 0.02))
+        ratio = float(np.exp(rng.uniform(np.log(10.0), np.log(1000.0))))
+        amp = float(rng.uniform(0.0, v_max))
+        rho_g = 1.0 / ratio
+        c = (L - 1) / 2.0
+        out.append(Workload(name=f"ensemble_droplet_{b}_{L}^3", nx=L, ny=L, nz=L, wall_z=0,
+                            rho_l=1.0, rho_g=rho_g, mu_l=0.1, mu_g=0.1 * rho_g, sigma=sigma, width=4.0,
+                            mobility=0.1, gravity=(0.0, 0.0, 0.0), rho_ref=1.0, body=(0.0, 0.0, 0.0),
+                            kind="droplet", center=(c, c, c), radius=R, noise=amp, seed=seed * 1000 + b))
+    return out

@@ -58,6 +58,15 @@ class LbmObs(ctypes.Structure):
         return out
 
 
+class LbmTuning(ctypes.Structure):
+    """Launch configuration of the ensemble kernels (lbm_tuning)."""
+    _fields_ = [("lbm_block", ctypes.c_int), ("ac_rows", ctypes.c_int), ("ac_zlen", ctypes.c_int),
+                ("graph_steps", ctypes.c_int), ("lbm_us", ctypes.c_double), ("ac_us", ctypes.c_double)]
+
+    def as_dict(self) -> dict:
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
 class LbmError(RuntimeError):
     def __init__(self, status: int, msg: str):
         super().__init__(f"{STATUS.get(status, status)}: {msg}")
@@ -97,6 +106,19 @@ def load(path: str = LIB_PATH):
         "lbm_abi_version": ([], i),
         "lbm_observables_noalloc": ([fp, fp, fp, i, i, i, ctypes.c_double, ctypes.c_double, vp,
                                      ctypes.POINTER(LbmObs)], i),
+        "lbm_ens_create": ([ctypes.POINTER(LbmParams), i, vp, ctypes.POINTER(vp)], i),
+        "lbm_ens_destroy": ([vp], None),
+        "lbm_ens_init_fields": ([vp, i, fp, fp, fp, i], i),
+        "lbm_ens_step": ([vp, i], i),
+        "lbm_ens_observables": ([vp, i, ctypes.POINTER(LbmObs)], i),
+        "lbm_ens_read_fields": ([vp, i, fp, fp, fp, i], i),
+        "lbm_ens_get_tuning": ([vp, ctypes.POINTER(LbmTuning)], i),
+        "lbm_ens_set_tuning": ([vp, ctypes.POINTER(LbmTuning)], i),
+        "lbm_ens_autotune": ([vp, i, ctypes.POINTER(LbmTuning)], i),
+        "lbm_ens_num_boxes": ([vp], i),
+        "lbm_ens_num_nodes": ([vp], ll),
+        "lbm_ens_box_nodes": ([vp, i], ll),
+        "lbm_ens_step_count": ([vp], ll),
     }
     for name, (args, res) in sigs.items():
         fn = getattr(L, name)
@@ -257,3 +279,106 @@ def from_workload(wl, stream=None, storage: int = LBM_FP32) -> Solver:
     s.init_fields(np.ascontiguousarray(wl.phi0(), np.float32), np.ascontiguousarray(wl.u0(), np.float32),
                   None if ps is None else np.ascontiguousarray(ps, np.float32))
     return s
+
+
+class Ensemble:
+    """Independent boxes advanced together by the batched kernels (lbm_ens_* of the C ABI).
+
+    ``boxes``: a list of parameter dicts (keyword arguments of make_params, e.g. Workload.params());
+    ``stream``: a torch.cuda.Stream (default: torch's current stream at construction)."""
+
+    def __init__(self, boxes, stream=None):
+        import torch
+        L = load()
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        arr = (LbmParams * len(boxes))()
+        for b, prm in enumerate(boxes):
+            arr[b] = make_params(stream=None, **prm)
+        self._params = arr
+        self._ens = ctypes.c_void_p()
+        _check(L.lbm_ens_create(arr, len(boxes), stream.cuda_stream, ctypes.byref(self._ens)))
+        self.nboxes = len(boxes)
+        self.shapes = [(p.nz, p.ny, p.nx) for p in arr]
+        self.sizes = [int(L.lbm_ens_box_nodes(self._ens, b)) for b in range(self.nboxes)]
+        self.n = int(L.lbm_ens_num_nodes(self._ens))
+
+    def close(self):
+        if getattr(self, "_ens", None) and self._ens.value:
+            load().lbm_ens_destroy(self._ens)
+            self._ens = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def init_fields(self, box: int, phi, u, pstar=None):
+        n = self.sizes[box]
+        pp, d1 = _ptr(phi, n, False)
+        up, d2 = _ptr(u, 3 * n, False)
+        sp, d3 = _ptr(pstar, n, False)
+        on_dev = {d for d in (d1, d2, d3) if d is not None}
+        if len(on_dev) != 1:
+            raise ValueError("inputs must all be host arrays or all device tensors")
+        _check(load().lbm_ens_init_fields(self._ens, int(box), pp, up, sp, on_dev.pop()))
+
+    def step(self, nsteps: int = 1):
+        _check(load().lbm_ens_step(self._ens, int(nsteps)))
+
+    @property
+    def step_count(self) -> int:
+        return int(load().lbm_ens_step_count(self._ens))
+
+    def observables(self, box: int, allow_nonfinite: bool = False) -> dict:
+        o = LbmObs()
+        st = load().lbm_ens_observables(self._ens, int(box), ctypes.byref(o))
+        if st == -4 and allow_nonfinite:
+            return o.as_dict()
+        _check(st)
+        return o.as_dict()
+
+    def read_fields(self, box: int):
+        """Host copies (phi[nz,ny,nx], u[3,nz,ny,nx], p[nz,ny,nx]) of one box."""
+        shape = self.shapes[box]
+        phi = np.empty(shape, np.float32)
+        u = np.empty((3,) + shape, np.float32)
+        p = np.empty(shape, np.float32)
+        _check(load().lbm_ens_read_fields(self._ens, int(box), phi.ctypes.data, u.ctypes.data, p.ctypes.data, 0))
+        return phi, u, p
+
+    @property
+    def tuning(self) -> dict:
+        t = LbmTuning()
+        _check(load().lbm_ens_get_tuning(self._ens, ctypes.byref(t)))
+        return t.as_dict()
+
+    def set_tuning(self, **kw):
+        t = LbmTuning()
+        _check(load().lbm_ens_get_tuning(self._ens, ctypes.byref(t)))
+        for k, v in kw.items():
+            setattr(t, k, v)
+        _check(load().lbm_ens_set_tuning(self._ens, ctypes.byref(t)))
+
+    def autotune(self, reps: int = 5) -> dict:
+        t = LbmTuning()
+        _check(load().lbm_ens_autotune(self._ens, int(reps), ctypes.byref(t)))
+        return t.as_dict()
+
+
+def ensemble_from_workloads(workloads, stream=None) -> Ensemble:
+    """Ensemble of inputs.Workload boxes, each initialised with its seeded phi0, u0 and p*0."""
+    e = Ensemble([wl.params() for wl in workloads], stream=stream)
+    for b, wl in enumerate(workloads):
+        ps = wl.pstar_init()
+        e.init_fields(b, np.ascontiguousarray(wl.phi0(), np.float32), np.ascontiguousarray(wl.u0(), np.float32),
+                      None if ps is None else np.ascontiguousarray(ps, np.float32))
+    return e

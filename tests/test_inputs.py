@@ -51,3 +51,25 @@ def test_sphere_profile():
     assert phi[16, 16, 16] > 0.999 and phi[0, 0, 0] < 1e-3
     bub = inputs.sphere_phi(32, 32, 32, (15.5, 15.5, 15.5), 8.0, 4.0, inside=0.0)
     np.testing.assert_allclose(bub, 1 - phi)
+
+
+def test_droplet_ensemble_draws():
+    """The 256-box ensemble: seeded, sizes and properties inside the stated ranges, equal
+    kinematic viscosity, and identical for the same seed."""
+    a = inputs.droplet_ensemble()
+    b = inputs.droplet_ensemble()
+    assert len(a) == 256
+    for wa, wb in zip(a, b):
+        assert wa.params() == wb.params() and wa.radius == wb.radius and wa.noise == wb.noise
+    L = np.array([w.nx for w in a])
+    assert L.min() >= 32 and L.max() <= 96 and len(set(L)) > 30
+    for w in a:
+        assert w.nx == w.ny == w.nz and w.wall_z == 0
+        assert 6.0 <= w.radius <= w.nx / 4.0
+        assert 0.001 <= w.sigma <= 0.02
+        assert 10.0 <= w.rho_l / w.rho_g <= 1000.0
+        assert abs(w.mu_l / w.rho_l - w.mu_g / w.rho_g) < 1e-12
+        assert 0.0 <= w.noise <= 0.02
+    ratios = np.log10([w.rho_l / w.rho_g for w in a])
+    assert abs(ratios.mean() - 2.0) < 0.15          # log-uniform over [1, 3] decades
+    assert inputs.droplet_ensemble(seed=5)[0].params() != a[0].params()
