@@ -276,6 +276,64 @@ long long lbm_ens_num_nodes(const lbm_ens *ens);
 long long lbm_ens_box_nodes(const lbm_ens *ens, int box);
 long long lbm_ens_step_count(const lbm_ens *ens);
 
+/* ---------------------------------------------------------------------------------------------
+ * Learned closure.  The paper has no learned component; this is the library's coarse-grid
+ * correction.  A 4-layer network of periodic 3x3x3 convolutions (channels 5 -> 32 -> 32 -> 32 ->
+ * 4, SiLU after the first three layers, biases on all four) maps the normalised state of a box,
+ * x = ((phi, ubar_x, ubar_y, ubar_z, p) - in_shift) / in_scale, to a correction y; the correction
+ * applied is dphi = out_scale[0] y_0 (minus its mean, so sum phi is unchanged) and
+ * dubar_a = out_scale[a+1] y_{a+1}.  Convolutions run on the tensor cores (BF16 weights and
+ * activations, FP32 accumulation); master weights, gradients and Adam moments are FP32.
+ * Parameter order (lbm_cnn_get_params / set_params / get_grads): W1, b1, W2, b2, W3, b3, W4, b4
+ * with W_l[o][i][k] (output channel, input channel, offset k = 9 (dz+1) + 3 (dy+1) + (dx+1)).
+ * Grids: periodic, nx a multiple of 32, ny, nz >= 1.
+ * ------------------------------------------------------------------------------------------- */
+typedef struct lbm_cnn lbm_cnn;
+
+typedef struct {
+    float in_shift[5], in_scale[5];   /* input normalisation of (phi, ubar_x, ubar_y, ubar_z, p) */
+    float out_scale[4];               /* correction scale of (phi, ubar_x, ubar_y, ubar_z) */
+} lbm_closure_norm;
+
+/* Network for nx x ny x nz grids; weights drawn from a seeded Glorot-uniform distribution, biases
+ * zero, Adam moments zero.  stream: the cudaStream_t all calls enqueue on (NULL: legacy default).
+ * LBM_ERR_ARG for nx % 32 != 0 or non-positive sizes. */
+lbm_status lbm_cnn_create(int nx, int ny, int nz, unsigned long long seed, void *stream, lbm_cnn **out);
+void lbm_cnn_destroy(lbm_cnn *cnn);
+int lbm_cnn_num_params(void);
+lbm_status lbm_cnn_get_params(lbm_cnn *cnn, float *params);        /* host, lbm_cnn_num_params() floats */
+lbm_status lbm_cnn_set_params(lbm_cnn *cnn, const float *params);  /* host; resets nothing else */
+lbm_status lbm_cnn_get_grads(lbm_cnn *cnn, float *grads);          /* host, the kept gradients */
+
+/* y = network(x): x [5][N] and y [4][N] FP32 channel-first device arrays (N = nx ny nz). */
+lbm_status lbm_cnn_forward(lbm_cnn *cnn, const float *x, float *y);
+
+/* Forward and backward pass for one sample with the mean-squared loss against t [4][N] (device):
+ * loss (may be NULL) = mean over 4 N values of (y - t)^2; the gradients are kept (added to the
+ * kept ones when accumulate != 0, else replacing them).  Synchronises the stream. */
+lbm_status lbm_cnn_grad(lbm_cnn *cnn, const float *x, const float *t, int accumulate, double *loss);
+
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8, learning rate lr) with the kept gradients
+ * multiplied by grad_scale (e.g. 1 / samples accumulated). */
+lbm_status lbm_cnn_adam_step(lbm_cnn *cnn, float lr, float grad_scale);
+
+/* Network input of a context's current state (FP32 storage): x [5][N] device array. */
+lbm_status lbm_closure_features(lbm_ctx *ctx, const lbm_closure_norm *norm, float *x);
+/* Training target against a reference state: t = ((phi, u)_ref - (phi, ubar)_ctx) / out_scale,
+ * ref: device [>= 4][N] channel-first (phi, u_x, u_y, u_z), t: device [4][N]. */
+lbm_status lbm_closure_target(lbm_ctx *ctx, const float *ref, const lbm_closure_norm *norm, float *t);
+/* Correct a context's state in place with the network (periodic boxes, FP32 storage, grid equal to
+ * the network's): phi += dphi (mean removed), ubar += du, populations shifted by
+ * f^eq(p*, ubar + du) - f^eq(p*, ubar).  Asynchronous on the context's stream. */
+lbm_status lbm_closure_apply(lbm_ctx *ctx, lbm_cnn *cnn, const lbm_closure_norm *norm);
+
+/* 2x restriction of a fine state to the coarse grid (device arrays, channel-first): phi and p
+ * averaged over the 8 fine nodes of a coarse cell, u averaged with weight rho(phi), and
+ * p* = 3 p / rho(phi).  phi, p: N floats; u: 3N; out: 6 N/8 floats (phi, u_x, u_y, u_z, p, p*).
+ * nx, ny, nz even.  rho_l, rho_g: the densities of the phases. */
+lbm_status lbm_restrict2(const float *phi, const float *u, const float *p, int nx, int ny, int nz, double rho_l,
+                         double rho_g, float *out, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

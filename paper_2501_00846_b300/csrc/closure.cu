@@ -1,0 +1,834 @@
+// Learned closure: a 4-layer periodic 3x3x3 convolutional network (5 -> 32 -> 32 -> 32 -> 4
+// channels, SiLU between layers) that corrects phi and ubar of a 2x-coarser grid after each step
+// (lbm_cnn_* and lbm_closure_apply in include/lbm.h).  The paper has no learned component; this
+// is the library's coarse-grid correction, judged against the fine-grid solver.
+//
+// Every convolution (forward, and the backward pass with respect to its input) is an implicit GEMM
+// on the tensor cores: D[o][n] = sum_{k, i} W[o][i][k] a[n + off_k][i], with the K dimension
+// walked in chunks of 16 input channels at one offset k.  A warp computes 32 consecutive nodes of
+// one x row (4 n8 tiles) for up to 32 output channels (2 m16 tiles) with mma.sync m16n8k16
+// (BF16 operands, FP32 accumulation); weights sit in shared memory in fragment order (one 16-byte
+// load per lane and m tile), activations are channel-last BF16 so that a B fragment is two 4-byte
+// loads per node.  The weight gradient, a reduction over all nodes, runs on the CUDA cores in FP32
+// with shared-memory tiles; master weights, gradients and Adam moments are FP32.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <new>
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include "lbm.h"
+#include "tslb_internal.h"
+
+namespace tslb {
+namespace {
+
+constexpr int NLAYER = 4;
+constexpr int CIN[NLAYER] = {5, 32, 32, 32};
+constexpr int COUT[NLAYER] = {32, 32, 32, 4};
+constexpr int CINP[NLAYER] = {16, 32, 32, 32};    // padded to multiples of 16
+constexpr int COUTP[NLAYER] = {32, 32, 32, 16};
+
+constexpr int wcount(int l) { return COUT[l] * CIN[l] * 27; }
+constexpr int pcount(int l) { return wcount(l) + COUT[l]; }
+
+// ---- tensor-core implicit-GEMM convolution -------------------------------------------------
+
+__device__ __forceinline__ void mma_bf16(float (&d)[4], const uint4 &a, uint32_t b0, uint32_t b1)
+{
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};\n"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a.x), "r"(a.y), "r"(a.z), "r"(a.w), "r"(b0), "r"(b1));
+}
+
+__device__ __forceinline__ int cwrap(int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); }
+
+// z[n][o] = bias[o] + sum_{k, i} W[o][i][k] in[n + off_k][i] for the MT*16 (padded) output
+// channels, over a periodic nx x ny x nz grid with nx % 32 == 0.  in: channel-last BF16 with
+// CB*16 channels; wfrag: fragment-ordered BF16 weights [27*CB][MT][32 lanes] (uint4 each);
+// z: channel-last FP32 with MT*16 channels.  A warp owns 32 consecutive nodes of one x row.
+template <int MT, int CB>
+__global__ void __launch_bounds__(128) conv_mma_kernel(int nx, int ny, int nz, const uint4 *__restrict__ wfrag,
+                                                       const __nv_bfloat16 *__restrict__ in,
+                                                       const float *__restrict__ bias, float *__restrict__ z,
+                                                       int ntiles)
+{
+    extern __shared__ uint4 sw[];
+    constexpr int NW = 27 * CB * MT * 32;
+    for (int i = threadIdx.x; i < NW; i += blockDim.x) sw[i] = wfrag[i];
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int g = lane >> 2, t = lane & 3;
+    const int nxy = nx * ny;
+    constexpr int CI = CB * 16, CO = MT * 16;
+    for (int tile = blockIdx.x * 4 + warp; tile < ntiles; tile += gridDim.x * 4) {
+        const int node0 = tile * 32;
+        const int zc = node0 / nxy;
+        const int rem = node0 - zc * nxy;
+        const int yc = rem / nx;
+        const int x0 = rem - yc * nx;
+        float acc[MT][4][4];
+#pragma unroll
+        for (int m = 0; m < MT; ++m)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) acc[m][j][0] = acc[m][j][1] = acc[m][j][2] = acc[m][j][3] = 0.0f;
+#pragma unroll 1
+        for (int k = 0; k < 27; ++k) {
+            const int dz = k / 9 - 1, dy = (k / 3) % 3 - 1, dx = k % 3 - 1;
+            const int row = (cwrap(zc + dz, nz) * ny + cwrap(yc + dy, ny)) * nx;
+            int nb[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) nb[j] = row + cwrap(x0 + 8 * j + g + dx, nx);
+#pragma unroll
+            for (int cb = 0; cb < CB; ++cb) {
+                uint32_t b[4][2];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const uint32_t *p = reinterpret_cast<const uint32_t *>(in + (size_t)nb[j] * CI + cb * 16);
+                    b[j][0] = __ldg(p + t);       // channels 2t, 2t+1 of the chunk
+                    b[j][1] = __ldg(p + t + 4);   // channels 2t+8, 2t+9
+                }
+#pragma unroll
+                for (int m = 0; m < MT; ++m) {
+                    const uint4 a = sw[((k * CB + cb) * MT + m) * 32 + lane];
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) mma_bf16(acc[m][j], a, b[j][0], b[j][1]);
+                }
+            }
+        }
+#pragma unroll
+        for (int m = 0; m < MT; ++m) {
+            const int o = m * 16 + g;
+            const float b0 = bias ? bias[o] : 0.0f, b1 = bias ? bias[o + 8] : 0.0f;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const size_t n = (size_t)node0 + 8 * j + 2 * t;
+                z[n * CO + o] = acc[m][j][0] + b0;
+                z[(n + 1) * CO + o] = acc[m][j][1] + b0;
+                z[n * CO + o + 8] = acc[m][j][2] + b1;
+                z[(n + 1) * CO + o + 8] = acc[m][j][3] + b1;
+            }
+        }
+    }
+}
+
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi)
+{
+    const uint32_t l = __bfloat16_as_ushort(__float2bfloat16_rn(lo));
+    const uint32_t h = __bfloat16_as_ushort(__float2bfloat16_rn(hi));
+    return l | (h << 16);
+}
+
+// Fragment-ordered BF16 weights of one layer from the FP32 master W[o][i][k] (cout x cin x 27).
+// TRANSPOSE builds the weights of the backward pass with respect to the input,
+// Wt[i][o][k] = W[o][i][26 - k], so that the same convolution kernel computes
+// da[n][i] = sum_{k, o} W[o][i][k] dz[n - off_k][o].
+__global__ void pack_weights_kernel(const float *__restrict__ W, int cout, int cin, int mt_count, int cb_count,
+                                    bool transpose, uint4 *__restrict__ frag)
+{
+    const int total = 27 * cb_count * mt_count * 32;
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= total) return;
+    const int lane = idx & 31;
+    const int m = (idx >> 5) % mt_count;
+    const int kc = (idx >> 5) / mt_count;
+    const int k = kc / cb_count, cb = kc % cb_count;
+    const int g = lane >> 2, t = lane & 3;
+    // the GEMM's (row, col) = (output channel, input channel) of this layer or of its transpose
+    const int rows = transpose ? cin : cout, cols = transpose ? cout : cin;
+    auto w = [&](int r, int c) -> float {
+        if (r >= rows || c >= cols) return 0.0f;
+        return transpose ? W[((size_t)c * cin + r) * 27 + (26 - k)] : W[((size_t)r * cin + c) * 27 + k];
+    };
+    const int r0 = m * 16 + g, c0 = cb * 16 + 2 * t;
+    uint4 f;
+    f.x = pack_bf16(w(r0, c0), w(r0, c0 + 1));
+    f.y = pack_bf16(w(r0 + 8, c0), w(r0 + 8, c0 + 1));
+    f.z = pack_bf16(w(r0, c0 + 8), w(r0, c0 + 9));
+    f.w = pack_bf16(w(r0 + 8, c0 + 8), w(r0 + 8, c0 + 9));
+    frag[idx] = f;
+}
+
+// ---- elementwise stages -------------------------------------------------------------------
+
+__device__ __forceinline__ float silu(float z) { return z / (1.0f + __expf(-z)); }
+__device__ __forceinline__ float silu_grad(float z)
+{
+    const float s = 1.0f / (1.0f + __expf(-z));
+    return s * (1.0f + z * (1.0f - s));
+}
+
+// x [5][N] (channel-first FP32) -> a0 [N][16] channel-last BF16, channels 5..15 zero
+__global__ void pack_input_kernel(const float *__restrict__ x, int N, __nv_bfloat16 *__restrict__ a0)
+{
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    uint32_t v[8];
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+        const float lo = 2 * c < 5 ? x[(size_t)(2 * c) * N + n] : 0.0f;
+        const float hi = 2 * c + 1 < 5 ? x[(size_t)(2 * c + 1) * N + n] : 0.0f;
+        v[c] = pack_bf16(lo, hi);
+    }
+    uint4 *d = reinterpret_cast<uint4 *>(a0 + (size_t)n * 16);
+    d[0] = make_uint4(v[0], v[1], v[2], v[3]);
+    d[1] = make_uint4(v[4], v[5], v[6], v[7]);
+}
+
+// a = silu(z), z and a channel-last with C channels (count = N * C)
+__global__ void silu_kernel(const float *__restrict__ z, size_t count, __nv_bfloat16 *__restrict__ a)
+{
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < count) a[i] = __float2bfloat16_rn(silu(z[i]));
+}
+
+// dz = da * silu'(z) (FP32 and its BF16 copy), count = N * C
+__global__ void silu_back_kernel(const float *__restrict__ da, const float *__restrict__ z, size_t count,
+                                 float *__restrict__ dz, __nv_bfloat16 *__restrict__ dzb)
+{
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    const float v = da[i] * silu_grad(z[i]);
+    dz[i] = v;
+    dzb[i] = __float2bfloat16_rn(v);
+}
+
+// y [4][N] channel-first from the last layer's z [N][16]
+__global__ void unpack_output_kernel(const float *__restrict__ z4, int N, float *__restrict__ y)
+{
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) y[(size_t)c * N + n] = z4[(size_t)n * 16 + c];
+}
+
+// Mean-squared loss over the 4 outputs and N nodes against t [4][N]; dz4 = 2 (y - t) / (4 N)
+// (channels 4..15 zero, FP32 and BF16); per-block FP64 partial sums of (y - t)^2.
+__global__ void __launch_bounds__(256) loss_kernel(const float *__restrict__ z4, const float *__restrict__ t, int N,
+                                                   float *__restrict__ dz, __nv_bfloat16 *__restrict__ dzb,
+                                                   double *__restrict__ partial)
+{
+    __shared__ double red[256];
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    double s = 0.0;
+    if (n < N) {
+        const float scale = 2.0f / (4.0f * (float)N);
+#pragma unroll
+        for (int c = 0; c < 16; ++c) {
+            float g = 0.0f;
+            if (c < 4) {
+                const float r = z4[(size_t)n * 16 + c] - t[(size_t)c * N + n];
+                s += (double)r * r;
+                g = scale * r;
+            }
+            dz[(size_t)n * 16 + c] = g;
+            dzb[(size_t)n * 16 + c] = __float2bfloat16_rn(g);
+        }
+    }
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) partial[blockIdx.x] = red[0];
+}
+
+// dW[o][i][k] += sum over a node chunk of dz[n][o] a[n + off_k][i] (FP32 on the CUDA cores).
+// Block (k, chunk): 256 threads; thread -> (o = tid / 8, i = 4 (tid % 8) .. +3); 64-node tiles of
+// dz and of the shifted activations are staged in shared memory.  cop / cip: channel counts of
+// the channel-last dz (FP32) and a (BF16) arrays.
+__global__ void __launch_bounds__(256) dweight_kernel(int nx, int ny, int nz, const float *__restrict__ dz, int cop,
+                                                      const __nv_bfloat16 *__restrict__ a, int cip, int cout, int cin,
+                                                      int chunk, float *__restrict__ dW)
+{
+    __shared__ float sdz[64][33];
+    __shared__ float sa[64][33];
+    const int k = blockIdx.x;
+    const int dzo = k / 9 - 1, dyo = (k / 3) % 3 - 1, dxo = k % 3 - 1;
+    const int N = nx * ny * nz, nxy = nx * ny;
+    const int n0 = blockIdx.y * chunk, n1 = min(N, n0 + chunk);
+    const int o = threadIdx.x >> 3, i0 = (threadIdx.x & 7) * 4;
+    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+    for (int base = n0; base < n1; base += 64) {
+        // stage 64 nodes x 32 channels of dz and of a(n + off_k)
+        for (int e = threadIdx.x; e < 64 * 32; e += 256) {
+            const int r = e >> 5, c = e & 31;
+            const int n = base + r;
+            float vdz = 0.0f, va = 0.0f;
+            if (n < n1) {
+                if (c < cop) vdz = dz[(size_t)n * cop + c];
+                const int zc = n / nxy, rem = n - zc * nxy, yc = rem / nx, xc = rem - yc * nx;
+                const int m = (cwrap(zc + dzo, nz) * ny + cwrap(yc + dyo, ny)) * nx + cwrap(xc + dxo, nx);
+                if (c < cip) va = __bfloat162float(a[(size_t)m * cip + c]);
+            }
+            sdz[r][c] = vdz;
+            sa[r][c] = va;
+        }
+        __syncthreads();
+#pragma unroll 8
+        for (int r = 0; r < 64; ++r) {
+            const float d = sdz[r][o];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) acc[q] = fmaf(d, sa[r][i0 + q], acc[q]);
+        }
+        __syncthreads();
+    }
+    if (o < cout)
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            if (i0 + q < cin) atomicAdd(&dW[((size_t)o * cin + i0 + q) * 27 + k], acc[q]);
+}
+
+// db[o] += sum over a node chunk of dz[n][o]
+__global__ void __launch_bounds__(256) dbias_kernel(const float *__restrict__ dz, int cop, int cout, int N, int chunk,
+                                                    float *__restrict__ db)
+{
+    __shared__ float red[8][33];
+    const int c = threadIdx.x & 31, row = threadIdx.x >> 5;
+    const int n0 = blockIdx.x * chunk, n1 = min(N, n0 + chunk);
+    float s = 0.0f;
+    if (c < cout)
+        for (int n = n0 + row; n < n1; n += 8) s += dz[(size_t)n * cop + c];
+    red[row][c] = s;
+    __syncthreads();
+    if (row == 0 && c < cout) {
+        float tot = 0.0f;
+        for (int r = 0; r < 8; ++r) tot += red[r][c];
+        atomicAdd(&db[c], tot);
+    }
+}
+
+// Adam (beta1 = 0.9, beta2 = 0.999, eps = 1e-8) on the flat FP32 parameters; step t >= 1
+__global__ void adam_kernel(float *__restrict__ p, const float *__restrict__ g, float *__restrict__ m,
+                            float *__restrict__ v, int count, float lr, float gscale, float bc1, float bc2)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    const float gi = g[i] * gscale;
+    const float mi = 0.9f * m[i] + 0.1f * gi;
+    const float vi = 0.999f * v[i] + 0.001f * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    p[i] -= lr * (mi / bc1) / (sqrtf(vi / bc2) + 1e-8f);
+}
+
+
+// ---- closure inputs, targets, correction and restriction --------------------------------
+
+// x = ((phi, ubar, p) - shift) / scale at every node of a one-box state (p = p* rho cs^2)
+__global__ void features_kernel(Grid G, Phys P, const float *__restrict__ g, const float *__restrict__ phi,
+                                const float *__restrict__ u, lbm_closure_norm nrm, float *__restrict__ x)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= G.N) return;
+    const size_t N = (size_t)G.N;
+    float ps = 0.0f;
+#pragma unroll
+    for (int i = 0; i < 27; ++i) ps += g[i * N + k];
+    const float ph = phi[k];
+    const float p = ps * fmaf(ph, P.drho, P.rho_g) * (1.0f / 3.0f);
+    const float v[5] = {ph, u[k], u[N + k], u[2 * N + k], p};
+#pragma unroll
+    for (int c = 0; c < 5; ++c) x[c * N + k] = (v[c] - nrm.in_shift[c]) / nrm.in_scale[c];
+}
+
+// t = ((phi, u) of the reference - (phi, ubar) of the state) / out_scale; ref: [>= 4][N]
+__global__ void target_kernel(int N, const float *__restrict__ phi, const float *__restrict__ u,
+                              const float *__restrict__ ref, lbm_closure_norm nrm, float *__restrict__ t)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= N) return;
+    t[k] = (ref[k] - phi[k]) / nrm.out_scale[0];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+        t[(size_t)(a + 1) * N + k] = (ref[(size_t)(a + 1) * N + k] - u[(size_t)a * N + k]) / nrm.out_scale[a + 1];
+}
+
+// sum of y[0..N) in FP64 (one value per block, then atomically summed)
+__global__ void __launch_bounds__(256) sum_kernel(const float *__restrict__ y, int N, double *__restrict__ out)
+{
+    __shared__ double red[256];
+    double s = 0.0;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < N; k += gridDim.x * blockDim.x) s += y[k];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) atomicAdd(out, red[0]);
+}
+
+// Apply the network's correction y [4][N] to a one-box FP32 state: dphi = s_0 y_0 minus its mean
+// (sum phi unchanged), du = s_a y_a; phi += dphi, ubar += du, and g_i += f^eq_i(p*, ubar + du) -
+// f^eq_i(p*, ubar) (Eq. eqts; p* = sum g unchanged), so the populations carry the new velocity.
+__global__ void correct_kernel(Grid G, const float *__restrict__ y, lbm_closure_norm nrm,
+                               const double *__restrict__ ysum, float *__restrict__ g, float *__restrict__ phi,
+                               float *__restrict__ u)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= G.N) return;
+    const size_t N = (size_t)G.N;
+    const float mean = (float)(*ysum / (double)G.N);
+    const float dphi = nrm.out_scale[0] * (y[k] - mean);
+    const float du[3] = {nrm.out_scale[1] * y[N + k], nrm.out_scale[2] * y[2 * N + k], nrm.out_scale[3] * y[3 * N + k]};
+    float ps = 0.0f;
+    float gi[27];
+#pragma unroll
+    for (int i = 0; i < 27; ++i) {
+        gi[i] = g[i * N + k];
+        ps += gi[i];
+    }
+    const float ux = u[k], uy = u[N + k], uz = u[2 * N + k];
+    float e0[27], e1[27];
+    equilibrium(ps, ux, uy, uz, e0);
+    equilibrium(ps, ux + du[0], uy + du[1], uz + du[2], e1);
+    // __fsub_rn / __fadd_rn are never contracted into an FMA with the products inside e0, e1, so
+    // a zero correction leaves g bit for bit
+#pragma unroll
+    for (int i = 0; i < 27; ++i) g[i * N + k] = __fadd_rn(gi[i], __fsub_rn(e1[i], e0[i]));
+    phi[k] += dphi;
+    u[k] = ux + du[0];
+    u[N + k] = uy + du[1];
+    u[2 * N + k] = uz + du[2];
+}
+
+// 2x restriction of a fine state (phi, u, p on an nx x ny x nz grid, channel-first) to the coarse
+// grid: phi and p averaged over the 8 fine nodes of a coarse cell, u averaged with rho(phi) as
+// weight (momentum / mass), and p* = 3 p / rho(phi_coarse).  out: [6][N/8] = (phi, u, p, p*).
+__global__ void restrict2_kernel(int nx, int ny, int nz, const float *__restrict__ phi, const float *__restrict__ u,
+                                 const float *__restrict__ p, float rho_g, float drho, float *__restrict__ out)
+{
+    const int cx = nx / 2, cy = ny / 2, cz = nz / 2;
+    const int Nc = cx * cy * cz;
+    const int kc = blockIdx.x * blockDim.x + threadIdx.x;
+    if (kc >= Nc) return;
+    const int z = kc / (cx * cy), rem = kc - z * cx * cy, y = rem / cx, x = rem - y * cx;
+    const size_t N = (size_t)nx * ny * nz;
+    float sphi = 0.f, sp = 0.f, sm = 0.f, sj[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+        const size_t f = ((size_t)(2 * z + (c >> 2)) * ny + (2 * y + ((c >> 1) & 1))) * nx + 2 * x + (c & 1);
+        const float ph = phi[f];
+        const float rho = fmaf(ph, drho, rho_g);
+        sphi += ph;
+        sp += p[f];
+        sm += rho;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) sj[a] += rho * u[a * N + f];
+    }
+    const float phc = 0.125f * sphi, pc = 0.125f * sp;
+    out[kc] = phc;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) out[(size_t)(a + 1) * Nc + kc] = sj[a] / sm;
+    out[(size_t)4 * Nc + kc] = pc;
+    out[(size_t)5 * Nc + kc] = 3.0f * pc / fmaf(phc, drho, rho_g);
+}
+
+}  // namespace
+}  // namespace tslb
+
+using tslb::CINP;
+using tslb::COUTP;
+
+struct lbm_cnn {
+    int nx = 0, ny = 0, nz = 0, N = 0;
+    cudaStream_t stream = nullptr;
+    int pofs[tslb::NLAYER + 1] = {};     // parameter offsets: layer l's W at pofs[l], b after it
+    int nparams = 0;
+    float *p = nullptr, *grad = nullptr, *m = nullptr, *v = nullptr;   // FP32 master state
+    uint4 *wf[tslb::NLAYER] = {};        // forward fragments
+    uint4 *wt[tslb::NLAYER] = {};        // transposed fragments (layers 2..4)
+    __nv_bfloat16 *a[tslb::NLAYER] = {}; // layer inputs, channel-last BF16: a[0] [N][16], a[1..3] [N][32]
+    float *z[tslb::NLAYER] = {};         // pre-activations, channel-last FP32 ([N][32], last [N][16])
+    float *dz = nullptr, *da = nullptr;  // [N][32] FP32
+    __nv_bfloat16 *dzb = nullptr;        // [N][32] BF16
+    float *xbuf = nullptr, *ybuf = nullptr;   // [5][N], [4][N] scratch of lbm_closure_apply
+    double *dsum = nullptr;              // loss partials / correction mean
+    double *h_sum = nullptr;             // pinned
+    int loss_blocks = 0;
+    long long adam_t = 0;
+    int conv_blocks = 0;
+};
+
+namespace {
+
+lbm_status cnn_fail(lbm_status s, const char *fmt, ...)
+{
+    char msg[384];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(msg, sizeof msg, fmt, ap);
+    va_end(ap);
+    tslb::set_last_error(msg);
+    return s;
+}
+
+#define CNN_TRY(call)                                                                              \
+    do {                                                                                           \
+        cudaError_t e_ = (call);                                                                   \
+        if (e_ != cudaSuccess)                                                                     \
+            return cnn_fail(LBM_ERR_CUDA, "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_),   \
+                            __FILE__, __LINE__);                                                   \
+    } while (0)
+
+void free_cnn(lbm_cnn *c)
+{
+    if (!c) return;
+    cudaFree(c->p);
+    cudaFree(c->grad);
+    cudaFree(c->m);
+    cudaFree(c->v);
+    for (int l = 0; l < tslb::NLAYER; ++l) {
+        cudaFree(c->wf[l]);
+        cudaFree(c->wt[l]);
+        cudaFree(c->a[l]);
+        cudaFree(c->z[l]);
+    }
+    cudaFree(c->dz);
+    cudaFree(c->da);
+    cudaFree(c->dzb);
+    cudaFree(c->xbuf);
+    cudaFree(c->ybuf);
+    cudaFree(c->dsum);
+    if (c->h_sum) cudaFreeHost(c->h_sum);
+    delete c;
+}
+
+int frag_count(int mt, int cb) { return 27 * cb * mt * 32; }
+
+// forward fragments of every layer and transposed fragments of layers 2..4 from the master weights
+cudaError_t repack(lbm_cnn *c)
+{
+    for (int l = 0; l < tslb::NLAYER; ++l) {
+        const int mt = COUTP[l] / 16, cb = CINP[l] / 16;
+        const int n = frag_count(mt, cb);
+        tslb::pack_weights_kernel<<<(n + 255) / 256, 256, 0, c->stream>>>(c->p + c->pofs[l], tslb::COUT[l],
+                                                                           tslb::CIN[l], mt, cb, false, c->wf[l]);
+        if (l > 0) {
+            const int mtt = CINP[l] / 16, cbt = COUTP[l] / 16;
+            const int nt = frag_count(mtt, cbt);
+            tslb::pack_weights_kernel<<<(nt + 255) / 256, 256, 0, c->stream>>>(c->p + c->pofs[l], tslb::COUT[l],
+                                                                                tslb::CIN[l], mtt, cbt, true, c->wt[l]);
+        }
+    }
+    return cudaGetLastError();
+}
+
+template <int MT, int CB>
+cudaError_t launch_conv(lbm_cnn *c, const uint4 *wfrag, const __nv_bfloat16 *in, const float *bias, float *out)
+{
+    const size_t smem = (size_t)frag_count(MT, CB) * sizeof(uint4);
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(tslb::conv_mma_kernel<MT, CB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    const int ntiles = c->N / 32;
+    int blocks = (ntiles + 3) / 4;
+    if (blocks > c->conv_blocks) blocks = c->conv_blocks;
+    tslb::conv_mma_kernel<MT, CB><<<blocks, 128, smem, c->stream>>>(c->nx, c->ny, c->nz, wfrag, in, bias, out, ntiles);
+    return cudaGetLastError();
+}
+
+cudaError_t forward(lbm_cnn *c, const float *x)
+{
+    const int N = c->N;
+    cudaError_t e;
+    tslb::pack_input_kernel<<<(N + 255) / 256, 256, 0, c->stream>>>(x, N, c->a[0]);
+    if ((e = launch_conv<2, 1>(c, c->wf[0], c->a[0], c->p + c->pofs[0] + tslb::wcount(0), c->z[0])) != cudaSuccess)
+        return e;
+    for (int l = 1; l < tslb::NLAYER; ++l) {
+        const size_t cnt = (size_t)N * 32;
+        tslb::silu_kernel<<<(unsigned)((cnt + 255) / 256), 256, 0, c->stream>>>(c->z[l - 1], cnt, c->a[l]);
+        const float *bias = c->p + c->pofs[l] + tslb::wcount(l);
+        e = l < 3 ? launch_conv<2, 2>(c, c->wf[l], c->a[l], bias, c->z[l])
+                  : launch_conv<1, 2>(c, c->wf[l], c->a[l], bias, c->z[l]);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t backward(lbm_cnn *c)
+{
+    const int N = c->N;
+    const int chunk = 4096;
+    const int nchunk = (N + chunk - 1) / chunk;
+    cudaError_t e;
+    // dz of the last layer is in dz / dzb with 16 channels (written by the loss kernel)
+    for (int l = tslb::NLAYER - 1; l >= 0; --l) {
+        const int cop = COUTP[l];
+        float *dW = c->grad + c->pofs[l];
+        float *db = dW + tslb::wcount(l);
+        tslb::dweight_kernel<<<dim3(27, nchunk), 256, 0, c->stream>>>(c->nx, c->ny, c->nz, c->dz, cop, c->a[l], CINP[l],
+                                                                       tslb::COUT[l], tslb::CIN[l], chunk, dW);
+        tslb::dbias_kernel<<<nchunk, 256, 0, c->stream>>>(c->dz, cop, tslb::COUT[l], N, chunk, db);
+        if (l == 0) break;
+        // da_{l-1}[n][i] = sum_{k,o} W_l[o][i][k] dz_l[n - off_k][o]
+        e = l == 3 ? launch_conv<2, 1>(c, c->wt[l], c->dzb, nullptr, c->da)
+                   : launch_conv<2, 2>(c, c->wt[l], c->dzb, nullptr, c->da);
+        if (e != cudaSuccess) return e;
+        const size_t cnt = (size_t)N * 32;
+        tslb::silu_back_kernel<<<(unsigned)((cnt + 255) / 256), 256, 0, c->stream>>>(c->da, c->z[l - 1], cnt, c->dz,
+                                                                                      c->dzb);
+    }
+    return cudaGetLastError();
+}
+
+// seeded Glorot-uniform weights (splitmix64 stream), zero biases
+void init_params(lbm_cnn *c, unsigned long long seed, float *h)
+{
+    unsigned long long s = seed + 0x9E3779B97F4A7C15ULL;
+    auto next = [&]() {
+        unsigned long long z = (s += 0x9E3779B97F4A7C15ULL);
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+        z ^= z >> 31;
+        return (double)(z >> 11) * (1.0 / 9007199254740992.0);
+    };
+    for (int l = 0; l < tslb::NLAYER; ++l) {
+        const double bound = sqrt(6.0 / (27.0 * (tslb::CIN[l] + tslb::COUT[l])));
+        float *w = h + c->pofs[l];
+        for (int i = 0; i < tslb::wcount(l); ++i) w[i] = (float)((2.0 * next() - 1.0) * bound);
+        for (int o = 0; o < tslb::COUT[l]; ++o) w[tslb::wcount(l) + o] = 0.0f;
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+int lbm_cnn_num_params(void)
+{
+    int n = 0;
+    for (int l = 0; l < tslb::NLAYER; ++l) n += tslb::pcount(l);
+    return n;
+}
+
+lbm_status lbm_cnn_create(int nx, int ny, int nz, unsigned long long seed, void *stream, lbm_cnn **out)
+{
+    if (!out) return cnn_fail(LBM_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (nx < 32 || nx % 32 != 0 || ny < 1 || nz < 1)
+        return cnn_fail(LBM_ERR_ARG, "network grid needs nx a positive multiple of 32 and ny, nz >= 1");
+    const long long n = (long long)nx * ny * nz;
+    if (n * 32 >= (1LL << 31)) return cnn_fail(LBM_ERR_ARG, "network grid too large");
+    lbm_cnn *c = new (std::nothrow) lbm_cnn;
+    if (!c) return cnn_fail(LBM_ERR_OOM, "host allocation failed");
+    c->nx = nx;
+    c->ny = ny;
+    c->nz = nz;
+    c->N = (int)n;
+    c->stream = (cudaStream_t)stream;
+    int ofs = 0;
+    for (int l = 0; l < tslb::NLAYER; ++l) {
+        c->pofs[l] = ofs;
+        ofs += tslb::pcount(l);
+    }
+    c->pofs[tslb::NLAYER] = ofs;
+    c->nparams = ofs;
+    const size_t N = (size_t)n;
+    c->loss_blocks = (int)((N + 255) / 256);
+    struct {
+        void **p;
+        size_t bytes;
+    } allocs[] = {
+        {(void **)&c->p, ofs * sizeof(float)},         {(void **)&c->grad, ofs * sizeof(float)},
+        {(void **)&c->m, ofs * sizeof(float)},         {(void **)&c->v, ofs * sizeof(float)},
+        {(void **)&c->dz, N * 32 * sizeof(float)},     {(void **)&c->da, N * 32 * sizeof(float)},
+        {(void **)&c->dzb, N * 32 * 2},                {(void **)&c->xbuf, 5 * N * sizeof(float)},
+        {(void **)&c->ybuf, 4 * N * sizeof(float)},
+        {(void **)&c->dsum, (size_t)(c->loss_blocks + 1) * sizeof(double)},
+    };
+    cudaError_t err = cudaSuccess;
+    for (auto &a : allocs)
+        if (err == cudaSuccess) err = cudaMalloc(a.p, a.bytes);
+    for (int l = 0; l < tslb::NLAYER && err == cudaSuccess; ++l) {
+        err = cudaMalloc(&c->wf[l], frag_count(COUTP[l] / 16, CINP[l] / 16) * sizeof(uint4));
+        if (err == cudaSuccess && l > 0) err = cudaMalloc(&c->wt[l], frag_count(CINP[l] / 16, COUTP[l] / 16) * sizeof(uint4));
+        if (err == cudaSuccess) err = cudaMalloc(&c->a[l], N * CINP[l] * 2);
+        if (err == cudaSuccess) err = cudaMalloc(&c->z[l], N * COUTP[l] * sizeof(float));
+    }
+    if (err == cudaSuccess) err = cudaMallocHost(&c->h_sum, sizeof(double) * 2);
+    int dev = 0, sms = 0;
+    if (err == cudaSuccess) err = cudaGetDevice(&dev);
+    if (err == cudaSuccess) err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (err != cudaSuccess) {
+        cudaGetLastError();
+        free_cnn(c);
+        return cnn_fail(err == cudaErrorMemoryAllocation ? LBM_ERR_OOM : LBM_ERR_CUDA, "network setup failed: %s",
+                        cudaGetErrorString(err));
+    }
+    c->conv_blocks = sms * 4;
+    float *h = new (std::nothrow) float[ofs];
+    if (!h) {
+        free_cnn(c);
+        return cnn_fail(LBM_ERR_OOM, "host allocation failed");
+    }
+    init_params(c, seed, h);
+    err = cudaMemcpyAsync(c->p, h, ofs * sizeof(float), cudaMemcpyHostToDevice, c->stream);
+    if (err == cudaSuccess) err = cudaMemsetAsync(c->grad, 0, ofs * sizeof(float), c->stream);
+    if (err == cudaSuccess) err = cudaMemsetAsync(c->m, 0, ofs * sizeof(float), c->stream);
+    if (err == cudaSuccess) err = cudaMemsetAsync(c->v, 0, ofs * sizeof(float), c->stream);
+    if (err == cudaSuccess) err = repack(c);
+    if (err == cudaSuccess) err = cudaStreamSynchronize(c->stream);
+    delete[] h;
+    if (err != cudaSuccess) {
+        free_cnn(c);
+        return cnn_fail(LBM_ERR_CUDA, "network initialisation failed: %s", cudaGetErrorString(err));
+    }
+    *out = c;
+    return LBM_OK;
+}
+
+void lbm_cnn_destroy(lbm_cnn *cnn)
+{
+    if (!cnn) return;
+    cudaStreamSynchronize(cnn->stream);
+    free_cnn(cnn);
+}
+
+lbm_status lbm_cnn_get_params(lbm_cnn *cnn, float *params)
+{
+    if (!cnn || !params) return cnn_fail(LBM_ERR_ARG, "network and params are required");
+    CNN_TRY(cudaMemcpyAsync(params, cnn->p, cnn->nparams * sizeof(float), cudaMemcpyDeviceToHost, cnn->stream));
+    CNN_TRY(cudaStreamSynchronize(cnn->stream));
+    return LBM_OK;
+}
+
+lbm_status lbm_cnn_set_params(lbm_cnn *cnn, const float *params)
+{
+    if (!cnn || !params) return cnn_fail(LBM_ERR_ARG, "network and params are required");
+    CNN_TRY(cudaMemcpyAsync(cnn->p, params, cnn->nparams * sizeof(float), cudaMemcpyHostToDevice, cnn->stream));
+    CNN_TRY(repack(cnn));
+    CNN_TRY(cudaStreamSynchronize(cnn->stream));
+    return LBM_OK;
+}
+
+lbm_status lbm_cnn_get_grads(lbm_cnn *cnn, float *grads)
+{
+    if (!cnn || !grads) return cnn_fail(LBM_ERR_ARG, "network and grads are required");
+    CNN_TRY(cudaMemcpyAsync(grads, cnn->grad, cnn->nparams * sizeof(float), cudaMemcpyDeviceToHost, cnn->stream));
+    CNN_TRY(cudaStreamSynchronize(cnn->stream));
+    return LBM_OK;
+}
+
+lbm_status lbm_cnn_forward(lbm_cnn *cnn, const float *x, float *y)
+{
+    if (!cnn || !x || !y) return cnn_fail(LBM_ERR_ARG, "network, x and y are required");
+    CNN_TRY(forward(cnn, x));
+    tslb::unpack_output_kernel<<<(cnn->N + 255) / 256, 256, 0, cnn->stream>>>(cnn->z[3], cnn->N, y);
+    CNN_TRY(cudaGetLastError());
+    return LBM_OK;
+}
+
+lbm_status lbm_cnn_grad(lbm_cnn *cnn, const float *x, const float *t, int accumulate, double *loss)
+{
+    if (!cnn || !x || !t) return cnn_fail(LBM_ERR_ARG, "network, x and t are required");
+    if (!accumulate) CNN_TRY(cudaMemsetAsync(cnn->grad, 0, cnn->nparams * sizeof(float), cnn->stream));
+    CNN_TRY(forward(cnn, x));
+    tslb::loss_kernel<<<cnn->loss_blocks, 256, 0, cnn->stream>>>(cnn->z[3], t, cnn->N, cnn->dz, cnn->dzb, cnn->dsum);
+    CNN_TRY(cudaGetLastError());
+    CNN_TRY(backward(cnn));
+    // loss: sum of the per-block partials
+    double *hp = new (std::nothrow) double[cnn->loss_blocks];
+    if (!hp) return cnn_fail(LBM_ERR_OOM, "host allocation failed");
+    cudaError_t err = cudaMemcpyAsync(hp, cnn->dsum, cnn->loss_blocks * sizeof(double), cudaMemcpyDeviceToHost,
+                                      cnn->stream);
+    if (err == cudaSuccess) err = cudaStreamSynchronize(cnn->stream);
+    if (err != cudaSuccess) {
+        delete[] hp;
+        return cnn_fail(LBM_ERR_CUDA, "loss read-back failed: %s", cudaGetErrorString(err));
+    }
+    double s = 0.0;
+    for (int b = 0; b < cnn->loss_blocks; ++b) s += hp[b];
+    delete[] hp;
+    if (loss) *loss = s / (4.0 * cnn->N);
+    return LBM_OK;
+}
+
+lbm_status lbm_cnn_adam_step(lbm_cnn *cnn, float lr, float grad_scale)
+{
+    if (!cnn) return cnn_fail(LBM_ERR_ARG, "network is NULL");
+    if (!(lr > 0.0f) || !isfinite(grad_scale)) return cnn_fail(LBM_ERR_ARG, "lr must be > 0, grad_scale finite");
+    ++cnn->adam_t;
+    const float bc1 = (float)(1.0 - pow(0.9, (double)cnn->adam_t));
+    const float bc2 = (float)(1.0 - pow(0.999, (double)cnn->adam_t));
+    tslb::adam_kernel<<<(cnn->nparams + 255) / 256, 256, 0, cnn->stream>>>(cnn->p, cnn->grad, cnn->m, cnn->v,
+                                                                            cnn->nparams, lr, grad_scale, bc1, bc2);
+    CNN_TRY(cudaGetLastError());
+    CNN_TRY(repack(cnn));
+    return LBM_OK;
+}
+
+lbm_status lbm_closure_features(lbm_ctx *ctx, const lbm_closure_norm *norm, float *x)
+{
+    if (!norm || !x) return cnn_fail(LBM_ERR_ARG, "norm and x are required");
+    tslb::CtxView v;
+    lbm_status st = tslb::ctx_view(ctx, &v);
+    if (st != LBM_OK) return st;
+    if (v.storage != LBM_FP32) return cnn_fail(LBM_ERR_ARG, "the closure needs FP32 population storage");
+    tslb::features_kernel<<<(v.G.N + 255) / 256, 256, 0, v.stream>>>(v.G, v.P, v.g, v.phi, v.u, *norm, x);
+    CNN_TRY(cudaGetLastError());
+    return LBM_OK;
+}
+
+lbm_status lbm_closure_target(lbm_ctx *ctx, const float *ref, const lbm_closure_norm *norm, float *t)
+{
+    if (!norm || !ref || !t) return cnn_fail(LBM_ERR_ARG, "ref, norm and t are required");
+    tslb::CtxView v;
+    lbm_status st = tslb::ctx_view(ctx, &v);
+    if (st != LBM_OK) return st;
+    tslb::target_kernel<<<(v.G.N + 255) / 256, 256, 0, v.stream>>>(v.G.N, v.phi, v.u, ref, *norm, t);
+    CNN_TRY(cudaGetLastError());
+    return LBM_OK;
+}
+
+lbm_status lbm_closure_apply(lbm_ctx *ctx, lbm_cnn *cnn, const lbm_closure_norm *norm)
+{
+    if (!cnn || !norm) return cnn_fail(LBM_ERR_ARG, "network and norm are required");
+    tslb::CtxView v;
+    lbm_status st = tslb::ctx_view(ctx, &v);
+    if (st != LBM_OK) return st;
+    if (v.storage != LBM_FP32) return cnn_fail(LBM_ERR_ARG, "the closure needs FP32 population storage");
+    if (v.G.wall) return cnn_fail(LBM_ERR_ARG, "the closure is for periodic boxes");
+    if (v.G.nx != cnn->nx || v.G.ny != cnn->ny || v.G.nz != cnn->nz)
+        return cnn_fail(LBM_ERR_ARG, "network grid %dx%dx%d differs from the box %dx%dx%d", cnn->nx, cnn->ny, cnn->nz,
+                        v.G.nx, v.G.ny, v.G.nz);
+    if (v.stream != cnn->stream) return cnn_fail(LBM_ERR_ARG, "network and context must share a stream");
+    const int N = v.G.N;
+    tslb::features_kernel<<<(N + 255) / 256, 256, 0, v.stream>>>(v.G, v.P, v.g, v.phi, v.u, *norm, cnn->xbuf);
+    CNN_TRY(cudaGetLastError());
+    CNN_TRY(forward(cnn, cnn->xbuf));
+    tslb::unpack_output_kernel<<<(N + 255) / 256, 256, 0, v.stream>>>(cnn->z[3], N, cnn->ybuf);
+    CNN_TRY(cudaMemsetAsync(cnn->dsum, 0, sizeof(double), v.stream));
+    tslb::sum_kernel<<<296, 256, 0, v.stream>>>(cnn->ybuf, N, cnn->dsum);
+    tslb::correct_kernel<<<(N + 255) / 256, 256, 0, v.stream>>>(v.G, cnn->ybuf, *norm, cnn->dsum, v.g, v.phi, v.u);
+    CNN_TRY(cudaGetLastError());
+    tslb::ctx_state_changed(ctx);
+    return LBM_OK;
+}
+
+lbm_status lbm_restrict2(const float *phi, const float *u, const float *p, int nx, int ny, int nz, double rho_l,
+                         double rho_g, float *out, void *stream)
+{
+    if (!phi || !u || !p || !out) return cnn_fail(LBM_ERR_ARG, "phi, u, p and out are required");
+    if (nx < 2 || ny < 2 || nz < 2 || nx % 2 || ny % 2 || nz % 2) return cnn_fail(LBM_ERR_ARG, "sizes must be even");
+    if ((long long)nx * ny * nz >= (1LL << 31)) return cnn_fail(LBM_ERR_ARG, "grid too large");
+    const int Nc = (nx / 2) * (ny / 2) * (nz / 2);
+    tslb::restrict2_kernel<<<(Nc + 255) / 256, 256, 0, (cudaStream_t)stream>>>(nx, ny, nz, phi, u, p, (float)rho_g,
+                                                                                (float)(rho_l - rho_g), out);
+    CNN_TRY(cudaGetLastError());
+    return LBM_OK;
+}
+
+}  // extern "C"

@@ -144,6 +144,24 @@ cudaMemcpyKind kind_out(int on_device) { return on_device ? cudaMemcpyDeviceToDe
 
 }  // namespace
 
+namespace tslb {
+lbm_status ctx_view(lbm_ctx *ctx, CtxView *v)
+{
+    if (!ctx) return fail(LBM_ERR_ARG, "context is NULL");
+    if (!ctx->initialized) return fail(LBM_ERR_STATE, "context is not initialised");
+    const int c = ctx->cur;
+    v->G = ctx->G;
+    v->P = ctx->P;
+    v->g = ctx->g[c];
+    v->phi = ctx->phi[c];
+    v->u = ctx->u[c];
+    v->storage = ctx->storage;
+    v->stream = ctx->stream;
+    return LBM_OK;
+}
+void ctx_state_changed(lbm_ctx *ctx) { ctx->w_valid = false; }
+}  // namespace tslb
+
 extern "C" {
 
 int lbm_abi_version(void) { return 1; }

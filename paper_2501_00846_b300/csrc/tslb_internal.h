@@ -83,4 +83,16 @@ void set_last_error(const char *msg);
 lbm_status check_params(const lbm_params *p);
 void params_to_consts(const lbm_params &p, Grid &G, Phys &P);
 
+// The one-box context's current state, for the closure (closure.cu).
+struct CtxView {
+    Grid G;
+    Phys P;
+    float *g, *phi, *u;
+    int storage;
+    cudaStream_t stream;
+};
+lbm_status ctx_view(lbm_ctx *ctx, CtxView *v);
+// Mark the context's carried Allen–Cahn flux stale after its state was changed in place.
+void ctx_state_changed(lbm_ctx *ctx);
+
 }  // namespace tslb

@@ -67,6 +67,20 @@ class LbmTuning(ctypes.Structure):
         return {name: getattr(self, name) for name, _ in self._fields_}
 
 
+class LbmClosureNorm(ctypes.Structure):
+    """Input normalisation and correction scales of the learned closure (lbm_closure_norm)."""
+    _fields_ = [("in_shift", ctypes.c_float * 5), ("in_scale", ctypes.c_float * 5),
+                ("out_scale", ctypes.c_float * 4)]
+
+    @classmethod
+    def make(cls, in_shift, in_scale, out_scale):
+        n = cls()
+        n.in_shift[:] = [float(v) for v in in_shift]
+        n.in_scale[:] = [float(v) for v in in_scale]
+        n.out_scale[:] = [float(v) for v in out_scale]
+        return n
+
+
 class LbmError(RuntimeError):
     def __init__(self, status: int, msg: str):
         super().__init__(f"{STATUS.get(status, status)}: {msg}")
@@ -119,6 +133,19 @@ def load(path: str = LIB_PATH):
         "lbm_ens_num_nodes": ([vp], ll),
         "lbm_ens_box_nodes": ([vp, i], ll),
         "lbm_ens_step_count": ([vp], ll),
+        "lbm_cnn_create": ([i, i, i, ctypes.c_ulonglong, vp, ctypes.POINTER(vp)], i),
+        "lbm_cnn_destroy": ([vp], None),
+        "lbm_cnn_num_params": ([], i),
+        "lbm_cnn_get_params": ([vp, fp], i),
+        "lbm_cnn_set_params": ([vp, fp], i),
+        "lbm_cnn_get_grads": ([vp, fp], i),
+        "lbm_cnn_forward": ([vp, fp, fp], i),
+        "lbm_cnn_grad": ([vp, fp, fp, i, ctypes.POINTER(ctypes.c_double)], i),
+        "lbm_cnn_adam_step": ([vp, ctypes.c_float, ctypes.c_float], i),
+        "lbm_closure_features": ([vp, ctypes.POINTER(LbmClosureNorm), fp], i),
+        "lbm_closure_target": ([vp, fp, ctypes.POINTER(LbmClosureNorm), fp], i),
+        "lbm_closure_apply": ([vp, vp, ctypes.POINTER(LbmClosureNorm)], i),
+        "lbm_restrict2": ([fp, fp, fp, i, i, i, ctypes.c_double, ctypes.c_double, fp, vp], i),
     }
     for name, (args, res) in sigs.items():
         fn = getattr(L, name)
@@ -382,3 +409,113 @@ def ensemble_from_workloads(workloads, stream=None) -> Ensemble:
         e.init_fields(b, np.ascontiguousarray(wl.phi0(), np.float32), np.ascontiguousarray(wl.u0(), np.float32),
                       None if ps is None else np.ascontiguousarray(ps, np.float32))
     return e
+
+
+# layer shapes of the closure network: (output channels, input channels)
+CNN_LAYERS = [(32, 5), (32, 32), (32, 32), (4, 32)]
+
+
+def _dev(t, n):
+    """Device pointer of a contiguous float32 CUDA tensor with n elements."""
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.float32 or not t.is_contiguous() \
+            or t.numel() != n:
+        raise ValueError(f"expected a contiguous float32 CUDA tensor of {n} elements")
+    return t.data_ptr()
+
+
+class Network:
+    """The learned closure's network (lbm_cnn_* of the C ABI) for nx x ny x nz periodic grids."""
+
+    def __init__(self, nx, ny, nz, seed=0, stream=None):
+        import torch
+        L = load()
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        self.shape = (nz, ny, nx)
+        self.n = nx * ny * nz
+        self._cnn = ctypes.c_void_p()
+        _check(L.lbm_cnn_create(nx, ny, nz, int(seed), stream.cuda_stream, ctypes.byref(self._cnn)))
+        self.num_params = int(L.lbm_cnn_num_params())
+
+    def close(self):
+        if getattr(self, "_cnn", None) and self._cnn.value:
+            load().lbm_cnn_destroy(self._cnn)
+            self._cnn = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def get_params(self) -> np.ndarray:
+        out = np.empty(self.num_params, np.float32)
+        _check(load().lbm_cnn_get_params(self._cnn, out.ctypes.data))
+        return out
+
+    def set_params(self, flat):
+        flat = np.ascontiguousarray(flat, np.float32)
+        if flat.size != self.num_params:
+            raise ValueError(f"expected {self.num_params} parameters")
+        _check(load().lbm_cnn_set_params(self._cnn, flat.ctypes.data))
+
+    def get_grads(self) -> np.ndarray:
+        out = np.empty(self.num_params, np.float32)
+        _check(load().lbm_cnn_get_grads(self._cnn, out.ctypes.data))
+        return out
+
+    @staticmethod
+    def split(flat):
+        """[(W [cout, cin, 27], b [cout]) per layer] views of a flat parameter vector."""
+        out, o = [], 0
+        for cout, cin in CNN_LAYERS:
+            w = flat[o:o + cout * cin * 27].reshape(cout, cin, 27)
+            o += cout * cin * 27
+            out.append((w, flat[o:o + cout]))
+            o += cout
+        return out
+
+    def forward(self, x, y):
+        _check(load().lbm_cnn_forward(self._cnn, _dev(x, 5 * self.n), _dev(y, 4 * self.n)))
+
+    def grad(self, x, t, accumulate=False) -> float:
+        loss = ctypes.c_double()
+        _check(load().lbm_cnn_grad(self._cnn, _dev(x, 5 * self.n), _dev(t, 4 * self.n), int(bool(accumulate)),
+                                   ctypes.byref(loss)))
+        return loss.value
+
+    def adam_step(self, lr, grad_scale=1.0):
+        _check(load().lbm_cnn_adam_step(self._cnn, float(lr), float(grad_scale)))
+
+
+def closure_features(s: "Solver", norm: LbmClosureNorm, x):
+    _check(load().lbm_closure_features(s._ctx, ctypes.byref(norm), _dev(x, 5 * s.n)))
+
+
+def closure_target(s: "Solver", ref, norm: LbmClosureNorm, t):
+    import torch
+    if not isinstance(ref, torch.Tensor) or not ref.is_cuda or ref.dtype != torch.float32 or not ref.is_contiguous() \
+            or ref.numel() < 4 * s.n:
+        raise ValueError("ref must be a contiguous float32 CUDA tensor of at least 4 N elements")
+    _check(load().lbm_closure_target(s._ctx, ref.data_ptr(), ctypes.byref(norm), _dev(t, 4 * s.n)))
+
+
+def closure_apply(s: "Solver", net: Network, norm: LbmClosureNorm):
+    _check(load().lbm_closure_apply(s._ctx, net._cnn, ctypes.byref(norm)))
+
+
+def restrict2(phi, u, p, nx, ny, nz, rho_l, rho_g, out, stream=None):
+    """Coarse (phi, u, p, p*) [6][N/8] of a fine state (device tensors, channel-first)."""
+    import torch
+    n = nx * ny * nz
+    st = (stream or torch.cuda.current_stream()).cuda_stream
+    _check(load().lbm_restrict2(_dev(phi, n), _dev(u, 3 * n), _dev(p, n), nx, ny, nz, float(rho_l), float(rho_g),
+                                _dev(out, 6 * (n // 8)), st))

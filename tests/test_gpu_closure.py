@@ -1,0 +1,192 @@
+"""Learned closure kernels against the FP64 reference network (oracle/closure_ref.py) and against
+their plain definitions.
+
+The GPU network multiplies BF16 weights by BF16 activations with FP32 accumulation, so its outputs
+and gradients differ from the FP64 reference by the BF16 rounding of both operands (unit roundoff
+2^-8 each, about 4e-3 per product, averaging down over the 27 x 32-term sums).  The bars: relative
+L2 error of the output 2e-2; of the gradient of every layer 3e-2, with cosine similarity >= 0.999
+to the reference gradient (a wrong sign, transpose or offset would give cosines far below 1).
+"""
+import numpy as np
+import pytest
+
+from oracle import closure_ref as R
+from paper_2501_00846_b300 import inputs, solver
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    torch.cuda.set_device(0)
+    solver.load()
+
+
+def _random_case(nx=32, ny=6, nz=5, seed=0):
+    rng = np.random.default_rng(seed)
+    flat = np.empty(solver.load().lbm_cnn_num_params(), np.float32)
+    o = 0
+    for cout, cin in solver.CNN_LAYERS:
+        n = cout * cin * 27
+        flat[o:o + n] = rng.uniform(-1, 1, n) * np.sqrt(6.0 / (27 * (cin + cout)))
+        o += n
+        flat[o:o + cout] = rng.uniform(-0.2, 0.2, cout)
+        o += cout
+    x = rng.standard_normal((5, nz, ny, nx)).astype(np.float32)
+    t = (0.3 * rng.standard_normal((4, nz, ny, nx))).astype(np.float32)
+    return flat, x, t
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def test_forward_matches_the_fp64_reference():
+    import torch
+    nx, ny, nz = 32, 6, 5
+    flat, x, _ = _random_case(nx, ny, nz)
+    with solver.Network(nx, ny, nz) as net:
+        net.set_params(flat)
+        xd = torch.from_numpy(x).cuda().reshape(-1)
+        yd = torch.empty(4 * net.n, device="cuda")
+        net.forward(xd, yd)
+        torch.cuda.synchronize()
+        y = yd.cpu().numpy().reshape(4, nz, ny, nx)
+    ref, _ = R.forward(solver.Network.split(flat.astype(np.float64)), x.astype(np.float64))
+    err = _rel(y, ref)
+    print(f"forward rel L2 error {err:.3e}")
+    assert err < 2e-2
+
+
+def test_gradients_match_the_fp64_reference():
+    import torch
+    nx, ny, nz = 32, 6, 5
+    flat, x, t = _random_case(nx, ny, nz, seed=1)
+    with solver.Network(nx, ny, nz) as net:
+        net.set_params(flat)
+        xd = torch.from_numpy(x).cuda().reshape(-1)
+        td = torch.from_numpy(t).cuda().reshape(-1)
+        loss = net.grad(xd, td)
+        g = net.get_grads()
+    ref_loss, ref = R.loss_and_grads(solver.Network.split(flat.astype(np.float64)), x.astype(np.float64),
+                                     t.astype(np.float64))
+    assert abs(loss / ref_loss - 1) < 2e-2
+    for l, ((gw, gb), (rw, rb)) in enumerate(zip(solver.Network.split(g), ref)):
+        a = np.concatenate([gw.ravel(), gb.ravel()])
+        b = np.concatenate([rw.ravel(), rb.ravel()])
+        err = _rel(a, b)
+        cos = float(a @ b / (np.linalg.norm(a) * np.linalg.norm(b)))
+        print(f"layer {l + 1}: gradient rel L2 error {err:.3e}, cosine {cos:.6f}")
+        assert err < 3e-2 and cos > 0.999
+
+
+def test_accumulated_gradients_add_up_and_adam_reduces_the_loss():
+    import torch
+    nx, ny, nz = 32, 4, 4
+    flat, x, t = _random_case(nx, ny, nz, seed=2)
+    with solver.Network(nx, ny, nz) as net:
+        net.set_params(flat)
+        xd = torch.from_numpy(x).cuda().reshape(-1)
+        td = torch.from_numpy(t).cuda().reshape(-1)
+        net.grad(xd, td)
+        g1 = net.get_grads()
+        net.grad(xd, td, accumulate=True)
+        g2 = net.get_grads()
+        assert np.allclose(g2, 2 * g1, rtol=1e-5, atol=1e-9)
+        losses = []
+        for _ in range(30):
+            losses.append(net.grad(xd, td))
+            net.adam_step(1e-3)
+    print("loss", losses[0], "->", losses[-1])
+    assert losses[-1] < 0.5 * losses[0]
+
+
+def test_restriction_matches_its_definition():
+    import torch
+    rng = np.random.default_rng(3)
+    nx, ny, nz = 8, 6, 4
+    phi = rng.uniform(0, 1, (nz, ny, nx)).astype(np.float32)
+    u = rng.standard_normal((3, nz, ny, nx)).astype(np.float32) * 0.01
+    p = rng.standard_normal((nz, ny, nx)).astype(np.float32) * 1e-3
+    rho_l, rho_g = 1.0, 0.01
+    out = torch.empty(6 * nx * ny * nz // 8, device="cuda")
+    solver.restrict2(torch.from_numpy(phi).cuda().reshape(-1), torch.from_numpy(u).cuda().reshape(-1),
+                     torch.from_numpy(p).cuda().reshape(-1), nx, ny, nz, rho_l, rho_g, out)
+    torch.cuda.synchronize()
+    got = out.cpu().numpy().reshape(6, nz // 2, ny // 2, nx // 2)
+    blk = lambda a: a.reshape(nz // 2, 2, ny // 2, 2, nx // 2, 2).astype(np.float64)
+    rho = rho_g + phi.astype(np.float64) * (rho_l - rho_g)
+    phic = blk(phi).mean(axis=(1, 3, 5))
+    assert np.allclose(got[0], phic, rtol=1e-6, atol=1e-7)
+    for a in range(3):
+        uc = (blk(rho * u[a]).sum(axis=(1, 3, 5))) / blk(rho).sum(axis=(1, 3, 5))
+        assert np.allclose(got[1 + a], uc, rtol=1e-5, atol=1e-9)
+    pc = blk(p).mean(axis=(1, 3, 5))
+    assert np.allclose(got[4], pc, rtol=1e-5, atol=1e-10)
+    assert np.allclose(got[5], 3 * pc / (rho_g + phic * (rho_l - rho_g)), rtol=1e-5, atol=1e-9)
+
+
+def _closure_box():
+    wl = inputs.static_droplet(L=32, radius=8.0, noise=0.01, seed=5)
+    return wl
+
+
+def test_zero_network_leaves_the_state_unchanged_and_a_constant_shifts_momentum():
+    import torch
+    wl = _closure_box()
+    norm = solver.LbmClosureNorm.make([0.5, 0, 0, 0, 0], [0.5, 0.01, 0.01, 0.01, 1e-3], [1e-3, 1e-3, 2e-3, 3e-3])
+    with solver.from_workload(wl) as s, solver.Network(wl.nx, wl.ny, wl.nz, stream=s.stream) as net:
+        s.step(3)
+        g0, phi0, u0 = s.get_state()
+        net.set_params(np.zeros(net.num_params, np.float32))
+        solver.closure_apply(s, net, norm)
+        g1, phi1, u1 = s.get_state()
+        assert np.array_equal(g0, g1) and np.array_equal(phi0, phi1) and np.array_equal(u0, u1)
+        # W4 = 0, b4 = (1, 1, -1, 2): y is constant, so dphi = 0 after the mean is removed and
+        # ubar shifts by out_scale * (1, -1, 2) everywhere
+        flat = np.zeros(net.num_params, np.float32)
+        flat[-4:] = [1.0, 1.0, -1.0, 2.0]
+        net.set_params(flat)
+        solver.closure_apply(s, net, norm)
+        g2, phi2, u2 = s.get_state()
+        s.step(2)                                   # the corrected state steps on
+        assert s.observables()["n_nonfinite"] == 0
+    assert np.abs(phi2 - phi1).max() < 1e-6
+    du = np.array([1e-3 * 1.0, 2e-3 * -1.0, 3e-3 * 2.0])
+    for a in range(3):
+        assert np.allclose(u2[a] - u1[a], du[a], atol=1e-7)
+    # populations: p* unchanged, first moment shifted by du (sum_i f^eq_i c_i = u)
+    c = np.array([[k % 3 - 1, (k // 3) % 3 - 1, k // 9 - 1] for k in range(27)], np.float64)
+    ps1, ps2 = g1.astype(np.float64).sum(0), g2.astype(np.float64).sum(0)
+    assert np.abs(ps2 - ps1).max() < 1e-6
+    for a in range(3):
+        j1 = np.tensordot(c[:, a], g1.astype(np.float64), axes=1)
+        j2 = np.tensordot(c[:, a], g2.astype(np.float64), axes=1)
+        assert np.allclose(j2 - j1, du[a], atol=2e-7)
+
+
+def test_features_and_targets_follow_their_definitions():
+    import torch
+    wl = _closure_box()
+    norm = solver.LbmClosureNorm.make([0.5, 0, 0, 0, 0.0], [0.5, 0.01, 0.02, 0.03, 1e-3], [1e-3, 2e-3, 3e-3, 4e-3])
+    with solver.from_workload(wl) as s:
+        s.step(4)
+        phi, u, p = s.read_fields()
+        x = torch.empty(5 * s.n, device="cuda")
+        solver.closure_features(s, norm, x)
+        ref = torch.from_numpy(np.concatenate([phi.reshape(1, -1) + 0.01, u.reshape(3, -1) - 0.002]).astype(
+            np.float32)).cuda().reshape(-1)
+        t = torch.empty(4 * s.n, device="cuda")
+        solver.closure_target(s, ref, norm, t)
+        torch.cuda.synchronize()
+        x, t = x.cpu().numpy().reshape(5, -1), t.cpu().numpy().reshape(4, -1)
+    fields = [phi.reshape(-1), u[0].reshape(-1), u[1].reshape(-1), u[2].reshape(-1), p.reshape(-1)]
+    for c in range(5):
+        want = (fields[c] - norm.in_shift[c]) / norm.in_scale[c]
+        assert np.allclose(x[c], want, rtol=1e-5, atol=1e-5 * np.abs(want).max())
+    assert np.allclose(t[0], 0.01 / 1e-3, rtol=1e-3)
+    for a in range(3):
+        assert np.allclose(t[1 + a], -0.002 / norm.out_scale[1 + a], rtol=1e-3)
