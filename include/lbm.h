@@ -270,6 +270,13 @@ lbm_status lbm_ens_get_tuning(const lbm_ens *ens, lbm_tuning *out);
 lbm_status lbm_ens_set_tuning(lbm_ens *ens, const lbm_tuning *t);
 lbm_status lbm_ens_autotune(lbm_ens *ens, int reps, lbm_tuning *out);
 
+/* Set the state of a coarse context (FP32 storage, half the box's size in every direction, same
+ * parameters rescaled by the caller) to the 2x restriction of box b's state: the populations, phi
+ * and ubar of each coarse cell are the means over its 8 fine nodes.  Enqueued on the coarse
+ * context's stream after the ensemble's pending work.  The library's own addition (data for the
+ * learned closure), not in the paper. */
+lbm_status lbm_ens_restrict_state(lbm_ens *ens, int box, lbm_ctx *coarse);
+
 /* Number of boxes, total nodes, nodes of box b, steps taken; 0 for NULL or a bad index. */
 int lbm_ens_num_boxes(const lbm_ens *ens);
 long long lbm_ens_num_nodes(const lbm_ens *ens);
@@ -323,8 +330,10 @@ lbm_status lbm_closure_features(lbm_ctx *ctx, const lbm_closure_norm *norm, floa
  * ref: device [>= 4][N] channel-first (phi, u_x, u_y, u_z), t: device [4][N]. */
 lbm_status lbm_closure_target(lbm_ctx *ctx, const float *ref, const lbm_closure_norm *norm, float *t);
 /* Correct a context's state in place with the network (periodic boxes, FP32 storage, grid equal to
- * the network's): phi += dphi (mean removed), ubar += du, populations shifted by
- * f^eq(p*, ubar + du) - f^eq(p*, ubar).  Asynchronous on the context's stream. */
+ * the network's): phi += dphi - w c with w = max(4 phi (1 - phi), 0) and c chosen so that sum phi
+ * is unchanged (the compensation sits in the interfaces, the bulk phases stay untouched), ubar +=
+ * du, populations shifted by f^eq(p*, ubar + du) - f^eq(p*, ubar).  Asynchronous on the context's
+ * stream. */
 lbm_status lbm_closure_apply(lbm_ctx *ctx, lbm_cnn *cnn, const lbm_closure_norm *norm);
 
 /* 2x restriction of a fine state to the coarse grid (device arrays, channel-first): phi and p

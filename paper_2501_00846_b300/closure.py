@@ -1,0 +1,263 @@
+"""Learned closure: training data from the solver's own fine-grid runs, training with the library's
+network kernels, and evaluation against the fine solver.
+
+The closure corrects (phi, ubar) of a 2x-coarser grid after every coarse step.  Data: seeded
+head-on droplet collisions (inputs.collision_set) run on the fine grid (L^3) in batches through the
+ensemble; at each snapshot the fine state is restricted 2x into a coarse context (populations,
+phi and ubar averaged over the 8 fine nodes of a coarse cell), the coarse context takes one step
+(= 2 fine steps in acoustic scaling) while the fine batch takes two, and the pair
+
+    x = features(coarse state after the step),    t = (restricted fine (phi, u) - coarse (phi, ubar)) / out_scale
+
+is stored on the device.  Training: Adam on the mean-squared error, minibatches accumulated in
+the network's gradient buffer.  Evaluation: a held-out collision run three ways from the same
+restricted initial state -- the fine solver (restricted 2x as the judge), the plain coarse solver,
+and the coarse solver corrected by the network after every step -- with RMS errors of phi and u
+against the judge and device times of each.
+
+Everything numerical runs in the library's CUDA kernels; torch provides device memory and the
+stream.
+
+    python -m paper_2501_00846_b300.closure --traj 200 --epochs 4 --out closure_run.json
+"""
+import argparse
+import json
+import math
+import sys
+import time
+
+import numpy as np
+
+from . import inputs, solver
+
+
+def _f32(a):
+    return np.ascontiguousarray(a, np.float32)
+
+
+def _coarse_context(col, stream):
+    """A coarse context with the collision's coarse parameters (state set later by restriction)."""
+    p = col.coarse_params()
+    s = solver.Solver(stream=stream, **p)
+    n = p["nx"] * p["ny"] * p["nz"]
+    s.init_fields(np.zeros(n, np.float32), np.zeros(3 * n, np.float32))
+    return s
+
+
+IDENTITY = solver.LbmClosureNorm.make([0.0] * 5, [1.0] * 5, [1.0] * 4)
+
+
+def generate(collisions, snapshots=20, stride=48, batch=25, norm=IDENTITY, stream=None, log=None):
+    """Training pairs (X [S, 5, Nc], T [S, 4, Nc], device tensors) from len(collisions) fine runs,
+    `snapshots` pairs each, one every `stride` fine steps."""
+    import torch
+    stream = stream or torch.cuda.current_stream()
+    L = collisions[0].L
+    Nc = (L // 2) ** 3
+    S = len(collisions) * snapshots
+    X = torch.empty((S, 5, Nc), device="cuda")
+    T = torch.empty((S, 4, Nc), device="cuda")
+    ref = torch.empty(4 * Nc, device="cuda")
+    idx = 0
+    with torch.cuda.stream(stream):
+        for b0 in range(0, len(collisions), batch):
+            cols = collisions[b0:b0 + batch]
+            t0 = time.perf_counter()
+            ens = solver.Ensemble([c.params() for c in cols], stream=stream)
+            for k, c in enumerate(cols):
+                phi, u, ps = c.fields()
+                ens.init_fields(k, _f32(phi), _f32(u), _f32(ps))
+            coarse = [_coarse_context(c, stream) for c in cols]
+            judge = _coarse_context(cols[0], stream)
+            for _ in range(snapshots):
+                ens.step(stride - 2)
+                for k in range(len(cols)):
+                    ens.restrict_state(k, coarse[k])
+                ens.step(2)
+                for k in range(len(cols)):
+                    coarse[k].step(1)
+                    ens.restrict_state(k, judge)
+                    judge.read_fields(phi=ref[:Nc], u=ref[Nc:])
+                    solver.closure_features(coarse[k], norm, X[idx].reshape(-1))
+                    solver.closure_target(coarse[k], ref, norm, T[idx].reshape(-1))
+                    idx += 1
+            torch.cuda.synchronize()
+            for c in coarse:
+                c.close()
+            judge.close()
+            ens.close()
+            if log:
+                log(f"data: collisions {b0}..{b0 + len(cols) - 1}, {idx} pairs, {time.perf_counter() - t0:.1f} s")
+    return X[:idx], T[:idx]
+
+
+def estimate_norm(collisions, snapshots=6, stride=48, stream=None):
+    """Input shifts and scales (mean and standard deviation of phi, u, p) and output scales
+    (standard deviation of the raw corrections) from a small pilot set, on the host."""
+    X, T = generate(collisions, snapshots=snapshots, stride=stride, batch=len(collisions), stream=stream)
+    x = X.permute(1, 0, 2).reshape(5, -1).double().cpu().numpy()
+    t = T.permute(1, 0, 2).reshape(4, -1).double().cpu().numpy()
+    shift = x.mean(axis=1)
+    scale = np.maximum(x.std(axis=1), 1e-12)
+    shift[0], scale[0] = 0.5, 0.5                      # phi in [0, 1]
+    shift[1:4] = 0.0                                   # velocities: symmetric
+    out = np.maximum(t.std(axis=1), 1e-12)
+    return solver.LbmClosureNorm.make(shift, scale, out)
+
+
+def train(net, X, T, epochs=4, lr=1e-3, batch=4, seed=0, log=None):
+    """Adam over the pairs in random order, `batch` samples per step; cosine learning-rate decay.
+    Returns the mean loss of every epoch."""
+    S = X.shape[0]
+    rng = np.random.default_rng(seed)
+    steps = epochs * math.ceil(S / batch)
+    k = 0
+    history = []
+    for ep in range(epochs):
+        order = rng.permutation(S)
+        tot = 0.0
+        t0 = time.perf_counter()
+        for i in range(0, S, batch):
+            ids = order[i:i + batch]
+            for j, s in enumerate(ids):
+                tot += net.grad(X[int(s)].reshape(-1), T[int(s)].reshape(-1), accumulate=j > 0)
+            rate = lr * 0.5 * (1.0 + math.cos(math.pi * k / steps))
+            net.adam_step(rate, 1.0 / len(ids))
+            k += 1
+        history.append(tot / S)
+        if log:
+            log(f"epoch {ep}: loss {history[-1]:.4e} ({time.perf_counter() - t0:.1f} s)")
+    return history
+
+
+def evaluate(net, norm, col, coarse_steps=240, every=24, stream=None):
+    """RMS errors of phi and u of the plain and the corrected coarse runs against the restricted
+    fine run of collision `col`, and device times per coarse step of the three runs."""
+    import torch
+    stream = stream or torch.cuda.current_stream()
+    n = (col.L // 2) ** 3
+    out = {"checkpoints": [], "steps": coarse_steps}
+    with torch.cuda.stream(stream):
+        fine = solver.Ensemble([col.params()], stream=stream)
+        phi, u, ps = col.fields()
+        fine.init_fields(0, _f32(phi), _f32(u), _f32(ps))
+        plain, corr, judge = (_coarse_context(col, stream) for _ in range(3))
+        fine.restrict_state(0, plain)
+        fine.restrict_state(0, corr)
+        e_plain, e_corr = [], []
+        for k in range(1, coarse_steps + 1):
+            fine.step(2)
+            plain.step(1)
+            corr.step(1)
+            solver.closure_apply(corr, net, norm)
+            if k % every == 0:
+                fine.restrict_state(0, judge)
+                jp, ju, _ = judge.read_fields()
+                row = {"step": k}
+                for name, s, acc in (("plain", plain, e_plain), ("closure", corr, e_corr)):
+                    sp, su, _ = s.read_fields()
+                    ephi = float(np.sqrt(np.mean((sp.astype(np.float64) - jp) ** 2)))
+                    eu = float(np.sqrt(np.mean((su.astype(np.float64) - ju) ** 2)))
+                    row[name] = {"phi_rms": ephi, "u_rms": eu}
+                    acc.append((ephi, eu))
+                out["checkpoints"].append(row)
+        for name, acc in (("plain", e_plain), ("closure", e_corr)):
+            a = np.array(acc)
+            out[name] = {"phi_rms_mean": float(a[:, 0].mean()), "u_rms_mean": float(a[:, 1].mean())}
+        out["ratio_phi"] = out["closure"]["phi_rms_mean"] / out["plain"]["phi_rms_mean"]
+        out["ratio_u"] = out["closure"]["u_rms_mean"] / out["plain"]["u_rms_mean"]
+        # device time per coarse step of each run (same number of steps, after the error run)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        nrep = 50
+
+        def timed(fn):
+            torch.cuda.synchronize()
+            ev[0].record(stream)
+            for _ in range(nrep):
+                fn()
+            ev[1].record(stream)
+            torch.cuda.synchronize()
+            return ev[0].elapsed_time(ev[1]) / nrep
+
+        ref_fine = solver.Solver(stream=stream, **col.params())    # the one-box fine path, for timing
+        ref_fine.init_fields(_f32(phi), _f32(u), _f32(ps))
+        out["ms_per_coarse_step"] = {
+            "fine_2_steps": timed(lambda: ref_fine.step(2)),
+            "coarse": timed(lambda: plain.step(1)),
+            "coarse_with_closure": timed(lambda: (corr.step(1), solver.closure_apply(corr, net, norm))),
+        }
+        for s in (plain, corr, judge, ref_fine):
+            s.close()
+        fine.close()
+    out["nodes"] = {"fine": col.L ** 3, "coarse": n}
+    return out
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description="train and evaluate the learned closure")
+    ap.add_argument("--traj", type=int, default=200)
+    ap.add_argument("--snapshots", type=int, default=20)
+    ap.add_argument("--stride", type=int, default=48)
+    ap.add_argument("--batch-traj", type=int, default=25)
+    ap.add_argument("--epochs", type=int, default=4)
+    ap.add_argument("--lr", type=float, default=1e-3)
+    ap.add_argument("--eval", type=int, default=2, help="held-out collisions to evaluate")
+    ap.add_argument("--eval-steps", type=int, default=240)
+    ap.add_argument("--L", type=int, default=128)
+    ap.add_argument("--seed", type=int, default=7)
+    ap.add_argument("--out", default=None, help="JSON file for the results")
+    ap.add_argument("--weights", default=None, help="npz file for the trained parameters and normalisation")
+    ap.add_argument("--load", default=None, help="evaluate parameters from an npz written by --weights (no training)")
+    ap.add_argument("--phi-only", action="store_true", help="apply only the phi correction when evaluating")
+    ap.add_argument("--u-relax", type=float, default=0.0,
+                    help="factor on the applied velocity correction (0: the phi correction alone)")
+    a = ap.parse_args(argv)
+    import torch
+    torch.cuda.set_device(0)
+    log = lambda m: print(m, file=sys.stderr, flush=True)
+    cols = inputs.collision_set(a.traj + a.eval, seed=a.seed, L=a.L, R=a.L * 20.0 / 128.0)
+    train_cols, eval_cols = cols[:a.traj], cols[a.traj:]
+    if a.load:
+        z = np.load(a.load)
+        out_scale = np.array(z["out_scale"], np.float64)
+        out_scale[1:] *= 0.0 if a.phi_only else a.u_relax
+        norm = solver.LbmClosureNorm.make(z["in_shift"], z["in_scale"], out_scale)
+        net = solver.Network(a.L // 2, a.L // 2, a.L // 2, seed=a.seed)
+        net.set_params(z["params"])
+        evals = [evaluate(net, norm, c, coarse_steps=a.eval_steps) for c in eval_cols]
+        print(json.dumps({"eval": evals}))
+        if a.out:
+            with open(a.out, "w") as fh:
+                json.dump({"eval": evals}, fh, indent=1)
+        net.close()
+        return 0
+    t0 = time.perf_counter()
+    norm = estimate_norm(train_cols[:4], stride=a.stride)
+    log(f"norm: in_shift {list(norm.in_shift)} in_scale {list(norm.in_scale)} out_scale {list(norm.out_scale)}")
+    X, T = generate(train_cols, snapshots=a.snapshots, stride=a.stride, batch=a.batch_traj, norm=norm, log=log)
+    t_data = time.perf_counter() - t0
+    net = solver.Network(a.L // 2, a.L // 2, a.L // 2, seed=a.seed)
+    t1 = time.perf_counter()
+    hist = train(net, X, T, epochs=a.epochs, lr=a.lr, log=log)
+    t_train = time.perf_counter() - t1
+    del X, T
+    applied = solver.LbmClosureNorm.make(norm.in_shift, norm.in_scale,
+                                         [norm.out_scale[0]] + [a.u_relax * v for v in list(norm.out_scale)[1:]])
+    evals = [evaluate(net, applied, c, coarse_steps=a.eval_steps) for c in eval_cols]
+    res = {"trajectories": a.traj, "pairs": a.traj * a.snapshots, "epochs": a.epochs, "loss": hist,
+           "seconds": {"data": t_data, "train": t_train}, "eval": evals,
+           "norm": {"in_shift": list(norm.in_shift), "in_scale": list(norm.in_scale),
+                    "out_scale": list(norm.out_scale)}}
+    print(json.dumps(res))
+    if a.out:
+        with open(a.out, "w") as fh:
+            json.dump(res, fh, indent=1)
+    if a.weights:
+        np.savez(a.weights, params=net.get_params(), in_shift=np.array(norm.in_shift),
+                 in_scale=np.array(norm.in_scale), out_scale=np.array(norm.out_scale))
+    net.close()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -351,33 +351,62 @@ __global__ void target_kernel(int N, const float *__restrict__ phi, const float 
         t[(size_t)(a + 1) * N + k] = (ref[(size_t)(a + 1) * N + k] - u[(size_t)a * N + k]) / nrm.out_scale[a + 1];
 }
 
-// sum of y[0..N) in FP64 (one value per block, then atomically summed)
-__global__ void __launch_bounds__(256) sum_kernel(const float *__restrict__ y, int N, double *__restrict__ out)
+// The phi correction before the conservation step: s_0 y_0 limited so that phi stays in [0, 1]
+// (a correction may not push a node out of the range the phase field has; phi already outside
+// it is not pushed further)
+__device__ __forceinline__ float bounded_dphi(float raw, float ph)
 {
-    __shared__ double red[256];
-    double s = 0.0;
-    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < N; k += gridDim.x * blockDim.x) s += y[k];
-    red[threadIdx.x] = s;
-    __syncthreads();
-    for (int w = 128; w > 0; w >>= 1) {
-        if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) atomicAdd(out, red[0]);
+    return fminf(fmaxf(raw, -fmaxf(ph, 0.0f)), fmaxf(1.0f - ph, 0.0f));
 }
 
-// Apply the network's correction y [4][N] to a one-box FP32 state: dphi = s_0 y_0 minus its mean
-// (sum phi unchanged), du = s_a y_a; phi += dphi, ubar += du, and g_i += f^eq_i(p*, ubar + du) -
-// f^eq_i(p*, ubar) (Eq. eqts; p* = sum g unchanged), so the populations carry the new velocity.
+// Sums for the conservative phi correction: out[0] += sum of the bounded corrections, out[1] +=
+// sum of the interface weight w = max(4 phi (1 - phi), 0) (FP64)
+__global__ void __launch_bounds__(256) corr_sums_kernel(const float *__restrict__ y, const float *__restrict__ phi,
+                                                        float s_phi, int N, double *__restrict__ out)
+{
+    __shared__ double r0[256], r1[256];
+    double s0 = 0.0, s1 = 0.0;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < N; k += gridDim.x * blockDim.x) {
+        const float p = phi[k];
+        s0 += bounded_dphi(s_phi * y[k], p);
+        s1 += fmaxf(4.0f * p * (1.0f - p), 0.0f);
+    }
+    r0[threadIdx.x] = s0;
+    r1[threadIdx.x] = s1;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (threadIdx.x < w) {
+            r0[threadIdx.x] += r0[threadIdx.x + w];
+            r1[threadIdx.x] += r1[threadIdx.x + w];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        atomicAdd(out, r0[0]);
+        atomicAdd(out + 1, r1[0]);
+    }
+}
+
+// Apply the network's correction y [4][N] to a one-box FP32 state.  phi: dphi = d - w c with d
+// the bounded correction s_0 y_0 (phi kept in [0, 1]), w = max(4 phi (1 - phi), 0) and
+// c = sum(d) / sum(w), so the sum of phi is unchanged and the compensation sits in the interfaces
+// (a uniform shift, or an unbounded correction, pushes the bulk phases out of [0, 1], and with a
+// density ratio of 100 rho(phi) turns negative at phi = -0.0101); with no interface (sum w = 0)
+// the plain mean is removed.  ubar: du = s_a y_a.  Populations:
+// g_i += f^eq_i(p*, ubar + du) - f^eq_i(p*, ubar) (Eq. eqts; p* = sum g unchanged), so they carry
+// the new velocity.
 __global__ void correct_kernel(Grid G, const float *__restrict__ y, lbm_closure_norm nrm,
-                               const double *__restrict__ ysum, float *__restrict__ g, float *__restrict__ phi,
+                               const double *__restrict__ sums, float *__restrict__ g, float *__restrict__ phi,
                                float *__restrict__ u)
 {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= G.N) return;
     const size_t N = (size_t)G.N;
-    const float mean = (float)(*ysum / (double)G.N);
-    const float dphi = nrm.out_scale[0] * (y[k] - mean);
+    const double total = sums[0];
+    const float ph = phi[k];
+    const float w = fmaxf(4.0f * ph * (1.0f - ph), 0.0f);
+    const float comp = sums[1] > 0.0 ? (float)(total / sums[1]) * w : (float)(total / (double)G.N);
+    const float dphi = bounded_dphi(nrm.out_scale[0] * y[k], ph) - comp;
     const float du[3] = {nrm.out_scale[1] * y[N + k], nrm.out_scale[2] * y[2 * N + k], nrm.out_scale[3] * y[3 * N + k]};
     float ps = 0.0f;
     float gi[27];
@@ -394,7 +423,7 @@ __global__ void correct_kernel(Grid G, const float *__restrict__ y, lbm_closure_
     // a zero correction leaves g bit for bit
 #pragma unroll
     for (int i = 0; i < 27; ++i) g[i * N + k] = __fadd_rn(gi[i], __fsub_rn(e1[i], e0[i]));
-    phi[k] += dphi;
+    phi[k] = ph + dphi;
     u[k] = ux + du[0];
     u[N + k] = uy + du[1];
     u[2 * N + k] = uz + du[2];
@@ -810,8 +839,8 @@ lbm_status lbm_closure_apply(lbm_ctx *ctx, lbm_cnn *cnn, const lbm_closure_norm 
     CNN_TRY(cudaGetLastError());
     CNN_TRY(forward(cnn, cnn->xbuf));
     tslb::unpack_output_kernel<<<(N + 255) / 256, 256, 0, v.stream>>>(cnn->z[3], N, cnn->ybuf);
-    CNN_TRY(cudaMemsetAsync(cnn->dsum, 0, sizeof(double), v.stream));
-    tslb::sum_kernel<<<296, 256, 0, v.stream>>>(cnn->ybuf, N, cnn->dsum);
+    CNN_TRY(cudaMemsetAsync(cnn->dsum, 0, 2 * sizeof(double), v.stream));
+    tslb::corr_sums_kernel<<<296, 256, 0, v.stream>>>(cnn->ybuf, v.phi, norm->out_scale[0], N, cnn->dsum);
     tslb::correct_kernel<<<(N + 255) / 256, 256, 0, v.stream>>>(v.G, cnn->ybuf, *norm, cnn->dsum, v.g, v.phi, v.u);
     CNN_TRY(cudaGetLastError());
     tslb::ctx_state_changed(ctx);

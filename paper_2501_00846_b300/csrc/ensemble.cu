@@ -106,6 +106,39 @@ __global__ void __launch_bounds__(AC_WPB * 32) ens_ac_kernel(const EnsBox *__res
     }
 }
 
+// 2x restriction of one box's state into a coarse state of half the size in every direction: the
+// populations, phi and ubar of the coarse cell are the means over its 8 fine nodes (the means of
+// the populations carry the fine non-equilibrium part over to the coarse grid).
+__global__ void restrict_state_kernel(Grid F, const float *__restrict__ g, const float *__restrict__ phi,
+                                      const float *__restrict__ u, Grid C, float *__restrict__ gc,
+                                      float *__restrict__ phic, float *__restrict__ uc)
+{
+    const int kc = blockIdx.x * blockDim.x + threadIdx.x;
+    if (kc >= C.N) return;
+    const int z = kc / C.nxy, rem = kc - z * C.nxy, y = rem / C.nx, x = rem - y * C.nx;
+    size_t f[8];
+#pragma unroll
+    for (int c = 0; c < 8; ++c)
+        f[c] = ((size_t)(2 * z + (c >> 2)) * F.ny + (2 * y + ((c >> 1) & 1))) * F.nx + 2 * x + (c & 1);
+    const size_t NF = (size_t)F.N, NC = (size_t)C.N;
+    for (int i = 0; i < 27; ++i) {
+        float s = 0.0f;
+#pragma unroll
+        for (int c = 0; c < 8; ++c) s += g[i * NF + f[c]];
+        gc[i * NC + kc] = 0.125f * s;
+    }
+    float sp = 0.0f;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) sp += phi[f[c]];
+    phic[kc] = 0.125f * sp;
+    for (int a = 0; a < 3; ++a) {
+        float su = 0.0f;
+#pragma unroll
+        for (int c = 0; c < 8; ++c) su += u[a * NF + f[c]];
+        uc[a * NC + kc] = 0.125f * su;
+    }
+}
+
 lbm_status ens_fail(lbm_status s, const char *fmt, ...)
 {
     char msg[384];
@@ -590,6 +623,33 @@ lbm_status lbm_ens_autotune(lbm_ens *ens, int reps, lbm_tuning *out)
         if (out) *out = ens->tun;
     }
     return st;
+}
+
+lbm_status lbm_ens_restrict_state(lbm_ens *ens, int box, lbm_ctx *coarse)
+{
+    if (!ens || !coarse) return ens_fail(LBM_ERR_ARG, "ensemble and coarse context are required");
+    if (box < 0 || box >= ens->nb) return ens_fail(LBM_ERR_ARG, "box %d out of range [0, %d)", box, ens->nb);
+    if (!ens->ready[box]) return ens_fail(LBM_ERR_STATE, "box %d is not initialised", box);
+    tslb::CtxView v;
+    lbm_status st = tslb::ctx_view(coarse, &v);
+    if (st != LBM_OK) return st;
+    const EnsBox &B = ens->box[box];
+    if (v.storage != LBM_FP32 || B.G.nx != 2 * v.G.nx || B.G.ny != 2 * v.G.ny || B.G.nz != 2 * v.G.nz)
+        return ens_fail(LBM_ERR_ARG, "coarse context must be FP32 with half the box size in every direction");
+    const size_t o = (size_t)B.off;
+    const int c = ens->cur;
+    // order the coarse stream after the ensemble's work on this machine
+    cudaEvent_t ev;
+    ENS_TRY(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    cudaError_t err = cudaEventRecord(ev, ens->stream);
+    if (err == cudaSuccess) err = cudaStreamWaitEvent(v.stream, ev, 0);
+    cudaEventDestroy(ev);
+    if (err != cudaSuccess) return ens_fail(LBM_ERR_CUDA, "stream ordering failed: %s", cudaGetErrorString(err));
+    tslb::restrict_state_kernel<<<(v.G.N + 255) / 256, 256, 0, v.stream>>>(
+        B.G, ens->g[c] + 27 * o, ens->phi[c] + o, ens->u[c] + 3 * o, v.G, v.g, v.phi, v.u);
+    ENS_TRY(cudaGetLastError());
+    tslb::ctx_state_changed(coarse);
+    return LBM_OK;
 }
 
 }  // extern "C"

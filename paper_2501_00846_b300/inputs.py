@@ -244,3 +244,95 @@ def droplet_ensemble(n=256, seed=2501, L_min=32, L_max=96, v_max=0.02):
                             mobility=0.1, gravity=(0.0, 0.0, 0.0), rho_ref=1.0, body=(0.0, 0.0, 0.0),
                             kind="droplet", center=(c, c, c), radius=R, noise=amp, seed=seed * 1000 + b))
     return out
+
+
+@dataclasses.dataclass
+class Collision:
+    """Head-on binary droplet collision in a periodic cube: two drops of radius R on the z axis,
+    their surfaces a gap apart, approaching each other at relative speed `speed` (each drop moves
+    at speed/2 towards the other), with an optional lateral offset b of the drop centres along x
+    and a seeded Fourier velocity noise.  Density ratio rho_L/rho_G, equal kinematic viscosity nu in
+    both phases, surface tension sigma, interface width W, mobility D."""
+    L: int = 128
+    R: float = 20.0
+    speed: float = 0.05
+    ratio: float = 100.0
+    gap: float = 12.0
+    offset: float = 0.0
+    nu: float = 0.04
+    sigma: float = 0.005
+    width: float = 4.0
+    mobility: float = 0.1
+    noise: float = 0.0
+    seed: int = 0
+    name: str = "collision"
+
+    @property
+    def nx(self):
+        return self.L
+
+    ny = nx
+    nz = nx
+
+    @property
+    def n(self):
+        return self.L ** 3
+
+    def _centres(self):
+        c = (self.L - 1) / 2.0
+        d = 2.0 * self.R + self.gap
+        return ((c + self.offset / 2, c, c - d / 2), (c - self.offset / 2, c, c + d / 2))
+
+    def _drops(self):
+        c1, c2 = self._centres()
+        return (sphere_phi(self.L, self.L, self.L, c1, self.R, self.width),
+                sphere_phi(self.L, self.L, self.L, c2, self.R, self.width))
+
+    def fields(self):
+        """(phi0, u0, p*0) in one pass: phi = the two drop profiles (capped at 1), u = +-speed/2
+        along z inside each drop plus the noise, p* = 3 p / rho(phi) with the Laplace jump
+        2 sigma / R inside each drop."""
+        p1, p2 = self._drops()
+        phi = np.minimum(p1 + p2, 1.0)
+        u = np.zeros((3, self.L, self.L, self.L))
+        u[2] = 0.5 * self.speed * (p1 - p2)
+        if self.noise > 0.0:
+            u += fourier_velocity(self.L, self.L, self.L, amplitude=self.noise, seed=self.seed)
+        rho = phi * 1.0 + (1.0 - phi) / self.ratio
+        return phi, u, 3.0 * (2.0 * self.sigma / self.R) * (p1 + p2) / rho
+
+    def phi0(self):
+        return self.fields()[0]
+
+    def u0(self):
+        return self.fields()[1]
+
+    def pstar_init(self):
+        return self.fields()[2]
+
+    def params(self) -> dict:
+        rho_g = 1.0 / self.ratio
+        return dict(nx=self.L, ny=self.L, nz=self.L, wall_z=0, rho_l=1.0, rho_g=rho_g, mu_l=self.nu,
+                    mu_g=self.nu * rho_g, sigma=self.sigma, width=self.width, mobility=self.mobility,
+                    gravity=(0.0, 0.0, 0.0), rho_ref=1.0, body=(0.0, 0.0, 0.0))
+
+    def coarse_params(self) -> dict:
+        """Parameters of the same flow on a 2x coarser grid in acoustic scaling (dx and dt doubled,
+        lattice velocities unchanged): nu, sigma and D halve in lattice units; the interface keeps
+        W lattice units (so it is twice as wide physically)."""
+        p = self.params()
+        p.update(nx=self.L // 2, ny=self.L // 2, nz=self.L // 2, mu_l=p["mu_l"] / 2, mu_g=p["mu_g"] / 2,
+                 sigma=p["sigma"] / 2, mobility=p["mobility"] / 2)
+        return p
+
+
+def collision_set(n=200, seed=7, L=128, R=20.0):
+    """Seeded head-on collisions: gap ~ U[6, 18], lateral offset ~ U[-1, 1] (nodes), speed
+    0.05 * U[0.9, 1.1], Fourier velocity noise of amplitude 0.001."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for k in range(n):
+        out.append(Collision(L=L, R=R, speed=0.05 * float(rng.uniform(0.9, 1.1)), gap=float(rng.uniform(6.0, 18.0)),
+                             offset=float(rng.uniform(-1.0, 1.0)), noise=0.001, seed=seed * 10000 + k,
+                             name=f"collision_{k}"))
+    return out

@@ -133,6 +133,7 @@ def load(path: str = LIB_PATH):
         "lbm_ens_num_nodes": ([vp], ll),
         "lbm_ens_box_nodes": ([vp, i], ll),
         "lbm_ens_step_count": ([vp], ll),
+        "lbm_ens_restrict_state": ([vp, i, vp], i),
         "lbm_cnn_create": ([i, i, i, ctypes.c_ulonglong, vp, ctypes.POINTER(vp)], i),
         "lbm_cnn_destroy": ([vp], None),
         "lbm_cnn_num_params": ([], i),
@@ -394,6 +395,10 @@ class Ensemble:
         for k, v in kw.items():
             setattr(t, k, v)
         _check(load().lbm_ens_set_tuning(self._ens, ctypes.byref(t)))
+
+    def restrict_state(self, box: int, coarse: "Solver"):
+        """Set a half-size context's state to the 2x restriction of box ``box``'s state."""
+        _check(load().lbm_ens_restrict_state(self._ens, int(box), coarse._ctx))
 
     def autotune(self, reps: int = 5) -> dict:
         t = LbmTuning()

@@ -145,8 +145,8 @@ def test_zero_network_leaves_the_state_unchanged_and_a_constant_shifts_momentum(
         solver.closure_apply(s, net, norm)
         g1, phi1, u1 = s.get_state()
         assert np.array_equal(g0, g1) and np.array_equal(phi0, phi1) and np.array_equal(u0, u1)
-        # W4 = 0, b4 = (1, 1, -1, 2): y is constant, so dphi = 0 after the mean is removed and
-        # ubar shifts by out_scale * (1, -1, 2) everywhere
+        # W4 = 0, b4 = (1, 1, -1, 2): y is constant; ubar shifts by out_scale * (1, -1, 2)
+        # everywhere, phi by out_scale[0] in the bulk phases, compensated inside the interfaces
         flat = np.zeros(net.num_params, np.float32)
         flat[-4:] = [1.0, 1.0, -1.0, 2.0]
         net.set_params(flat)
@@ -154,7 +154,10 @@ def test_zero_network_leaves_the_state_unchanged_and_a_constant_shifts_momentum(
         g2, phi2, u2 = s.get_state()
         s.step(2)                                   # the corrected state steps on
         assert s.observables()["n_nonfinite"] == 0
-    assert np.abs(phi2 - phi1).max() < 1e-6
+    # phi: the sum is unchanged and no node leaves [min(phi, 0), max(phi, 1)]
+    assert abs(phi2.astype(np.float64).sum() - phi1.astype(np.float64).sum()) < 1e-6 * phi1.size
+    assert (phi2 >= np.minimum(phi1, 0) - 1e-6).all() and (phi2 <= np.maximum(phi1, 1) + 1e-6).all()
+    assert np.abs(phi2 - phi1).max() > 1e-4
     du = np.array([1e-3 * 1.0, 2e-3 * -1.0, 3e-3 * 2.0])
     for a in range(3):
         assert np.allclose(u2[a] - u1[a], du[a], atol=1e-7)
@@ -190,3 +193,24 @@ def test_features_and_targets_follow_their_definitions():
     assert np.allclose(t[0], 0.01 / 1e-3, rtol=1e-3)
     for a in range(3):
         assert np.allclose(t[1 + a], -0.002 / norm.out_scale[1 + a], rtol=1e-3)
+
+
+def test_trained_closure_beats_the_plain_coarse_run():
+    """The whole pipeline at a small size: 32 seeded collisions on a 64^3 fine grid (R = 10),
+    10 pairs each, 10 epochs; then a held-out collision run on the 32^3 coarse grid with and
+    without the phi correction after every step, against the restricted fine run.  The closure
+    must cut the RMS error of phi by at least a third over 120 coarse steps and keep the run
+    finite."""
+    from paper_2501_00846_b300 import closure
+    cols = inputs.collision_set(33, seed=3, L=64, R=10.0)
+    norm = closure.estimate_norm(cols[:4], stride=24)
+    X, T = closure.generate(cols[:32], snapshots=10, stride=24, batch=16, norm=norm)
+    with solver.Network(32, 32, 32, seed=3) as net:
+        hist = closure.train(net, X, T, epochs=10, lr=2e-3)
+        del X, T
+        applied = solver.LbmClosureNorm.make(norm.in_shift, norm.in_scale, [norm.out_scale[0], 0.0, 0.0, 0.0])
+        res = closure.evaluate(net, applied, cols[32], coarse_steps=120, every=20)
+    print("loss", hist[0], "->", hist[-1], "plain", res["plain"], "closure", res["closure"])
+    assert hist[-1] < 0.5 * hist[0]
+    assert np.isfinite(res["closure"]["phi_rms_mean"])
+    assert res["ratio_phi"] < 0.67
