@@ -312,6 +312,11 @@ lbm_status lbm_cnn_get_params(lbm_cnn *cnn, float *params);        /* host, lbm_
 lbm_status lbm_cnn_set_params(lbm_cnn *cnn, const float *params);  /* host; resets nothing else */
 lbm_status lbm_cnn_get_grads(lbm_cnn *cnn, float *grads);          /* host, the kept gradients */
 
+/* Convolution kernel: 0 (default) stages each block's input tile in shared memory (cp.async, ldmatrix);
+ * 1 reads the MMA fragments straight from global memory.  Both issue the same MMAs in the same order
+ * and give identical results.  LBM_ERR_ARG for other values. */
+lbm_status lbm_cnn_set_conv_kernel(lbm_cnn *cnn, int kernel);
+
 /* y = network(x): x [5][N] and y [4][N] FP32 channel-first device arrays (N = nx ny nz). */
 lbm_status lbm_cnn_forward(lbm_cnn *cnn, const float *x, float *y);
 

@@ -118,6 +118,146 @@ __global__ void __launch_bounds__(128) conv_mma_kernel(int nx, int ny, int nz, c
     }
 }
 
+// ---- the same convolution with the input tile staged in shared memory ----------------------
+//
+// A block owns a 32 x 8 column tile of nodes (one x row of 32 nodes per warp) and marches a z
+// chunk.  The tile's halo-1 plane (34 x 10 nodes, all input channels, channel stride padded by 8
+// so that the eight 16-byte rows an ldmatrix reads fall in distinct banks) lives in a 4-slot ring
+// of shared-memory planes filled by cp.async two planes ahead; each B fragment pair is one
+// ldmatrix.x4 (8 nodes x 16 channels of two n8 tiles).  The MMAs and their order are those of
+// conv_mma_kernel, so both kernels give the same result bit for bit.
+
+constexpr int CT_TY = 8;                 // y rows per block, one per warp
+constexpr int CT_HX = 34, CT_HY = CT_TY + 2;
+constexpr int CT_SLOTS = 4;
+
+template <int CB>
+struct CtGeom {
+    static constexpr int CI = CB * 16;
+    static constexpr int CS = CI + 8;                 // staged channel stride (bf16)
+    static constexpr int PLANE = CT_HY * CT_HX * CS;  // bf16 per staged plane
+};
+
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
+{
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+__device__ __forceinline__ void ldmatrix_x4(uint32_t (&r)[4], const void *smem)
+{
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(sa));
+}
+
+__device__ __forceinline__ int mwrap(int v, int n)
+{
+    v %= n;
+    return v < 0 ? v + n : v;
+}
+
+// stage plane p (any integer z; wrapped) of the halo-1 tile at (x0, y0) into a slot
+template <int CB>
+__device__ __forceinline__ void ct_load_plane(__nv_bfloat16 *slot, const __nv_bfloat16 *__restrict__ in, int nx,
+                                              int ny, int nz, int x0, int y0, int p)
+{
+    using Gm = CtGeom<CB>;
+    constexpr int CHUNKS = Gm::CI / 8;   // 16-byte chunks per node
+    const size_t plane = (size_t)mwrap(p, nz) * nx * ny;
+    for (int e = threadIdx.x; e < CT_HY * CT_HX * CHUNKS; e += blockDim.x) {
+        const int chunk = e % CHUNKS, node = e / CHUNKS;
+        const int hy = node / CT_HX, hx = node - hy * CT_HX;
+        const size_t src = plane + (size_t)mwrap(y0 - 1 + hy, ny) * nx + mwrap(x0 - 1 + hx, nx);
+        cp_async16(slot + (size_t)(hy * CT_HX + hx) * Gm::CS + chunk * 8, in + src * Gm::CI + chunk * 8);
+    }
+}
+
+template <int MT, int CB>
+__global__ void __launch_bounds__(256) conv_tile_kernel(int nx, int ny, int nz, const uint4 *__restrict__ wfrag,
+                                                        const __nv_bfloat16 *__restrict__ in,
+                                                        const float *__restrict__ bias, float *__restrict__ z,
+                                                        int zlen)
+{
+    using Gm = CtGeom<CB>;
+    extern __shared__ uint4 smem[];
+    constexpr int NW = 27 * CB * MT * 32;
+    constexpr int CO = MT * 16;
+    uint4 *sw = smem;
+    __nv_bfloat16 *win = reinterpret_cast<__nv_bfloat16 *>(smem + NW);
+    const int ntx = nx / 32;
+    const int x0 = (blockIdx.x % ntx) * 32, y0 = (blockIdx.x / ntx) * CT_TY;
+    const int z0 = blockIdx.y * zlen, z1 = min(nz, z0 + zlen);
+    if (z0 >= nz) return;   // whole block
+    for (int i = threadIdx.x; i < NW; i += blockDim.x) sw[i] = wfrag[i];
+    auto slot = [&](int p) { return win + (size_t)((p - (z0 - 1)) & (CT_SLOTS - 1)) * Gm::PLANE; };
+#pragma unroll 1
+    for (int j = 0; j < 3; ++j) ct_load_plane<CB>(slot(z0 - 1 + j), in, nx, ny, nz, x0, y0, z0 - 1 + j);
+    cp_async_commit();
+    cp_async_wait_all();
+    __syncthreads();
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int g = lane >> 2, t = lane & 3, q = lane >> 3, r = lane & 7;
+    const int yout = y0 + warp;
+#pragma unroll 1
+    for (int zc = z0; zc < z1; ++zc) {
+        if (zc + 2 <= z1) ct_load_plane<CB>(slot(zc + 2), in, nx, ny, nz, x0, y0, zc + 2);
+        cp_async_commit();
+        float acc[MT][4][4];
+#pragma unroll
+        for (int m = 0; m < MT; ++m)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) acc[m][j][0] = acc[m][j][1] = acc[m][j][2] = acc[m][j][3] = 0.0f;
+#pragma unroll 1
+        for (int k = 0; k < 27; ++k) {
+            const int dz = k / 9 - 1, dy = (k / 3) % 3 - 1, dx = k % 3 - 1;
+            const __nv_bfloat16 *pl = slot(zc + dz) + (size_t)(warp + 1 + dy) * CT_HX * Gm::CS;
+#pragma unroll
+            for (int cb = 0; cb < CB; ++cb) {
+                uint32_t b[4][2];
+#pragma unroll
+                for (int jj = 0; jj < 2; ++jj) {
+                    const int hx = 8 * (2 * jj + (q >> 1)) + r + 1 + dx;
+                    uint32_t rr[4];
+                    ldmatrix_x4(rr, pl + (size_t)hx * Gm::CS + cb * 16 + 8 * (q & 1));
+                    b[2 * jj][0] = rr[0];
+                    b[2 * jj][1] = rr[1];
+                    b[2 * jj + 1][0] = rr[2];
+                    b[2 * jj + 1][1] = rr[3];
+                }
+#pragma unroll
+                for (int m = 0; m < MT; ++m) {
+                    const uint4 a = sw[((k * CB + cb) * MT + m) * 32 + lane];
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) mma_bf16(acc[m][j], a, b[j][0], b[j][1]);
+                }
+            }
+        }
+        if (yout < ny) {
+            const size_t node0 = ((size_t)zc * ny + yout) * nx + x0;
+#pragma unroll
+            for (int m = 0; m < MT; ++m) {
+                const int o = m * 16 + g;
+                const float b0 = bias ? bias[o] : 0.0f, b1 = bias ? bias[o + 8] : 0.0f;
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const size_t n = node0 + 8 * j + 2 * t;
+                    z[n * CO + o] = acc[m][j][0] + b0;
+                    z[(n + 1) * CO + o] = acc[m][j][1] + b0;
+                    z[n * CO + o + 8] = acc[m][j][2] + b1;
+                    z[(n + 1) * CO + o + 8] = acc[m][j][3] + b1;
+                }
+            }
+        }
+        cp_async_wait_all();
+        __syncthreads();
+    }
+}
+
 __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi)
 {
     const uint32_t l = __bfloat16_as_ushort(__float2bfloat16_rn(lo));
@@ -485,6 +625,8 @@ struct lbm_cnn {
     int loss_blocks = 0;
     long long adam_t = 0;
     int conv_blocks = 0;
+    int sms = 0;
+    int conv_kernel = 0;                 // 0: shared-memory tiles; 1: fragments straight from global memory
 };
 
 namespace {
@@ -554,6 +696,26 @@ cudaError_t repack(lbm_cnn *c)
 template <int MT, int CB>
 cudaError_t launch_conv(lbm_cnn *c, const uint4 *wfrag, const __nv_bfloat16 *in, const float *bias, float *out)
 {
+    if (c->conv_kernel == 0) {   // shared-memory tiles (default)
+        const size_t smem = (size_t)frag_count(MT, CB) * sizeof(uint4) +
+                            (size_t)tslb::CT_SLOTS * tslb::CtGeom<CB>::PLANE * sizeof(__nv_bfloat16);
+        static bool attr = false;
+        if (!attr) {
+            cudaError_t e = cudaFuncSetAttribute(tslb::conv_tile_kernel<MT, CB>,
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+            attr = true;
+        }
+        const int tiles = (c->nx / 32) * ((c->ny + tslb::CT_TY - 1) / tslb::CT_TY);
+        int nzc = c->sms / tiles;                   // about one block per SM
+        if (nzc < 1) nzc = 1;
+        if (nzc > c->nz) nzc = c->nz;
+        const int zlen = (c->nz + nzc - 1) / nzc;
+        nzc = (c->nz + zlen - 1) / zlen;
+        tslb::conv_tile_kernel<MT, CB><<<dim3(tiles, nzc), 256, smem, c->stream>>>(c->nx, c->ny, c->nz, wfrag, in,
+                                                                                    bias, out, zlen);
+        return cudaGetLastError();
+    }
     const size_t smem = (size_t)frag_count(MT, CB) * sizeof(uint4);
     static bool attr = false;
     if (!attr) {
@@ -698,6 +860,7 @@ lbm_status lbm_cnn_create(int nx, int ny, int nz, unsigned long long seed, void 
                         cudaGetErrorString(err));
     }
     c->conv_blocks = sms * 4;
+    c->sms = sms;
     float *h = new (std::nothrow) float[ofs];
     if (!h) {
         free_cnn(c);
@@ -748,6 +911,14 @@ lbm_status lbm_cnn_get_grads(lbm_cnn *cnn, float *grads)
     if (!cnn || !grads) return cnn_fail(LBM_ERR_ARG, "network and grads are required");
     CNN_TRY(cudaMemcpyAsync(grads, cnn->grad, cnn->nparams * sizeof(float), cudaMemcpyDeviceToHost, cnn->stream));
     CNN_TRY(cudaStreamSynchronize(cnn->stream));
+    return LBM_OK;
+}
+
+lbm_status lbm_cnn_set_conv_kernel(lbm_cnn *cnn, int kernel)
+{
+    if (!cnn) return cnn_fail(LBM_ERR_ARG, "network is NULL");
+    if (kernel != 0 && kernel != 1) return cnn_fail(LBM_ERR_ARG, "kernel must be 0 or 1");
+    cnn->conv_kernel = kernel;
     return LBM_OK;
 }
 

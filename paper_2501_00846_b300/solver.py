@@ -141,6 +141,7 @@ def load(path: str = LIB_PATH):
         "lbm_cnn_set_params": ([vp, fp], i),
         "lbm_cnn_get_grads": ([vp, fp], i),
         "lbm_cnn_forward": ([vp, fp, fp], i),
+        "lbm_cnn_set_conv_kernel": ([vp, i], i),
         "lbm_cnn_grad": ([vp, fp, fp, i, ctypes.POINTER(ctypes.c_double)], i),
         "lbm_cnn_adam_step": ([vp, ctypes.c_float, ctypes.c_float], i),
         "lbm_closure_features": ([vp, ctypes.POINTER(LbmClosureNorm), fp], i),
@@ -487,6 +488,10 @@ class Network:
             out.append((w, flat[o:o + cout]))
             o += cout
         return out
+
+    def set_conv_kernel(self, kernel: int):
+        """0: shared-memory tiles (default); 1: fragments straight from global memory."""
+        _check(load().lbm_cnn_set_conv_kernel(self._cnn, int(kernel)))
 
     def forward(self, x, y):
         _check(load().lbm_cnn_forward(self._cnn, _dev(x, 5 * self.n), _dev(y, 4 * self.n)))

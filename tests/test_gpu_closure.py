@@ -214,3 +214,26 @@ def test_trained_closure_beats_the_plain_coarse_run():
     assert hist[-1] < 0.5 * hist[0]
     assert np.isfinite(res["closure"]["phi_rms_mean"])
     assert res["ratio_phi"] < 0.67
+
+
+@pytest.mark.parametrize("shape", [(64, 16, 8), (32, 6, 5), (32, 3, 2)], ids=["tiles", "ragged-y", "tiny"])
+def test_tiled_and_direct_convolutions_agree_bit_for_bit(shape):
+    """The shared-memory tile kernel issues the same MMAs in the same order as the kernel that
+    reads its fragments from global memory: outputs and gradients are identical."""
+    import torch
+    nx, ny, nz = shape
+    flat, x, t = _random_case(nx, ny, nz, seed=4)
+    out = []
+    for kernel in (0, 1):
+        with solver.Network(nx, ny, nz) as net:
+            net.set_conv_kernel(kernel)
+            net.set_params(flat)
+            xd = torch.from_numpy(x).cuda().reshape(-1)
+            td = torch.from_numpy(t).cuda().reshape(-1)
+            yd = torch.empty(4 * net.n, device="cuda")
+            net.forward(xd, yd)
+            net.grad(xd, td)
+            torch.cuda.synchronize()
+            out.append((yd.cpu().numpy(), net.get_grads()))
+    assert np.array_equal(out[0][0], out[1][0])
+    assert np.array_equal(out[0][1], out[1][1])
