@@ -312,9 +312,12 @@ lbm_status lbm_cnn_get_params(lbm_cnn *cnn, float *params);        /* host, lbm_
 lbm_status lbm_cnn_set_params(lbm_cnn *cnn, const float *params);  /* host; resets nothing else */
 lbm_status lbm_cnn_get_grads(lbm_cnn *cnn, float *grads);          /* host, the kept gradients */
 
-/* Convolution kernel: 0 (default) stages each block's input tile in shared memory (cp.async, ldmatrix);
- * 1 reads the MMA fragments straight from global memory.  Both issue the same MMAs in the same order
- * and give identical results.  LBM_ERR_ARG for other values. */
+/* Convolution kernel: 0 tcgen05.mma with TMEM accumulators (shared-memory descriptors); 1 (default,
+ * the fastest measured) mma.sync from shared-memory tiles (cp.async, ldmatrix); 2 mma.sync with
+ * fragments straight from global memory.  All three add the same BF16 products in the same order
+ * per output and gave identical results on every tested grid.  lbm_cnn_forward and lbm_cnn_grad return
+ * LBM_ERR_TIMEOUT if a tensor-core kernel gave up waiting for its MMAs.  LBM_ERR_ARG for other
+ * values. */
 lbm_status lbm_cnn_set_conv_kernel(lbm_cnn *cnn, int kernel);
 
 /* y = network(x): x [5][N] and y [4][N] FP32 channel-first device arrays (N = nx ny nz). */

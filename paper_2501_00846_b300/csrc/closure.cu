@@ -258,6 +258,254 @@ __global__ void __launch_bounds__(256) conv_tile_kernel(int nx, int ny, int nz, 
     }
 }
 
+// ---- the same convolution on the 5th-generation tensor cores (tcgen05, TMEM) ---------------
+//
+// GEMM orientation: D[n][o] = sum_{k, i} a[n + off_k][i] W[o][i][k] with M = 128 nodes (an 8 x 16
+// x-by-y patch of one plane), N = the output channels (32 or 16) and K = 16 input channels at one
+// offset per tcgen05.mma (kind::f16: BF16 operands, FP32 accumulation in TMEM).  Both operands
+// are read by the tensor core from shared memory through K-major, unswizzled matrix descriptors:
+//   A: the block's halo tile, staged channel-group-major ([channel group of 8][hy][hx][8]), so the
+//      8 x-consecutive nodes of a patch row are one 8 x 16-byte core matrix; patch rows are SBO =
+//      HX * 16 bytes apart, the two channel groups of a K step LBO = HY * HX * 16 bytes apart, and a
+//      neighbour offset (dx, dy) only moves the start address;
+//   B: the weights, [k][channel chunk][group of 8 channels][o][8] (LBO = N * 16, SBO = 128).
+// A block of 4 warps owns a 16 x 16 column tile (two patches) and marches a z chunk: one thread
+// issues the 2 x 27 x CB MMAs of plane zc into one of two TMEM accumulator buffers and commits them
+// to an mbarrier; meanwhile all four warps read back plane zc - 1's accumulators (tcgen05.ld, warp
+// w owns TMEM lanes 32w..32w+31 = patch rows 4w..4w+3), add the bias and store; the input ring
+// (4 planes, cp.async) is refilled two planes ahead once the MMAs that read the slot are done.
+// Every mbarrier wait is bounded: on expiry the kernel records an error, stops issuing work and
+// still releases its TMEM.
+
+constexpr int UM_TX = 16, UM_TY = 16;              // column tile: two 8 x 16 patches
+constexpr int UM_HX = UM_TX + 2, UM_HY = UM_TY + 2;
+constexpr int UM_SLOTS = 4;
+constexpr int UM_SPIN = 1 << 24;                   // mbarrier polls before giving up
+
+template <int CB>
+struct UmGeom {
+    static constexpr int CG = CB * 2;                              // groups of 8 input channels
+    static constexpr int PLANE_BYTES = CG * UM_HY * UM_HX * 16;    // one staged plane
+};
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// K-major, unswizzled shared-memory matrix descriptor (sm_100 layout: start >> 4, LBO >> 4,
+// SBO >> 4, descriptor version 1)
+__device__ __forceinline__ uint64_t umma_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo)
+{
+    return (uint64_t)((saddr >> 4) & 0x3FFF) | ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | ((uint64_t)1 << 46);
+}
+
+__device__ __forceinline__ void umma_bf16(uint32_t tmem, uint64_t da, uint64_t db, uint32_t idesc, uint32_t acc)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem),
+        "l"(da), "l"(db), "r"(idesc), "r"(acc));
+}
+
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity)
+{
+    for (int it = 0; it < UM_SPIN; ++it) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}\n"
+            : "=r"(done)
+            : "r"(mbar), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+template <int CB>
+__device__ __forceinline__ void um_load_plane(uint8_t *slot, const __nv_bfloat16 *__restrict__ in, int nx, int ny,
+                                              int nz, int x0, int y0, int p)
+{
+    constexpr int CG = UmGeom<CB>::CG;
+    const size_t plane = (size_t)mwrap(p, nz) * nx * ny;
+    for (int e = threadIdx.x; e < CG * UM_HY * UM_HX; e += blockDim.x) {
+        const int node = e % (UM_HY * UM_HX), cg = e / (UM_HY * UM_HX);
+        const int hy = node / UM_HX, hx = node - hy * UM_HX;
+        const size_t src = plane + (size_t)mwrap(y0 - 1 + hy, ny) * nx + mwrap(x0 - 1 + hx, nx);
+        cp_async16(slot + (size_t)e * 16, in + src * (CB * 16) + cg * 8);
+    }
+}
+
+// z[n][o] = bias[o] + sum_{k, i} W[o][i][k] in[n + off_k][i], CO = MT * 16 output channels (padded),
+// CB * 16 input channels (padded); wpack: [27][CB][2][CO][8] BF16 (pack_weights_umma_kernel).
+template <int MT, int CB>
+__global__ void __launch_bounds__(128, 1) conv_umma_kernel(int nx, int ny, int nz, const __nv_bfloat16 *__restrict__ wpack,
+                                                           const __nv_bfloat16 *__restrict__ in,
+                                                           const float *__restrict__ bias, float *__restrict__ z,
+                                                           int zlen, int *__restrict__ err)
+{
+    constexpr int CO = MT * 16;
+    constexpr int WBYTES = 27 * CB * 2 * CO * 16;
+    constexpr int PB = UmGeom<CB>::PLANE_BYTES;
+    constexpr uint32_t TCOLS = 2 * 2 * CO < 32 ? 32 : (2 * 2 * CO <= 64 ? 64 : 128);   // 2 buffers x 2 patches
+    extern __shared__ __align__(1024) uint8_t usm[];
+    __shared__ __align__(8) uint64_t mbar[2];
+    __shared__ uint32_t tmem_base;
+    __shared__ int abort_flag;
+    uint8_t *sw = usm;
+    uint8_t *ring = usm + ((WBYTES + 1023) / 1024) * 1024;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int ntx = nx / UM_TX;
+    const int x0 = (blockIdx.x % ntx) * UM_TX, y0 = (blockIdx.x / ntx) * UM_TY;
+    const int z0 = blockIdx.y * zlen, z1 = min(nz, z0 + zlen);
+    if (z0 >= nz) return;   // whole block
+
+    {   // weights (plain 16-byte copies)
+        const uint4 *src = reinterpret_cast<const uint4 *>(wpack);
+        uint4 *dst = reinterpret_cast<uint4 *>(sw);
+        for (int i = tid; i < WBYTES / 16; i += blockDim.x) dst[i] = src[i];
+    }
+    auto slot = [&](int p) { return ring + (size_t)((p - (z0 - 1)) & (UM_SLOTS - 1)) * PB; };
+    for (int j = 0; j < 3; ++j) um_load_plane<CB>(slot(z0 - 1 + j), in, nx, ny, nz, x0, y0, z0 - 1 + j);
+    cp_async_commit();
+    if (tid == 0) {
+        abort_flag = 0;
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_addr(&mbar[0])));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_addr(&mbar[1])));
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_addr(&tmem_base)),
+                     "r"(TCOLS));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
+    }
+    cp_async_wait_all();
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    const uint32_t tmem = tmem_base;
+    const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(CO >> 3) << 17) | ((128u >> 4) << 24);
+    const uint32_t lbo_a = UM_HY * UM_HX * 16, sbo_a = UM_HX * 16;
+    const uint32_t lbo_b = CO * 16, sbo_b = 128;
+    const uint32_t sw_addr = smem_addr(sw);
+    uint32_t phase[2] = {0u, 0u};
+
+    // read back the accumulators of plane p (buffer b), add the bias, store
+    auto epilogue = [&](int p, int b) {
+        const int mrow = 32 * warp + lane;             // patch row index: node (mrow % 8, mrow / 8)
+        const int yy = y0 + mrow / 8;
+#pragma unroll
+        for (int pt = 0; pt < 2; ++pt) {
+            uint32_t r[CO];
+            const uint32_t taddr = tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(b * 2 * CO + pt * CO);
+            if constexpr (CO == 32) {
+                asm volatile(
+                    "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,"
+                    "%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
+                    : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                      "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+                      "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
+                      "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
+                      "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+                    : "r"(taddr));
+            } else {
+                asm volatile(
+                    "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
+                    "[%16];\n"
+                    : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                      "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+                      "=r"(r[15])
+                    : "r"(taddr));
+            }
+            asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+            if (yy < ny) {
+                const size_t node = ((size_t)p * ny + yy) * nx + x0 + pt * 8 + (mrow % 8);
+                float4 *dst = reinterpret_cast<float4 *>(z + node * CO);
+#pragma unroll
+                for (int o = 0; o < CO; o += 4)
+                    dst[o / 4] = make_float4(__uint_as_float(r[o]) + (bias ? bias[o] : 0.0f),
+                                             __uint_as_float(r[o + 1]) + (bias ? bias[o + 1] : 0.0f),
+                                             __uint_as_float(r[o + 2]) + (bias ? bias[o + 2] : 0.0f),
+                                             __uint_as_float(r[o + 3]) + (bias ? bias[o + 3] : 0.0f));
+            }
+        }
+    };
+
+    bool ok = true;
+    for (int zc = z0; zc < z1 && ok; ++zc) {
+        const int b = (zc - z0) & 1;
+        if (tid == 0) {   // the MMAs of plane zc
+#pragma unroll 1
+            for (int pt = 0; pt < 2; ++pt) {
+                const uint32_t dt = tmem + (uint32_t)(b * 2 * CO + pt * CO);
+                uint32_t acc = 0;
+#pragma unroll 1
+                for (int k = 0; k < 27; ++k) {
+                    const int dz = k / 9 - 1, dy = (k / 3) % 3 - 1, dx = k % 3 - 1;
+                    const uint32_t abase = smem_addr(slot(zc + dz)) + (uint32_t)(((1 + dy) * UM_HX + pt * 8 + 1 + dx) * 16);
+#pragma unroll
+                    for (int cb = 0; cb < CB; ++cb) {
+                        const uint64_t da = umma_desc(abase + (uint32_t)(2 * cb) * lbo_a, lbo_a, sbo_a);
+                        const uint64_t db = umma_desc(sw_addr + (uint32_t)((k * CB + cb) * 2 * CO * 16), lbo_b, sbo_b);
+                        umma_bf16(dt, da, db, idesc, acc);
+                        acc = 1;
+                    }
+                }
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                smem_addr(&mbar[b])));
+        }
+        if (zc > z0) {   // plane zc - 1: wait for its MMAs, read back (a warp decides as one)
+            const bool good = __all_sync(0xffffffffu, mbar_wait(smem_addr(&mbar[1 - b]), phase[1 - b]));
+            phase[1 - b] ^= 1u;
+            asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+            if (good)
+                epilogue(zc - 1, 1 - b);
+            else if (lane == 0)
+                abort_flag = 1;
+        }
+        // refill: plane zc + 2 into the slot of plane zc - 2 (read only by plane zc - 1's MMAs)
+        if (zc + 2 <= z1) um_load_plane<CB>(slot(zc + 2), in, nx, ny, nz, x0, y0, zc + 2);
+        cp_async_commit();
+        cp_async_wait_all();
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+        asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+        __syncthreads();
+        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+        ok = abort_flag == 0;
+    }
+    if (ok) {   // the last plane
+        const int b = (z1 - 1 - z0) & 1;
+        const bool good = __all_sync(0xffffffffu, mbar_wait(smem_addr(&mbar[b]), phase[b]));
+        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+        if (good)
+            epilogue(z1 - 1, b);
+        else if (lane == 0)
+            abort_flag = 1;
+    }
+    if (abort_flag && tid == 0) atomicExch(err, 1);
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(TCOLS));
+}
+
+// Weights for conv_umma_kernel: [27][CB][2][rows (CO)][8] BF16 with value(o, i, k) = W[o][i][k], or
+// for the input gradient (transpose) W[i][o][26 - k]; zero for padded rows or channels.
+__global__ void pack_weights_umma_kernel(const float *__restrict__ W, int cout, int cin, int co_pad, int cb_count,
+                                         bool transpose, __nv_bfloat16 *__restrict__ out)
+{
+    const int total = 27 * cb_count * 2 * co_pad * 8;
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= total) return;
+    const int e = idx % 8, o = (idx / 8) % co_pad, cg = (idx / (8 * co_pad)) % 2;
+    const int kc = idx / (16 * co_pad);
+    const int cb = kc % cb_count, k = kc / cb_count;
+    const int i = cb * 16 + cg * 8 + e;
+    const int rows = transpose ? cin : cout, cols = transpose ? cout : cin;
+    float v = 0.0f;
+    if (o < rows && i < cols) v = transpose ? W[((size_t)i * cin + o) * 27 + (26 - k)] : W[((size_t)o * cin + i) * 27 + k];
+    out[idx] = __float2bfloat16_rn(v);
+}
+
 __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi)
 {
     const uint32_t l = __bfloat16_as_ushort(__float2bfloat16_rn(lo));
@@ -615,6 +863,9 @@ struct lbm_cnn {
     float *p = nullptr, *grad = nullptr, *m = nullptr, *v = nullptr;   // FP32 master state
     uint4 *wf[tslb::NLAYER] = {};        // forward fragments
     uint4 *wt[tslb::NLAYER] = {};        // transposed fragments (layers 2..4)
+    __nv_bfloat16 *wu[tslb::NLAYER] = {};   // tcgen05 operand layout of the weights
+    __nv_bfloat16 *wut[tslb::NLAYER] = {};  // ... and of the transposed weights (layers 2..4)
+    int *derr = nullptr;                 // set by a tensor-core kernel whose mbarrier wait expired
     __nv_bfloat16 *a[tslb::NLAYER] = {}; // layer inputs, channel-last BF16: a[0] [N][16], a[1..3] [N][32]
     float *z[tslb::NLAYER] = {};         // pre-activations, channel-last FP32 ([N][32], last [N][16])
     float *dz = nullptr, *da = nullptr;  // [N][32] FP32
@@ -626,7 +877,8 @@ struct lbm_cnn {
     long long adam_t = 0;
     int conv_blocks = 0;
     int sms = 0;
-    int conv_kernel = 0;                 // 0: shared-memory tiles; 1: fragments straight from global memory
+    int conv_kernel = 1;                 // 0: tcgen05 / TMEM; 1: mma.sync from shared-memory tiles (default,
+                                         // fastest measured); 2: mma.sync from global memory
 };
 
 namespace {
@@ -660,6 +912,8 @@ void free_cnn(lbm_cnn *c)
     for (int l = 0; l < tslb::NLAYER; ++l) {
         cudaFree(c->wf[l]);
         cudaFree(c->wt[l]);
+        cudaFree(c->wu[l]);
+        cudaFree(c->wut[l]);
         cudaFree(c->a[l]);
         cudaFree(c->z[l]);
     }
@@ -669,6 +923,7 @@ void free_cnn(lbm_cnn *c)
     cudaFree(c->xbuf);
     cudaFree(c->ybuf);
     cudaFree(c->dsum);
+    cudaFree(c->derr);
     if (c->h_sum) cudaFreeHost(c->h_sum);
     delete c;
 }
@@ -683,20 +938,50 @@ cudaError_t repack(lbm_cnn *c)
         const int n = frag_count(mt, cb);
         tslb::pack_weights_kernel<<<(n + 255) / 256, 256, 0, c->stream>>>(c->p + c->pofs[l], tslb::COUT[l],
                                                                            tslb::CIN[l], mt, cb, false, c->wf[l]);
+        const int nu = 27 * cb * 2 * COUTP[l] * 8;
+        tslb::pack_weights_umma_kernel<<<(nu + 255) / 256, 256, 0, c->stream>>>(c->p + c->pofs[l], tslb::COUT[l],
+                                                                                 tslb::CIN[l], COUTP[l], cb, false,
+                                                                                 c->wu[l]);
         if (l > 0) {
             const int mtt = CINP[l] / 16, cbt = COUTP[l] / 16;
             const int nt = frag_count(mtt, cbt);
             tslb::pack_weights_kernel<<<(nt + 255) / 256, 256, 0, c->stream>>>(c->p + c->pofs[l], tslb::COUT[l],
                                                                                 tslb::CIN[l], mtt, cbt, true, c->wt[l]);
+            const int nut = 27 * cbt * 2 * CINP[l] * 8;
+            tslb::pack_weights_umma_kernel<<<(nut + 255) / 256, 256, 0, c->stream>>>(c->p + c->pofs[l], tslb::COUT[l],
+                                                                                      tslb::CIN[l], CINP[l], cbt, true,
+                                                                                      c->wut[l]);
         }
     }
     return cudaGetLastError();
 }
 
 template <int MT, int CB>
-cudaError_t launch_conv(lbm_cnn *c, const uint4 *wfrag, const __nv_bfloat16 *in, const float *bias, float *out)
+cudaError_t launch_conv(lbm_cnn *c, int layer, bool transpose, const __nv_bfloat16 *in, const float *bias, float *out)
 {
-    if (c->conv_kernel == 0) {   // shared-memory tiles (default)
+    const uint4 *wfrag = transpose ? c->wt[layer] : c->wf[layer];
+    const __nv_bfloat16 *wpack = transpose ? c->wut[layer] : c->wu[layer];
+    if (c->conv_kernel == 0 && c->nx % tslb::UM_TX == 0) {   // tcgen05 / TMEM
+        constexpr int WB = 27 * CB * 2 * MT * 16 * 16;
+        const size_t smem = (size_t)((WB + 1023) / 1024) * 1024 + (size_t)tslb::UM_SLOTS * tslb::UmGeom<CB>::PLANE_BYTES;
+        static bool attr = false;
+        if (!attr) {
+            cudaError_t e = cudaFuncSetAttribute(tslb::conv_umma_kernel<MT, CB>,
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+            attr = true;
+        }
+        const int tiles = (c->nx / tslb::UM_TX) * ((c->ny + tslb::UM_TY - 1) / tslb::UM_TY);
+        int nzc = c->sms / tiles;
+        if (nzc < 1) nzc = 1;
+        if (nzc > c->nz) nzc = c->nz;
+        const int zlen = (c->nz + nzc - 1) / nzc;
+        nzc = (c->nz + zlen - 1) / zlen;
+        tslb::conv_umma_kernel<MT, CB><<<dim3(tiles, nzc), 128, smem, c->stream>>>(c->nx, c->ny, c->nz, wpack, in, bias,
+                                                                                    out, zlen, c->derr);
+        return cudaGetLastError();
+    }
+    if (c->conv_kernel <= 1) {   // mma.sync from shared-memory tiles
         const size_t smem = (size_t)frag_count(MT, CB) * sizeof(uint4) +
                             (size_t)tslb::CT_SLOTS * tslb::CtGeom<CB>::PLANE * sizeof(__nv_bfloat16);
         static bool attr = false;
@@ -736,14 +1021,14 @@ cudaError_t forward(lbm_cnn *c, const float *x)
     const int N = c->N;
     cudaError_t e;
     tslb::pack_input_kernel<<<(N + 255) / 256, 256, 0, c->stream>>>(x, N, c->a[0]);
-    if ((e = launch_conv<2, 1>(c, c->wf[0], c->a[0], c->p + c->pofs[0] + tslb::wcount(0), c->z[0])) != cudaSuccess)
+    if ((e = launch_conv<2, 1>(c, 0, false, c->a[0], c->p + c->pofs[0] + tslb::wcount(0), c->z[0])) != cudaSuccess)
         return e;
     for (int l = 1; l < tslb::NLAYER; ++l) {
         const size_t cnt = (size_t)N * 32;
         tslb::silu_kernel<<<(unsigned)((cnt + 255) / 256), 256, 0, c->stream>>>(c->z[l - 1], cnt, c->a[l]);
         const float *bias = c->p + c->pofs[l] + tslb::wcount(l);
-        e = l < 3 ? launch_conv<2, 2>(c, c->wf[l], c->a[l], bias, c->z[l])
-                  : launch_conv<1, 2>(c, c->wf[l], c->a[l], bias, c->z[l]);
+        e = l < 3 ? launch_conv<2, 2>(c, l, false, c->a[l], bias, c->z[l])
+                  : launch_conv<1, 2>(c, l, false, c->a[l], bias, c->z[l]);
         if (e != cudaSuccess) return e;
     }
     return cudaGetLastError();
@@ -765,8 +1050,8 @@ cudaError_t backward(lbm_cnn *c)
         tslb::dbias_kernel<<<nchunk, 256, 0, c->stream>>>(c->dz, cop, tslb::COUT[l], N, chunk, db);
         if (l == 0) break;
         // da_{l-1}[n][i] = sum_{k,o} W_l[o][i][k] dz_l[n - off_k][o]
-        e = l == 3 ? launch_conv<2, 1>(c, c->wt[l], c->dzb, nullptr, c->da)
-                   : launch_conv<2, 2>(c, c->wt[l], c->dzb, nullptr, c->da);
+        e = l == 3 ? launch_conv<2, 1>(c, l, true, c->dzb, nullptr, c->da)
+                   : launch_conv<2, 2>(c, l, true, c->dzb, nullptr, c->da);
         if (e != cudaSuccess) return e;
         const size_t cnt = (size_t)N * 32;
         tslb::silu_back_kernel<<<(unsigned)((cnt + 255) / 256), 256, 0, c->stream>>>(c->da, c->z[l - 1], cnt, c->dz,
@@ -846,10 +1131,14 @@ lbm_status lbm_cnn_create(int nx, int ny, int nz, unsigned long long seed, void 
     for (int l = 0; l < tslb::NLAYER && err == cudaSuccess; ++l) {
         err = cudaMalloc(&c->wf[l], frag_count(COUTP[l] / 16, CINP[l] / 16) * sizeof(uint4));
         if (err == cudaSuccess && l > 0) err = cudaMalloc(&c->wt[l], frag_count(CINP[l] / 16, COUTP[l] / 16) * sizeof(uint4));
+        if (err == cudaSuccess) err = cudaMalloc(&c->wu[l], (size_t)27 * CINP[l] * COUTP[l] * 2);
+        if (err == cudaSuccess && l > 0) err = cudaMalloc(&c->wut[l], (size_t)27 * CINP[l] * COUTP[l] * 2);
         if (err == cudaSuccess) err = cudaMalloc(&c->a[l], N * CINP[l] * 2);
         if (err == cudaSuccess) err = cudaMalloc(&c->z[l], N * COUTP[l] * sizeof(float));
     }
     if (err == cudaSuccess) err = cudaMallocHost(&c->h_sum, sizeof(double) * 2);
+    if (err == cudaSuccess) err = cudaMalloc(&c->derr, sizeof(int));
+    if (err == cudaSuccess) err = cudaMemset(c->derr, 0, sizeof(int));
     int dev = 0, sms = 0;
     if (err == cudaSuccess) err = cudaGetDevice(&dev);
     if (err == cudaSuccess) err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -917,8 +1206,18 @@ lbm_status lbm_cnn_get_grads(lbm_cnn *cnn, float *grads)
 lbm_status lbm_cnn_set_conv_kernel(lbm_cnn *cnn, int kernel)
 {
     if (!cnn) return cnn_fail(LBM_ERR_ARG, "network is NULL");
-    if (kernel != 0 && kernel != 1) return cnn_fail(LBM_ERR_ARG, "kernel must be 0 or 1");
+    if (kernel < 0 || kernel > 2) return cnn_fail(LBM_ERR_ARG, "kernel must be 0, 1 or 2");
     cnn->conv_kernel = kernel;
+    return LBM_OK;
+}
+
+// LBM_ERR_TIMEOUT once a tensor-core kernel reported an expired mbarrier wait (synchronises)
+lbm_status check_timeout(lbm_cnn *cnn)
+{
+    int h = 0;
+    CNN_TRY(cudaMemcpyAsync(&h, cnn->derr, sizeof(int), cudaMemcpyDeviceToHost, cnn->stream));
+    CNN_TRY(cudaStreamSynchronize(cnn->stream));
+    if (h) return cnn_fail(LBM_ERR_TIMEOUT, "a tensor-core convolution gave up waiting for its MMAs");
     return LBM_OK;
 }
 
@@ -928,7 +1227,7 @@ lbm_status lbm_cnn_forward(lbm_cnn *cnn, const float *x, float *y)
     CNN_TRY(forward(cnn, x));
     tslb::unpack_output_kernel<<<(cnn->N + 255) / 256, 256, 0, cnn->stream>>>(cnn->z[3], cnn->N, y);
     CNN_TRY(cudaGetLastError());
-    return LBM_OK;
+    return check_timeout(cnn);
 }
 
 lbm_status lbm_cnn_grad(lbm_cnn *cnn, const float *x, const float *t, int accumulate, double *loss)
@@ -953,7 +1252,7 @@ lbm_status lbm_cnn_grad(lbm_cnn *cnn, const float *x, const float *t, int accumu
     for (int b = 0; b < cnn->loss_blocks; ++b) s += hp[b];
     delete[] hp;
     if (loss) *loss = s / (4.0 * cnn->N);
-    return LBM_OK;
+    return check_timeout(cnn);
 }
 
 lbm_status lbm_cnn_adam_step(lbm_cnn *cnn, float lr, float grad_scale)

@@ -490,7 +490,8 @@ class Network:
         return out
 
     def set_conv_kernel(self, kernel: int):
-        """0: shared-memory tiles (default); 1: fragments straight from global memory."""
+        """0: tcgen05 with TMEM accumulators; 1: mma.sync from shared-memory tiles (default);
+        2: mma.sync with fragments straight from global memory."""
         _check(load().lbm_cnn_set_conv_kernel(self._cnn, int(kernel)))
 
     def forward(self, x, y):
