@@ -47,9 +47,10 @@ def _coarse_context(col, stream):
 IDENTITY = solver.LbmClosureNorm.make([0.0] * 5, [1.0] * 5, [1.0] * 4)
 
 
-def generate(collisions, snapshots=20, stride=48, batch=25, norm=IDENTITY, stream=None, log=None):
+def generate(collisions, snapshots=20, stride=48, batch=25, norm=IDENTITY, stream=None, log=None, every=1):
     """Training pairs (X [S, 5, Nc], T [S, 4, Nc], device tensors) from len(collisions) fine runs,
-    `snapshots` pairs each, one every `stride` fine steps."""
+    `snapshots` pairs each, one every `stride` fine steps; the coarse context takes `every` steps
+    between restriction and comparison (the fine runs 2 * every)."""
     import torch
     stream = stream or torch.cuda.current_stream()
     L = collisions[0].L
@@ -70,12 +71,12 @@ def generate(collisions, snapshots=20, stride=48, batch=25, norm=IDENTITY, strea
             coarse = [_coarse_context(c, stream) for c in cols]
             judge = _coarse_context(cols[0], stream)
             for _ in range(snapshots):
-                ens.step(stride - 2)
+                ens.step(stride - 2 * every)
                 for k in range(len(cols)):
                     ens.restrict_state(k, coarse[k])
-                ens.step(2)
+                ens.step(2 * every)
                 for k in range(len(cols)):
-                    coarse[k].step(1)
+                    coarse[k].step(every)
                     ens.restrict_state(k, judge)
                     judge.read_fields(phi=ref[:Nc], u=ref[Nc:])
                     solver.closure_features(coarse[k], norm, X[idx].reshape(-1))
@@ -91,10 +92,10 @@ def generate(collisions, snapshots=20, stride=48, batch=25, norm=IDENTITY, strea
     return X[:idx], T[:idx]
 
 
-def estimate_norm(collisions, snapshots=6, stride=48, stream=None):
+def estimate_norm(collisions, snapshots=6, stride=48, stream=None, every=1):
     """Input shifts and scales (mean and standard deviation of phi, u, p) and output scales
     (standard deviation of the raw corrections) from a small pilot set, on the host."""
-    X, T = generate(collisions, snapshots=snapshots, stride=stride, batch=len(collisions), stream=stream)
+    X, T = generate(collisions, snapshots=snapshots, stride=stride, batch=len(collisions), stream=stream, every=every)
     x = X.permute(1, 0, 2).reshape(5, -1).double().cpu().numpy()
     t = T.permute(1, 0, 2).reshape(4, -1).double().cpu().numpy()
     shift = x.mean(axis=1)
@@ -130,9 +131,10 @@ def train(net, X, T, epochs=4, lr=1e-3, batch=4, seed=0, log=None):
     return history
 
 
-def evaluate(net, norm, col, coarse_steps=240, every=24, stream=None):
+def evaluate(net, norm, col, coarse_steps=240, every=24, stream=None, apply_every=1):
     """RMS errors of phi and u of the plain and the corrected coarse runs against the restricted
-    fine run of collision `col`, and device times per coarse step of the three runs."""
+    fine run of collision `col` (checked every `every` coarse steps), and device times per coarse
+    step of the three runs.  The correction is applied after every `apply_every` coarse steps."""
     import torch
     stream = stream or torch.cuda.current_stream()
     n = (col.L // 2) ** 3
@@ -149,7 +151,8 @@ def evaluate(net, norm, col, coarse_steps=240, every=24, stream=None):
             fine.step(2)
             plain.step(1)
             corr.step(1)
-            solver.closure_apply(corr, net, norm)
+            if k % apply_every == 0:
+                solver.closure_apply(corr, net, norm)
             if k % every == 0:
                 fine.restrict_state(0, judge)
                 jp, ju, _ = judge.read_fields()
@@ -184,8 +187,10 @@ def evaluate(net, norm, col, coarse_steps=240, every=24, stream=None):
         out["ms_per_coarse_step"] = {
             "fine_2_steps": timed(lambda: ref_fine.step(2)),
             "coarse": timed(lambda: plain.step(1)),
-            "coarse_with_closure": timed(lambda: (corr.step(1), solver.closure_apply(corr, net, norm))),
+            "coarse_with_closure": timed(lambda: (corr.step(apply_every), solver.closure_apply(corr, net, norm)))
+            / apply_every,
         }
+        out["apply_every"] = apply_every
         for s in (plain, corr, judge, ref_fine):
             s.close()
         fine.close()
@@ -209,6 +214,7 @@ def main(argv=None):
     ap.add_argument("--weights", default=None, help="npz file for the trained parameters and normalisation")
     ap.add_argument("--load", default=None, help="evaluate parameters from an npz written by --weights (no training)")
     ap.add_argument("--phi-only", action="store_true", help="apply only the phi correction when evaluating")
+    ap.add_argument("--every", type=int, default=1, help="coarse steps per correction")
     ap.add_argument("--u-relax", type=float, default=0.0,
                     help="factor on the applied velocity correction (0: the phi correction alone)")
     a = ap.parse_args(argv)
@@ -224,7 +230,7 @@ def main(argv=None):
         norm = solver.LbmClosureNorm.make(z["in_shift"], z["in_scale"], out_scale)
         net = solver.Network(a.L // 2, a.L // 2, a.L // 2, seed=a.seed)
         net.set_params(z["params"])
-        evals = [evaluate(net, norm, c, coarse_steps=a.eval_steps) for c in eval_cols]
+        evals = [evaluate(net, norm, c, coarse_steps=a.eval_steps, apply_every=a.every) for c in eval_cols]
         print(json.dumps({"eval": evals}))
         if a.out:
             with open(a.out, "w") as fh:
@@ -232,9 +238,10 @@ def main(argv=None):
         net.close()
         return 0
     t0 = time.perf_counter()
-    norm = estimate_norm(train_cols[:4], stride=a.stride)
+    norm = estimate_norm(train_cols[:4], stride=a.stride, every=a.every)
     log(f"norm: in_shift {list(norm.in_shift)} in_scale {list(norm.in_scale)} out_scale {list(norm.out_scale)}")
-    X, T = generate(train_cols, snapshots=a.snapshots, stride=a.stride, batch=a.batch_traj, norm=norm, log=log)
+    X, T = generate(train_cols, snapshots=a.snapshots, stride=a.stride, batch=a.batch_traj, norm=norm, log=log,
+                    every=a.every)
     t_data = time.perf_counter() - t0
     net = solver.Network(a.L // 2, a.L // 2, a.L // 2, seed=a.seed)
     t1 = time.perf_counter()
@@ -243,8 +250,8 @@ def main(argv=None):
     del X, T
     applied = solver.LbmClosureNorm.make(norm.in_shift, norm.in_scale,
                                          [norm.out_scale[0]] + [a.u_relax * v for v in list(norm.out_scale)[1:]])
-    evals = [evaluate(net, applied, c, coarse_steps=a.eval_steps) for c in eval_cols]
-    res = {"trajectories": a.traj, "pairs": a.traj * a.snapshots, "epochs": a.epochs, "loss": hist,
+    evals = [evaluate(net, applied, c, coarse_steps=a.eval_steps, apply_every=a.every) for c in eval_cols]
+    res = {"trajectories": a.traj, "pairs": a.traj * a.snapshots, "epochs": a.epochs, "every": a.every, "loss": hist,
            "seconds": {"data": t_data, "train": t_train}, "eval": evals,
            "norm": {"in_shift": list(norm.in_shift), "in_scale": list(norm.in_scale),
                     "out_scale": list(norm.out_scale)}}
