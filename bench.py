@@ -56,10 +56,12 @@ METRIC = "MLUPS & % HBM peak: coupled LBM+Allen-Cahn step, FP32 vs BF16 store"
 # sources that define each step kernel's device code (the profile of a kernel is reused only while
 # these files are unchanged)
 KERNEL_SOURCES = {
-    "lbm_kernel": ["paper_2501_00846_b300/csrc/step_unfused.cu", "paper_2501_00846_b300/csrc/tslb_device.cuh"],
+    "lbm_kernel": ["paper_2501_00846_b300/csrc/step_unfused.cu", "paper_2501_00846_b300/csrc/lbm_node.cuh",
+                   "paper_2501_00846_b300/csrc/tslb_device.cuh"],
     "fused2_kernel": ["paper_2501_00846_b300/csrc/step_fused2.cu", "paper_2501_00846_b300/csrc/tslb_device.cuh"],
     "lbm16_kernel": ["paper_2501_00846_b300/csrc/step_lbm16.cu", "paper_2501_00846_b300/csrc/tslb_device.cuh"],
-    "ac_div_kernel": ["paper_2501_00846_b300/csrc/step_split.cu", "paper_2501_00846_b300/csrc/tslb_device.cuh"],
+    "ac_div_kernel": ["paper_2501_00846_b300/csrc/step_split.cu", "paper_2501_00846_b300/csrc/ac_div.cuh",
+                      "paper_2501_00846_b300/csrc/tslb_device.cuh"],
 }
 KERNEL_NAMES = {0: "lbm_kernel", 1: "lbm_kernel", 2: "fused2_kernel"}
 
