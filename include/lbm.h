@@ -52,8 +52,25 @@ typedef enum {
 typedef enum {
     LBM_FP32 = 0,            /* populations stored as FP32 */
     LBM_BF16 = 1,            /* populations stored as BF16 deviations (see below) */
-    LBM_FP16 = 2             /* populations stored as FP16 deviations (see below) */
+    LBM_FP16 = 2,            /* populations stored as FP16 deviations (see below) */
+    LBM_MOM = 3              /* moment-only storage: 13 FP32 moments per node (see below) */
 } lbm_storage;
+
+/*
+ * Moment-only storage (LBM_MOM).  The paper's collision forms every post-collision population
+ * from macroscopic fields alone (Section "Thread-safe lattice Boltzmann": Eq. LBexp with
+ * Eqs. eqts and noneqts and the forcing), so the populations leaving a node are a fixed
+ * polynomial in c_i of its p*, u, a = F / rho and B = 4.5 (1 - omega) A (A: the regularised
+ * second-order non-equilibrium moment).  This storage keeps those 13 FP32 numbers per node
+ * (u in the velocity arrays, the other 10 as m[q N + node], q = 0 p*, 1..3 a, 4..9 B xx yy zz
+ * xy xz yz) and rebuilds g_i(x - c_i) from the moments of x - c_i when it streams: 104 bytes
+ * per node and step move instead of 248, for more arithmetic.  Path 0 runs a tiled kernel
+ * (populations staged in shared memory), path 1 a one-thread-per-node kernel that rebuilds
+ * every population from global memory (the cross-check; the two agree to FP32 rounding); path 2
+ * is rejected.  lbm_get_state expands the moments to FP32 g; lbm_set_state projects g onto the
+ * moments (p* = sum g, a = 2 (sum g c - u), B from sum g c c), which is exact up to rounding
+ * for any state this library produced and the Hermite projection of any other.
+ */
 
 /*
  * 16-bit population storage (LBM_BF16, LBM_FP16).  The paper stores FP32 populations; this is a
@@ -115,7 +132,7 @@ typedef struct {
 
 /* Create a context: validates *params, allocates every device buffer (two copies of g, phi,
  * ubar: 2 x 31 floats per node with FP32 storage, 2 x (27 halves + 5 floats) with 16-bit
- * storage, plus scratch).  The caller owns *out and releases it
+ * storage, 2 x 14 floats with moment storage, plus scratch).  The caller owns *out and releases it
  * with lbm_destroy.  On error *out = NULL and nothing is leaked. */
 lbm_status lbm_create(const lbm_params *params, lbm_ctx **out);
 
@@ -169,7 +186,8 @@ lbm_status lbm_read_fields(lbm_ctx *ctx, float *phi, float *u, float *p, int on_
  * by lbm_get_state and restored by lbm_set_state continues bit-identically with FP32 storage.
  * With 16-bit storage g is exchanged as FP32 g_i = w_i (h_i + p*): lbm_get_state expands it and
  * lbm_set_state rounds it back (a round trip is not guaranteed to reproduce the stored h bit
- * for bit).  lbm_set_state sets the step counter to `step`.  Both synchronise the stream. */
+ * for bit).  With moment storage g is the expansion of the moments, and lbm_set_state projects
+ * it back (exact up to rounding for a state of this library).  lbm_set_state sets the step counter to `step`.  Both synchronise the stream. */
 lbm_status lbm_get_state(lbm_ctx *ctx, float *g, float *phi, float *u, int on_device);
 lbm_status lbm_set_state(lbm_ctx *ctx, const float *g, const float *phi, const float *u,
                          long long step, int on_device);
@@ -188,7 +206,7 @@ long long lbm_step_count(const lbm_ctx *ctx);
  *      stencils from global memory; the simplest form, kept as a cross-check)
  *   2  one fused kernel: the Allen–Cahn stencils of a z-marching shared-memory window and the
  *      lattice Boltzmann update of each plane in the same kernel
- * LBM_ERR_ARG for other values, and for path 2 with 16-bit storage. */
+ * LBM_ERR_ARG for other values, and for path 2 with any storage but LBM_FP32. */
 lbm_status lbm_set_path(lbm_ctx *ctx, int path);
 
 /* Work split of the z-marching kernels (paths 0 and 2): the number of z chunks each 32 x 8

@@ -7,7 +7,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 SOURCES = ["lbm_api.cu", "step_split.cu", "step_fused2.cu", "step_unfused.cu", "step_lbm16.cu", "observables.cu",
-           "observables_noalloc.cu", "ensemble.cu", "closure.cu"]
+           "observables_noalloc.cu", "ensemble.cu", "closure.cu", "step_mom.cu"]
 LIB = os.path.join(HERE, "libtslb_b300.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

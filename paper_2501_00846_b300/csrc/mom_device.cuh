@@ -1,0 +1,177 @@
+// Moment-only ("thread-safe") storage of the lattice Boltzmann state.
+//
+// The paper's collision rebuilds each post-collision population from macroscopic fields alone
+// (Section "Thread-safe lattice Boltzmann", Eq. LBexp with the equilibrium Eq. eqts, the
+// regularised non-equilibrium Eq. noneqts and the forcing): the populations leaving a node are a
+// fixed polynomial in c_i of that node's
+//     p*,  u,  a = F / rho,  B = k2 A,   k2 = (1 - omega) / (2 cs^4) = 4.5 (1 - omega),
+// 13 numbers (A symmetric).  Storing those instead of the 27 populations, and letting the node
+// that pulls g_i(x - c_i) rebuild it from the moments of x - c_i, moves 52 bytes per node and
+// step each way instead of 108.
+//
+// Per unit weight, with cu = c.u, ca = c.a, cBc = c^T B c (the same even/odd contraction as
+// collide_node):
+//     g_{+-c} / w = E +- O,
+//     E = K0 + 4.5 cu (cu + ca) + cBc,              K0 = p* - 1.5 u^2 - 1.5 u.a - tr(B) / 3
+//     O = cu (K1 + 4.5 cu^2 + 3 cBc) + c.v,         K1 = 3 - 4.5 u^2 - tr(B),   v = 1.5 a - 2 B u.
+// The moments of these populations give the set back (used to import a population state):
+//     sum g = p*,   sum g c = u + a / 2,   sum g c c = p* I / 3 + (2/9) T,
+//     T = B + 4.5 u u + 4.5 sym(u a),   sym(u a)_{ab} = (u_a a_b + u_b a_a) / 2
+// (fourth-order isotropy of D3Q27: sum w c_a c_b c_c c_d = (d_ab d_cd + d_ac d_bd + d_ad d_bc) / 9).
+//
+// Array layout of a moment state: m[q * N + node], q = 0 p*, 1..3 a, 4..9 B (xx yy zz xy xz yz);
+// u lives in the context's velocity arrays.
+#pragma once
+
+#include "tslb_device.cuh"
+
+namespace tslb {
+
+constexpr int kMomArrays = 10;
+
+struct Mom {
+    float ps, ux, uy, uz, ax, ay, az, bxx, byy, bzz, bxy, bxz, byz;
+};
+
+// Node constants of the population polynomial.
+struct MomPoly {
+    float K0, K1, vx, vy, vz, b2xy, b2xz, b2yz;
+};
+
+__device__ __forceinline__ Mom mom_load(const float *__restrict__ m, const float *__restrict__ u, size_t N, int k)
+{
+    Mom r;
+    r.ps = __ldg(m + k);
+    r.ax = __ldg(m + N + k);
+    r.ay = __ldg(m + 2 * N + k);
+    r.az = __ldg(m + 3 * N + k);
+    r.bxx = __ldg(m + 4 * N + k);
+    r.byy = __ldg(m + 5 * N + k);
+    r.bzz = __ldg(m + 6 * N + k);
+    r.bxy = __ldg(m + 7 * N + k);
+    r.bxz = __ldg(m + 8 * N + k);
+    r.byz = __ldg(m + 9 * N + k);
+    r.ux = __ldg(u + k);
+    r.uy = __ldg(u + N + k);
+    r.uz = __ldg(u + 2 * N + k);
+    return r;
+}
+
+// The moment set left by a collision: B = 4.5 (1 - omega) A.
+__device__ __forceinline__ Mom mom_from_collided(const Collided &c)
+{
+    const float k2 = 4.5f * (1.0f - c.omega);
+    Mom m;
+    m.ps = c.ps;
+    m.ux = c.ux, m.uy = c.uy, m.uz = c.uz;
+    m.ax = c.ax, m.ay = c.ay, m.az = c.az;
+    m.bxx = k2 * c.Axx, m.byy = k2 * c.Ayy, m.bzz = k2 * c.Azz;
+    m.bxy = k2 * c.Axy, m.bxz = k2 * c.Axz, m.byz = k2 * c.Ayz;
+    return m;
+}
+
+__device__ __forceinline__ void mom_store(const Mom &r, float *__restrict__ m, float *__restrict__ u, size_t N, int k)
+{
+    m[k] = r.ps;
+    m[N + k] = r.ax;
+    m[2 * N + k] = r.ay;
+    m[3 * N + k] = r.az;
+    m[4 * N + k] = r.bxx;
+    m[5 * N + k] = r.byy;
+    m[6 * N + k] = r.bzz;
+    m[7 * N + k] = r.bxy;
+    m[8 * N + k] = r.bxz;
+    m[9 * N + k] = r.byz;
+    u[k] = r.ux;
+    u[N + k] = r.uy;
+    u[2 * N + k] = r.uz;
+}
+
+// The polynomial is evaluated with explicit round-to-nearest intrinsics (no contraction or
+// reordering left to the compiler), so every kernel and every staging variant that evaluates a
+// population gets the same bits, and a mirrored moment set gives exactly the negated odd terms.
+__device__ __forceinline__ MomPoly mom_poly(const Mom &m)
+{
+    MomPoly q;
+    const float u2 = __fmaf_rn(m.uz, m.uz, __fmaf_rn(m.uy, m.uy, __fmul_rn(m.ux, m.ux)));
+    const float ua = __fmaf_rn(m.uz, m.az, __fmaf_rn(m.uy, m.ay, __fmul_rn(m.ux, m.ax)));
+    const float trb = __fadd_rn(__fadd_rn(m.bxx, m.byy), m.bzz);
+    q.K0 = __fmaf_rn(-1.0f / 3.0f, trb, __fmaf_rn(-1.5f, ua, __fmaf_rn(-1.5f, u2, m.ps)));
+    q.K1 = __fmaf_rn(-4.5f, u2, __fsub_rn(3.0f, trb));
+    const float bux = __fmaf_rn(m.bxz, m.uz, __fmaf_rn(m.bxy, m.uy, __fmul_rn(m.bxx, m.ux)));
+    const float buy = __fmaf_rn(m.byz, m.uz, __fmaf_rn(m.byy, m.uy, __fmul_rn(m.bxy, m.ux)));
+    const float buz = __fmaf_rn(m.bzz, m.uz, __fmaf_rn(m.byz, m.uy, __fmul_rn(m.bxz, m.ux)));
+    q.vx = __fmaf_rn(-2.0f, bux, __fmul_rn(1.5f, m.ax));
+    q.vy = __fmaf_rn(-2.0f, buy, __fmul_rn(1.5f, m.ay));
+    q.vz = __fmaf_rn(-2.0f, buz, __fmul_rn(1.5f, m.az));
+    q.b2xy = __fmul_rn(2.0f, m.bxy);
+    q.b2xz = __fmul_rn(2.0f, m.bxz);
+    q.b2yz = __fmul_rn(2.0f, m.byz);
+    return q;
+}
+
+// s + c v for a lattice component c in {-1, 0, 1} (c a compile-time constant after unrolling)
+__device__ __forceinline__ float mom_acc(float s, int c, float v)
+{
+    return c > 0 ? __fadd_rn(s, v) : c < 0 ? __fsub_rn(s, v) : s;
+}
+
+// g_i / w_i and g_{26-i} / w_i of the pair i < 13 (i a compile-time constant after unrolling).
+__device__ __forceinline__ void mom_pair(int i, const Mom &m, const MomPoly &q, float &gp, float &gm)
+{
+    const int X = cx(i), Y = cy(i), Z = cz(i);
+    const float cu = mom_acc(mom_acc(mom_acc(0.0f, X, m.ux), Y, m.uy), Z, m.uz);
+    const float ca = mom_acc(mom_acc(mom_acc(0.0f, X, m.ax), Y, m.ay), Z, m.az);
+    const float cv = mom_acc(mom_acc(mom_acc(0.0f, X, q.vx), Y, q.vy), Z, q.vz);
+    float cbc = mom_acc(mom_acc(mom_acc(0.0f, X * X, m.bxx), Y * Y, m.byy), Z * Z, m.bzz);
+    cbc = mom_acc(mom_acc(mom_acc(cbc, X * Y, q.b2xy), X * Z, q.b2xz), Y * Z, q.b2yz);
+    const float hcu = __fmul_rn(4.5f, cu);
+    const float E = __fadd_rn(__fmaf_rn(hcu, __fadd_rn(cu, ca), q.K0), cbc);
+    const float O = __fmaf_rn(cu, __fmaf_rn(3.0f, cbc, __fmaf_rn(hcu, cu, q.K1)), cv);
+    gp = __fadd_rn(E, O);
+    gm = __fsub_rn(E, O);
+}
+
+// g_i / w_i of one direction (i a compile-time constant after unrolling)
+__device__ __forceinline__ float mom_one(int i, const Mom &m, const MomPoly &q)
+{
+    if (i == 13) return q.K0;
+    float gp, gm;
+    mom_pair(i < 13 ? i : 26 - i, m, q, gp, gm);
+    return i < 13 ? gp : gm;
+}
+
+// Mirror image x -> -x of a moment set (the components odd in x change sign): the population
+// of direction (cx, cy, cz) of the mirrored set is that of (-cx, cy, cz) of the original.
+__device__ __forceinline__ Mom mom_mirror_x(const Mom &m)
+{
+    Mom r = m;
+    r.ux = -m.ux;
+    r.ax = -m.ax;
+    r.bxy = -m.bxy;
+    r.bxz = -m.bxz;
+    return r;
+}
+
+// The lattice Boltzmann update of one node once its 27 streamed populations f_i and the phi^{n+1}
+// stencil values psi_i = phi^{n+1}(x + c_i) are in registers: the collision's moments, the new
+// moment set, and the Allen–Cahn flux of the new state (as lbm_node).
+__device__ __forceinline__ void mom_collide_store(const float (&f)[27], const float (&psi)[27], float ubx, float uby,
+                                                  float ubz, const Phys &P, float *__restrict__ m_out,
+                                                  float *__restrict__ u_out, float *__restrict__ w_out, size_t N,
+                                                  int k)
+{
+    float gx, gy, gz, lap;
+    grad_lap27(psi, gx, gy, gz, lap);
+    const Collided c = collide_moments(f, psi[13], gx, gy, gz, lap, ubx, uby, ubz, P);
+    mom_store(mom_from_collided(c), m_out, u_out, N, k);
+    if (w_out) {
+        float wx, wy, wz;
+        ac_flux(psi[13], gx, gy, gz, c.ux, c.uy, c.uz, P, wx, wy, wz);
+        w_out[k] = wx;
+        w_out[N + k] = wy;
+        w_out[2 * N + k] = wz;
+    }
+}
+
+}  // namespace tslb

@@ -51,7 +51,9 @@ __global__ void __launch_bounds__(kThreads) obs_partial_kernel(Grid G, double rh
         const int y = rem / G.nx;
         const int x = rem - y * G.nx;
         double ps = 0.0;
-        if (pst) {   // 16-bit formats: p* = P + sum_i w_i h_i
+        if (storage == LBM_MOM) {   // moment storage: p* is the first moment array
+            ps = ((const float *)gv)[k];
+        } else if (pst) {   // 16-bit formats: p* = P + sum_i w_i h_i
             float s = pst[k];
 #pragma unroll
             for (int i = 0; i < 27; ++i) s = fmaf(wgt(i), load_h16(gv, storage, i * N + k), s);

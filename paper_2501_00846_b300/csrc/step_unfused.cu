@@ -198,7 +198,9 @@ __global__ void __launch_bounds__(128) pressure_kernel(Grid G, Phys P, const flo
     const size_t N = (size_t)G.N;
     const int k = (z * G.ny + y) * G.nx + x;
     float s = 0.0f;
-    if (pst) {   // 16-bit formats: p* = P + sum_i w_i h_i
+    if (storage == LBM_MOM) {   // moment storage: p* is the first moment array
+        s = g[k];
+    } else if (pst) {   // 16-bit formats: p* = P + sum_i w_i h_i
         s = pst[k];
 #pragma unroll
         for (int i = 0; i < 27; ++i) s = fmaf(wgt(i), load_h16(g, storage, i * N + k), s);
@@ -242,6 +244,8 @@ cudaError_t launch_lbm(const Grid &G, const Phys &P, int storage, const void *g_
         lbm_kernel<StoreF16><<<grid, 128, 0, s>>>(G, P, (const __half *)g_in, p_in, phi_new, u_in, (__half *)g_out,
                                                   p_out, u_out, w_out);
         break;
+    case LBM_MOM:
+        return launch_mom_plain(G, P, (const float *)g_in, u_in, phi_new, (float *)g_out, u_out, w_out, s);
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();

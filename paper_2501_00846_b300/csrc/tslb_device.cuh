@@ -102,11 +102,20 @@ __device__ __forceinline__ void grad_lap27(const float (&psi)[27], float &gx, fl
 // h_i = (g_i - f^eq_i(p*, u)) / w_i = ((1 - omega) f^neq_i + S_i / 2) / w_i: the same E and O with
 // their equilibrium terms dropped (K0 -> -1.5 u.a - 1.5 (1-omega) trA, K1 -> -k2 trA, no 4.5 cu^2),
 // so the small deviation is formed without cancellation.  ps_out receives p*.
-template <bool NEQ = false>
-__device__ __forceinline__ void collide_node(const float (&f)[27], float phi, float gpx, float gpy, float gpz,
-                                             float lap, float ubx, float uby, float ubz, const Phys &P,
-                                             float (&g)[27], float &ux, float &uy, float &uz, float *ps_out = nullptr)
+// The macroscopic part of the collision (everything before the populations are formed), shared
+// by collide_node and the moment-storage kernels: p*, u, the acceleration a = F / rho, the
+// pre-regularisation second moment A and the relaxation factor omega of the node.
+struct Collided {
+    float ps, ux, uy, uz, ax, ay, az;
+    float Axx, Ayy, Azz, Axy, Axz, Ayz;
+    float omega;
+};
+
+__device__ __forceinline__ Collided collide_moments(const float (&f)[27], float phi, float gpx, float gpy,
+                                                    float gpz, float lap, float ubx, float uby, float ubz,
+                                                    const Phys &P)
 {
+    Collided c;
     // moments over opposite pairs
     float ps = f[13];
     float jx = 0.f, jy = 0.f, jz = 0.f;
@@ -146,15 +155,32 @@ __device__ __forceinline__ void collide_node(const float (&f)[27], float phi, fl
     const float ax = Fx * irho, ay = Fy * irho, az = Fz * irho;
 
     // velocity (Eq. moments1) and pre-regularisation (closed form of Eq. hermite_neq2)
-    ux = fmaf(0.5f, ax, jx);
-    uy = fmaf(0.5f, ay, jy);
-    uz = fmaf(0.5f, az, jz);
-    const float Axx = pxx - pc - ux * ux + ux * ax;
-    const float Ayy = pyy - pc - uy * uy + uy * ay;
-    const float Azz = pzz - pc - uz * uz + uz * az;
-    const float Axy = pxy - ux * uy + 0.5f * (ux * ay + ax * uy);
-    const float Axz = pxz - ux * uz + 0.5f * (ux * az + ax * uz);
-    const float Ayz = pyz - uy * uz + 0.5f * (uy * az + ay * uz);
+    const float ux = fmaf(0.5f, ax, jx);
+    const float uy = fmaf(0.5f, ay, jy);
+    const float uz = fmaf(0.5f, az, jz);
+    c.ps = ps;
+    c.ux = ux, c.uy = uy, c.uz = uz;
+    c.ax = ax, c.ay = ay, c.az = az;
+    c.Axx = pxx - pc - ux * ux + ux * ax;
+    c.Ayy = pyy - pc - uy * uy + uy * ay;
+    c.Azz = pzz - pc - uz * uz + uz * az;
+    c.Axy = pxy - ux * uy + 0.5f * (ux * ay + ax * uy);
+    c.Axz = pxz - ux * uz + 0.5f * (ux * az + ax * uz);
+    c.Ayz = pyz - uy * uz + 0.5f * (uy * az + ay * uz);
+    c.omega = omega;
+    return c;
+}
+
+template <bool NEQ = false>
+__device__ __forceinline__ void collide_node(const float (&f)[27], float phi, float gpx, float gpy, float gpz,
+                                             float lap, float ubx, float uby, float ubz, const Phys &P,
+                                             float (&g)[27], float &ux, float &uy, float &uz, float *ps_out = nullptr)
+{
+    const Collided c = collide_moments(f, phi, gpx, gpy, gpz, lap, ubx, uby, ubz, P);
+    const float ps = c.ps, omega = c.omega;
+    const float ax = c.ax, ay = c.ay, az = c.az;
+    const float Axx = c.Axx, Ayy = c.Ayy, Azz = c.Azz, Axy = c.Axy, Axz = c.Axz, Ayz = c.Ayz;
+    ux = c.ux, uy = c.uy, uz = c.uz;
 
     // collision constants
     const float om1 = 1.0f - omega;

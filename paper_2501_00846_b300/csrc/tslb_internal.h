@@ -4,12 +4,13 @@
 #include <cuda_runtime.h>
 
 #include "lbm.h"
+#include "mom_device.cuh"
 #include "tslb_device.cuh"
 
 namespace tslb {
 
 struct StepArgs {
-    const float *g_in;       // populations (FP32 g, or 16-bit h for storage 1 / 2)
+    const float *g_in;       // populations (FP32 g, 16-bit h for storage 1 / 2, moments for 3)
     float *g_out;
     const float *phi_in;
     float *phi_out;
@@ -17,7 +18,7 @@ struct StepArgs {
     float *u_out;
     float *flux;           // 3N Allen–Cahn flux W: read (W^n) and rewritten (W^{n+1}) by the two-kernel
                            // step; scratch of the unfused path; unused by the fused path
-    int storage = 0;       // 0 FP32, 1 BF16, 2 FP16 (16-bit formats: two-kernel path only)
+    int storage = 0;       // 0 FP32, 1 BF16, 2 FP16, 3 moments (paths 0 and 1 only for 1..3)
     const float *p_in = nullptr;   // stored p* of the 16-bit formats
     float *p_out = nullptr;
 };
@@ -33,7 +34,8 @@ cudaError_t launch_step_fused2(const Grid &G, const Phys &P, const StepArgs &a, 
 // which also writes W^{n+1} = W(phi^{n+1}, u^{n+1}) into w_out when w_out is not null.
 cudaError_t launch_ac_div(const Grid &G, const Phys &P, const float *phi_in, const float *w, float *phi_out,
                           int zchunks, cudaStream_t s);
-// storage: 0 FP32 g; 1 BF16, 2 FP16 h (see the storage formats) with P in p_in / p_out.
+// storage: 0 FP32 g; 1 BF16, 2 FP16 h (see the storage formats) with P in p_in / p_out; 3 the
+// moment arrays (one thread per node, lbm_mom_plain_kernel).
 cudaError_t launch_lbm(const Grid &G, const Phys &P, int storage, const void *g_in, const float *p_in,
                        const float *phi_new, const float *u_in, void *g_out, float *p_out, float *u_out,
                        float *w_out, cudaStream_t s);
@@ -58,10 +60,24 @@ cudaError_t launch_compress16(const Grid &G, int storage, const float *g, const 
                               void *h, float *pst, float *corr, cudaStream_t s);
 cudaError_t launch_finish16(const Grid &G, const float *corr, float *pst, cudaStream_t s);
 
+// Moment storage (mom_device.cuh): the tiled step kernel (zchunks as for the marching kernels),
+// the one-thread-per-node kernel, the equilibrium start (p* = pstar or 0, a = B = 0), the
+// expansion to FP32 g (directions [i0, i0+ni) at g[(i-i0)*N + node]), and the import of FP32 g:
+// acc += population moments of directions [i0, i0+ni), then (p*, a, B) from the sums and u.
+cudaError_t launch_mom(const Grid &G, const Phys &P, const float *m_in, const float *u_in, const float *phi_new,
+                       float *m_out, float *u_out, float *w_out, int zchunks, cudaStream_t s);
+cudaError_t launch_mom_plain(const Grid &G, const Phys &P, const float *m_in, const float *u_in, const float *phi_new,
+                             float *m_out, float *u_out, float *w_out, cudaStream_t s);
+cudaError_t launch_mom_init(const Grid &G, const float *pstar, float *m, cudaStream_t s);
+cudaError_t launch_mom_expand(const Grid &G, const float *m, const float *u, int i0, int ni, float *g, cudaStream_t s);
+cudaError_t launch_mom_project(const Grid &G, const float *g, int i0, int ni, float *acc, cudaStream_t s);
+cudaError_t launch_mom_finish(const Grid &G, const float *u, float *m, cudaStream_t s);
+
 // g = f^eq(p*, u); pstar may be nullptr (p* = 0).
 cudaError_t launch_init(const Grid &G, const float *pstar, const float *u, float *g, cudaStream_t s);
 
-// p = p* rho cs^2 with p* = sum_i g_i (FP32, pst null) or P + sum_i w_i h_i (16-bit formats).
+// p = p* rho cs^2 with p* = sum_i g_i (FP32, pst null), P + sum_i w_i h_i (16-bit formats) or the
+// stored p* (moment storage: g holds the moment arrays, p* first).
 cudaError_t launch_pressure(const Grid &G, const Phys &P, int storage, const void *g, const float *pst,
                             const float *phi, float *p, cudaStream_t s);
 
@@ -70,7 +86,8 @@ constexpr int kObsFields = 32;
 int observables_blocks(const Grid &G);
 // rho_l, rho_g in FP64 so the mass sum uses the exact parameter values.
 // p* is summed from the 27 FP32 population arrays g, or (storage 1 / 2, pst not null) is
-// P + sum_i w_i h_i of a 16-bit format whose h arrays g points to.
+// P + sum_i w_i h_i of a 16-bit format whose h arrays g points to, or (storage 3) is the first
+// of the moment arrays g points to.
 cudaError_t launch_observables(const Grid &G, double rho_l, double rho_g, const void *g, const float *phi,
                                const float *u, double *partials, int nblocks, double *result, cudaStream_t s,
                                int storage = 0, const float *pst = nullptr);

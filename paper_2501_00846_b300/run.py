@@ -17,7 +17,7 @@ import numpy as np
 
 from . import inputs, solver
 
-STORAGE = {"fp32": solver.LBM_FP32, "bf16": solver.LBM_BF16, "fp16": solver.LBM_FP16}
+STORAGE = {"fp32": solver.LBM_FP32, "bf16": solver.LBM_BF16, "fp16": solver.LBM_FP16, "mom": solver.LBM_MOM}
 
 
 def workload(name: str):

@@ -1,0 +1,298 @@
+"""Moment-only storage (LBM_MOM) against the FP64 oracle, the FP32 population form, and itself.
+
+The moment form keeps (p*, u, a, B) per node in FP32 and rebuilds every streamed population from
+them with FP32 arithmetic; it computes the same step as the FP32 population form up to rounding,
+so it is held to the FP32 bars: max|d phi| <= 1e-5, relative u and p <= 1e-4 after 100 steps,
+integral observables within 0.5% on long runs.  The tiled kernel (path 0) gives identical bits
+for every z split (each chunk rebuilds its halo planes' populations with the same arithmetic as
+their owners).  It and the one-node-per-thread kernel (path 1) rebuild identical populations, but
+the compiler may contract the collision's FP32 products differently in the two kernels, so they
+agree to FP32 rounding, not bit for bit.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2501_00846_b300 import inputs, solver
+
+pytestmark = pytest.mark.gpu
+
+MOM = solver.LBM_MOM
+TOL = (1e-5, 1e-4, 1e-4)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    torch.cuda.set_device(0)
+    solver.load()
+
+
+def _f32(a):
+    return np.ascontiguousarray(a, dtype=np.float32)
+
+
+def _pstar0(wl):
+    ps = wl.pstar_init()
+    return None if ps is None else _f32(ps)
+
+
+def _run(wl, nsteps, storage=MOM, path=0, split=0):
+    with solver.Solver(storage=storage, **wl.params()) as s:
+        s.set_path(path)
+        s.set_split(split)
+        s.init_fields(_f32(wl.phi0()), _f32(wl.u0()), _pstar0(wl))
+        s.step(nsteps)
+        phi, u, p = s.read_fields()
+        g, _, _ = s.get_state()
+        obs = s.observables()
+    return phi, u, p, g, obs
+
+
+def _oracle(wl, nsteps):
+    P = oracle.Params(**wl.params())
+    ps = _pstar0(wl)
+    st = oracle.run(P, oracle.init(P, _f32(wl.phi0()).astype(np.float64), _f32(wl.u0()).astype(np.float64),
+                                   None if ps is None else ps.astype(np.float64)), nsteps)
+    return P, st
+
+
+def _check(out, P, ref, label, factor=1.0):
+    phi, u, p = out[:3]
+    pref = oracle.pressure(P, ref)
+    dphi = float(np.abs(phi - ref.phi).max())
+    du = float(np.abs(u - ref.u).max() / np.abs(ref.u).max())
+    dp = float(np.abs(p - pref).max() / np.abs(pref).max())
+    print(f"{label}: max|dphi| {dphi:.3e} rel du {du:.3e} rel dp {dp:.3e}")
+    tphi, tu, tp = (factor * t for t in TOL)
+    assert dphi <= tphi and du <= tu and dp <= tp, (label, dphi, du, dp)
+
+
+def _same(a, b):
+    for x, y in zip(a[:4], b[:4]):
+        assert np.array_equal(x, y)
+
+
+@pytest.fixture(scope="module")
+def droplet48():
+    wl = inputs.static_droplet(L=48, radius=12.0, noise=0.01, seed=1234)
+    return (wl,) + _oracle(wl, 100)
+
+
+PATHS = [0, 1]
+PATH_IDS = ["tiled", "plain"]
+
+
+@pytest.mark.parametrize("path", PATHS, ids=PATH_IDS)
+def test_droplet48_100_steps(droplet48, path):
+    wl, P, ref = droplet48
+    _check(_run(wl, 100, path=path), P, ref, f"droplet48 path={path}")
+
+
+@pytest.mark.parametrize("path", PATHS, ids=PATH_IDS)
+def test_ragged_walled_bubble_ratio1000(path):
+    wl = inputs.rising_bubble(nx=37, ny=21, nz=19, R=5.0, zc=8.0, sqrt_gR=0.04, mobility=0.1)
+    wl.noise, wl.seed = 0.005, 99
+    P, ref = _oracle(wl, 60)
+    _check(_run(wl, 60, path=path), P, ref, f"ragged walled bubble path={path}")
+
+
+@pytest.mark.parametrize("path", PATHS, ids=PATH_IDS)
+def test_ragged_periodic_droplet_across_boundary(path):
+    wl = inputs.static_droplet(L=24, radius=6.0, noise=0.01, seed=5)
+    wl.nx, wl.ny, wl.nz = 45, 29, 27
+    wl.center = (2.0, 27.5, 25.0)
+    P, ref = _oracle(wl, 80)
+    _check(_run(wl, 80, path=path), P, ref, f"ragged periodic droplet path={path}")
+
+
+def test_minimum_boxes():
+    """4^3 periodic and 4 x 5 x 4 walled: every tile is ragged, every halo wraps, and a tile's
+    lanes hold several copies of the same node."""
+    for walled in (False, True):
+        wl = inputs.static_droplet(L=4, radius=1.5, noise=0.01, seed=3)
+        if walled:
+            wl.ny, wl.wall_z, wl.gravity = 5, 1, (0.0, 0.0, -1e-5)
+        P, ref = _oracle(wl, 10)
+        for path in PATHS:
+            _check(_run(wl, 10, path=path), P, ref, f"minimum box walled={walled} path={path}", 4.0)
+
+
+def test_tiled_and_plain_kernels_agree():
+    """Measured after 20 steps: max|d phi| ~ 2e-7, relative du and dp ~ 5e-7; a halo or
+    bounce-back error would show at 1e-3 or more."""
+    walled = inputs.rising_bubble(nx=37, ny=21, nz=19, R=5.0, zc=8.0, sqrt_gR=0.04, mobility=0.1)
+    walled.noise, walled.seed = 0.005, 99
+    periodic = inputs.static_droplet(L=24, radius=6.0, noise=0.01, seed=5)
+    periodic.nx, periodic.ny, periodic.nz = 45, 29, 27
+    for wl in (walled, periodic):
+        a, b = _run(wl, 20, path=0), _run(wl, 20, path=1)
+        dphi = np.abs(a[0] - b[0]).max()
+        du = np.abs(a[1] - b[1]).max() / np.abs(b[1]).max()
+        dp = np.abs(a[2] - b[2]).max() / np.abs(b[2]).max()
+        print(f"tiled vs plain: {dphi:.2e} {du:.2e} {dp:.2e}")
+        assert dphi <= 2e-6 and du <= 5e-6 and dp <= 5e-6
+
+
+def test_z_split_does_not_change_the_result():
+    """Each z chunk stages the plane below and above it from the same moments its neighbour
+    chunk reads, so any split gives identical bits (1 chunk, uneven chunks, one plane each)."""
+    wl = inputs.rising_bubble(nx=37, ny=21, nz=19, R=5.0, zc=8.0, sqrt_gR=0.04, mobility=0.1)
+    wl.noise, wl.seed = 0.005, 99
+    ref = _run(wl, 12, split=1)
+    for split in (2, 3, 7, 19):
+        _same(ref, _run(wl, 12, split=split))
+    pwl = inputs.static_droplet(L=24, radius=6.0, noise=0.01, seed=5)
+    pref = _run(pwl, 12, split=1)
+    for split in (5, 24):
+        _same(pref, _run(pwl, 12, split=split))
+
+
+def test_agrees_with_the_fp32_population_form():
+    wl = inputs.static_droplet(L=32, radius=8.0, noise=0.01, seed=21)
+    a, b = _run(wl, 200), _run(wl, 200, storage=solver.LBM_FP32)
+    assert np.abs(a[0] - b[0]).max() <= 1e-6
+    assert np.abs(a[1] - b[1]).max() <= 1e-4 * np.abs(b[1]).max()
+    assert np.abs(a[2] - b[2]).max() <= 1e-4 * np.abs(b[2]).max()
+    assert np.abs(a[3] - b[3]).max() <= 1e-5 * np.abs(b[3]).max()
+
+
+def test_pstar_sum_is_conserved_like_the_fp32_form():
+    wl = inputs.static_droplet(L=32, radius=8.0, noise=0.01, seed=7)
+    with solver.Solver(storage=MOM, **wl.params()) as s:
+        s.init_fields(_f32(wl.phi0()), _f32(wl.u0()), _pstar0(wl))
+        o0 = s.observables()
+        s.step(200)
+        o = s.observables()
+        g, _, _ = s.get_state()
+    gsum = float(g.astype(np.float64).sum())
+    assert math.isclose(o["sum_pstar"], gsum, rel_tol=1e-6, abs_tol=1e-6 * np.abs(g).sum())
+    o32 = _run(wl, 200, storage=solver.LBM_FP32)[4]
+    drift_m = abs(o["sum_pstar"] - o0["sum_pstar"])
+    drift32 = abs(o32["sum_pstar"] - o0["sum_pstar"])
+    print(f"sum p* drift over 200 steps: moments {drift_m:.3e}, FP32 {drift32:.3e}")
+    assert drift_m <= 4 * drift32 + 1e-9 * s.n
+
+
+def test_state_round_trip_and_resume():
+    """get_state expands the moments to FP32 g; set_state projects g back.  The projection is
+    exact in exact arithmetic for these populations, so the round trip changes a population by
+    FP32 rounding only, and a resumed run follows the uninterrupted one."""
+    wl = inputs.static_droplet(L=32, radius=8.0, noise=0.01, seed=11)
+    with solver.Solver(storage=MOM, **wl.params()) as s:
+        s.init_fields(_f32(wl.phi0()), _f32(wl.u0()), _pstar0(wl))
+        s.step(10)
+        state = s.get_state()
+        s.set_state(*state, step=10)
+        again = s.get_state()
+        s.step(15)
+        a = s.read_fields()
+        s.set_state(*state, step=10)
+        s.step(15)
+        b = s.read_fields()
+        assert s.step_count == 25
+    change = np.abs(again[0] - state[0]).max()
+    print(f"round trip: max population change {change:.3e}")
+    assert change <= 1e-6 * np.abs(state[0]).max()
+    assert np.array_equal(again[1], state[1]) and np.array_equal(again[2], state[2])
+    assert np.abs(a[0] - b[0]).max() <= 1e-7
+    assert np.abs(a[1] - b[1]).max() <= 1e-5 * np.abs(a[1]).max()
+
+
+def test_fp32_state_imported_into_moment_storage_continues_the_fp32_run():
+    """A post-collision state of the FP32 population form lies in the span the moments describe,
+    so importing it and stepping on tracks the FP32 run to FP32 rounding."""
+    wl = inputs.rising_bubble(nx=37, ny=21, nz=19, R=5.0, zc=8.0, sqrt_gR=0.04, mobility=0.1)
+    wl.noise, wl.seed = 0.005, 99
+    with solver.Solver(storage=solver.LBM_FP32, **wl.params()) as s:
+        s.init_fields(_f32(wl.phi0()), _f32(wl.u0()), _pstar0(wl))
+        s.step(20)
+        state = s.get_state()
+        s.step(30)
+        ref = s.read_fields()
+    with solver.Solver(storage=MOM, **wl.params()) as s:
+        s.set_state(*state, step=20)
+        s.step(30)
+        got = s.read_fields()
+    assert np.abs(got[0] - ref[0]).max() <= 1e-6
+    assert np.abs(got[1] - ref[1]).max() <= 1e-4 * np.abs(ref[1]).max()
+    assert np.abs(got[2] - ref[2]).max() <= 1e-4 * np.abs(ref[2]).max()
+
+
+def test_device_pointer_state_matches_host():
+    import torch
+    wl = inputs.static_droplet(L=20, radius=5.0, noise=0.01, seed=2)
+    with solver.Solver(storage=MOM, **wl.params()) as s:
+        s.init_fields(_f32(wl.phi0()), _f32(wl.u0()), _pstar0(wl))
+        s.step(5)
+        g_host, phi, u = s.get_state()
+        g_dev = torch.empty(27 * s.n, device="cuda")
+        phi_d = torch.from_numpy(phi).cuda().reshape(-1)
+        u_d = torch.from_numpy(u).cuda().reshape(-1)
+        assert solver.load().lbm_get_state(s._ctx, g_dev.data_ptr(), None, None, 1) == 0
+        assert np.array_equal(g_dev.cpu().numpy(), g_host.reshape(-1))
+        s.set_state(g_dev, phi_d, u_d, step=5)
+        from_dev = s.get_state()[0]
+        s.set_state(g_host, phi, u, step=5)
+        from_host = s.get_state()[0]
+    # one FP64 sum over 27 directions vs three partial sums rounded to FP32
+    assert np.abs(from_dev - from_host).max() <= 1e-6 * np.abs(from_host).max()
+
+
+def test_fused_path_rejects_moment_storage():
+    wl = inputs.static_droplet(L=16, radius=4.0)
+    with solver.Solver(storage=MOM, **wl.params()) as s:
+        s.set_path(0)
+        s.set_path(1)
+        with pytest.raises(solver.LbmError) as e:
+            s.set_path(2)
+        assert e.value.status == -1
+
+
+def test_rising_bubble_full_size_two_steps():
+    """The benchmark workload (128 x 128 x 256, ratios 1000 / 100) in the benchmark's launch
+    configuration, two steps against the oracle."""
+    wl = inputs.rising_bubble()
+    P, ref = _oracle(wl, 2)
+    phi, u, p, _, _ = _run(wl, 2)
+    pref = oracle.pressure(P, ref)
+    dphi = float(np.abs(phi - ref.phi).max())
+    dp = float(np.abs(p - pref).max() / np.abs(pref).max())
+    du = float(np.abs(u - ref.u).max())
+    print(f"bubble full size: {dphi:.3e} {du:.3e} {dp:.3e}")
+    assert dphi <= TOL[0] and dp <= TOL[2]
+    assert du <= TOL[1] * 0.04      # velocities ~1e-6 after two steps: scale sqrt(gR) = 0.04
+
+
+def test_long_run_small_rising_bubble_observables():
+    wl = inputs.rising_bubble(nx=24, ny=24, nz=96, R=5.0, zc=14.0, Eo=10.0, Mo=1e-2, rho_ratio=100.0,
+                              mu_ratio=10.0, sqrt_gR=0.04, mobility=0.1)
+    P, ref = _oracle(wl, 800)
+    o, obs = oracle.observables(P, ref), _run(wl, 800)[4]
+    rise_o = o["centroid_gas"][2] - 14.0
+    rise_g = obs["centroid_gas"][2] - 14.0
+    print(f"rise oracle {rise_o:.5f} gpu {rise_g:.5f}")
+    assert abs(rise_g / rise_o - 1) < 5e-3
+    assert abs(obs["vel_gas"][2] / o["vel_gas"][2] - 1) < 5e-3
+    assert abs(obs["mass"] / o["mass"] - 1) < 5e-3
+    assert abs(obs["sum_phi"] / o["sum_phi"] - 1) < 5e-3
+
+
+def test_laplace_law():
+    """Static droplet, 48^3, R = 12: p_in - p_out -> 2 sigma / R_eff, equal to the FP32 form's."""
+    wl = inputs.static_droplet(L=48, radius=12.0)
+    ratios = {}
+    for st in (solver.LBM_FP32, MOM):
+        with solver.Solver(storage=st, **wl.params()) as s:
+            s.init_fields(_f32(wl.phi0()), _f32(wl.u0()), _pstar0(wl))
+            s.step(4000)
+            o = s.observables()
+        reff = (3 * o["sum_phi"] / (4 * math.pi)) ** (1 / 3)
+        ratios[st] = (o["p_liq"] - o["p_gas"]) / (2 * wl.sigma / reff)
+    print(f"Laplace ratio FP32 {ratios[solver.LBM_FP32]:.5f} moments {ratios[MOM]:.5f}")
+    assert abs(ratios[MOM] - 1) < 0.05
+    assert abs(ratios[MOM] - ratios[solver.LBM_FP32]) < 1e-4
