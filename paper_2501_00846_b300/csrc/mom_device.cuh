@@ -153,21 +153,45 @@ __device__ __forceinline__ Mom mom_mirror_x(const Mom &m)
     return r;
 }
 
-// The lattice Boltzmann update of one node once its 27 streamed populations f_i and the phi^{n+1}
-// stencil values psi_i = phi^{n+1}(x + c_i) are in registers: the collision's moments, the new
-// moment set, and the Allen–Cahn flux of the new state (as lbm_node).
-__device__ __forceinline__ void mom_collide_store(const float (&f)[27], const float (&psi)[27], float ubx, float uby,
-                                                  float ubz, const Phys &P, float *__restrict__ m_out,
-                                                  float *__restrict__ u_out, float *__restrict__ w_out, size_t N,
-                                                  int k)
+// Raw moments of streamed populations given per unit weight, f_i = w_i gh_i (the weights folded
+// into the sums instead of multiplying each population).
+__device__ __forceinline__ RawMoments raw_moments_hat(const float (&gh)[27])
 {
-    float gx, gy, gz, lap;
-    grad_lap27(psi, gx, gy, gz, lap);
-    const Collided c = collide_moments(f, psi[13], gx, gy, gz, lap, ubx, uby, ubz, P);
+    RawMoments r;
+    float ps = wgt(13) * gh[13];
+    float jx = 0.f, jy = 0.f, jz = 0.f;
+    float pxx = 0.f, pyy = 0.f, pzz = 0.f, pxy = 0.f, pxz = 0.f, pyz = 0.f;
+#pragma unroll
+    for (int i = 0; i < 13; ++i) {
+        const float w = wgt(i);
+        const float s = gh[i] + gh[26 - i];
+        const float d = gh[i] - gh[26 - i];
+        ps = fmaf(w, s, ps);
+        if (cx(i)) { jx = fmaf(cx(i) * w, d, jx); pxx = fmaf(w, s, pxx); }
+        if (cy(i)) { jy = fmaf(cy(i) * w, d, jy); pyy = fmaf(w, s, pyy); }
+        if (cz(i)) { jz = fmaf(cz(i) * w, d, jz); pzz = fmaf(w, s, pzz); }
+        if (cx(i) * cy(i)) pxy = fmaf((cx(i) * cy(i)) * w, s, pxy);
+        if (cx(i) * cz(i)) pxz = fmaf((cx(i) * cz(i)) * w, s, pxz);
+        if (cy(i) * cz(i)) pyz = fmaf((cy(i) * cz(i)) * w, s, pyz);
+    }
+    r.ps = ps;
+    r.jx = jx, r.jy = jy, r.jz = jz;
+    r.pxx = pxx, r.pyy = pyy, r.pzz = pzz, r.pxy = pxy, r.pxz = pxz, r.pyz = pyz;
+    return r;
+}
+
+// The lattice Boltzmann update of one node once the raw moments of its streamed populations and
+// the gradient and Laplacian of phi^{n+1} are known: the collision, the new moment set, and the
+// Allen–Cahn flux of the new state (as lbm_node).
+__device__ __forceinline__ void mom_finish(const RawMoments &r, float phi, float gx, float gy, float gz, float lap,
+                                           float ubx, float uby, float ubz, const Phys &P, float *__restrict__ m_out,
+                                           float *__restrict__ u_out, float *__restrict__ w_out, size_t N, int k)
+{
+    const Collided c = collide_from_moments(r, phi, gx, gy, gz, lap, ubx, uby, ubz, P);
     mom_store(mom_from_collided(c), m_out, u_out, N, k);
     if (w_out) {
         float wx, wy, wz;
-        ac_flux(psi[13], gx, gy, gz, c.ux, c.uy, c.uz, P, wx, wy, wz);
+        ac_flux(phi, gx, gy, gz, c.ux, c.uy, c.uz, P, wx, wy, wz);
         w_out[k] = wx;
         w_out[N + k] = wy;
         w_out[2 * N + k] = wz;

@@ -31,14 +31,15 @@ constexpr int PS = SX * SY;              // floats of one staged plane (340)
 constexpr int SLOT = 9 * PS;             // one plane's populations of one c_z, rows i % 9
 constexpr int kMomThreads = MX * MY;
 constexpr int kSlots = 7;
-constexpr size_t kMomSmem = (size_t)(kSlots * SLOT + 3 * PS) * sizeof(float);
+constexpr int kHalo = 2 * MX + 2 * SY;   // halo nodes of a staged plane (84)
+constexpr int kPhiRing = 4;              // phi^{n+1} planes z-1, z, z+1 and the one in flight
+constexpr size_t kMomSmem = (size_t)(kSlots * SLOT + 13 * kHalo + kPhiRing * PS) * sizeof(float);
 
-// Which populations a staged node keeps.  ZK: 0 all, +1 / -1 only those with c_z = ZK (the
-// planes below / above a z chunk).  AX, SG: a halo node keeps only c_AX = SG (AX 0 = x, 1 = y,
-// -1: no restriction).
-__host__ __device__ constexpr bool mom_keep(int i, int AX, int SG, int ZK)
+// Which populations a staged node keeps.  ZF: 2 all, -1 / 0 / +1 only those with c_z = ZF.
+// AX, SG: a halo node keeps only c_AX = SG (AX 0 = x, 1 = y; -1: no restriction).
+__host__ __device__ constexpr bool mom_keep(int i, int AX, int SG, int ZF)
 {
-    return (ZK == 0 || cz(i) == ZK) && (AX < 0 || (AX == 0 ? cx(i) : cy(i)) == SG);
+    return (ZF == 2 || cz(i) == ZF) && (AX < 0 || (AX == 0 ? cx(i) : cy(i)) == SG);
 }
 
 __device__ __forceinline__ float *slot_of(int i, float *rm, float *r0, float *rp)
@@ -49,56 +50,157 @@ __device__ __forceinline__ float *slot_of(int i, float *rm, float *r0, float *rp
 // Write the kept populations of one staged node, g_i / w_i, at row i % 9 of slot c_z(i); pos is
 // the node's offset within a plane (the mirrored right column passes pos - 2 PS, which moves
 // direction (+1, cy, cz) of the mirrored moments to the row of (-1, cy, cz)).
-template <int AX, int SG, int ZK>
+template <int AX, int SG, int ZF>
 __device__ __forceinline__ void mom_emit(const Mom &m, float *rm, float *r0, float *rp, int pos)
 {
     const MomPoly q = mom_poly(m);
 #pragma unroll
     for (int i = 0; i < 13; ++i) {
-        const bool ki = mom_keep(i, AX, SG, ZK), kj = mom_keep(26 - i, AX, SG, ZK);
+        const bool ki = mom_keep(i, AX, SG, ZF), kj = mom_keep(26 - i, AX, SG, ZF);
         if (!ki && !kj) continue;
         float gp, gm;
         mom_pair(i, m, q, gp, gm);
         if (ki) slot_of(i, rm, r0, rp)[(i % 9) * PS + pos] = gp;
         if (kj) slot_of(26 - i, rm, r0, rp)[((26 - i) % 9) * PS + pos] = gm;
     }
-    if (mom_keep(13, AX, SG, ZK)) r0[4 * PS + pos] = q.K0;
+    if (mom_keep(13, AX, SG, ZF)) r0[4 * PS + pos] = q.K0;
 }
 
-// Halo node of a thread (warps 0..2; see the file comment).
-struct MomHalo {
+__device__ __forceinline__ void cp_async4(float *dst, const float *src)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
+                 "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+// The 84 halo nodes of a staged plane, numbered hn: 0..31 the row below the tile (keeps c_y = +1),
+// 32..63 the row above (c_y = -1), 64..73 the left column over staged rows 0..9 (c_x = +1),
+// 74..83 the right column (c_x = -1, evaluated from x-mirrored moments).  Thread hn fetches
+// halo node hn's moments (into hb[q * kHalo + hn], q as in mom_lds) and phi^{n+1}.
+struct HaloFetch {
     int xy;       // offset of the node within a z plane of the box
-    int pos;      // staged position (plus -2 PS for the mirrored right column)
     int phi_pos;  // staged position
     bool on;
-    bool mirror;
 };
 
-// Stage one plane: the thread's own node from its moments mo (loaded ahead), its halo node's
-// from global memory (see mom_emit for ZK).
-template <int ZK>
-__device__ __forceinline__ void mom_stage_plane(const float *__restrict__ m_in, const float *__restrict__ u_in,
-                                                size_t N, int plane, const Mom &mo, int own, int row, const MomHalo &h,
-                                                float *rm, float *r0, float *rp)
+__device__ __forceinline__ void halo_fetch(const float *__restrict__ m_in, const float *__restrict__ u_in, size_t N,
+                                           int plane, const HaloFetch &h, float *hb)
 {
-    Mom mh;
-    if (h.on) mh = mom_load(m_in, u_in, N, plane + h.xy);
-    mom_emit<-1, 0, ZK>(mo, rm, r0, rp, own);
-    if (h.on) {
-        if (row == 0)
-            mom_emit<1, 1, ZK>(mh, rm, r0, rp, h.pos);
-        else if (row == 1)
-            mom_emit<1, -1, ZK>(mh, rm, r0, rp, h.pos);
-        else
-            mom_emit<0, 1, ZK>(h.mirror ? mom_mirror_x(mh) : mh, rm, r0, rp, h.pos);
+    if (!h.on) return;
+    const int k = plane + h.xy;
+#pragma unroll
+    for (int q = 0; q < kMomArrays; ++q) cp_async4(hb + q * kHalo + threadIdx.x, m_in + q * N + k);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) cp_async4(hb + (kMomArrays + a) * kHalo + threadIdx.x, u_in + a * N + k);
+}
+
+__device__ __forceinline__ void halo_fetch_phi(const float *__restrict__ phi, int plane, const HaloFetch &h,
+                                               float *ring)
+{
+    if (h.on) cp_async4(ring + h.phi_pos, phi + plane + h.xy);
+}
+
+__device__ __forceinline__ Mom halo_lds(const float *hb, int hn)
+{
+    Mom r;
+    r.ps = hb[hn];
+    r.ax = hb[kHalo + hn];
+    r.ay = hb[2 * kHalo + hn];
+    r.az = hb[3 * kHalo + hn];
+    r.bxx = hb[4 * kHalo + hn];
+    r.byy = hb[5 * kHalo + hn];
+    r.bzz = hb[6 * kHalo + hn];
+    r.bxy = hb[7 * kHalo + hn];
+    r.bxz = hb[8 * kHalo + hn];
+    r.byz = hb[9 * kHalo + hn];
+    r.ux = hb[10 * kHalo + hn];
+    r.uy = hb[11 * kHalo + hn];
+    r.uz = hb[12 * kHalo + hn];
+    return r;
+}
+
+// Halo populations of one staged plane, spread over the 8 warps by c_z: warps 0..2 the row below
+// (c_z = -1, 0, +1), warps 3..5 the row above, warp 6 the columns' c_z = -1 and +1, warp 7 their
+// c_z = 0 (3 populations per halo node and item).  PZ: the plane's filter (2 all, +-1 the planes
+// below / above a z chunk).
+template <int AX, int SG, int CZ, int PZ>
+__device__ __forceinline__ void halo_item(const Mom &m, float *rm, float *r0, float *rp, int pos)
+{
+    if (PZ == 2 || PZ == CZ) mom_emit<AX, SG, CZ>(m, rm, r0, rp, pos);
+}
+
+template <int PZ>
+__device__ __forceinline__ void mom_stage_halo(const float *hb, int row, int lane, float *rm, float *r0, float *rp)
+{
+    if (row < 3) {
+        if (PZ != 2 && PZ != row - 1) return;
+        const Mom m = halo_lds(hb, lane);
+        const int pos = lane + 1;
+        if (row == 0) halo_item<1, 1, -1, PZ>(m, rm, r0, rp, pos);
+        else if (row == 1) halo_item<1, 1, 0, PZ>(m, rm, r0, rp, pos);
+        else halo_item<1, 1, 1, PZ>(m, rm, r0, rp, pos);
+    } else if (row < 6) {
+        if (PZ != 2 && PZ != row - 4) return;
+        const Mom m = halo_lds(hb, MX + lane);
+        const int pos = (SY - 1) * SX + lane + 1;
+        if (row == 3) halo_item<1, -1, -1, PZ>(m, rm, r0, rp, pos);
+        else if (row == 4) halo_item<1, -1, 0, PZ>(m, rm, r0, rp, pos);
+        else halo_item<1, -1, 1, PZ>(m, rm, r0, rp, pos);
+    } else if (lane < 2 * SY) {
+        if (row == 6 && PZ == 0) return;
+        if (row == 7 && PZ != 2 && PZ != 0) return;
+        const bool mirror = lane >= SY;
+        Mom m = halo_lds(hb, 2 * MX + lane);
+        if (mirror) m = mom_mirror_x(m);
+        const int pos = (mirror ? lane - SY : lane) * SX + (mirror ? SX - 1 - 2 * PS : 0);
+        if (row == 6) {
+            halo_item<0, 1, -1, PZ>(m, rm, r0, rp, pos);
+            halo_item<0, 1, 1, PZ>(m, rm, r0, rp, pos);
+        } else {
+            halo_item<0, 1, 0, PZ>(m, rm, r0, rp, pos);
+        }
     }
 }
 
-__device__ __forceinline__ void mom_stage_phi(float own_phi, const float *__restrict__ phi, int plane,
-                                              const MomHalo &h, int own, float *ring)
+// In-plane partial sums of the 27-point stencils at staged position pos of a phi^{n+1} plane pl:
+//   A = S_x S_y phi,   X = S_y (phi(x+1) - phi(x-1)),   Y = S_x (phi(y+1) - phi(y-1)),
+// with S f = f(-1) / 6 + 2 f(0) / 3 + f(+1) / 6 along one axis (the D3Q27 weights factor as
+// w(c) = w1(cx) w1(cy) w1(cz), w1(0) = 2/3, w1(+-1) = 1/6).
+struct PhiPartials {
+    float A, X, Y;
+};
+
+__device__ __forceinline__ float smooth3(float m, float c, float p)
 {
-    ring[own] = own_phi;
-    if (h.on) ring[h.phi_pos] = __ldg(phi + plane + h.xy);
+    return fmaf(1.0f / 6.0f, m + p, (2.0f / 3.0f) * c);
+}
+
+__device__ __forceinline__ PhiPartials phi_partials(const float *pl, int pos)
+{
+    const float a0 = pl[pos - SX - 1], a1 = pl[pos - SX], a2 = pl[pos - SX + 1];
+    const float b0 = pl[pos - 1], b1 = pl[pos], b2 = pl[pos + 1];
+    const float c0 = pl[pos + SX - 1], c1 = pl[pos + SX], c2 = pl[pos + SX + 1];
+    const float s0 = smooth3(a0, b0, c0), s1 = smooth3(a1, b1, c1), s2 = smooth3(a2, b2, c2);
+    PhiPartials r;
+    r.A = smooth3(s0, s1, s2);
+    r.X = s2 - s0;
+    r.Y = smooth3(c0 - a0, c1 - a1, c2 - a2);
+    return r;
+}
+
+// Gradient and Laplacian of phi^{n+1} at a node from the partial sums of planes z-1, z, z+1
+// (the 27-point formulas of the paper's finite differences, evaluated separably):
+//   grad_x = 3 sum w c_x phi = S_z X / 2,  grad_y = S_z Y / 2,  grad_z = (A(z+1) - A(z-1)) / 2,
+//   lap = 6 (sum w phi - phi0) = (A(z-1) - phi0) + (A(z+1) - phi0) + 4 (A(z) - phi0).
+__device__ __forceinline__ void phi_stencils(const PhiPartials &m, const PhiPartials &c, const PhiPartials &p,
+                                             float phi0, float &gx, float &gy, float &gz, float &lap)
+{
+    gx = fmaf(1.0f / 12.0f, m.X + p.X, (1.0f / 3.0f) * c.X);
+    gy = fmaf(1.0f / 12.0f, m.Y + p.Y, (1.0f / 3.0f) * c.Y);
+    gz = 0.5f * (p.A - m.A);
+    lap = fmaf(4.0f, c.A - phi0, (m.A - phi0) + (p.A - phi0));
 }
 
 template <bool WALL>
@@ -125,71 +227,106 @@ __global__ void __launch_bounds__(kMomThreads, 2)
     const int own_xy = y * G.nx + x;
     const int own = (row + 1) * SX + lane + 1;
 
-    MomHalo h{0, 0, 0, false, false};
-    if (row < 2) {
-        const int hy = row == 0 ? (y0 - 1 + G.ny) % G.ny : (y0 + MY) % G.ny;
-        h.xy = hy * G.nx + x;
-        h.pos = h.phi_pos = (row == 0 ? 0 : SY - 1) * SX + lane + 1;
-        h.on = true;
-    } else if (row == 2 && lane < 2 * SY) {
-        h.mirror = lane >= SY;
-        const int sy = h.mirror ? lane - SY : lane;
-        const int hx = h.mirror ? (x0 + MX) % G.nx : (x0 - 1 + G.nx) % G.nx;
+    HaloFetch h{0, 0, threadIdx.x < kHalo};
+    if (threadIdx.x < MX) {
+        h.xy = ((y0 - 1 + G.ny) % G.ny) * G.nx + (x0 + threadIdx.x) % G.nx;
+        h.phi_pos = threadIdx.x + 1;
+    } else if (threadIdx.x < 2 * MX) {
+        const int c = threadIdx.x - MX;
+        h.xy = ((y0 + MY) % G.ny) * G.nx + (x0 + c) % G.nx;
+        h.phi_pos = (SY - 1) * SX + c + 1;
+    } else if (threadIdx.x < kHalo) {
+        const int c = threadIdx.x - 2 * MX;
+        const bool right = c >= SY;
+        const int sy = right ? c - SY : c;
+        const int hx = right ? (x0 + MX) % G.nx : (x0 - 1 + G.nx) % G.nx;
         h.xy = ((y0 - 1 + sy + G.ny) % G.ny) * G.nx + hx;
-        h.phi_pos = sy * SX + (h.mirror ? SX - 1 : 0);
-        h.pos = h.mirror ? h.phi_pos - 2 * PS : h.phi_pos;
-        h.on = true;
+        h.phi_pos = sy * SX + (right ? SX - 1 : 0);
     }
 
     float *rp_prev = sm, *rp_cur = sm + SLOT, *rp_next = sm + 2 * SLOT;
     float *r0_cur = sm + 3 * SLOT, *r0_next = sm + 4 * SLOT;
     float *rm_cur = sm + 5 * SLOT, *rm_next = sm + 6 * SLOT;
-    float *ph_prev = sm + kSlots * SLOT, *ph_cur = ph_prev + PS, *ph_next = ph_cur + PS;
+    float *const hb = sm + kSlots * SLOT;
+    float *const ring = hb + 13 * kHalo;
+    auto ring_of = [&](int zs) { return ring + ((zs - z0 + 1) & 3) * PS; };   // phi^{n+1} of plane zs
 
     // planes staged around the chunk (-1: none, beyond a wall); phi^{n+1} beyond a wall is the
     // mirror image of the wall plane
     auto moment_plane = [&](int zs) { return zs < 0 ? (WALL ? -1 : G.nz - 1) : zs >= G.nz ? (WALL ? -1 : 0) : zs; };
     auto phi_plane = [&](int zs) { return zs < 0 ? (WALL ? 0 : G.nz - 1) : zs >= G.nz ? (WALL ? G.nz - 1 : 0) : zs; };
 
-    // prologue: the c_z = +1 populations of the plane below the chunk, the chunk's first plane,
-    // phi^{n+1} of planes z0-1 and z0; the own moments and phi of plane z0+1 are loaded ahead
+    // prologue: the c_z = +1 populations of the plane below the chunk, then the chunk's first
+    // plane with phi^{n+1} of planes z0-1 and z0; the own node's moments and phi of plane z0+1
+    // are loaded into registers, its halo's into shared memory
     Mom mo;
     const int zb = moment_plane(z0 - 1);
     if (zb >= 0) {
         mo = mom_load(m_in, u_in, N, zb * nxy + own_xy);
-        mom_stage_plane<1>(m_in, u_in, N, zb * nxy, mo, own, row, h, rm_next, r0_next, rp_prev);
+        halo_fetch(m_in, u_in, N, zb * nxy, h, hb);
+        cp_async_commit();
+        cp_async_wait_all();
+        __syncthreads();
+        mom_emit<-1, 0, 1>(mo, rm_next, r0_next, rp_prev, own);
+        mom_stage_halo<1>(hb, row, lane, rm_next, r0_next, rp_prev);
+        __syncthreads();
     }
     mo = mom_load(m_in, u_in, N, z0 * nxy + own_xy);
-    mom_stage_plane<0>(m_in, u_in, N, z0 * nxy, mo, own, row, h, rm_cur, r0_cur, rp_cur);
+    halo_fetch(m_in, u_in, N, z0 * nxy, h, hb);
+    ring_of(z0 - 1)[own] = __ldg(phi_new + phi_plane(z0 - 1) * nxy + own_xy);
+    halo_fetch_phi(phi_new, phi_plane(z0 - 1) * nxy, h, ring_of(z0 - 1));
+    ring_of(z0)[own] = __ldg(phi_new + z0 * nxy + own_xy);
+    halo_fetch_phi(phi_new, z0 * nxy, h, ring_of(z0));
+    cp_async_commit();
+    cp_async_wait_all();
+    __syncthreads();
+    PhiPartials pm = phi_partials(ring_of(z0 - 1), own), p0 = phi_partials(ring_of(z0), own);
+    mom_emit<-1, 0, 2>(mo, rm_cur, r0_cur, rp_cur, own);
+    mom_stage_halo<2>(hb, row, lane, rm_cur, r0_cur, rp_cur);
     float ubx = mo.ux, uby = mo.uy, ubz = mo.uz;
-    mom_stage_phi(__ldg(phi_new + phi_plane(z0 - 1) * nxy + own_xy), phi_new, phi_plane(z0 - 1) * nxy, h, own,
-                  ph_prev);
-    mom_stage_phi(__ldg(phi_new + z0 * nxy + own_xy), phi_new, z0 * nxy, h, own, ph_cur);
+    __syncthreads();
     int zn = moment_plane(z0 + 1);
-    if (zn >= 0) mo = mom_load(m_in, u_in, N, zn * nxy + own_xy);
+    if (zn >= 0) {
+        mo = mom_load(m_in, u_in, N, zn * nxy + own_xy);
+        halo_fetch(m_in, u_in, N, zn * nxy, h, hb);
+    }
     float phn = __ldg(phi_new + phi_plane(z0 + 1) * nxy + own_xy);
+    halo_fetch_phi(phi_new, phi_plane(z0 + 1) * nxy, h, ring_of(z0 + 1));
+    cp_async_commit();
+    cp_async_wait_all();
+    __syncthreads();
 
     for (int z = z0; z < z1; ++z) {
         // stage plane z+1 (all of it inside the chunk, its c_z = -1 populations above the
         // chunk, nothing beyond a wall) and its phi^{n+1}
         const float nbx = mo.ux, nby = mo.uy, nbz = mo.uz;
-        if (z + 1 < z1)
-            mom_stage_plane<0>(m_in, u_in, N, zn * nxy, mo, own, row, h, rm_next, r0_next, rp_next);
-        else if (zn >= 0)
-            mom_stage_plane<-1>(m_in, u_in, N, zn * nxy, mo, own, row, h, rm_next, r0_next, rp_next);
-        mom_stage_phi(phn, phi_new, phi_plane(z + 1) * nxy, h, own, ph_next);
+        if (z + 1 < z1) {
+            mom_emit<-1, 0, 2>(mo, rm_next, r0_next, rp_next, own);
+            mom_stage_halo<2>(hb, row, lane, rm_next, r0_next, rp_next);
+        } else if (zn >= 0) {
+            mom_emit<-1, 0, -1>(mo, rm_next, r0_next, rp_next, own);
+            mom_stage_halo<-1>(hb, row, lane, rm_next, r0_next, rp_next);
+        }
+        ring_of(z + 1)[own] = phn;
         __syncthreads();
 
-        // own moments and phi of plane z+2, in flight during the collision
+        // plane z+2 in flight during the collision: own moments and phi into registers, the
+        // halo's into shared memory
         if (z + 1 < z1) {
             zn = moment_plane(z + 2);
-            if (zn >= 0) mo = mom_load(m_in, u_in, N, zn * nxy + own_xy);
+            if (zn >= 0) {
+                mo = mom_load(m_in, u_in, N, zn * nxy + own_xy);
+                halo_fetch(m_in, u_in, N, zn * nxy, h, hb);
+            }
             phn = __ldg(phi_new + phi_plane(z + 2) * nxy + own_xy);
+            halo_fetch_phi(phi_new, phi_plane(z + 2) * nxy, h, ring_of(z + 2));
         }
+        cp_async_commit();
 
+        const PhiPartials pp = phi_partials(ring_of(z + 1), own);
         if (active) {
             const bool wlo = WALL && z == 0, whi = WALL && z == G.nz - 1;
-            float f[27];
+            float gh[27];
 #pragma unroll
             for (int i = 0; i < 27; ++i) {
                 const int nb = own - cy(i) * SX - cx(i);
@@ -200,23 +337,22 @@ __global__ void __launch_bounds__(kMomThreads, 2)
                     src = r0_cur + (i % 9) * PS + nb;
                 else
                     src = whi ? rp_cur + ((26 - i) % 9) * PS + own : rm_next + (i % 9) * PS + nb;
-                f[i] = __fmul_rn(wgt(i), *src);   // not fused into the moment sums: same bits as the plain kernel
+                gh[i] = *src;
             }
-            float psi[27];
-#pragma unroll
-            for (int i = 0; i < 27; ++i) {
-                const float *pr = cz(i) < 0 ? ph_prev : cz(i) == 0 ? ph_cur : ph_next;
-                psi[i] = pr[own + cy(i) * SX + cx(i)];
-            }
-            mom_collide_store(f, psi, ubx, uby, ubz, P, m_out, u_out, w_out, N, z * nxy + own_xy);
+            const float phi0 = ring_of(z)[own];
+            float gx, gy, gz, lap;
+            phi_stencils(pm, p0, pp, phi0, gx, gy, gz, lap);
+            mom_finish(raw_moments_hat(gh), phi0, gx, gy, gz, lap, ubx, uby, ubz, P, m_out, u_out, w_out, N,
+                       z * nxy + own_xy);
         }
+        pm = p0, p0 = pp;
+        cp_async_wait_all();
         __syncthreads();
 
         float *t = rp_prev;
         rp_prev = rp_cur, rp_cur = rp_next, rp_next = t;
         t = r0_cur, r0_cur = r0_next, r0_next = t;
         t = rm_cur, rm_cur = rm_next, rm_next = t;
-        t = ph_prev, ph_prev = ph_cur, ph_cur = ph_next, ph_next = t;
         ubx = nbx, uby = nby, ubz = nbz;
     }
 }
@@ -233,21 +369,22 @@ __global__ void __launch_bounds__(128)
     const int k = n.zo[1] + n.yo[1] + x;
     const size_t N = (size_t)G.N;
     const bool wlo = WALL && z == 0, whi = WALL && z == G.nz - 1;
-    float f[27];
+    float gh[27];
 #pragma unroll
     for (int i = 0; i < 27; ++i) {
         const bool bounce = (cz(i) == 1 && wlo) || (cz(i) == -1 && whi);
         const int src = bounce ? k : n.zo[1 - cz(i)] + n.yo[1 - cy(i)] + n.xo[1 - cx(i)];
         const Mom m = mom_load(m_in, u_in, N, src);
         const MomPoly q = mom_poly(m);
-        const float gi = bounce ? mom_one(26 - i, m, q) : mom_one(i, m, q);
-        f[i] = __fmul_rn(wgt(i), gi);
+        gh[i] = bounce ? mom_one(26 - i, m, q) : mom_one(i, m, q);
     }
     float psi[27];
 #pragma unroll
     for (int i = 0; i < 27; ++i) psi[i] = __ldg(phi_new + nidx(n, i));
-    mom_collide_store(f, psi, __ldg(u_in + k), __ldg(u_in + N + k), __ldg(u_in + 2 * N + k), P, m_out, u_out, w_out,
-                      N, k);
+    float gx, gy, gz, lap;
+    grad_lap27(psi, gx, gy, gz, lap);
+    mom_finish(raw_moments_hat(gh), psi[13], gx, gy, gz, lap, __ldg(u_in + k), __ldg(u_in + N + k),
+               __ldg(u_in + 2 * N + k), P, m_out, u_out, w_out, N, k);
 }
 
 // Equilibrium start: p* = pstar (or 0), a = 0, B = 0 (u is already in place).

@@ -111,12 +111,14 @@ struct Collided {
     float omega;
 };
 
-__device__ __forceinline__ Collided collide_moments(const float (&f)[27], float phi, float gpx, float gpy,
-                                                    float gpz, float lap, float ubx, float uby, float ubz,
-                                                    const Phys &P)
+// Raw moments of the streamed populations: p* = sum f, j = sum f c, Pi = sum f c c.
+struct RawMoments {
+    float ps, jx, jy, jz, pxx, pyy, pzz, pxy, pxz, pyz;
+};
+
+__device__ __forceinline__ RawMoments raw_moments(const float (&f)[27])
 {
-    Collided c;
-    // moments over opposite pairs
+    RawMoments r;
     float ps = f[13];
     float jx = 0.f, jy = 0.f, jz = 0.f;
     float pxx = 0.f, pyy = 0.f, pzz = 0.f, pxy = 0.f, pxz = 0.f, pyz = 0.f;
@@ -132,6 +134,19 @@ __device__ __forceinline__ Collided collide_moments(const float (&f)[27], float 
         if (cx(i) * cz(i)) pxz += (cx(i) * cz(i)) * s;
         if (cy(i) * cz(i)) pyz += (cy(i) * cz(i)) * s;
     }
+    r.ps = ps;
+    r.jx = jx, r.jy = jy, r.jz = jz;
+    r.pxx = pxx, r.pyy = pyy, r.pzz = pzz, r.pxy = pxy, r.pxz = pxz, r.pyz = pyz;
+    return r;
+}
+
+__device__ __forceinline__ Collided collide_from_moments(const RawMoments &r, float phi, float gpx, float gpy,
+                                                         float gpz, float lap, float ubx, float uby, float ubz,
+                                                         const Phys &P)
+{
+    Collided c;
+    const float ps = r.ps, jx = r.jx, jy = r.jy, jz = r.jz;
+    const float pxx = r.pxx, pyy = r.pyy, pzz = r.pzz, pxy = r.pxy, pxz = r.pxz, pyz = r.pyz;
 
     // local properties
     const float rho = fmaf(phi, P.drho, P.rho_g);
@@ -169,6 +184,13 @@ __device__ __forceinline__ Collided collide_moments(const float (&f)[27], float 
     c.Ayz = pyz - uy * uz + 0.5f * (uy * az + ay * uz);
     c.omega = omega;
     return c;
+}
+
+__device__ __forceinline__ Collided collide_moments(const float (&f)[27], float phi, float gpx, float gpy,
+                                                    float gpz, float lap, float ubx, float uby, float ubz,
+                                                    const Phys &P)
+{
+    return collide_from_moments(raw_moments(f), phi, gpx, gpy, gpz, lap, ubx, uby, ubz, P);
 }
 
 template <bool NEQ = false>
