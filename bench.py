@@ -44,13 +44,17 @@ sys.path.insert(0, ROOT)
 #   16-bit: 27 h (2 B) + P + phi + 3 ubar floats = 74 B, twice
 # (the Allen-Cahn flux W that this design carries from the lattice Boltzmann kernel of one step
 # to the Allen-Cahn kernel of the next, 24 B per node, is extra traffic and not counted here)
-STEP_BYTES = {"fp32": 248, "bf16": 148, "fp16": 148}
+STEP_BYTES = {"fp32": 248, "bf16": 148, "fp16": 148, "mom": 112}
 # algorithmic bytes per node of each kernel that can dominate a step
 KERNEL_BYTES = {"lbm_kernel": 256,      # read 27 g + phi^{n+1} + 3 ubar, write 27 g + 3 ubar + 3 W
                 "fused2_kernel": 248,
                 "lbm16_kernel": 156,    # read 27 h + P + phi^{n+1} + 3 ubar, write 27 h + P + 3 ubar + 3 W
+                "lbm_mom_kernel": 120,  # read 13 moments + phi^{n+1}, write 13 moments + 3 W
+                "lbm_mom_plain_kernel": 120,
                 "ac_div_kernel": 20}    # read phi^n + 3 W^n, write phi^{n+1}
-STORES = {"fp32": 0, "bf16": 1, "fp16": 2}
+STORES = {"fp32": 0, "bf16": 1, "fp16": 2, "mom": 3}
+# floats (or their 16-bit share) of one copy of the state per node: g + phi + u, or h/2 + P + phi + u
+STATE_FLOATS = {"fp32": 31, "bf16": 18.5, "fp16": 18.5, "mom": 14}
 FALLBACK_HBM_GBS = 6400.0
 METRIC = "MLUPS & % HBM peak: coupled LBM+Allen-Cahn step, FP32 vs BF16 store"
 # sources that define each step kernel's device code (the profile of a kernel is reused only while
@@ -62,11 +66,15 @@ KERNEL_SOURCES = {
     "lbm16_kernel": ["paper_2501_00846_b300/csrc/step_lbm16.cu", "paper_2501_00846_b300/csrc/tslb_device.cuh"],
     "ac_div_kernel": ["paper_2501_00846_b300/csrc/step_split.cu", "paper_2501_00846_b300/csrc/ac_div.cuh",
                       "paper_2501_00846_b300/csrc/tslb_device.cuh"],
+    "lbm_mom_kernel": ["paper_2501_00846_b300/csrc/step_mom.cu", "paper_2501_00846_b300/csrc/mom_device.cuh",
+                       "paper_2501_00846_b300/csrc/tslb_device.cuh"],
 }
 KERNEL_NAMES = {0: "lbm_kernel", 1: "lbm_kernel", 2: "fused2_kernel"}
 
 
 def kernel_name(path, store):
+    if store == "mom":
+        return "lbm_mom_kernel" if path == 0 else "lbm_mom_plain_kernel"
     if store != "fp32":
         return "lbm16_kernel" if path == 0 else "lbm_kernel"
     return KERNEL_NAMES[path]
@@ -97,7 +105,7 @@ def measured_traffic(kernel, wl_name, nodes, store="fp32"):
     sources (else None)."""
     if kernel not in KERNEL_SOURCES:
         return None
-    tag = kernel if store == "fp32" else f"{kernel}_{store}"
+    tag = kernel if store in ("fp32", "mom") else f"{kernel}_{store}"
     path = os.path.join(ROOT, "profiles", f"{tag}_{wl_name}.txt")
     if not os.path.exists(path):
         return None
@@ -446,7 +454,8 @@ def main():
         return 0
 
     value = world * N * args.steps / (ms_max * 1e-3) / 1e6
-    dtype = {"fp32": "f32", "bf16": "f32 compute, bf16 store", "fp16": "f32 compute, f16 store"}[args.store]
+    dtype = {"fp32": "f32", "bf16": "f32 compute, bf16 store", "fp16": "f32 compute, f16 store",
+             "mom": "f32, moment store"}[args.store]
     line = {
         "metric": METRIC,
         "value": value,
@@ -461,7 +470,8 @@ def main():
         "dtype": dtype,
         "data": "synthetic",
         "config": {"workload": wl.name, "nodes": N, "store": args.store, "path": args.path, "split": args.split,
-                   "l2": "state >= 0.6 GB per copy >> 126 MB L2: inputs larger than L2, no flush",
+                   "l2": f"state {STATE_FLOATS[args.store] * 4 * N / 1e9:.2f} GB per copy > 126 MB L2: inputs "
+                         "larger than L2, no flush",
                    "parallelism": f"replicas x{world}", "sum_phi_after": obs["sum_phi"],
                    "nonfinite_after": obs["n_nonfinite"]},
         "roofline": roofline(args.store, ms / args.steps, kernel_ms),

@@ -116,14 +116,24 @@ __device__ __forceinline__ float mom_acc(float s, int c, float v)
     return c > 0 ? __fadd_rn(s, v) : c < 0 ? __fsub_rn(s, v) : s;
 }
 
+// c_x a + c_y b + c_z c for lattice components in {-1, 0, 1} (compile-time constants after
+// unrolling), summed in the order x, y, z; the first nonzero term is taken as it is (a negation is
+// exact), so no addition to zero is executed.
+__device__ __forceinline__ float mom_dot(int X, int Y, int Z, float a, float b, float c)
+{
+    if (X) return mom_acc(mom_acc(X > 0 ? a : -a, Y, b), Z, c);
+    if (Y) return mom_acc(Y > 0 ? b : -b, Z, c);
+    return Z > 0 ? c : Z < 0 ? -c : 0.0f;
+}
+
 // g_i / w_i and g_{26-i} / w_i of the pair i < 13 (i a compile-time constant after unrolling).
 __device__ __forceinline__ void mom_pair(int i, const Mom &m, const MomPoly &q, float &gp, float &gm)
 {
     const int X = cx(i), Y = cy(i), Z = cz(i);
-    const float cu = mom_acc(mom_acc(mom_acc(0.0f, X, m.ux), Y, m.uy), Z, m.uz);
-    const float ca = mom_acc(mom_acc(mom_acc(0.0f, X, m.ax), Y, m.ay), Z, m.az);
-    const float cv = mom_acc(mom_acc(mom_acc(0.0f, X, q.vx), Y, q.vy), Z, q.vz);
-    float cbc = mom_acc(mom_acc(mom_acc(0.0f, X * X, m.bxx), Y * Y, m.byy), Z * Z, m.bzz);
+    const float cu = mom_dot(X, Y, Z, m.ux, m.uy, m.uz);
+    const float ca = mom_dot(X, Y, Z, m.ax, m.ay, m.az);
+    const float cv = mom_dot(X, Y, Z, q.vx, q.vy, q.vz);
+    float cbc = mom_dot(X * X, Y * Y, Z * Z, m.bxx, m.byy, m.bzz);
     cbc = mom_acc(mom_acc(mom_acc(cbc, X * Y, q.b2xy), X * Z, q.b2xz), Y * Z, q.b2yz);
     const float hcu = __fmul_rn(4.5f, cu);
     const float E = __fadd_rn(__fmaf_rn(hcu, __fadd_rn(cu, ca), q.K0), cbc);

@@ -325,19 +325,27 @@ __global__ void __launch_bounds__(kMomThreads, 2)
 
         const PhiPartials pp = phi_partials(ring_of(z + 1), own);
         if (active) {
-            const bool wlo = WALL && z == 0, whi = WALL && z == G.nz - 1;
             float gh[27];
+            if (WALL && (z == 0 || z == G.nz - 1)) {   // a wall plane (uniform across the CTA)
+                const bool wlo = z == 0, whi = z == G.nz - 1;
 #pragma unroll
-            for (int i = 0; i < 27; ++i) {
-                const int nb = own - cy(i) * SX - cx(i);
-                const float *src;
-                if (cz(i) == 1)
-                    src = wlo ? rm_cur + ((26 - i) % 9) * PS + own : rp_prev + (i % 9) * PS + nb;
-                else if (cz(i) == 0)
-                    src = r0_cur + (i % 9) * PS + nb;
-                else
-                    src = whi ? rp_cur + ((26 - i) % 9) * PS + own : rm_next + (i % 9) * PS + nb;
-                gh[i] = *src;
+                for (int i = 0; i < 27; ++i) {
+                    const int nb = own - cy(i) * SX - cx(i);
+                    const float *src;
+                    if (cz(i) == 1)
+                        src = wlo ? rm_cur + ((26 - i) % 9) * PS + own : rp_prev + (i % 9) * PS + nb;
+                    else if (cz(i) == 0)
+                        src = r0_cur + (i % 9) * PS + nb;
+                    else
+                        src = whi ? rp_cur + ((26 - i) % 9) * PS + own : rm_next + (i % 9) * PS + nb;
+                    gh[i] = *src;
+                }
+            } else {
+#pragma unroll
+                for (int i = 0; i < 27; ++i) {
+                    const float *sl = cz(i) == 1 ? rp_prev : cz(i) == 0 ? r0_cur : rm_next;
+                    gh[i] = sl[(i % 9) * PS + own - cy(i) * SX - cx(i)];
+                }
             }
             const float phi0 = ring_of(z)[own];
             float gx, gy, gz, lap;
