@@ -330,10 +330,11 @@ lbm_status lbm_cnn_get_params(lbm_cnn *cnn, float *params);        /* host, lbm_
 lbm_status lbm_cnn_set_params(lbm_cnn *cnn, const float *params);  /* host; resets nothing else */
 lbm_status lbm_cnn_get_grads(lbm_cnn *cnn, float *grads);          /* host, the kept gradients */
 
-/* Convolution kernel: 0 tcgen05.mma with TMEM accumulators (shared-memory descriptors); 1 (default,
- * the fastest measured) mma.sync from shared-memory tiles (cp.async, ldmatrix); 2 mma.sync with
- * fragments straight from global memory.  All three add the same BF16 products in the same order
- * per output and gave identical results on every tested grid.  lbm_cnn_forward and lbm_cnn_grad return
+/* Convolution kernel: 0 (default, the fastest measured) tcgen05.mma with TMEM accumulators
+ * (shared-memory descriptors, the activation fused into its epilogue); 1 mma.sync from
+ * shared-memory tiles (cp.async, ldmatrix); 2 mma.sync with fragments straight from global
+ * memory.  All three add the same BF16 products in the same order per output and gave identical
+ * results on every tested grid.  lbm_cnn_forward and lbm_cnn_grad return
  * LBM_ERR_TIMEOUT if a tensor-core kernel gave up waiting for its MMAs.  LBM_ERR_ARG for other
  * values. */
 lbm_status lbm_cnn_set_conv_kernel(lbm_cnn *cnn, int kernel);

@@ -145,6 +145,22 @@ __device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi)
+{
+    const uint32_t l = __bfloat16_as_ushort(__float2bfloat16_rn(lo));
+    const uint32_t h = __bfloat16_as_ushort(__float2bfloat16_rn(hi));
+    return l | (h << 16);
+}
+
+// silu(z) = z / (1 + e^-z) with the fast division (every kernel evaluates it through this function)
+__device__ __forceinline__ float silu(float z) { return __fdividef(z, 1.0f + __expf(-z)); }
+
+// wait until at most N of this thread's most recent cp.async groups are still pending
+template <int N>
+__device__ __forceinline__ void cp_async_wait_group()
+{
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
 
 __device__ __forceinline__ void ldmatrix_x4(uint32_t (&r)[4], const void *smem)
 {
@@ -269,17 +285,21 @@ __global__ void __launch_bounds__(256) conv_tile_kernel(int nx, int ny, int nz, 
 //      HX * 16 bytes apart, the two channel groups of a K step LBO = HY * HX * 16 bytes apart, and a
 //      neighbour offset (dx, dy) only moves the start address;
 //   B: the weights, [k][channel chunk][group of 8 channels][o][8] (LBO = N * 16, SBO = 128).
-// A block of 4 warps owns a 16 x 16 column tile (two patches) and marches a z chunk: one thread
-// issues the 2 x 27 x CB MMAs of plane zc into one of two TMEM accumulator buffers and commits them
-// to an mbarrier; meanwhile all four warps read back plane zc - 1's accumulators (tcgen05.ld, warp
-// w owns TMEM lanes 32w..32w+31 = patch rows 4w..4w+3), add the bias and store; the input ring
-// (4 planes, cp.async) is refilled two planes ahead once the MMAs that read the slot are done.
-// Every mbarrier wait is bounded: on expiry the kernel records an error, stops issuing work and
-// still releases its TMEM.
+// A block of 8 warps owns a 16 x 16 column tile (two patches) and marches a z chunk: one thread
+// issues the 2 x 27 x CB MMAs of plane zc (fully unrolled; the descriptors are precomputed words
+// plus compile-time offsets) into one of two TMEM accumulator buffers and commits them to an
+// mbarrier; meanwhile all warps read back plane zc - 1's accumulators (tcgen05.ld; warp w owns
+// TMEM lanes 32 (w % 4) .. + 31 = patch rows 4 (w % 4) .. + 3 and half w / 4 of the output
+// channels), add the bias, store z and, for the forward pass, the next layer's input silu(z) in
+// BF16.  The input ring (6
+// planes, cp.async) is refilled four planes ahead as soon as the MMAs that read a slot are done,
+// so a plane's copy has three planes of MMAs to arrive.  Every mbarrier wait is bounded: on
+// expiry the kernel records an error, stops issuing work and still releases its TMEM.
 
 constexpr int UM_TX = 16, UM_TY = 16;              // column tile: two 8 x 16 patches
 constexpr int UM_HX = UM_TX + 2, UM_HY = UM_TY + 2;
-constexpr int UM_SLOTS = 4;
+constexpr int UM_SLOTS = 6;                        // planes zc-1..zc+1 read, zc+2..zc+4 in flight
+constexpr int UM_AHEAD = 4;                        // a plane is loaded this many planes ahead
 constexpr int UM_SPIN = 1 << 24;                   // mbarrier polls before giving up
 
 template <int CB>
@@ -336,11 +356,14 @@ __device__ __forceinline__ void um_load_plane(uint8_t *slot, const __nv_bfloat16
 
 // z[n][o] = bias[o] + sum_{k, i} W[o][i][k] in[n + off_k][i], CO = MT * 16 output channels (padded),
 // CB * 16 input channels (padded); wpack: [27][CB][2][CO][8] BF16 (pack_weights_umma_kernel).
+constexpr int UM_THREADS = 256;   // 8 warps: warp w reads TMEM lanes 32 (w % 4).., columns half w / 4
+
 template <int MT, int CB>
-__global__ void __launch_bounds__(128, 1) conv_umma_kernel(int nx, int ny, int nz, const __nv_bfloat16 *__restrict__ wpack,
+__global__ void __launch_bounds__(UM_THREADS, 1) conv_umma_kernel(int nx, int ny, int nz, const __nv_bfloat16 *__restrict__ wpack,
                                                            const __nv_bfloat16 *__restrict__ in,
                                                            const float *__restrict__ bias, float *__restrict__ z,
-                                                           int zlen, int *__restrict__ err)
+                                                           __nv_bfloat16 *__restrict__ act, int zlen,
+                                                           int *__restrict__ err)
 {
     constexpr int CO = MT * 16;
     constexpr int WBYTES = 27 * CB * 2 * CO * 16;
@@ -350,6 +373,7 @@ __global__ void __launch_bounds__(128, 1) conv_umma_kernel(int nx, int ny, int n
     __shared__ __align__(8) uint64_t mbar[2];
     __shared__ uint32_t tmem_base;
     __shared__ int abort_flag;
+    __shared__ float sbias[CO];
     uint8_t *sw = usm;
     uint8_t *ring = usm + ((WBYTES + 1023) / 1024) * 1024;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -358,14 +382,18 @@ __global__ void __launch_bounds__(128, 1) conv_umma_kernel(int nx, int ny, int n
     const int z0 = blockIdx.y * zlen, z1 = min(nz, z0 + zlen);
     if (z0 >= nz) return;   // whole block
 
-    {   // weights (plain 16-byte copies)
+    {   // weights (plain 16-byte copies) and the (padded) bias
         const uint4 *src = reinterpret_cast<const uint4 *>(wpack);
         uint4 *dst = reinterpret_cast<uint4 *>(sw);
         for (int i = tid; i < WBYTES / 16; i += blockDim.x) dst[i] = src[i];
+        if (tid < CO) sbias[tid] = bias ? bias[tid] : 0.0f;
     }
-    auto slot = [&](int p) { return ring + (size_t)((p - (z0 - 1)) & (UM_SLOTS - 1)) * PB; };
-    for (int j = 0; j < 3; ++j) um_load_plane<CB>(slot(z0 - 1 + j), in, nx, ny, nz, x0, y0, z0 - 1 + j);
-    cp_async_commit();
+    auto slot = [&](int p) { return ring + (size_t)((p - (z0 - 1)) % UM_SLOTS) * PB; };
+    // planes z0-1 .. z0+3, one cp.async group each (empty groups past the chunk keep the count)
+    for (int j = 0; j <= UM_AHEAD; ++j) {
+        if (z0 - 1 + j <= z1) um_load_plane<CB>(slot(z0 - 1 + j), in, nx, ny, nz, x0, y0, z0 - 1 + j);
+        cp_async_commit();
+    }
     if (tid == 0) {
         abort_flag = 0;
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_addr(&mbar[0])));
@@ -377,7 +405,7 @@ __global__ void __launch_bounds__(128, 1) conv_umma_kernel(int nx, int ny, int n
                      "r"(TCOLS));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
     }
-    cp_async_wait_all();
+    cp_async_wait_group<UM_AHEAD - 2>();   // planes z0-1, z0, z0+1
     asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
     asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
     __syncthreads();
@@ -387,27 +415,24 @@ __global__ void __launch_bounds__(128, 1) conv_umma_kernel(int nx, int ny, int n
     const uint32_t lbo_a = UM_HY * UM_HX * 16, sbo_a = UM_HX * 16;
     const uint32_t lbo_b = CO * 16, sbo_b = 128;
     const uint32_t sw_addr = smem_addr(sw);
+    // descriptor words: the start address is the low 14 bits of the low word (address >> 4; shared
+    // addresses stay below 2^18 bytes, so adding an offset never carries out of the field)
+    const uint32_t a_hi = (uint32_t)(umma_desc(0, lbo_a, sbo_a) >> 32);
+    const uint32_t b_lo = (uint32_t)umma_desc(sw_addr, lbo_b, sbo_b), b_hi = (uint32_t)(umma_desc(sw_addr, lbo_b, sbo_b) >> 32);
     uint32_t phase[2] = {0u, 0u};
 
-    // read back the accumulators of plane p (buffer b), add the bias, store
+    // read back the accumulators of plane p (buffer b), add the bias, store: warp w owns TMEM lanes
+    // 32 (w % 4) .. + 31 (patch rows) and the output channels of half w / 4
     auto epilogue = [&](int p, int b) {
-        const int mrow = 32 * warp + lane;             // patch row index: node (mrow % 8, mrow / 8)
+        constexpr int CH = CO / 2;
+        const int q = warp & 3, h = warp >> 2;
+        const int mrow = 32 * q + lane;                // patch row index: node (mrow % 8, mrow / 8)
         const int yy = y0 + mrow / 8;
 #pragma unroll
         for (int pt = 0; pt < 2; ++pt) {
-            uint32_t r[CO];
-            const uint32_t taddr = tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(b * 2 * CO + pt * CO);
-            if constexpr (CO == 32) {
-                asm volatile(
-                    "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,"
-                    "%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
-                    : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-                      "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
-                      "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
-                      "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
-                      "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-                    : "r"(taddr));
-            } else {
+            uint32_t r[CH];
+            const uint32_t taddr = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(b * 2 * CO + pt * CO + h * CH);
+            if constexpr (CH == 16) {
                 asm volatile(
                     "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
                     "[%16];\n"
@@ -415,17 +440,30 @@ __global__ void __launch_bounds__(128, 1) conv_umma_kernel(int nx, int ny, int n
                       "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
                       "=r"(r[15])
                     : "r"(taddr));
+            } else {
+                asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];\n"
+                             : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+                               "=r"(r[7])
+                             : "r"(taddr));
             }
             asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
             if (yy < ny) {
                 const size_t node = ((size_t)p * ny + yy) * nx + x0 + pt * 8 + (mrow % 8);
-                float4 *dst = reinterpret_cast<float4 *>(z + node * CO);
+                float v[CH];
 #pragma unroll
-                for (int o = 0; o < CO; o += 4)
-                    dst[o / 4] = make_float4(__uint_as_float(r[o]) + (bias ? bias[o] : 0.0f),
-                                             __uint_as_float(r[o + 1]) + (bias ? bias[o + 1] : 0.0f),
-                                             __uint_as_float(r[o + 2]) + (bias ? bias[o + 2] : 0.0f),
-                                             __uint_as_float(r[o + 3]) + (bias ? bias[o + 3] : 0.0f));
+                for (int o = 0; o < CH; ++o) v[o] = __uint_as_float(r[o]) + sbias[h * CH + o];
+                float4 *dst = reinterpret_cast<float4 *>(z + node * CO + h * CH);
+#pragma unroll
+                for (int o = 0; o < CH; o += 4) dst[o / 4] = make_float4(v[o], v[o + 1], v[o + 2], v[o + 3]);
+                if (act) {   // the next layer's input, silu(z) in BF16
+                    uint4 *ad = reinterpret_cast<uint4 *>(act + node * CO + h * CH);
+#pragma unroll
+                    for (int o = 0; o < CH; o += 8)
+                        ad[o / 8] = make_uint4(pack_bf16(silu(v[o]), silu(v[o + 1])),
+                                               pack_bf16(silu(v[o + 2]), silu(v[o + 3])),
+                                               pack_bf16(silu(v[o + 4]), silu(v[o + 5])),
+                                               pack_bf16(silu(v[o + 6]), silu(v[o + 7])));
+                }
             }
         }
     };
@@ -434,39 +472,44 @@ __global__ void __launch_bounds__(128, 1) conv_umma_kernel(int nx, int ny, int n
     for (int zc = z0; zc < z1 && ok; ++zc) {
         const int b = (zc - z0) & 1;
         if (tid == 0) {   // the MMAs of plane zc
-#pragma unroll 1
+            const uint32_t a_lo[3] = {(uint32_t)umma_desc(smem_addr(slot(zc - 1)), lbo_a, sbo_a),
+                                      (uint32_t)umma_desc(smem_addr(slot(zc)), lbo_a, sbo_a),
+                                      (uint32_t)umma_desc(smem_addr(slot(zc + 1)), lbo_a, sbo_a)};
+#pragma unroll
             for (int pt = 0; pt < 2; ++pt) {
                 const uint32_t dt = tmem + (uint32_t)(b * 2 * CO + pt * CO);
-                uint32_t acc = 0;
-#pragma unroll 1
+#pragma unroll
                 for (int k = 0; k < 27; ++k) {
                     const int dz = k / 9 - 1, dy = (k / 3) % 3 - 1, dx = k % 3 - 1;
-                    const uint32_t abase = smem_addr(slot(zc + dz)) + (uint32_t)(((1 + dy) * UM_HX + pt * 8 + 1 + dx) * 16);
+                    const uint32_t aoff = (uint32_t)((1 + dy) * UM_HX + pt * 8 + 1 + dx);   // 16-byte units
 #pragma unroll
                     for (int cb = 0; cb < CB; ++cb) {
-                        const uint64_t da = umma_desc(abase + (uint32_t)(2 * cb) * lbo_a, lbo_a, sbo_a);
-                        const uint64_t db = umma_desc(sw_addr + (uint32_t)((k * CB + cb) * 2 * CO * 16), lbo_b, sbo_b);
-                        umma_bf16(dt, da, db, idesc, acc);
-                        acc = 1;
+                        const uint64_t da = ((uint64_t)a_hi << 32) | (a_lo[dz + 1] + aoff + (uint32_t)(2 * cb) * (lbo_a >> 4));
+                        const uint64_t db =
+                            ((uint64_t)b_hi << 32) | (b_lo + (uint32_t)((k * CB + cb) * 2 * CO));   // 16-byte units
+                        umma_bf16(dt, da, db, idesc, (k | cb) != 0 ? 1u : 0u);
                     }
                 }
             }
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
                 smem_addr(&mbar[b])));
         }
-        if (zc > z0) {   // plane zc - 1: wait for its MMAs, read back (a warp decides as one)
-            const bool good = __all_sync(0xffffffffu, mbar_wait(smem_addr(&mbar[1 - b]), phase[1 - b]));
+        bool good = true;
+        if (zc > z0) {   // plane zc - 1: wait for its MMAs (a warp decides as one)
+            good = __all_sync(0xffffffffu, mbar_wait(smem_addr(&mbar[1 - b]), phase[1 - b]));
             phase[1 - b] ^= 1u;
             asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+        }
+        // refill: plane zc + 4 into the slot of plane zc - 2, which only plane zc - 1's MMAs read
+        if (good && zc + UM_AHEAD <= z1) um_load_plane<CB>(slot(zc + UM_AHEAD), in, nx, ny, nz, x0, y0, zc + UM_AHEAD);
+        cp_async_commit();
+        if (zc > z0) {   // read back plane zc - 1
             if (good)
                 epilogue(zc - 1, 1 - b);
             else if (lane == 0)
                 abort_flag = 1;
         }
-        // refill: plane zc + 2 into the slot of plane zc - 2 (read only by plane zc - 1's MMAs)
-        if (zc + 2 <= z1) um_load_plane<CB>(slot(zc + 2), in, nx, ny, nz, x0, y0, zc + 2);
-        cp_async_commit();
-        cp_async_wait_all();
+        cp_async_wait_group<UM_AHEAD - 2>();   // plane zc + 2, read by the next plane's MMAs
         asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
         asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
         __syncthreads();
@@ -506,12 +549,6 @@ __global__ void pack_weights_umma_kernel(const float *__restrict__ W, int cout, 
     out[idx] = __float2bfloat16_rn(v);
 }
 
-__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi)
-{
-    const uint32_t l = __bfloat16_as_ushort(__float2bfloat16_rn(lo));
-    const uint32_t h = __bfloat16_as_ushort(__float2bfloat16_rn(hi));
-    return l | (h << 16);
-}
 
 // Fragment-ordered BF16 weights of one layer from the FP32 master W[o][i][k] (cout x cin x 27).
 // TRANSPOSE builds the weights of the backward pass with respect to the input,
@@ -545,7 +582,6 @@ __global__ void pack_weights_kernel(const float *__restrict__ W, int cout, int c
 
 // ---- elementwise stages -------------------------------------------------------------------
 
-__device__ __forceinline__ float silu(float z) { return z / (1.0f + __expf(-z)); }
 __device__ __forceinline__ float silu_grad(float z)
 {
     const float s = 1.0f / (1.0f + __expf(-z));
@@ -567,6 +603,12 @@ __global__ void pack_input_kernel(const float *__restrict__ x, int N, __nv_bfloa
     uint4 *d = reinterpret_cast<uint4 *>(a0 + (size_t)n * 16);
     d[0] = make_uint4(v[0], v[1], v[2], v[3]);
     d[1] = make_uint4(v[4], v[5], v[6], v[7]);
+}
+
+// bpad[o] = bias[o] for o < cout, 0 up to 32 (one block of 32 threads)
+__global__ void pad_bias_kernel(const float *__restrict__ bias, int cout, float *__restrict__ bpad)
+{
+    bpad[threadIdx.x] = (int)threadIdx.x < cout ? bias[threadIdx.x] : 0.0f;
 }
 
 // a = silu(z), z and a channel-last with C channels (count = N * C)
@@ -865,6 +907,7 @@ struct lbm_cnn {
     uint4 *wt[tslb::NLAYER] = {};        // transposed fragments (layers 2..4)
     __nv_bfloat16 *wu[tslb::NLAYER] = {};   // tcgen05 operand layout of the weights
     __nv_bfloat16 *wut[tslb::NLAYER] = {};  // ... and of the transposed weights (layers 2..4)
+    float *bpad = nullptr;               // biases zero-padded to 32 channels per layer (repack)
     int *derr = nullptr;                 // set by a tensor-core kernel whose mbarrier wait expired
     __nv_bfloat16 *a[tslb::NLAYER] = {}; // layer inputs, channel-last BF16: a[0] [N][16], a[1..3] [N][32]
     float *z[tslb::NLAYER] = {};         // pre-activations, channel-last FP32 ([N][32], last [N][16])
@@ -877,8 +920,9 @@ struct lbm_cnn {
     long long adam_t = 0;
     int conv_blocks = 0;
     int sms = 0;
-    int conv_kernel = 1;                 // 0: tcgen05 / TMEM; 1: mma.sync from shared-memory tiles (default,
-                                         // fastest measured); 2: mma.sync from global memory
+    int conv_kernel = 0;                 // 0: tcgen05 / TMEM (default, fastest measured; SiLU fused into
+                                         // its epilogue); 1: mma.sync from shared-memory tiles; 2: mma.sync
+                                         // from global memory
 };
 
 namespace {
@@ -924,15 +968,20 @@ void free_cnn(lbm_cnn *c)
     cudaFree(c->ybuf);
     cudaFree(c->dsum);
     cudaFree(c->derr);
+    cudaFree(c->bpad);
     if (c->h_sum) cudaFreeHost(c->h_sum);
     delete c;
 }
 
 int frag_count(int mt, int cb) { return 27 * cb * mt * 32; }
 
-// forward fragments of every layer and transposed fragments of layers 2..4 from the master weights
+// forward fragments of every layer and transposed fragments of layers 2..4 from the master weights,
+// and the biases zero-padded to 32 channels per layer
 cudaError_t repack(lbm_cnn *c)
 {
+    for (int l = 0; l < tslb::NLAYER; ++l)
+        tslb::pad_bias_kernel<<<1, 32, 0, c->stream>>>(c->p + c->pofs[l] + tslb::wcount(l), tslb::COUT[l],
+                                                      c->bpad + 32 * l);
     for (int l = 0; l < tslb::NLAYER; ++l) {
         const int mt = COUTP[l] / 16, cb = CINP[l] / 16;
         const int n = frag_count(mt, cb);
@@ -956,31 +1005,10 @@ cudaError_t repack(lbm_cnn *c)
     return cudaGetLastError();
 }
 
+// the two mma.sync forms of the convolution (kernels 1 and 2)
 template <int MT, int CB>
-cudaError_t launch_conv(lbm_cnn *c, int layer, bool transpose, const __nv_bfloat16 *in, const float *bias, float *out)
+cudaError_t launch_conv_mma(lbm_cnn *c, const uint4 *wfrag, const __nv_bfloat16 *in, const float *bias, float *out)
 {
-    const uint4 *wfrag = transpose ? c->wt[layer] : c->wf[layer];
-    const __nv_bfloat16 *wpack = transpose ? c->wut[layer] : c->wu[layer];
-    if (c->conv_kernel == 0 && c->nx % tslb::UM_TX == 0) {   // tcgen05 / TMEM
-        constexpr int WB = 27 * CB * 2 * MT * 16 * 16;
-        const size_t smem = (size_t)((WB + 1023) / 1024) * 1024 + (size_t)tslb::UM_SLOTS * tslb::UmGeom<CB>::PLANE_BYTES;
-        static bool attr = false;
-        if (!attr) {
-            cudaError_t e = cudaFuncSetAttribute(tslb::conv_umma_kernel<MT, CB>,
-                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            if (e != cudaSuccess) return e;
-            attr = true;
-        }
-        const int tiles = (c->nx / tslb::UM_TX) * ((c->ny + tslb::UM_TY - 1) / tslb::UM_TY);
-        int nzc = c->sms / tiles;
-        if (nzc < 1) nzc = 1;
-        if (nzc > c->nz) nzc = c->nz;
-        const int zlen = (c->nz + nzc - 1) / nzc;
-        nzc = (c->nz + zlen - 1) / zlen;
-        tslb::conv_umma_kernel<MT, CB><<<dim3(tiles, nzc), 128, smem, c->stream>>>(c->nx, c->ny, c->nz, wpack, in, bias,
-                                                                                    out, zlen, c->derr);
-        return cudaGetLastError();
-    }
     if (c->conv_kernel <= 1) {   // mma.sync from shared-memory tiles
         const size_t smem = (size_t)frag_count(MT, CB) * sizeof(uint4) +
                             (size_t)tslb::CT_SLOTS * tslb::CtGeom<CB>::PLANE * sizeof(__nv_bfloat16);
@@ -1016,18 +1044,53 @@ cudaError_t launch_conv(lbm_cnn *c, int layer, bool transpose, const __nv_bfloat
     return cudaGetLastError();
 }
 
+// out = conv(in) + bias (FP32, channel-last); with act non-null also act = silu(out) in BF16 (the
+// next layer's input; fused into the tcgen05 kernel's epilogue, a separate pass for the others).
+template <int MT, int CB>
+cudaError_t launch_conv(lbm_cnn *c, int layer, bool transpose, const __nv_bfloat16 *in, const float *bias, float *out,
+                        __nv_bfloat16 *act = nullptr)
+{
+    const uint4 *wfrag = transpose ? c->wt[layer] : c->wf[layer];
+    const __nv_bfloat16 *wpack = transpose ? c->wut[layer] : c->wu[layer];
+    if (c->conv_kernel == 0 && c->nx % tslb::UM_TX == 0) {   // tcgen05 / TMEM
+        constexpr int WB = 27 * CB * 2 * MT * 16 * 16;
+        const size_t smem = (size_t)((WB + 1023) / 1024) * 1024 + (size_t)tslb::UM_SLOTS * tslb::UmGeom<CB>::PLANE_BYTES;
+        static bool attr = false;
+        if (!attr) {
+            cudaError_t e = cudaFuncSetAttribute(tslb::conv_umma_kernel<MT, CB>,
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+            attr = true;
+        }
+        const int tiles = (c->nx / tslb::UM_TX) * ((c->ny + tslb::UM_TY - 1) / tslb::UM_TY);
+        int nzc = c->sms / tiles;
+        if (nzc < 1) nzc = 1;
+        if (nzc > c->nz) nzc = c->nz;
+        const int zlen = (c->nz + nzc - 1) / nzc;
+        nzc = (c->nz + zlen - 1) / zlen;
+        tslb::conv_umma_kernel<MT, CB><<<dim3(tiles, nzc), tslb::UM_THREADS, smem, c->stream>>>(
+            c->nx, c->ny, c->nz, wpack, in, bias, out, act, zlen, c->derr);
+        return cudaGetLastError();
+    }
+    cudaError_t e = launch_conv_mma<MT, CB>(c, wfrag, in, bias, out);
+    if (e == cudaSuccess && act) {
+        const size_t cnt = (size_t)c->N * MT * 16;
+        tslb::silu_kernel<<<(unsigned)((cnt + 255) / 256), 256, 0, c->stream>>>(out, cnt, act);
+        e = cudaGetLastError();
+    }
+    return e;
+}
+
 cudaError_t forward(lbm_cnn *c, const float *x)
 {
     const int N = c->N;
     cudaError_t e;
     tslb::pack_input_kernel<<<(N + 255) / 256, 256, 0, c->stream>>>(x, N, c->a[0]);
-    if ((e = launch_conv<2, 1>(c, 0, false, c->a[0], c->p + c->pofs[0] + tslb::wcount(0), c->z[0])) != cudaSuccess)
-        return e;
+    // z_l = conv_l(a_l) + b_l and a_{l+1} = silu(z_l); biases zero-padded to the padded channels
+    if ((e = launch_conv<2, 1>(c, 0, false, c->a[0], c->bpad, c->z[0], c->a[1])) != cudaSuccess) return e;
     for (int l = 1; l < tslb::NLAYER; ++l) {
-        const size_t cnt = (size_t)N * 32;
-        tslb::silu_kernel<<<(unsigned)((cnt + 255) / 256), 256, 0, c->stream>>>(c->z[l - 1], cnt, c->a[l]);
-        const float *bias = c->p + c->pofs[l] + tslb::wcount(l);
-        e = l < 3 ? launch_conv<2, 2>(c, l, false, c->a[l], bias, c->z[l])
+        const float *bias = c->bpad + 32 * l;
+        e = l < 3 ? launch_conv<2, 2>(c, l, false, c->a[l], bias, c->z[l], c->a[l + 1])
                   : launch_conv<1, 2>(c, l, false, c->a[l], bias, c->z[l]);
         if (e != cudaSuccess) return e;
     }
@@ -1124,6 +1187,7 @@ lbm_status lbm_cnn_create(int nx, int ny, int nz, unsigned long long seed, void 
         {(void **)&c->dzb, N * 32 * 2},                {(void **)&c->xbuf, 5 * N * sizeof(float)},
         {(void **)&c->ybuf, 4 * N * sizeof(float)},
         {(void **)&c->dsum, (size_t)(c->loss_blocks + 1) * sizeof(double)},
+        {(void **)&c->bpad, (size_t)tslb::NLAYER * 32 * sizeof(float)},
     };
     cudaError_t err = cudaSuccess;
     for (auto &a : allocs)
