@@ -209,6 +209,14 @@ long long lbm_step_count(const lbm_ctx *ctx);
  * LBM_ERR_ARG for other values, and for path 2 with any storage but LBM_FP32. */
 lbm_status lbm_set_path(lbm_ctx *ctx, int path);
 
+/* Advection term of the Allen–Cahn update.  0 (default): flux form div(ubar phi), which conserves
+ * sum phi to rounding (the reading the library applies everywhere; it equals ubar . grad(phi) when
+ * div ubar = 0).  1: the paper's literal form ubar . G[phi] (Section "Model extension": the
+ * advection term of the phase-field equation and its FTCS update), whose sum phi drifts by
+ * -sum ubar . G[phi] per step; for studying that drift.  Form 1 runs on path 1 only: LBM_ERR_ARG
+ * unless the path is 1, and lbm_set_path rejects paths 0 and 2 while form 1 is set. */
+lbm_status lbm_set_advection(lbm_ctx *ctx, int form);
+
 /* Work split of the z-marching kernels (paths 0 and 2): the number of z chunks each 32 x 8
  * column tile is cut into.  0 restores the library's default.
  * Results are bit-identical for every value:

@@ -37,6 +37,7 @@ class _Params(ctypes.Structure):
         ("gravity", ctypes.c_double * 3),
         ("rho_ref", ctypes.c_double),
         ("body", ctypes.c_double * 3),
+        ("advect", ctypes.c_int),
     ]
 
 
@@ -57,6 +58,7 @@ class Params:
     gravity: tuple = (0.0, 0.0, 0.0)
     rho_ref: float = 1.0
     body: tuple = (0.0, 0.0, 0.0)
+    advect: int = 0          # 0: flux form div(ubar phi) (reading R4); 1: literal ubar . grad(phi)
 
     @property
     def shape(self):
@@ -74,6 +76,7 @@ class Params:
         p.gravity[:] = list(self.gravity)
         p.rho_ref = self.rho_ref
         p.body[:] = list(self.body)
+        p.advect = int(self.advect)
         return p
 
 

@@ -38,7 +38,8 @@
  *   R1  S_i uses the acceleration a = F/rho; u = sum f c + a/2.
  *   R2  Laplacian  L[psi] = (2/cs^2) sum_{i!=0} w_i (psi(x+c_i) - psi(x)).
  *   R3  collision  g = fbar^eq + (1-omega) f^neq + S  with fbar^eq = f^eq - S/2.
- *   R4  advection in flux form div(ubar phi).
+ *   R4  advection in flux form div(ubar phi) (advect = 0, the default); advect = 1 takes the
+ *       literal form ubar . G[phi] of the paper's update, which does not conserve sum phi.
  *   R5  n = grad(phi) / max(|grad(phi)|, 1e-12).
  *   R6  F^nu uses f^eq(p*, ubar^n) (lagged velocity); contraction [..]_{ab} d_b rho.
  *   R7  f^neq_i = w_i [H2_i:A/(2cs^4) + H3_i:a3/(6cs^6)],  a3 = sym(u (x) A).
@@ -71,6 +72,7 @@ typedef struct {
     double gravity[3];     /* gravitational acceleration vector */
     double rho_ref;        /* reference density of the buoyancy force */
     double body[3];        /* uniform body-force density */
+    int advect;            /* 0: flux form div(ubar phi); 1: literal form ubar . grad(phi) */
 } oracle_params;
 
 /* ------------------------------------------------------------------------------------------ */
@@ -419,7 +421,7 @@ void oracle_ac_update(const oracle_params *P, const double *phi, const double *u
                 double den = mag > 1e-12 ? mag : 1e-12;
                 double p = phi[k];
                 for (int a = 0; a < 3; ++a)
-                    V[a * N + k] = ubar[a * N + k] * p + kac * fmax(p * (1.0 - p), 0.0) * g[a] / den;
+                    V[a * N + k] = (P->advect ? 0.0 : ubar[a * N + k] * p) + kac * fmax(p * (1.0 - p), 0.0) * g[a] / den;
             }
 
     #pragma omp parallel for collapse(2) schedule(static)
@@ -427,7 +429,13 @@ void oracle_ac_update(const oracle_params *P, const double *phi, const double *u
         for (int y = 0; y < P->ny; ++y)
             for (int x = 0; x < P->nx; ++x) {
                 long k = node(P, x, y, z);
-                phi_new[k] = phi[k] - div_at(P, V, x, y, z) + P->mobility * lap_at(P, phi, x, y, z);
+                double adv = 0.0;   /* the literal advection term ubar . G[phi] */
+                if (P->advect) {
+                    double g[3];
+                    grad_at(P, phi, x, y, z, g);
+                    for (int a = 0; a < 3; ++a) adv += ubar[a * N + k] * g[a];
+                }
+                phi_new[k] = phi[k] - adv - div_at(P, V, x, y, z) + P->mobility * lap_at(P, phi, x, y, z);
             }
     free(V);
 }

@@ -86,6 +86,7 @@ struct lbm_ctx {
     int path = 0;
     int split = 0;
     int storage = LBM_FP32;
+    int advect = 0;                   // 1: literal advection u . grad(phi) (path 1)
 };
 
 namespace {
@@ -253,7 +254,19 @@ lbm_status lbm_set_path(lbm_ctx *ctx, int path)
         return fail(LBM_ERR_ARG, "path must be 0 (two kernels), 1 (three kernels) or 2 (one fused kernel)");
     if (path == 2 && ctx->storage != LBM_FP32)
         return fail(LBM_ERR_ARG, "16-bit and moment storage run on paths 0 and 1 only");
+    if (path != 1 && ctx->advect)
+        return fail(LBM_ERR_ARG, "the literal advection form runs on path 1 only");
     ctx->path = path;
+    return LBM_OK;
+}
+
+lbm_status lbm_set_advection(lbm_ctx *ctx, int form)
+{
+    if (!ctx) return fail(LBM_ERR_ARG, "context is NULL");
+    if (form != 0 && form != 1) return fail(LBM_ERR_ARG, "advection form must be 0 (flux) or 1 (literal)");
+    if (form == 1 && ctx->path != 1)
+        return fail(LBM_ERR_ARG, "the literal advection form runs on path 1 only (lbm_set_path(ctx, 1) first)");
+    ctx->advect = form;
     return LBM_OK;
 }
 
@@ -305,7 +318,7 @@ lbm_status lbm_step(lbm_ctx *ctx, int nsteps)
             ctx->w_valid = true;
         }
         tslb::StepArgs args{ctx->g[a], ctx->g[b], ctx->phi[a], ctx->phi[b], ctx->u[a], ctx->u[b], ctx->flux,
-                            ctx->storage, ctx->pst[a], ctx->pst[b]};
+                            ctx->storage, ctx->pst[a], ctx->pst[b], ctx->advect};
         cudaError_t e = ctx->path == 0   ? tslb::launch_step_split(ctx->G, ctx->P, args, ctx->split, ctx->stream)
                          : ctx->path == 2 ? tslb::launch_step_fused2(ctx->G, ctx->P, args, ctx->split, ctx->stream)
                                           : tslb::launch_step_unfused(ctx->G, ctx->P, args, ctx->stream);

@@ -20,8 +20,9 @@ __device__ __forceinline__ bool node_coords(const Grid &G, int &x, int &y, int &
     return x < G.nx;
 }
 
+// advect = 1 leaves the advective flux u phi out of W (the update adds u . grad(phi) instead)
 __global__ void __launch_bounds__(128) ac_flux_kernel(Grid G, Phys P, const float *__restrict__ phi,
-                                                      const float *__restrict__ u, float *__restrict__ W)
+                                                      const float *__restrict__ u, float *__restrict__ W, int advect)
 {
     int x, y, z;
     if (!node_coords(G, x, y, z)) return;
@@ -35,13 +36,22 @@ __global__ void __launch_bounds__(128) ac_flux_kernel(Grid G, Phys P, const floa
     const int k = n.zo[1] + n.yo[1] + x;
     const float p = ps[13];
     const float s = P.kac * fmaxf(p * (1.0f - p), 0.0f) * inv;
-    W[k] = fmaf(u[k], p, s * gx);
-    W[G.N + k] = fmaf(u[G.N + k], p, s * gy);
-    W[2 * G.N + k] = fmaf(u[2 * G.N + k], p, s * gz);
+    if (advect) {
+        W[k] = s * gx;
+        W[G.N + k] = s * gy;
+        W[2 * G.N + k] = s * gz;
+    } else {
+        W[k] = fmaf(u[k], p, s * gx);
+        W[G.N + k] = fmaf(u[G.N + k], p, s * gy);
+        W[2 * G.N + k] = fmaf(u[2 * G.N + k], p, s * gz);
+    }
 }
 
+// phi^{n+1} = phi - div W + D lap(phi), and with advect = 1 also - ubar . grad(phi) (the literal
+// advection term; W then holds the sharpening flux alone)
 __global__ void __launch_bounds__(128) ac_update_kernel(Grid G, Phys P, const float *__restrict__ phi,
-                                                        const float *__restrict__ W, float *__restrict__ phi_out)
+                                                        const float *__restrict__ W, const float *__restrict__ u,
+                                                        int advect, float *__restrict__ phi_out)
 {
     int x, y, z;
     if (!node_coords(G, x, y, z)) return;
@@ -59,7 +69,10 @@ __global__ void __launch_bounds__(128) ac_update_kernel(Grid G, Phys P, const fl
     }
     float gx, gy, gz, lap;
     grad_lap27(ps, gx, gy, gz, lap);
-    phi_out[n.zo[1] + n.yo[1] + x] = ps[13] - div + P.mob * lap;
+    const int k = n.zo[1] + n.yo[1] + x;
+    float p0 = ps[13];
+    if (advect) p0 -= fmaf(u[k], gx, fmaf(u[G.N + k], gy, u[2 * G.N + k] * gz));
+    phi_out[k] = p0 - div + P.mob * lap;
 }
 
 // Lattice Boltzmann update, one thread per node (x from the thread, y and z from the block); the
@@ -218,8 +231,8 @@ dim3 node_grid(const Grid &G) { return dim3((G.nx + 127) / 128, G.ny, G.nz); }
 cudaError_t launch_step_unfused(const Grid &G, const Phys &P, const StepArgs &a, cudaStream_t s)
 {
     const dim3 grid = node_grid(G);
-    ac_flux_kernel<<<grid, 128, 0, s>>>(G, P, a.phi_in, a.u_in, a.flux);
-    ac_update_kernel<<<grid, 128, 0, s>>>(G, P, a.phi_in, a.flux, a.phi_out);
+    ac_flux_kernel<<<grid, 128, 0, s>>>(G, P, a.phi_in, a.u_in, a.flux, a.advect);
+    ac_update_kernel<<<grid, 128, 0, s>>>(G, P, a.phi_in, a.flux, a.u_in, a.advect, a.phi_out);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     // the scratch flux is consumed: the lattice Boltzmann kernel leaves W^{n+1} in it

@@ -21,6 +21,7 @@ struct StepArgs {
     int storage = 0;       // 0 FP32, 1 BF16, 2 FP16, 3 moments (paths 0 and 1 only for 1..3)
     const float *p_in = nullptr;   // stored p* of the 16-bit formats
     float *p_out = nullptr;
+    int advect = 0;                // 1: literal advection u . grad(phi) (unfused path only)
 };
 
 // One step S^n -> S^{n+1}.  zchunks = z chunks per column tile of the marching kernels (<= 0:

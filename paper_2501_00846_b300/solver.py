@@ -114,6 +114,7 @@ def load(path: str = LIB_PATH):
         "lbm_step_count": ([vp], ll),
         "lbm_set_path": ([vp, i], i),
         "lbm_set_split": ([vp, i], i),
+        "lbm_set_advection": ([vp, i], i),
         "lbm_run_phase": ([vp, i, i], i),
         "lbm_destroy": ([vp], None),
         "lbm_status_string": ([i], ctypes.c_char_p),
@@ -249,6 +250,10 @@ class Solver:
 
     def set_path(self, path: int):
         _check(load().lbm_set_path(self._ctx, int(path)))
+
+    def set_advection(self, form: int):
+        """0: flux form div(ubar phi) (default); 1: literal ubar . grad(phi), path 1 only."""
+        _check(load().lbm_set_advection(self._ctx, int(form)))
 
     def set_split(self, split: int):
         """z chunks per column tile of the marching kernels (paths 0 and 2); 0 = default."""

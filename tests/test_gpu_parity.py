@@ -332,3 +332,33 @@ def test_laplace_law_on_gpu():
     ratio = (o["p_liq"] - o["p_gas"]) / (2 * wl.sigma / reff)
     print(f"Laplace 48^3 R=12: dp ratio {ratio:.4f}, umax {o['umax']:.2e}")
     assert abs(ratio - 1) < 0.05
+
+
+def test_literal_advection_form_on_path_1():
+    """lbm_set_advection(ctx, 1): the paper's literal ubar . G[phi] advection on the unfused path,
+    against the oracle with the same form (advect = 1), 100 steps on the noise droplet, whose
+    velocity field is not divergence-free.  Sum phi is no longer an invariant: the GPU's drift
+    follows the oracle's.  The form is refused on paths 0 and 2."""
+    wl = inputs.static_droplet(L=32, radius=8.0, noise=0.02, seed=17)
+    phi0, u0, ps = _f32(wl.phi0()), _f32(wl.u0()), _pstar0(wl)
+    P = oracle.Params(**wl.params())
+    P.advect = 1
+    ref = oracle.run(P, oracle.init(P, phi0.astype(np.float64), u0.astype(np.float64),
+                                    None if ps is None else ps.astype(np.float64)), 100)
+    with solver.Solver(**wl.params()) as s:
+        with pytest.raises(solver.LbmError):
+            s.set_advection(1)            # path 0
+        s.set_path(1)
+        s.set_advection(1)
+        for path in (0, 2):
+            with pytest.raises(solver.LbmError):
+                s.set_path(path)
+        s.init_fields(phi0, u0, ps)
+        s.step(100)
+        phi, u, p = s.read_fields()
+    _assert_parity((phi, u, p), P, ref, "literal advection path 1")
+    drift_o = ref.phi.sum() - phi0.astype(np.float64).sum()
+    drift_g = phi.astype(np.float64).sum() - phi0.astype(np.float64).sum()
+    print(f"sum phi drift over 100 steps: oracle {drift_o:.6e}, GPU {drift_g:.6e}")
+    assert abs(drift_o) > 1e-4
+    assert abs(drift_g - drift_o) <= 1e-3 * abs(drift_o) + 1e-4

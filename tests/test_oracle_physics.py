@@ -191,3 +191,40 @@ def test_sharpening_weight_vanishes_outside_unit_interval():
     np.testing.assert_allclose(oracle.ac_update(P, below, zero_u), below + 0.1 * oracle.lap(P, below), atol=1e-15)
     inside = 0.5 + 0.1 * rng.random(P.shape)
     assert np.abs(oracle.ac_update(P, inside, zero_u) - (inside + 0.1 * oracle.lap(P, inside))).max() > 1e-4
+
+
+def _grad27(psi):
+    """3 sum_i w_i c_i psi(x + c_i) on a periodic box, written out with np.roll (psi[z, y, x])."""
+    g = np.zeros((3,) + psi.shape)
+    w1 = {-1: 1.0 / 6.0, 0: 2.0 / 3.0, 1: 1.0 / 6.0}
+    for cz in (-1, 0, 1):
+        for cy in (-1, 0, 1):
+            for cx in (-1, 0, 1):
+                w = w1[cx] * w1[cy] * w1[cz]
+                s = np.roll(psi, shift=(-cz, -cy, -cx), axis=(0, 1, 2))
+                g[0] += 3 * w * cx * s
+                g[1] += 3 * w * cy * s
+                g[2] += 3 * w * cz * s
+    return g
+
+
+def test_literal_advection_form():
+    """Reading R4 and its alternative.  The literal update phi - ubar . G[phi] equals the flux form
+    phi - G . (ubar phi) when ubar is uniform (G is linear), and otherwise changes sum phi by
+    exactly -sum ubar . G[phi] per step (every other term telescopes)."""
+    L = 12
+    base = dict(rho_l=1.0, rho_g=0.1, mu_l=0.1, mu_g=0.01, sigma=0.01)
+    phi = inputs.sphere_phi(L, L, L, (5.3, 6.1, 5.7), 3.5, 4.0, periodic=(True, True, True))
+    P0, P1 = oracle.Params(L, L, L, advect=0, **base), oracle.Params(L, L, L, advect=1, **base)
+
+    uni = np.zeros((3,) + P0.shape)
+    uni[0], uni[1], uni[2] = 0.013, -0.007, 0.021
+    a, b = oracle.ac_update(P0, phi, uni), oracle.ac_update(P1, phi, uni)
+    assert np.abs(a - b).max() < 1e-15
+
+    u = inputs.fourier_velocity(L, L, L, amplitude=0.02, seed=11)   # not divergence-free
+    a, b = oracle.ac_update(P0, phi, u), oracle.ac_update(P1, phi, u)
+    assert abs(a.sum() - phi.sum()) < 1e-12 * phi.sum()
+    drift = -(u * _grad27(phi)).sum()
+    assert abs(drift) > 1e-4
+    assert abs((b.sum() - phi.sum()) - drift) < 1e-12 * phi.sum()
