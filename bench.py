@@ -44,7 +44,7 @@ sys.path.insert(0, ROOT)
 #   16-bit: 27 h (2 B) + P + phi + 3 ubar floats = 74 B, twice
 # (the Allen-Cahn flux W that this design carries from the lattice Boltzmann kernel of one step
 # to the Allen-Cahn kernel of the next, 24 B per node, is extra traffic and not counted here)
-STEP_BYTES = {"fp32": 248, "bf16": 148, "fp16": 148, "mom": 112}
+STEP_BYTES = {"fp32": 248, "bf16": 148, "fp16": 148, "mom": 112, "mom_bf16": 80, "mom_fp16": 80}
 # algorithmic bytes per node of each kernel that can dominate a step
 KERNEL_BYTES = {"lbm_kernel": 256,      # read 27 g + phi^{n+1} + 3 ubar, write 27 g + 3 ubar + 3 W
                 "fused2_kernel": 248,
@@ -52,9 +52,9 @@ KERNEL_BYTES = {"lbm_kernel": 256,      # read 27 g + phi^{n+1} + 3 ubar, write 
                 "lbm_mom_kernel": 120,  # read 13 moments + phi^{n+1}, write 13 moments + 3 W
                 "lbm_mom_plain_kernel": 120,
                 "ac_div_kernel": 20}    # read phi^n + 3 W^n, write phi^{n+1}
-STORES = {"fp32": 0, "bf16": 1, "fp16": 2, "mom": 3}
+STORES = {"fp32": 0, "bf16": 1, "fp16": 2, "mom": 3, "mom_bf16": 4, "mom_fp16": 5}
 # floats (or their 16-bit share) of one copy of the state per node: g + phi + u, or h/2 + P + phi + u
-STATE_FLOATS = {"fp32": 31, "bf16": 18.5, "fp16": 18.5, "mom": 14}
+STATE_FLOATS = {"fp32": 31, "bf16": 18.5, "fp16": 18.5, "mom": 14, "mom_bf16": 10, "mom_fp16": 10}
 FALLBACK_HBM_GBS = 6400.0
 METRIC = "MLUPS & % HBM peak: coupled LBM+Allen-Cahn step, FP32 vs BF16 store"
 # sources that define each step kernel's device code (the profile of a kernel is reused only while
@@ -72,8 +72,13 @@ KERNEL_SOURCES = {
 KERNEL_NAMES = {0: "lbm_kernel", 1: "lbm_kernel", 2: "fused2_kernel"}
 
 
+# algorithmic bytes per node and launch of the moment kernel with 16-bit a and B: read p* + 5 packed
+# words + 3 u + phi^{n+1}, write p* + 5 words + 3 u + 3 W
+MOM16_KERNEL_BYTES = 88
+
+
 def kernel_name(path, store):
-    if store == "mom":
+    if store.startswith("mom"):
         return "lbm_mom_kernel" if path == 0 else "lbm_mom_plain_kernel"
     if store != "fp32":
         return "lbm16_kernel" if path == 0 else "lbm_kernel"
@@ -106,6 +111,8 @@ def measured_traffic(kernel, wl_name, nodes, store="fp32"):
     if kernel not in KERNEL_SOURCES:
         return None
     tag = kernel if store in ("fp32", "mom") else f"{kernel}_{store}"
+    if store in ("mom_bf16", "mom_fp16"):
+        tag = f"{kernel}_{store[4:]}"
     path = os.path.join(ROOT, "profiles", f"{tag}_{wl_name}.txt")
     if not os.path.exists(path):
         return None
@@ -393,7 +400,7 @@ def main():
 
     def roofline(store, ms_step, kernel_ms):
         kernel = kernel_name(args.path, store)
-        kbytes = KERNEL_BYTES[kernel]
+        kbytes = MOM16_KERNEL_BYTES if store in ("mom_bf16", "mom_fp16") else KERNEL_BYTES[kernel]
         achieved = kbytes * N / (kernel_ms * 1e-3) / 1e9
         step_gbs = STEP_BYTES[store] * N / (ms_step * 1e-3) / 1e9
         return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
@@ -455,7 +462,8 @@ def main():
 
     value = world * N * args.steps / (ms_max * 1e-3) / 1e6
     dtype = {"fp32": "f32", "bf16": "f32 compute, bf16 store", "fp16": "f32 compute, f16 store",
-             "mom": "f32, moment store"}[args.store]
+             "mom": "f32, moment store", "mom_bf16": "f32 compute, bf16 moment store",
+             "mom_fp16": "f32 compute, f16 moment store"}[args.store]
     line = {
         "metric": METRIC,
         "value": value,

@@ -53,7 +53,9 @@ typedef enum {
     LBM_FP32 = 0,            /* populations stored as FP32 */
     LBM_BF16 = 1,            /* populations stored as BF16 deviations (see below) */
     LBM_FP16 = 2,            /* populations stored as FP16 deviations (see below) */
-    LBM_MOM = 3              /* moment-only storage: 13 FP32 moments per node (see below) */
+    LBM_MOM = 3,             /* moment-only storage: 13 FP32 moments per node (see below) */
+    LBM_MOM_BF16 = 4,        /* moment-only storage, the 9 deviation moments in BF16 (see below) */
+    LBM_MOM_FP16 = 5         /* moment-only storage, the 9 deviation moments in FP16 (see below) */
 } lbm_storage;
 
 /*
@@ -70,6 +72,13 @@ typedef enum {
  * is rejected.  lbm_get_state expands the moments to FP32 g; lbm_set_state projects g onto the
  * moments (p* = sum g, a = 2 (sum g c - u), B from sum g c c), which is exact up to rounding
  * for any state this library produced and the Hermite projection of any other.
+ *
+ * LBM_MOM_BF16 / LBM_MOM_FP16 keep p* and u in FP32 and store the 9 moments a and B, which vanish
+ * at equilibrium (deviations by construction), in BF16 or in FP16 as 2^12 times the value, packed
+ * per node in five 32-bit words (p*[N] FP32, then words[5 N]): 36 bytes of moments per node
+ * instead of 52.  Arithmetic stays FP32, and sum_i g_i = p* holds for
+ * any rounded a and B, so sum p* does not drift from the rounding.  lbm_set_state allocates a
+ * temporary FP32 buffer of 10 N floats for the projection with these two storages.
  */
 
 /*

@@ -126,8 +126,8 @@ lbm_status validate(const lbm_params *p)
     for (int a = 0; a < 3; ++a)
         if (!isfinite(p->gravity[a]) || !isfinite(p->body[a])) return fail(LBM_ERR_ARG, "forces must be finite");
     if (!isfinite(p->rho_ref)) return fail(LBM_ERR_ARG, "rho_ref must be finite");
-    if (p->storage != LBM_FP32 && p->storage != LBM_BF16 && p->storage != LBM_FP16 && p->storage != LBM_MOM)
-        return fail(LBM_ERR_ARG, "storage must be LBM_FP32, LBM_BF16, LBM_FP16 or LBM_MOM (got %d)", p->storage);
+    if (p->storage < LBM_FP32 || p->storage > LBM_MOM_FP16)
+        return fail(LBM_ERR_ARG, "storage must be an lbm_storage value (got %d)", p->storage);
     return LBM_OK;
 }
 
@@ -199,7 +199,7 @@ lbm_status lbm_create(const lbm_params *params, lbm_ctx **out)
 
     c->stream = (cudaStream_t)params->stream;   // NULL: the legacy default stream
     c->storage = params->storage;
-    const size_t g_bytes = c->storage == LBM_MOM    ? tslb::kMomArrays * N * sizeof(float)
+    const size_t g_bytes = c->storage >= LBM_MOM    ? tslb::mom_state_bytes(c->storage, N)
                            : c->storage == LBM_FP32 ? 27 * N * sizeof(float)
                                                     : 27 * N * 2;
     const size_t pst_bytes = c->storage == LBM_BF16 || c->storage == LBM_FP16 ? N * sizeof(float) : 0;
@@ -293,8 +293,8 @@ lbm_status lbm_init_fields(lbm_ctx *ctx, const float *phi, const float *u, const
     }
     if (ctx->storage == LBM_FP32)
         CUDA_TRY(tslb::launch_init(ctx->G, ps, ctx->u[c], ctx->g[c], ctx->stream));
-    else if (ctx->storage == LBM_MOM)
-        CUDA_TRY(tslb::launch_mom_init(ctx->G, ps, ctx->g[c], ctx->stream));
+    else if (ctx->storage >= LBM_MOM)
+        CUDA_TRY(tslb::launch_mom_init(ctx->G, ctx->storage, ps, ctx->g[c], ctx->stream));
     else
         CUDA_TRY(tslb::launch_init16(ctx->G, ctx->storage, ps, ctx->g[c], ctx->pst[c], ctx->stream));
     CUDA_TRY(tslb::launch_flux(ctx->G, ctx->P, ctx->phi[c], ctx->u[c], ctx->flux, ctx->stream));
@@ -347,9 +347,9 @@ lbm_status lbm_run_phase(lbm_ctx *ctx, int phase, int nrep)
     for (int r = 0; r < nrep; ++r) {
         cudaError_t e = phase == 0 ? tslb::launch_ac_div(ctx->G, ctx->P, ctx->phi[a], ctx->flux, ctx->phi[b], ctx->split,
                                                          ctx->stream)
-                         : ctx->storage == LBM_MOM
-                             ? tslb::launch_mom(ctx->G, ctx->P, ctx->g[a], ctx->u[a], ctx->phi[b], ctx->g[b], ctx->u[b],
-                                                ctx->flux, ctx->split, ctx->stream)
+                         : ctx->storage >= LBM_MOM
+                             ? tslb::launch_mom(ctx->G, ctx->P, ctx->storage, ctx->g[a], ctx->u[a], ctx->phi[b],
+                                                ctx->g[b], ctx->u[b], ctx->flux, ctx->split, ctx->stream)
                          : ctx->storage != LBM_FP32
                              ? tslb::launch_lbm16(ctx->G, ctx->P, ctx->storage, ctx->g[a], ctx->pst[a], ctx->phi[b],
                                                   ctx->u[a], ctx->g[b], ctx->pst[b], ctx->u[b], ctx->flux, ctx->stream)
@@ -430,13 +430,14 @@ lbm_status lbm_get_state(lbm_ctx *ctx, float *g, float *phi, float *u, int on_de
     const int c = ctx->cur;
     if (g && ctx->storage == LBM_FP32) {
         CUDA_TRY(cudaMemcpyAsync(g, ctx->g[c], 27 * N * sizeof(float), kind_out(on_device), ctx->stream));
-    } else if (g && ctx->storage == LBM_MOM) {
-        // g_i = w_i (g_i / w_i)(moments): straight into a device buffer, or 10 directions at a time
-        // through the idle moment buffer (10 N floats)
-        for (int i0 = 0; i0 < 27; i0 += on_device ? 27 : tslb::kMomArrays) {
-            const int ni = on_device ? 27 : (i0 + tslb::kMomArrays <= 27 ? tslb::kMomArrays : 27 - i0);
+    } else if (g && ctx->storage >= LBM_MOM) {
+        // g_i = w_i (g_i / w_i)(moments): straight into a device buffer, or a few directions at a time
+        // through the idle moment buffer
+        const int chunk = (int)(tslb::mom_state_bytes(ctx->storage, N) / (N * sizeof(float)));
+        for (int i0 = 0; i0 < 27; i0 += on_device ? 27 : chunk) {
+            const int ni = on_device ? 27 : (i0 + chunk <= 27 ? chunk : 27 - i0);
             float *dst = on_device ? g : ctx->g[1 - c];
-            CUDA_TRY(tslb::launch_mom_expand(ctx->G, ctx->g[c], ctx->u[c], i0, ni, dst, ctx->stream));
+            CUDA_TRY(tslb::launch_mom_expand(ctx->G, ctx->storage, ctx->g[c], ctx->u[c], i0, ni, dst, ctx->stream));
             if (!on_device)
                 CUDA_TRY(cudaMemcpyAsync(g + (size_t)i0 * N, dst, ni * N * sizeof(float), cudaMemcpyDeviceToHost,
                                          ctx->stream));
@@ -472,21 +473,38 @@ lbm_status lbm_set_state(lbm_ctx *ctx, const float *g, const float *phi, const f
     CUDA_TRY(cudaMemcpyAsync(ctx->u[c], u, 3 * N * sizeof(float), kind_in(on_device), ctx->stream));
     if (ctx->storage == LBM_FP32) {
         CUDA_TRY(cudaMemcpyAsync(ctx->g[c], g, 27 * N * sizeof(float), kind_in(on_device), ctx->stream));
-    } else if (ctx->storage == LBM_MOM) {
-        // population moments summed into the moment buffer (host input staged 10 directions at a
-        // time in the idle moment buffer), then converted to (p*, a, B) with u already in place
-        CUDA_TRY(cudaMemsetAsync(ctx->g[c], 0, tslb::kMomArrays * N * sizeof(float), ctx->stream));
-        for (int i0 = 0; i0 < 27; i0 += on_device ? 27 : tslb::kMomArrays) {
-            const int ni = on_device ? 27 : (i0 + tslb::kMomArrays <= 27 ? tslb::kMomArrays : 27 - i0);
+    } else if (ctx->storage >= LBM_MOM) {
+        // population moments summed into an FP32 accumulator (the moment buffer itself with FP32
+        // storage, else a temporary buffer; host input staged a few directions at a time in the idle
+        // moment buffer), then converted to (p*, a, B) with u already in place
+        float *acc = ctx->g[c];
+        if (ctx->storage != LBM_MOM) {
+            cudaError_t e = cudaMalloc(&acc, tslb::kMomArrays * N * sizeof(float));
+            if (e != cudaSuccess) {
+                cudaGetLastError();
+                return fail(e == cudaErrorMemoryAllocation ? LBM_ERR_OOM : LBM_ERR_CUDA,
+                            "cudaMalloc of the projection buffer failed: %s", cudaGetErrorString(e));
+            }
+        }
+        const int chunk = (int)(tslb::mom_state_bytes(ctx->storage, N) / (N * sizeof(float)));
+        cudaError_t e = cudaMemsetAsync(acc, 0, tslb::kMomArrays * N * sizeof(float), ctx->stream);
+        for (int i0 = 0; i0 < 27 && e == cudaSuccess; i0 += on_device ? 27 : chunk) {
+            const int ni = on_device ? 27 : (i0 + chunk <= 27 ? chunk : 27 - i0);
             const float *src = g;
             if (!on_device) {
-                CUDA_TRY(cudaMemcpyAsync(ctx->g[1 - c], g + (size_t)i0 * N, ni * N * sizeof(float),
-                                         cudaMemcpyHostToDevice, ctx->stream));
+                e = cudaMemcpyAsync(ctx->g[1 - c], g + (size_t)i0 * N, ni * N * sizeof(float), cudaMemcpyHostToDevice,
+                                    ctx->stream);
                 src = ctx->g[1 - c];
             }
-            CUDA_TRY(tslb::launch_mom_project(ctx->G, src, i0, ni, ctx->g[c], ctx->stream));
+            if (e == cudaSuccess) e = tslb::launch_mom_project(ctx->G, src, i0, ni, acc, ctx->stream);
         }
-        CUDA_TRY(tslb::launch_mom_finish(ctx->G, ctx->u[c], ctx->g[c], ctx->stream));
+        if (e == cudaSuccess) e = tslb::launch_mom_finish(ctx->G, ctx->storage, ctx->u[c], acc, ctx->g[c], ctx->stream);
+        if (acc != ctx->g[c]) {
+            const cudaError_t e2 = cudaStreamSynchronize(ctx->stream);
+            cudaFree(acc);
+            if (e == cudaSuccess) e = e2;
+        }
+        if (e != cudaSuccess) return fail(LBM_ERR_CUDA, "moment import failed: %s", cudaGetErrorString(e));
     } else {
         // P = sum g (mode 0), then h_i = g_i / w_i - P - f^eq_i(0, u) / w_i and P -= sum w_i h_i
         // (mode 1 + finish), with u already in place.  Host input is staged 13 directions at a

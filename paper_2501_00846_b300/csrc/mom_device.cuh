@@ -19,9 +19,15 @@
 //     T = B + 4.5 u u + 4.5 sym(u a),   sym(u a)_{ab} = (u_a a_b + u_b a_a) / 2
 // (fourth-order isotropy of D3Q27: sum w c_a c_b c_c c_d = (d_ab d_cd + d_ac d_bd + d_ad d_bc) / 9).
 //
-// Array layout of a moment state: m[q * N + node], q = 0 p*, 1..3 a, 4..9 B (xx yy zz xy xz yz);
-// u lives in the context's velocity arrays.
+// Array layout of a moment state: p*[node] in FP32, then the 9 deviation moments a (3) and
+// B (xx yy zz xy xz yz; 6).  FP32 storage: arrays d[q * N + node] (so m[q * N + node] for q = 0 p*,
+// 1..3 a, 4..9 B).  BF16 / FP16 storage (FP16 holding 2^12 times the value; a and B vanish at
+// equilibrium, so 16 bits round only the deviation, as for 16-bit populations): the 9 values of a
+// node packed in five 32-bit words, d16[10 node + q] with the tenth half zero, so a node's
+// moments move in five aligned 4-byte accesses.  u lives in the context's velocity arrays.
 #pragma once
+
+#include <string.h>
 
 #include "tslb_device.cuh"
 
@@ -38,19 +44,71 @@ struct MomPoly {
     float K0, K1, vx, vy, vz, b2xy, b2xz, b2yz;
 };
 
+// the deviation part of a moment state m (after the N FP32 values of p*)
+template <class S>
+__device__ __forceinline__ const typename S::T *mom_dev(const float *m, size_t N)
+{
+    return reinterpret_cast<const typename S::T *>(m + N);
+}
+template <class S>
+__device__ __forceinline__ typename S::T *mom_dev(float *m, size_t N)
+{
+    return reinterpret_cast<typename S::T *>(m + N);
+}
+
+constexpr int kMomWords = 5;   // 32-bit words of a node's packed 16-bit deviation moments
+
+// a 16-bit storage value from / to its bits
+template <class S>
+__device__ __forceinline__ float mom_h2f(unsigned short b)
+{
+    typename S::T t;
+    memcpy(&t, &b, 2);
+    return S::to_f(t);
+}
+template <class S>
+__device__ __forceinline__ uint32_t mom_f2h(float v)
+{
+    const typename S::T t = S::from_f(v);
+    unsigned short b;
+    memcpy(&b, &t, 2);
+    return b;
+}
+
+// the 9 deviation moments of a node from its packed words (16-bit storage)
+template <class S>
+__device__ __forceinline__ void mom_unpack(const uint32_t (&w)[kMomWords], Mom &r)
+{
+    r.ax = mom_h2f<S>(w[0] & 0xFFFF), r.ay = mom_h2f<S>(w[0] >> 16);
+    r.az = mom_h2f<S>(w[1] & 0xFFFF), r.bxx = mom_h2f<S>(w[1] >> 16);
+    r.byy = mom_h2f<S>(w[2] & 0xFFFF), r.bzz = mom_h2f<S>(w[2] >> 16);
+    r.bxy = mom_h2f<S>(w[3] & 0xFFFF), r.bxz = mom_h2f<S>(w[3] >> 16);
+    r.byz = mom_h2f<S>(w[4] & 0xFFFF);
+}
+
+template <class S = StoreF32>
 __device__ __forceinline__ Mom mom_load(const float *__restrict__ m, const float *__restrict__ u, size_t N, int k)
 {
     Mom r;
     r.ps = __ldg(m + k);
-    r.ax = __ldg(m + N + k);
-    r.ay = __ldg(m + 2 * N + k);
-    r.az = __ldg(m + 3 * N + k);
-    r.bxx = __ldg(m + 4 * N + k);
-    r.byy = __ldg(m + 5 * N + k);
-    r.bzz = __ldg(m + 6 * N + k);
-    r.bxy = __ldg(m + 7 * N + k);
-    r.bxz = __ldg(m + 8 * N + k);
-    r.byz = __ldg(m + 9 * N + k);
+    if constexpr (sizeof(typename S::T) == 4) {
+        const float *d = m + N;
+        r.ax = __ldg(d + k);
+        r.ay = __ldg(d + N + k);
+        r.az = __ldg(d + 2 * N + k);
+        r.bxx = __ldg(d + 3 * N + k);
+        r.byy = __ldg(d + 4 * N + k);
+        r.bzz = __ldg(d + 5 * N + k);
+        r.bxy = __ldg(d + 6 * N + k);
+        r.bxz = __ldg(d + 7 * N + k);
+        r.byz = __ldg(d + 8 * N + k);
+    } else {
+        const uint32_t *wp = reinterpret_cast<const uint32_t *>(m + N) + (size_t)kMomWords * k;
+        uint32_t w[kMomWords];
+#pragma unroll
+        for (int j = 0; j < kMomWords; ++j) w[j] = __ldg(wp + j);
+        mom_unpack<S>(w, r);
+    }
     r.ux = __ldg(u + k);
     r.uy = __ldg(u + N + k);
     r.uz = __ldg(u + 2 * N + k);
@@ -70,18 +128,36 @@ __device__ __forceinline__ Mom mom_from_collided(const Collided &c)
     return m;
 }
 
-__device__ __forceinline__ void mom_store(const Mom &r, float *__restrict__ m, float *__restrict__ u, size_t N, int k)
+// p* and the deviation moments of a node (not u)
+template <class S = StoreF32>
+__device__ __forceinline__ void mom_store_dev(const Mom &r, float *__restrict__ m, size_t N, int k)
 {
     m[k] = r.ps;
-    m[N + k] = r.ax;
-    m[2 * N + k] = r.ay;
-    m[3 * N + k] = r.az;
-    m[4 * N + k] = r.bxx;
-    m[5 * N + k] = r.byy;
-    m[6 * N + k] = r.bzz;
-    m[7 * N + k] = r.bxy;
-    m[8 * N + k] = r.bxz;
-    m[9 * N + k] = r.byz;
+    if constexpr (sizeof(typename S::T) == 4) {
+        float *d = m + N;
+        d[k] = r.ax;
+        d[N + k] = r.ay;
+        d[2 * N + k] = r.az;
+        d[3 * N + k] = r.bxx;
+        d[4 * N + k] = r.byy;
+        d[5 * N + k] = r.bzz;
+        d[6 * N + k] = r.bxy;
+        d[7 * N + k] = r.bxz;
+        d[8 * N + k] = r.byz;
+    } else {
+        uint32_t *wp = reinterpret_cast<uint32_t *>(m + N) + (size_t)kMomWords * k;
+        wp[0] = mom_f2h<S>(r.ax) | (mom_f2h<S>(r.ay) << 16);
+        wp[1] = mom_f2h<S>(r.az) | (mom_f2h<S>(r.bxx) << 16);
+        wp[2] = mom_f2h<S>(r.byy) | (mom_f2h<S>(r.bzz) << 16);
+        wp[3] = mom_f2h<S>(r.bxy) | (mom_f2h<S>(r.bxz) << 16);
+        wp[4] = mom_f2h<S>(r.byz);
+    }
+}
+
+template <class S = StoreF32>
+__device__ __forceinline__ void mom_store(const Mom &r, float *__restrict__ m, float *__restrict__ u, size_t N, int k)
+{
+    mom_store_dev<S>(r, m, N, k);
     u[k] = r.ux;
     u[N + k] = r.uy;
     u[2 * N + k] = r.uz;
@@ -193,12 +269,13 @@ __device__ __forceinline__ RawMoments raw_moments_hat(const float (&gh)[27])
 // The lattice Boltzmann update of one node once the raw moments of its streamed populations and
 // the gradient and Laplacian of phi^{n+1} are known: the collision, the new moment set, and the
 // Allen–Cahn flux of the new state (as lbm_node).
+template <class S = StoreF32>
 __device__ __forceinline__ void mom_finish(const RawMoments &r, float phi, float gx, float gy, float gz, float lap,
                                            float ubx, float uby, float ubz, const Phys &P, float *__restrict__ m_out,
                                            float *__restrict__ u_out, float *__restrict__ w_out, size_t N, int k)
 {
     const Collided c = collide_from_moments(r, phi, gx, gy, gz, lap, ubx, uby, ubz, P);
-    mom_store(mom_from_collided(c), m_out, u_out, N, k);
+    mom_store<S>(mom_from_collided(c), m_out, u_out, N, k);
     if (w_out) {
         float wx, wy, wz;
         ac_flux(phi, gx, gy, gz, c.ux, c.uy, c.uz, P, wx, wy, wz);

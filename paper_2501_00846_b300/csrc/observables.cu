@@ -51,7 +51,7 @@ __global__ void __launch_bounds__(kThreads) obs_partial_kernel(Grid G, double rh
         const int y = rem / G.nx;
         const int x = rem - y * G.nx;
         double ps = 0.0;
-        if (storage == LBM_MOM) {   // moment storage: p* is the first moment array
+        if (storage >= LBM_MOM) {   // moment storages: p* is the first moment array
             ps = ((const float *)gv)[k];
         } else if (pst) {   // 16-bit formats: p* = P + sum_i w_i h_i
             float s = pst[k];

@@ -85,13 +85,25 @@ struct HaloFetch {
     bool on;
 };
 
+// Copies of one halo node's moments into hb[q * kHalo + hn]: q = 0 p*, 1..9 the deviation moments
+// (FP32 storage: one value each; 16-bit storage: the node's 5 packed words in q = 1..5),
+// 10..12 u.
+template <class S>
 __device__ __forceinline__ void halo_fetch(const float *__restrict__ m_in, const float *__restrict__ u_in, size_t N,
                                            int plane, const HaloFetch &h, float *hb)
 {
     if (!h.on) return;
     const int k = plane + h.xy;
+    cp_async4(hb + threadIdx.x, m_in + k);
+    const float *d = m_in + N;
+    if constexpr (sizeof(typename S::T) == 4) {
 #pragma unroll
-    for (int q = 0; q < kMomArrays; ++q) cp_async4(hb + q * kHalo + threadIdx.x, m_in + q * N + k);
+        for (int q = 0; q < 9; ++q) cp_async4(hb + (1 + q) * kHalo + threadIdx.x, d + q * N + k);
+    } else {
+#pragma unroll
+        for (int j = 0; j < kMomWords; ++j)
+            cp_async4(hb + (1 + j) * kHalo + threadIdx.x, d + (size_t)kMomWords * k + j);
+    }
 #pragma unroll
     for (int a = 0; a < 3; ++a) cp_async4(hb + (kMomArrays + a) * kHalo + threadIdx.x, u_in + a * N + k);
 }
@@ -102,19 +114,27 @@ __device__ __forceinline__ void halo_fetch_phi(const float *__restrict__ phi, in
     if (h.on) cp_async4(ring + h.phi_pos, phi + plane + h.xy);
 }
 
+template <class S>
 __device__ __forceinline__ Mom halo_lds(const float *hb, int hn)
 {
     Mom r;
     r.ps = hb[hn];
-    r.ax = hb[kHalo + hn];
-    r.ay = hb[2 * kHalo + hn];
-    r.az = hb[3 * kHalo + hn];
-    r.bxx = hb[4 * kHalo + hn];
-    r.byy = hb[5 * kHalo + hn];
-    r.bzz = hb[6 * kHalo + hn];
-    r.bxy = hb[7 * kHalo + hn];
-    r.bxz = hb[8 * kHalo + hn];
-    r.byz = hb[9 * kHalo + hn];
+    if constexpr (sizeof(typename S::T) == 4) {
+        r.ax = hb[kHalo + hn];
+        r.ay = hb[2 * kHalo + hn];
+        r.az = hb[3 * kHalo + hn];
+        r.bxx = hb[4 * kHalo + hn];
+        r.byy = hb[5 * kHalo + hn];
+        r.bzz = hb[6 * kHalo + hn];
+        r.bxy = hb[7 * kHalo + hn];
+        r.bxz = hb[8 * kHalo + hn];
+        r.byz = hb[9 * kHalo + hn];
+    } else {
+        uint32_t w[kMomWords];
+#pragma unroll
+        for (int j = 0; j < kMomWords; ++j) w[j] = __float_as_uint(hb[(1 + j) * kHalo + hn]);
+        mom_unpack<S>(w, r);
+    }
     r.ux = hb[10 * kHalo + hn];
     r.uy = hb[11 * kHalo + hn];
     r.uz = hb[12 * kHalo + hn];
@@ -131,19 +151,19 @@ __device__ __forceinline__ void halo_item(const Mom &m, float *rm, float *r0, fl
     if (PZ == 2 || PZ == CZ) mom_emit<AX, SG, CZ>(m, rm, r0, rp, pos);
 }
 
-template <int PZ>
+template <class S, int PZ>
 __device__ __forceinline__ void mom_stage_halo(const float *hb, int row, int lane, float *rm, float *r0, float *rp)
 {
     if (row < 3) {
         if (PZ != 2 && PZ != row - 1) return;
-        const Mom m = halo_lds(hb, lane);
+        const Mom m = halo_lds<S>(hb, lane);
         const int pos = lane + 1;
         if (row == 0) halo_item<1, 1, -1, PZ>(m, rm, r0, rp, pos);
         else if (row == 1) halo_item<1, 1, 0, PZ>(m, rm, r0, rp, pos);
         else halo_item<1, 1, 1, PZ>(m, rm, r0, rp, pos);
     } else if (row < 6) {
         if (PZ != 2 && PZ != row - 4) return;
-        const Mom m = halo_lds(hb, MX + lane);
+        const Mom m = halo_lds<S>(hb, MX + lane);
         const int pos = (SY - 1) * SX + lane + 1;
         if (row == 3) halo_item<1, -1, -1, PZ>(m, rm, r0, rp, pos);
         else if (row == 4) halo_item<1, -1, 0, PZ>(m, rm, r0, rp, pos);
@@ -152,7 +172,7 @@ __device__ __forceinline__ void mom_stage_halo(const float *hb, int row, int lan
         if (row == 6 && PZ == 0) return;
         if (row == 7 && PZ != 2 && PZ != 0) return;
         const bool mirror = lane >= SY;
-        Mom m = halo_lds(hb, 2 * MX + lane);
+        Mom m = halo_lds<S>(hb, 2 * MX + lane);
         if (mirror) m = mom_mirror_x(m);
         const int pos = (mirror ? lane - SY : lane) * SX + (mirror ? SX - 1 - 2 * PS : 0);
         if (row == 6) {
@@ -203,7 +223,7 @@ __device__ __forceinline__ void phi_stencils(const PhiPartials &m, const PhiPart
     lap = fmaf(4.0f, c.A - phi0, (m.A - phi0) + (p.A - phi0));
 }
 
-template <bool WALL>
+template <bool WALL, class S>
 __global__ void __launch_bounds__(kMomThreads, 2)
     lbm_mom_kernel(Grid G, Phys P, const float *__restrict__ m_in, const float *__restrict__ u_in,
                    const float *__restrict__ phi_new, float *__restrict__ m_out, float *__restrict__ u_out,
@@ -262,17 +282,17 @@ __global__ void __launch_bounds__(kMomThreads, 2)
     Mom mo;
     const int zb = moment_plane(z0 - 1);
     if (zb >= 0) {
-        mo = mom_load(m_in, u_in, N, zb * nxy + own_xy);
-        halo_fetch(m_in, u_in, N, zb * nxy, h, hb);
+        mo = mom_load<S>(m_in, u_in, N, zb * nxy + own_xy);
+        halo_fetch<S>(m_in, u_in, N, zb * nxy, h, hb);
         cp_async_commit();
         cp_async_wait_all();
         __syncthreads();
         mom_emit<-1, 0, 1>(mo, rm_next, r0_next, rp_prev, own);
-        mom_stage_halo<1>(hb, row, lane, rm_next, r0_next, rp_prev);
+        mom_stage_halo<S, 1>(hb, row, lane, rm_next, r0_next, rp_prev);
         __syncthreads();
     }
-    mo = mom_load(m_in, u_in, N, z0 * nxy + own_xy);
-    halo_fetch(m_in, u_in, N, z0 * nxy, h, hb);
+    mo = mom_load<S>(m_in, u_in, N, z0 * nxy + own_xy);
+    halo_fetch<S>(m_in, u_in, N, z0 * nxy, h, hb);
     ring_of(z0 - 1)[own] = __ldg(phi_new + phi_plane(z0 - 1) * nxy + own_xy);
     halo_fetch_phi(phi_new, phi_plane(z0 - 1) * nxy, h, ring_of(z0 - 1));
     ring_of(z0)[own] = __ldg(phi_new + z0 * nxy + own_xy);
@@ -282,13 +302,13 @@ __global__ void __launch_bounds__(kMomThreads, 2)
     __syncthreads();
     PhiPartials pm = phi_partials(ring_of(z0 - 1), own), p0 = phi_partials(ring_of(z0), own);
     mom_emit<-1, 0, 2>(mo, rm_cur, r0_cur, rp_cur, own);
-    mom_stage_halo<2>(hb, row, lane, rm_cur, r0_cur, rp_cur);
+    mom_stage_halo<S, 2>(hb, row, lane, rm_cur, r0_cur, rp_cur);
     float ubx = mo.ux, uby = mo.uy, ubz = mo.uz;
     __syncthreads();
     int zn = moment_plane(z0 + 1);
     if (zn >= 0) {
-        mo = mom_load(m_in, u_in, N, zn * nxy + own_xy);
-        halo_fetch(m_in, u_in, N, zn * nxy, h, hb);
+        mo = mom_load<S>(m_in, u_in, N, zn * nxy + own_xy);
+        halo_fetch<S>(m_in, u_in, N, zn * nxy, h, hb);
     }
     float phn = __ldg(phi_new + phi_plane(z0 + 1) * nxy + own_xy);
     halo_fetch_phi(phi_new, phi_plane(z0 + 1) * nxy, h, ring_of(z0 + 1));
@@ -302,10 +322,10 @@ __global__ void __launch_bounds__(kMomThreads, 2)
         const float nbx = mo.ux, nby = mo.uy, nbz = mo.uz;
         if (z + 1 < z1) {
             mom_emit<-1, 0, 2>(mo, rm_next, r0_next, rp_next, own);
-            mom_stage_halo<2>(hb, row, lane, rm_next, r0_next, rp_next);
+            mom_stage_halo<S, 2>(hb, row, lane, rm_next, r0_next, rp_next);
         } else if (zn >= 0) {
             mom_emit<-1, 0, -1>(mo, rm_next, r0_next, rp_next, own);
-            mom_stage_halo<-1>(hb, row, lane, rm_next, r0_next, rp_next);
+            mom_stage_halo<S, -1>(hb, row, lane, rm_next, r0_next, rp_next);
         }
         ring_of(z + 1)[own] = phn;
         __syncthreads();
@@ -315,8 +335,8 @@ __global__ void __launch_bounds__(kMomThreads, 2)
         if (z + 1 < z1) {
             zn = moment_plane(z + 2);
             if (zn >= 0) {
-                mo = mom_load(m_in, u_in, N, zn * nxy + own_xy);
-                halo_fetch(m_in, u_in, N, zn * nxy, h, hb);
+                mo = mom_load<S>(m_in, u_in, N, zn * nxy + own_xy);
+                halo_fetch<S>(m_in, u_in, N, zn * nxy, h, hb);
             }
             phn = __ldg(phi_new + phi_plane(z + 2) * nxy + own_xy);
             halo_fetch_phi(phi_new, phi_plane(z + 2) * nxy, h, ring_of(z + 2));
@@ -350,8 +370,8 @@ __global__ void __launch_bounds__(kMomThreads, 2)
             const float phi0 = ring_of(z)[own];
             float gx, gy, gz, lap;
             phi_stencils(pm, p0, pp, phi0, gx, gy, gz, lap);
-            mom_finish(raw_moments_hat(gh), phi0, gx, gy, gz, lap, ubx, uby, ubz, P, m_out, u_out, w_out, N,
-                       z * nxy + own_xy);
+            mom_finish<S>(raw_moments_hat(gh), phi0, gx, gy, gz, lap, ubx, uby, ubz, P, m_out, u_out, w_out, N,
+                          z * nxy + own_xy);
         }
         pm = p0, p0 = pp;
         cp_async_wait_all();
@@ -365,7 +385,7 @@ __global__ void __launch_bounds__(kMomThreads, 2)
     }
 }
 
-template <bool WALL>
+template <bool WALL, class S>
 __global__ void __launch_bounds__(128)
     lbm_mom_plain_kernel(Grid G, Phys P, const float *__restrict__ m_in, const float *__restrict__ u_in,
                          const float *__restrict__ phi_new, float *__restrict__ m_out, float *__restrict__ u_out,
@@ -382,7 +402,7 @@ __global__ void __launch_bounds__(128)
     for (int i = 0; i < 27; ++i) {
         const bool bounce = (cz(i) == 1 && wlo) || (cz(i) == -1 && whi);
         const int src = bounce ? k : n.zo[1 - cz(i)] + n.yo[1 - cy(i)] + n.xo[1 - cx(i)];
-        const Mom m = mom_load(m_in, u_in, N, src);
+        const Mom m = mom_load<S>(m_in, u_in, N, src);
         const MomPoly q = mom_poly(m);
         gh[i] = bounce ? mom_one(26 - i, m, q) : mom_one(i, m, q);
     }
@@ -391,28 +411,31 @@ __global__ void __launch_bounds__(128)
     for (int i = 0; i < 27; ++i) psi[i] = __ldg(phi_new + nidx(n, i));
     float gx, gy, gz, lap;
     grad_lap27(psi, gx, gy, gz, lap);
-    mom_finish(raw_moments_hat(gh), psi[13], gx, gy, gz, lap, __ldg(u_in + k), __ldg(u_in + N + k),
-               __ldg(u_in + 2 * N + k), P, m_out, u_out, w_out, N, k);
+    mom_finish<S>(raw_moments_hat(gh), psi[13], gx, gy, gz, lap, __ldg(u_in + k), __ldg(u_in + N + k),
+                  __ldg(u_in + 2 * N + k), P, m_out, u_out, w_out, N, k);
 }
 
 // Equilibrium start: p* = pstar (or 0), a = 0, B = 0 (u is already in place).
+template <class S>
 __global__ void mom_init_kernel(Grid G, const float *__restrict__ pstar, float *__restrict__ m)
 {
     const size_t N = (size_t)G.N;
     for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < N; k += (size_t)gridDim.x * blockDim.x) {
-        m[k] = pstar ? pstar[k] : 0.0f;
-#pragma unroll
-        for (int q = 1; q < kMomArrays; ++q) m[q * N + k] = 0.0f;
+        Mom r;
+        r.ps = pstar ? pstar[k] : 0.0f;
+        r.ax = r.ay = r.az = r.bxx = r.byy = r.bzz = r.bxy = r.bxz = r.byz = 0.0f;
+        mom_store_dev<S>(r, m, N, (int)k);
     }
 }
 
 // g[(i - i0) N + node] = w_i (g_i / w_i)(moments of the node) for i in [i0, i0 + ni)
+template <class S>
 __global__ void mom_expand_kernel(Grid G, const float *__restrict__ m, const float *__restrict__ u, int i0, int ni,
                                   float *__restrict__ g)
 {
     const size_t N = (size_t)G.N;
     for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < N; k += (size_t)gridDim.x * blockDim.x) {
-        const Mom mm = mom_load(m, u, N, (int)k);
+        const Mom mm = mom_load<S>(m, u, N, (int)k);
         const MomPoly q = mom_poly(mm);
 #pragma unroll
         for (int i = 0; i < 27; ++i)
@@ -441,25 +464,31 @@ __global__ void mom_project_kernel(Grid G, const float *__restrict__ g, int i0, 
     }
 }
 
-// Moment set from the population moments (in place): p* = sum g, a = 2 (sum g c - u),
-// B = T - 4.5 u u - 4.5 sym(u a) with T = 4.5 (sum g c c - p* I / 3).
-__global__ void mom_finish_kernel(Grid G, const float *__restrict__ u, float *__restrict__ m)
+// Moment set from the population moments acc (FP32, 10 arrays: sum g, sum g c, sum g c c):
+// p* = sum g, a = 2 (sum g c - u), B = T - 4.5 u u - 4.5 sym(u a) with T = 4.5 (sum g c c - p* I / 3),
+// written to m in the storage S (m may be acc itself for FP32 storage).
+template <class S>
+__global__ void mom_finish_kernel(Grid G, const float *__restrict__ u, const float *acc, float *m)
 {
     const size_t N = (size_t)G.N;
     for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < N; k += (size_t)gridDim.x * blockDim.x) {
-        const double ps = m[k];
+        const double ps = acc[k];
         const double ux = u[k], uy = u[N + k], uz = u[2 * N + k];
-        const double ax = 2.0 * (m[N + k] - ux), ay = 2.0 * (m[2 * N + k] - uy), az = 2.0 * (m[3 * N + k] - uz);
+        const double ax = 2.0 * (acc[N + k] - ux), ay = 2.0 * (acc[2 * N + k] - uy), az = 2.0 * (acc[3 * N + k] - uz);
         const double p3 = ps / 3.0;
-        m[N + k] = (float)ax;
-        m[2 * N + k] = (float)ay;
-        m[3 * N + k] = (float)az;
-        m[4 * N + k] = (float)(4.5 * (m[4 * N + k] - p3) - 4.5 * ux * ux - 4.5 * ux * ax);
-        m[5 * N + k] = (float)(4.5 * (m[5 * N + k] - p3) - 4.5 * uy * uy - 4.5 * uy * ay);
-        m[6 * N + k] = (float)(4.5 * (m[6 * N + k] - p3) - 4.5 * uz * uz - 4.5 * uz * az);
-        m[7 * N + k] = (float)(4.5 * m[7 * N + k] - 4.5 * ux * uy - 2.25 * (ux * ay + uy * ax));
-        m[8 * N + k] = (float)(4.5 * m[8 * N + k] - 4.5 * ux * uz - 2.25 * (ux * az + uz * ax));
-        m[9 * N + k] = (float)(4.5 * m[9 * N + k] - 4.5 * uy * uz - 2.25 * (uy * az + uz * ay));
+        const double pxx = acc[4 * N + k], pyy = acc[5 * N + k], pzz = acc[6 * N + k];
+        const double pxy = acc[7 * N + k], pxz = acc[8 * N + k], pyz = acc[9 * N + k];
+        Mom r;
+        r.ps = (float)ps;
+        r.ux = (float)ux, r.uy = (float)uy, r.uz = (float)uz;
+        r.ax = (float)ax, r.ay = (float)ay, r.az = (float)az;
+        r.bxx = (float)(4.5 * (pxx - p3) - 4.5 * ux * ux - 4.5 * ux * ax);
+        r.byy = (float)(4.5 * (pyy - p3) - 4.5 * uy * uy - 4.5 * uy * ay);
+        r.bzz = (float)(4.5 * (pzz - p3) - 4.5 * uz * uz - 4.5 * uz * az);
+        r.bxy = (float)(4.5 * pxy - 4.5 * ux * uy - 2.25 * (ux * ay + uy * ax));
+        r.bxz = (float)(4.5 * pxz - 4.5 * ux * uz - 2.25 * (ux * az + uz * ax));
+        r.byz = (float)(4.5 * pyz - 4.5 * uy * uz - 2.25 * (uy * az + uz * ay));
+        mom_store_dev<S>(r, m, N, (int)k);
     }
 }
 
@@ -468,17 +497,17 @@ struct LaunchMom {
     int blocks_per_sm = 0;
 };
 
-template <bool WALL>
+template <bool WALL, class S>
 cudaError_t prepare_mom(LaunchMom &L)
 {
     int dev = 0;
     cudaError_t e;
     if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
     if ((e = cudaDeviceGetAttribute(&L.sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-    if ((e = cudaFuncSetAttribute(lbm_mom_kernel<WALL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMomSmem)) !=
-        cudaSuccess)
+    if ((e = cudaFuncSetAttribute(lbm_mom_kernel<WALL, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)kMomSmem)) != cudaSuccess)
         return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&L.blocks_per_sm, lbm_mom_kernel<WALL>, kMomThreads,
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&L.blocks_per_sm, lbm_mom_kernel<WALL, S>, kMomThreads,
                                                          kMomSmem);
 }
 
@@ -488,15 +517,14 @@ int grid_stride_blocks(const Grid &G)
     return (int)(b < 148 * 16 ? b : 148 * 16);
 }
 
-}  // namespace
-
-cudaError_t launch_mom(const Grid &G, const Phys &P, const float *m_in, const float *u_in, const float *phi_new,
-                       float *m_out, float *u_out, float *w_out, int zchunks, cudaStream_t s)
+template <class S>
+cudaError_t launch_mom_t(const Grid &G, const Phys &P, const float *m_in, const float *u_in, const float *phi_new,
+                         float *m_out, float *u_out, float *w_out, int zchunks, cudaStream_t s)
 {
     static LaunchMom lw[2];
     LaunchMom &L = lw[G.wall ? 1 : 0];
     if (L.sms == 0) {
-        cudaError_t e = G.wall ? prepare_mom<true>(L) : prepare_mom<false>(L);
+        cudaError_t e = G.wall ? prepare_mom<true, S>(L) : prepare_mom<false, S>(L);
         if (e != cudaSuccess) {
             L.sms = 0;
             return e;
@@ -527,36 +555,67 @@ cudaError_t launch_mom(const Grid &G, const Phys &P, const float *m_in, const fl
     const long long blocks = ncols * m;
     if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
     if (G.wall)
-        lbm_mom_kernel<true><<<(unsigned)blocks, kMomThreads, kMomSmem, s>>>(G, P, m_in, u_in, phi_new, m_out, u_out,
-                                                                             w_out, tiles_x, tiles_y, zlen);
+        lbm_mom_kernel<true, S><<<(unsigned)blocks, kMomThreads, kMomSmem, s>>>(G, P, m_in, u_in, phi_new, m_out,
+                                                                                u_out, w_out, tiles_x, tiles_y, zlen);
     else
-        lbm_mom_kernel<false><<<(unsigned)blocks, kMomThreads, kMomSmem, s>>>(G, P, m_in, u_in, phi_new, m_out, u_out,
-                                                                              w_out, tiles_x, tiles_y, zlen);
+        lbm_mom_kernel<false, S><<<(unsigned)blocks, kMomThreads, kMomSmem, s>>>(G, P, m_in, u_in, phi_new, m_out,
+                                                                                 u_out, w_out, tiles_x, tiles_y, zlen);
     return cudaGetLastError();
 }
 
-cudaError_t launch_mom_plain(const Grid &G, const Phys &P, const float *m_in, const float *u_in, const float *phi_new,
-                             float *m_out, float *u_out, float *w_out, cudaStream_t s)
+template <class S>
+cudaError_t launch_mom_plain_t(const Grid &G, const Phys &P, const float *m_in, const float *u_in,
+                               const float *phi_new, float *m_out, float *u_out, float *w_out, cudaStream_t s)
 {
     const dim3 grid((G.nx + 127) / 128, G.ny, G.nz);
     if (G.wall)
-        lbm_mom_plain_kernel<true><<<grid, 128, 0, s>>>(G, P, m_in, u_in, phi_new, m_out, u_out, w_out);
+        lbm_mom_plain_kernel<true, S><<<grid, 128, 0, s>>>(G, P, m_in, u_in, phi_new, m_out, u_out, w_out);
     else
-        lbm_mom_plain_kernel<false><<<grid, 128, 0, s>>>(G, P, m_in, u_in, phi_new, m_out, u_out, w_out);
+        lbm_mom_plain_kernel<false, S><<<grid, 128, 0, s>>>(G, P, m_in, u_in, phi_new, m_out, u_out, w_out);
     return cudaGetLastError();
 }
 
-cudaError_t launch_mom_init(const Grid &G, const float *pstar, float *m, cudaStream_t s)
+}  // namespace
+
+// storage: LBM_MOM (FP32 deviations), LBM_MOM_BF16, LBM_MOM_FP16
+#define TSLB_MOM_DISPATCH(storage, ...)                                                            \
+    switch (storage) {                                                                             \
+    case LBM_MOM: { using S = StoreF32; __VA_ARGS__; }                                                  \
+    case LBM_MOM_BF16: { using S = StoreB16; __VA_ARGS__; }                                             \
+    case LBM_MOM_FP16: { using S = StoreF16; __VA_ARGS__; }                                             \
+    default: return cudaErrorInvalidValue;                                                         \
+    }
+
+size_t mom_state_bytes(int storage, size_t N)
 {
-    mom_init_kernel<<<grid_stride_blocks(G), 256, 0, s>>>(G, pstar, m);
-    return cudaGetLastError();
+    // p* in FP32, then 9 FP32 arrays or 5 packed 32-bit words per node
+    return N * sizeof(float) + (storage == LBM_MOM ? 9 : kMomWords) * N * sizeof(uint32_t);
 }
 
-cudaError_t launch_mom_expand(const Grid &G, const float *m, const float *u, int i0, int ni, float *g, cudaStream_t s)
+cudaError_t launch_mom(const Grid &G, const Phys &P, int storage, const float *m_in, const float *u_in,
+                       const float *phi_new, float *m_out, float *u_out, float *w_out, int zchunks, cudaStream_t s)
+{
+    TSLB_MOM_DISPATCH(storage, return launch_mom_t<S>(G, P, m_in, u_in, phi_new, m_out, u_out, w_out, zchunks, s))
+}
+
+cudaError_t launch_mom_plain(const Grid &G, const Phys &P, int storage, const float *m_in, const float *u_in,
+                             const float *phi_new, float *m_out, float *u_out, float *w_out, cudaStream_t s)
+{
+    TSLB_MOM_DISPATCH(storage, return launch_mom_plain_t<S>(G, P, m_in, u_in, phi_new, m_out, u_out, w_out, s))
+}
+
+cudaError_t launch_mom_init(const Grid &G, int storage, const float *pstar, float *m, cudaStream_t s)
+{
+    TSLB_MOM_DISPATCH(storage, mom_init_kernel<S><<<grid_stride_blocks(G), 256, 0, s>>>(G, pstar, m);
+                      return cudaGetLastError())
+}
+
+cudaError_t launch_mom_expand(const Grid &G, int storage, const float *m, const float *u, int i0, int ni, float *g,
+                              cudaStream_t s)
 {
     if (i0 < 0 || ni < 1 || i0 + ni > 27) return cudaErrorInvalidValue;
-    mom_expand_kernel<<<grid_stride_blocks(G), 256, 0, s>>>(G, m, u, i0, ni, g);
-    return cudaGetLastError();
+    TSLB_MOM_DISPATCH(storage, mom_expand_kernel<S><<<grid_stride_blocks(G), 256, 0, s>>>(G, m, u, i0, ni, g);
+                      return cudaGetLastError())
 }
 
 cudaError_t launch_mom_project(const Grid &G, const float *g, int i0, int ni, float *acc, cudaStream_t s)
@@ -566,10 +625,10 @@ cudaError_t launch_mom_project(const Grid &G, const float *g, int i0, int ni, fl
     return cudaGetLastError();
 }
 
-cudaError_t launch_mom_finish(const Grid &G, const float *u, float *m, cudaStream_t s)
+cudaError_t launch_mom_finish(const Grid &G, int storage, const float *u, const float *acc, float *m, cudaStream_t s)
 {
-    mom_finish_kernel<<<grid_stride_blocks(G), 256, 0, s>>>(G, u, m);
-    return cudaGetLastError();
+    TSLB_MOM_DISPATCH(storage, mom_finish_kernel<S><<<grid_stride_blocks(G), 256, 0, s>>>(G, u, acc, m);
+                      return cudaGetLastError())
 }
 
 }  // namespace tslb

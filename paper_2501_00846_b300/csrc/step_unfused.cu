@@ -211,7 +211,7 @@ __global__ void __launch_bounds__(128) pressure_kernel(Grid G, Phys P, const flo
     const size_t N = (size_t)G.N;
     const int k = (z * G.ny + y) * G.nx + x;
     float s = 0.0f;
-    if (storage == LBM_MOM) {   // moment storage: p* is the first moment array
+    if (storage >= LBM_MOM) {   // moment storages: p* is the first moment array
         s = g[k];
     } else if (pst) {   // 16-bit formats: p* = P + sum_i w_i h_i
         s = pst[k];
@@ -258,7 +258,9 @@ cudaError_t launch_lbm(const Grid &G, const Phys &P, int storage, const void *g_
                                                   p_out, u_out, w_out);
         break;
     case LBM_MOM:
-        return launch_mom_plain(G, P, (const float *)g_in, u_in, phi_new, (float *)g_out, u_out, w_out, s);
+    case LBM_MOM_BF16:
+    case LBM_MOM_FP16:
+        return launch_mom_plain(G, P, storage, (const float *)g_in, u_in, phi_new, (float *)g_out, u_out, w_out, s);
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();

@@ -18,7 +18,7 @@ struct StepArgs {
     float *u_out;
     float *flux;           // 3N Allen–Cahn flux W: read (W^n) and rewritten (W^{n+1}) by the two-kernel
                            // step; scratch of the unfused path; unused by the fused path
-    int storage = 0;       // 0 FP32, 1 BF16, 2 FP16, 3 moments (paths 0 and 1 only for 1..3)
+    int storage = 0;       // 0 FP32, 1 BF16, 2 FP16, 3..5 moments (paths 0 and 1 only for 1..5)
     const float *p_in = nullptr;   // stored p* of the 16-bit formats
     float *p_out = nullptr;
     int advect = 0;                // 1: literal advection u . grad(phi) (unfused path only)
@@ -61,24 +61,28 @@ cudaError_t launch_compress16(const Grid &G, int storage, const float *g, const 
                               void *h, float *pst, float *corr, cudaStream_t s);
 cudaError_t launch_finish16(const Grid &G, const float *corr, float *pst, cudaStream_t s);
 
-// Moment storage (mom_device.cuh): the tiled step kernel (zchunks as for the marching kernels),
-// the one-thread-per-node kernel, the equilibrium start (p* = pstar or 0, a = B = 0), the
-// expansion to FP32 g (directions [i0, i0+ni) at g[(i-i0)*N + node]), and the import of FP32 g:
-// acc += population moments of directions [i0, i0+ni), then (p*, a, B) from the sums and u.
-cudaError_t launch_mom(const Grid &G, const Phys &P, const float *m_in, const float *u_in, const float *phi_new,
-                       float *m_out, float *u_out, float *w_out, int zchunks, cudaStream_t s);
-cudaError_t launch_mom_plain(const Grid &G, const Phys &P, const float *m_in, const float *u_in, const float *phi_new,
-                             float *m_out, float *u_out, float *w_out, cudaStream_t s);
-cudaError_t launch_mom_init(const Grid &G, const float *pstar, float *m, cudaStream_t s);
-cudaError_t launch_mom_expand(const Grid &G, const float *m, const float *u, int i0, int ni, float *g, cudaStream_t s);
+// Moment storage (mom_device.cuh; storage LBM_MOM, LBM_MOM_BF16 or LBM_MOM_FP16): bytes of one
+// state copy, the tiled step kernel (zchunks as for the marching kernels), the
+// one-thread-per-node kernel, the equilibrium start (p* = pstar or 0, a = B = 0), the expansion to
+// FP32 g (directions [i0, i0+ni) at g[(i-i0)*N + node]), and the import of FP32 g: acc (10 FP32
+// arrays) += population moments of directions [i0, i0+ni), then (p*, a, B) from acc and u into m
+// (m may be acc for LBM_MOM).
+size_t mom_state_bytes(int storage, size_t N);
+cudaError_t launch_mom(const Grid &G, const Phys &P, int storage, const float *m_in, const float *u_in,
+                       const float *phi_new, float *m_out, float *u_out, float *w_out, int zchunks, cudaStream_t s);
+cudaError_t launch_mom_plain(const Grid &G, const Phys &P, int storage, const float *m_in, const float *u_in,
+                             const float *phi_new, float *m_out, float *u_out, float *w_out, cudaStream_t s);
+cudaError_t launch_mom_init(const Grid &G, int storage, const float *pstar, float *m, cudaStream_t s);
+cudaError_t launch_mom_expand(const Grid &G, int storage, const float *m, const float *u, int i0, int ni, float *g,
+                              cudaStream_t s);
 cudaError_t launch_mom_project(const Grid &G, const float *g, int i0, int ni, float *acc, cudaStream_t s);
-cudaError_t launch_mom_finish(const Grid &G, const float *u, float *m, cudaStream_t s);
+cudaError_t launch_mom_finish(const Grid &G, int storage, const float *u, const float *acc, float *m, cudaStream_t s);
 
 // g = f^eq(p*, u); pstar may be nullptr (p* = 0).
 cudaError_t launch_init(const Grid &G, const float *pstar, const float *u, float *g, cudaStream_t s);
 
 // p = p* rho cs^2 with p* = sum_i g_i (FP32, pst null), P + sum_i w_i h_i (16-bit formats) or the
-// stored p* (moment storage: g holds the moment arrays, p* first).
+// stored p* (moment storages: g holds the moment state, p* first).
 cudaError_t launch_pressure(const Grid &G, const Phys &P, int storage, const void *g, const float *pst,
                             const float *phi, float *p, cudaStream_t s);
 
@@ -87,8 +91,8 @@ constexpr int kObsFields = 32;
 int observables_blocks(const Grid &G);
 // rho_l, rho_g in FP64 so the mass sum uses the exact parameter values.
 // p* is summed from the 27 FP32 population arrays g, or (storage 1 / 2, pst not null) is
-// P + sum_i w_i h_i of a 16-bit format whose h arrays g points to, or (storage 3) is the first
-// of the moment arrays g points to.
+// P + sum_i w_i h_i of a 16-bit format whose h arrays g points to, or (storage 3..5) is the
+// first array of the moment state g points to.
 cudaError_t launch_observables(const Grid &G, double rho_l, double rho_g, const void *g, const float *phi,
                                const float *u, double *partials, int nblocks, double *result, cudaStream_t s,
                                int storage = 0, const float *pst = nullptr);

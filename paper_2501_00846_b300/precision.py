@@ -1,4 +1,4 @@
-"""Precision study of the storage formats (FP32, BF16, FP16 populations; FP32 moments) on long runs.
+"""Precision study of the storage formats (FP32, BF16, FP16 populations and moments) on long runs.
 
     python -m paper_2501_00846_b300.precision --bubble-steps 20000 --droplet-L 512 --droplet-steps 2000
 
@@ -21,7 +21,8 @@ import numpy as np
 
 from . import inputs, solver
 
-STORES = {"fp32": solver.LBM_FP32, "bf16": solver.LBM_BF16, "fp16": solver.LBM_FP16, "mom": solver.LBM_MOM}
+STORES = {"fp32": solver.LBM_FP32, "bf16": solver.LBM_BF16, "fp16": solver.LBM_FP16, "mom": solver.LBM_MOM,
+          "mom_bf16": solver.LBM_MOM_BF16, "mom_fp16": solver.LBM_MOM_FP16}
 
 
 def bubble(steps, every, stores):
@@ -81,7 +82,7 @@ def main(argv=None):
     ap.add_argument("--every", type=int, default=1000)
     ap.add_argument("--droplet-L", type=int, default=512)
     ap.add_argument("--droplet-steps", type=int, default=2000)
-    ap.add_argument("--stores", default="fp32,bf16,fp16,mom")
+    ap.add_argument("--stores", default="fp32,bf16,fp16,mom,mom_bf16,mom_fp16")
     ap.add_argument("--out", default=None)
     a = ap.parse_args(argv)
     import torch

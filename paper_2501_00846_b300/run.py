@@ -17,7 +17,8 @@ import numpy as np
 
 from . import inputs, solver
 
-STORAGE = {"fp32": solver.LBM_FP32, "bf16": solver.LBM_BF16, "fp16": solver.LBM_FP16, "mom": solver.LBM_MOM}
+STORAGE = {"fp32": solver.LBM_FP32, "bf16": solver.LBM_BF16, "fp16": solver.LBM_FP16, "mom": solver.LBM_MOM,
+           "mom_bf16": solver.LBM_MOM_BF16, "mom_fp16": solver.LBM_MOM_FP16}
 
 
 def workload(name: str):

@@ -18,6 +18,7 @@ LIB_PATH = os.path.join(_HERE, "libtslb_b300.so")
 LBM_OK = 0
 LBM_FP32, LBM_BF16, LBM_FP16 = 0, 1, 2     # lbm_storage: population storage formats
 LBM_MOM = 3                                 # lbm_storage: moment-only storage (p*, u, a, B per node)
+LBM_MOM_BF16, LBM_MOM_FP16 = 4, 5           # ... with a and B stored in BF16 / FP16
 STATUS = {0: "LBM_OK", -1: "LBM_ERR_ARG", -2: "LBM_ERR_OOM", -3: "LBM_ERR_CUDA",
           -4: "LBM_ERR_NONFINITE", -5: "LBM_ERR_TIMEOUT", -6: "LBM_ERR_STATE"}
 
@@ -308,7 +309,8 @@ class Solver:
 
 def from_workload(wl, stream=None, storage: int = LBM_FP32) -> Solver:
     """Solver for an inputs.Workload, initialised with its seeded phi0, u0 and p*0 (FP64 -> FP32).
-    ``storage``: LBM_FP32, LBM_BF16 or LBM_FP16 population storage, or LBM_MOM moment storage."""
+    ``storage``: LBM_FP32, LBM_BF16 or LBM_FP16 population storage, or LBM_MOM, LBM_MOM_BF16 or
+    LBM_MOM_FP16 moment storage."""
     s = Solver(stream=stream, storage=storage, **wl.params())
     ps = wl.pstar_init()
     s.init_fields(np.ascontiguousarray(wl.phi0(), np.float32), np.ascontiguousarray(wl.u0(), np.float32),
