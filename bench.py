@@ -256,9 +256,9 @@ def run_reference(args):
 
 def run_ensemble(args, stream):
     """The batched ensemble: 256 seeded static droplets in uneven periodic boxes (32^3 .. 96^3,
-    density ratios 10 .. 1000), autotuned, K_e steps replayed from CUDA graphs, device-timed;
-    beside it the same boxes advanced one context at a time (each box's two kernels launched
-    separately), device-timed over fewer steps."""
+    density ratios 10 .. 1000), autotuned, K_e steps replayed from CUDA graphs, device-timed, with
+    FP32 populations and with BF16 moments; beside it the same boxes advanced one context at a time
+    (each box's two kernels launched separately), device-timed over fewer steps."""
     import numpy as np
     import torch
     from paper_2501_00846_b300 import inputs, solver
@@ -267,8 +267,11 @@ def run_ensemble(args, stream):
     ke = min(args.steps, 400)
     f32 = lambda a: None if a is None else np.ascontiguousarray(a, np.float32)
     fields = [(f32(wl.phi0()), f32(wl.u0()), f32(wl.pstar_init())) for wl in wls]
-    with torch.cuda.stream(stream):
-        e = solver.Ensemble([wl.params() for wl in wls], stream=stream)
+
+    def batched(storage):
+        """Autotuned batched run of every box with one storage: (ms per ke steps, tuning, boxes
+        that went non-finite)."""
+        e = solver.Ensemble([dict(wl.params(), storage=storage) for wl in wls], stream=stream)
         for b, (phi0, u0, ps0) in enumerate(fields):
             e.init_fields(b, phi0, u0, ps0)
         e.step(2)
@@ -283,6 +286,12 @@ def run_ensemble(args, stream):
         ms = e0.elapsed_time(e1)
         bad = sum(e.observables(b, allow_nonfinite=True)["n_nonfinite"] > 0 for b in range(len(wls)))
         e.close()
+        return ms, tun, bad
+
+    with torch.cuda.stream(stream):
+        ms, tun, bad = batched(solver.LBM_FP32)
+        ms_m, tun_m, bad_m = batched(solver.LBM_MOM_BF16)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         # the same boxes one context each, every box stepped in turn
         ku = 20
         ctxs = []
@@ -311,7 +320,10 @@ def run_ensemble(args, stream):
             "tuning": {k: tun[k] for k in ("lbm_block", "ac_rows", "ac_zlen", "lbm_us", "ac_us")},
             "unbatched": {"value": unbatched, "unit": "MLUPS", "steps": ku, "ms_per_step": ms_u / ku,
                           "launches_per_step": 2 * len(wls)},
-            "speedup": value / unbatched, "boxes_nonfinite": int(bad)}
+            "speedup": value / unbatched, "boxes_nonfinite": int(bad),
+            "bf16_moments": {"value": n_nodes * ke / (ms_m * 1e-3) / 1e6, "unit": "MLUPS", "steps": ke,
+                             "ms_per_step": ms_m / ke, "ac_us": tun_m["ac_us"], "lbm_us": tun_m["lbm_us"],
+                             "boxes_nonfinite": int(bad_m)}}
 
 
 def main():

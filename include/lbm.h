@@ -256,10 +256,12 @@ int lbm_abi_version(void);
  * Batched ensemble: many independent boxes advanced together.  The paper has no counterpart (it
  * runs one box); this is the library's batching of its step for ensembles of small boxes, which
  * one at a time cannot fill the GPU.  Every box has its own lbm_params (size, walls, densities,
- * viscosities, surface tension, mobility, forces; storage must be LBM_FP32) and its own state;
- * the boxes never interact.  A step advances every box by one time step with two launches for
- * the whole ensemble: the Allen–Cahn kernel over the (column tile, z chunk) tasks of all boxes,
- * then the lattice Boltzmann kernel over the node blocks of all boxes.  Each box's arithmetic is
+ * viscosities, surface tension, mobility, forces; the storage, LBM_FP32 or one of the moment
+ * storages, is the same for every box) and its own state; the boxes never interact.  A step
+ * advances every box by one time step with two launches for the whole ensemble: the Allen–Cahn
+ * kernel over the (column tile, z chunk) tasks of all boxes, then the lattice Boltzmann kernel
+ * over the node blocks of all boxes (moment storage: over the (32 x 8 column tile, 32-plane
+ * chunk) tasks of all boxes, each running the one-box tiled kernel's code).  Each box's arithmetic is
  * exactly that of lbm_step on a context with the same parameters (bit-identical results), for
  * every tuning.  Steps are replayed from a captured CUDA graph of graph_steps steps.
  * ------------------------------------------------------------------------------------------- */
@@ -267,7 +269,8 @@ typedef struct lbm_ens lbm_ens;
 
 /* Launch configuration of the ensemble kernels (lbm_ens_autotune chooses one). */
 typedef struct {
-    int lbm_block;       /* threads per block of the lattice Boltzmann kernel: 64, 128 or 256 */
+    int lbm_block;       /* threads per block of the lattice Boltzmann kernel: 64, 128 or 256
+                            (FP32 populations; kept but unused with moment storage) */
     int ac_rows;         /* output rows per warp of the Allen–Cahn kernel: 2 or 4 */
     int ac_zlen;         /* planes per Allen–Cahn task (z-march depth), >= 1 */
     int graph_steps;     /* steps per captured CUDA graph: even and >= 2, or 0 for direct launches */
@@ -309,7 +312,8 @@ lbm_status lbm_ens_autotune(lbm_ens *ens, int reps, lbm_tuning *out);
  * parameters rescaled by the caller) to the 2x restriction of box b's state: the populations, phi
  * and ubar of each coarse cell are the means over its 8 fine nodes.  Enqueued on the coarse
  * context's stream after the ensemble's pending work.  The library's own addition (data for the
- * learned closure), not in the paper. */
+ * learned closure), not in the paper.  LBM_ERR_ARG for an ensemble that does not store FP32
+ * populations. */
 lbm_status lbm_ens_restrict_state(lbm_ens *ens, int box, lbm_ctx *coarse);
 
 /* Number of boxes, total nodes, nodes of box b, steps taken; 0 for NULL or a bad index. */

@@ -9,7 +9,9 @@
 //      ac_div_task (ac_div.cuh) on it;
 //   2. the lattice Boltzmann kernel over a block list that concatenates every box's node blocks;
 //      a block finds its box the same way and each thread runs lbm_node (lbm_node.cuh) on its node.
-// Both device functions are the ones the one-box kernels use, so every box evolves bit-identically
+//      With moment storage (LBM_MOM, LBM_MOM_BF16, LBM_MOM_FP16) the list concatenates every box's
+//      (32 x 8 column tile, z chunk) tasks instead and a CTA runs mom_tile_task (mom_tile.cuh).
+// The device functions are the ones the one-box kernels use, so every box evolves bit-identically
 // to lbm_step on its own context.  Steps are replayed from a CUDA graph captured once per tuning
 // (graph_steps steps, an even number so the ping-pong buffers return to their start).
 //
@@ -31,6 +33,7 @@
 #include "ac_div.cuh"
 #include "lbm.h"
 #include "lbm_node.cuh"
+#include "mom_tile.cuh"
 #include "tslb_internal.h"
 
 namespace tslb {
@@ -44,18 +47,23 @@ struct EnsBox {
     int task0;       // first task of the box in the Allen–Cahn task list
     int ncols;       // Allen–Cahn column tiles of the box
     int zlen;        // planes per Allen–Cahn task of the box
+    int mtask0;      // first task of the box in the moment-storage lattice Boltzmann task list
+    int mzlen;       // planes per moment-storage task of the box
 };
+
+constexpr int kEnsMomZlen = 32;   // planes per moment-storage task (2 partial halo planes each)
 
 constexpr int AC_WPB = 4;   // warps per Allen–Cahn CTA
 
-// The last box whose first block (FIELD 0) or first task (FIELD 1) is <= v; box 0 starts at 0.
+// The last box whose first block (FIELD 0), first task (FIELD 1) or first moment-storage task
+// (FIELD 2) is <= v; box 0 starts at 0.
 template <int FIELD>
 __device__ __forceinline__ int find_box(const EnsBox *__restrict__ boxes, int nb, int v)
 {
     int lo = 0, hi = nb - 1;
     while (lo < hi) {
         const int mid = (lo + hi + 1) >> 1;
-        const int start = FIELD == 0 ? boxes[mid].blk0 : boxes[mid].task0;
+        const int start = FIELD == 0 ? boxes[mid].blk0 : FIELD == 1 ? boxes[mid].task0 : boxes[mid].mtask0;
         if (start <= v)
             lo = mid;
         else
@@ -81,6 +89,35 @@ __global__ void __launch_bounds__(256, 3) ens_lbm_kernel(const EnsBox *__restric
     const int x = rem - y * G.nx;
     lbm_node<StoreF32>(G, P, g_in + 27 * o, nullptr, phi_new + o, u_in + 3 * o, g_out + 27 * o, nullptr,
                        u_out + 3 * o, w_out + 3 * o, x, y, z);
+}
+
+// Moment storage: one CTA per (box, column tile, z chunk) task; fpn = floats per node of a box's
+// moment state (box b's state starts at float fpn * off_b).
+template <class S>
+__global__ void __launch_bounds__(momt::kMomThreads, 2)
+    ens_mom_kernel(const EnsBox *__restrict__ boxes, int nb, int fpn, const float *__restrict__ m_in,
+                   const float *__restrict__ phi_new, const float *__restrict__ u_in, float *__restrict__ m_out,
+                   float *__restrict__ u_out, float *__restrict__ w_out)
+{
+    const int b = find_box<2>(boxes, nb, blockIdx.x);
+    const Grid G = boxes[b].G;
+    const Phys P = boxes[b].P;
+    const size_t o = (size_t)boxes[b].off;
+    const int tiles_x = (G.nx + momt::MX - 1) / momt::MX, tiles_y = (G.ny + momt::MY - 1) / momt::MY;
+    int t = blockIdx.x - boxes[b].mtask0;
+    const int tx = t % tiles_x;
+    t /= tiles_x;
+    const int ty = t % tiles_y;
+    const int z0 = (t / tiles_y) * boxes[b].mzlen;
+    const int z1 = min(z0 + boxes[b].mzlen, G.nz);
+    const float *mi = m_in + (size_t)fpn * o;
+    float *mo = m_out + (size_t)fpn * o;
+    if (G.wall)   // uniform across the CTA
+        momt::mom_tile_task<true, S>(G, P, mi, u_in + 3 * o, phi_new + o, mo, u_out + 3 * o, w_out + 3 * o,
+                                     tx * momt::MX, ty * momt::MY, z0, z1);
+    else
+        momt::mom_tile_task<false, S>(G, P, mi, u_in + 3 * o, phi_new + o, mo, u_out + 3 * o, w_out + 3 * o,
+                                      tx * momt::MX, ty * momt::MY, z0, z1);
 }
 
 template <int RY>
@@ -170,7 +207,10 @@ struct lbm_ens {
     std::vector<EnsBox> box;          // host copy of the box table
     EnsBox *box_d = nullptr;          // device copy
     long long ntot = 0;
-    float *g[2] = {nullptr, nullptr};
+    float *g[2] = {nullptr, nullptr};  // FP32 populations, or the boxes' moment states
+    int storage = LBM_FP32;
+    int fpn = 27;                     // floats per node of g (27, or 10 / 6 for the moment storages)
+    int mom_tasks = 0;                // moment-storage lattice Boltzmann tasks of all boxes
     float *phi[2] = {nullptr, nullptr};
     float *u[2] = {nullptr, nullptr};
     float *w = nullptr;               // Allen–Cahn flux of the current state, all boxes
@@ -218,7 +258,7 @@ bool tuning_valid(const lbm_tuning &t)
 // Box table for the current tuning: block and task ranges of every box, uploaded to the device.
 lbm_status build_tables(lbm_ens *e)
 {
-    long long blk = 0, task = 0;
+    long long blk = 0, task = 0, mtask = 0;
     const int ry = e->tun.ac_rows;
     for (int b = 0; b < e->nb; ++b) {
         EnsBox &B = e->box[b];
@@ -230,10 +270,15 @@ lbm_status build_tables(lbm_ens *e)
         B.zlen = zlen;
         blk += (B.G.N + e->tun.lbm_block - 1) / e->tun.lbm_block;
         task += (long long)B.ncols * m;
+        B.mtask0 = (int)mtask;
+        B.mzlen = tslb::kEnsMomZlen < B.G.nz ? tslb::kEnsMomZlen : B.G.nz;
+        mtask += (long long)((B.G.nx + tslb::momt::MX - 1) / tslb::momt::MX) *
+                 ((B.G.ny + tslb::momt::MY - 1) / tslb::momt::MY) * ((B.G.nz + B.mzlen - 1) / B.mzlen);
     }
-    if (blk >= (1LL << 31) || task >= (1LL << 31))
+    if (blk >= (1LL << 31) || task >= (1LL << 31) || mtask >= (1LL << 31))
         return ens_fail(LBM_ERR_ARG, "ensemble too large for one launch (%lld blocks, %lld tasks)", blk, task);
     e->lbm_blocks = (int)blk;
+    e->mom_tasks = (int)mtask;
     e->ac_tasks = (int)task;
     const long long warp_slots = (long long)e->sms * e->ac_bps[ry == 2 ? 0 : 1] * tslb::AC_WPB;
     const long long warps = task < warp_slots ? task : warp_slots;
@@ -258,11 +303,32 @@ cudaError_t ens_launch_ac(lbm_ens *e, int a, cudaStream_t s)
     return cudaGetLastError();
 }
 
+template <class S>
+cudaError_t ens_launch_mom(lbm_ens *e, int a, cudaStream_t s)
+{
+    tslb::ens_mom_kernel<S><<<e->mom_tasks, tslb::momt::kMomThreads, tslb::momt::kMomSmem, s>>>(
+        e->box_d, e->nb, e->fpn, e->g[a], e->phi[1 - a], e->u[a], e->g[1 - a], e->u[1 - a], e->w);
+    return cudaGetLastError();
+}
+
 cudaError_t ens_launch_lbm(lbm_ens *e, int a, cudaStream_t s)
 {
+    switch (e->storage) {
+    case LBM_MOM: return ens_launch_mom<tslb::StoreF32>(e, a, s);
+    case LBM_MOM_BF16: return ens_launch_mom<tslb::StoreB16>(e, a, s);
+    case LBM_MOM_FP16: return ens_launch_mom<tslb::StoreF16>(e, a, s);
+    default: break;
+    }
     tslb::ens_lbm_kernel<<<e->lbm_blocks, e->tun.lbm_block, 0, s>>>(e->box_d, e->nb, e->g[a], e->phi[1 - a], e->u[a],
                                                                       e->g[1 - a], e->u[1 - a], e->w);
     return cudaGetLastError();
+}
+
+template <class S>
+cudaError_t ens_prepare_mom()
+{
+    return cudaFuncSetAttribute(tslb::ens_mom_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)tslb::momt::kMomSmem);
 }
 
 // One step from buffers a to 1 - a.
@@ -332,12 +398,17 @@ lbm_status lbm_ens_create(const lbm_params *params, int nboxes, void *stream, lb
             tslb::set_last_error(msg);
             return st;
         }
-        if (params[b].storage != LBM_FP32) return ens_fail(LBM_ERR_ARG, "box %d: ensembles use LBM_FP32 storage", b);
+        if (params[b].storage != params[0].storage)
+            return ens_fail(LBM_ERR_ARG, "box %d: every box of an ensemble has the same storage", b);
+        if (params[b].storage != LBM_FP32 && params[b].storage < LBM_MOM)
+            return ens_fail(LBM_ERR_ARG, "box %d: ensembles use LBM_FP32 or a moment storage", b);
     }
     lbm_ens *e = new (std::nothrow) lbm_ens;
     if (!e) return ens_fail(LBM_ERR_OOM, "host allocation failed");
     e->nb = nboxes;
     e->stream = (cudaStream_t)stream;
+    e->storage = params[0].storage;
+    e->fpn = e->storage == LBM_FP32 ? 27 : (int)(tslb::mom_state_bytes(e->storage, 1) / sizeof(float));
     e->prm.assign(params, params + nboxes);
     e->box.resize(nboxes);
     e->ready.assign(nboxes, 0);
@@ -360,7 +431,7 @@ lbm_status lbm_ens_create(const lbm_params *params, int nboxes, void *stream, lb
         void **p;
         size_t bytes;
     } allocs[] = {
-        {(void **)&e->g[0], 27 * N * sizeof(float)}, {(void **)&e->g[1], 27 * N * sizeof(float)},
+        {(void **)&e->g[0], e->fpn * N * sizeof(float)}, {(void **)&e->g[1], e->fpn * N * sizeof(float)},
         {(void **)&e->phi[0], N * sizeof(float)},    {(void **)&e->phi[1], N * sizeof(float)},
         {(void **)&e->u[0], 3 * N * sizeof(float)},  {(void **)&e->u[1], 3 * N * sizeof(float)},
         {(void **)&e->w, 3 * N * sizeof(float)},     {(void **)&e->box_d, nboxes * sizeof(EnsBox)},
@@ -385,6 +456,9 @@ lbm_status lbm_ens_create(const lbm_params *params, int nboxes, void *stream, lb
         err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&e->ac_bps[0], tslb::ens_ac_kernel<2>, tslb::AC_WPB * 32, 0);
     if (err == cudaSuccess)
         err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&e->ac_bps[1], tslb::ens_ac_kernel<4>, tslb::AC_WPB * 32, 0);
+    if (err == cudaSuccess && e->storage == LBM_MOM) err = ens_prepare_mom<tslb::StoreF32>();
+    if (err == cudaSuccess && e->storage == LBM_MOM_BF16) err = ens_prepare_mom<tslb::StoreB16>();
+    if (err == cudaSuccess && e->storage == LBM_MOM_FP16) err = ens_prepare_mom<tslb::StoreF16>();
     if (err != cudaSuccess) {
         cudaGetLastError();
         free_ens(e);
@@ -431,11 +505,15 @@ lbm_status lbm_ens_init_fields(lbm_ens *ens, int box, const float *phi, const fl
     ENS_TRY(cudaMemcpyAsync(ens->phi[c] + o, phi, n * sizeof(float), k, ens->stream));
     ENS_TRY(cudaMemcpyAsync(ens->u[c] + 3 * o, u, 3 * n * sizeof(float), k, ens->stream));
     const float *ps = nullptr;
-    if (pstar) {   // stage p*0 in the box's idle population slice
-        ENS_TRY(cudaMemcpyAsync(ens->g[1 - c] + 27 * o, pstar, n * sizeof(float), k, ens->stream));
-        ps = ens->g[1 - c] + 27 * o;
+    const size_t go = (size_t)ens->fpn * o;   // the box's slice of the population / moment state
+    if (pstar) {   // stage p*0 in the box's idle state slice
+        ENS_TRY(cudaMemcpyAsync(ens->g[1 - c] + go, pstar, n * sizeof(float), k, ens->stream));
+        ps = ens->g[1 - c] + go;
     }
-    ENS_TRY(tslb::launch_init(B.G, ps, ens->u[c] + 3 * o, ens->g[c] + 27 * o, ens->stream));
+    if (ens->storage == LBM_FP32)
+        ENS_TRY(tslb::launch_init(B.G, ps, ens->u[c] + 3 * o, ens->g[c] + go, ens->stream));
+    else
+        ENS_TRY(tslb::launch_mom_init(B.G, ens->storage, ps, ens->g[c] + go, ens->stream));
     ENS_TRY(tslb::launch_flux(B.G, B.P, ens->phi[c] + o, ens->u[c] + 3 * o, ens->w + 3 * o, ens->stream));
     if (!on_device) ENS_TRY(cudaStreamSynchronize(ens->stream));
     ens->ready[box] = 1;
@@ -477,8 +555,9 @@ lbm_status lbm_ens_observables(lbm_ens *ens, int box, lbm_obs *out)
     const lbm_params &p = ens->prm[box];
     const size_t o = (size_t)B.off;
     const int c = ens->cur;
-    ENS_TRY(tslb::launch_observables(B.G, p.rho_l, p.rho_g, ens->g[c] + 27 * o, ens->phi[c] + o, ens->u[c] + 3 * o,
-                                     ens->partials, tslb::observables_blocks(B.G), ens->result, ens->stream));
+    ENS_TRY(tslb::launch_observables(B.G, p.rho_l, p.rho_g, ens->g[c] + (size_t)ens->fpn * o, ens->phi[c] + o,
+                                     ens->u[c] + 3 * o, ens->partials, tslb::observables_blocks(B.G), ens->result,
+                                     ens->stream, ens->storage));
     ENS_TRY(cudaMemcpyAsync(ens->h_result, ens->result, tslb::kObsFields * sizeof(double), cudaMemcpyDeviceToHost,
                             ens->stream));
     ENS_TRY(cudaStreamSynchronize(ens->stream));
@@ -518,9 +597,11 @@ lbm_status lbm_ens_read_fields(lbm_ens *ens, int box, float *phi, float *u, floa
     const cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
     if (phi) ENS_TRY(cudaMemcpyAsync(phi, ens->phi[c] + o, n * sizeof(float), k, ens->stream));
     if (u) ENS_TRY(cudaMemcpyAsync(u, ens->u[c] + 3 * o, 3 * n * sizeof(float), k, ens->stream));
-    if (p) {   // p into the box's idle population slice, then copy
-        float *tmp = ens->g[1 - c] + 27 * o;
-        ENS_TRY(tslb::launch_pressure(B.G, B.P, 0, ens->g[c] + 27 * o, nullptr, ens->phi[c] + o, tmp, ens->stream));
+    if (p) {   // p into the box's idle state slice, then copy
+        const size_t go = (size_t)ens->fpn * o;
+        float *tmp = ens->g[1 - c] + go;
+        ENS_TRY(tslb::launch_pressure(B.G, B.P, ens->storage, ens->g[c] + go, nullptr, ens->phi[c] + o, tmp,
+                                      ens->stream));
         ENS_TRY(cudaMemcpyAsync(p, tmp, n * sizeof(float), k, ens->stream));
     }
     ENS_TRY(cudaStreamSynchronize(ens->stream));
@@ -588,10 +669,13 @@ lbm_status lbm_ens_autotune(lbm_ens *ens, int reps, lbm_tuning *out)
         }
     // lattice Boltzmann kernel: reads g, ubar of the current state and the idle phi just written;
     // writes the idle g, ubar and W (W of the current state is recomputed below)
+    // (moment storage: one tiled configuration; lbm_block does not apply and only the time is kept)
     double best_lbm = 1e30;
     const int blocks[3] = {64, 128, 256};
-    for (int bi = 0; bi < 3 && st == LBM_OK; ++bi) {
-        ens->tun.lbm_block = blocks[bi];
+    const int nblock = ens->storage == LBM_FP32 ? 3 : 1;
+    if (ens->storage != LBM_FP32) best.lbm_block = ens->tun.lbm_block;
+    for (int bi = 0; bi < nblock && st == LBM_OK; ++bi) {
+        if (ens->storage == LBM_FP32) ens->tun.lbm_block = blocks[bi];
         if ((st = build_tables(ens)) != LBM_OK) break;
         err = ens_launch_lbm(ens, a, ens->stream);
         if (err == cudaSuccess) err = cudaEventRecord(t0, ens->stream);
@@ -607,7 +691,7 @@ lbm_status lbm_ens_autotune(lbm_ens *ens, int reps, lbm_tuning *out)
         const double us = 1e3 * ms / reps;
         if (us < best_lbm) {
             best_lbm = us;
-            best.lbm_block = blocks[bi];
+            if (ens->storage == LBM_FP32) best.lbm_block = blocks[bi];
         }
     }
     cudaEventDestroy(t0);
@@ -634,6 +718,7 @@ lbm_status lbm_ens_restrict_state(lbm_ens *ens, int box, lbm_ctx *coarse)
     lbm_status st = tslb::ctx_view(coarse, &v);
     if (st != LBM_OK) return st;
     const EnsBox &B = ens->box[box];
+    if (ens->storage != LBM_FP32) return ens_fail(LBM_ERR_ARG, "restriction needs an ensemble with FP32 populations");
     if (v.storage != LBM_FP32 || B.G.nx != 2 * v.G.nx || B.G.ny != 2 * v.G.ny || B.G.nz != 2 * v.G.nz)
         return ens_fail(LBM_ERR_ARG, "coarse context must be FP32 with half the box size in every direction");
     const size_t o = (size_t)B.off;

@@ -415,9 +415,10 @@ class Ensemble:
         return t.as_dict()
 
 
-def ensemble_from_workloads(workloads, stream=None) -> Ensemble:
-    """Ensemble of inputs.Workload boxes, each initialised with its seeded phi0, u0 and p*0."""
-    e = Ensemble([wl.params() for wl in workloads], stream=stream)
+def ensemble_from_workloads(workloads, stream=None, storage: int = LBM_FP32) -> Ensemble:
+    """Ensemble of inputs.Workload boxes, each initialised with its seeded phi0, u0 and p*0.
+    ``storage``: LBM_FP32 or one of the moment storages (the same for every box)."""
+    e = Ensemble([dict(wl.params(), storage=storage) for wl in workloads], stream=stream)
     for b, wl in enumerate(workloads):
         ps = wl.pstar_init()
         e.init_fields(b, np.ascontiguousarray(wl.phi0(), np.float32), np.ascontiguousarray(wl.u0(), np.float32),

@@ -160,3 +160,44 @@ def test_ensemble_errors():
     with pytest.raises(solver.LbmError) as err:
         solver.Ensemble([wls[1].params(), bad])
     assert err.value.status == -1 and "box 1" in str(err.value)
+
+
+MOM_STORES = [solver.LBM_MOM, solver.LBM_MOM_BF16, solver.LBM_MOM_FP16]
+
+
+@pytest.mark.parametrize("store", MOM_STORES, ids=["mom", "mom_bf16", "mom_fp16"])
+def test_moment_storage_ensemble_equals_boxes_run_alone(mixed, store):
+    """With moment storage the ensemble's lattice Boltzmann kernel runs the one-box tiled kernel's
+    code on every (box, tile, z chunk) task; the one-box result does not depend on the z chunks,
+    so every box matches its run alone bit for bit (direct steps and graph replays)."""
+    wls, _ = mixed
+    ref = []
+    for wl in wls:
+        with solver.from_workload(wl, storage=store) as s:
+            s.step(21)
+            ref.append(s.read_fields())
+    with solver.ensemble_from_workloads(wls, storage=store) as e:
+        e.step(21)
+        got = [e.read_fields(b) for b in range(len(wls))]
+        obs = e.observables(0)
+    _assert_same(got, ref, f"moment storage {store}")
+    with solver.from_workload(wls[0], storage=store) as s:
+        s.step(21)
+        o1 = s.observables()
+    assert obs["sum_pstar"] == o1["sum_pstar"] and obs["sum_phi"] == o1["sum_phi"]
+
+
+def test_moment_storage_ensemble_rules():
+    """Every box of an ensemble has the same storage; the 2x restriction (closure data) needs FP32
+    populations."""
+    wls = inputs.droplet_ensemble(n=2, seed=3, L_min=24, L_max=32)
+    mixed_params = [dict(wls[0].params(), storage=solver.LBM_FP32), dict(wls[1].params(), storage=solver.LBM_MOM)]
+    with pytest.raises(solver.LbmError):
+        solver.Ensemble(mixed_params)
+    big = inputs.static_droplet(L=24, radius=6.0)
+    with solver.ensemble_from_workloads([big], storage=solver.LBM_MOM_BF16) as e:
+        coarse_params = dict(big.params(), nx=12, ny=12, nz=12)
+        with solver.Solver(**coarse_params) as c:
+            c.init_fields(np.zeros((12, 12, 12), np.float32), np.zeros((3, 12, 12, 12), np.float32))
+            with pytest.raises(solver.LbmError):
+                e.restrict_state(0, c)
