@@ -66,8 +66,8 @@ KERNEL_SOURCES = {
     "lbm16_kernel": ["paper_2501_00846_b300/csrc/step_lbm16.cu", "paper_2501_00846_b300/csrc/tslb_device.cuh"],
     "ac_div_kernel": ["paper_2501_00846_b300/csrc/step_split.cu", "paper_2501_00846_b300/csrc/ac_div.cuh",
                       "paper_2501_00846_b300/csrc/tslb_device.cuh"],
-    "lbm_mom_kernel": ["paper_2501_00846_b300/csrc/step_mom.cu", "paper_2501_00846_b300/csrc/mom_device.cuh",
-                       "paper_2501_00846_b300/csrc/tslb_device.cuh"],
+    "lbm_mom_kernel": ["paper_2501_00846_b300/csrc/step_mom.cu", "paper_2501_00846_b300/csrc/mom_tile.cuh",
+                       "paper_2501_00846_b300/csrc/mom_device.cuh", "paper_2501_00846_b300/csrc/tslb_device.cuh"],
 }
 KERNEL_NAMES = {0: "lbm_kernel", 1: "lbm_kernel", 2: "fused2_kernel"}
 
