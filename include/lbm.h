@@ -360,6 +360,14 @@ lbm_status lbm_cnn_get_grads(lbm_cnn *cnn, float *grads);          /* host, the 
  * values. */
 lbm_status lbm_cnn_set_conv_kernel(lbm_cnn *cnn, int kernel);
 
+/* Test hook of the bounded waits.  With on = 1, every tensor-core convolution (kernel 0) first
+ * waits, with a short poll limit, on an mbarrier that no MMA is committed to, so the wait expires
+ * before the kernel issues any MMA; the kernel then records the expiry, waits for its own copies,
+ * frees its TMEM and returns, and lbm_cnn_forward / lbm_cnn_grad return LBM_ERR_TIMEOUT (the
+ * record is cleared once reported, so the network stays usable).  on = 0 restores normal
+ * operation.  LBM_ERR_ARG for other values. */
+lbm_status lbm_cnn_test_expire_wait(lbm_cnn *cnn, int on);
+
 /* y = network(x): x [5][N] and y [4][N] FP32 channel-first device arrays (N = nx ny nz). */
 lbm_status lbm_cnn_forward(lbm_cnn *cnn, const float *x, float *y);
 

@@ -326,9 +326,9 @@ __device__ __forceinline__ void umma_bf16(uint32_t tmem, uint64_t da, uint64_t d
         "l"(da), "l"(db), "r"(idesc), "r"(acc));
 }
 
-__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity)
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity, int spins = UM_SPIN)
 {
-    for (int it = 0; it < UM_SPIN; ++it) {
+    for (int it = 0; it < spins; ++it) {
         uint32_t done;
         asm volatile(
             "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}\n"
@@ -363,7 +363,7 @@ __global__ void __launch_bounds__(UM_THREADS, 1) conv_umma_kernel(int nx, int ny
                                                            const __nv_bfloat16 *__restrict__ in,
                                                            const float *__restrict__ bias, float *__restrict__ z,
                                                            __nv_bfloat16 *__restrict__ act, int zlen,
-                                                           int *__restrict__ err)
+                                                           int *__restrict__ err, int stall)
 {
     constexpr int CO = MT * 16;
     constexpr int WBYTES = 27 * CB * 2 * CO * 16;
@@ -469,6 +469,11 @@ __global__ void __launch_bounds__(UM_THREADS, 1) conv_umma_kernel(int nx, int ny
     };
 
     bool ok = true;
+    if (stall) {   // test hook: wait (briefly) on a barrier no MMA is committed to, before issuing any
+        const bool good = __all_sync(0xffffffffu, mbar_wait(smem_addr(&mbar[0]), 0u, 1 << 10));
+        if (!good && lane == 0) abort_flag = 1;
+        ok = false;
+    }
     for (int zc = z0; zc < z1 && ok; ++zc) {
         const int b = (zc - z0) & 1;
         if (tid == 0) {   // the MMAs of plane zc
@@ -525,6 +530,8 @@ __global__ void __launch_bounds__(UM_THREADS, 1) conv_umma_kernel(int nx, int ny
         else if (lane == 0)
             abort_flag = 1;
     }
+    cp_async_wait_all();   // no copy of this block is still in flight when it returns
+    __syncthreads();
     if (abort_flag && tid == 0) atomicExch(err, 1);
     asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
     __syncthreads();
@@ -908,6 +915,7 @@ struct lbm_cnn {
     __nv_bfloat16 *wu[tslb::NLAYER] = {};   // tcgen05 operand layout of the weights
     __nv_bfloat16 *wut[tslb::NLAYER] = {};  // ... and of the transposed weights (layers 2..4)
     float *bpad = nullptr;               // biases zero-padded to 32 channels per layer (repack)
+    int test_expire = 0;                 // test hook: tensor-core waits expire (lbm_cnn_test_expire_wait)
     int *derr = nullptr;                 // set by a tensor-core kernel whose mbarrier wait expired
     __nv_bfloat16 *a[tslb::NLAYER] = {}; // layer inputs, channel-last BF16: a[0] [N][16], a[1..3] [N][32]
     float *z[tslb::NLAYER] = {};         // pre-activations, channel-last FP32 ([N][32], last [N][16])
@@ -1069,7 +1077,7 @@ cudaError_t launch_conv(lbm_cnn *c, int layer, bool transpose, const __nv_bfloat
         const int zlen = (c->nz + nzc - 1) / nzc;
         nzc = (c->nz + zlen - 1) / zlen;
         tslb::conv_umma_kernel<MT, CB><<<dim3(tiles, nzc), tslb::UM_THREADS, smem, c->stream>>>(
-            c->nx, c->ny, c->nz, wpack, in, bias, out, act, zlen, c->derr);
+            c->nx, c->ny, c->nz, wpack, in, bias, out, act, zlen, c->derr, c->test_expire);
         return cudaGetLastError();
     }
     cudaError_t e = launch_conv_mma<MT, CB>(c, wfrag, in, bias, out);
@@ -1281,7 +1289,19 @@ lbm_status check_timeout(lbm_cnn *cnn)
     int h = 0;
     CNN_TRY(cudaMemcpyAsync(&h, cnn->derr, sizeof(int), cudaMemcpyDeviceToHost, cnn->stream));
     CNN_TRY(cudaStreamSynchronize(cnn->stream));
-    if (h) return cnn_fail(LBM_ERR_TIMEOUT, "a tensor-core convolution gave up waiting for its MMAs");
+    if (h) {   // report once; the flag is cleared so that the network stays usable
+        CNN_TRY(cudaMemsetAsync(cnn->derr, 0, sizeof(int), cnn->stream));
+        CNN_TRY(cudaStreamSynchronize(cnn->stream));
+        return cnn_fail(LBM_ERR_TIMEOUT, "a tensor-core convolution gave up waiting for its MMAs");
+    }
+    return LBM_OK;
+}
+
+lbm_status lbm_cnn_test_expire_wait(lbm_cnn *cnn, int on)
+{
+    if (!cnn) return cnn_fail(LBM_ERR_ARG, "network is NULL");
+    if (on != 0 && on != 1) return cnn_fail(LBM_ERR_ARG, "on must be 0 or 1");
+    cnn->test_expire = on;
     return LBM_OK;
 }
 

@@ -145,6 +145,7 @@ def load(path: str = LIB_PATH):
         "lbm_cnn_get_grads": ([vp, fp], i),
         "lbm_cnn_forward": ([vp, fp, fp], i),
         "lbm_cnn_set_conv_kernel": ([vp, i], i),
+        "lbm_cnn_test_expire_wait": ([vp, i], i),
         "lbm_cnn_grad": ([vp, fp, fp, i, ctypes.POINTER(ctypes.c_double)], i),
         "lbm_cnn_adam_step": ([vp, ctypes.c_float, ctypes.c_float], i),
         "lbm_closure_features": ([vp, ctypes.POINTER(LbmClosureNorm), fp], i),
@@ -497,6 +498,10 @@ class Network:
             out.append((w, flat[o:o + cout]))
             o += cout
         return out
+
+    def test_expire_wait(self, on: bool):
+        """Test hook: make the tensor-core convolutions' waits expire (LBM_ERR_TIMEOUT)."""
+        _check(load().lbm_cnn_test_expire_wait(self._cnn, int(bool(on))))
 
     def set_conv_kernel(self, kernel: int):
         """0: tcgen05 with TMEM accumulators; 1: mma.sync from shared-memory tiles (default);

@@ -245,3 +245,30 @@ def test_convolution_kernels_agree(shape):
     print(f"{shape}: tcgen05 vs mma.sync: output {_rel(out[0][0], out[1][0]):.2e}, grads {_rel(out[0][1], out[1][1]):.2e}")
     assert _rel(out[0][0], out[1][0]) < 1e-5
     assert _rel(out[0][1], out[1][1]) < 1e-4
+
+
+def test_tensor_core_wait_expiry_is_reported_and_the_network_recovers():
+    """The tensor-core convolution bounds every mbarrier wait.  The test hook makes the first wait
+    of every such launch expire (on a barrier no MMA is committed to, before any MMA is issued):
+    forward and grad return LBM_ERR_TIMEOUT, and once the hook is off the same network gives the
+    same outputs and loss as before."""
+    import torch
+    with solver.Network(32, 32, 16, seed=5) as net:
+        net.set_conv_kernel(0)
+        x = torch.randn(5 * net.n, device="cuda")
+        t = 0.1 * torch.randn(4 * net.n, device="cuda")
+        y0 = torch.empty(4 * net.n, device="cuda")
+        net.forward(x, y0)
+        loss0 = net.grad(x, t)
+        net.test_expire_wait(True)
+        y = torch.empty_like(y0)
+        with pytest.raises(solver.LbmError) as e:
+            net.forward(x, y)
+        assert e.value.status == -5
+        with pytest.raises(solver.LbmError) as e:
+            net.grad(x, t)
+        assert e.value.status == -5
+        net.test_expire_wait(False)
+        net.forward(x, y)
+        assert torch.equal(y, y0)
+        assert net.grad(x, t) == loss0
