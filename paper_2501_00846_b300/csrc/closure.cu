@@ -677,50 +677,140 @@ __global__ void __launch_bounds__(256) loss_kernel(const float *__restrict__ z4,
     if (threadIdx.x == 0) partial[blockIdx.x] = red[0];
 }
 
-// dW[o][i][k] += sum over a node chunk of dz[n][o] a[n + off_k][i] (FP32 on the CUDA cores).
-// Block (k, chunk): 256 threads; thread -> (o = tid / 8, i = 4 (tid % 8) .. +3); 64-node tiles of
-// dz and of the shifted activations are staged in shared memory.  cop / cip: channel counts of
-// the channel-last dz (FP32) and a (BF16) arrays.
-__global__ void __launch_bounds__(256) dweight_kernel(int nx, int ny, int nz, const float *__restrict__ dz, int cop,
-                                                      const __nv_bfloat16 *__restrict__ a, int cip, int cout, int cin,
-                                                      int chunk, float *__restrict__ dW)
+// ---- the weight gradient on the tensor cores -------------------------------------------------
+//
+// dW[o][i][k] = sum_n dz[n][o] a[n + off_k][i] as mma.sync m16n8k16 products with M = output
+// channels o, N = input channels i and K = 16 nodes of one x row: the A operand dz^T and the B
+// operand (the activations shifted by off_k) are both read from channel-last shared-memory tiles
+// with transposing ldmatrix.  A block owns a 32 x 8 column tile, a z chunk and one z offset
+// (blockIdx.y = dz + 1): per plane it stages dz of the plane (BF16, no halo) and the activation
+// plane zc + dz with its one-node halo (the forward kernel's staging, ct_load_plane), double
+// buffered with cp.async, and warp (m, n) accumulates the 9 offsets (dy, dx) of its 16 x 8
+// output tile in registers and stores them as the block's partial sums; dw_reduce_kernel adds the
+// partials of all blocks in a fixed order (the gradient is reproducible bit for bit).
+
+__device__ __forceinline__ void ldmatrix_x4_trans(uint32_t (&r)[4], const void *smem)
 {
-    __shared__ float sdz[64][33];
-    __shared__ float sa[64][33];
-    const int k = blockIdx.x;
-    const int dzo = k / 9 - 1, dyo = (k / 3) % 3 - 1, dxo = k % 3 - 1;
-    const int N = nx * ny * nz, nxy = nx * ny;
-    const int n0 = blockIdx.y * chunk, n1 = min(N, n0 + chunk);
-    const int o = threadIdx.x >> 3, i0 = (threadIdx.x & 7) * 4;
-    float acc[4] = {0.f, 0.f, 0.f, 0.f};
-    for (int base = n0; base < n1; base += 64) {
-        // stage 64 nodes x 32 channels of dz and of a(n + off_k)
-        for (int e = threadIdx.x; e < 64 * 32; e += 256) {
-            const int r = e >> 5, c = e & 31;
-            const int n = base + r;
-            float vdz = 0.0f, va = 0.0f;
-            if (n < n1) {
-                if (c < cop) vdz = dz[(size_t)n * cop + c];
-                const int zc = n / nxy, rem = n - zc * nxy, yc = rem / nx, xc = rem - yc * nx;
-                const int m = (cwrap(zc + dzo, nz) * ny + cwrap(yc + dyo, ny)) * nx + cwrap(xc + dxo, nx);
-                if (c < cip) va = __bfloat162float(a[(size_t)m * cip + c]);
-            }
-            sdz[r][c] = vdz;
-            sa[r][c] = va;
-        }
-        __syncthreads();
-#pragma unroll 8
-        for (int r = 0; r < 64; ++r) {
-            const float d = sdz[r][o];
-#pragma unroll
-            for (int q = 0; q < 4; ++q) acc[q] = fmaf(d, sa[r][i0 + q], acc[q]);
-        }
-        __syncthreads();
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(sa));
+}
+
+__device__ __forceinline__ void ldmatrix_x2_trans(uint32_t (&r)[2], const void *smem)
+{
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("ldmatrix.sync.aligned.m8n8.x2.trans.shared.b16 {%0,%1}, [%2];\n"
+                 : "=r"(r[0]), "=r"(r[1])
+                 : "r"(sa));
+}
+
+// dz tile of one plane: 8 rows x 32 nodes, cop channels at stride cop + 8 (conflict-free ldmatrix
+// rows); rows past ny are zero
+template <int MT>
+__device__ __forceinline__ void dw_load_dz(__nv_bfloat16 *dst, const __nv_bfloat16 *__restrict__ dzb, int nx, int ny,
+                                           int x0, int y0, int zc)
+{
+    constexpr int COP = MT * 16, DS = COP + 8, CH = COP / 8;   // 16-byte chunks per node
+    for (int e = threadIdx.x; e < CT_TY * 32 * CH; e += blockDim.x) {
+        const int chunk = e % CH, node = e / CH;
+        const int yr = node / 32, xr = node - yr * 32;
+        __nv_bfloat16 *d = dst + (size_t)node * DS + chunk * 8;
+        if (y0 + yr < ny)
+            cp_async16(d, dzb + ((((size_t)zc * ny + y0 + yr) * nx + x0 + xr) * COP + chunk * 8));
+        else
+            *reinterpret_cast<uint4 *>(d) = make_uint4(0u, 0u, 0u, 0u);
     }
-    if (o < cout)
+}
+
+// partial sums of block (bx, bz) of z offset group gz: part[((gz * nblk + blk) * 9 + q) * 1024 + o * 32 + i]
+// with blk = bz * gridDim.x + bx and q = 3 (dy + 1) + (dx + 1)
+template <int MT, int CB>
+__global__ void __launch_bounds__(256) dweight_mma_kernel(int nx, int ny, int nz, const __nv_bfloat16 *__restrict__ dzb,
+                                                          const __nv_bfloat16 *__restrict__ a, int zlen,
+                                                          float *__restrict__ part)
+{
+    using Gm = CtGeom<CB>;
+    constexpr int COP = MT * 16, DS = COP + 8, NT = Gm::CI / 8;
+    constexpr int DZB = CT_TY * 32 * DS;   // bf16 of one dz tile
+    extern __shared__ uint4 dsm[];
+    __nv_bfloat16 *act = reinterpret_cast<__nv_bfloat16 *>(dsm);   // 2 staged activation planes
+    __nv_bfloat16 *dzs = act + 2 * Gm::PLANE;                       // 2 dz tiles
+    const int ntx = nx / 32;
+    const int x0 = (blockIdx.x % ntx) * 32, y0 = (blockIdx.x / ntx) * CT_TY;
+    const int z0 = blockIdx.z * zlen, z1 = min(nz, z0 + zlen);
+    const int dz = (int)blockIdx.y - 1;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const bool on = warp < MT * NT;
+    const int m = warp / NT, n = warp % NT;
+    float acc[9][4];
 #pragma unroll
-        for (int q = 0; q < 4; ++q)
-            if (i0 + q < cin) atomicAdd(&dW[((size_t)o * cin + i0 + q) * 27 + k], acc[q]);
+    for (int q = 0; q < 9; ++q) acc[q][0] = acc[q][1] = acc[q][2] = acc[q][3] = 0.0f;
+
+    ct_load_plane<CB>(act, a, nx, ny, nz, x0, y0, z0 + dz);
+    dw_load_dz<MT>(dzs, dzb, nx, ny, x0, y0, z0);
+    cp_async_commit();
+#pragma unroll 1
+    for (int zc = z0; zc < z1; ++zc) {
+        const int b = (zc - z0) & 1;
+        if (zc + 1 < z1) {   // the next plane into the other buffers
+            ct_load_plane<CB>(act + (1 - b) * Gm::PLANE, a, nx, ny, nz, x0, y0, zc + 1 + dz);
+            dw_load_dz<MT>(dzs + (1 - b) * DZB, dzb, nx, ny, x0, y0, zc + 1);
+        }
+        cp_async_commit();
+        cp_async_wait_group<1>();
+        __syncthreads();
+        if (on) {
+            const __nv_bfloat16 *pa = act + b * Gm::PLANE, *pd = dzs + b * DZB;
+#pragma unroll 1
+            for (int yr = 0; yr < CT_TY; ++yr) {
+                if (y0 + yr >= ny) break;   // uniform
+#pragma unroll
+                for (int xs = 0; xs < 32; xs += 16) {
+                    // A = dz^T of 16 nodes: matrices (o 0-7 | 8-15) x (nodes 0-7 | 8-15)
+                    uint32_t ar[4];
+                    ldmatrix_x4_trans(ar, pd + (size_t)(yr * 32 + xs + (lane & 7) + ((lane >> 4) & 1) * 8) * DS +
+                                              m * 16 + ((lane >> 3) & 1) * 8);
+                    const uint4 af = make_uint4(ar[0], ar[1], ar[2], ar[3]);
+#pragma unroll
+                    for (int ky = 0; ky < 3; ++ky)
+#pragma unroll
+                        for (int kx = 0; kx < 3; ++kx) {
+                            // B = the activations of the same 16 nodes shifted by (kx - 1, ky - 1)
+                            uint32_t br[2];
+                            const int hx = xs + kx + (lane & 7) + ((lane >> 3) & 1) * 8;
+                            ldmatrix_x2_trans(br, pa + (size_t)((yr + ky) * CT_HX + hx) * Gm::CS + n * 8);
+                            mma_bf16(acc[ky * 3 + kx], af, br[0], br[1]);
+                        }
+                }
+            }
+        }
+        __syncthreads();   // buffer b is refilled by the next iteration
+    }
+    if (!on) return;
+    const int g = lane >> 2, t = lane & 3;
+    const size_t nblk = (size_t)gridDim.x * gridDim.z, blk = (size_t)blockIdx.z * gridDim.x + blockIdx.x;
+    float *pp = part + ((size_t)blockIdx.y * nblk + blk) * 9 * 1024;
+#pragma unroll
+    for (int q = 0; q < 9; ++q)
+#pragma unroll
+        for (int h = 0; h < 4; ++h) {
+            const int o = m * 16 + g + (h >> 1) * 8, i = n * 8 + 2 * t + (h & 1);
+            pp[q * 1024 + o * 32 + i] = acc[q][h];
+        }
+}
+
+// dW[o][i][k] += sum over the nblk blocks of k's z offset group, in block order
+__global__ void dw_reduce_kernel(const float *__restrict__ part, int nblk, int cout, int cin, float *__restrict__ dW)
+{
+    const int w = blockIdx.x * blockDim.x + threadIdx.x;
+    if (w >= cout * cin * 27) return;
+    const int k = w % 27, oi = w / 27, o = oi / cin, i = oi - o * cin;
+    const int gz = k / 9, q = k - 9 * gz;
+    const float *pp = part + ((size_t)gz * nblk * 9 + q) * 1024 + o * 32 + i;
+    float s = 0.0f;
+    for (int b = 0; b < nblk; ++b) s += pp[(size_t)b * 9 * 1024];
+    dW[w] += s;
 }
 
 // db[o] += sum over a node chunk of dz[n][o]
@@ -915,6 +1005,7 @@ struct lbm_cnn {
     __nv_bfloat16 *wu[tslb::NLAYER] = {};   // tcgen05 operand layout of the weights
     __nv_bfloat16 *wut[tslb::NLAYER] = {};  // ... and of the transposed weights (layers 2..4)
     float *bpad = nullptr;               // biases zero-padded to 32 channels per layer (repack)
+    float *dwpart = nullptr;             // per-block partial sums of the weight gradient
     int test_expire = 0;                 // test hook: tensor-core waits expire (lbm_cnn_test_expire_wait)
     int *derr = nullptr;                 // set by a tensor-core kernel whose mbarrier wait expired
     __nv_bfloat16 *a[tslb::NLAYER] = {}; // layer inputs, channel-last BF16: a[0] [N][16], a[1..3] [N][32]
@@ -977,6 +1068,7 @@ void free_cnn(lbm_cnn *c)
     cudaFree(c->dsum);
     cudaFree(c->derr);
     cudaFree(c->bpad);
+    cudaFree(c->dwpart);
     if (c->h_sum) cudaFreeHost(c->h_sum);
     delete c;
 }
@@ -1105,6 +1197,43 @@ cudaError_t forward(lbm_cnn *c, const float *x)
     return cudaGetLastError();
 }
 
+// block grid of the weight-gradient kernel: column tiles, and z chunks so that the 3 z offset groups
+// give about 4 blocks per SM
+int dw_tiles(const lbm_cnn *c) { return (c->nx / 32) * ((c->ny + tslb::CT_TY - 1) / tslb::CT_TY); }
+int dw_chunks(const lbm_cnn *c)
+{
+    int nzc = (4 * c->sms) / (3 * dw_tiles(c));
+    if (nzc < 1) nzc = 1;
+    if (nzc > c->nz) nzc = c->nz;
+    const int zlen = (c->nz + nzc - 1) / nzc;
+    return (c->nz + zlen - 1) / zlen;
+}
+
+// dW_l += sum_n dz_l[n][o] a_l[n + off_k][i] on the tensor cores (dweight_mma_kernel, then the
+// ordered reduction of the blocks' partial sums), MT = COUTP/16, CB = CINP/16
+template <int MT, int CB>
+cudaError_t launch_dweight(lbm_cnn *c, int layer, float *dW)
+{
+    using Gm = tslb::CtGeom<CB>;
+    const size_t smem = (size_t)(2 * Gm::PLANE + 2 * tslb::CT_TY * 32 * (MT * 16 + 8)) * sizeof(__nv_bfloat16);
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(tslb::dweight_mma_kernel<MT, CB>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    const int tiles = dw_tiles(c), nzc = dw_chunks(c), zlen = (c->nz + nzc - 1) / nzc;
+    tslb::dweight_mma_kernel<MT, CB><<<dim3(tiles, 3, nzc), 256, smem, c->stream>>>(c->nx, c->ny, c->nz, c->dzb,
+                                                                                   c->a[layer], zlen, c->dwpart);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const int nw = tslb::COUT[layer] * tslb::CIN[layer] * 27;
+    tslb::dw_reduce_kernel<<<(nw + 255) / 256, 256, 0, c->stream>>>(c->dwpart, tiles * nzc, tslb::COUT[layer],
+                                                                     tslb::CIN[layer], dW);
+    return cudaGetLastError();
+}
+
 cudaError_t backward(lbm_cnn *c)
 {
     const int N = c->N;
@@ -1116,8 +1245,10 @@ cudaError_t backward(lbm_cnn *c)
         const int cop = COUTP[l];
         float *dW = c->grad + c->pofs[l];
         float *db = dW + tslb::wcount(l);
-        tslb::dweight_kernel<<<dim3(27, nchunk), 256, 0, c->stream>>>(c->nx, c->ny, c->nz, c->dz, cop, c->a[l], CINP[l],
-                                                                       tslb::COUT[l], tslb::CIN[l], chunk, dW);
+        e = l == 0   ? launch_dweight<2, 1>(c, l, dW)
+            : l == 3 ? launch_dweight<1, 2>(c, l, dW)
+                     : launch_dweight<2, 2>(c, l, dW);
+        if (e != cudaSuccess) return e;
         tslb::dbias_kernel<<<nchunk, 256, 0, c->stream>>>(c->dz, cop, tslb::COUT[l], N, chunk, db);
         if (l == 0) break;
         // da_{l-1}[n][i] = sum_{k,o} W_l[o][i][k] dz_l[n - off_k][o]
@@ -1222,6 +1353,14 @@ lbm_status lbm_cnn_create(int nx, int ny, int nz, unsigned long long seed, void 
     }
     c->conv_blocks = sms * 4;
     c->sms = sms;
+    // weight-gradient partials: 3 z offset groups x blocks x 9 offsets x 32 x 32
+    err = cudaMalloc(&c->dwpart, (size_t)3 * dw_tiles(c) * dw_chunks(c) * 9 * 1024 * sizeof(float));
+    if (err != cudaSuccess) {
+        cudaGetLastError();
+        free_cnn(c);
+        return cnn_fail(err == cudaErrorMemoryAllocation ? LBM_ERR_OOM : LBM_ERR_CUDA, "network setup failed: %s",
+                        cudaGetErrorString(err));
+    }
     float *h = new (std::nothrow) float[ofs];
     if (!h) {
         free_cnn(c);
