@@ -87,6 +87,8 @@ __global__ void __launch_bounds__(NT) lbm16_kernel(Grid G, Phys P, const typenam
     __shared__ float sb[HN];     // B = 3 - 4.5 |ubar|^2
     __shared__ float sphi[HN];   // phi^{n+1}
 
+    pdl_trigger();
+    pdl_wait();
     const int tid = threadIdx.x;
     const int tx = tid % TX, ty = (tid / TX) % TY, tz = tid / (TX * TY);
     const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY, z0 = blockIdx.z * TZ;
@@ -166,14 +168,12 @@ cudaError_t launch_lbm16(const Grid &G, const Phys &P, int storage, const void *
 {
     const dim3 grid((G.nx + TX - 1) / TX, (G.ny + TY - 1) / TY, (G.nz + TZ - 1) / TZ);
     if (storage == 1)
-        lbm16_kernel<StoreB16><<<grid, NT, 0, s>>>(G, P, (const __nv_bfloat16 *)h_in, p_in, phi_new, u_in,
-                                                   (__nv_bfloat16 *)h_out, p_out, u_out, w_out);
-    else if (storage == 2)
-        lbm16_kernel<StoreF16><<<grid, NT, 0, s>>>(G, P, (const __half *)h_in, p_in, phi_new, u_in,
-                                                   (__half *)h_out, p_out, u_out, w_out);
-    else
-        return cudaErrorInvalidValue;
-    return cudaGetLastError();
+        return launch_pdl(lbm16_kernel<StoreB16>, grid, dim3(NT), 0, s, G, P, (const __nv_bfloat16 *)h_in, p_in, phi_new,
+                          u_in, (__nv_bfloat16 *)h_out, p_out, u_out, w_out);
+    if (storage == 2)
+        return launch_pdl(lbm16_kernel<StoreF16>, grid, dim3(NT), 0, s, G, P, (const __half *)h_in, p_in, phi_new, u_in,
+                          (__half *)h_out, p_out, u_out, w_out);
+    return cudaErrorInvalidValue;
 }
 
 }  // namespace tslb

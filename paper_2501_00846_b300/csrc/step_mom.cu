@@ -24,6 +24,8 @@ __global__ void __launch_bounds__(momt::kMomThreads, 2)
                    const float *__restrict__ phi_new, float *__restrict__ m_out, float *__restrict__ u_out,
                    float *__restrict__ w_out, int tiles_x, int tiles_y, int zlen)
 {
+    pdl_trigger();
+    pdl_wait();
     int b = blockIdx.x;
     const int tx = b % tiles_x;
     b /= tiles_x;
@@ -202,13 +204,9 @@ cudaError_t launch_mom_t(const Grid &G, const Phys &P, const float *m_in, const 
     m = (G.nz + zlen - 1) / zlen;
     const long long blocks = ncols * m;
     if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
-    if (G.wall)
-        lbm_mom_kernel<true, S><<<(unsigned)blocks, kMomThreads, kMomSmem, s>>>(G, P, m_in, u_in, phi_new, m_out,
-                                                                                u_out, w_out, tiles_x, tiles_y, zlen);
-    else
-        lbm_mom_kernel<false, S><<<(unsigned)blocks, kMomThreads, kMomSmem, s>>>(G, P, m_in, u_in, phi_new, m_out,
-                                                                                 u_out, w_out, tiles_x, tiles_y, zlen);
-    return cudaGetLastError();
+    return launch_pdl(G.wall ? lbm_mom_kernel<true, S> : lbm_mom_kernel<false, S>, dim3((unsigned)blocks),
+                      dim3(kMomThreads), kMomSmem, s, G, P, m_in, u_in, phi_new, m_out, u_out, w_out, tiles_x, tiles_y,
+                      zlen);
 }
 
 template <class S>

@@ -1,6 +1,8 @@
 // Two-kernel step: the Allen–Cahn kernel (ac_div.cuh: a linear stencil of phi^n and the flux
 // W^n) writes phi^{n+1}; the one-thread-per-node lattice Boltzmann kernel (step_unfused.cu, or
 // step_lbm16.cu for 16-bit populations) then streams the populations and writes W^{n+1}.
+#include <cstdint>
+
 #include "ac_div.cuh"
 #include "tslb_internal.h"
 
@@ -15,6 +17,8 @@ __global__ void __launch_bounds__(WPB * 32) ac_div_kernel(Grid G, Phys P, const 
                                                           const float *__restrict__ w, float *__restrict__ phi_out,
                                                           int ncols, int zlen, int tasks)
 {
+    pdl_trigger();
+    pdl_wait();
     const int nwarps = gridDim.x * WPB;
     for (int task = blockIdx.x * WPB + (threadIdx.x >> 5); task < tasks; task += nwarps) {
         const int col = task % ncols;
@@ -23,19 +27,41 @@ __global__ void __launch_bounds__(WPB * 32) ac_div_kernel(Grid G, Phys P, const 
     }
 }
 
-struct LaunchAC {
-    int blocks_per_sm = 0;
-    int sms = 0;
-};
+constexpr int RYV = 2;              // output rows per warp, vector form
+constexpr bool PREF = true;         // vector form: load the next plane while computing this one
 
-template <bool WALL>
-cudaError_t prepare_ac(LaunchAC &L)
+template <bool WALL, bool XWRAP>
+__global__ void __launch_bounds__(WPB * 32) ac_div4_kernel(Grid G, Phys P, const float *__restrict__ phi,
+                                                           const float *__restrict__ w, float *__restrict__ phi_out,
+                                                           int ncols, int zlen, int tasks)
 {
-    int dev = 0;
-    cudaError_t e;
-    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
-    if ((e = cudaDeviceGetAttribute(&L.sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&L.blocks_per_sm, ac_div_kernel<WALL>, WPB * 32, 0);
+    pdl_trigger();
+    pdl_wait();
+    const int nwarps = gridDim.x * WPB;
+    for (int task = blockIdx.x * WPB + (threadIdx.x >> 5); task < tasks; task += nwarps) {
+        const int col = task % ncols;
+        const int z0 = (task / ncols) * zlen;
+        ac_div_task4<WALL, RYV, XWRAP, PREF>(G, P, phi, w, phi_out, col, z0, min(G.nz, z0 + zlen));
+    }
+}
+
+using AcKernel = void (*)(Grid, Phys, const float *, const float *, float *, int, int, int);
+
+// The kernel for a box: the vector form when the x extent is a multiple of 128 and the arrays
+// are 16-byte aligned, else the scalar form; rows is its number of output rows per warp.
+AcKernel pick_ac(const Grid &G, const float *phi_in, const float *w, const float *phi_out, int &rows, int &xcols)
+{
+    const bool aligned = ((reinterpret_cast<uintptr_t>(phi_in) | reinterpret_cast<uintptr_t>(w) |
+                           reinterpret_cast<uintptr_t>(phi_out)) & 15) == 0;
+    if (G.nx % AC_XV == 0 && aligned) {
+        rows = RYV;
+        xcols = AC_XV;
+        if (G.nx == AC_XV) return G.wall ? ac_div4_kernel<true, true> : ac_div4_kernel<false, true>;
+        return G.wall ? ac_div4_kernel<true, false> : ac_div4_kernel<false, false>;
+    }
+    rows = RY;
+    xcols = AC_XO;
+    return G.wall ? ac_div_kernel<true> : ac_div_kernel<false>;
 }
 
 }  // namespace
@@ -43,15 +69,16 @@ cudaError_t prepare_ac(LaunchAC &L)
 cudaError_t launch_ac_div(const Grid &G, const Phys &P, const float *phi_in, const float *w, float *phi_out,
                           int zchunks, cudaStream_t s)
 {
-    static LaunchAC lw[2];
-    LaunchAC &L = lw[G.wall ? 1 : 0];
-    if (L.sms == 0) {
-        cudaError_t e = G.wall ? prepare_ac<true>(L) : prepare_ac<false>(L);
-        if (e != cudaSuccess) return e;
-        if (L.blocks_per_sm < 1) return cudaErrorInvalidConfiguration;
-    }
-    const int warp_slots = L.sms * L.blocks_per_sm * WPB;
-    const int ncols = ((G.nx + AC_XO - 1) / AC_XO) * ((G.ny + RY - 1) / RY);
+    int rows = 0, xcols = 0;
+    const AcKernel k = pick_ac(G, phi_in, w, phi_out, rows, xcols);
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaError_t e;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, WPB * 32, 0)) != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    const int warp_slots = sms * per_sm * WPB;
+    const int ncols = ((G.nx + xcols - 1) / xcols) * ((G.ny + rows - 1) / rows);
     // default: about one task per resident warp, chunks of at least 16 planes (2 halo planes each)
     int m = zchunks;
     if (m <= 0) {
@@ -65,11 +92,7 @@ cudaError_t launch_ac_div(const Grid &G, const Phys &P, const float *phi_in, con
     const int tasks = ncols * m;
     const int warps = tasks < warp_slots ? tasks : warp_slots;
     const int ctas = (warps + WPB - 1) / WPB;
-    if (G.wall)
-        ac_div_kernel<true><<<ctas, WPB * 32, 0, s>>>(G, P, phi_in, w, phi_out, ncols, zlen, tasks);
-    else
-        ac_div_kernel<false><<<ctas, WPB * 32, 0, s>>>(G, P, phi_in, w, phi_out, ncols, zlen, tasks);
-    return cudaGetLastError();
+    return launch_pdl(k, dim3(ctas), dim3(WPB * 32), 0, s, G, P, phi_in, w, phi_out, ncols, zlen, tasks);
 }
 
 cudaError_t launch_step_split(const Grid &G, const Phys &P, const StepArgs &a, int zchunks, cudaStream_t s)

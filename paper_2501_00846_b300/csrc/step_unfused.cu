@@ -84,6 +84,8 @@ __global__ void __launch_bounds__(128) lbm_kernel(Grid G, Phys P, const typename
                                                   float *__restrict__ pout, float *__restrict__ uout,
                                                   float *__restrict__ wout)
 {
+    pdl_trigger();
+    pdl_wait();
     int x, y, z;
     if (!node_coords(G, x, y, z)) return;
     lbm_node<S>(G, P, gin, pin, phi_new, ubar, gout, pout, uout, wout, x, y, z);
@@ -246,17 +248,14 @@ cudaError_t launch_lbm(const Grid &G, const Phys &P, int storage, const void *g_
     const dim3 grid = node_grid(G);
     switch (storage) {
     case 0:
-        lbm_kernel<StoreF32><<<grid, 128, 0, s>>>(G, P, (const float *)g_in, nullptr, phi_new, u_in, (float *)g_out,
-                                                  nullptr, u_out, w_out);
-        break;
+        return launch_pdl(lbm_kernel<StoreF32>, grid, dim3(128), 0, s, G, P, (const float *)g_in, (const float *)nullptr,
+                          phi_new, u_in, (float *)g_out, (float *)nullptr, u_out, w_out);
     case 1:
-        lbm_kernel<StoreB16><<<grid, 128, 0, s>>>(G, P, (const __nv_bfloat16 *)g_in, p_in, phi_new, u_in,
-                                                  (__nv_bfloat16 *)g_out, p_out, u_out, w_out);
-        break;
+        return launch_pdl(lbm_kernel<StoreB16>, grid, dim3(128), 0, s, G, P, (const __nv_bfloat16 *)g_in, p_in, phi_new,
+                          u_in, (__nv_bfloat16 *)g_out, p_out, u_out, w_out);
     case 2:
-        lbm_kernel<StoreF16><<<grid, 128, 0, s>>>(G, P, (const __half *)g_in, p_in, phi_new, u_in, (__half *)g_out,
-                                                  p_out, u_out, w_out);
-        break;
+        return launch_pdl(lbm_kernel<StoreF16>, grid, dim3(128), 0, s, G, P, (const __half *)g_in, p_in, phi_new, u_in,
+                          (__half *)g_out, p_out, u_out, w_out);
     case LBM_MOM:
     case LBM_MOM_BF16:
     case LBM_MOM_FP16:

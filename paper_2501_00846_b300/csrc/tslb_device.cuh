@@ -40,6 +40,15 @@ struct Grid {
     int wall;              // 1: z walls
 };
 
+// Programmatic dependent launch between the kernels of a step.  A kernel launched with
+// programmatic stream serialisation (launch_pdl) may be scheduled while the kernel before it on
+// the stream is still draining; pdl_wait() holds it until that kernel has completed and its
+// writes are visible, so it comes before the kernel's first global memory access, and ordering
+// is the same as for an ordinary launch.  pdl_trigger() lets the next kernel be scheduled once
+// every block of this one has issued it.  Both are no-ops in a kernel launched the ordinary way.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 // Minimum |grad phi| of the interface normal n = grad(phi) / max(|grad(phi)|, eps) in FP32.
 // The sharpening flux kappa_AC max(phi (1 - phi), 0) n weights the normal by zero wherever phi
 // has left [0, 1] (an overshoot extremum, where n is undefined).

@@ -9,6 +9,30 @@
 
 namespace tslb {
 
+// Launches kernel k with programmatic stream serialisation, so that it is scheduled while the
+// previous kernel on the stream drains; k must call pdl_wait() before touching global memory.
+constexpr bool kUsePdl = true;
+
+template <class... KArgs, class... Args>
+cudaError_t launch_pdl(void (*k)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, Args... args)
+{
+    if (!kUsePdl) {
+        k<<<grid, block, smem, s>>>(args...);
+        return cudaGetLastError();
+    }
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k, static_cast<KArgs>(args)...);
+}
+
 struct StepArgs {
     const float *g_in;       // populations (FP32 g, 16-bit h for storage 1 / 2, moments for 3)
     float *g_out;

@@ -27,7 +27,9 @@ def _f32(a):
 
 def _mixed_boxes():
     """Uneven boxes: cubes of several sizes and properties, a ragged walled bubble with gravity,
-    the minimum 4^3 box, and a thin box narrower than one Allen–Cahn tile."""
+    the minimum 4^3 box, a thin box narrower than one Allen–Cahn tile, and a box 128 wide (which
+    the one-box path updates with the vector Allen–Cahn kernel, the ensemble with the scalar one:
+    the two must give the same bits)."""
     wls = inputs.droplet_ensemble(n=3, seed=7, L_min=24, L_max=40)
     b = inputs.rising_bubble(nx=37, ny=21, nz=19, R=5.0, zc=8.0, sqrt_gR=0.04, mobility=0.1)
     b.noise, b.seed = 0.005, 99
@@ -37,6 +39,10 @@ def _mixed_boxes():
     thin.nx, thin.ny, thin.nz = 5, 33, 18
     thin.center = (2.0, 16.0, 9.0)
     wls.append(thin)
+    wide = inputs.rising_bubble(nx=128, ny=7, nz=10, R=3.0, zc=5.0, sqrt_gR=0.04, mobility=0.1, rho_ratio=100.0)
+    wide.center = (127.0, 3.0, 5.0)
+    wide.noise, wide.seed = 0.005, 43
+    wls.append(wide)
     return wls
 
 

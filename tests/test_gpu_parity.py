@@ -187,6 +187,36 @@ def test_minimum_box(path):
     _assert_parity(_gpu_run(wl, 10, path=path), P, ref, "4x5x4 walled box")
 
 
+# -- boxes whose x extent is a multiple of 128 take the vector Allen–Cahn kernel ---------------
+
+def _wide_box(which):
+    if which == "128_walled":
+        # the warp spans the whole periodic row: the x halo is the shuffle wrap-around
+        wl = inputs.rising_bubble(nx=128, ny=11, nz=20, R=3.5, zc=8.0, sqrt_gR=0.04, mobility=0.1)
+        wl.center = (126.5, 5.0, 8.0)            # across the periodic x boundary
+        wl.noise, wl.seed = 0.005, 41
+    else:
+        # two warps per row: lanes 0 and 31 load the halo columns; odd ny leaves a ragged row tile
+        wl = inputs.rising_bubble(nx=256, ny=5, nz=12, R=3.0, zc=6.0, sqrt_gR=0.04, mobility=0.1,
+                                  rho_ratio=100.0)
+        wl.wall_z = 0
+        wl.center = (128.0, 2.0, 11.0)           # across the tile boundary x = 128 and the periodic z
+        wl.noise, wl.seed = 0.005, 42
+    return wl
+
+
+@pytest.mark.parametrize("which", ["128_walled", "256_periodic"])
+def test_wide_boxes_vector_allen_cahn(which):
+    wl = _wide_box(which)
+    P, ref = _oracle_run(wl, 40)
+    _assert_parity(_gpu_run(wl, 40), P, ref, f"{which} box")
+    a = _gpu_run(wl, 13, chunk=0)
+    for chunk in (1, 5):
+        b = _gpu_run(wl, 13, chunk=chunk)
+        for x, y in zip(a[:4], b[:4]):
+            assert np.array_equal(x, y), chunk
+
+
 # -- determinism and invariances of the fused kernel -------------------------------------------
 
 @pytest.mark.parametrize("path", [0, 2], ids=["two_kernel", "fused"])
