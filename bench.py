@@ -507,8 +507,16 @@ def main():
     if ensemble is not None:
         line["ensemble"] = ensemble
     if world == 1 and not args.no_cpu_baseline:
+        import oracle
         v, desc, cores = oracle_sample(args.cpu_seconds)
         line["cpu_baseline"] = {"value": v, "unit": "MLUPS", "cores": cores, "kind": "oracle", "sample": desc}
+        # the same oracle on one thread, on a third of the time
+        oracle.set_threads(1)
+        try:
+            v1, desc1, _ = oracle_sample(max(2.0, args.cpu_seconds / 3))
+        finally:
+            oracle.set_threads(cores)
+        line["cpu_baseline"]["single_thread"] = {"value": v1, "unit": "MLUPS", "cores": 1, "sample": desc1}
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
