@@ -197,7 +197,8 @@ __device__ __forceinline__ void ac_div_task(const Grid &G, const Phys &P, const 
 // each, and no lane is spent on a halo column: when the warp spans the whole periodic row
 // (XWRAP, nx = 128) the halo is the shuffle's wrap-around, otherwise lane 0 loads column x0 - 1
 // and lane 31 column x0 + 128.  Every node takes ac_ysum and ac_node in the same order as the
-// scalar form, so the two forms give the same bits.
+// scalar form, so the two forms give the same bits.  phi^{n+1} is stored with the L2 evict-last
+// hint: the lattice Boltzmann kernel reads it next, and the Allen–Cahn kernel of the next step.
 constexpr int AC_XV = 128;
 
 template <int NROW>
@@ -295,7 +296,7 @@ __device__ __forceinline__ void ac_div_task4(const Grid &G, const Phys &P, const
             o.z = ac_node(m1, m2, m3, sg, D, acc1[r][2], acc2[r][2], cprev[r][2]);
             o.w = ac_node(m2, m3, rr, sg, D, acc1[r][3], acc2[r][3], cprev[r][3]);
             if (store && y0 + r < ny)
-                *reinterpret_cast<float4 *>(phi_out + (size_t)(p - 1) * nxy + (y0 + r) * nx + xl) = o;
+                st_keep4(phi_out + (size_t)(p - 1) * nxy + (y0 + r) * nx + xl, o, l2_keep_policy());
         }
         if (PREF) {
             cur = nxt;

@@ -75,9 +75,10 @@ __device__ __forceinline__ void lbm_node(const Grid &G, const Phys &P, const typ
     if (wout) {   // Allen–Cahn flux of the new state for the next step
         float wx, wy, wz;
         ac_flux(ps[13], gx, gy, gz, ux, uy, uz, P, wx, wy, wz);
-        wout[k] = wx;
-        wout[N + k] = wy;
-        wout[2 * N + k] = wz;
+        const unsigned long long pol = l2_keep_policy();
+        st_keep(wout + k, wx, pol);
+        st_keep(wout + N + k, wy, pol);
+        st_keep(wout + 2 * N + k, wz, pol);
     }
 }
 

@@ -279,9 +279,10 @@ __device__ __forceinline__ void mom_finish(const RawMoments &r, float phi, float
     if (w_out) {
         float wx, wy, wz;
         ac_flux(phi, gx, gy, gz, c.ux, c.uy, c.uz, P, wx, wy, wz);
-        w_out[k] = wx;
-        w_out[N + k] = wy;
-        w_out[2 * N + k] = wz;
+        const unsigned long long pol = l2_keep_policy();
+        st_keep(w_out + k, wx, pol);
+        st_keep(w_out + N + k, wy, pol);
+        st_keep(w_out + 2 * N + k, wz, pol);
     }
 }
 

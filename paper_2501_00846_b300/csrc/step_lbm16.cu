@@ -154,9 +154,10 @@ __global__ void __launch_bounds__(NT) lbm16_kernel(Grid G, Phys P, const typenam
     if (wout) {   // Allen–Cahn flux of the new state for the next step
         float wx, wy, wz;
         ac_flux(ps[13], gx, gy, gz, ux, uy, uz, P, wx, wy, wz);
-        wout[k] = wx;
-        wout[N + k] = wy;
-        wout[2 * N + k] = wz;
+        const unsigned long long pol = l2_keep_policy();
+        st_keep(wout + k, wx, pol);
+        st_keep(wout + N + k, wy, pol);
+        st_keep(wout + 2 * N + k, wz, pol);
     }
 }
 

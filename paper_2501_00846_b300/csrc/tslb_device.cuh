@@ -49,6 +49,28 @@ struct Grid {
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 __device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
+// Stores of what the next kernel of the step reads (the flux W for the Allen–Cahn kernel, phi^{n+1}
+// for the lattice Boltzmann kernel), with an L2 evict-last hint so that, on boxes whose W and phi
+// fit in the 126 MB L2 beside the population stream, they are still there when read.
+__device__ __forceinline__ unsigned long long l2_keep_policy()
+{
+    unsigned long long pol;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
+}
+
+__device__ __forceinline__ void st_keep(float *p, float v, unsigned long long pol)
+{
+    asm volatile("st.global.L2::cache_hint.f32 [%0], %1, %2;" ::"l"(p), "f"(v), "l"(pol) : "memory");
+}
+
+__device__ __forceinline__ void st_keep4(float *p, float4 v, unsigned long long pol)
+{
+    asm volatile("st.global.L2::cache_hint.v4.f32 [%0], {%1, %2, %3, %4}, %5;" ::"l"(p), "f"(v.x), "f"(v.y), "f"(v.z),
+                 "f"(v.w), "l"(pol)
+                 : "memory");
+}
+
 // Minimum |grad phi| of the interface normal n = grad(phi) / max(|grad(phi)|, eps) in FP32.
 // The sharpening flux kappa_AC max(phi (1 - phi), 0) n weights the normal by zero wherever phi
 // has left [0, 1] (an overshoot extremum, where n is undefined).
