@@ -11,15 +11,9 @@ namespace tslb {
 
 // Launches kernel k with programmatic stream serialisation, so that it is scheduled while the
 // previous kernel on the stream drains; k must call pdl_wait() before touching global memory.
-constexpr bool kUsePdl = true;
-
 template <class... KArgs, class... Args>
 cudaError_t launch_pdl(void (*k)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, Args... args)
 {
-    if (!kUsePdl) {
-        k<<<grid, block, smem, s>>>(args...);
-        return cudaGetLastError();
-    }
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
     attr[0].val.programmaticStreamSerializationAllowed = 1;
