@@ -1,7 +1,7 @@
 """FP64 reference of the learned closure's network (test infrastructure, like the rest of oracle/).
 
 The paper has no learned component; the closure is this project's own addition (a coarse-grid
-correction judged against the fine-grid solver).  This module is the plain, slow, obviously
+correction measured against the fine-grid solver).  This module is the plain, slow, obviously
 correct definition that the GPU kernels' forward pass and gradients are checked against.  It is
 never imported by the CUDA path.
 

@@ -11,9 +11,9 @@ phi and ubar averaged over the 8 fine nodes of a coarse cell), the coarse contex
 
 is stored on the device.  Training: Adam on the mean-squared error, minibatches accumulated in
 the network's gradient buffer.  Evaluation: a held-out collision run three ways from the same
-restricted initial state -- the fine solver (restricted 2x as the judge), the plain coarse solver,
+restricted initial state -- the fine solver (restricted 2x, the reference), the plain coarse solver,
 and the coarse solver corrected by the network after every step -- with RMS errors of phi and u
-against the judge and device times of each.
+against that reference and device times of each.
 
 Everything numerical runs in the library's CUDA kernels; torch provides device memory and the
 stream.
@@ -69,7 +69,7 @@ def generate(collisions, snapshots=20, stride=48, batch=25, norm=IDENTITY, strea
                 phi, u, ps = c.fields()
                 ens.init_fields(k, _f32(phi), _f32(u), _f32(ps))
             coarse = [_coarse_context(c, stream) for c in cols]
-            judge = _coarse_context(cols[0], stream)
+            restricted = _coarse_context(cols[0], stream)
             for _ in range(snapshots):
                 ens.step(stride - 2 * every)
                 for k in range(len(cols)):
@@ -77,15 +77,15 @@ def generate(collisions, snapshots=20, stride=48, batch=25, norm=IDENTITY, strea
                 ens.step(2 * every)
                 for k in range(len(cols)):
                     coarse[k].step(every)
-                    ens.restrict_state(k, judge)
-                    judge.read_fields(phi=ref[:Nc], u=ref[Nc:])
+                    ens.restrict_state(k, restricted)
+                    restricted.read_fields(phi=ref[:Nc], u=ref[Nc:])
                     solver.closure_features(coarse[k], norm, X[idx].reshape(-1))
                     solver.closure_target(coarse[k], ref, norm, T[idx].reshape(-1))
                     idx += 1
             torch.cuda.synchronize()
             for c in coarse:
                 c.close()
-            judge.close()
+            restricted.close()
             ens.close()
             if log:
                 log(f"data: collisions {b0}..{b0 + len(cols) - 1}, {idx} pairs, {time.perf_counter() - t0:.1f} s")
@@ -143,7 +143,7 @@ def evaluate(net, norm, col, coarse_steps=240, every=24, stream=None, apply_ever
         fine = solver.Ensemble([col.params()], stream=stream)
         phi, u, ps = col.fields()
         fine.init_fields(0, _f32(phi), _f32(u), _f32(ps))
-        plain, corr, judge = (_coarse_context(col, stream) for _ in range(3))
+        plain, corr, restricted = (_coarse_context(col, stream) for _ in range(3))
         fine.restrict_state(0, plain)
         fine.restrict_state(0, corr)
         e_plain, e_corr = [], []
@@ -154,8 +154,8 @@ def evaluate(net, norm, col, coarse_steps=240, every=24, stream=None, apply_ever
             if k % apply_every == 0:
                 solver.closure_apply(corr, net, norm)
             if k % every == 0:
-                fine.restrict_state(0, judge)
-                jp, ju, _ = judge.read_fields()
+                fine.restrict_state(0, restricted)
+                jp, ju, _ = restricted.read_fields()
                 row = {"step": k}
                 for name, s, acc in (("plain", plain, e_plain), ("closure", corr, e_corr)):
                     sp, su, _ = s.read_fields()
@@ -191,7 +191,7 @@ def evaluate(net, norm, col, coarse_steps=240, every=24, stream=None, apply_ever
             / apply_every,
         }
         out["apply_every"] = apply_every
-        for s in (plain, corr, judge, ref_fine):
+        for s in (plain, corr, restricted, ref_fine):
             s.close()
         fine.close()
     out["nodes"] = {"fine": col.L ** 3, "coarse": n}

@@ -1,7 +1,7 @@
 // Learned closure: a 4-layer periodic 3x3x3 convolutional network (5 -> 32 -> 32 -> 32 -> 4
 // channels, SiLU between layers) that corrects phi and ubar of a 2x-coarser grid after each step
 // (lbm_cnn_* and lbm_closure_apply in include/lbm.h).  The paper has no learned component; this
-// is the library's coarse-grid correction, judged against the fine-grid solver.
+// is the library's coarse-grid correction, measured against the fine-grid solver.
 //
 // Every convolution (forward, and the backward pass with respect to its input) is an implicit GEMM
 // on the tensor cores: D[o][n] = sum_{k, i} W[o][i][k] a[n + off_k][i], with the K dimension
