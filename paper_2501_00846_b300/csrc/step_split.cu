@@ -2,6 +2,7 @@
 // W^n) writes phi^{n+1}; the one-thread-per-node lattice Boltzmann kernel (step_unfused.cu, or
 // step_lbm16.cu for 16-bit populations) then streams the populations and writes W^{n+1}.
 #include <cstdint>
+#include <mutex>
 
 #include "ac_div.cuh"
 #include "tslb_internal.h"
@@ -64,20 +65,46 @@ AcKernel pick_ac(const Grid &G, const float *phi_in, const float *w, const float
     return G.wall ? ac_div_kernel<true> : ac_div_kernel<false>;
 }
 
+// Resident warps of an Allen–Cahn kernel on the current device, computed once per (device,
+// kernel) and then read from a small table.
+cudaError_t ac_warp_slots(AcKernel k, int &slots)
+{
+    struct Entry {
+        int dev;
+        AcKernel k;
+        int slots;
+    };
+    constexpr int kEntries = 32;
+    static Entry table[kEntries];
+    static int used = 0;
+    static std::mutex mu;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lock(mu);
+    for (int i = 0; i < used; ++i)
+        if (table[i].dev == dev && table[i].k == k) {
+            slots = table[i].slots;
+            return cudaSuccess;
+        }
+    int sms = 0, per_sm = 0;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, WPB * 32, 0)) != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    slots = sms * per_sm * WPB;
+    if (used < kEntries) table[used++] = Entry{dev, k, slots};
+    return cudaSuccess;
+}
+
 }  // namespace
 
 cudaError_t launch_ac_div(const Grid &G, const Phys &P, const float *phi_in, const float *w, float *phi_out,
                           int zchunks, cudaStream_t s)
 {
-    int rows = 0, xcols = 0;
+    int rows = 0, xcols = 0, warp_slots = 0;
     const AcKernel k = pick_ac(G, phi_in, w, phi_out, rows, xcols);
-    int dev = 0, sms = 0, per_sm = 0;
-    cudaError_t e;
-    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
-    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, WPB * 32, 0)) != cudaSuccess) return e;
-    if (per_sm < 1) return cudaErrorInvalidConfiguration;
-    const int warp_slots = sms * per_sm * WPB;
+    const cudaError_t e = ac_warp_slots(k, warp_slots);
+    if (e != cudaSuccess) return e;
     const int ncols = ((G.nx + xcols - 1) / xcols) * ((G.ny + rows - 1) / rows);
     // default: about one task per resident warp, chunks of at least 16 planes (2 halo planes each)
     int m = zchunks;
