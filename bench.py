@@ -222,7 +222,7 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
-    budget = 150.0
+    budget = args.reference_seconds
     # calibrate the per-node cost, then size the sub-box so warmup + steps fit the budget
     wl = inputs.rising_bubble(nx=16, ny=16, nz=32, R=4.0, zc=8.0)
     P = oracle.Params(**wl.params())
@@ -337,6 +337,8 @@ def main():
                     help="step launch: 0 two kernels (default), 1 three kernels, 2 one fused kernel")
     ap.add_argument("--split", type=int, default=0, help="work split of the fused kernel (0 = default)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--reference-seconds", type=float, default=150.0,
+                    help="CPU time budget of the reference arm (warm-up and timed steps together)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--store", default="fp32", choices=list(STORES),
                     help="population storage of the headline line (the others go to store_compare)")
