@@ -215,6 +215,23 @@ def oracle_sample(seconds, max_steps=None):
     return P.n * steps / dt / 1e6, desc, oracle.get_threads()
 
 
+def replica_max(x, world, device):
+    """The largest of the ranks' values of x (the slowest replica bounds the job); x itself on one
+    rank.  Collective over the default process group when world > 1."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], device=device, dtype=torch.float64)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_mlups(n_nodes, steps, seconds, world):
+    """Whole-job MLUPS of `world` replicas that each advanced n_nodes nodes `steps` times, timed by
+    the slowest (seconds = the max over ranks)."""
+    return world * n_nodes * steps / seconds / 1e6
+
+
 def run_reference(args):
     """Reference arm: the FP64 CPU oracle, each step on a bounded sub-box of the workload."""
     import oracle
@@ -429,10 +446,7 @@ def main():
     sampler = ClockSampler(local)
     ms, kernel_ms, obs, s = device_timed(args.store, args.steps, sampler)
     clocks = sampler.stop()
-    t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
+    ms_max = replica_max(ms, world, "cuda")
 
     # ---- end to end through the public API from pinned host buffers --------------------------
     phi_h = torch.from_numpy(phi0.reshape(-1)).pin_memory().numpy()
@@ -447,11 +461,7 @@ def main():
     s.step(args.steps)
     s.observables(allow_nonfinite=True)
     s.read_fields(*outs)
-    e2e_s = time.perf_counter() - t0
-    te = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
-    if world > 1:
-        dist.all_reduce(te, op=dist.ReduceOp.MAX)
-    e2e_s = float(te.item())
+    e2e_s = replica_max(time.perf_counter() - t0, world, "cuda")
     s.close()
 
     # ---- the other population stores on the same workload (device-timed, fewer steps) -------
@@ -474,7 +484,7 @@ def main():
             dist.destroy_process_group()
         return 0
 
-    value = world * N * args.steps / (ms_max * 1e-3) / 1e6
+    value = replica_mlups(N, args.steps, ms_max * 1e-3, world)
     dtype = {"fp32": "f32", "bf16": "f32 compute, bf16 store", "fp16": "f32 compute, f16 store",
              "mom": "f32, moment store", "mom_bf16": "f32 compute, bf16 moment store",
              "mom_fp16": "f32 compute, f16 moment store"}[args.store]
@@ -497,7 +507,7 @@ def main():
                    "parallelism": f"replicas x{world}", "sum_phi_after": obs["sum_phi"],
                    "nonfinite_after": obs["n_nonfinite"]},
         "roofline": roofline(args.store, ms / args.steps, kernel_ms),
-        "e2e": {"value": world * N * args.steps / e2e_s / 1e6, "unit": "MLUPS",
+        "e2e": {"value": replica_mlups(N, args.steps, e2e_s, world), "unit": "MLUPS",
                 "h2d_bytes_per_step": 5 * 4 * N / args.steps,
                 "d2h_bytes_per_step": (5 * 4 * N + 8 * 64) / args.steps,
                 "includes": "init_fields from pinned host, K steps, observables, read_fields to pinned host"},
