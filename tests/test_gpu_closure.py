@@ -216,8 +216,15 @@ def test_trained_closure_beats_the_plain_coarse_run():
     assert res["ratio_phi"] < 0.67
 
 
-@pytest.mark.parametrize("shape", [(64, 16, 8), (32, 6, 5), (32, 3, 2), (48, 20, 3)],
-                         ids=["tiles", "ragged-y", "tiny", "ragged-xy"])
+def test_network_rejects_widths_that_are_not_a_multiple_of_32():
+    """The convolution tiles x by 32 nodes: other widths are refused at creation (LBM_ERR_ARG)."""
+    for nx in (48, 16, 0):
+        with pytest.raises(solver.LbmError) as e:
+            solver.Network(nx, 20, 3)
+        assert e.value.status == -1
+
+
+@pytest.mark.parametrize("shape", [(64, 16, 8), (32, 6, 5), (32, 3, 2)], ids=["tiles", "ragged-y", "tiny"])
 def test_convolution_kernels_agree(shape):
     """Kernels 1 (mma.sync from shared-memory tiles) and 2 (mma.sync from global memory) issue the
     same MMAs in the same order: identical outputs and gradients.  Kernel 0 (tcgen05, TMEM
@@ -225,8 +232,6 @@ def test_convolution_kernels_agree(shape):
     outputs within 1e-5 and gradients within 1e-4 (relative L2) of kernel 1 (measured: identical)."""
     import torch
     nx, ny, nz = shape
-    if nx % 32:
-        pytest.skip("the network needs nx % 32 == 0")
     flat, x, t = _random_case(nx, ny, nz, seed=4)
     out = []
     for kernel in (0, 1, 2):
