@@ -1,11 +1,12 @@
 #!/usr/bin/env python
 """Benchmark of the coupled TSLB + Allen-Cahn step on B300 (one JSON line on rank 0).
 
-Workload (default): the rising bubble, 128 x 128 x 256 nodes, walls on z, periodic x and y,
-gas bubble R = 16 at z = 40, density ratio 1000, viscosity ratio 100, gravity from Eo = 10 and
-Mo = 1e-4, W = 4; synthetic seeded inputs.  A step is one time step of the whole box: two kernel
-launches by default (the z-marching Allen-Cahn kernel, then the lattice Boltzmann kernel).  The
-state (1.04 GB of FP32 populations and fields per copy, 0.62 GB with 16-bit populations) is far
+Workload (default): the static droplet in a periodic 512^3 box (134M nodes), R = 128 centred,
+W = 4, density ratio 10, viscosity ratio 10, sigma = 0.01, fluid at rest, balanced initial
+pressure; synthetic seeded inputs.  It is the largest single-GPU configuration of the MLUPS sweep
+and the box of the paper's own performance tables (a 512^3 water-air box).  A step is one time
+step of the whole box: two kernel launches by default (the z-marching Allen-Cahn kernel, then the
+lattice Boltzmann kernel).  The state (16.6 GB of FP32 populations and fields per copy) is far
 larger than the 126 MB L2, so consecutive steps stream from HBM and no flush is needed.
 
   value  MLUPS = nodes * K / device time of K steps (CUDA events on the solver's stream),
@@ -17,11 +18,14 @@ larger than the 126 MB L2, so consecutive steps stream from HBM and no flush is 
          16-bit 156 B) over its mean launch duration, against the measured HBM copy peak; step_*
          the same for the whole step against the method's state (248 B / 148 B per node update:
          the state read once and written once; the flux this design carries is not counted).
-  store_compare  the same workload with the other population stores (FP32 / BF16 / FP16),
-         device-timed over min(K, 2000) steps.
+  store_compare  the same workload with the other stores (BF16 / FP16 populations, FP32 / BF16 /
+         FP16 moments), device-timed over min(K, 2000) steps.
+  rising_bubble  the 128 x 128 x 256 rising bubble (walls on z, density ratio 1000, viscosity
+         ratio 100, Eo = 10, Mo = 1e-4) with FP32 populations and with BF16 moments.
   ensemble  the batched ensemble of 256 seeded droplets (32^3 .. 96^3 boxes): autotuned, min(K, 400)
          steps from CUDA graphs, next to the same boxes advanced one context at a time.
-  cpu_baseline  the FP64 oracle (plain C, OpenMP) on the host cores, on a bounded sample.
+  cpu_baseline  the FP64 oracle (plain C, OpenMP) on the host cores, on a bounded sub-box of the
+         same workload.
 
 --impl reference runs the FP64 CPU oracle as the reference arm (rank 0 only).
 """
@@ -96,6 +100,18 @@ def workload(name):
     raise SystemExit(f"unknown workload {name}")
 
 
+def sub_workload(name, nodes):
+    """A box of about `nodes` nodes of the same family and parameters as workload `name` (a
+    droplet: L^3 with R = L/4; the bubble: L x L x 2L with R = L/4 at z = L/2), for the CPU
+    oracle's bounded samples: the per-node arithmetic does not depend on the box size."""
+    from paper_2501_00846_b300 import inputs
+    if name.startswith("droplet"):
+        L = int(max(8, min(int(name[len("droplet"):]), round(nodes ** (1 / 3)))))
+        return inputs.static_droplet(L=L)
+    L = int(max(8, min(128, round((nodes / 2) ** (1 / 3)))))
+    return inputs.rising_bubble(nx=L, ny=L, nz=2 * L, R=max(1.5, L / 4), zc=L / 2)
+
+
 def kernel_source_hash(kernel):
     h = hashlib.sha256()
     for rel in KERNEL_SOURCES[kernel]:
@@ -104,17 +120,36 @@ def kernel_source_hash(kernel):
     return h.hexdigest()
 
 
-def measured_traffic(kernel, wl_name, nodes, store="fp32"):
-    """DRAM bytes per launch of a step kernel from the committed ncu summary
-    profiles/<kernel>[_<store>]_<workload>.txt, if its source hash matches the current kernel
-    sources (else None)."""
-    if kernel not in KERNEL_SOURCES:
-        return None
+# workloads too large for a multi-pass ncu capture take the DRAM traffic of the same kernel on a
+# smaller box of the same family, scaled per node (per-node traffic does not depend on the box
+# size once the state is far larger than L2)
+TRAFFIC_PROXY = {"droplet512": "droplet256"}
+PROFILE_NAMES = {"droplet512": "static_droplet_512", "droplet256": "static_droplet_256",
+                 "droplet128": "static_droplet_128", "rising_bubble": "rising_bubble"}
+
+
+def traffic_source(kernel, wl_name, store="fp32"):
+    """(path of the committed ncu summary that measured_traffic reads, workload it was taken on)."""
     tag = kernel if store in ("fp32", "mom") else f"{kernel}_{store}"
     if store in ("mom_bf16", "mom_fp16"):
         tag = f"{kernel}_{store[4:]}"
-    path = os.path.join(ROOT, "profiles", f"{tag}_{wl_name}.txt")
-    if not os.path.exists(path):
+    for name in (wl_name, TRAFFIC_PROXY.get(wl_name)):
+        if name is None:
+            continue
+        path = os.path.join(ROOT, "profiles", f"{tag}_{PROFILE_NAMES.get(name, name)}.txt")
+        if os.path.exists(path):
+            return path, name
+    return None, None
+
+
+def measured_traffic(kernel, wl_name, nodes, store="fp32"):
+    """DRAM bytes per launch of a step kernel from the committed ncu summary
+    profiles/<kernel>[_<store>]_<workload>.txt (or of the workload's smaller proxy, scaled per
+    node), if its source hash matches the current kernel sources (else None)."""
+    if kernel not in KERNEL_SOURCES:
+        return None
+    path, _ = traffic_source(kernel, wl_name, store)
+    if path is None:
         return None
     kv = {}
     for line in open(path):
@@ -186,32 +221,28 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
-def oracle_sample(seconds, max_steps=None):
-    """Time the FP64 oracle on a rising-bubble sub-box (same parameters and per-node arithmetic
-    as the benchmark workload) for about `seconds`; returns (MLUPS, description, threads)."""
+def oracle_sample(seconds, wl_name="droplet512", max_steps=None):
+    """Time the FP64 oracle on a sub-box of workload wl_name (same family and parameters, so the
+    same per-node arithmetic) for about `seconds`; returns (MLUPS, description, threads)."""
     import oracle
-    from paper_2501_00846_b300 import inputs
-    L = 16
-    wl = inputs.rising_bubble(nx=L, ny=L, nz=2 * L, R=L / 4, zc=L / 2)
+    wl = sub_workload(wl_name, 16 * 16 * 32)
     P = oracle.Params(**wl.params())
-    s = oracle.init(P, wl.phi0(), wl.u0())
+    s = oracle.init(P, wl.phi0(), wl.u0(), wl.pstar_init())
     t0 = time.perf_counter()
     s = oracle.run(P, s, 2)
     per_node = (time.perf_counter() - t0) / (2 * P.n)
-    # choose the sub-box so that one step takes ~seconds/8, at least 16^2 x 32 nodes
-    target_nodes = max(P.n, min(128 * 128 * 256, seconds / 8 / per_node))
-    L = max(16, int((target_nodes / 2) ** (1 / 3)) // 4 * 4)
-    wl = inputs.rising_bubble(nx=L, ny=L, nz=2 * L, R=L / 4, zc=L / 2)
+    # choose the sub-box so that one step takes ~seconds/8
+    wl = sub_workload(wl_name, max(P.n, min(128 * 128 * 256, seconds / 8 / per_node)))
     P = oracle.Params(**wl.params())
-    s = oracle.init(P, wl.phi0(), wl.u0())
+    s = oracle.init(P, wl.phi0(), wl.u0(), wl.pstar_init())
     steps = 0
     t0 = time.perf_counter()
     while time.perf_counter() - t0 < seconds and (max_steps is None or steps < max_steps):
         s = oracle.step(P, s)
         steps += 1
     dt = time.perf_counter() - t0
-    desc = (f"oracle on a {L}x{L}x{2 * L} rising-bubble sub-box with the benchmark's parameters, "
-            f"{steps} steps in {dt:.1f} s")
+    desc = (f"oracle on a {wl.nx}x{wl.ny}x{wl.nz} sub-box of the benchmark workload (same family and "
+            f"parameters), {steps} steps in {dt:.1f} s")
     return P.n * steps / dt / 1e6, desc, oracle.get_threads()
 
 
@@ -235,29 +266,27 @@ def replica_mlups(n_nodes, steps, seconds, world):
 def run_reference(args):
     """Reference arm: the FP64 CPU oracle, each step on a bounded sub-box of the workload."""
     import oracle
-    from paper_2501_00846_b300 import inputs
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
     budget = args.reference_seconds
     # calibrate the per-node cost, then size the sub-box so warmup + steps fit the budget
-    wl = inputs.rising_bubble(nx=16, ny=16, nz=32, R=4.0, zc=8.0)
+    wl = sub_workload(args.workload, 16 * 16 * 32)
     P = oracle.Params(**wl.params())
-    s = oracle.init(P, wl.phi0(), wl.u0())
+    s = oracle.init(P, wl.phi0(), wl.u0(), wl.pstar_init())
     t0 = time.perf_counter()
     oracle.run(P, s, 2)
     per_node = (time.perf_counter() - t0) / (2 * P.n)
-    nodes = budget / max(1, args.steps + args.warmup) / per_node
-    L = int(max(4, min(128, (nodes / 2) ** (1 / 3))))
-    wl = inputs.rising_bubble(nx=L, ny=L, nz=2 * L, R=max(1.5, L / 4), zc=L / 2)
+    wl = sub_workload(args.workload, budget / max(1, args.steps + args.warmup) / per_node)
     P = oracle.Params(**wl.params())
-    s = oracle.init(P, wl.phi0(), wl.u0())
+    s = oracle.init(P, wl.phi0(), wl.u0(), wl.pstar_init())
     s = oracle.run(P, s, args.warmup)
     t0 = time.perf_counter()
     s = oracle.run(P, s, args.steps)
     dt = time.perf_counter() - t0
     value = P.n * args.steps / dt / 1e6
-    desc = f"each step: one oracle step of a {L}x{L}x{2 * L} rising-bubble sub-box with the workload's parameters"
+    desc = (f"each step: one oracle step of a {wl.nx}x{wl.ny}x{wl.nz} sub-box of the workload "
+            "(same family and parameters)")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
@@ -349,7 +378,7 @@ def main():
     ap.add_argument("--steps", type=int, default=5000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="b300", choices=["b300", "reference"])
-    ap.add_argument("--workload", default="rising_bubble")
+    ap.add_argument("--workload", default="droplet512")
     ap.add_argument("--path", type=int, default=0,
                     help="step launch: 0 two kernels (default), 1 three kernels, 2 one fused kernel")
     ap.add_argument("--split", type=int, default=0, help="work split of the fused kernel (0 = default)")
@@ -361,6 +390,7 @@ def main():
                     help="population storage of the headline line (the others go to store_compare)")
     ap.add_argument("--no-store-compare", action="store_true")
     ap.add_argument("--no-ensemble", action="store_true", help="skip the 256-droplet batched ensemble")
+    ap.add_argument("--no-bubble", action="store_true", help="skip the rising bubble beside a droplet workload")
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")
@@ -386,19 +416,25 @@ def main():
     # an explicit stream: the library enqueues every kernel on it and the events are recorded on it
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
-    phi0 = np.ascontiguousarray(wl.phi0(), np.float32)
-    u0 = np.ascontiguousarray(wl.u0(), np.float32)
-    ps0 = np.ascontiguousarray(wl.pstar0(), np.float32)
 
-    def device_timed(store, steps, sampler=None):
+    def fields_of(w):
+        return (np.ascontiguousarray(w.phi0(), np.float32), np.ascontiguousarray(w.u0(), np.float32),
+                np.ascontiguousarray(w.pstar0(), np.float32))
+
+    phi0, u0, ps0 = fields_of(wl)
+
+    def device_timed(store, steps, sampler=None, w=None, fields=None):
         """K steps of one store on the device, CUDA events on the solver's stream; then the
         dominant kernel alone (paths 0 and 1: the lattice Boltzmann kernel relaunched without
-        advancing the state; path 2: the step is one kernel).  Returns (ms of K steps, ms per
+        advancing the state; path 2: the step is one kernel).  w, fields: another workload and
+        its initial fields (default: the benchmark workload).  Returns (ms of K steps, ms per
         dominant-kernel launch, observables after the K steps, the solver)."""
-        s = solver.Solver(stream=stream, storage=STORES[store], **wl.params())
+        w = wl if w is None else w
+        f_phi, f_u, f_ps = (phi0, u0, ps0) if fields is None else fields
+        s = solver.Solver(stream=stream, storage=STORES[store], **w.params())
         s.set_path(args.path)
         s.set_split(args.split)
-        s.init_fields(phi0, u0, ps0)
+        s.init_fields(f_phi, f_u, f_ps)
         s.step(args.warmup)
         torch.cuda.synchronize()
         if sampler is not None:
@@ -429,16 +465,24 @@ def main():
         obs = s.observables(allow_nonfinite=True)
         return ms, kernel_ms, obs, s
 
-    def roofline(store, ms_step, kernel_ms):
+    def roofline(store, ms_step, kernel_ms, wl_name=None, nodes=None):
+        wl_name = args.workload if wl_name is None else wl_name
+        nodes = N if nodes is None else nodes
         kernel = kernel_name(args.path, store)
         kbytes = MOM16_KERNEL_BYTES if store in ("mom_bf16", "mom_fp16") else KERNEL_BYTES[kernel]
-        achieved = kbytes * N / (kernel_ms * 1e-3) / 1e9
-        step_gbs = STEP_BYTES[store] * N / (ms_step * 1e-3) / 1e9
-        return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": measured_traffic(kernel, args.workload, N, store),
-                "kernel": kernel, "kernel_ms": kernel_ms, "bytes_per_lup": kbytes,
-                "step_achieved": step_gbs, "step_frac": step_gbs / peak, "step_bytes_per_lup": STEP_BYTES[store],
-                "peak_source": f"{peak_src} hbm_gbs"}
+        achieved = kbytes * nodes / (kernel_ms * 1e-3) / 1e9
+        step_gbs = STEP_BYTES[store] * nodes / (ms_step * 1e-3) / 1e9
+        traffic = measured_traffic(kernel, wl_name, nodes, store)
+        src_path, src_wl = traffic_source(kernel, wl_name, store)
+        out = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+               "traffic": traffic,
+               "kernel": kernel, "kernel_ms": kernel_ms, "bytes_per_lup": kbytes,
+               "step_achieved": step_gbs, "step_frac": step_gbs / peak, "step_bytes_per_lup": STEP_BYTES[store],
+               "peak_source": f"{peak_src} hbm_gbs"}
+        if traffic is not None and src_wl != wl_name:
+            out["traffic_source"] = (f"{os.path.relpath(src_path, ROOT)}: ncu DRAM bytes of the same kernel on the "
+                                     f"{src_wl} box, scaled per node to this box")
+        return out
 
     peak, peak_src = hbm_peak()
 
@@ -476,6 +520,22 @@ def main():
             compare[store] = {"value": world * N * kc / (cms * 1e-3) / 1e6, "unit": "MLUPS", "steps": kc,
                               "ms_per_step": cms / kc, "roofline": roofline(store, cms / kc, ckms),
                               "sum_phi_after": cobs["sum_phi"], "nonfinite_after": cobs["n_nonfinite"]}
+
+    # ---- the rising bubble beside the headline workload (device-timed, fewer steps) ----------
+    bubble = None
+    if args.workload != "rising_bubble" and not args.no_bubble and args.path in (0, 1):
+        bw = workload("rising_bubble")
+        bf = fields_of(bw)
+        bubble = {"workload": bw.name, "nodes": bw.n}
+        kb = min(args.steps, 2000)
+        for store in ("fp32", "mom_bf16"):
+            bms, bkms, bobs, bs = device_timed(store, kb, w=bw, fields=bf)
+            bs.close()
+            bubble[store] = {"value": world * bw.n * kb / (bms * 1e-3) / 1e6, "unit": "MLUPS", "steps": kb,
+                             "ms_per_step": bms / kb,
+                             "roofline": roofline(store, bms / kb, bkms, "rising_bubble", bw.n),
+                             "sum_phi_after": bobs["sum_phi"], "nonfinite_after": bobs["n_nonfinite"]}
+        del bf
 
     ensemble = None if args.no_ensemble or rank != 0 else run_ensemble(args, stream)
 
@@ -516,16 +576,18 @@ def main():
     }
     if compare:
         line["store_compare"] = compare
+    if bubble is not None:
+        line["rising_bubble"] = bubble
     if ensemble is not None:
         line["ensemble"] = ensemble
     if world == 1 and not args.no_cpu_baseline:
         import oracle
-        v, desc, cores = oracle_sample(args.cpu_seconds)
+        v, desc, cores = oracle_sample(args.cpu_seconds, args.workload)
         line["cpu_baseline"] = {"value": v, "unit": "MLUPS", "cores": cores, "kind": "oracle", "sample": desc}
         # the same oracle on one thread, on a third of the time
         oracle.set_threads(1)
         try:
-            v1, desc1, _ = oracle_sample(max(2.0, args.cpu_seconds / 3))
+            v1, desc1, _ = oracle_sample(max(2.0, args.cpu_seconds / 3), args.workload)
         finally:
             oracle.set_threads(cores)
         line["cpu_baseline"]["single_thread"] = {"value": v1, "unit": "MLUPS", "cores": 1, "sample": desc1}

@@ -174,14 +174,18 @@ lbm_status lbm_observables(lbm_ctx *ctx, lbm_obs *out);
  * must not call cudaMalloc because it would synchronise the device and stall queued work.
  *   g, phi, u   device pointers to populations (27N floats), phi (N) and ubar (3N) in the
  *               layouts above; nx, ny, nz the box; rho_l, rho_g the phase densities
- *   stream      cudaStream_t to run on (NULL: the legacy default stream); synchronised on return
+ *   stream      cudaStream_t to run on (NULL: the legacy default stream).  Every call ends by
+ *               copying its result to the host and synchronising this stream.
  *   out         filled as by lbm_observables, except out->step = 0
  * The reduction's scratch is a fixed array of 1185 x 32 doubles (303,360 bytes) inside the
  * library, held by every GPU that loads the library until the process exits.  Boxes of up to
  * 2^31 - 1 nodes fit; larger boxes return LBM_ERR_ARG.  The first call on a device looks up the
- * array's device address (cudaGetSymbolAddress) with that device current; make that first call
- * before any stream capture.  All calls share the array and nothing in it carries over between
- * calls, but calls whose work overlaps on the GPU (e.g. on two streams) race on it.
+ * array's device address (cudaGetSymbolAddress) with that device current and keeps it for the
+ * life of the process; make that first call before any stream capture.  A process that resets
+ * the device (cudaDeviceReset) afterwards must not call this entry point again: the kept
+ * address belongs to the context that the reset destroyed.  All calls share the array and
+ * nothing in it carries over between calls, but calls whose work overlaps on the GPU (e.g. on
+ * two streams) race on it.
  * Returns LBM_ERR_NONFINITE when out->n_nonfinite > 0 (out filled), LBM_ERR_ARG for bad
  * arguments, LBM_ERR_CUDA if a CUDA call fails.  Calls no allocating routine. */
 lbm_status lbm_observables_noalloc(const float *g, const float *phi, const float *u, int nx, int ny,
@@ -360,8 +364,10 @@ lbm_status lbm_cnn_get_grads(lbm_cnn *cnn, float *grads);          /* host, the 
  * values. */
 lbm_status lbm_cnn_set_conv_kernel(lbm_cnn *cnn, int kernel);
 
-/* Test hook of the bounded waits.  With on = 1, every tensor-core convolution (kernel 0) first
- * waits, with a short poll limit, on an mbarrier that no MMA is committed to, so the wait expires
+/* Test hook of the bounded waits.  Every mbarrier wait of the tensor-core convolution is bounded
+ * in time (20 ms of the GPU's global timer; a plane's MMAs take about a microsecond).  With
+ * on = 1, every tensor-core convolution (kernel 0) first waits, with a 20 us limit, on an
+ * mbarrier that no MMA is committed to, so the wait expires
  * before the kernel issues any MMA; the kernel then records the expiry, waits for its own copies,
  * frees its TMEM and returns, and lbm_cnn_forward / lbm_cnn_grad return LBM_ERR_TIMEOUT (the
  * record is cleared once reported, so the network stays usable).  on = 0 restores normal
@@ -375,6 +381,15 @@ lbm_status lbm_cnn_forward(lbm_cnn *cnn, const float *x, float *y);
  * loss (may be NULL) = mean over 4 N values of (y - t)^2; the gradients are kept (added to the
  * kept ones when accumulate != 0, else replacing them).  Synchronises the stream. */
 lbm_status lbm_cnn_grad(lbm_cnn *cnn, const float *x, const float *t, int accumulate, double *loss);
+
+/* Inspection of one layer l = 0..3 (host arrays, channel-first, any pointer may be NULL):
+ *   a_in  the layer's input as the tensor cores read it, BF16 widened exactly to FP32 [CIN_l][N]
+ *         (layer 0: the rounded network input x; layers 1..3: silu(z_{l-1}) rounded to BF16)
+ *   z     the layer's FP32 pre-activation from the last lbm_cnn_forward or lbm_cnn_grad [COUT_l][N]
+ *   dz    d loss / d z_l in FP32 from the last lbm_cnn_grad [COUT_l][N]
+ * with CIN = 5, 32, 32, 32 and COUT = 32, 32, 32, 4.  For testing the convolutions one at a time
+ * against their definition; synchronises the stream.  LBM_ERR_ARG for a bad layer. */
+lbm_status lbm_cnn_get_layer(lbm_cnn *cnn, int layer, float *a_in, float *z, float *dz);
 
 /* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8, learning rate lr) with the kept gradients
  * multiplied by grad_scale (e.g. 1 / samples accumulated). */

@@ -38,6 +38,7 @@ class _Params(ctypes.Structure):
         ("rho_ref", ctypes.c_double),
         ("body", ctypes.c_double * 3),
         ("advect", ctypes.c_int),
+        ("literal_weight", ctypes.c_int),
     ]
 
 
@@ -59,6 +60,7 @@ class Params:
     rho_ref: float = 1.0
     body: tuple = (0.0, 0.0, 0.0)
     advect: int = 0          # 0: flux form div(ubar phi) (reading R4); 1: literal ubar . grad(phi)
+    literal_weight: int = 0  # 0: sharpening weight max(phi (1 - phi), 0) (reading R15); 1: phi (1 - phi)
 
     @property
     def shape(self):
@@ -77,6 +79,7 @@ class Params:
         p.rho_ref = self.rho_ref
         p.body[:] = list(self.body)
         p.advect = int(self.advect)
+        p.literal_weight = int(self.literal_weight)
         return p
 
 

@@ -49,7 +49,8 @@
  *       vector fields mirrored with their z component negated.
  *   R15 the sharpening weight phi (1 - phi) is taken as max(phi (1 - phi), 0): the paper's phi
  *       lives in [0, 1]; outside it the weight would turn the sharpening flux around exactly
- *       where phi has an extremum and the normal is undefined.
+ *       where phi has an extremum and the normal is undefined.  literal_weight = 1 takes the
+ *       printed phi (1 - phi) everywhere, to measure how far the reading moves the results.
  */
 #include <math.h>
 #include <stdlib.h>
@@ -73,6 +74,7 @@ typedef struct {
     double rho_ref;        /* reference density of the buoyancy force */
     double body[3];        /* uniform body-force density */
     int advect;            /* 0: flux form div(ubar phi); 1: literal form ubar . grad(phi) */
+    int literal_weight;    /* 0: sharpening weight max(phi (1 - phi), 0) (R15); 1: phi (1 - phi) as printed */
 } oracle_params;
 
 /* ------------------------------------------------------------------------------------------ */
@@ -420,8 +422,9 @@ void oracle_ac_update(const oracle_params *P, const double *phi, const double *u
                 double mag = sqrt(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]);
                 double den = mag > 1e-12 ? mag : 1e-12;
                 double p = phi[k];
+                double wgt = P->literal_weight ? p * (1.0 - p) : fmax(p * (1.0 - p), 0.0);
                 for (int a = 0; a < 3; ++a)
-                    V[a * N + k] = (P->advect ? 0.0 : ubar[a * N + k] * p) + kac * fmax(p * (1.0 - p), 0.0) * g[a] / den;
+                    V[a * N + k] = (P->advect ? 0.0 : ubar[a * N + k] * p) + kac * wgt * g[a] / den;
             }
 
     #pragma omp parallel for collapse(2) schedule(static)

@@ -2,6 +2,7 @@
 import os
 import subprocess
 import sys
+from concurrent.futures import ThreadPoolExecutor
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
@@ -18,14 +19,18 @@ def nvcc_flags(extra=()):
 
 
 def build(verbose: bool = False, extra=()) -> str:
-    objs = []
     bdir = os.path.join(HERE, "_build")
     os.makedirs(bdir, exist_ok=True)
-    for src in SOURCES:
-        obj = os.path.join(bdir, src.replace(".cu", ".o"))
+    objs = [os.path.join(bdir, src.replace(".cu", ".o")) for src in SOURCES]
+
+    def compile_one(src, obj):
         cmd = nvcc_flags(extra) + (["-Xptxas=-v"] if verbose else []) + ["-c", os.path.join(CSRC, src), "-o", obj]
         subprocess.run(cmd, check=True)
-        objs.append(obj)
+
+    # translation units compile independently: one nvcc process each, a few at a time
+    with ThreadPoolExecutor(max_workers=min(len(SOURCES), os.cpu_count() or 1)) as pool:
+        for f in [pool.submit(compile_one, s, o) for s, o in zip(SOURCES, objs)]:
+            f.result()
     tmp = LIB + ".tmp"
     subprocess.run(["nvcc", *ARCH, "-shared", "-o", tmp, *objs], check=True)
     os.replace(tmp, LIB)

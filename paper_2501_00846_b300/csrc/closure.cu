@@ -300,7 +300,11 @@ constexpr int UM_TX = 16, UM_TY = 16;              // column tile: two 8 x 16 pa
 constexpr int UM_HX = UM_TX + 2, UM_HY = UM_TY + 2;
 constexpr int UM_SLOTS = 6;                        // planes zc-1..zc+1 read, zc+2..zc+4 in flight
 constexpr int UM_AHEAD = 4;                        // a plane is loaded this many planes ahead
-constexpr int UM_SPIN = 1 << 24;                   // mbarrier polls before giving up
+// Bounds of the mbarrier waits, in nanoseconds of %globaltimer: a plane's MMAs take about a
+// microsecond, so a wait still open after 20 ms has failed; the test hook's wait gives up after
+// 20 us.  Time bounds, unlike poll counts, do not depend on how long each poll suspends.
+constexpr unsigned long long UM_WAIT_NS = 20000000ull;
+constexpr unsigned long long UM_TEST_WAIT_NS = 20000ull;
 
 template <int CB>
 struct UmGeom {
@@ -326,9 +330,19 @@ __device__ __forceinline__ void umma_bf16(uint32_t tmem, uint64_t da, uint64_t d
         "l"(da), "l"(db), "r"(idesc), "r"(acc));
 }
 
-__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity, int spins = UM_SPIN)
+__device__ __forceinline__ unsigned long long globaltimer_ns()
 {
-    for (int it = 0; it < spins; ++it) {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Waits until the phase of parity `parity` of the mbarrier has completed; false once limit_ns
+// nanoseconds have passed without that.
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity, unsigned long long limit_ns = UM_WAIT_NS)
+{
+    const unsigned long long t0 = globaltimer_ns();
+    for (;;) {
         uint32_t done;
         asm volatile(
             "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}\n"
@@ -336,8 +350,8 @@ __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity, int sp
             : "r"(mbar), "r"(parity)
             : "memory");
         if (done) return true;
+        if (globaltimer_ns() - t0 > limit_ns) return false;
     }
-    return false;
 }
 
 template <int CB>
@@ -469,8 +483,10 @@ __global__ void __launch_bounds__(UM_THREADS, 1) conv_umma_kernel(int nx, int ny
     };
 
     bool ok = true;
+    // inflight[b]: MMAs committed to mbar[b] whose completion this warp has not yet seen
+    bool inflight[2] = {false, false};
     if (stall) {   // test hook: wait (briefly) on a barrier no MMA is committed to, before issuing any
-        const bool good = __all_sync(0xffffffffu, mbar_wait(smem_addr(&mbar[0]), 0u, 1 << 10));
+        const bool good = __all_sync(0xffffffffu, mbar_wait(smem_addr(&mbar[0]), 0u, UM_TEST_WAIT_NS));
         if (!good && lane == 0) abort_flag = 1;
         ok = false;
     }
@@ -499,10 +515,14 @@ __global__ void __launch_bounds__(UM_THREADS, 1) conv_umma_kernel(int nx, int ny
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
                 smem_addr(&mbar[b])));
         }
+        inflight[b] = true;
         bool good = true;
         if (zc > z0) {   // plane zc - 1: wait for its MMAs (a warp decides as one)
             good = __all_sync(0xffffffffu, mbar_wait(smem_addr(&mbar[1 - b]), phase[1 - b]));
-            phase[1 - b] ^= 1u;
+            if (good) {
+                phase[1 - b] ^= 1u;
+                inflight[1 - b] = false;
+            }
             asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
         }
         // refill: plane zc + 4 into the slot of plane zc - 2, which only plane zc - 1's MMAs read
@@ -525,11 +545,18 @@ __global__ void __launch_bounds__(UM_THREADS, 1) conv_umma_kernel(int nx, int ny
         const int b = (z1 - 1 - z0) & 1;
         const bool good = __all_sync(0xffffffffu, mbar_wait(smem_addr(&mbar[b]), phase[b]));
         asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-        if (good)
+        if (good) {
+            inflight[b] = false;
             epilogue(z1 - 1, b);
-        else if (lane == 0)
+        } else if (lane == 0) {
             abort_flag = 1;
+        }
     }
+    // After an expiry, MMAs committed earlier may still be reading the ring and writing TMEM:
+    // wait for them once more (bounded) before the ring is left and the TMEM freed.
+#pragma unroll
+    for (int bb = 0; bb < 2; ++bb)
+        if (inflight[bb]) __all_sync(0xffffffffu, mbar_wait(smem_addr(&mbar[bb]), phase[bb]));
     cp_async_wait_all();   // no copy of this block is still in flight when it returns
     __syncthreads();
     if (abort_flag && tid == 0) atomicExch(err, 1);
@@ -1010,7 +1037,8 @@ struct lbm_cnn {
     int *derr = nullptr;                 // set by a tensor-core kernel whose mbarrier wait expired
     __nv_bfloat16 *a[tslb::NLAYER] = {}; // layer inputs, channel-last BF16: a[0] [N][16], a[1..3] [N][32]
     float *z[tslb::NLAYER] = {};         // pre-activations, channel-last FP32 ([N][32], last [N][16])
-    float *dz = nullptr, *da = nullptr;  // [N][32] FP32
+    float *dz[tslb::NLAYER] = {};        // gradient of the loss w.r.t. z_l, channel-last FP32 [N][COUTP[l]]
+    float *da = nullptr;                 // [N][32] FP32
     __nv_bfloat16 *dzb = nullptr;        // [N][32] BF16
     float *xbuf = nullptr, *ybuf = nullptr;   // [5][N], [4][N] scratch of lbm_closure_apply
     double *dsum = nullptr;              // loss partials / correction mean
@@ -1060,7 +1088,7 @@ void free_cnn(lbm_cnn *c)
         cudaFree(c->a[l]);
         cudaFree(c->z[l]);
     }
-    cudaFree(c->dz);
+    for (int l = 0; l < tslb::NLAYER; ++l) cudaFree(c->dz[l]);
     cudaFree(c->da);
     cudaFree(c->dzb);
     cudaFree(c->xbuf);
@@ -1249,15 +1277,15 @@ cudaError_t backward(lbm_cnn *c)
             : l == 3 ? launch_dweight<1, 2>(c, l, dW)
                      : launch_dweight<2, 2>(c, l, dW);
         if (e != cudaSuccess) return e;
-        tslb::dbias_kernel<<<nchunk, 256, 0, c->stream>>>(c->dz, cop, tslb::COUT[l], N, chunk, db);
+        tslb::dbias_kernel<<<nchunk, 256, 0, c->stream>>>(c->dz[l], cop, tslb::COUT[l], N, chunk, db);
         if (l == 0) break;
         // da_{l-1}[n][i] = sum_{k,o} W_l[o][i][k] dz_l[n - off_k][o]
         e = l == 3 ? launch_conv<2, 1>(c, l, true, c->dzb, nullptr, c->da)
                    : launch_conv<2, 2>(c, l, true, c->dzb, nullptr, c->da);
         if (e != cudaSuccess) return e;
         const size_t cnt = (size_t)N * 32;
-        tslb::silu_back_kernel<<<(unsigned)((cnt + 255) / 256), 256, 0, c->stream>>>(c->da, c->z[l - 1], cnt, c->dz,
-                                                                                      c->dzb);
+        tslb::silu_back_kernel<<<(unsigned)((cnt + 255) / 256), 256, 0, c->stream>>>(c->da, c->z[l - 1], cnt,
+                                                                                      c->dz[l - 1], c->dzb);
     }
     return cudaGetLastError();
 }
@@ -1322,7 +1350,7 @@ lbm_status lbm_cnn_create(int nx, int ny, int nz, unsigned long long seed, void 
     } allocs[] = {
         {(void **)&c->p, ofs * sizeof(float)},         {(void **)&c->grad, ofs * sizeof(float)},
         {(void **)&c->m, ofs * sizeof(float)},         {(void **)&c->v, ofs * sizeof(float)},
-        {(void **)&c->dz, N * 32 * sizeof(float)},     {(void **)&c->da, N * 32 * sizeof(float)},
+        {(void **)&c->da, N * 32 * sizeof(float)},
         {(void **)&c->dzb, N * 32 * 2},                {(void **)&c->xbuf, 5 * N * sizeof(float)},
         {(void **)&c->ybuf, 4 * N * sizeof(float)},
         {(void **)&c->dsum, (size_t)(c->loss_blocks + 1) * sizeof(double)},
@@ -1338,6 +1366,7 @@ lbm_status lbm_cnn_create(int nx, int ny, int nz, unsigned long long seed, void 
         if (err == cudaSuccess && l > 0) err = cudaMalloc(&c->wut[l], (size_t)27 * CINP[l] * COUTP[l] * 2);
         if (err == cudaSuccess) err = cudaMalloc(&c->a[l], N * CINP[l] * 2);
         if (err == cudaSuccess) err = cudaMalloc(&c->z[l], N * COUTP[l] * sizeof(float));
+        if (err == cudaSuccess) err = cudaMalloc(&c->dz[l], N * COUTP[l] * sizeof(float));
     }
     if (err == cudaSuccess) err = cudaMallocHost(&c->h_sum, sizeof(double) * 2);
     if (err == cudaSuccess) err = cudaMalloc(&c->derr, sizeof(int));
@@ -1458,7 +1487,8 @@ lbm_status lbm_cnn_grad(lbm_cnn *cnn, const float *x, const float *t, int accumu
     if (!cnn || !x || !t) return cnn_fail(LBM_ERR_ARG, "network, x and t are required");
     if (!accumulate) CNN_TRY(cudaMemsetAsync(cnn->grad, 0, cnn->nparams * sizeof(float), cnn->stream));
     CNN_TRY(forward(cnn, x));
-    tslb::loss_kernel<<<cnn->loss_blocks, 256, 0, cnn->stream>>>(cnn->z[3], t, cnn->N, cnn->dz, cnn->dzb, cnn->dsum);
+    tslb::loss_kernel<<<cnn->loss_blocks, 256, 0, cnn->stream>>>(cnn->z[3], t, cnn->N, cnn->dz[3], cnn->dzb,
+                                                                  cnn->dsum);
     CNN_TRY(cudaGetLastError());
     CNN_TRY(backward(cnn));
     // loss: sum of the per-block partials
@@ -1476,6 +1506,44 @@ lbm_status lbm_cnn_grad(lbm_cnn *cnn, const float *x, const float *t, int accumu
     delete[] hp;
     if (loss) *loss = s / (4.0 * cnn->N);
     return check_timeout(cnn);
+}
+
+lbm_status lbm_cnn_get_layer(lbm_cnn *cnn, int layer, float *a_in, float *z, float *dz)
+{
+    if (!cnn) return cnn_fail(LBM_ERR_ARG, "network is NULL");
+    if (layer < 0 || layer >= tslb::NLAYER) return cnn_fail(LBM_ERR_ARG, "layer must be 0..3");
+    const size_t N = (size_t)cnn->N;
+    const int cin = tslb::CIN[layer], cinp = CINP[layer], cout = tslb::COUT[layer], coutp = COUTP[layer];
+    // copy the channel-last device buffer to the host, then reorder to channel-first there
+    if (a_in) {
+        uint16_t *h = new (std::nothrow) uint16_t[N * cinp];
+        if (!h) return cnn_fail(LBM_ERR_OOM, "host allocation failed");
+        cudaError_t e = cudaMemcpyAsync(h, cnn->a[layer], N * cinp * 2, cudaMemcpyDeviceToHost, cnn->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(cnn->stream);
+        if (e == cudaSuccess)
+            for (size_t n = 0; n < N; ++n)
+                for (int i = 0; i < cin; ++i) {
+                    const uint32_t bits = (uint32_t)h[n * cinp + i] << 16;   // BF16 is the top half of FP32
+                    memcpy(&a_in[(size_t)i * N + n], &bits, 4);
+                }
+        delete[] h;
+        if (e != cudaSuccess) return cnn_fail(LBM_ERR_CUDA, "layer input read-back: %s", cudaGetErrorString(e));
+    }
+    const float *src[2] = {cnn->z[layer], cnn->dz[layer]};
+    float *dst[2] = {z, dz};
+    for (int q = 0; q < 2; ++q) {
+        if (!dst[q]) continue;
+        float *h = new (std::nothrow) float[N * coutp];
+        if (!h) return cnn_fail(LBM_ERR_OOM, "host allocation failed");
+        cudaError_t e = cudaMemcpyAsync(h, src[q], N * coutp * sizeof(float), cudaMemcpyDeviceToHost, cnn->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(cnn->stream);
+        if (e == cudaSuccess)
+            for (size_t n = 0; n < N; ++n)
+                for (int o = 0; o < cout; ++o) dst[q][(size_t)o * N + n] = h[n * coutp + o];
+        delete[] h;
+        if (e != cudaSuccess) return cnn_fail(LBM_ERR_CUDA, "layer read-back: %s", cudaGetErrorString(e));
+    }
+    return LBM_OK;
 }
 
 lbm_status lbm_cnn_adam_step(lbm_cnn *cnn, float lr, float grad_scale)

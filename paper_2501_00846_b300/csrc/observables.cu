@@ -45,9 +45,10 @@ __global__ void __launch_bounds__(kThreads) obs_partial_kernel(Grid G, double rh
     r[F_PHIMAX] = -DBL_MAX;
     const size_t N = (size_t)G.N;
 
-    for (int k = blockIdx.x * kThreads + threadIdx.x; k < G.N; k += gridDim.x * kThreads) {
-        const int z = k / G.nxy;
-        const int rem = k - z * G.nxy;
+    // 64-bit node index: with N close to 2^31 an int index would wrap past INT_MAX on its last stride.
+    for (size_t k = (size_t)blockIdx.x * kThreads + threadIdx.x; k < N; k += (size_t)gridDim.x * kThreads) {
+        const int z = (int)(k / (size_t)G.nxy);
+        const int rem = (int)(k - (size_t)z * G.nxy);
         const int y = rem / G.nx;
         const int x = rem - y * G.nx;
         double ps = 0.0;
@@ -132,7 +133,7 @@ __global__ void obs_final_kernel(const double *__restrict__ partials, int nblock
 int observables_blocks(const Grid &G)
 {
     const long long need = ((long long)G.N + kThreads - 1) / kThreads;
-    return (int)(need < 148 * 8 ? need : 148 * 8);
+    return (int)(need < kObsMaxBlocks ? need : kObsMaxBlocks);
 }
 
 cudaError_t launch_observables(const Grid &G, double rho_l, double rho_g, const void *g, const float *phi,

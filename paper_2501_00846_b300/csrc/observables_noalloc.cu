@@ -27,10 +27,11 @@
 
 namespace {
 
-constexpr int kMaxBlocks = 148 * 8;   // the most blocks the reduction's first pass launches
+constexpr int kMaxBlocks = tslb::kObsMaxBlocks;   // the most blocks the reduction's first pass launches
 constexpr int kMaxDevices = 64;
 
 static __device__ __align__(256) double g_obs_scratch[(kMaxBlocks + 1) * tslb::kObsFields];
+static_assert(sizeof(g_obs_scratch) == 303360, "the scratch size is stated in lbm.h: update it there too");
 
 // Device address of the scratch array, looked up once per device with that device current.
 // In host code the name g_obs_scratch is only a host-side stand-in for the symbol, not a device

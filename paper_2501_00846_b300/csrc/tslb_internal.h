@@ -106,7 +106,9 @@ cudaError_t launch_pressure(const Grid &G, const Phys &P, int storage, const voi
 
 // FP64 reductions: number of doubles in one partial record, and the two-pass reduction.
 constexpr int kObsFields = 32;
-int observables_blocks(const Grid &G);
+// Most blocks the first pass launches (it strides over the grid beyond that): 8 per SM of a B300.
+constexpr int kObsMaxBlocks = 148 * 8;
+int observables_blocks(const Grid &G);   // min(ceil(N / 256), kObsMaxBlocks)
 // rho_l, rho_g in FP64 so the mass sum uses the exact parameter values.
 // p* is summed from the 27 FP32 population arrays g, or (storage 1 / 2, pst not null) is
 // P + sum_i w_i h_i of a 16-bit format whose h arrays g points to, or (storage 3..5) is the

@@ -25,6 +25,14 @@ def _grid(nx, ny, nz):
     return x, y, z
 
 
+def _axes(nx, ny, nz):
+    """Node coordinates as broadcastable axes of shapes (1, 1, nx), (1, ny, 1), (nz, 1, 1): the
+    same values as _grid without three full-size arrays (a 512^3 box would need 3 GB for them).
+    Callers must combine all three so that the result has the full (nz, ny, nx) shape."""
+    return (np.arange(nx, dtype=np.float64)[None, None, :], np.arange(ny, dtype=np.float64)[None, :, None],
+            np.arange(nz, dtype=np.float64)[:, None, None])
+
+
 def _min_image(d, n, periodic):
     if not periodic:
         return d
@@ -33,7 +41,7 @@ def _min_image(d, n, periodic):
 
 def sphere_phi(nx, ny, nz, center, radius, width, inside=1.0, periodic=(True, True, True)):
     """tanh sphere: phi -> inside at the centre, 1 - inside far away."""
-    x, y, z = _grid(nx, ny, nz)
+    x, y, z = _axes(nx, ny, nz)
     dx = _min_image(x - center[0], nx, periodic[0])
     dy = _min_image(y - center[1], ny, periodic[1])
     dz = _min_image(z - center[2], nz, periodic[2])
@@ -69,7 +77,7 @@ def fourier_velocity(nx, ny, nz, modes=8, amplitude=0.01, seed=1234):
     """Smooth random periodic velocity: `modes` random Fourier modes with wave numbers 1..2 per
     axis, random phases and directions, scaled so that max |u| = amplitude.  FP64."""
     rng = np.random.default_rng(seed)
-    x, y, z = _grid(nx, ny, nz)
+    x, y, z = _axes(nx, ny, nz)
     u = np.zeros((3, nz, ny, nx))
     for _ in range(modes):
         k = rng.integers(-2, 3, size=3)
@@ -147,7 +155,7 @@ class Workload:
         Laplace jump 2 sigma / R inside it, plus the hydrostatic head of the body force
         (rho - rho_ref) g in each phase, taken about the sphere's centre."""
         chi = self.inside()
-        x, y, z = _grid(self.nx, self.ny, self.nz)
+        x, y, z = _axes(self.nx, self.ny, self.nz)
         per = (True, True, not self.wall_z)
         r = [_min_image(c - c0, n, pp) for c, c0, n, pp in
              zip((x, y, z), self.center, (self.nx, self.ny, self.nz), per)]

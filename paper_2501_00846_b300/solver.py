@@ -143,6 +143,7 @@ def load(path: str = LIB_PATH):
         "lbm_cnn_get_params": ([vp, fp], i),
         "lbm_cnn_set_params": ([vp, fp], i),
         "lbm_cnn_get_grads": ([vp, fp], i),
+        "lbm_cnn_get_layer": ([vp, i, fp, fp, fp], i),
         "lbm_cnn_forward": ([vp, fp, fp], i),
         "lbm_cnn_set_conv_kernel": ([vp, i], i),
         "lbm_cnn_test_expire_wait": ([vp, i], i),
@@ -487,6 +488,17 @@ class Network:
         out = np.empty(self.num_params, np.float32)
         _check(load().lbm_cnn_get_grads(self._cnn, out.ctypes.data))
         return out
+
+    def get_layer(self, layer: int):
+        """(a_in [CIN][nz, ny, nx], z [COUT][...], dz [COUT][...]) of layer 0..3 as FP32 host arrays:
+        the layer's BF16 input widened to FP32, its pre-activation from the last forward or grad
+        call, and d loss / d z from the last grad call."""
+        cout, cin = CNN_LAYERS[layer]
+        a = np.empty((cin,) + self.shape, np.float32)
+        z = np.empty((cout,) + self.shape, np.float32)
+        dz = np.empty((cout,) + self.shape, np.float32)
+        _check(load().lbm_cnn_get_layer(self._cnn, int(layer), a.ctypes.data, z.ctypes.data, dz.ctypes.data))
+        return a, z, dz
 
     @staticmethod
     def split(flat):

@@ -1,11 +1,21 @@
 """Learned closure kernels against the FP64 reference network (oracle/closure_ref.py) and against
 their plain definitions.
 
-The GPU network multiplies BF16 weights by BF16 activations with FP32 accumulation, so its outputs
-and gradients differ from the FP64 reference by the BF16 rounding of both operands (unit roundoff
-2^-8 each, about 4e-3 per product, averaging down over the 27 x 32-term sums).  The bars: relative
-L2 error of the output 2e-2; of the gradient of every layer 3e-2, with cosine similarity >= 0.999
-to the reference gradient (a wrong sign, transpose or offset would give cosines far below 1).
+Element by element, link by link (test_every_operation_matches_its_definition_elementwise): the
+library's BF16 inputs, FP32 pre-activations and FP32 loss gradients of every layer are read back
+(lbm_cnn_get_layer) and each operation of the pass is checked at every element against its
+definition in the library's operand precision, evaluated in FP64 on the same values, within the
+rigorous bound of FP32 accumulation (closure_ref: layer_bound, activation_bound, input_grad_bound,
+weight_grad_bound; the FP32 loss gradient bit for bit).  Those bounds are below a quarter of one
+product term of a convolution, so one wrong neighbour, channel group or plane fails them; they run
+at the closure's 64^3 grid and on a ragged 64 x 40 x 37 grid (partial column tiles, uneven z
+chunks), on the tcgen05 kernel and the mma.sync kernel.  End to end, the output stays within the
+propagated bound of forward_lib at every element.
+
+Against the FP64 network itself (BF16 rounding of both operands, unit roundoff 2^-8 each, about
+4e-3 per product, averaging down over the 27 x 32-term sums): relative L2 error of the output
+2e-2; of the gradient of every layer 3e-2, with cosine similarity >= 0.999 to the reference
+gradient (a wrong sign, transpose or offset would give cosines far below 1).
 """
 import numpy as np
 import pytest
@@ -37,6 +47,25 @@ def _random_case(nx=32, ny=6, nz=5, seed=0):
         o += cout
     x = rng.standard_normal((5, nz, ny, nx)).astype(np.float32)
     t = (0.3 * rng.standard_normal((4, nz, ny, nx))).astype(np.float32)
+    return flat, x, t
+
+
+def _positive_case(nx, ny, nz, seed=0):
+    """Weights >= 0, biases > 0, inputs in [0, 1] and targets below the output: every activation,
+    loss gradient and layer gradient is positive, so no sum cancels and the weight-gradient bounds
+    are tight relative to the gradients themselves."""
+    rng = np.random.default_rng(seed)
+    flat = np.empty(solver.load().lbm_cnn_num_params(), np.float32)
+    o = 0
+    for cout, cin in solver.CNN_LAYERS:
+        n = cout * cin * 27
+        flat[o:o + n] = rng.uniform(0, 2.0 / (27 * cin), n)
+        o += n
+        flat[o:o + cout] = rng.uniform(0.05, 0.3, cout)
+        o += cout
+    x = rng.uniform(0, 1, (5, nz, ny, nx)).astype(np.float32)
+    y64, _ = R.forward(solver.Network.split(flat.astype(np.float64)), x.astype(np.float64))
+    t = (y64 - 0.5).astype(np.float32)
     return flat, x, t
 
 
@@ -277,3 +306,77 @@ def test_tensor_core_wait_expiry_is_reported_and_the_network_recovers():
         net.forward(x, y)
         assert torch.equal(y, y0)
         assert net.grad(x, t) == loss0
+
+
+def _dweight_chain(nx, ny, nz):
+    """Most FP32 additions along one product's path in the weight-gradient kernel, for any z split:
+    16 inside its MMA, at most 16 nz accumulations in its block (16 MMAs of a 32 x 8 column tile
+    per plane, at most nz planes), and at most (column tiles x nz) block partials in the ordered
+    reduction."""
+    tiles = (nx // 32) * (-(-ny // 8))
+    return 16 + 16 * nz + tiles * nz
+
+
+@pytest.mark.parametrize("shape,kernel,positive", [
+    ((64, 64, 64), 0, False), ((64, 64, 64), 0, True), ((64, 40, 37), 0, False), ((64, 40, 37), 1, False)],
+    ids=["64cube-tcgen05", "64cube-tcgen05-positive", "ragged-tcgen05", "ragged-mma.sync"])
+def test_every_operation_matches_its_definition_elementwise(shape, kernel, positive):
+    import torch
+    nx, ny, nz = shape
+    flat, x, t = (_positive_case if positive else _random_case)(nx, ny, nz, seed=11)
+    params = solver.Network.split(flat.astype(np.float64))
+    with solver.Network(nx, ny, nz) as net:
+        net.set_conv_kernel(kernel)
+        net.set_params(flat)
+        xd = torch.from_numpy(x).cuda().reshape(-1)
+        td = torch.from_numpy(t).cuda().reshape(-1)
+        yd = torch.empty(4 * net.n, device="cuda")
+        net.forward(xd, yd)
+        net.grad(xd, td)
+        torch.cuda.synchronize()
+        y = yd.cpu().numpy().reshape(4, nz, ny, nx)
+        grads = solver.Network.split(net.get_grads())
+        layers = [net.get_layer(l) for l in range(4)]
+    worst = check_against_definitions(params, x, t, y, grads, layers)
+    y64, _ = R.forward(params, x.astype(np.float64))
+    err = _rel(y, y64)
+    print(f"{shape} kernel {kernel}{' positive' if positive else ''}: rel L2 vs FP64 {err:.2e}; "
+          "largest |error| / bound: " + ", ".join(f"{k} {v:.2g}" for k, v in worst.items()))
+    assert err < 2e-2
+
+
+def check_against_definitions(params, x, t, y, grads, layers):
+    """Every element of every operation of one forward and backward pass (the library's values y,
+    grads [(dW, db)], layers [(a_in, z, dz)]) against its definition; returns the largest
+    |error| / bound of each."""
+    nz, ny, nx = x.shape[1:]
+    worst = {}
+
+    def within(name, got, ref, bound):
+        ex = np.abs(np.asarray(got, np.float64) - ref) - bound
+        assert (ex <= 0).all(), f"{name}: {int((ex > 0).sum())} elements outside the bound, worst excess {ex.max():.3e}"
+        worst[name] = float((np.abs(np.asarray(got, np.float64) - ref) / np.maximum(bound, 1e-300)).max())
+
+    assert np.array_equal(layers[0][0], R.bf16(x)), "layer-0 input is not bf16(x)"
+    for l in range(4):
+        a, z, _ = layers[l]
+        zr, bz = R.layer_bound(*params[l], a)
+        within(f"z{l}", z, zr, bz)
+        if l < 3:
+            r, ea = R.activation_bound(z)
+            within(f"a{l + 1}", layers[l + 1][0], r, ea)
+    assert np.array_equal(y, layers[3][1]), "output differs from the last pre-activation"
+    assert np.array_equal(layers[3][2], R.loss_grad_fp32(layers[3][1], t)), "loss gradient is not the FP32 one"
+    for l in range(3, 0, -1):
+        ref, bz = R.input_grad_bound(params[l][0], layers[l][2], layers[l - 1][1])
+        within(f"dz{l - 1}", layers[l - 1][2], ref, bz)
+    n = nx * ny * nz
+    for l in range(4):
+        a, _, dz = layers[l]
+        dW, bW = R.weight_grad_bound(dz, a, _dweight_chain(nx, ny, nz))
+        within(f"dW{l}", grads[l][0], dW, bW)
+        dz64 = dz.astype(np.float64)
+        within(f"db{l}", grads[l][1], dz64.sum(axis=(1, 2, 3)), R.chain_gamma(n) * np.abs(dz64).sum(axis=(1, 2, 3)))
+    fwd = R.forward_lib(params, x)
+    within("y (end to end)", y, fwd[-1]["z"], fwd[-1]["D"])
+    return worst

@@ -228,3 +228,33 @@ def test_literal_advection_form():
     drift = -(u * _grad27(phi)).sum()
     assert abs(drift) > 1e-4
     assert abs((b.sum() - phi.sum()) - drift) < 1e-12 * phi.sum()
+
+
+def test_literal_sharpening_weight_differs_only_where_phi_leaves_the_unit_interval():
+    """Reading R15 against the printed weight phi (1 - phi) (Params.literal_weight = 1).  On a
+    field inside [0, 1] the two updates are the same bits.  With planted overshoots the difference
+    of one update is exactly -kappa_AC div(min(phi (1 - phi), 0) n) (the term R15 drops), the
+    printed weight's sharpening flux at the overshoots, and both forms conserve sum phi."""
+    L = 10
+    base = dict(rho_l=1.0, rho_g=0.1, mu_l=0.1, mu_g=0.01, sigma=0.01, mobility=0.1, width=4.0)
+    P0, P1 = oracle.Params(L, L, L, **base), oracle.Params(L, L, L, literal_weight=1, **base)
+    phi = inputs.sphere_phi(L, L, L, (4.6, 5.2, 4.9), 3.0, 4.0, periodic=(True, True, True))
+    u = inputs.fourier_velocity(L, L, L, amplitude=0.01, seed=3)
+    assert phi.min() >= 0.0 and phi.max() <= 1.0
+    assert np.array_equal(oracle.ac_update(P0, phi, u), oracle.ac_update(P1, phi, u))
+    rng = np.random.default_rng(5)
+    over = phi.copy()
+    bulk = np.abs(phi - 0.5) > 0.3              # plant overshoots in both bulk phases
+    over[bulk] += np.sign(phi[bulk] - 0.5) * 0.02 * rng.random(int(bulk.sum()))
+    over[bulk] = np.where(phi[bulk] > 0.5, np.maximum(over[bulk], 1.0 + 1e-3 * rng.random(int(bulk.sum()))),
+                          np.minimum(over[bulk], -1e-3 * rng.random(int(bulk.sum()))))
+    assert over.max() > 1.0 and over.min() < 0.0
+    a, b = oracle.ac_update(P0, over, u), oracle.ac_update(P1, over, u)
+    g = oracle.grad(P0, over)
+    n = g / np.maximum(np.sqrt((g ** 2).sum(axis=0)), 1e-12)
+    dropped = np.minimum(over * (1.0 - over), 0.0)
+    kac = 4.0 * P0.mobility / P0.width
+    expect = -kac * oracle.div(P0, dropped[None] * n)
+    assert np.abs(b - a).max() > 1e-6
+    np.testing.assert_allclose(b - a, expect, atol=1e-15)
+    assert abs(a.sum() - over.sum()) < 1e-12 * over.sum() and abs(b.sum() - over.sum()) < 1e-12 * over.sum()
