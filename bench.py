@@ -24,6 +24,8 @@ larger than the 126 MB L2, so consecutive steps stream from HBM and no flush is 
          ratio 100, Eo = 10, Mo = 1e-4) with FP32 populations and with BF16 moments.
   ensemble  the batched ensemble of 256 seeded droplets (32^3 .. 96^3 boxes): autotuned, min(K, 400)
          steps from CUDA graphs, next to the same boxes advanced one context at a time.
+  closure_network  the learned closure's network on the 64^3 coarse grid: device time of a forward
+         pass (and its useful BF16 TFLOP/s against the measured tensor peak) and of a training step.
   cpu_baseline  the FP64 oracle (plain C, OpenMP) on the host cores, on a bounded sub-box of the
          same workload.
 
@@ -164,6 +166,16 @@ def measured_traffic(kernel, wl_name, nodes, store="fp32"):
     except (KeyError, ValueError):
         return None
     return b * nodes / n
+
+
+def bf16_peak():
+    """Dense BF16 tensor peak in TFLOP/s: the measured burst figure (a network pass is timed on its
+    own), else the fallback."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return float(json.load(fh)["bf16_tflops"])
+    except (OSError, KeyError, ValueError):
+        return 1800.0
 
 
 def hbm_peak():
@@ -314,14 +326,16 @@ def run_ensemble(args, stream):
     f32 = lambda a: None if a is None else np.ascontiguousarray(a, np.float32)
     fields = [(f32(wl.phi0()), f32(wl.u0()), f32(wl.pstar_init())) for wl in wls]
 
-    def batched(storage):
+    def batched(storage, persistent=False):
         """Autotuned batched run of every box with one storage: (ms per ke steps, tuning, boxes
-        that went non-finite)."""
+        that went non-finite).  persistent: one cooperative launch per step instead of the two
+        graph-replayed launches."""
         e = solver.Ensemble([dict(wl.params(), storage=storage) for wl in wls], stream=stream)
         for b, (phi0, u0, ps0) in enumerate(fields):
             e.init_fields(b, phi0, u0, ps0)
         e.step(2)
         tun = e.autotune(reps=3)
+        e.set_persistent(persistent)
         e.step(16)
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -337,6 +351,8 @@ def run_ensemble(args, stream):
     with torch.cuda.stream(stream):
         ms, tun, bad = batched(solver.LBM_FP32)
         ms_m, tun_m, bad_m = batched(solver.LBM_MOM_BF16)
+        ms_p, _, bad_p = batched(solver.LBM_FP32, persistent=True)
+        ms_pm, _, bad_pm = batched(solver.LBM_MOM_BF16, persistent=True)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         # the same boxes one context each, every box stepped in turn
         ku = 20
@@ -369,7 +385,12 @@ def run_ensemble(args, stream):
             "speedup": value / unbatched, "boxes_nonfinite": int(bad),
             "bf16_moments": {"value": n_nodes * ke / (ms_m * 1e-3) / 1e6, "unit": "MLUPS", "steps": ke,
                              "ms_per_step": ms_m / ke, "ac_us": tun_m["ac_us"], "lbm_us": tun_m["lbm_us"],
-                             "boxes_nonfinite": int(bad_m)}}
+                             "boxes_nonfinite": int(bad_m)},
+            "persistent": {"launches_per_step": 1,
+                           "fp32": {"value": n_nodes * ke / (ms_p * 1e-3) / 1e6, "unit": "MLUPS", "steps": ke,
+                                    "ms_per_step": ms_p / ke, "boxes_nonfinite": int(bad_p)},
+                           "bf16_moments": {"value": n_nodes * ke / (ms_pm * 1e-3) / 1e6, "unit": "MLUPS",
+                                            "steps": ke, "ms_per_step": ms_pm / ke, "boxes_nonfinite": int(bad_pm)}}}
 
 
 def main():
@@ -391,6 +412,7 @@ def main():
     ap.add_argument("--no-store-compare", action="store_true")
     ap.add_argument("--no-ensemble", action="store_true", help="skip the 256-droplet batched ensemble")
     ap.add_argument("--no-bubble", action="store_true", help="skip the rising bubble beside a droplet workload")
+    ap.add_argument("--no-closure", action="store_true", help="skip timing the learned closure's network")
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")
@@ -538,6 +560,12 @@ def main():
         del bf
 
     ensemble = None if args.no_ensemble or rank != 0 else run_ensemble(args, stream)
+    closure_net = None
+    if not args.no_closure and rank == 0:
+        from paper_2501_00846_b300 import closure
+        closure_net = closure.time_network(64, reps=20, stream=stream)
+        closure_net["peak_tflops"] = bf16_peak()
+        closure_net["frac"] = closure_net["forward_tflops"] / closure_net["peak_tflops"]
 
     if rank != 0:
         if world > 1:
@@ -580,6 +608,8 @@ def main():
         line["rising_bubble"] = bubble
     if ensemble is not None:
         line["ensemble"] = ensemble
+    if closure_net is not None:
+        line["closure_network"] = closure_net
     if world == 1 and not args.no_cpu_baseline:
         import oracle
         v, desc, cores = oracle_sample(args.cpu_seconds, args.workload)

@@ -312,6 +312,23 @@ lbm_status lbm_ens_get_tuning(const lbm_ens *ens, lbm_tuning *out);
 lbm_status lbm_ens_set_tuning(lbm_ens *ens, const lbm_tuning *t);
 lbm_status lbm_ens_autotune(lbm_ens *ens, int reps, lbm_tuning *out);
 
+/* Launch form of lbm_ens_step.  on = 0 (default): two launches per step, replayed from the CUDA
+ * graph.  on = 1: one persistent cooperative launch per step (as many 256-thread CTAs as the GPU
+ * holds at once): every warp takes Allen–Cahn tasks, the CTAs meet at a grid barrier, then take
+ * the lattice Boltzmann work; results are bit-identical to the two-launch form.  Each wait at the
+ * barrier is bounded (100 ms of the GPU's global timer); when one expires, that launch and every
+ * later one of the same lbm_ens_step call do nothing further, and lbm_ens_step returns
+ * LBM_ERR_TIMEOUT with the state of the last completed step (its step count, fields and flux), so
+ * the ensemble stays usable.  In this form lbm_ens_step synchronises the stream before it returns.
+ * Synchronises the stream.  LBM_ERR_ARG for other values of on. */
+lbm_status lbm_ens_set_persistent(lbm_ens *ens, int on);
+
+/* Test hook of the bounded barrier: with on = 1, CTA 0 of every persistent launch skips its arrival
+ * at the grid barrier and the wait limit drops to 2 ms, so every wait expires and lbm_ens_step
+ * returns LBM_ERR_TIMEOUT without advancing the state.  on = 0 restores normal operation
+ * (100 ms).  Synchronises the stream. */
+lbm_status lbm_ens_test_stall_barrier(lbm_ens *ens, int on);
+
 /* Set the state of a coarse context (FP32 storage, half the box's size in every direction, same
  * parameters rescaled by the caller) to the 2x restriction of box b's state: the populations, phi
  * and ubar of each coarse cell are the means over its 8 fine nodes.  Enqueued on the coarse

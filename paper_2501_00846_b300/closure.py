@@ -198,6 +198,43 @@ def evaluate(net, norm, col, coarse_steps=240, every=24, stream=None, apply_ever
     return out
 
 
+# useful multiply-adds per node of one forward pass: 27 offsets x (5x32 + 32x32 + 32x32 + 32x4)
+FORWARD_MACS_PER_NODE = 27 * sum(o * i for o, i in solver.CNN_LAYERS)
+
+
+def time_network(L=64, reps=50, kernel=0, seed=3, stream=None):
+    """Device time of one forward pass and of one training step (forward, loss, backward) of the
+    network on an L^3 grid with seeded inputs, CUDA events over `reps` calls each after a warm-up.
+    Returns a dict with milliseconds and the forward pass's useful TFLOP/s (2 flops per
+    multiply-add of the unpadded channels)."""
+    import torch
+    stream = stream or torch.cuda.current_stream()
+    with torch.cuda.stream(stream), solver.Network(L, L, L, seed=seed, stream=stream) as net:
+        net.set_conv_kernel(kernel)
+        g = torch.Generator(device="cuda").manual_seed(seed)
+        x = torch.randn(5 * net.n, device="cuda", generator=g)
+        t = 0.1 * torch.randn(4 * net.n, device="cuda", generator=g)
+        y = torch.empty(4 * net.n, device="cuda")
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+
+        def timed(fn):
+            for _ in range(3):
+                fn()
+            torch.cuda.synchronize()
+            ev[0].record(stream)
+            for _ in range(reps):
+                fn()
+            ev[1].record(stream)
+            torch.cuda.synchronize()
+            return ev[0].elapsed_time(ev[1]) / reps
+
+        fwd = timed(lambda: net.forward(x, y))
+        grad = timed(lambda: net.grad(x, t))
+        n = net.n
+    return {"grid": f"{L}^3", "kernel": kernel, "forward_ms": fwd, "train_step_ms": grad,
+            "forward_tflops": 2.0 * FORWARD_MACS_PER_NODE * n / (fwd * 1e-3) / 1e12}
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description="train and evaluate the learned closure")
     ap.add_argument("--traj", type=int, default=200)
@@ -217,9 +254,15 @@ def main(argv=None):
     ap.add_argument("--every", type=int, default=1, help="coarse steps per correction")
     ap.add_argument("--u-relax", type=float, default=0.0,
                     help="factor on the applied velocity correction (0: the phi correction alone)")
+    ap.add_argument("--time-network", type=int, default=0, metavar="L",
+                    help="only time the network's forward pass and training step on an L^3 grid")
+    ap.add_argument("--reps", type=int, default=50)
     a = ap.parse_args(argv)
     import torch
     torch.cuda.set_device(0)
+    if a.time_network:
+        print(json.dumps(time_network(a.time_network, reps=a.reps)))
+        return 0
     log = lambda m: print(m, file=sys.stderr, flush=True)
     cols = inputs.collision_set(a.traj + a.eval, seed=a.seed, L=a.L, R=a.L * 20.0 / 128.0)
     train_cols, eval_cols = cols[:a.traj], cols[a.traj:]

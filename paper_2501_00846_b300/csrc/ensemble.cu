@@ -26,6 +26,7 @@
 #include <string.h>
 
 #include <new>
+#include <type_traits>
 #include <vector>
 
 #include <cuda_runtime.h>
@@ -143,6 +144,154 @@ __global__ void __launch_bounds__(AC_WPB * 32) ens_ac_kernel(const EnsBox *__res
     }
 }
 
+// ---- one persistent launch per step ------------------------------------------------------------
+//
+// The persistent form runs a whole step in one cooperative launch of as many 256-thread CTAs as
+// fit on the GPU at once: every warp takes Allen–Cahn tasks from the concatenated task list, the
+// CTAs meet at a grid barrier, then every CTA takes lattice Boltzmann work (node blocks of
+// lbm_block threads, or the moment storages' column-tile tasks).  The barrier is a counter and a
+// generation word in global memory; a CTA's wait for the generation to move on is bounded by
+// EnsSync::limit_ns of the GPU's global timer.  On expiry the CTA records the failure and returns
+// without its lattice Boltzmann work; every later launch sees the record and returns at once, so
+// the state of the last completed step is kept (apart from the flux W, which the host recomputes).
+
+struct EnsSync {
+    unsigned count;                 // CTAs arrived at the current barrier
+    unsigned gen;                   // barrier generation: moves on when the last CTA arrives
+    int err;                        // a wait expired; later launches do nothing
+    unsigned done;                  // CTAs that completed a step (a step adds gridDim.x)
+    unsigned long long limit_ns;    // bound of one barrier wait
+    int stall;                      // test hook: CTA 0 does not arrive at the barrier
+};
+
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned *p)
+{
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ unsigned long long gtimer_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Grid barrier of a cooperative launch: false if this CTA gave up after sync->limit_ns.
+__device__ __forceinline__ bool ens_grid_barrier(EnsSync *sync, bool arrive)
+{
+    __shared__ int ok_s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        const unsigned g = ld_acquire_u32(&sync->gen);
+        if (arrive) {
+            __threadfence();   // this CTA's writes before its arrival
+            if (atomicAdd(&sync->count, 1u) == gridDim.x - 1) {
+                atomicExch(&sync->count, 0u);
+                __threadfence();
+                atomicAdd(&sync->gen, 1u);
+            }
+        }
+        const unsigned long long t0 = gtimer_ns(), limit = sync->limit_ns;
+        while (ld_acquire_u32(&sync->gen) == g) {
+            if (gtimer_ns() - t0 > limit) {
+                ok = 0;
+                break;
+            }
+            __nanosleep(200);
+        }
+        __threadfence();
+        ok_s = ok;
+    }
+    __syncthreads();
+    return ok_s != 0;
+}
+
+// STORE: LBM_FP32 or one of the moment storages (LBM_MOM, LBM_MOM_BF16, LBM_MOM_FP16)
+template <int RY, int STORE>
+__global__ void __launch_bounds__(256, 2)
+    ens_persistent_kernel(const EnsBox *__restrict__ boxes, int nb, int ac_tasks, int lbm_work, int lbm_block,
+                          int fpn, const float *__restrict__ phi, const float *__restrict__ w,
+                          float *__restrict__ phi_new, const float *__restrict__ g_in, const float *__restrict__ u_in,
+                          float *__restrict__ g_out, float *__restrict__ u_out, float *__restrict__ w_out,
+                          EnsSync *sync)
+{
+    __shared__ int failed;
+    if (threadIdx.x == 0) failed = *(volatile int *)&sync->err;
+    __syncthreads();
+    if (failed) return;   // an earlier step failed: keep its state
+    // phase 1: Allen–Cahn tasks, one warp each
+    const int nwarps = gridDim.x * 8;
+    for (int task = blockIdx.x * 8 + (threadIdx.x >> 5); task < ac_tasks; task += nwarps) {
+        const int b = find_box<1>(boxes, nb, task);
+        const Grid G = boxes[b].G;
+        const Phys P = boxes[b].P;
+        const size_t o = (size_t)boxes[b].off;
+        const int local = task - boxes[b].task0;
+        const int ncols = boxes[b].ncols, zlen = boxes[b].zlen;
+        const int col = local % ncols;
+        const int z0 = (local / ncols) * zlen;
+        const int zend = min(G.nz, z0 + zlen);
+        if (G.wall)
+            ac_div_task<true, RY>(G, P, phi + o, w + 3 * o, phi_new + o, col, z0, zend);
+        else
+            ac_div_task<false, RY>(G, P, phi + o, w + 3 * o, phi_new + o, col, z0, zend);
+    }
+    if (!ens_grid_barrier(sync, !(sync->stall && blockIdx.x == 0))) {
+        if (threadIdx.x == 0) atomicExch(&sync->err, 1);
+        return;
+    }
+    // phase 2: lattice Boltzmann work
+    if constexpr (STORE == LBM_FP32) {
+        const long long total = (long long)lbm_work * lbm_block;
+        for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < total;
+             v += (long long)gridDim.x * blockDim.x) {
+            const int vblk = (int)(v / lbm_block);
+            const int b = find_box<0>(boxes, nb, vblk);
+            const Grid G = boxes[b].G;
+            const int node = (vblk - boxes[b].blk0) * lbm_block + (int)(v - (long long)vblk * lbm_block);
+            if (node >= G.N) continue;
+            const Phys P = boxes[b].P;
+            const size_t o = (size_t)boxes[b].off;
+            const int z = node / G.nxy;
+            const int rem = node - z * G.nxy;
+            const int y = rem / G.nx;
+            const int x = rem - y * G.nx;
+            lbm_node<StoreF32>(G, P, g_in + 27 * o, nullptr, phi_new + o, u_in + 3 * o, g_out + 27 * o, nullptr,
+                               u_out + 3 * o, w_out + 3 * o, x, y, z);
+        }
+    } else {
+        using S = typename std::conditional<STORE == LBM_MOM, StoreF32,
+                                            typename std::conditional<STORE == LBM_MOM_BF16, StoreB16,
+                                                                      StoreF16>::type>::type;
+        for (int task = blockIdx.x; task < lbm_work; task += gridDim.x) {
+            const int b = find_box<2>(boxes, nb, task);
+            const Grid G = boxes[b].G;
+            const Phys P = boxes[b].P;
+            const size_t o = (size_t)boxes[b].off;
+            const int tiles_x = (G.nx + momt::MX - 1) / momt::MX, tiles_y = (G.ny + momt::MY - 1) / momt::MY;
+            int t = task - boxes[b].mtask0;
+            const int tx = t % tiles_x;
+            t /= tiles_x;
+            const int ty = t % tiles_y;
+            const int z0 = (t / tiles_y) * boxes[b].mzlen;
+            const int z1 = min(z0 + boxes[b].mzlen, G.nz);
+            const float *mi = g_in + (size_t)fpn * o;
+            float *mo = g_out + (size_t)fpn * o;
+            __syncthreads();   // the previous task's shared memory is free
+            if (G.wall)
+                momt::mom_tile_task<true, S>(G, P, mi, u_in + 3 * o, phi_new + o, mo, u_out + 3 * o, w_out + 3 * o,
+                                             tx * momt::MX, ty * momt::MY, z0, z1);
+            else
+                momt::mom_tile_task<false, S>(G, P, mi, u_in + 3 * o, phi_new + o, mo, u_out + 3 * o,
+                                              w_out + 3 * o, tx * momt::MX, ty * momt::MY, z0, z1);
+        }
+    }
+    if (threadIdx.x == 0) atomicAdd(&sync->done, 1u);
+}
+
 // 2x restriction of one box's state into a coarse state of half the size in every direction: the
 // populations, phi and ubar of the coarse cell are the means over its 8 fine nodes (the means of
 // the populations carry the fine non-equilibrium part over to the coarse grid).
@@ -227,6 +376,10 @@ struct lbm_ens {
     int ac_bps[2] = {0, 0};           // resident Allen–Cahn CTAs per SM, ac_rows 2 and 4
     int lbm_blocks = 0, ac_tasks = 0, ac_ctas = 0;
     cudaGraphExec_t exec = nullptr;   // graph_steps steps from cur = 0
+    int persistent = 0;               // 1: one cooperative launch per step (ens_persistent_kernel)
+    int pers_ctas[2] = {0, 0};        // co-resident CTAs of the persistent kernel, ac_rows 2 and 4
+    tslb::EnsSync *sync = nullptr;    // barrier state of the persistent kernel
+    unsigned done_seen = 0;           // sync->done after the last completed persistent step
 };
 
 namespace {
@@ -241,6 +394,7 @@ void free_ens(lbm_ens *e)
         cudaFree(e->u[b]);
     }
     cudaFree(e->w);
+    cudaFree(e->sync);
     cudaFree(e->box_d);
     cudaFree(e->partials);
     cudaFree(e->result);
@@ -339,6 +493,86 @@ cudaError_t ens_launch_step(lbm_ens *e, int a, cudaStream_t s)
     return ens_launch_lbm(e, a, s);
 }
 
+lbm_status recompute_flux(lbm_ens *e);
+
+template <int RY, int STORE>
+cudaError_t ens_persistent_launch(lbm_ens *e, int a, cudaStream_t s)
+{
+    int ac_tasks = e->ac_tasks, lbm_work = STORE == LBM_FP32 ? e->lbm_blocks : e->mom_tasks, lbm_block = e->tun.lbm_block,
+        fpn = e->fpn, nb = e->nb;
+    const EnsBox *boxes = e->box_d;
+    const float *phi = e->phi[a], *w = e->w, *g_in = e->g[a], *u_in = e->u[a];
+    float *phi_new = e->phi[1 - a], *g_out = e->g[1 - a], *u_out = e->u[1 - a], *w_out = e->w;
+    tslb::EnsSync *sync = e->sync;
+    void *args[] = {&boxes, &nb, &ac_tasks, &lbm_work, &lbm_block, &fpn, &phi, &w, &phi_new,
+                    &g_in, &u_in, &g_out, &u_out, &w_out, &sync};
+    const size_t smem = STORE == LBM_FP32 ? 0 : tslb::momt::kMomSmem;
+    return cudaLaunchCooperativeKernel((const void *)tslb::ens_persistent_kernel<RY, STORE>,
+                                       dim3(e->pers_ctas[RY == 2 ? 0 : 1]), dim3(256), args, smem, s);
+}
+
+template <int RY>
+cudaError_t ens_persistent_step(lbm_ens *e, int a, cudaStream_t s)
+{
+    switch (e->storage) {
+    case LBM_MOM: return ens_persistent_launch<RY, LBM_MOM>(e, a, s);
+    case LBM_MOM_BF16: return ens_persistent_launch<RY, LBM_MOM_BF16>(e, a, s);
+    case LBM_MOM_FP16: return ens_persistent_launch<RY, LBM_MOM_FP16>(e, a, s);
+    default: return ens_persistent_launch<RY, LBM_FP32>(e, a, s);
+    }
+}
+
+// Co-resident CTAs of the persistent kernel (ac_rows 2 and 4) for the ensemble's storage.
+template <int STORE>
+cudaError_t ens_persistent_setup(lbm_ens *e)
+{
+    const size_t smem = STORE == LBM_FP32 ? 0 : tslb::momt::kMomSmem;
+    int bps[2] = {0, 0};
+    cudaError_t err = cudaFuncSetAttribute(tslb::ens_persistent_kernel<2, STORE>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err == cudaSuccess)
+        err = cudaFuncSetAttribute(tslb::ens_persistent_kernel<4, STORE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)smem);
+    if (err == cudaSuccess)
+        err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps[0], tslb::ens_persistent_kernel<2, STORE>, 256, smem);
+    if (err == cudaSuccess)
+        err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps[1], tslb::ens_persistent_kernel<4, STORE>, 256, smem);
+    e->pers_ctas[0] = bps[0] * e->sms;
+    e->pers_ctas[1] = bps[1] * e->sms;
+    return err;
+}
+
+// Persistent steps: one cooperative launch each, then the barrier record is read.  Returns the
+// steps completed; *timed_out when a barrier wait expired (the state is that of the last
+// completed step, its flux W recomputed, and the record reset).
+lbm_status ens_persistent_run(lbm_ens *e, int nsteps)
+{
+    for (int k = 0; k < nsteps; ++k) {
+        const int a = e->cur ^ (k & 1);
+        ENS_TRY(e->tun.ac_rows == 2 ? ens_persistent_step<2>(e, a, e->stream) : ens_persistent_step<4>(e, a, e->stream));
+    }
+    tslb::EnsSync h;
+    ENS_TRY(cudaMemcpyAsync(&h, e->sync, sizeof h, cudaMemcpyDeviceToHost, e->stream));
+    ENS_TRY(cudaStreamSynchronize(e->stream));
+    const unsigned grid = (unsigned)e->pers_ctas[e->tun.ac_rows == 2 ? 0 : 1];
+    const unsigned completed = (h.done - e->done_seen) / grid;
+    e->done_seen += completed * grid;
+    e->cur ^= (int)(completed & 1u);
+    e->step += completed;
+    if (!h.err) return LBM_OK;
+    // a wait expired: reset the record (the counter of a barrier that never completed, the done
+    // count of CTAs of an incomplete step) and recompute the flux of the kept state
+    h.count = 0;
+    h.err = 0;
+    h.done = e->done_seen;
+    ENS_TRY(cudaMemcpyAsync(e->sync, &h, sizeof h, cudaMemcpyHostToDevice, e->stream));
+    lbm_status st = recompute_flux(e);
+    if (st != LBM_OK) return st;
+    ENS_TRY(cudaStreamSynchronize(e->stream));
+    return ens_fail(LBM_ERR_TIMEOUT, "a grid barrier wait of the persistent step expired after %u of %d steps",
+                    completed, nsteps);
+}
+
 // Capture graph_steps steps starting from buffers 0 on the private stream.
 lbm_status build_graph(lbm_ens *e)
 {
@@ -435,6 +669,7 @@ lbm_status lbm_ens_create(const lbm_params *params, int nboxes, void *stream, lb
         {(void **)&e->phi[0], N * sizeof(float)},    {(void **)&e->phi[1], N * sizeof(float)},
         {(void **)&e->u[0], 3 * N * sizeof(float)},  {(void **)&e->u[1], 3 * N * sizeof(float)},
         {(void **)&e->w, 3 * N * sizeof(float)},     {(void **)&e->box_d, nboxes * sizeof(EnsBox)},
+        {(void **)&e->sync, sizeof(tslb::EnsSync)},
         {(void **)&e->partials, (size_t)max_obs * tslb::kObsFields * sizeof(double)},
         {(void **)&e->result, tslb::kObsFields * sizeof(double)},
     };
@@ -456,6 +691,19 @@ lbm_status lbm_ens_create(const lbm_params *params, int nboxes, void *stream, lb
         err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&e->ac_bps[0], tslb::ens_ac_kernel<2>, tslb::AC_WPB * 32, 0);
     if (err == cudaSuccess)
         err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&e->ac_bps[1], tslb::ens_ac_kernel<4>, tslb::AC_WPB * 32, 0);
+    if (err == cudaSuccess) {   // barrier record: no arrivals, 100 ms per wait
+        tslb::EnsSync h{};
+        h.limit_ns = 100000000ull;
+        err = cudaMemcpy(e->sync, &h, sizeof h, cudaMemcpyHostToDevice);
+    }
+    if (err == cudaSuccess) {
+        switch (e->storage) {
+        case LBM_MOM: err = ens_persistent_setup<LBM_MOM>(e); break;
+        case LBM_MOM_BF16: err = ens_persistent_setup<LBM_MOM_BF16>(e); break;
+        case LBM_MOM_FP16: err = ens_persistent_setup<LBM_MOM_FP16>(e); break;
+        default: err = ens_persistent_setup<LBM_FP32>(e); break;
+        }
+    }
     if (err == cudaSuccess && e->storage == LBM_MOM) err = ens_prepare_mom<tslb::StoreF32>();
     if (err == cudaSuccess && e->storage == LBM_MOM_BF16) err = ens_prepare_mom<tslb::StoreB16>();
     if (err == cudaSuccess && e->storage == LBM_MOM_FP16) err = ens_prepare_mom<tslb::StoreF16>();
@@ -525,6 +773,7 @@ lbm_status lbm_ens_step(lbm_ens *ens, int nsteps)
     if (!ens) return ens_fail(LBM_ERR_ARG, "ensemble is NULL");
     if (nsteps < 0) return ens_fail(LBM_ERR_ARG, "nsteps must be >= 0");
     if (!all_ready(ens)) return ens_fail(LBM_ERR_STATE, "lbm_ens_step before every box was initialised");
+    if (ens->persistent) return ens_persistent_run(ens, nsteps);
     const int K = ens->tun.graph_steps;
     while (nsteps > 0) {
         if (K >= 2 && ens->cur == 0 && nsteps >= K) {
@@ -707,6 +956,31 @@ lbm_status lbm_ens_autotune(lbm_ens *ens, int reps, lbm_tuning *out)
         if (out) *out = ens->tun;
     }
     return st;
+}
+
+lbm_status lbm_ens_set_persistent(lbm_ens *ens, int on)
+{
+    if (!ens) return ens_fail(LBM_ERR_ARG, "ensemble is NULL");
+    if (on != 0 && on != 1) return ens_fail(LBM_ERR_ARG, "on must be 0 or 1");
+    if (on && (ens->pers_ctas[0] < 1 || ens->pers_ctas[1] < 1))
+        return ens_fail(LBM_ERR_CUDA, "the persistent ensemble kernel does not fit an SM");
+    ENS_TRY(cudaStreamSynchronize(ens->stream));
+    ens->persistent = on;
+    return LBM_OK;
+}
+
+lbm_status lbm_ens_test_stall_barrier(lbm_ens *ens, int on)
+{
+    if (!ens) return ens_fail(LBM_ERR_ARG, "ensemble is NULL");
+    if (on != 0 && on != 1) return ens_fail(LBM_ERR_ARG, "on must be 0 or 1");
+    tslb::EnsSync h;
+    ENS_TRY(cudaMemcpyAsync(&h, ens->sync, sizeof h, cudaMemcpyDeviceToHost, ens->stream));
+    ENS_TRY(cudaStreamSynchronize(ens->stream));
+    h.stall = on;
+    h.limit_ns = on ? 2000000ull : 100000000ull;
+    ENS_TRY(cudaMemcpyAsync(ens->sync, &h, sizeof h, cudaMemcpyHostToDevice, ens->stream));
+    ENS_TRY(cudaStreamSynchronize(ens->stream));
+    return LBM_OK;
 }
 
 lbm_status lbm_ens_restrict_state(lbm_ens *ens, int box, lbm_ctx *coarse)

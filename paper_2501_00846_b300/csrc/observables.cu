@@ -45,10 +45,12 @@ __global__ void __launch_bounds__(kThreads) obs_partial_kernel(Grid G, double rh
     r[F_PHIMAX] = -DBL_MAX;
     const size_t N = (size_t)G.N;
 
-    // 64-bit node index: with N close to 2^31 an int index would wrap past INT_MAX on its last stride.
+    // 64-bit node index: with N close to 2^31 an int index would wrap past INT_MAX on its last
+    // stride.  Inside the loop k < N < 2^31, so the coordinates come from 32-bit divisions.
     for (size_t k = (size_t)blockIdx.x * kThreads + threadIdx.x; k < N; k += (size_t)gridDim.x * kThreads) {
-        const int z = (int)(k / (size_t)G.nxy);
-        const int rem = (int)(k - (size_t)z * G.nxy);
+        const int kk = (int)k;
+        const int z = kk / G.nxy;
+        const int rem = kk - z * G.nxy;
         const int y = rem / G.nx;
         const int x = rem - y * G.nx;
         double ps = 0.0;

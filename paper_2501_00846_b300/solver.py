@@ -137,6 +137,8 @@ def load(path: str = LIB_PATH):
         "lbm_ens_box_nodes": ([vp, i], ll),
         "lbm_ens_step_count": ([vp], ll),
         "lbm_ens_restrict_state": ([vp, i, vp], i),
+        "lbm_ens_set_persistent": ([vp, i], i),
+        "lbm_ens_test_stall_barrier": ([vp, i], i),
         "lbm_cnn_create": ([i, i, i, ctypes.c_ulonglong, vp, ctypes.POINTER(vp)], i),
         "lbm_cnn_destroy": ([vp], None),
         "lbm_cnn_num_params": ([], i),
@@ -415,6 +417,14 @@ class Ensemble:
         t = LbmTuning()
         _check(load().lbm_ens_autotune(self._ens, int(reps), ctypes.byref(t)))
         return t.as_dict()
+
+    def set_persistent(self, on: bool):
+        """One persistent cooperative launch per step (True) or two graph-replayed launches (False)."""
+        _check(load().lbm_ens_set_persistent(self._ens, int(bool(on))))
+
+    def test_stall_barrier(self, on: bool):
+        """Test hook: make every grid-barrier wait of the persistent step expire (LBM_ERR_TIMEOUT)."""
+        _check(load().lbm_ens_test_stall_barrier(self._ens, int(bool(on))))
 
 
 def ensemble_from_workloads(workloads, stream=None, storage: int = LBM_FP32) -> Ensemble:

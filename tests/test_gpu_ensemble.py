@@ -207,3 +207,50 @@ def test_moment_storage_ensemble_rules():
             c.init_fields(np.zeros((12, 12, 12), np.float32), np.zeros((3, 12, 12, 12), np.float32))
             with pytest.raises(solver.LbmError):
                 e.restrict_state(0, c)
+
+
+@pytest.mark.parametrize("store", [solver.LBM_FP32, solver.LBM_MOM_BF16], ids=["fp32", "mom_bf16"])
+def test_persistent_step_equals_boxes_run_alone(mixed, store):
+    """One persistent cooperative launch per step (Allen–Cahn tasks, grid barrier, lattice
+    Boltzmann work) runs the same device functions as the two-launch form: every box matches its
+    run alone bit for bit, also with a non-default tuning."""
+    wls, ref = mixed
+    if store != solver.LBM_FP32:
+        ref = []
+        for wl in wls:
+            with solver.from_workload(wl, storage=store) as s:
+                s.step(21)
+                ref.append(s.read_fields())
+    for tuning in ({}, dict(lbm_block=64, ac_rows=2, ac_zlen=8)):
+        with solver.ensemble_from_workloads(wls, storage=store) as e:
+            if tuning:
+                e.set_tuning(**tuning)
+            e.set_persistent(True)
+            e.step(13)
+            e.step(8)
+            assert e.step_count == 21
+            got = [e.read_fields(b) for b in range(len(wls))]
+        _assert_same(got, ref, f"persistent {store} {tuning}")
+
+
+def test_persistent_barrier_expiry_is_reported_and_the_ensemble_recovers(mixed):
+    """The grid barrier's waits are bounded.  The test hook keeps CTA 0 from arriving and cuts the
+    limit to 2 ms: every wait expires, lbm_ens_step returns LBM_ERR_TIMEOUT, no step is counted and
+    the fields are those of the last completed step; with the hook off the ensemble steps on and
+    ends exactly where an undisturbed run ends."""
+    wls, ref = mixed
+    with solver.ensemble_from_workloads(wls) as e:
+        e.set_persistent(True)
+        e.step(10)
+        before = [e.read_fields(b) for b in range(len(wls))]
+        e.test_stall_barrier(True)
+        with pytest.raises(solver.LbmError) as err:
+            e.step(3)
+        assert err.value.status == -5
+        assert e.step_count == 10
+        _assert_same([e.read_fields(b) for b in range(len(wls))], before, "after the expired step")
+        e.test_stall_barrier(False)
+        e.step(11)
+        assert e.step_count == 21
+        got = [e.read_fields(b) for b in range(len(wls))]
+    _assert_same(got, ref, "after recovery")
