@@ -420,8 +420,9 @@ lbm_status lbm_closure_target(lbm_ctx *ctx, const float *ref, const lbm_closure_
 /* Correct a context's state in place with the network (periodic boxes, FP32 storage, grid equal to
  * the network's): phi += dphi - w c with w = max(4 phi (1 - phi), 0) and c chosen so that sum phi
  * is unchanged (the compensation sits in the interfaces, the bulk phases stay untouched), ubar +=
- * du, populations shifted by f^eq(p*, ubar + du) - f^eq(p*, ubar).  Asynchronous on the context's
- * stream. */
+ * du - sum(rho du) / sum(rho) with rho = rho(phi) before the correction (the correction adds no
+ * momentum), populations shifted by f^eq(p*, ubar + du') - f^eq(p*, ubar) for that du'.
+ * Asynchronous on the context's stream. */
 lbm_status lbm_closure_apply(lbm_ctx *ctx, lbm_cnn *cnn, const lbm_closure_norm *norm);
 
 /* 2x restriction of a fine state to the coarse grid (device arrays, channel-first): phi and p

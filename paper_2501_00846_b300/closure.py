@@ -47,10 +47,13 @@ def _coarse_context(col, stream):
 IDENTITY = solver.LbmClosureNorm.make([0.0] * 5, [1.0] * 5, [1.0] * 4)
 
 
-def generate(collisions, snapshots=20, stride=48, batch=25, norm=IDENTITY, stream=None, log=None, every=1):
+def generate(collisions, snapshots=20, stride=48, batch=25, norm=IDENTITY, stream=None, log=None, every=1,
+             burn=(0, 0), seed=0):
     """Training pairs (X [S, 5, Nc], T [S, 4, Nc], device tensors) from len(collisions) fine runs,
-    `snapshots` pairs each, one every `stride` fine steps; the coarse context takes `every` steps
-    between restriction and comparison (the fine runs 2 * every)."""
+    `snapshots` pairs each, one every `stride` fine steps; the coarse context takes b + `every`
+    steps between restriction and comparison (the fine runs 2 (b + every)), b drawn per snapshot
+    from the range `burn` (seeded): with b > 0 the pair is taken on a coarse state that has run
+    past the transient that follows a restriction and carries the coarse solver's own drift."""
     import torch
     stream = stream or torch.cuda.current_stream()
     L = collisions[0].L
@@ -60,6 +63,10 @@ def generate(collisions, snapshots=20, stride=48, batch=25, norm=IDENTITY, strea
     T = torch.empty((S, 4, Nc), device="cuda")
     ref = torch.empty(4 * Nc, device="cuda")
     idx = 0
+    rng = np.random.default_rng(seed)
+    burns = [int(rng.integers(burn[0], burn[1] + 1)) for _ in range(snapshots)]
+    if stride < 2 * (max(burns) + every):
+        raise ValueError("stride too short for the burn-in and the compared steps")
     with torch.cuda.stream(stream):
         for b0 in range(0, len(collisions), batch):
             cols = collisions[b0:b0 + batch]
@@ -70,13 +77,14 @@ def generate(collisions, snapshots=20, stride=48, batch=25, norm=IDENTITY, strea
                 ens.init_fields(k, _f32(phi), _f32(u), _f32(ps))
             coarse = [_coarse_context(c, stream) for c in cols]
             restricted = _coarse_context(cols[0], stream)
-            for _ in range(snapshots):
-                ens.step(stride - 2 * every)
+            for snap in range(snapshots):
+                m = burns[snap] + every
+                ens.step(stride - 2 * m)
                 for k in range(len(cols)):
                     ens.restrict_state(k, coarse[k])
-                ens.step(2 * every)
+                ens.step(2 * m)
                 for k in range(len(cols)):
-                    coarse[k].step(every)
+                    coarse[k].step(m)
                     ens.restrict_state(k, restricted)
                     restricted.read_fields(phi=ref[:Nc], u=ref[Nc:])
                     solver.closure_features(coarse[k], norm, X[idx].reshape(-1))
@@ -196,6 +204,117 @@ def evaluate(net, norm, col, coarse_steps=240, every=24, stream=None, apply_ever
         fine.close()
     out["nodes"] = {"fine": col.L ** 3, "coarse": n}
     return out
+
+
+def _block_mean(a, f):
+    """Mean over f x f x f blocks of the last three axes."""
+    *lead, nz, ny, nx = a.shape
+    return a.reshape(*lead, nz // f, f, ny // f, f, nx // f, f).mean(axis=(-5, -3, -1))
+
+
+def accuracy_ladder(net, norm, col, coarse_steps=240, check_every=24, resolutions=(64, 96), compare=32,
+                    stream=None, apply_every=1):
+    """Accuracy and cost of the plain solver on a ladder of grids against the fine run, beside the
+    corrected coarse run.  The fine collision col (col.L^3) is the reference; every other run is
+    the same physical collision rescaled to its grid (inputs.rescaled_collision: acoustic
+    scaling, the initial profiles of the same physical width, the solver's interface width W
+    lattice units everywhere), started from its own initial fields.  Each run is compared at the
+    same physical times, every check_every steps of the coarsest grid, after block-averaging phi
+    and u to compare^3 (every grid a multiple of it).  The corrected run is the coarsest grid
+    (col.L / 2) with the closure applied every apply_every steps.  Returns per grid the mean RMS
+    error of phi and u over the checks and the device milliseconds per unit physical time (one
+    step of the coarsest grid), plus the corrected run's."""
+    import torch
+    stream = stream or torch.cuda.current_stream()
+    Lc = col.L // 2
+    assert all(L % compare == 0 for L in resolutions + (col.L,)) and Lc in resolutions
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    out = {"compare": f"{compare}^3", "coarse_steps": coarse_steps, "runs": {}}
+    with torch.cuda.stream(stream):
+        def make(L):
+            c = col if L == col.L else inputs.rescaled_collision(col, L)
+            s = solver.Solver(stream=stream, **c.params())
+            phi, u, ps = c.fields()
+            s.init_fields(_f32(phi), _f32(u), _f32(ps))
+            return s
+
+        # steps of each grid per coarse step: L / Lc (acoustic scaling), integral for every grid
+        runs = {("fine", col.L): make(col.L)}
+        for L in resolutions:
+            runs[("plain", L)] = make(L)
+        runs[("closure", Lc)] = make(Lc)
+        per = {k: k[1] // Lc if k[1] % Lc == 0 else None for k in runs}
+        for k in runs:
+            if per[k] is None:
+                per[k] = k[1] / Lc
+        errs = {k: [] for k in runs if k[0] != "fine"}
+        done = {k: 0 for k in runs}
+        for c in range(1, coarse_steps // check_every + 1):
+            target = c * check_every
+            for k, s in runs.items():
+                n = int(round(target * per[k])) - done[k]
+                if k[0] == "closure":
+                    for _ in range(n):
+                        s.step(1)
+                        done[k] += 1
+                        if done[k] % apply_every == 0:
+                            solver.closure_apply(s, net, norm)
+                else:
+                    s.step(n)
+                    done[k] += n
+            ref = runs[("fine", col.L)].read_fields()
+            rphi = _block_mean(ref[0].astype(np.float64), col.L // compare)
+            ru = _block_mean(ref[1].astype(np.float64), col.L // compare)
+            for k in errs:
+                f = runs[k].read_fields()
+                phi = _block_mean(f[0].astype(np.float64), k[1] // compare)
+                u = _block_mean(f[1].astype(np.float64), k[1] // compare)
+                errs[k].append((float(np.sqrt(np.mean((phi - rphi) ** 2))), float(np.sqrt(np.mean((u - ru) ** 2)))))
+
+        def timed(k, nrep=20):
+            s = runs[k]
+            steps = per[k]
+            torch.cuda.synchronize()
+            ev[0].record(stream)
+            for _ in range(nrep):
+                if k[0] == "closure":
+                    s.step(1)
+                    if (done[k] + 1) % apply_every == 0:
+                        solver.closure_apply(s, net, norm)
+                    done[k] += 1
+                else:
+                    s.step(int(round(steps)) if float(steps).is_integer() else 1)
+            ev[1].record(stream)
+            torch.cuda.synchronize()
+            ms = ev[0].elapsed_time(ev[1]) / nrep
+            return ms if float(steps).is_integer() or k[0] == "closure" else ms * steps
+
+        for k in runs:
+            e = np.array(errs[k]) if k in errs else None
+            out["runs"][f"{k[0]}_{k[1]}"] = {
+                "grid": f"{k[1]}^3", "steps_per_coarse_step": per[k], "ms_per_coarse_step": timed(k),
+                **({"phi_rms_mean": float(e[:, 0].mean()), "u_rms_mean": float(e[:, 1].mean())} if e is not None else {})}
+        for s in runs.values():
+            s.close()
+    return out
+
+
+def equal_accuracy(ladder, coarse=64, finer=96):
+    """From an accuracy ladder: fit the plain solver's phi error to e(L) = C L^-p through the two
+    plain grids, solve e(L*) = the corrected run's error, and price the plain solver at L* with
+    the cost law t(L) = t(coarse) (L / coarse)^q fitted through the same two grids' measured
+    times.  Returns L*, the plain solver's time per unit physical time at L*, and the corrected
+    run's."""
+    r = ladder["runs"]
+    e1, e2 = r[f"plain_{coarse}"]["phi_rms_mean"], r[f"plain_{finer}"]["phi_rms_mean"]
+    t1, t2 = r[f"plain_{coarse}"]["ms_per_coarse_step"], r[f"plain_{finer}"]["ms_per_coarse_step"]
+    ec, tc = r[f"closure_{coarse}"]["phi_rms_mean"], r[f"closure_{coarse}"]["ms_per_coarse_step"]
+    p = math.log(e1 / e2) / math.log(finer / coarse)
+    q = math.log(t2 / t1) / math.log(finer / coarse)
+    Ls = coarse * (e1 / ec) ** (1.0 / p)
+    return {"error_exponent": p, "cost_exponent": q, "equal_accuracy_grid": Ls,
+            "plain_ms_at_equal_accuracy": t1 * (Ls / coarse) ** q, "closure_ms": tc,
+            "speedup": t1 * (Ls / coarse) ** q / tc}
 
 
 # useful multiply-adds per node of one forward pass: 27 offsets x (5x32 + 32x32 + 32x32 + 32x4)

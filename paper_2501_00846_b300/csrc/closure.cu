@@ -913,32 +913,35 @@ __device__ __forceinline__ float bounded_dphi(float raw, float ph)
     return fminf(fmaxf(raw, -fmaxf(ph, 0.0f)), fmaxf(1.0f - ph, 0.0f));
 }
 
-// Sums for the conservative phi correction: out[0] += sum of the bounded corrections, out[1] +=
-// sum of the interface weight w = max(4 phi (1 - phi), 0) (FP64)
+// Sums for the conservative corrections (FP64): out[0] += sum of the bounded phi corrections,
+// out[1] += sum of the interface weight w = max(4 phi (1 - phi), 0), out[2..4] += sum of rho du
+// (the momentum the velocity correction would add), out[5] += sum of rho
 __global__ void __launch_bounds__(256) corr_sums_kernel(const float *__restrict__ y, const float *__restrict__ phi,
-                                                        float s_phi, int N, double *__restrict__ out)
+                                                        lbm_closure_norm nrm, float rho_g, float drho, int N,
+                                                        double *__restrict__ out)
 {
-    __shared__ double r0[256], r1[256];
-    double s0 = 0.0, s1 = 0.0;
+    __shared__ double red[6][256];
+    double s[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    const size_t NN = (size_t)N;
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < N; k += gridDim.x * blockDim.x) {
         const float p = phi[k];
-        s0 += bounded_dphi(s_phi * y[k], p);
-        s1 += fmaxf(4.0f * p * (1.0f - p), 0.0f);
+        const double rho = (double)fmaf(p, drho, rho_g);
+        s[0] += bounded_dphi(nrm.out_scale[0] * y[k], p);
+        s[1] += fmaxf(4.0f * p * (1.0f - p), 0.0f);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) s[2 + a] += rho * (double)(nrm.out_scale[a + 1] * y[(a + 1) * NN + k]);
+        s[5] += rho;
     }
-    r0[threadIdx.x] = s0;
-    r1[threadIdx.x] = s1;
+#pragma unroll
+    for (int q = 0; q < 6; ++q) red[q][threadIdx.x] = s[q];
     __syncthreads();
     for (int w = 128; w > 0; w >>= 1) {
-        if (threadIdx.x < w) {
-            r0[threadIdx.x] += r0[threadIdx.x + w];
-            r1[threadIdx.x] += r1[threadIdx.x + w];
-        }
+        if (threadIdx.x < w)
+#pragma unroll
+            for (int q = 0; q < 6; ++q) red[q][threadIdx.x] += red[q][threadIdx.x + w];
         __syncthreads();
     }
-    if (threadIdx.x == 0) {
-        atomicAdd(out, r0[0]);
-        atomicAdd(out + 1, r1[0]);
-    }
+    if (threadIdx.x < 6) atomicAdd(out + threadIdx.x, red[threadIdx.x][0]);
 }
 
 // Apply the network's correction y [4][N] to a one-box FP32 state.  phi: dphi = d - w c with d
@@ -946,7 +949,8 @@ __global__ void __launch_bounds__(256) corr_sums_kernel(const float *__restrict_
 // c = sum(d) / sum(w), so the sum of phi is unchanged and the compensation sits in the interfaces
 // (a uniform shift, or an unbounded correction, pushes the bulk phases out of [0, 1], and with a
 // density ratio of 100 rho(phi) turns negative at phi = -0.0101); with no interface (sum w = 0)
-// the plain mean is removed.  ubar: du = s_a y_a.  Populations:
+// the plain mean is removed.  ubar: du = s_a y_a - sum(rho s_a y_a) / sum(rho), so the correction
+// adds no momentum to the box (as the step itself, on a periodic box).  Populations:
 // g_i += f^eq_i(p*, ubar + du) - f^eq_i(p*, ubar) (Eq. eqts; p* = sum g unchanged), so they carry
 // the new velocity.
 __global__ void correct_kernel(Grid G, const float *__restrict__ y, lbm_closure_norm nrm,
@@ -961,7 +965,9 @@ __global__ void correct_kernel(Grid G, const float *__restrict__ y, lbm_closure_
     const float w = fmaxf(4.0f * ph * (1.0f - ph), 0.0f);
     const float comp = sums[1] > 0.0 ? (float)(total / sums[1]) * w : (float)(total / (double)G.N);
     const float dphi = bounded_dphi(nrm.out_scale[0] * y[k], ph) - comp;
-    const float du[3] = {nrm.out_scale[1] * y[N + k], nrm.out_scale[2] * y[2 * N + k], nrm.out_scale[3] * y[3 * N + k]};
+    const float du[3] = {nrm.out_scale[1] * y[N + k] - (float)(sums[2] / sums[5]),
+                         nrm.out_scale[2] * y[2 * N + k] - (float)(sums[3] / sums[5]),
+                         nrm.out_scale[3] * y[3 * N + k] - (float)(sums[4] / sums[5])};
     float ps = 0.0f;
     float gi[27];
 #pragma unroll
@@ -1353,7 +1359,7 @@ lbm_status lbm_cnn_create(int nx, int ny, int nz, unsigned long long seed, void 
         {(void **)&c->da, N * 32 * sizeof(float)},
         {(void **)&c->dzb, N * 32 * 2},                {(void **)&c->xbuf, 5 * N * sizeof(float)},
         {(void **)&c->ybuf, 4 * N * sizeof(float)},
-        {(void **)&c->dsum, (size_t)(c->loss_blocks + 1) * sizeof(double)},
+        {(void **)&c->dsum, (size_t)(c->loss_blocks + 8) * sizeof(double)},
         {(void **)&c->bpad, (size_t)tslb::NLAYER * 32 * sizeof(float)},
     };
     cudaError_t err = cudaSuccess;
@@ -1600,8 +1606,8 @@ lbm_status lbm_closure_apply(lbm_ctx *ctx, lbm_cnn *cnn, const lbm_closure_norm 
     CNN_TRY(cudaGetLastError());
     CNN_TRY(forward(cnn, cnn->xbuf));
     tslb::unpack_output_kernel<<<(N + 255) / 256, 256, 0, v.stream>>>(cnn->z[3], N, cnn->ybuf);
-    CNN_TRY(cudaMemsetAsync(cnn->dsum, 0, 2 * sizeof(double), v.stream));
-    tslb::corr_sums_kernel<<<296, 256, 0, v.stream>>>(cnn->ybuf, v.phi, norm->out_scale[0], N, cnn->dsum);
+    CNN_TRY(cudaMemsetAsync(cnn->dsum, 0, 6 * sizeof(double), v.stream));
+    tslb::corr_sums_kernel<<<296, 256, 0, v.stream>>>(cnn->ybuf, v.phi, *norm, v.P.rho_g, v.P.drho, N, cnn->dsum);
     tslb::correct_kernel<<<(N + 255) / 256, 256, 0, v.stream>>>(v.G, cnn->ybuf, *norm, cnn->dsum, v.g, v.phi, v.u);
     CNN_TRY(cudaGetLastError());
     tslb::ctx_state_changed(ctx);

@@ -274,6 +274,7 @@ class Collision:
     noise: float = 0.0
     seed: int = 0
     name: str = "collision"
+    profile_width: float = None   # width of the initial tanh profiles (default: width)
 
     @property
     def nx(self):
@@ -293,8 +294,9 @@ class Collision:
 
     def _drops(self):
         c1, c2 = self._centres()
-        return (sphere_phi(self.L, self.L, self.L, c1, self.R, self.width),
-                sphere_phi(self.L, self.L, self.L, c2, self.R, self.width))
+        w = self.width if self.profile_width is None else self.profile_width
+        return (sphere_phi(self.L, self.L, self.L, c1, self.R, w),
+                sphere_phi(self.L, self.L, self.L, c2, self.R, w))
 
     def fields(self):
         """(phi0, u0, p*0) in one pass: phi = the two drop profiles (capped at 1), u = +-speed/2
@@ -332,6 +334,19 @@ class Collision:
         p.update(nx=self.L // 2, ny=self.L // 2, nz=self.L // 2, mu_l=p["mu_l"] / 2, mu_g=p["mu_g"] / 2,
                  sigma=p["sigma"] / 2, mobility=p["mobility"] / 2)
         return p
+
+
+def rescaled_collision(col: Collision, L: int) -> Collision:
+    """The same physical collision on an L^3 grid in acoustic scaling (lattice velocities kept,
+    dx and dt scaled by f = col.L / L): lengths (R, gap, offset, the initial profile's width)
+    scale by 1/f, nu, sigma and D by 1/f in lattice units; the solver's interface width stays
+    col.width lattice units, as on every grid.  The seeded Fourier noise has the same physical
+    modes at every L."""
+    f = col.L / L
+    pw = col.width if col.profile_width is None else col.profile_width
+    return dataclasses.replace(col, L=L, R=col.R / f, gap=col.gap / f, offset=col.offset / f, nu=col.nu / f,
+                               sigma=col.sigma / f, mobility=col.mobility / f, profile_width=pw / f,
+                               name=f"{col.name}_at_{L}")
 
 
 def collision_set(n=200, seed=7, L=128, R=20.0):

@@ -163,8 +163,10 @@ def _closure_box():
     return wl
 
 
-def test_zero_network_leaves_the_state_unchanged_and_a_constant_shifts_momentum():
-    import torch
+def test_zero_network_leaves_the_state_unchanged_and_a_constant_shifts_phi_only():
+    """A zero network leaves the state bit for bit.  A constant network shifts phi in the bulk and
+    compensates inside the interfaces (sum phi kept); its uniform velocity output is all momentum,
+    which the correction removes, so ubar and the populations' first moment stay as they were."""
     wl = _closure_box()
     norm = solver.LbmClosureNorm.make([0.5, 0, 0, 0, 0], [0.5, 0.01, 0.01, 0.01, 1e-3], [1e-3, 1e-3, 2e-3, 3e-3])
     with solver.from_workload(wl) as s, solver.Network(wl.nx, wl.ny, wl.nz, stream=s.stream) as net:
@@ -174,8 +176,6 @@ def test_zero_network_leaves_the_state_unchanged_and_a_constant_shifts_momentum(
         solver.closure_apply(s, net, norm)
         g1, phi1, u1 = s.get_state()
         assert np.array_equal(g0, g1) and np.array_equal(phi0, phi1) and np.array_equal(u0, u1)
-        # W4 = 0, b4 = (1, 1, -1, 2): y is constant; ubar shifts by out_scale * (1, -1, 2)
-        # everywhere, phi by out_scale[0] in the bulk phases, compensated inside the interfaces
         flat = np.zeros(net.num_params, np.float32)
         flat[-4:] = [1.0, 1.0, -1.0, 2.0]
         net.set_params(flat)
@@ -187,17 +187,47 @@ def test_zero_network_leaves_the_state_unchanged_and_a_constant_shifts_momentum(
     assert abs(phi2.astype(np.float64).sum() - phi1.astype(np.float64).sum()) < 1e-6 * phi1.size
     assert (phi2 >= np.minimum(phi1, 0) - 1e-6).all() and (phi2 <= np.maximum(phi1, 1) + 1e-6).all()
     assert np.abs(phi2 - phi1).max() > 1e-4
-    du = np.array([1e-3 * 1.0, 2e-3 * -1.0, 3e-3 * 2.0])
-    for a in range(3):
-        assert np.allclose(u2[a] - u1[a], du[a], atol=1e-7)
-    # populations: p* unchanged, first moment shifted by du (sum_i f^eq_i c_i = u)
+    assert np.abs(u2 - u1).max() < 1e-9
     c = np.array([[k % 3 - 1, (k // 3) % 3 - 1, k // 9 - 1] for k in range(27)], np.float64)
-    ps1, ps2 = g1.astype(np.float64).sum(0), g2.astype(np.float64).sum(0)
-    assert np.abs(ps2 - ps1).max() < 1e-6
+    assert np.abs(g2.astype(np.float64).sum(0) - g1.astype(np.float64).sum(0)).max() < 1e-6
     for a in range(3):
         j1 = np.tensordot(c[:, a], g1.astype(np.float64), axes=1)
         j2 = np.tensordot(c[:, a], g2.astype(np.float64), axes=1)
-        assert np.allclose(j2 - j1, du[a], atol=2e-7)
+        assert np.abs(j2 - j1).max() < 2e-7
+
+
+def test_velocity_correction_follows_its_definition_and_adds_no_momentum():
+    """With a random network: ubar changes by du = out_scale y minus its rho-weighted mean (y the
+    network's output on the state's features, rho from phi before the correction), so the box
+    gains no momentum, and the populations' first moment moves by exactly du."""
+    import torch
+    wl = _closure_box()
+    norm = solver.LbmClosureNorm.make([0.5, 0, 0, 0, 0], [0.5, 0.01, 0.01, 0.01, 1e-3], [0.0, 1e-3, 2e-3, 3e-3])
+    flat, _, _ = _random_case(wl.nx, wl.ny, wl.nz, seed=12)
+    with solver.from_workload(wl) as s, solver.Network(wl.nx, wl.ny, wl.nz, stream=s.stream) as net:
+        net.set_params(flat)
+        s.step(3)
+        g1, phi1, u1 = s.get_state()
+        x = torch.empty(5 * s.n, device="cuda")
+        y = torch.empty(4 * s.n, device="cuda")
+        solver.closure_features(s, norm, x)
+        net.forward(x, y)
+        solver.closure_apply(s, net, norm)
+        g2, phi2, u2 = s.get_state()
+        torch.cuda.synchronize()
+        y = y.cpu().numpy().astype(np.float64).reshape((4,) + phi1.shape)
+    assert np.array_equal(phi1, phi2)                       # out_scale[0] = 0: no phi correction
+    rho = wl.rho_g + phi1.astype(np.float64) * (wl.rho_l - wl.rho_g)
+    c = np.array([[k % 3 - 1, (k // 3) % 3 - 1, k // 9 - 1] for k in range(27)], np.float64)
+    for a in range(3):
+        raw = norm.out_scale[a + 1] * y[a + 1]
+        du = raw - (rho * raw).sum() / rho.sum()
+        assert np.abs(raw).max() > 1e-4
+        np.testing.assert_allclose(u2[a] - u1[a], du, atol=2e-8)
+        assert abs((rho * (u2[a].astype(np.float64) - u1[a])).sum()) < 1e-6 * (rho * np.abs(du)).sum()
+        j1 = np.tensordot(c[:, a], g1.astype(np.float64), axes=1)
+        j2 = np.tensordot(c[:, a], g2.astype(np.float64), axes=1)
+        np.testing.assert_allclose(j2 - j1, du, atol=2e-7)
 
 
 def test_features_and_targets_follow_their_definitions():
