@@ -402,7 +402,8 @@ lbm_status lbm_cnn_grad(lbm_cnn *cnn, const float *x, const float *t, int accumu
 /* Inspection of one layer l = 0..3 (host arrays, channel-first, any pointer may be NULL):
  *   a_in  the layer's input as the tensor cores read it, BF16 widened exactly to FP32 [CIN_l][N]
  *         (layer 0: the rounded network input x; layers 1..3: silu(z_{l-1}) rounded to BF16)
- *   z     the layer's FP32 pre-activation from the last lbm_cnn_forward or lbm_cnn_grad [COUT_l][N]
+ *   z     the layer's FP32 pre-activation from the last lbm_cnn_grad [COUT_l][N] (layer 3: also
+ *         from lbm_cnn_forward; a forward pass without gradients keeps only the output layer's)
  *   dz    d loss / d z_l in FP32 from the last lbm_cnn_grad [COUT_l][N]
  * with CIN = 5, 32, 32, 32 and COUT = 32, 32, 32, 4.  For testing the convolutions one at a time
  * against their definition; synchronises the stream.  LBM_ERR_ARG for a bad layer. */

@@ -48,25 +48,34 @@ IDENTITY = solver.LbmClosureNorm.make([0.0] * 5, [1.0] * 5, [1.0] * 4)
 
 
 def generate(collisions, snapshots=20, stride=48, batch=25, norm=IDENTITY, stream=None, log=None, every=1,
-             burn=(0, 0), seed=0):
+             burn=(0, 0), seed=0, policy=None, rollout=1):
     """Training pairs (X [S, 5, Nc], T [S, 4, Nc], device tensors) from len(collisions) fine runs,
-    `snapshots` pairs each, one every `stride` fine steps; the coarse context takes b + `every`
-    steps between restriction and comparison (the fine runs 2 (b + every)), b drawn per snapshot
-    from the range `burn` (seeded): with b > 0 the pair is taken on a coarse state that has run
-    past the transient that follows a restriction and carries the coarse solver's own drift."""
+    one snapshot every `stride` fine steps.
+
+    At a snapshot the fine state is restricted into a coarse context, which then runs `rollout`
+    legs; a leg is b + `every` coarse steps (b drawn per snapshot from the range `burn`, seeded)
+    while the fine run takes twice as many, and gives the pair
+        x = features(coarse state after the leg),
+        t = (restricted fine (phi, u) - coarse (phi, ubar)) / out_scale.
+    With a `policy` (network, norm), the coarse state is corrected by that network after every
+    leg but the last, so the later legs start from states the corrected solver itself reaches
+    (on-policy data for iterated training); without one, rollout must be 1.  Returns
+    len(collisions) * snapshots * rollout pairs."""
     import torch
+    if policy is None and rollout != 1:
+        raise ValueError("rollouts longer than one leg need a policy network")
     stream = stream or torch.cuda.current_stream()
     L = collisions[0].L
     Nc = (L // 2) ** 3
-    S = len(collisions) * snapshots
+    S = len(collisions) * snapshots * rollout
     X = torch.empty((S, 5, Nc), device="cuda")
     T = torch.empty((S, 4, Nc), device="cuda")
     ref = torch.empty(4 * Nc, device="cuda")
     idx = 0
     rng = np.random.default_rng(seed)
     burns = [int(rng.integers(burn[0], burn[1] + 1)) for _ in range(snapshots)]
-    if stride < 2 * (max(burns) + every):
-        raise ValueError("stride too short for the burn-in and the compared steps")
+    if stride < 2 * rollout * (max(burns) + every):
+        raise ValueError("stride too short for the rollout")
     with torch.cuda.stream(stream):
         for b0 in range(0, len(collisions), batch):
             cols = collisions[b0:b0 + batch]
@@ -79,17 +88,20 @@ def generate(collisions, snapshots=20, stride=48, batch=25, norm=IDENTITY, strea
             restricted = _coarse_context(cols[0], stream)
             for snap in range(snapshots):
                 m = burns[snap] + every
-                ens.step(stride - 2 * m)
+                ens.step(stride - 2 * m * rollout)
                 for k in range(len(cols)):
                     ens.restrict_state(k, coarse[k])
-                ens.step(2 * m)
-                for k in range(len(cols)):
-                    coarse[k].step(m)
-                    ens.restrict_state(k, restricted)
-                    restricted.read_fields(phi=ref[:Nc], u=ref[Nc:])
-                    solver.closure_features(coarse[k], norm, X[idx].reshape(-1))
-                    solver.closure_target(coarse[k], ref, norm, T[idx].reshape(-1))
-                    idx += 1
+                for leg in range(rollout):
+                    ens.step(2 * m)
+                    for k in range(len(cols)):
+                        coarse[k].step(m)
+                        ens.restrict_state(k, restricted)
+                        restricted.read_fields(phi=ref[:Nc], u=ref[Nc:])
+                        solver.closure_features(coarse[k], norm, X[idx].reshape(-1))
+                        solver.closure_target(coarse[k], ref, norm, T[idx].reshape(-1))
+                        idx += 1
+                        if policy is not None and leg < rollout - 1:
+                            solver.closure_apply(coarse[k], policy[0], policy[1])
             torch.cuda.synchronize()
             for c in coarse:
                 c.close()
@@ -116,8 +128,15 @@ def estimate_norm(collisions, snapshots=6, stride=48, stream=None, every=1):
 
 def train(net, X, T, epochs=4, lr=1e-3, batch=4, seed=0, log=None):
     """Adam over the pairs in random order, `batch` samples per step; cosine learning-rate decay.
+    X, T: tensors [S, ...] or lists of them (several data sets used together without copying).
     Returns the mean loss of every epoch."""
-    S = X.shape[0]
+    if isinstance(X, (list, tuple)):
+        where = [(j, i) for j, x in enumerate(X) for i in range(x.shape[0])]
+        Xl, Tl = X, T
+    else:
+        where = [(0, i) for i in range(X.shape[0])]
+        Xl, Tl = [X], [T]
+    S = len(where)
     rng = np.random.default_rng(seed)
     steps = epochs * math.ceil(S / batch)
     k = 0
@@ -129,7 +148,8 @@ def train(net, X, T, epochs=4, lr=1e-3, batch=4, seed=0, log=None):
         for i in range(0, S, batch):
             ids = order[i:i + batch]
             for j, s in enumerate(ids):
-                tot += net.grad(X[int(s)].reshape(-1), T[int(s)].reshape(-1), accumulate=j > 0)
+                d, i_ = where[int(s)]
+                tot += net.grad(Xl[d][i_].reshape(-1), Tl[d][i_].reshape(-1), accumulate=j > 0)
             rate = lr * 0.5 * (1.0 + math.cos(math.pi * k / steps))
             net.adam_step(rate, 1.0 / len(ids))
             k += 1
@@ -375,6 +395,13 @@ def main(argv=None):
                     help="factor on the applied velocity correction (0: the phi correction alone)")
     ap.add_argument("--time-network", type=int, default=0, metavar="L",
                     help="only time the network's forward pass and training step on an L^3 grid")
+    ap.add_argument("--ladder", action="store_true",
+                    help="also run the accuracy ladder (plain L/2 and 3L/4 grids, corrected L/2) on the "
+                         "first held-out collision and report the plain grid of equal phi accuracy")
+    ap.add_argument("--policy-rounds", type=int, default=0,
+                    help="rounds of on-policy data: roll the coarse run out with the current network, add "
+                         "the pairs, retrain")
+    ap.add_argument("--rollout", type=int, default=6, help="legs of each on-policy rollout")
     ap.add_argument("--reps", type=int, default=50)
     a = ap.parse_args(argv)
     import torch
@@ -408,15 +435,31 @@ def main(argv=None):
     net = solver.Network(a.L // 2, a.L // 2, a.L // 2, seed=a.seed)
     t1 = time.perf_counter()
     hist = train(net, X, T, epochs=a.epochs, lr=a.lr, log=log)
-    t_train = time.perf_counter() - t1
-    del X, T
     applied = solver.LbmClosureNorm.make(norm.in_shift, norm.in_scale,
                                          [norm.out_scale[0]] + [a.u_relax * v for v in list(norm.out_scale)[1:]])
+    Xs, Ts = [X], [T]
+    for r in range(a.policy_rounds):   # on-policy data from the current network's own rollouts
+        # as many pairs per round as the first data set: snapshots / rollout rollouts per collision
+        Xp, Tp = generate(train_cols, snapshots=max(1, a.snapshots // a.rollout), stride=a.stride,
+                          batch=a.batch_traj, norm=norm,
+                          log=log, every=a.every, policy=(net, applied), rollout=a.rollout, seed=r + 1)
+        Xs.append(Xp)
+        Ts.append(Tp)
+        hist += train(net, Xs, Ts, epochs=a.epochs, lr=a.lr, seed=r + 1, log=log)
+    t_train = time.perf_counter() - t1
+    npairs = sum(x.shape[0] for x in Xs)
+    del X, T, Xs, Ts
     evals = [evaluate(net, applied, c, coarse_steps=a.eval_steps, apply_every=a.every) for c in eval_cols]
-    res = {"trajectories": a.traj, "pairs": a.traj * a.snapshots, "epochs": a.epochs, "every": a.every, "loss": hist,
+    res = {"trajectories": a.traj, "pairs": npairs, "epochs": a.epochs, "every": a.every,
+           "policy_rounds": a.policy_rounds, "u_relax": a.u_relax, "loss": hist,
            "seconds": {"data": t_data, "train": t_train}, "eval": evals,
            "norm": {"in_shift": list(norm.in_shift), "in_scale": list(norm.in_scale),
                     "out_scale": list(norm.out_scale)}}
+    if a.ladder:
+        lad = accuracy_ladder(net, applied, eval_cols[0], coarse_steps=a.eval_steps,
+                              resolutions=(a.L // 2, 3 * a.L // 4), compare=a.L // 4, apply_every=a.every)
+        res["ladder"] = lad
+        res["equal_accuracy"] = equal_accuracy(lad, coarse=a.L // 2, finer=3 * a.L // 4)
     print(json.dumps(res))
     if a.out:
         with open(a.out, "w") as fh:

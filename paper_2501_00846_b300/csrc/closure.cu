@@ -11,6 +11,7 @@
 // load per lane and m tile), activations are channel-last BF16 so that a B fragment is two 4-byte
 // loads per node.  The weight gradient, a reduction over all nodes, runs on the CUDA cores in FP32
 // with shared-memory tiles; master weights, gradients and Adam moments are FP32.
+#include <limits.h>
 #include <math.h>
 #include <stdarg.h>
 #include <stdio.h>
@@ -285,21 +286,28 @@ __global__ void __launch_bounds__(256) conv_tile_kernel(int nx, int ny, int nz, 
 //      HX * 16 bytes apart, the two channel groups of a K step LBO = HY * HX * 16 bytes apart, and a
 //      neighbour offset (dx, dy) only moves the start address;
 //   B: the weights, [k][channel chunk][group of 8 channels][o][8] (LBO = N * 16, SBO = 128).
-// A block of 8 warps owns a 16 x 16 column tile (two patches) and marches a z chunk: one thread
-// issues the 2 x 27 x CB MMAs of plane zc (fully unrolled; the descriptors are precomputed words
-// plus compile-time offsets) into one of two TMEM accumulator buffers and commits them to an
-// mbarrier; meanwhile all warps read back plane zc - 1's accumulators (tcgen05.ld; warp w owns
-// TMEM lanes 32 (w % 4) .. + 31 = patch rows 4 (w % 4) .. + 3 and half w / 4 of the output
-// channels), add the bias, store z and, for the forward pass, the next layer's input silu(z) in
-// BF16.  The input ring (6
-// planes, cp.async) is refilled four planes ahead as soon as the MMAs that read a slot are done,
-// so a plane's copy has three planes of MMAs to arrive.  Every mbarrier wait is bounded: on
-// expiry the kernel records an error, stops issuing work and still releases its TMEM.
+// A block owns a 16 x 16 column tile (two patches) and marches a z chunk, with warps in two roles
+// that hand work to each other through mbarriers:
+//   warp 8 (the MMA warp): one thread issues the 2 x 27 x CB MMAs of plane zc (fully unrolled; the
+//     descriptors are precomputed words plus compile-time offsets) into one of two TMEM
+//     accumulator buffers as soon as planes zc-1..zc+1 are staged and the buffer has been read
+//     back, then commits them to the buffer's "full" barrier and to the "empty" barrier of the
+//     slot of plane zc-1, which no later MMA reads;
+//   warps 0..7 (load and epilogue): read back plane zc's accumulators when its barrier completes
+//     (tcgen05.ld; warp w owns TMEM lanes 32 (w % 4) .. + 31 = patch rows 4 (w % 4) .. + 3 and
+//     half w / 4 of the output channels), report the buffer drained, add the bias and store z
+//     (when kept) and, for the forward pass, the next layer's input silu(z) in BF16; then stage
+//     plane zc + 5 into the ring slot plane zc - 1 frees (cp.async; the copies of one plane are
+//     waited for, fenced for the async proxy and reported "full" one iteration later).
+// The MMAs of a plane thus run while the epilogue of the previous plane drains and the staging of
+// later planes is in flight, and no barrier of the whole block sits on the per-plane path.  The
+// weights are staged with cp.async as well.  Every mbarrier wait is bounded in time: on expiry
+// the kernel records an error, every role stops at its next wait, the MMA thread waits once more
+// for the MMAs it committed, the copies in flight are waited for and the TMEM is released.
 
 constexpr int UM_TX = 16, UM_TY = 16;              // column tile: two 8 x 16 patches
 constexpr int UM_HX = UM_TX + 2, UM_HY = UM_TY + 2;
-constexpr int UM_SLOTS = 6;                        // planes zc-1..zc+1 read, zc+2..zc+4 in flight
-constexpr int UM_AHEAD = 4;                        // a plane is loaded this many planes ahead
+constexpr int UM_SLOTS = 6;                        // ring of staged planes: zc-1..zc+1 read, later ones in flight
 // Bounds of the mbarrier waits, in nanoseconds of %globaltimer: a plane's MMAs take about a
 // microsecond, so a wait still open after 20 ms has failed; the test hook's wait gives up after
 // 20 us.  Time bounds, unlike poll counts, do not depend on how long each poll suspends.
@@ -338,8 +346,9 @@ __device__ __forceinline__ unsigned long long globaltimer_ns()
 }
 
 // Waits until the phase of parity `parity` of the mbarrier has completed; false once limit_ns
-// nanoseconds have passed without that.
-__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity, unsigned long long limit_ns = UM_WAIT_NS)
+// nanoseconds have passed without that, or (abort not null) once *abort is set.
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity, unsigned long long limit_ns = UM_WAIT_NS,
+                                          const volatile int *abort = nullptr)
 {
     const unsigned long long t0 = globaltimer_ns();
     for (;;) {
@@ -350,8 +359,24 @@ __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity, unsign
             : "r"(mbar), "r"(parity)
             : "memory");
         if (done) return true;
-        if (globaltimer_ns() - t0 > limit_ns) return false;
+        if ((abort && *abort) || globaltimer_ns() - t0 > limit_ns) return false;
     }
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_addr(bar)), "r"(count));
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_addr(bar)) : "memory");
+}
+
+__device__ __forceinline__ void umma_commit(uint64_t *bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(smem_addr(bar))
+                 : "memory");
 }
 
 template <int CB>
@@ -370,21 +395,29 @@ __device__ __forceinline__ void um_load_plane(uint8_t *slot, const __nv_bfloat16
 
 // z[n][o] = bias[o] + sum_{k, i} W[o][i][k] in[n + off_k][i], CO = MT * 16 output channels (padded),
 // CB * 16 input channels (padded); wpack: [27][CB][2][CO][8] BF16 (pack_weights_umma_kernel).
-constexpr int UM_THREADS = 256;   // 8 warps: warp w reads TMEM lanes 32 (w % 4).., columns half w / 4
+// z is written when keep_z != 0 or act is null; act (not null): the next layer's input silu(z).
+constexpr int UM_EPI_WARPS = 8;                          // load and epilogue warps
+constexpr int UM_THREADS = 32 * (UM_EPI_WARPS + 1);      // plus the MMA warp
+constexpr int UM_EPI_THREADS = 32 * UM_EPI_WARPS;
 
 template <int MT, int CB>
 __global__ void __launch_bounds__(UM_THREADS, 1) conv_umma_kernel(int nx, int ny, int nz, const __nv_bfloat16 *__restrict__ wpack,
                                                            const __nv_bfloat16 *__restrict__ in,
                                                            const float *__restrict__ bias, float *__restrict__ z,
                                                            __nv_bfloat16 *__restrict__ act, int zlen,
-                                                           int *__restrict__ err, int stall)
+                                                           int *__restrict__ err, int stall, int keep_z)
 {
     constexpr int CO = MT * 16;
     constexpr int WBYTES = 27 * CB * 2 * CO * 16;
     constexpr int PB = UmGeom<CB>::PLANE_BYTES;
+    constexpr int CG = UmGeom<CB>::CG;
     constexpr uint32_t TCOLS = 2 * 2 * CO < 32 ? 32 : (2 * 2 * CO <= 64 ? 64 : 128);   // 2 buffers x 2 patches
     extern __shared__ __align__(1024) uint8_t usm[];
-    __shared__ __align__(8) uint64_t mbar[2];
+    __shared__ __align__(8) uint64_t bar_full[UM_SLOTS];     // a plane is staged in the slot
+    __shared__ __align__(8) uint64_t bar_empty[UM_SLOTS];    // the MMAs reading the slot are done
+    __shared__ __align__(8) uint64_t bar_acc[2];             // the accumulator buffer holds a finished plane
+    __shared__ __align__(8) uint64_t bar_drained[2];         // the accumulator buffer has been read back
+    __shared__ __align__(8) uint64_t bar_fin;                // every MMA this block committed is done
     __shared__ uint32_t tmem_base;
     __shared__ int abort_flag;
     __shared__ float sbias[CO];
@@ -395,23 +428,41 @@ __global__ void __launch_bounds__(UM_THREADS, 1) conv_umma_kernel(int nx, int ny
     const int x0 = (blockIdx.x % ntx) * UM_TX, y0 = (blockIdx.x / ntx) * UM_TY;
     const int z0 = blockIdx.y * zlen, z1 = min(nz, z0 + zlen);
     if (z0 >= nz) return;   // whole block
+    volatile int *abort_v = &abort_flag;
 
-    {   // weights (plain 16-byte copies) and the (padded) bias
-        const uint4 *src = reinterpret_cast<const uint4 *>(wpack);
-        uint4 *dst = reinterpret_cast<uint4 *>(sw);
-        for (int i = tid; i < WBYTES / 16; i += blockDim.x) dst[i] = src[i];
-        if (tid < CO) sbias[tid] = bias ? bias[tid] : 0.0f;
-    }
-    auto slot = [&](int p) { return ring + (size_t)((p - (z0 - 1)) % UM_SLOTS) * PB; };
-    // planes z0-1 .. z0+3, one cp.async group each (empty groups past the chunk keep the count)
-    for (int j = 0; j <= UM_AHEAD; ++j) {
-        if (z0 - 1 + j <= z1) um_load_plane<CB>(slot(z0 - 1 + j), in, nx, ny, nz, x0, y0, z0 - 1 + j);
+    // planes z0 - 1 .. z1 take slots in turn: slot and fill number of plane p
+    auto slot_of = [&](int p) { return (p - (z0 - 1)) % UM_SLOTS; };
+    auto fill_of = [&](int p) { return (p - (z0 - 1)) / UM_SLOTS; };
+    auto slot = [&](int p) { return ring + (size_t)slot_of(p) * PB; };
+    auto stage = [&](int p) {   // cp.async copies of plane p by the epilogue threads (one group)
+        const size_t plane = (size_t)mwrap(p, nz) * nx * ny;
+        uint8_t *dst = slot(p);
+        for (int e = tid; e < CG * UM_HY * UM_HX; e += UM_EPI_THREADS) {
+            const int node = e % (UM_HY * UM_HX), cg = e / (UM_HY * UM_HX);
+            const int hy = node / UM_HX, hx = node - hy * UM_HX;
+            const size_t src = plane + (size_t)mwrap(y0 - 1 + hy, ny) * nx + mwrap(x0 - 1 + hx, nx);
+            cp_async16(dst + (size_t)e * 16, in + src * (CB * 16) + cg * 8);
+        }
         cp_async_commit();
-    }
+    };
+    // the staged copies are complete: make them visible to the tensor core (async proxy), report
+    auto report_full = [&](int p) {
+        cp_async_wait_all();
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+        mbar_arrive(&bar_full[slot_of(p)]);
+    };
+
     if (tid == 0) {
         abort_flag = 0;
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_addr(&mbar[0])));
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_addr(&mbar[1])));
+        for (int q = 0; q < UM_SLOTS; ++q) {
+            mbar_init(&bar_full[q], UM_EPI_THREADS);
+            mbar_init(&bar_empty[q], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&bar_acc[b], 1);
+            mbar_init(&bar_drained[b], UM_EPI_WARPS);
+        }
+        mbar_init(&bar_fin, 1);
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     }
     if (warp == 0) {
@@ -419,149 +470,169 @@ __global__ void __launch_bounds__(UM_THREADS, 1) conv_umma_kernel(int nx, int ny
                      "r"(TCOLS));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
     }
-    cp_async_wait_group<UM_AHEAD - 2>();   // planes z0-1, z0, z0+1
-    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+    __syncthreads();   // barriers initialised before any arrival
+
+    // prologue (epilogue threads): weights, bias and the first UM_SLOTS planes
+    const int npro = min(UM_SLOTS, z1 - (z0 - 1) + 1);
+    if (tid < UM_EPI_THREADS) {
+        for (int i = tid; i < WBYTES / 16; i += UM_EPI_THREADS) cp_async16(sw + (size_t)i * 16, wpack + (size_t)i * 8);
+        if (tid < CO) sbias[tid] = bias ? bias[tid] : 0.0f;
+        for (int j = 0; j < npro; ++j) stage(z0 - 1 + j);
+        cp_async_wait_all();
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+        for (int j = 0; j < npro; ++j) mbar_arrive(&bar_full[slot_of(z0 - 1 + j)]);
+    }
     asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
-    __syncthreads();
+    __syncthreads();   // weights, bias and TMEM address visible to every role
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
     const uint32_t tmem = tmem_base;
-    const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(CO >> 3) << 17) | ((128u >> 4) << 24);
-    const uint32_t lbo_a = UM_HY * UM_HX * 16, sbo_a = UM_HX * 16;
-    const uint32_t lbo_b = CO * 16, sbo_b = 128;
-    const uint32_t sw_addr = smem_addr(sw);
-    // descriptor words: the start address is the low 14 bits of the low word (address >> 4; shared
-    // addresses stay below 2^18 bytes, so adding an offset never carries out of the field)
-    const uint32_t a_hi = (uint32_t)(umma_desc(0, lbo_a, sbo_a) >> 32);
-    const uint32_t b_lo = (uint32_t)umma_desc(sw_addr, lbo_b, sbo_b), b_hi = (uint32_t)(umma_desc(sw_addr, lbo_b, sbo_b) >> 32);
-    uint32_t phase[2] = {0u, 0u};
 
-    // read back the accumulators of plane p (buffer b), add the bias, store: warp w owns TMEM lanes
-    // 32 (w % 4) .. + 31 (patch rows) and the output channels of half w / 4
-    auto epilogue = [&](int p, int b) {
+    if (warp == UM_EPI_WARPS) {
+        // ---- MMA warp -------------------------------------------------------------------------
+        const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(CO >> 3) << 17) | ((128u >> 4) << 24);
+        const uint32_t lbo_a = UM_HY * UM_HX * 16, sbo_a = UM_HX * 16;
+        const uint32_t lbo_b = CO * 16, sbo_b = 128;
+        const uint32_t sw_addr = smem_addr(sw);
+        const uint32_t a_hi = (uint32_t)(umma_desc(0, lbo_a, sbo_a) >> 32);
+        const uint32_t b_lo = (uint32_t)umma_desc(sw_addr, lbo_b, sbo_b), b_hi = (uint32_t)(umma_desc(sw_addr, lbo_b, sbo_b) >> 32);
+        bool ok = true;
+        if (stall) {   // test hook: wait (briefly) on a barrier nothing is committed to, before any MMA
+            ok = __all_sync(0xffffffffu, mbar_wait(smem_addr(&bar_fin), 0u, UM_TEST_WAIT_NS));
+            if (!ok && lane == 0) abort_flag = 1;
+            ok = false;
+        }
+        for (int zc = z0; zc < z1 && ok; ++zc) {
+            const int b = (zc - z0) & 1;
+            // planes zc-1, zc, zc+1 staged, and buffer b read back (plane zc - 2)
+            bool good = true;
+#pragma unroll
+            for (int d = -1; d <= 1; ++d)
+                good = good && mbar_wait(smem_addr(&bar_full[slot_of(zc + d)]), (uint32_t)(fill_of(zc + d) & 1),
+                                         UM_WAIT_NS, abort_v);
+            if (good && zc - z0 >= 2)
+                good = mbar_wait(smem_addr(&bar_drained[b]), (uint32_t)(((zc - z0) / 2 - 1) & 1), UM_WAIT_NS, abort_v);
+            good = __all_sync(0xffffffffu, good);
+            if (!good) {
+                if (lane == 0) abort_flag = 1;
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+            if (lane == 0) {
+                const uint32_t a_lo[3] = {(uint32_t)umma_desc(smem_addr(slot(zc - 1)), lbo_a, sbo_a),
+                                          (uint32_t)umma_desc(smem_addr(slot(zc)), lbo_a, sbo_a),
+                                          (uint32_t)umma_desc(smem_addr(slot(zc + 1)), lbo_a, sbo_a)};
+#pragma unroll
+                for (int pt = 0; pt < 2; ++pt) {
+                    const uint32_t dt = tmem + (uint32_t)(b * 2 * CO + pt * CO);
+#pragma unroll
+                    for (int k = 0; k < 27; ++k) {
+                        const int dz = k / 9 - 1, dy = (k / 3) % 3 - 1, dx = k % 3 - 1;
+                        const uint32_t aoff = (uint32_t)((1 + dy) * UM_HX + pt * 8 + 1 + dx);   // 16-byte units
+#pragma unroll
+                        for (int cb = 0; cb < CB; ++cb) {
+                            const uint64_t da = ((uint64_t)a_hi << 32) | (a_lo[dz + 1] + aoff + (uint32_t)(2 * cb) * (lbo_a >> 4));
+                            const uint64_t db =
+                                ((uint64_t)b_hi << 32) | (b_lo + (uint32_t)((k * CB + cb) * 2 * CO));   // 16-byte units
+                            umma_bf16(dt, da, db, idesc, (k | cb) != 0 ? 1u : 0u);
+                        }
+                    }
+                }
+                umma_commit(&bar_acc[b]);                 // the plane's accumulators are complete
+                umma_commit(&bar_empty[slot_of(zc - 1)]);   // plane zc-1: no later MMA reads it
+            }
+            __syncwarp();
+        }
+        // every committed MMA done before the TMEM and the ring are released
+        if (lane == 0) umma_commit(&bar_fin);
+        __syncwarp();
+        const bool fin = __all_sync(0xffffffffu, mbar_wait(smem_addr(&bar_fin), 0u, UM_WAIT_NS));
+        if (!fin && lane == 0) abort_flag = 1;
+    } else {
+        // ---- load and epilogue warps ----------------------------------------------------------
         constexpr int CH = CO / 2;
         const int q = warp & 3, h = warp >> 2;
         const int mrow = 32 * q + lane;                // patch row index: node (mrow % 8, mrow / 8)
         const int yy = y0 + mrow / 8;
-#pragma unroll
-        for (int pt = 0; pt < 2; ++pt) {
-            uint32_t r[CH];
-            const uint32_t taddr = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(b * 2 * CO + pt * CO + h * CH);
-            if constexpr (CH == 16) {
-                asm volatile(
-                    "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
-                    "[%16];\n"
-                    : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-                      "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
-                      "=r"(r[15])
-                    : "r"(taddr));
-            } else {
-                asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];\n"
-                             : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-                               "=r"(r[7])
-                             : "r"(taddr));
+        int pending = INT_MIN;                         // plane staged last iteration, not yet reported
+        for (int zc = z0; zc < z1; ++zc) {
+            const int b = (zc - z0) & 1;
+            const bool good = __all_sync(0xffffffffu, mbar_wait(smem_addr(&bar_acc[b]),
+                                                                (uint32_t)(((zc - z0) / 2) & 1), UM_WAIT_NS, abort_v));
+            if (!good) {
+                if (lane == 0) abort_flag = 1;
+                break;
             }
-            asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
-            if (yy < ny) {
-                const size_t node = ((size_t)p * ny + yy) * nx + x0 + pt * 8 + (mrow % 8);
-                float v[CH];
-#pragma unroll
-                for (int o = 0; o < CH; ++o) v[o] = __uint_as_float(r[o]) + sbias[h * CH + o];
-                float4 *dst = reinterpret_cast<float4 *>(z + node * CO + h * CH);
-#pragma unroll
-                for (int o = 0; o < CH; o += 4) dst[o / 4] = make_float4(v[o], v[o + 1], v[o + 2], v[o + 3]);
-                if (act) {   // the next layer's input, silu(z) in BF16
-                    uint4 *ad = reinterpret_cast<uint4 *>(act + node * CO + h * CH);
-#pragma unroll
-                    for (int o = 0; o < CH; o += 8)
-                        ad[o / 8] = make_uint4(pack_bf16(silu(v[o]), silu(v[o + 1])),
-                                               pack_bf16(silu(v[o + 2]), silu(v[o + 3])),
-                                               pack_bf16(silu(v[o + 4]), silu(v[o + 5])),
-                                               pack_bf16(silu(v[o + 6]), silu(v[o + 7])));
-                }
-            }
-        }
-    };
-
-    bool ok = true;
-    // inflight[b]: MMAs committed to mbar[b] whose completion this warp has not yet seen
-    bool inflight[2] = {false, false};
-    if (stall) {   // test hook: wait (briefly) on a barrier no MMA is committed to, before issuing any
-        const bool good = __all_sync(0xffffffffu, mbar_wait(smem_addr(&mbar[0]), 0u, UM_TEST_WAIT_NS));
-        if (!good && lane == 0) abort_flag = 1;
-        ok = false;
-    }
-    for (int zc = z0; zc < z1 && ok; ++zc) {
-        const int b = (zc - z0) & 1;
-        if (tid == 0) {   // the MMAs of plane zc
-            const uint32_t a_lo[3] = {(uint32_t)umma_desc(smem_addr(slot(zc - 1)), lbo_a, sbo_a),
-                                      (uint32_t)umma_desc(smem_addr(slot(zc)), lbo_a, sbo_a),
-                                      (uint32_t)umma_desc(smem_addr(slot(zc + 1)), lbo_a, sbo_a)};
+            asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+            uint32_t r[2][CH];
 #pragma unroll
             for (int pt = 0; pt < 2; ++pt) {
-                const uint32_t dt = tmem + (uint32_t)(b * 2 * CO + pt * CO);
+                const uint32_t taddr = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(b * 2 * CO + pt * CO + h * CH);
+                if constexpr (CH == 16) {
+                    asm volatile(
+                        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
+                        "[%16];\n"
+                        : "=r"(r[pt][0]), "=r"(r[pt][1]), "=r"(r[pt][2]), "=r"(r[pt][3]), "=r"(r[pt][4]), "=r"(r[pt][5]),
+                          "=r"(r[pt][6]), "=r"(r[pt][7]), "=r"(r[pt][8]), "=r"(r[pt][9]), "=r"(r[pt][10]), "=r"(r[pt][11]),
+                          "=r"(r[pt][12]), "=r"(r[pt][13]), "=r"(r[pt][14]), "=r"(r[pt][15])
+                        : "r"(taddr));
+                } else {
+                    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];\n"
+                                 : "=r"(r[pt][0]), "=r"(r[pt][1]), "=r"(r[pt][2]), "=r"(r[pt][3]), "=r"(r[pt][4]),
+                                   "=r"(r[pt][5]), "=r"(r[pt][6]), "=r"(r[pt][7])
+                                 : "r"(taddr));
+                }
+            }
+            asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+            asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&bar_drained[b]);   // the MMA warp may reuse buffer b
+            if (yy < ny) {
 #pragma unroll
-                for (int k = 0; k < 27; ++k) {
-                    const int dz = k / 9 - 1, dy = (k / 3) % 3 - 1, dx = k % 3 - 1;
-                    const uint32_t aoff = (uint32_t)((1 + dy) * UM_HX + pt * 8 + 1 + dx);   // 16-byte units
+                for (int pt = 0; pt < 2; ++pt) {
+                    const size_t node = ((size_t)zc * ny + yy) * nx + x0 + pt * 8 + (mrow % 8);
+                    float v[CH];
 #pragma unroll
-                    for (int cb = 0; cb < CB; ++cb) {
-                        const uint64_t da = ((uint64_t)a_hi << 32) | (a_lo[dz + 1] + aoff + (uint32_t)(2 * cb) * (lbo_a >> 4));
-                        const uint64_t db =
-                            ((uint64_t)b_hi << 32) | (b_lo + (uint32_t)((k * CB + cb) * 2 * CO));   // 16-byte units
-                        umma_bf16(dt, da, db, idesc, (k | cb) != 0 ? 1u : 0u);
+                    for (int o = 0; o < CH; ++o) v[o] = __uint_as_float(r[pt][o]) + sbias[h * CH + o];
+                    if (keep_z || !act) {
+                        float4 *dst = reinterpret_cast<float4 *>(z + node * CO + h * CH);
+#pragma unroll
+                        for (int o = 0; o < CH; o += 4) dst[o / 4] = make_float4(v[o], v[o + 1], v[o + 2], v[o + 3]);
+                    }
+                    if (act) {   // the next layer's input, silu(z) in BF16
+                        uint4 *ad = reinterpret_cast<uint4 *>(act + node * CO + h * CH);
+#pragma unroll
+                        for (int o = 0; o < CH; o += 8)
+                            ad[o / 8] = make_uint4(pack_bf16(silu(v[o]), silu(v[o + 1])),
+                                                   pack_bf16(silu(v[o + 2]), silu(v[o + 3])),
+                                                   pack_bf16(silu(v[o + 4]), silu(v[o + 5])),
+                                                   pack_bf16(silu(v[o + 6]), silu(v[o + 7])));
                     }
                 }
             }
-            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
-                smem_addr(&mbar[b])));
-        }
-        inflight[b] = true;
-        bool good = true;
-        if (zc > z0) {   // plane zc - 1: wait for its MMAs (a warp decides as one)
-            good = __all_sync(0xffffffffu, mbar_wait(smem_addr(&mbar[1 - b]), phase[1 - b]));
-            if (good) {
-                phase[1 - b] ^= 1u;
-                inflight[1 - b] = false;
+            // staging: report the plane staged last iteration, then stage plane zc + 5 into the
+            // slot plane zc - 1 frees once the MMAs of plane zc are done (they are: bar_acc)
+            if (pending != INT_MIN) {
+                report_full(pending);
+                pending = INT_MIN;
             }
-            asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+            const int p = zc + UM_SLOTS - 1;
+            if (p <= z1) {
+                const bool free = __all_sync(0xffffffffu, mbar_wait(smem_addr(&bar_empty[slot_of(p)]),
+                                                                    (uint32_t)((fill_of(p) - 1) & 1), UM_WAIT_NS, abort_v));
+                if (!free) {
+                    if (lane == 0) abort_flag = 1;
+                    break;
+                }
+                stage(p);
+                pending = p;
+            }
         }
-        // refill: plane zc + 4 into the slot of plane zc - 2, which only plane zc - 1's MMAs read
-        if (good && zc + UM_AHEAD <= z1) um_load_plane<CB>(slot(zc + UM_AHEAD), in, nx, ny, nz, x0, y0, zc + UM_AHEAD);
-        cp_async_commit();
-        if (zc > z0) {   // read back plane zc - 1
-            if (good)
-                epilogue(zc - 1, 1 - b);
-            else if (lane == 0)
-                abort_flag = 1;
-        }
-        cp_async_wait_group<UM_AHEAD - 2>();   // plane zc + 2, read by the next plane's MMAs
-        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-        asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
-        __syncthreads();
-        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-        ok = abort_flag == 0;
+        if (pending != INT_MIN && !*abort_v) report_full(pending);
+        cp_async_wait_all();   // no copy of this block is still in flight when it returns
     }
-    if (ok) {   // the last plane
-        const int b = (z1 - 1 - z0) & 1;
-        const bool good = __all_sync(0xffffffffu, mbar_wait(smem_addr(&mbar[b]), phase[b]));
-        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-        if (good) {
-            inflight[b] = false;
-            epilogue(z1 - 1, b);
-        } else if (lane == 0) {
-            abort_flag = 1;
-        }
-    }
-    // After an expiry, MMAs committed earlier may still be reading the ring and writing TMEM:
-    // wait for them once more (bounded) before the ring is left and the TMEM freed.
-#pragma unroll
-    for (int bb = 0; bb < 2; ++bb)
-        if (inflight[bb]) __all_sync(0xffffffffu, mbar_wait(smem_addr(&mbar[bb]), phase[bb]));
-    cp_async_wait_all();   // no copy of this block is still in flight when it returns
-    __syncthreads();
-    if (abort_flag && tid == 0) atomicExch(err, 1);
     asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
     __syncthreads();
+    if (abort_flag && tid == 0) atomicExch(err, 1);
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(TCOLS));
 }
 
@@ -1182,7 +1253,7 @@ cudaError_t launch_conv_mma(lbm_cnn *c, const uint4 *wfrag, const __nv_bfloat16 
 // next layer's input; fused into the tcgen05 kernel's epilogue, a separate pass for the others).
 template <int MT, int CB>
 cudaError_t launch_conv(lbm_cnn *c, int layer, bool transpose, const __nv_bfloat16 *in, const float *bias, float *out,
-                        __nv_bfloat16 *act = nullptr)
+                        __nv_bfloat16 *act = nullptr, bool keep_z = true)
 {
     const uint4 *wfrag = transpose ? c->wt[layer] : c->wf[layer];
     const __nv_bfloat16 *wpack = transpose ? c->wut[layer] : c->wu[layer];
@@ -1203,7 +1274,7 @@ cudaError_t launch_conv(lbm_cnn *c, int layer, bool transpose, const __nv_bfloat
         const int zlen = (c->nz + nzc - 1) / nzc;
         nzc = (c->nz + zlen - 1) / zlen;
         tslb::conv_umma_kernel<MT, CB><<<dim3(tiles, nzc), tslb::UM_THREADS, smem, c->stream>>>(
-            c->nx, c->ny, c->nz, wpack, in, bias, out, act, zlen, c->derr, c->test_expire);
+            c->nx, c->ny, c->nz, wpack, in, bias, out, act, zlen, c->derr, c->test_expire, keep_z ? 1 : 0);
         return cudaGetLastError();
     }
     cudaError_t e = launch_conv_mma<MT, CB>(c, wfrag, in, bias, out);
@@ -1215,16 +1286,18 @@ cudaError_t launch_conv(lbm_cnn *c, int layer, bool transpose, const __nv_bfloat
     return e;
 }
 
-cudaError_t forward(lbm_cnn *c, const float *x)
+// train: keep every layer's pre-activation z (the backward pass needs it); otherwise only the last
+// layer's, the output (the tensor-core kernel then skips the other z stores)
+cudaError_t forward(lbm_cnn *c, const float *x, bool train)
 {
     const int N = c->N;
     cudaError_t e;
     tslb::pack_input_kernel<<<(N + 255) / 256, 256, 0, c->stream>>>(x, N, c->a[0]);
     // z_l = conv_l(a_l) + b_l and a_{l+1} = silu(z_l); biases zero-padded to the padded channels
-    if ((e = launch_conv<2, 1>(c, 0, false, c->a[0], c->bpad, c->z[0], c->a[1])) != cudaSuccess) return e;
+    if ((e = launch_conv<2, 1>(c, 0, false, c->a[0], c->bpad, c->z[0], c->a[1], train)) != cudaSuccess) return e;
     for (int l = 1; l < tslb::NLAYER; ++l) {
         const float *bias = c->bpad + 32 * l;
-        e = l < 3 ? launch_conv<2, 2>(c, l, false, c->a[l], bias, c->z[l], c->a[l + 1])
+        e = l < 3 ? launch_conv<2, 2>(c, l, false, c->a[l], bias, c->z[l], c->a[l + 1], train)
                   : launch_conv<1, 2>(c, l, false, c->a[l], bias, c->z[l]);
         if (e != cudaSuccess) return e;
     }
@@ -1482,7 +1555,7 @@ lbm_status lbm_cnn_test_expire_wait(lbm_cnn *cnn, int on)
 lbm_status lbm_cnn_forward(lbm_cnn *cnn, const float *x, float *y)
 {
     if (!cnn || !x || !y) return cnn_fail(LBM_ERR_ARG, "network, x and y are required");
-    CNN_TRY(forward(cnn, x));
+    CNN_TRY(forward(cnn, x, false));
     tslb::unpack_output_kernel<<<(cnn->N + 255) / 256, 256, 0, cnn->stream>>>(cnn->z[3], cnn->N, y);
     CNN_TRY(cudaGetLastError());
     return check_timeout(cnn);
@@ -1492,7 +1565,7 @@ lbm_status lbm_cnn_grad(lbm_cnn *cnn, const float *x, const float *t, int accumu
 {
     if (!cnn || !x || !t) return cnn_fail(LBM_ERR_ARG, "network, x and t are required");
     if (!accumulate) CNN_TRY(cudaMemsetAsync(cnn->grad, 0, cnn->nparams * sizeof(float), cnn->stream));
-    CNN_TRY(forward(cnn, x));
+    CNN_TRY(forward(cnn, x, true));
     tslb::loss_kernel<<<cnn->loss_blocks, 256, 0, cnn->stream>>>(cnn->z[3], t, cnn->N, cnn->dz[3], cnn->dzb,
                                                                   cnn->dsum);
     CNN_TRY(cudaGetLastError());
@@ -1604,7 +1677,7 @@ lbm_status lbm_closure_apply(lbm_ctx *ctx, lbm_cnn *cnn, const lbm_closure_norm 
     const int N = v.G.N;
     tslb::features_kernel<<<(N + 255) / 256, 256, 0, v.stream>>>(v.G, v.P, v.g, v.phi, v.u, *norm, cnn->xbuf);
     CNN_TRY(cudaGetLastError());
-    CNN_TRY(forward(cnn, cnn->xbuf));
+    CNN_TRY(forward(cnn, cnn->xbuf, false));
     tslb::unpack_output_kernel<<<(N + 255) / 256, 256, 0, v.stream>>>(cnn->z[3], N, cnn->ybuf);
     CNN_TRY(cudaMemsetAsync(cnn->dsum, 0, 6 * sizeof(double), v.stream));
     tslb::corr_sums_kernel<<<296, 256, 0, v.stream>>>(cnn->ybuf, v.phi, *norm, v.P.rho_g, v.P.drho, N, cnn->dsum);
