@@ -211,7 +211,7 @@ __device__ __forceinline__ bool ens_grid_barrier(EnsSync *sync, bool arrive)
 
 // STORE: LBM_FP32 or one of the moment storages (LBM_MOM, LBM_MOM_BF16, LBM_MOM_FP16)
 template <int RY, int STORE>
-__global__ void __launch_bounds__(256, STORE == LBM_FP32 ? 3 : 2)
+__global__ void __launch_bounds__(256, 2)
     ens_persistent_kernel(const EnsBox *__restrict__ boxes, int nb, int ac_tasks, int lbm_work, int lbm_block,
                           int fpn, const float *__restrict__ phi, const float *__restrict__ w,
                           float *__restrict__ phi_new, const float *__restrict__ g_in, const float *__restrict__ u_in,

@@ -352,7 +352,8 @@ lbm_status lbm_run_phase(lbm_ctx *ctx, int phase, int nrep)
                                                 ctx->g[b], ctx->u[b], ctx->flux, ctx->split, ctx->stream)
                          : ctx->storage != LBM_FP32
                              ? tslb::launch_lbm16(ctx->G, ctx->P, ctx->storage, ctx->g[a], ctx->pst[a], ctx->phi[b],
-                                                  ctx->u[a], ctx->g[b], ctx->pst[b], ctx->u[b], ctx->flux, ctx->stream)
+                                                  ctx->u[a], ctx->g[b], ctx->pst[b], ctx->u[b], ctx->flux, ctx->split,
+                                                  ctx->stream)
                              : tslb::launch_lbm(ctx->G, ctx->P, 0, ctx->g[a], nullptr, ctx->phi[b], ctx->u[a],
                                                 ctx->g[b], nullptr, ctx->u[b], ctx->flux, ctx->stream);
         if (e != cudaSuccess) return fail(LBM_ERR_CUDA, "phase launch failed: %s", cudaGetErrorString(e));

@@ -129,7 +129,8 @@ cudaError_t launch_step_split(const Grid &G, const Phys &P, const StepArgs &a, i
     if (a.storage >= LBM_MOM)
         return launch_mom(G, P, a.storage, a.g_in, a.u_in, a.phi_out, a.g_out, a.u_out, a.flux, zchunks, s);
     if (a.storage != 0)
-        return launch_lbm16(G, P, a.storage, a.g_in, a.p_in, a.phi_out, a.u_in, a.g_out, a.p_out, a.u_out, a.flux, s);
+        return launch_lbm16(G, P, a.storage, a.g_in, a.p_in, a.phi_out, a.u_in, a.g_out, a.p_out, a.u_out, a.flux,
+                            zchunks, s);
     return launch_lbm(G, P, 0, a.g_in, nullptr, a.phi_out, a.u_in, a.g_out, nullptr, a.u_out, a.flux, s);
 }
 

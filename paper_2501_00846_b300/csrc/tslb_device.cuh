@@ -224,16 +224,15 @@ __device__ __forceinline__ Collided collide_moments(const float (&f)[27], float 
     return collide_from_moments(raw_moments(f), phi, gpx, gpy, gpz, lap, ubx, uby, ubz, P);
 }
 
+// The post-collision populations g (NEQ: the deviations h) of a collided node, in the even/odd
+// form described above collide_node.
 template <bool NEQ = false>
-__device__ __forceinline__ void collide_node(const float (&f)[27], float phi, float gpx, float gpy, float gpz,
-                                             float lap, float ubx, float uby, float ubz, const Phys &P,
-                                             float (&g)[27], float &ux, float &uy, float &uz, float *ps_out = nullptr)
+__device__ __forceinline__ void populations_from(const Collided &c, float (&g)[27])
 {
-    const Collided c = collide_moments(f, phi, gpx, gpy, gpz, lap, ubx, uby, ubz, P);
     const float ps = c.ps, omega = c.omega;
+    const float ux = c.ux, uy = c.uy, uz = c.uz;
     const float ax = c.ax, ay = c.ay, az = c.az;
     const float Axx = c.Axx, Ayy = c.Ayy, Azz = c.Azz, Axy = c.Axy, Axz = c.Axz, Ayz = c.Ayz;
-    ux = c.ux, uy = c.uy, uz = c.uz;
 
     // collision constants
     const float om1 = 1.0f - omega;
@@ -250,7 +249,6 @@ __device__ __forceinline__ void collide_node(const float (&f)[27], float phi, fl
     const float vz = 1.5f * az - twok2 * (Axz * ux + Ayz * uy + Azz * uz);
     const float A2xy = 2.0f * Axy, A2xz = 2.0f * Axz, A2yz = 2.0f * Ayz;
 
-    if (ps_out) *ps_out = ps;
     g[13] = NEQ ? K0 : wgt(13) * K0;
 #pragma unroll
     for (int i = 0; i < 13; ++i) {
@@ -267,6 +265,17 @@ __device__ __forceinline__ void collide_node(const float (&f)[27], float phi, fl
         g[i] = NEQ ? E + O : wgt(i) * (E + O);
         g[26 - i] = NEQ ? E - O : wgt(i) * (E - O);
     }
+}
+
+template <bool NEQ = false>
+__device__ __forceinline__ void collide_node(const float (&f)[27], float phi, float gpx, float gpy, float gpz,
+                                             float lap, float ubx, float uby, float ubz, const Phys &P,
+                                             float (&g)[27], float &ux, float &uy, float &uz, float *ps_out = nullptr)
+{
+    const Collided c = collide_moments(f, phi, gpx, gpy, gpz, lap, ubx, uby, ubz, P);
+    ux = c.ux, uy = c.uy, uz = c.uz;
+    if (ps_out) *ps_out = c.ps;
+    populations_from<NEQ>(c, g);
 }
 
 // Allen–Cahn flux W = ubar phi + kappa_AC max(phi (1 - phi), 0) n with the normal

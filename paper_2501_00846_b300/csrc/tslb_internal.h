@@ -62,11 +62,12 @@ cudaError_t launch_lbm(const Grid &G, const Phys &P, int storage, const void *g_
 // from outside the step (initialisation, restore, after a path that does not keep W).
 cudaError_t launch_flux(const Grid &G, const Phys &P, const float *phi, const float *u, float *w, cudaStream_t s);
 
-// Tiled lattice Boltzmann kernel for the 16-bit formats (storage 1 BF16, 2 FP16), with (P, ubar)
-// and phi^{n+1} staged in shared memory; same arguments as launch_lbm.
+// z-marching lattice Boltzmann kernel for the 16-bit formats (storage 1 BF16, 2 FP16), with (P,
+// ubar) and phi^{n+1} staged in shared memory once per plane; arguments as launch_lbm, zchunks as
+// for the other marching kernels (<= 0: the default for the grid and GPU).
 cudaError_t launch_lbm16(const Grid &G, const Phys &P, int storage, const void *h_in, const float *p_in,
                          const float *phi_new, const float *u_in, void *h_out, float *p_out, float *u_out,
-                         float *w_out, cudaStream_t s);
+                         float *w_out, int zchunks, cudaStream_t s);
 
 // 16-bit population formats (h and P; see the storage formats in tslb_device.cuh):
 // initialise from equilibrium (h = 0, P = p*0 or 0), expand to FP32 g (directions [i0, i0+ni)

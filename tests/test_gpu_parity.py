@@ -313,23 +313,30 @@ def test_step_before_init_and_nonfinite_detection():
 
 # -- the benchmark workload at full size, in the benchmark's launch configuration --------------
 
+# 20 steps: the start-up flow is developed (max|u| ~ 0.1 in the gas) and the velocity is compared
+# with the same relative bar as everywhere else.  Beyond ~25 steps this transient at density ratio
+# 1000 amplifies rounding: the FP64 oracle started from inputs perturbed by one FP32 rounding
+# (2^-24 relative) differs from itself by 5e-8 in phi after 20 steps but 4e-6 after 30 and 5e-5
+# after 40, so no FP32 result can be held to 1e-5 there.
+FULL_STEPS = 20
+
+
 @pytest.fixture(scope="module")
 def bubble_full():
     wl = inputs.rising_bubble()          # 128 x 128 x 256, walls on z, ratios 1000 / 100
-    P, ref = _oracle_run(wl, 2)
+    P, ref = _oracle_run(wl, FULL_STEPS)
     return wl, P, ref
 
 
 @pytest.mark.parametrize("path", [0, 2], ids=["two_kernel", "fused"])
-def test_rising_bubble_full_size_two_steps(bubble_full, path):
+def test_rising_bubble_full_size(bubble_full, path):
+    """The whole benchmark box, element by element against the oracle after 20 steps, in the
+    benchmark's launch configuration (path 0) and with the fused kernel (path 2), at the FP32 bars
+    (phi absolute, u and p relative to their maxima)."""
     wl, P, ref = bubble_full
-    gpu = _gpu_run(wl, 2, path=path)
-    dphi, du, dp = _compare(gpu, P, ref)
-    print(f"rising bubble 128x128x256, 2 steps: {dphi:.3e} {du:.3e} {dp:.3e}")
-    assert dphi <= TOL_PHI
-    # at rest after two steps velocities are ~1e-6: compare against the velocity scale sqrt(gR)
-    assert np.abs(gpu[1] - ref.u).max() <= TOL_U * 0.04
-    assert dp <= TOL_P
+    gpu = _gpu_run(wl, FULL_STEPS, path=path)
+    assert np.abs(ref.u).max() > 1e-4
+    _assert_parity(gpu, P, ref, f"rising bubble 128x128x256, {FULL_STEPS} steps, path {path}")
 
 
 # -- long runs: integral observables within 0.5% ---------------------------------------------------
