@@ -434,15 +434,26 @@ __global__ void __launch_bounds__(UM_THREADS, 1) conv_umma_kernel(int nx, int ny
     auto slot_of = [&](int p) { return (p - (z0 - 1)) % UM_SLOTS; };
     auto fill_of = [&](int p) { return (p - (z0 - 1)) / UM_SLOTS; };
     auto slot = [&](int p) { return ring + (size_t)slot_of(p) * PB; };
+    // the 16-byte chunks this epilogue thread stages in every plane: element offsets within a plane
+    // of the input (wrapped once here; -1 past the end)
+    constexpr int NCHUNK = CG * UM_HY * UM_HX;
+    constexpr int PER = (NCHUNK + UM_EPI_THREADS - 1) / UM_EPI_THREADS;
+    int soff[PER];
+#pragma unroll
+    for (int j = 0; j < PER; ++j) {
+        const int e = tid + j * UM_EPI_THREADS;
+        const int node = e % (UM_HY * UM_HX), cg = e / (UM_HY * UM_HX);
+        const int hy = node / UM_HX, hx = node - hy * UM_HX;
+        soff[j] = e < NCHUNK && tid < UM_EPI_THREADS
+                      ? (mwrap(y0 - 1 + hy, ny) * nx + mwrap(x0 - 1 + hx, nx)) * (CB * 16) + cg * 8
+                      : -1;
+    }
     auto stage = [&](int p) {   // cp.async copies of plane p by the epilogue threads (one group)
-        const size_t plane = (size_t)mwrap(p, nz) * nx * ny;
-        uint8_t *dst = slot(p);
-        for (int e = tid; e < CG * UM_HY * UM_HX; e += UM_EPI_THREADS) {
-            const int node = e % (UM_HY * UM_HX), cg = e / (UM_HY * UM_HX);
-            const int hy = node / UM_HX, hx = node - hy * UM_HX;
-            const size_t src = plane + (size_t)mwrap(y0 - 1 + hy, ny) * nx + mwrap(x0 - 1 + hx, nx);
-            cp_async16(dst + (size_t)e * 16, in + src * (CB * 16) + cg * 8);
-        }
+        const __nv_bfloat16 *src = in + (size_t)mwrap(p, nz) * nx * ny * (CB * 16);
+        uint8_t *dst = slot(p) + (size_t)tid * 16;
+#pragma unroll
+        for (int j = 0; j < PER; ++j)
+            if (soff[j] >= 0) cp_async16(dst + (size_t)j * UM_EPI_THREADS * 16, src + soff[j]);
         cp_async_commit();
     };
     // the staged copies are complete: make them visible to the tensor core (async proxy), report
@@ -553,6 +564,9 @@ __global__ void __launch_bounds__(UM_THREADS, 1) conv_umma_kernel(int nx, int ny
         const int q = warp & 3, h = warp >> 2;
         const int mrow = 32 * q + lane;                // patch row index: node (mrow % 8, mrow / 8)
         const int yy = y0 + mrow / 8;
+        float bv[CH];                                  // this warp's half of the bias, in registers
+#pragma unroll
+        for (int o = 0; o < CH; ++o) bv[o] = sbias[h * CH + o];
         int pending = INT_MIN;                         // plane staged last iteration, not yet reported
         for (int zc = z0; zc < z1; ++zc) {
             const int b = (zc - z0) & 1;
@@ -592,7 +606,7 @@ __global__ void __launch_bounds__(UM_THREADS, 1) conv_umma_kernel(int nx, int ny
                     const size_t node = ((size_t)zc * ny + yy) * nx + x0 + pt * 8 + (mrow % 8);
                     float v[CH];
 #pragma unroll
-                    for (int o = 0; o < CH; ++o) v[o] = __uint_as_float(r[pt][o]) + sbias[h * CH + o];
+                    for (int o = 0; o < CH; ++o) v[o] = __uint_as_float(r[pt][o]) + bv[o];
                     if (keep_z || !act) {
                         float4 *dst = reinterpret_cast<float4 *>(z + node * CO + h * CH);
 #pragma unroll
