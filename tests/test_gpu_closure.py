@@ -292,10 +292,7 @@ def test_convolution_kernels_agree(shape):
     differences into an occasional one-unit flip of a BF16 activation, so the two agree to 2e-3
     relative L2 (measured 2.5e-4), ten times inside the 2e-2 bar each keeps against the FP64
     network; every element of kernel 0 is checked against its definition elsewhere
-    (test_every_operation_matches_its_definition_elementwise)."""Kernels 1 (mma.sync from shared-memory tiles) and 2 (mma.sync from global memory) issue the
-    same MMAs in the same order: identical outputs and gradients.  Kernel 0 (tcgen05, TMEM
-    accumulators) adds the same BF16 products per output in the same K order; it is held to
-    outputs within 1e-5 and gradients within 1e-4 (relative L2) of kernel 1 (measured: identical)."""
+    (test_every_operation_matches_its_definition_elementwise)."""
     import torch
     nx, ny, nz = shape
     flat, x, t = _random_case(nx, ny, nz, seed=4)
