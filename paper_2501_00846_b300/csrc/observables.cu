@@ -61,10 +61,18 @@ __global__ void __launch_bounds__(kThreads) obs_partial_kernel(Grid G, double rh
 #pragma unroll
             for (int i = 0; i < 27; ++i) s = fmaf(wgt(i), load_h16(gv, storage, i * N + k), s);
             ps = s;
-        } else {
+        } else {   // FP32 populations: an error-free FP32 sum (TwoSum; hi + lo carries p* to ~2^-46), then FP64
             const float *g = (const float *)gv;
+            float hi = 0.0f, lo = 0.0f;
 #pragma unroll
-            for (int i = 0; i < 27; ++i) ps += (double)g[i * N + k];
+            for (int i = 0; i < 27; ++i) {
+                const float a = g[i * N + k];
+                const float sum = __fadd_rn(hi, a);
+                const float bp = __fsub_rn(sum, hi);
+                lo = __fadd_rn(lo, __fadd_rn(__fsub_rn(hi, __fsub_rn(sum, bp)), __fsub_rn(a, bp)));
+                hi = sum;
+            }
+            ps = (double)hi + (double)lo;
         }
         const double ph = phi[k];
         const double ux = u[k], uy = u[N + k], uz = u[2 * N + k];
@@ -73,9 +81,10 @@ __global__ void __launch_bounds__(kThreads) obs_partial_kernel(Grid G, double rh
             continue;
         }
         const double rho = rho_g + ph * drho;
-        const double gas = 1.0 - ph;
+        // the (1 - phi)-weighted sums are formed at the end as (count, sum x, sum u) minus the
+        // phi-weighted ones (obs_final_kernel); here F_SUM_GAS, F_XGAS, F_UGAS hold the former
         r[F_SUM_PHI] += ph;
-        r[F_SUM_GAS] += gas;
+        r[F_SUM_GAS] += 1.0;
         r[F_MASS] += rho;
         r[F_SUM_PS] += ps;
         r[F_MOM + 0] += rho * ux;
@@ -84,15 +93,15 @@ __global__ void __launch_bounds__(kThreads) obs_partial_kernel(Grid G, double rh
         r[F_XPHI + 0] += ph * x;
         r[F_XPHI + 1] += ph * y;
         r[F_XPHI + 2] += ph * z;
-        r[F_XGAS + 0] += gas * x;
-        r[F_XGAS + 1] += gas * y;
-        r[F_XGAS + 2] += gas * z;
+        r[F_XGAS + 0] += (double)x;
+        r[F_XGAS + 1] += (double)y;
+        r[F_XGAS + 2] += (double)z;
         r[F_UPHI + 0] += ph * ux;
         r[F_UPHI + 1] += ph * uy;
         r[F_UPHI + 2] += ph * uz;
-        r[F_UGAS + 0] += gas * ux;
-        r[F_UGAS + 1] += gas * uy;
-        r[F_UGAS + 2] += gas * uz;
+        r[F_UGAS + 0] += ux;
+        r[F_UGAS + 1] += uy;
+        r[F_UGAS + 2] += uz;
         const double p = ps * rho * (1.0 / 3.0);
         if (ph > 0.999) { r[F_PLIQ] += p; r[F_NLIQ] += 1.0; }
         if (ph < 0.001) { r[F_PGAS] += p; r[F_NGAS] += 1.0; }
@@ -123,11 +132,20 @@ __global__ void __launch_bounds__(kThreads) obs_partial_kernel(Grid G, double rh
 
 __global__ void obs_final_kernel(const double *__restrict__ partials, int nblocks, double *__restrict__ out)
 {
+    __shared__ double tot[F_USED];
     const int f = threadIdx.x;
+    if (f < F_USED) {
+        double acc = partials[f];
+        for (int b = 1; b < nblocks; ++b) acc = combine(f, acc, partials[(size_t)b * kObsFields + f]);
+        tot[f] = acc;
+    }
+    __syncwarp();
     if (f >= F_USED) return;
-    double acc = partials[f];
-    for (int b = 1; b < nblocks; ++b) acc = combine(f, acc, partials[(size_t)b * kObsFields + f]);
-    out[f] = acc;
+    double v = tot[f];   // (1 - phi)-weighted sums: (count, sum x, sum u) minus the phi-weighted ones
+    if (f == F_SUM_GAS) v -= tot[F_SUM_PHI];
+    if (f >= F_XGAS && f < F_XGAS + 3) v -= tot[F_XPHI + f - F_XGAS];
+    if (f >= F_UGAS && f < F_UGAS + 3) v -= tot[F_UPHI + f - F_UGAS];
+    out[f] = v;
 }
 
 }  // namespace
