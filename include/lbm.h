@@ -373,13 +373,13 @@ lbm_status lbm_cnn_set_params(lbm_cnn *cnn, const float *params);  /* host; rese
 lbm_status lbm_cnn_get_grads(lbm_cnn *cnn, float *grads);          /* host, the kept gradients */
 
 /* Convolution kernel: 0 (default, the fastest measured) tcgen05.mma with TMEM accumulators
- * (shared-memory descriptors, four MMA-issuing warps, the activation fused into its epilogue);
- * 1 mma.sync from shared-memory tiles; 2 mma.sync with fragments straight from global memory.
- * Kernels 1 and 2 add the same BF16 products in the same order per output and give identical
- * results; kernel 0 adds them in two halves of the 27 offsets, so its results differ in the last
- * bits (and, through the BF16 rounding of the next layer's input, by ~1e-4 relative at the
- * output).  lbm_cnn_forward and lbm_cnn_grad return LBM_ERR_TIMEOUT if a tensor-core kernel gave
- * up waiting for its MMAs.  LBM_ERR_ARG for other values. */
+ * (shared-memory descriptors; each input plane read once for its three z offsets, N = 3 x the
+ * output channels; the activation fused into its epilogue; launched with programmatic dependent
+ * launch); 1 mma.sync from shared-memory tiles; 2 mma.sync with fragments straight from global
+ * memory.  All three add the same BF16 products in the same FP32 order per output and give
+ * identical results.  Training is deterministic: no reduction uses atomics.  lbm_cnn_forward and
+ * lbm_cnn_grad return LBM_ERR_TIMEOUT if a tensor-core kernel gave up waiting for its MMAs.
+ * LBM_ERR_ARG for other values. */
 lbm_status lbm_cnn_set_conv_kernel(lbm_cnn *cnn, int kernel);
 
 /* Test hook of the bounded waits.  Every mbarrier wait of the tensor-core convolution is bounded

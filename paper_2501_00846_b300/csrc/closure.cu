@@ -4,19 +4,22 @@
 // is the library's coarse-grid correction, measured against the fine-grid solver.
 //
 // Every convolution (forward, and the backward pass with respect to its input) is an implicit GEMM
-// on the tensor cores: D[o][n] = sum_{k, i} W[o][i][k] a[n + off_k][i], with the K dimension
-// walked in chunks of 16 input channels at one offset k.  A warp computes 32 consecutive nodes of
-// one x row (4 n8 tiles) for up to 32 output channels (2 m16 tiles) with mma.sync m16n8k16
-// (BF16 operands, FP32 accumulation); weights sit in shared memory in fragment order (one 16-byte
-// load per lane and m tile), activations are channel-last BF16 so that a B fragment is two 4-byte
-// loads per node.  The weight gradient, a reduction over all nodes, runs on the CUDA cores in FP32
-// with shared-memory tiles; master weights, gradients and Adam moments are FP32.
+// on the tensor cores: D[o][n] = sum_{k, i} W[o][i][k] a[n + off_k][i], BF16 operands, FP32
+// accumulation, channel-last BF16 activations.  Three forms compute it with the same products in
+// the same order (identical results): the default conv_umma_kernel (tcgen05.mma, accumulators in
+// TMEM, operands staged in shared memory; described above it), and two mma.sync m16n8k16 forms
+// (conv_tile_kernel from shared-memory tiles, conv_mma_kernel from global memory), where a warp
+// computes 32 consecutive nodes of one x row for up to 32 output channels.  The weight gradient,
+// a reduction over all nodes, runs on mma.sync from channel-last tiles with per-block partials
+// added in a fixed order; master weights, gradients and Adam moments are FP32, and no reduction
+// uses atomics, so training is reproducible run to run.
 #include <limits.h>
 #include <math.h>
 #include <stdarg.h>
 #include <stdio.h>
 #include <string.h>
 
+#include <algorithm>
 #include <new>
 
 #include <cuda_bf16.h>
@@ -35,6 +38,8 @@ constexpr int CINP[NLAYER] = {16, 32, 32, 32};    // padded to multiples of 16
 constexpr int COUTP[NLAYER] = {32, 32, 32, 16};
 
 constexpr int wcount(int l) { return COUT[l] * CIN[l] * 27; }
+constexpr int kBiasChunk = 4096;   // nodes per block of the bias gradient
+constexpr int kCorrBlocks = 296;   // blocks of the correction's sums
 constexpr int pcount(int l) { return wcount(l) + COUT[l]; }
 
 // ---- tensor-core implicit-GEMM convolution -------------------------------------------------
@@ -146,6 +151,8 @@ __device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+// every cp.async group of this thread but the most recent one is complete
+__device__ __forceinline__ void cp_async_wait_but_last() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
 __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi)
 {
     const uint32_t l = __bfloat16_as_ushort(__float2bfloat16_rn(lo));
@@ -277,38 +284,56 @@ __global__ void __launch_bounds__(256) conv_tile_kernel(int nx, int ny, int nz, 
 
 // ---- the same convolution on the 5th-generation tensor cores (tcgen05, TMEM) ---------------
 //
-// GEMM orientation: D[n][o] = sum_{k, i} a[n + off_k][i] W[o][i][k] with M = 128 nodes (an 8 x 16
-// x-by-y patch of one plane), N = the output channels (32 or 16) and K = 16 input channels at one
-// offset per tcgen05.mma (kind::f16: BF16 operands, FP32 accumulation in TMEM).  Both operands
-// are read by the tensor core from shared memory through K-major, unswizzled matrix descriptors:
+// GEMM orientation: one tcgen05.mma (kind::f16: BF16 operands, FP32 accumulation in TMEM) computes
+//   D[n][(jb, o)] += sum_i a_zi[n + (dx, dy)][i] W[o][i][dx, dy, dz = 1 - jb]
+// with M = 128 nodes n (an 8 x 16 x-by-y patch of input plane zi), K = 16 input channels at one
+// in-plane offset (dx, dy), and N = 3 CO: the three z offsets of the stencil side by side.  Column
+// block jb of the result is input plane zi's contribution to output plane zi - 1 + jb, so each
+// staged input plane is read by the tensor core once, for all 27 taps, and the weights are three
+// times wider per instruction than with one z offset at a time.  That matters because both
+// operands come from shared memory: with N = CO = 32 an MMA reads 5 KB for 64 Ki MACs, more bytes
+// per cycle than shared memory delivers; with N = 96 it reads 7 KB for 192 Ki MACs.
 //   A: the block's halo tile, staged channel-group-major ([channel group of 8][hy][hx][8]), so the
 //      8 x-consecutive nodes of a patch row are one 8 x 16-byte core matrix; patch rows are SBO =
-//      HX * 16 bytes apart, the two channel groups of a K step LBO = HY * HX * 16 bytes apart, and a
-//      neighbour offset (dx, dy) only moves the start address;
-//   B: the weights, [k][channel chunk][group of 8 channels][o][8] (LBO = N * 16, SBO = 128).
-// A block owns a 16 x 16 column tile (two patches) and marches a z chunk, with warps in two roles
-// that hand work to each other through mbarriers:
-//   warps 8..11 (the MMA warps, one per patch and half of the 27 offsets, each on its own
-//     scheduler): one thread of each issues its share of plane zc's MMAs (fully unrolled; the
-//     descriptors are precomputed words plus compile-time offsets) into its own accumulator of one
-//     of two TMEM buffers, as soon as planes zc-1..zc+1 are staged and the buffer has been read
-//     back, then commits them to the buffer's "full" barrier and to the "empty" barrier of the
-//     slot of plane zc-1, which no later MMA reads;
-//   warps 0..7 (load and epilogue): read back plane zc's accumulators (both halves, added) when its barrier completes
-//     (tcgen05.ld; warp w owns TMEM lanes 32 (w % 4) .. + 31 = patch rows 4 (w % 4) .. + 3 and
-//     half w / 4 of the output channels), report the buffer drained, add the bias and store z
-//     (when kept) and, for the forward pass, the next layer's input silu(z) in BF16; then stage
-//     plane zc + 5 into the ring slot plane zc - 1 frees (cp.async; the copies of one plane are
-//     waited for, fenced for the async proxy and reported "full" one iteration later).
-// The MMAs of a plane thus run while the epilogue of the previous plane drains and the staging of
-// later planes is in flight, and no barrier of the whole block sits on the per-plane path.  The
-// weights are staged with cp.async as well.  Every mbarrier wait is bounded in time: on expiry
-// the kernel records an error, every role stops at its next wait, the MMA thread waits once more
-// for the MMAs it committed, the copies in flight are waited for and the TMEM is released.
+//      HX * 16 bytes apart, the two channel groups of a K step LBO = HY * HX * 16 bytes apart, and an
+//      in-plane offset (dx, dy) only moves the start address (K-major, unswizzled descriptors);
+//   B: the weights, [(dx, dy)][channel chunk][group of 8 channels][(jb, o)][8] (LBO = 3 CO * 16,
+//      SBO = 128); a sub-range of the z blocks is a sub-range of rows.
+//   D: per patch, a ring of UM_ACC output planes of CO columns each; the three column blocks of an
+//      MMA are three consecutive planes of the ring (an MMA that would wrap is split in two).
+//      Block 2 is always the first write of output plane zi + 1: the first MMA of each input plane
+//      issues it separately with accumulation off, so no accumulator is ever cleared.
+// A block owns a 16 x 16 column tile (two patches) and marches a z chunk z0 .. z1 - 1 over input
+// planes z0 - 1 .. z1 (at the chunk's ends only the blocks that land inside it are issued), with
+// warps in two roles that hand work to each other through mbarriers:
+//   warps 8, 9 (the MMA warps, one per patch): one thread of each issues input plane zi's MMAs
+//     (9 offsets x CB channel chunks, fully unrolled; descriptors are precomputed words plus
+//     compile-time offsets) as soon as the plane is staged and, when the MMAs open a new output
+//     plane, that plane's accumulator slot has been read back; then commits them to the "empty"
+//     barrier of the plane's staging slot and to the "done" barrier of output plane zi - 1;
+//   warps 0..7 (load and epilogue): read back output plane p when its barrier completes
+//     (tcgen05.ld; warp w owns TMEM lanes 32 (w % 4) .. + 31 = patch rows 4 (w % 4) .. + 3 and half
+//     w / 4 of the output channels), report the slot drained, add the bias and store z (when
+//     kept) and, for the forward pass, the next layer's input silu(z) in BF16; then stage the input
+//     planes whose slots the consumed planes freed (cp.async; the copies are waited for, fenced for
+//     the async proxy and reported "full" one iteration later, after that iteration's stores).
+// The MMAs of later planes run while the epilogue drains and the staging is in flight, and no
+// barrier of the whole block sits on the per-plane path.  The weights are staged with cp.async as
+// well.  Every mbarrier wait is bounded in time: on expiry the kernel records an error, every role
+// stops at its next wait, the MMA threads wait once more for the MMAs they committed, the copies in
+// flight are waited for and the TMEM is released.
 
 constexpr int UM_TX = 16, UM_TY = 16;              // column tile: two 8 x 16 patches
 constexpr int UM_HX = UM_TX + 2, UM_HY = UM_TY + 2;
-constexpr int UM_SLOTS = 6;                        // ring of staged planes: zc-1..zc+1 read, later ones in flight
+constexpr int UM_SLOTS = 6;                        // ring of staged input planes
+// planes are reported staged one epilogue iteration after their copies are issued, and output
+// plane z0 + 1 needs input plane z0 + 2 before the first such report: the prologue's planes
+// z0 - 1 .. z0 + 2 must fit the ring
+static_assert(UM_SLOTS >= 4, "staging ring too short: the pipeline would wait on itself");
+// ring of output-plane accumulators per patch (TMEM): 8 planes, or 4 where the block's shared
+// memory lets two blocks share an SM (CB = 1), so that two blocks' allocations fit the 512 columns
+template <int CB>
+__host__ __device__ constexpr int um_acc() { return CB == 1 ? 4 : 8; }
 // Bounds of the mbarrier waits, in nanoseconds of %globaltimer: a plane's MMAs take about a
 // microsecond, so a wait still open after 20 ms has failed; the test hook's wait gives up after
 // 20 us.  Time bounds, unlike poll counts, do not depend on how long each poll suspends.
@@ -395,11 +420,10 @@ __device__ __forceinline__ void um_load_plane(uint8_t *slot, const __nv_bfloat16
 }
 
 // z[n][o] = bias[o] + sum_{k, i} W[o][i][k] in[n + off_k][i], CO = MT * 16 output channels (padded),
-// CB * 16 input channels (padded); wpack: [27][CB][2][CO][8] BF16 (pack_weights_umma_kernel).
+// CB * 16 input channels (padded); wpack: [9][CB][2][3 CO][8] BF16 (pack_weights_umma_kernel).
 // z is written when keep_z != 0 or act is null; act (not null): the next layer's input silu(z).
 constexpr int UM_EPI_WARPS = 8;                          // load and epilogue warps
-constexpr int UM_MMA_WARPS = 4;                          // MMA warps: one per patch and half of the offsets
-constexpr int UM_KSPLIT = 14;                            // offsets 0..13 and 14..26 accumulate separately
+constexpr int UM_MMA_WARPS = 2;                          // MMA warps: one per patch
 constexpr int UM_THREADS = 32 * (UM_EPI_WARPS + UM_MMA_WARPS);
 constexpr int UM_EPI_THREADS = 32 * UM_EPI_WARPS;
 
@@ -411,16 +435,18 @@ __global__ void __launch_bounds__(UM_THREADS, 1) conv_umma_kernel(int nx, int ny
                                                            int *__restrict__ err, int stall, int keep_z)
 {
     constexpr int CO = MT * 16;
-    constexpr int WBYTES = 27 * CB * 2 * CO * 16;
+    constexpr int ROWS = 3 * CO;                       // B rows (jb, o)
+    constexpr int WBYTES = 9 * CB * 2 * ROWS * 16;
     constexpr int PB = UmGeom<CB>::PLANE_BYTES;
     constexpr int CG = UmGeom<CB>::CG;
-    // 2 buffers x 2 halves of the offsets x 2 patches, CO columns each
-    constexpr uint32_t TCOLS = 8 * CO < 32 ? 32 : (8 * CO <= 64 ? 64 : (8 * CO <= 128 ? 128 : 256));
+    constexpr int UM_ACC = um_acc<CB>();
+    constexpr uint32_t TCOLS = 2 * UM_ACC * CO;        // 2 patches x UM_ACC planes x CO columns
+    static_assert(TCOLS == 256 || TCOLS == 512, "TMEM allocation is a power of two");
     extern __shared__ __align__(1024) uint8_t usm[];
-    __shared__ __align__(8) uint64_t bar_full[UM_SLOTS];     // a plane is staged in the slot
+    __shared__ __align__(8) uint64_t bar_full[UM_SLOTS];     // an input plane is staged in the slot
     __shared__ __align__(8) uint64_t bar_empty[UM_SLOTS];    // the MMAs reading the slot are done
-    __shared__ __align__(8) uint64_t bar_acc[2];             // the accumulator buffer holds a finished plane
-    __shared__ __align__(8) uint64_t bar_drained[2];         // the accumulator buffer has been read back
+    __shared__ __align__(8) uint64_t bar_acc[UM_ACC];        // the accumulator slot holds a finished plane
+    __shared__ __align__(8) uint64_t bar_drained[UM_ACC];    // the accumulator slot has been read back
     __shared__ __align__(8) uint64_t bar_fin;                // every MMA this block committed is done
     __shared__ uint32_t tmem_base;
     __shared__ int abort_flag;
@@ -431,40 +457,42 @@ __global__ void __launch_bounds__(UM_THREADS, 1) conv_umma_kernel(int nx, int ny
     const int ntx = nx / UM_TX;
     const int x0 = (blockIdx.x % ntx) * UM_TX, y0 = (blockIdx.x / ntx) * UM_TY;
     const int z0 = blockIdx.y * zlen, z1 = min(nz, z0 + zlen);
+    pdl_trigger();          // the next kernel may be scheduled; it waits for this one before its loads
     if (z0 >= nz) return;   // whole block
     volatile int *abort_v = &abort_flag;
 
-    // planes z0 - 1 .. z1 take slots in turn: slot and fill number of plane p
+    // input planes z0 - 1 .. z1 take the staging slots in turn: slot and fill number of plane p
     auto slot_of = [&](int p) { return (p - (z0 - 1)) % UM_SLOTS; };
     auto fill_of = [&](int p) { return (p - (z0 - 1)) / UM_SLOTS; };
     auto slot = [&](int p) { return ring + (size_t)slot_of(p) * PB; };
+    // output planes z0 .. z1 - 1 take the accumulator slots in turn: slot and use number of plane q
+    auto aslot = [&](int q) { return (q - z0) % UM_ACC; };
+    auto ause = [&](int q) { return (q - z0) / UM_ACC; };
     // the 16-byte chunks this epilogue thread stages in every plane: element offsets within a plane
-    // of the input (wrapped once here; -1 past the end)
+    // of the input (wrapped once here; -1 past the end) and byte offsets within the slot.  Chunk
+    // e = node * CG + cg, the channel group fastest, so that a warp copies the 8 x 64 contiguous
+    // bytes of 8 x-consecutive nodes (4 lines per instruction, not 32) and writes the 8 nodes x 4
+    // groups to every shared-memory bank exactly 4 times (the groups are HY * HX * 16 bytes apart,
+    // 16 banks mod 32)
     constexpr int NCHUNK = CG * UM_HY * UM_HX;
     constexpr int PER = (NCHUNK + UM_EPI_THREADS - 1) / UM_EPI_THREADS;
-    int soff[PER];
+    int soff[PER], doff[PER];
 #pragma unroll
     for (int j = 0; j < PER; ++j) {
         const int e = tid + j * UM_EPI_THREADS;
-        const int node = e % (UM_HY * UM_HX), cg = e / (UM_HY * UM_HX);
+        const int node = e / CG, cg = e - node * CG;
         const int hy = node / UM_HX, hx = node - hy * UM_HX;
-        soff[j] = e < NCHUNK && tid < UM_EPI_THREADS
-                      ? (mwrap(y0 - 1 + hy, ny) * nx + mwrap(x0 - 1 + hx, nx)) * (CB * 16) + cg * 8
-                      : -1;
+        const bool mine = e < NCHUNK && tid < UM_EPI_THREADS;
+        soff[j] = mine ? (mwrap(y0 - 1 + hy, ny) * nx + mwrap(x0 - 1 + hx, nx)) * (CB * 16) + cg * 8 : -1;
+        doff[j] = (cg * UM_HY * UM_HX + node) * 16;
     }
     auto stage = [&](int p) {   // cp.async copies of plane p by the epilogue threads (one group)
         const __nv_bfloat16 *src = in + (size_t)mwrap(p, nz) * nx * ny * (CB * 16);
-        uint8_t *dst = slot(p) + (size_t)tid * 16;
+        uint8_t *dst = slot(p);
 #pragma unroll
         for (int j = 0; j < PER; ++j)
-            if (soff[j] >= 0) cp_async16(dst + (size_t)j * UM_EPI_THREADS * 16, src + soff[j]);
+            if (soff[j] >= 0) cp_async16(dst + doff[j], src + soff[j]);
         cp_async_commit();
-    };
-    // the staged copies are complete: make them visible to the tensor core (async proxy), report
-    auto report_full = [&](int p) {
-        cp_async_wait_all();
-        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-        mbar_arrive(&bar_full[slot_of(p)]);
     };
 
     if (tid == 0) {
@@ -473,9 +501,9 @@ __global__ void __launch_bounds__(UM_THREADS, 1) conv_umma_kernel(int nx, int ny
             mbar_init(&bar_full[q], UM_EPI_THREADS);
             mbar_init(&bar_empty[q], UM_MMA_WARPS);
         }
-        for (int b = 0; b < 2; ++b) {
-            mbar_init(&bar_acc[b], UM_MMA_WARPS);
-            mbar_init(&bar_drained[b], UM_EPI_WARPS);
+        for (int q = 0; q < UM_ACC; ++q) {
+            mbar_init(&bar_acc[q], UM_MMA_WARPS);
+            mbar_init(&bar_drained[q], UM_EPI_WARPS);
         }
         mbar_init(&bar_fin, UM_MMA_WARPS);
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
@@ -485,50 +513,61 @@ __global__ void __launch_bounds__(UM_THREADS, 1) conv_umma_kernel(int nx, int ny
                      "r"(TCOLS));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
     }
-    __syncthreads();   // barriers initialised before any arrival
-
-    // prologue (epilogue threads): weights, bias and the first UM_SLOTS planes
-    const int npro = min(UM_SLOTS, z1 - (z0 - 1) + 1);
-    if (tid < UM_EPI_THREADS) {
-        for (int i = tid; i < WBYTES / 16; i += UM_EPI_THREADS) cp_async16(sw + (size_t)i * 16, wpack + (size_t)i * 8);
-        if (tid < CO) sbias[tid] = bias ? bias[tid] : 0.0f;
-        for (int j = 0; j < npro; ++j) stage(z0 - 1 + j);
-        cp_async_wait_all();
-        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-        for (int j = 0; j < npro; ++j) mbar_arrive(&bar_full[slot_of(z0 - 1 + j)]);
-    }
     asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
-    __syncthreads();   // weights, bias and TMEM address visible to every role
+    __syncthreads();   // barriers initialised and the TMEM address visible before any other step
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
     const uint32_t tmem = tmem_base;
 
+    // prologue (epilogue threads): the weights and bias (written before the previous kernel of the
+    // stream, so they are read before waiting for it), then the first UM_SLOTS input planes (that
+    // kernel's output).  Group 0 holds the weights and plane z0 - 1, group j plane z0 - 1 + j; a
+    // plane is reported full as soon as its group has landed, with the next one already in flight,
+    // so the MMAs start after the first group rather than after the whole prologue.
+    const int npro = min(UM_SLOTS, z1 - z0 + 2);
+    if (tid < UM_EPI_THREADS) {
+        for (int i = tid; i < WBYTES / 16; i += UM_EPI_THREADS) cp_async16(sw + (size_t)i * 16, wpack + (size_t)i * 8);
+        if (tid < CO) sbias[tid] = bias ? bias[tid] : 0.0f;
+        pdl_wait();
+        stage(z0 - 1);
+        for (int j = 1; j <= npro; ++j) {
+            if (j < npro) {
+                stage(z0 - 1 + j);
+                cp_async_wait_but_last();
+            } else {
+                cp_async_wait_all();
+            }
+            asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+            mbar_arrive(&bar_full[slot_of(z0 - 2 + j)]);
+        }
+        asm volatile("bar.sync 1, %0;\n" ::"n"(UM_EPI_THREADS) : "memory");   // sbias visible to the epilogue
+    }
+
     if (warp >= UM_EPI_WARPS) {
-        // ---- MMA warps: warp UM_EPI_WARPS + 2 hk + pt issues the MMAs of patch pt over half hk of
-        // the offsets (k in [0, UM_KSPLIT) or [UM_KSPLIT, 27)) into its own accumulator -----------
-        const int pt = (warp - UM_EPI_WARPS) & 1, hk = (warp - UM_EPI_WARPS) >> 1;
-        const int kbeg = hk ? UM_KSPLIT : 0, kend = hk ? 27 : UM_KSPLIT;
-        const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(CO >> 3) << 17) | ((128u >> 4) << 24);
+        // ---- MMA warps: warp UM_EPI_WARPS + pt issues the MMAs of patch pt ---------------------
+        const int pt = warp - UM_EPI_WARPS;
+        // instruction descriptor: FP32 accumulator, BF16 A and B, both K-major, M = 128, N = nb CO
+        const uint32_t idesc0 = (1u << 4) | (1u << 7) | (1u << 10) | ((128u >> 4) << 24);
+        auto idesc = [&](int nb) { return idesc0 | ((uint32_t)((nb * CO) >> 3) << 17); };
         const uint32_t lbo_a = UM_HY * UM_HX * 16, sbo_a = UM_HX * 16;
-        const uint32_t lbo_b = CO * 16, sbo_b = 128;
-        const uint32_t sw_addr = smem_addr(sw);
+        const uint32_t lbo_b = ROWS * 16, sbo_b = 128;
+        const uint64_t bdesc = umma_desc(smem_addr(sw), lbo_b, sbo_b);
         const uint32_t a_hi = (uint32_t)(umma_desc(0, lbo_a, sbo_a) >> 32);
-        const uint32_t b_lo = (uint32_t)umma_desc(sw_addr, lbo_b, sbo_b), b_hi = (uint32_t)(umma_desc(sw_addr, lbo_b, sbo_b) >> 32);
+        const uint32_t b_lo = (uint32_t)bdesc, b_hi = (uint32_t)(bdesc >> 32);
+        const uint32_t tpatch = tmem + (uint32_t)(pt * UM_ACC * CO);   // this patch's accumulator ring
         bool ok = true;
         if (stall) {   // test hook: wait (briefly) on a barrier nothing is committed to, before any MMA
             ok = __all_sync(0xffffffffu, mbar_wait(smem_addr(&bar_fin), 0u, UM_TEST_WAIT_NS));
             if (!ok && lane == 0) abort_flag = 1;
             ok = false;
         }
-        for (int zc = z0; zc < z1 && ok; ++zc) {
-            const int b = (zc - z0) & 1;
-            // planes zc-1, zc, zc+1 staged, and buffer b read back (plane zc - 2)
-            bool good = true;
-#pragma unroll
-            for (int d = -1; d <= 1; ++d)
-                good = good && mbar_wait(smem_addr(&bar_full[slot_of(zc + d)]), (uint32_t)(fill_of(zc + d) & 1),
-                                         UM_WAIT_NS, abort_v);
-            if (good && zc - z0 >= 2)
-                good = mbar_wait(smem_addr(&bar_drained[b]), (uint32_t)(((zc - z0) / 2 - 1) & 1), UM_WAIT_NS, abort_v);
+        for (int zi = z0 - 1; zi <= z1 && ok; ++zi) {
+            // column blocks lo..hi of this input plane land in output planes zi - 1 + jb of the chunk
+            const int lo = max(0, z0 - zi + 1), hi = min(2, z1 - zi);
+            bool good = mbar_wait(smem_addr(&bar_full[slot_of(zi)]), (uint32_t)(fill_of(zi) & 1), UM_WAIT_NS, abort_v);
+            // block 2 opens output plane zi + 1: the plane before it in that slot must be read back
+            if (good && hi == 2 && zi + 1 - z0 >= UM_ACC)
+                good = mbar_wait(smem_addr(&bar_drained[aslot(zi + 1)]), (uint32_t)((ause(zi + 1) - 1) & 1),
+                                 UM_WAIT_NS, abort_v);
             good = __all_sync(0xffffffffu, good);
             if (!good) {
                 if (lane == 0) abort_flag = 1;
@@ -536,25 +575,37 @@ __global__ void __launch_bounds__(UM_THREADS, 1) conv_umma_kernel(int nx, int ny
             }
             asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
             if (lane == 0) {
-                const uint32_t a_lo[3] = {(uint32_t)umma_desc(smem_addr(slot(zc - 1)), lbo_a, sbo_a),
-                                          (uint32_t)umma_desc(smem_addr(slot(zc)), lbo_a, sbo_a),
-                                          (uint32_t)umma_desc(smem_addr(slot(zc + 1)), lbo_a, sbo_a)};
-                const uint32_t dt = tmem + (uint32_t)(((b * 2 + hk) * 2 + pt) * CO);
+                const uint32_t a_lo = (uint32_t)umma_desc(smem_addr(slot(zi)), lbo_a, sbo_a);
+                // blocks lo..hi split where the ring of accumulator slots wraps: segments [b0, b1]
+                // starting at accumulator slot sa
+                const int s_lo = aslot(zi - 1 + lo);
+                const int n1 = min(hi - lo + 1, UM_ACC - s_lo);
+                const int seg_b0[2] = {lo, lo + n1}, seg_b1[2] = {lo + n1 - 1, hi}, seg_sa[2] = {s_lo, 0};
+                const int nseg = lo + n1 <= hi ? 2 : 1;
 #pragma unroll
-                for (int k = 0; k < 27; ++k) {
-                    if (k < kbeg || k >= kend) continue;
-                    const int dz = k / 9 - 1, dy = (k / 3) % 3 - 1, dx = k % 3 - 1;
-                    const uint32_t aoff = (uint32_t)((1 + dy) * UM_HX + pt * 8 + 1 + dx);   // 16-byte units
-#pragma unroll
-                    for (int cb = 0; cb < CB; ++cb) {
-                        const uint64_t da = ((uint64_t)a_hi << 32) | (a_lo[dz + 1] + aoff + (uint32_t)(2 * cb) * (lbo_a >> 4));
-                        const uint64_t db =
-                            ((uint64_t)b_hi << 32) | (b_lo + (uint32_t)((k * CB + cb) * 2 * CO));   // 16-byte units
-                        umma_bf16(dt, da, db, idesc, (k != kbeg || cb != 0) ? 1u : 0u);
+                for (int j = 0; j < 9 * CB; ++j) {   // j = (in-plane offset) * CB + channel chunk
+                    const int j9 = j / CB, cb = j % CB;
+                    const int dy = j9 / 3 - 1, dx = j9 % 3 - 1;
+                    const uint32_t aoff = (uint32_t)((1 + dy) * UM_HX + pt * 8 + 1 + dx) +
+                                          (uint32_t)(2 * cb) * (lbo_a >> 4);   // 16-byte units
+                    const uint64_t da = ((uint64_t)a_hi << 32) | (a_lo + aoff);
+                    const uint32_t bj = b_lo + (uint32_t)(j * 2 * ROWS);          // 16-byte units
+                    for (int sg = 0; sg < nseg; ++sg) {
+                        const int b0 = seg_b0[sg], b1 = seg_b1[sg];
+                        const uint32_t dcol = tpatch + (uint32_t)(seg_sa[sg] * CO);
+                        if (j == 0 && b1 == 2) {   // plane zi + 1's first write: accumulation off for block 2
+                            if (b0 < 2)
+                                umma_bf16(dcol, da, ((uint64_t)b_hi << 32) | (bj + (uint32_t)(b0 * CO)), idesc(2 - b0), 1u);
+                            umma_bf16(dcol + (uint32_t)((2 - b0) * CO), da, ((uint64_t)b_hi << 32) | (bj + 2u * CO),
+                                      idesc(1), 0u);
+                        } else {
+                            umma_bf16(dcol, da, ((uint64_t)b_hi << 32) | (bj + (uint32_t)(b0 * CO)), idesc(b1 - b0 + 1),
+                                      1u);
+                        }
                     }
                 }
-                umma_commit(&bar_acc[b]);                 // the plane's accumulators are complete
-                umma_commit(&bar_empty[slot_of(zc - 1)]);   // plane zc-1: no later MMA reads it
+                umma_commit(&bar_empty[slot_of(zi)]);                 // no later MMA reads input plane zi
+                if (zi - 1 >= z0) umma_commit(&bar_acc[aslot(zi - 1)]);   // output plane zi - 1 is complete
             }
             __syncwarp();
         }
@@ -572,52 +623,49 @@ __global__ void __launch_bounds__(UM_THREADS, 1) conv_umma_kernel(int nx, int ny
         float bv[CH];                                  // this warp's half of the bias, in registers
 #pragma unroll
         for (int o = 0; o < CH; ++o) bv[o] = sbias[h * CH + o];
-        int pending = INT_MIN;                         // plane staged last iteration, not yet reported
-        for (int zc = z0; zc < z1; ++zc) {
-            const int b = (zc - z0) & 1;
-            const bool good = __all_sync(0xffffffffu, mbar_wait(smem_addr(&bar_acc[b]),
-                                                                (uint32_t)(((zc - z0) / 2) & 1), UM_WAIT_NS, abort_v));
-            if (!good) {
+        int staged = z0 - 1 + npro;                    // next input plane to stage
+        int reported = staged;                         // planes reported .. staged - 1 are in flight
+        bool aborted = false;                          // this warp gave up at a wait
+        for (int p = z0; p < z1; ++p) {
+            const int sa = aslot(p);
+            aborted = !__all_sync(0xffffffffu, mbar_wait(smem_addr(&bar_acc[sa]), (uint32_t)(ause(p) & 1),
+                                                         UM_WAIT_NS, abort_v));
+            if (aborted) {
                 if (lane == 0) abort_flag = 1;
                 break;
             }
             asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-            // both halves of the offsets for both patches: r[hk][pt]
-            uint32_t r[2][2][CH];
+            uint32_t r[2][CH];
 #pragma unroll
-            for (int hk = 0; hk < 2; ++hk)
-#pragma unroll
-                for (int pt = 0; pt < 2; ++pt) {
-                    const uint32_t taddr =
-                        tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(((b * 2 + hk) * 2 + pt) * CO + h * CH);
-                    uint32_t(&rr)[CH] = r[hk][pt];
-                    if constexpr (CH == 16) {
-                        asm volatile(
-                            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
-                            "[%16];\n"
-                            : "=r"(rr[0]), "=r"(rr[1]), "=r"(rr[2]), "=r"(rr[3]), "=r"(rr[4]), "=r"(rr[5]), "=r"(rr[6]),
-                              "=r"(rr[7]), "=r"(rr[8]), "=r"(rr[9]), "=r"(rr[10]), "=r"(rr[11]), "=r"(rr[12]),
-                              "=r"(rr[13]), "=r"(rr[14]), "=r"(rr[15])
-                            : "r"(taddr));
-                    } else {
-                        asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];\n"
-                                     : "=r"(rr[0]), "=r"(rr[1]), "=r"(rr[2]), "=r"(rr[3]), "=r"(rr[4]), "=r"(rr[5]),
-                                       "=r"(rr[6]), "=r"(rr[7])
-                                     : "r"(taddr));
-                    }
+            for (int pt = 0; pt < 2; ++pt) {
+                const uint32_t taddr = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)((pt * UM_ACC + sa) * CO + h * CH);
+                uint32_t(&rr)[CH] = r[pt];
+                if constexpr (CH == 16) {
+                    asm volatile(
+                        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
+                        "[%16];\n"
+                        : "=r"(rr[0]), "=r"(rr[1]), "=r"(rr[2]), "=r"(rr[3]), "=r"(rr[4]), "=r"(rr[5]), "=r"(rr[6]),
+                          "=r"(rr[7]), "=r"(rr[8]), "=r"(rr[9]), "=r"(rr[10]), "=r"(rr[11]), "=r"(rr[12]),
+                          "=r"(rr[13]), "=r"(rr[14]), "=r"(rr[15])
+                        : "r"(taddr));
+                } else {
+                    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];\n"
+                                 : "=r"(rr[0]), "=r"(rr[1]), "=r"(rr[2]), "=r"(rr[3]), "=r"(rr[4]), "=r"(rr[5]),
+                                   "=r"(rr[6]), "=r"(rr[7])
+                                 : "r"(taddr));
                 }
+            }
             asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
             asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
             __syncwarp();
-            if (lane == 0) mbar_arrive(&bar_drained[b]);   // the MMA warp may reuse buffer b
+            if (lane == 0) mbar_arrive(&bar_drained[sa]);   // the MMA warps may reuse the slot
             if (yy < ny) {
 #pragma unroll
                 for (int pt = 0; pt < 2; ++pt) {
-                    const size_t node = ((size_t)zc * ny + yy) * nx + x0 + pt * 8 + (mrow % 8);
+                    const size_t node = ((size_t)p * ny + yy) * nx + x0 + pt * 8 + (mrow % 8);
                     float v[CH];
 #pragma unroll
-                    for (int o = 0; o < CH; ++o)
-                        v[o] = (__uint_as_float(r[0][pt][o]) + __uint_as_float(r[1][pt][o])) + bv[o];
+                    for (int o = 0; o < CH; ++o) v[o] = __uint_as_float(r[pt][o]) + bv[o];
                     if (keep_z || !act) {
                         float4 *dst = reinterpret_cast<float4 *>(z + node * CO + h * CH);
 #pragma unroll
@@ -634,25 +682,31 @@ __global__ void __launch_bounds__(UM_THREADS, 1) conv_umma_kernel(int nx, int ny
                     }
                 }
             }
-            // staging: report the plane staged last iteration, then stage plane zc + 5 into the
-            // slot plane zc - 1 frees once the MMAs of plane zc are done (they are: bar_acc)
-            if (pending != INT_MIN) {
-                report_full(pending);
-                pending = INT_MIN;
+            // staging: report the planes staged last iteration (their copies had this iteration's
+            // stores to land), then, output plane p being done, input planes up to p + 1 have been
+            // consumed and their slots take input planes up to p + 1 + UM_SLOTS
+            if (reported < staged) {
+                cp_async_wait_all();
+                asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+                for (; reported < staged; ++reported) mbar_arrive(&bar_full[slot_of(reported)]);
             }
-            const int p = zc + UM_SLOTS - 1;
-            if (p <= z1) {
-                const bool free = __all_sync(0xffffffffu, mbar_wait(smem_addr(&bar_empty[slot_of(p)]),
-                                                                    (uint32_t)((fill_of(p) - 1) & 1), UM_WAIT_NS, abort_v));
-                if (!free) {
-                    if (lane == 0) abort_flag = 1;
-                    break;
-                }
-                stage(p);
-                pending = p;
+            while (staged <= z1 && staged <= p + 1 + UM_SLOTS) {
+                aborted = !__all_sync(0xffffffffu, mbar_wait(smem_addr(&bar_empty[slot_of(staged)]),
+                                                             (uint32_t)((fill_of(staged) - 1) & 1), UM_WAIT_NS, abort_v));
+                if (aborted) break;
+                stage(staged);
+                ++staged;
+            }
+            if (aborted) {
+                if (lane == 0) abort_flag = 1;
+                break;
             }
         }
-        if (pending != INT_MIN && !*abort_v) report_full(pending);
+        if (reported < staged && !aborted) {
+            cp_async_wait_all();
+            asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+            for (; reported < staged; ++reported) mbar_arrive(&bar_full[slot_of(reported)]);
+        }
         cp_async_wait_all();   // no copy of this block is still in flight when it returns
     }
     asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
@@ -661,17 +715,22 @@ __global__ void __launch_bounds__(UM_THREADS, 1) conv_umma_kernel(int nx, int ny
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(TCOLS));
 }
 
-// Weights for conv_umma_kernel: [27][CB][2][rows (CO)][8] BF16 with value(o, i, k) = W[o][i][k], or
-// for the input gradient (transpose) W[i][o][26 - k]; zero for padded rows or channels.
+// Weights for conv_umma_kernel: [9 in-plane offsets][CB][2][rows (jb, o): 3 CO][8] BF16.  Row
+// (jb, o) of in-plane offset j9 = 3 (dy + 1) + (dx + 1) holds the tap of z offset dz = 1 - jb,
+// k = 9 (2 - jb) + j9: value(o, i, k) = W[o][i][k], or for the input gradient (transpose)
+// W[i][o][26 - k]; zero for padded rows or channels.
 __global__ void pack_weights_umma_kernel(const float *__restrict__ W, int cout, int cin, int co_pad, int cb_count,
                                          bool transpose, __nv_bfloat16 *__restrict__ out)
 {
-    const int total = 27 * cb_count * 2 * co_pad * 8;
+    const int rows3 = 3 * co_pad;
+    const int total = 9 * cb_count * 2 * rows3 * 8;
     const int idx = blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= total) return;
-    const int e = idx % 8, o = (idx / 8) % co_pad, cg = (idx / (8 * co_pad)) % 2;
-    const int kc = idx / (16 * co_pad);
-    const int cb = kc % cb_count, k = kc / cb_count;
+    const int e = idx % 8, r = (idx / 8) % rows3, cg = (idx / (8 * rows3)) % 2;
+    const int jc = idx / (16 * rows3);
+    const int cb = jc % cb_count, j9 = jc / cb_count;
+    const int jb = r / co_pad, o = r % co_pad;
+    const int k = 9 * (2 - jb) + j9;
     const int i = cb * 16 + cg * 8 + e;
     const int rows = transpose ? cin : cout, cols = transpose ? cout : cin;
     float v = 0.0f;
@@ -937,8 +996,10 @@ __global__ void dw_reduce_kernel(const float *__restrict__ part, int nblk, int c
 }
 
 // db[o] += sum over a node chunk of dz[n][o]
+// Bias gradient in two deterministic passes (no atomics, so training is reproducible run to run):
+// block b sums chunk b of the nodes into part[b][32]; dbias_reduce_kernel adds the chunks in order.
 __global__ void __launch_bounds__(256) dbias_kernel(const float *__restrict__ dz, int cop, int cout, int N, int chunk,
-                                                    float *__restrict__ db)
+                                                    float *__restrict__ part)
 {
     __shared__ float red[8][33];
     const int c = threadIdx.x & 31, row = threadIdx.x >> 5;
@@ -951,7 +1012,25 @@ __global__ void __launch_bounds__(256) dbias_kernel(const float *__restrict__ dz
     if (row == 0 && c < cout) {
         float tot = 0.0f;
         for (int r = 0; r < 8; ++r) tot += red[r][c];
-        atomicAdd(&db[c], tot);
+        part[(size_t)blockIdx.x * 32 + c] = tot;
+    }
+}
+
+// one block of 256 threads: row r = threadIdx.x / 32 adds chunks r, r + 8, ... of channel
+// threadIdx.x % 32 in order, then row 0 adds the 8 rows in order (a fixed order: deterministic)
+__global__ void __launch_bounds__(256) dbias_reduce_kernel(const float *__restrict__ part, int nchunk, int cout,
+                                                           float *__restrict__ db)
+{
+    __shared__ float red[8][33];
+    const int c = threadIdx.x & 31, row = threadIdx.x >> 5;
+    float s = 0.0f;
+    for (int b = row; b < nchunk; b += 8) s += part[(size_t)b * 32 + c];
+    red[row][c] = s;
+    __syncthreads();
+    if (row == 0 && c < cout) {
+        float tot = 0.0f;
+        for (int r = 0; r < 8; ++r) tot += red[r][c];
+        db[c] += tot;
     }
 }
 
@@ -1014,7 +1093,7 @@ __device__ __forceinline__ float bounded_dphi(float raw, float ph)
 // (the momentum the velocity correction would add), out[5] += sum of rho
 __global__ void __launch_bounds__(256) corr_sums_kernel(const float *__restrict__ y, const float *__restrict__ phi,
                                                         lbm_closure_norm nrm, float rho_g, float drho, int N,
-                                                        double *__restrict__ out)
+                                                        double *__restrict__ part)
 {
     __shared__ double red[6][256];
     double s[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
@@ -1037,7 +1116,19 @@ __global__ void __launch_bounds__(256) corr_sums_kernel(const float *__restrict_
             for (int q = 0; q < 6; ++q) red[q][threadIdx.x] += red[q][threadIdx.x + w];
         __syncthreads();
     }
-    if (threadIdx.x < 6) atomicAdd(out + threadIdx.x, red[threadIdx.x][0]);
+    if (threadIdx.x < 6) part[(size_t)blockIdx.x * 6 + threadIdx.x] = red[threadIdx.x][0];
+}
+
+// the six sums of corr_sums_kernel from its blocks' records, in a fixed order (deterministic):
+// warp q takes sum q, lane l adds records l, l + 32, ... in order, then a fixed shuffle tree
+__global__ void __launch_bounds__(192) corr_final_kernel(const double *__restrict__ part, int nblocks,
+                                                         double *__restrict__ out)
+{
+    const int q = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    double s = 0.0;
+    for (int b = lane; b < nblocks; b += 32) s += part[(size_t)b * 6 + q];
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
+    if (lane == 0) out[q] = s;
 }
 
 // Apply the network's correction y [4][N] to a one-box FP32 state.  phi: dphi = d - w c with d
@@ -1135,6 +1226,7 @@ struct lbm_cnn {
     __nv_bfloat16 *wut[tslb::NLAYER] = {};  // ... and of the transposed weights (layers 2..4)
     float *bpad = nullptr;               // biases zero-padded to 32 channels per layer (repack)
     float *dwpart = nullptr;             // per-block partial sums of the weight gradient
+    float *dbpart = nullptr;             // per-chunk partial sums of the bias gradient [chunks][32]
     int test_expire = 0;                 // test hook: tensor-core waits expire (lbm_cnn_test_expire_wait)
     int *derr = nullptr;                 // set by a tensor-core kernel whose mbarrier wait expired
     __nv_bfloat16 *a[tslb::NLAYER] = {}; // layer inputs, channel-last BF16: a[0] [N][16], a[1..3] [N][32]
@@ -1199,6 +1291,7 @@ void free_cnn(lbm_cnn *c)
     cudaFree(c->derr);
     cudaFree(c->bpad);
     cudaFree(c->dwpart);
+    cudaFree(c->dbpart);
     if (c->h_sum) cudaFreeHost(c->h_sum);
     delete c;
 }
@@ -1283,7 +1376,7 @@ cudaError_t launch_conv(lbm_cnn *c, int layer, bool transpose, const __nv_bfloat
     const uint4 *wfrag = transpose ? c->wt[layer] : c->wf[layer];
     const __nv_bfloat16 *wpack = transpose ? c->wut[layer] : c->wu[layer];
     if (c->conv_kernel == 0 && c->nx % tslb::UM_TX == 0) {   // tcgen05 / TMEM
-        constexpr int WB = 27 * CB * 2 * MT * 16 * 16;
+        constexpr int WB = 9 * CB * 2 * 3 * MT * 16 * 16;
         const size_t smem = (size_t)((WB + 1023) / 1024) * 1024 + (size_t)tslb::UM_SLOTS * tslb::UmGeom<CB>::PLANE_BYTES;
         static bool attr = false;
         if (!attr) {
@@ -1298,9 +1391,13 @@ cudaError_t launch_conv(lbm_cnn *c, int layer, bool transpose, const __nv_bfloat
         if (nzc > c->nz) nzc = c->nz;
         const int zlen = (c->nz + nzc - 1) / nzc;
         nzc = (c->nz + zlen - 1) / zlen;
-        tslb::conv_umma_kernel<MT, CB><<<dim3(tiles, nzc), tslb::UM_THREADS, smem, c->stream>>>(
-            c->nx, c->ny, c->nz, wpack, in, bias, out, act, zlen, c->derr, c->test_expire, keep_z ? 1 : 0);
-        return cudaGetLastError();
+        // programmatic dependent launch: the kernel sets up and loads its weights and bias while the
+        // previous kernel drains, and waits for it before reading its input.  So no kernel that
+        // writes packed weights or biases may directly precede a convolution on the stream (repack
+        // is always followed by pack_input_kernel or another ordinary launch).
+        return tslb::launch_pdl(tslb::conv_umma_kernel<MT, CB>, dim3(tiles, nzc), dim3(tslb::UM_THREADS), smem, c->stream,
+                                c->nx, c->ny, c->nz, wpack, in, bias, out, act, zlen, c->derr, c->test_expire,
+                                keep_z ? 1 : 0);
     }
     cudaError_t e = launch_conv_mma<MT, CB>(c, wfrag, in, bias, out);
     if (e == cudaSuccess && act) {
@@ -1369,7 +1466,7 @@ cudaError_t launch_dweight(lbm_cnn *c, int layer, float *dW)
 cudaError_t backward(lbm_cnn *c)
 {
     const int N = c->N;
-    const int chunk = 4096;
+    const int chunk = tslb::kBiasChunk;
     const int nchunk = (N + chunk - 1) / chunk;
     cudaError_t e;
     // dz of the last layer is in dz / dzb with 16 channels (written by the loss kernel)
@@ -1381,7 +1478,8 @@ cudaError_t backward(lbm_cnn *c)
             : l == 3 ? launch_dweight<1, 2>(c, l, dW)
                      : launch_dweight<2, 2>(c, l, dW);
         if (e != cudaSuccess) return e;
-        tslb::dbias_kernel<<<nchunk, 256, 0, c->stream>>>(c->dz[l], cop, tslb::COUT[l], N, chunk, db);
+        tslb::dbias_kernel<<<nchunk, 256, 0, c->stream>>>(c->dz[l], cop, tslb::COUT[l], N, chunk, c->dbpart);
+        tslb::dbias_reduce_kernel<<<1, 256, 0, c->stream>>>(c->dbpart, nchunk, tslb::COUT[l], db);
         if (l == 0) break;
         // da_{l-1}[n][i] = sum_{k,o} W_l[o][i][k] dz_l[n - off_k][o]
         e = l == 3 ? launch_conv<2, 1>(c, l, true, c->dzb, nullptr, c->da)
@@ -1457,7 +1555,9 @@ lbm_status lbm_cnn_create(int nx, int ny, int nz, unsigned long long seed, void 
         {(void **)&c->da, N * 32 * sizeof(float)},
         {(void **)&c->dzb, N * 32 * 2},                {(void **)&c->xbuf, 5 * N * sizeof(float)},
         {(void **)&c->ybuf, 4 * N * sizeof(float)},
-        {(void **)&c->dsum, (size_t)(c->loss_blocks + 8) * sizeof(double)},
+        // loss partials, or the correction's 6 sums then its blocks' records at offset 8
+        {(void **)&c->dsum, (size_t)(std::max(c->loss_blocks, tslb::kCorrBlocks * 6) + 8) * sizeof(double)},
+        {(void **)&c->dbpart, (size_t)((N + tslb::kBiasChunk - 1) / tslb::kBiasChunk) * 32 * sizeof(float)},
         {(void **)&c->bpad, (size_t)tslb::NLAYER * 32 * sizeof(float)},
     };
     cudaError_t err = cudaSuccess;
@@ -1704,8 +1804,9 @@ lbm_status lbm_closure_apply(lbm_ctx *ctx, lbm_cnn *cnn, const lbm_closure_norm 
     CNN_TRY(cudaGetLastError());
     CNN_TRY(forward(cnn, cnn->xbuf, false));
     tslb::unpack_output_kernel<<<(N + 255) / 256, 256, 0, v.stream>>>(cnn->z[3], N, cnn->ybuf);
-    CNN_TRY(cudaMemsetAsync(cnn->dsum, 0, 6 * sizeof(double), v.stream));
-    tslb::corr_sums_kernel<<<296, 256, 0, v.stream>>>(cnn->ybuf, v.phi, *norm, v.P.rho_g, v.P.drho, N, cnn->dsum);
+    tslb::corr_sums_kernel<<<tslb::kCorrBlocks, 256, 0, v.stream>>>(cnn->ybuf, v.phi, *norm, v.P.rho_g, v.P.drho, N,
+                                                                     cnn->dsum + 8);
+    tslb::corr_final_kernel<<<1, 192, 0, v.stream>>>(cnn->dsum + 8, tslb::kCorrBlocks, cnn->dsum);
     tslb::correct_kernel<<<(N + 255) / 256, 256, 0, v.stream>>>(v.G, cnn->ybuf, *norm, cnn->dsum, v.g, v.phi, v.u);
     CNN_TRY(cudaGetLastError());
     tslb::ctx_state_changed(ctx);
