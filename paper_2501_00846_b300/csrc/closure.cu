@@ -427,7 +427,7 @@ constexpr int UM_MMA_WARPS = 2;                          // MMA warps: one per p
 constexpr int UM_THREADS = 32 * (UM_EPI_WARPS + UM_MMA_WARPS);
 constexpr int UM_EPI_THREADS = 32 * UM_EPI_WARPS;
 
-template <int MT, int CB>
+template <int MT, int CB, bool XF>
 __global__ void __launch_bounds__(UM_THREADS, 1) conv_umma_kernel(int nx, int ny, int nz, const __nv_bfloat16 *__restrict__ wpack,
                                                            const __nv_bfloat16 *__restrict__ in,
                                                            const float *__restrict__ bias, float *__restrict__ z,
@@ -436,7 +436,11 @@ __global__ void __launch_bounds__(UM_THREADS, 1) conv_umma_kernel(int nx, int ny
 {
     constexpr int CO = MT * 16;
     constexpr int ROWS = 3 * CO;                       // B rows (jb, o)
-    constexpr int WBYTES = 9 * CB * 2 * ROWS * 16;
+    // in-plane taps per plane: 9 (dx, dy), or 3 (dy) when the input carries its x neighbours in
+    // its channels (XF: the first layer's folded input, pack_input_kernel)
+    constexpr int JT = XF ? 3 : 9;
+    static_assert(!XF || CB == 1, "the folded input has one 16-channel chunk");
+    constexpr int WBYTES = JT * CB * 2 * ROWS * 16;
     constexpr int PB = UmGeom<CB>::PLANE_BYTES;
     constexpr int CG = UmGeom<CB>::CG;
     constexpr int UM_ACC = um_acc<CB>();
@@ -583,9 +587,9 @@ __global__ void __launch_bounds__(UM_THREADS, 1) conv_umma_kernel(int nx, int ny
                 const int seg_b0[2] = {lo, lo + n1}, seg_b1[2] = {lo + n1 - 1, hi}, seg_sa[2] = {s_lo, 0};
                 const int nseg = lo + n1 <= hi ? 2 : 1;
 #pragma unroll
-                for (int j = 0; j < 9 * CB; ++j) {   // j = (in-plane offset) * CB + channel chunk
+                for (int j = 0; j < JT * CB; ++j) {   // j = (in-plane offset) * CB + channel chunk
                     const int j9 = j / CB, cb = j % CB;
-                    const int dy = j9 / 3 - 1, dx = j9 % 3 - 1;
+                    const int dy = XF ? j9 - 1 : j9 / 3 - 1, dx = XF ? 0 : j9 % 3 - 1;
                     const uint32_t aoff = (uint32_t)((1 + dy) * UM_HX + pt * 8 + 1 + dx) +
                                           (uint32_t)(2 * cb) * (lbo_a >> 4);   // 16-byte units
                     const uint64_t da = ((uint64_t)a_hi << 32) | (a_lo + aoff);
@@ -718,23 +722,30 @@ __global__ void __launch_bounds__(UM_THREADS, 1) conv_umma_kernel(int nx, int ny
 // Weights for conv_umma_kernel: [9 in-plane offsets][CB][2][rows (jb, o): 3 CO][8] BF16.  Row
 // (jb, o) of in-plane offset j9 = 3 (dy + 1) + (dx + 1) holds the tap of z offset dz = 1 - jb,
 // k = 9 (2 - jb) + j9: value(o, i, k) = W[o][i][k], or for the input gradient (transpose)
-// W[i][o][26 - k]; zero for padded rows or channels.
+// W[i][o][26 - k]; zero for padded rows or channels.  xfold (the first layer, forward): 3 in-plane
+// offsets j9 = dy + 1, channel i = 5 dx' + c of the folded input holding tap k = 9 (2 - jb) + 3 j9
+// + dx' of channel c (dx' = dx + 1), channel 15 zero.
 __global__ void pack_weights_umma_kernel(const float *__restrict__ W, int cout, int cin, int co_pad, int cb_count,
-                                         bool transpose, __nv_bfloat16 *__restrict__ out)
+                                         bool transpose, bool xfold, __nv_bfloat16 *__restrict__ out)
 {
     const int rows3 = 3 * co_pad;
-    const int total = 9 * cb_count * 2 * rows3 * 8;
+    const int total = (xfold ? 3 : 9) * cb_count * 2 * rows3 * 8;
     const int idx = blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= total) return;
     const int e = idx % 8, r = (idx / 8) % rows3, cg = (idx / (8 * rows3)) % 2;
     const int jc = idx / (16 * rows3);
     const int cb = jc % cb_count, j9 = jc / cb_count;
     const int jb = r / co_pad, o = r % co_pad;
-    const int k = 9 * (2 - jb) + j9;
     const int i = cb * 16 + cg * 8 + e;
-    const int rows = transpose ? cin : cout, cols = transpose ? cout : cin;
     float v = 0.0f;
-    if (o < rows && i < cols) v = transpose ? W[((size_t)i * cin + o) * 27 + (26 - k)] : W[((size_t)o * cin + i) * 27 + k];
+    if (xfold) {
+        if (o < cout && i < 15) v = W[((size_t)o * cin + i % 5) * 27 + 9 * (2 - jb) + 3 * j9 + i / 5];
+    } else {
+        const int k = 9 * (2 - jb) + j9;
+        const int rows = transpose ? cin : cout, cols = transpose ? cout : cin;
+        if (o < rows && i < cols)
+            v = transpose ? W[((size_t)i * cin + o) * 27 + (26 - k)] : W[((size_t)o * cin + i) * 27 + k];
+    }
     out[idx] = __float2bfloat16_rn(v);
 }
 
@@ -744,7 +755,7 @@ __global__ void pack_weights_umma_kernel(const float *__restrict__ W, int cout, 
 // Wt[i][o][k] = W[o][i][26 - k], so that the same convolution kernel computes
 // da[n][i] = sum_{k, o} W[o][i][k] dz[n - off_k][o].
 __global__ void pack_weights_kernel(const float *__restrict__ W, int cout, int cin, int mt_count, int cb_count,
-                                    bool transpose, uint4 *__restrict__ frag)
+                                    bool transpose, bool xfold, uint4 *__restrict__ frag)
 {
     const int total = 27 * cb_count * mt_count * 32;
     const int idx = blockIdx.x * blockDim.x + threadIdx.x;
@@ -757,6 +768,10 @@ __global__ void pack_weights_kernel(const float *__restrict__ W, int cout, int c
     // the GEMM's (row, col) = (output channel, input channel) of this layer or of its transpose
     const int rows = transpose ? cin : cout, cols = transpose ? cout : cin;
     auto w = [&](int r, int c) -> float {
+        if (xfold) {   // folded first-layer input: only the dx = 0 taps, carrying all three x taps
+            if (r >= cout || c >= 15 || k % 3 != 1) return 0.0f;
+            return W[((size_t)r * cin + c % 5) * 27 + (k - 1 + c / 5)];
+        }
         if (r >= rows || c >= cols) return 0.0f;
         return transpose ? W[((size_t)c * cin + r) * 27 + (26 - k)] : W[((size_t)r * cin + c) * 27 + k];
     };
@@ -777,18 +792,26 @@ __device__ __forceinline__ float silu_grad(float z)
     return s * (1.0f + z * (1.0f - s));
 }
 
-// x [5][N] (channel-first FP32) -> a0 [N][16] channel-last BF16, channels 5..15 zero
-__global__ void pack_input_kernel(const float *__restrict__ x, int N, __nv_bfloat16 *__restrict__ a0)
+// x [5][N] (channel-first FP32) -> a0 [N][16] channel-last BF16 with the node's x neighbours
+// folded into the channels: a0[n][5 dx + c] = x[c][n + (dx - 1) e_x] (periodic in x) for dx = 0..2,
+// channel 15 zero.  The first layer then takes its three x taps of one (dy, dz) offset in one
+// 16-channel step (3 tensor-core steps per plane rather than 9 steps of 5 real channels in 16).
+__global__ void pack_input_kernel(const float *__restrict__ x, int nx, int N, __nv_bfloat16 *__restrict__ a0)
 {
     const int n = blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= N) return;
+    const int xx = n % nx, row = n - xx;
+    float f[16];
+#pragma unroll
+    for (int dx = 0; dx < 3; ++dx) {
+        const size_t src = (size_t)row + mwrap(xx + dx - 1, nx);
+#pragma unroll
+        for (int c = 0; c < 5; ++c) f[5 * dx + c] = x[(size_t)c * N + src];
+    }
+    f[15] = 0.0f;
     uint32_t v[8];
 #pragma unroll
-    for (int c = 0; c < 8; ++c) {
-        const float lo = 2 * c < 5 ? x[(size_t)(2 * c) * N + n] : 0.0f;
-        const float hi = 2 * c + 1 < 5 ? x[(size_t)(2 * c + 1) * N + n] : 0.0f;
-        v[c] = pack_bf16(lo, hi);
-    }
+    for (int c = 0; c < 8; ++c) v[c] = pack_bf16(f[2 * c], f[2 * c + 1]);
     uint4 *d = reinterpret_cast<uint4 *>(a0 + (size_t)n * 16);
     d[0] = make_uint4(v[0], v[1], v[2], v[3]);
     d[1] = make_uint4(v[4], v[5], v[6], v[7]);
@@ -983,13 +1006,17 @@ __global__ void __launch_bounds__(256) dweight_mma_kernel(int nx, int ny, int nz
 }
 
 // dW[o][i][k] += sum over the nblk blocks of k's z offset group, in block order
-__global__ void dw_reduce_kernel(const float *__restrict__ part, int nblk, int cout, int cin, float *__restrict__ dW)
+// xfold (the first layer): the gradient of tap k of input channel i is that of the folded input's
+// channel 5 dx' + i at the dx = 0 tap k - dx' + 1 (dx' = k % 3)
+__global__ void dw_reduce_kernel(const float *__restrict__ part, int nblk, int cout, int cin, bool xfold,
+                                 float *__restrict__ dW)
 {
     const int w = blockIdx.x * blockDim.x + threadIdx.x;
     if (w >= cout * cin * 27) return;
     const int k = w % 27, oi = w / 27, o = oi / cin, i = oi - o * cin;
-    const int gz = k / 9, q = k - 9 * gz;
-    const float *pp = part + ((size_t)gz * nblk * 9 + q) * 1024 + o * 32 + i;
+    const int ks = xfold ? k - k % 3 + 1 : k, is = xfold ? 5 * (k % 3) + i : i;
+    const int gz = ks / 9, q = ks - 9 * gz;
+    const float *pp = part + ((size_t)gz * nblk * 9 + q) * 1024 + o * 32 + is;
     float s = 0.0f;
     for (int b = 0; b < nblk; ++b) s += pp[(size_t)b * 9 * 1024];
     dW[w] += s;
@@ -1308,21 +1335,23 @@ cudaError_t repack(lbm_cnn *c)
     for (int l = 0; l < tslb::NLAYER; ++l) {
         const int mt = COUTP[l] / 16, cb = CINP[l] / 16;
         const int n = frag_count(mt, cb);
+        const bool xfold = l == 0;   // the first layer's input carries its x neighbours (pack_input_kernel)
         tslb::pack_weights_kernel<<<(n + 255) / 256, 256, 0, c->stream>>>(c->p + c->pofs[l], tslb::COUT[l],
-                                                                           tslb::CIN[l], mt, cb, false, c->wf[l]);
-        const int nu = 27 * cb * 2 * COUTP[l] * 8;
+                                                                           tslb::CIN[l], mt, cb, false, xfold, c->wf[l]);
+        const int nu = (xfold ? 3 : 9) * cb * 2 * 3 * COUTP[l] * 8;
         tslb::pack_weights_umma_kernel<<<(nu + 255) / 256, 256, 0, c->stream>>>(c->p + c->pofs[l], tslb::COUT[l],
                                                                                  tslb::CIN[l], COUTP[l], cb, false,
-                                                                                 c->wu[l]);
+                                                                                 xfold, c->wu[l]);
         if (l > 0) {
             const int mtt = CINP[l] / 16, cbt = COUTP[l] / 16;
             const int nt = frag_count(mtt, cbt);
             tslb::pack_weights_kernel<<<(nt + 255) / 256, 256, 0, c->stream>>>(c->p + c->pofs[l], tslb::COUT[l],
-                                                                                tslb::CIN[l], mtt, cbt, true, c->wt[l]);
+                                                                                tslb::CIN[l], mtt, cbt, true, false,
+                                                                                c->wt[l]);
             const int nut = 27 * cbt * 2 * CINP[l] * 8;
             tslb::pack_weights_umma_kernel<<<(nut + 255) / 256, 256, 0, c->stream>>>(c->p + c->pofs[l], tslb::COUT[l],
                                                                                       tslb::CIN[l], CINP[l], cbt, true,
-                                                                                      c->wut[l]);
+                                                                                      false, c->wut[l]);
         }
     }
     return cudaGetLastError();
@@ -1369,18 +1398,18 @@ cudaError_t launch_conv_mma(lbm_cnn *c, const uint4 *wfrag, const __nv_bfloat16 
 
 // out = conv(in) + bias (FP32, channel-last); with act non-null also act = silu(out) in BF16 (the
 // next layer's input; fused into the tcgen05 kernel's epilogue, a separate pass for the others).
-template <int MT, int CB>
+template <int MT, int CB, bool XF = false>
 cudaError_t launch_conv(lbm_cnn *c, int layer, bool transpose, const __nv_bfloat16 *in, const float *bias, float *out,
                         __nv_bfloat16 *act = nullptr, bool keep_z = true)
 {
     const uint4 *wfrag = transpose ? c->wt[layer] : c->wf[layer];
     const __nv_bfloat16 *wpack = transpose ? c->wut[layer] : c->wu[layer];
     if (c->conv_kernel == 0 && c->nx % tslb::UM_TX == 0) {   // tcgen05 / TMEM
-        constexpr int WB = 9 * CB * 2 * 3 * MT * 16 * 16;
+        constexpr int WB = (XF ? 3 : 9) * CB * 2 * 3 * MT * 16 * 16;
         const size_t smem = (size_t)((WB + 1023) / 1024) * 1024 + (size_t)tslb::UM_SLOTS * tslb::UmGeom<CB>::PLANE_BYTES;
         static bool attr = false;
         if (!attr) {
-            cudaError_t e = cudaFuncSetAttribute(tslb::conv_umma_kernel<MT, CB>,
+            cudaError_t e = cudaFuncSetAttribute(tslb::conv_umma_kernel<MT, CB, XF>,
                                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             if (e != cudaSuccess) return e;
             attr = true;
@@ -1395,7 +1424,7 @@ cudaError_t launch_conv(lbm_cnn *c, int layer, bool transpose, const __nv_bfloat
         // previous kernel drains, and waits for it before reading its input.  So no kernel that
         // writes packed weights or biases may directly precede a convolution on the stream (repack
         // is always followed by pack_input_kernel or another ordinary launch).
-        return tslb::launch_pdl(tslb::conv_umma_kernel<MT, CB>, dim3(tiles, nzc), dim3(tslb::UM_THREADS), smem, c->stream,
+        return tslb::launch_pdl(tslb::conv_umma_kernel<MT, CB, XF>, dim3(tiles, nzc), dim3(tslb::UM_THREADS), smem, c->stream,
                                 c->nx, c->ny, c->nz, wpack, in, bias, out, act, zlen, c->derr, c->test_expire,
                                 keep_z ? 1 : 0);
     }
@@ -1414,9 +1443,9 @@ cudaError_t forward(lbm_cnn *c, const float *x, bool train)
 {
     const int N = c->N;
     cudaError_t e;
-    tslb::pack_input_kernel<<<(N + 255) / 256, 256, 0, c->stream>>>(x, N, c->a[0]);
+    tslb::pack_input_kernel<<<(N + 255) / 256, 256, 0, c->stream>>>(x, c->nx, N, c->a[0]);
     // z_l = conv_l(a_l) + b_l and a_{l+1} = silu(z_l); biases zero-padded to the padded channels
-    if ((e = launch_conv<2, 1>(c, 0, false, c->a[0], c->bpad, c->z[0], c->a[1], train)) != cudaSuccess) return e;
+    if ((e = launch_conv<2, 1, true>(c, 0, false, c->a[0], c->bpad, c->z[0], c->a[1], train)) != cudaSuccess) return e;
     for (int l = 1; l < tslb::NLAYER; ++l) {
         const float *bias = c->bpad + 32 * l;
         e = l < 3 ? launch_conv<2, 2>(c, l, false, c->a[l], bias, c->z[l], c->a[l + 1], train)
@@ -1459,7 +1488,7 @@ cudaError_t launch_dweight(lbm_cnn *c, int layer, float *dW)
     if (e != cudaSuccess) return e;
     const int nw = tslb::COUT[layer] * tslb::CIN[layer] * 27;
     tslb::dw_reduce_kernel<<<(nw + 255) / 256, 256, 0, c->stream>>>(c->dwpart, tiles * nzc, tslb::COUT[layer],
-                                                                     tslb::CIN[layer], dW);
+                                                                     tslb::CIN[layer], layer == 0, dW);
     return cudaGetLastError();
 }
 
@@ -1727,7 +1756,9 @@ lbm_status lbm_cnn_get_layer(lbm_cnn *cnn, int layer, float *a_in, float *z, flo
         if (e == cudaSuccess)
             for (size_t n = 0; n < N; ++n)
                 for (int i = 0; i < cin; ++i) {
-                    const uint32_t bits = (uint32_t)h[n * cinp + i] << 16;   // BF16 is the top half of FP32
+                    // the first layer's input holds the node's own channels at 5 .. 9 (pack_input_kernel)
+                    const int is = layer == 0 ? 5 + i : i;
+                    const uint32_t bits = (uint32_t)h[n * cinp + is] << 16;   // BF16 is the top half of FP32
                     memcpy(&a_in[(size_t)i * N + n], &bits, 4);
                 }
         delete[] h;
