@@ -38,7 +38,6 @@ constexpr int CINP[NLAYER] = {16, 32, 32, 32};    // padded to multiples of 16
 constexpr int COUTP[NLAYER] = {32, 32, 32, 16};
 
 constexpr int wcount(int l) { return COUT[l] * CIN[l] * 27; }
-constexpr int kBiasChunk = 4096;   // nodes per block of the bias gradient
 constexpr int kCorrBlocks = 296;   // blocks of the correction's sums
 constexpr int pcount(int l) { return wcount(l) + COUT[l]; }
 
@@ -831,14 +830,38 @@ __global__ void silu_kernel(const float *__restrict__ z, size_t count, __nv_bflo
 }
 
 // dz = da * silu'(z) (FP32 and its BF16 copy), count = N * C
-__global__ void silu_back_kernel(const float *__restrict__ da, const float *__restrict__ z, size_t count,
-                                 float *__restrict__ dz, __nv_bfloat16 *__restrict__ dzb)
+// dz = da silu'(z) on [N][32] channel-last (FP32, and BF16 for the weight gradient), in float4
+// groups q = 8 n + g (channels 4 g .. 4 g + 3 of node n), grid-stride with a stride that is a
+// multiple of 8, so each thread keeps one channel group; and the bias gradient's per-block partial
+// sums part[block][32] of the new dz: each thread adds its groups in order, then thread c adds the
+// block's 32 per-thread sums of channel c in order (deterministic, no second pass over dz).
+constexpr int kBackBlocks = 4 * 148;
+__global__ void __launch_bounds__(256) silu_back_kernel(const float4 *__restrict__ da, const float4 *__restrict__ z,
+                                                        size_t nq, float4 *__restrict__ dz, uint2 *__restrict__ dzb,
+                                                        float *__restrict__ part)
 {
-    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= count) return;
-    const float v = da[i] * silu_grad(z[i]);
-    dz[i] = v;
-    dzb[i] = __float2bfloat16_rn(v);
+    __shared__ float red[32][33];
+    float s[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    for (size_t q = (size_t)blockIdx.x * 256 + threadIdx.x; q < nq; q += (size_t)gridDim.x * 256) {
+        const float4 a = da[q], zz = z[q];
+        const float4 v = make_float4(a.x * silu_grad(zz.x), a.y * silu_grad(zz.y), a.z * silu_grad(zz.z),
+                                     a.w * silu_grad(zz.w));
+        dz[q] = v;
+        dzb[q] = make_uint2(pack_bf16(v.x, v.y), pack_bf16(v.z, v.w));
+        s[0] += v.x;
+        s[1] += v.y;
+        s[2] += v.z;
+        s[3] += v.w;
+    }
+    const int g = threadIdx.x & 7, m = threadIdx.x >> 3;   // channel group, and rank within it
+#pragma unroll
+    for (int c = 0; c < 4; ++c) red[m][4 * g + c] = s[c];
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        float tot = 0.0f;
+        for (int r = 0; r < 32; ++r) tot += red[r][threadIdx.x];
+        part[(size_t)blockIdx.x * 32 + threadIdx.x] = tot;
+    }
 }
 
 // y [4][N] channel-first from the last layer's z [N][16]
@@ -852,29 +875,46 @@ __global__ void unpack_output_kernel(const float *__restrict__ z4, int N, float 
 
 // Mean-squared loss over the 4 outputs and N nodes against t [4][N]; dz4 = 2 (y - t) / (4 N)
 // (channels 4..15 zero, FP32 and BF16); per-block FP64 partial sums of (y - t)^2.
+// Mean-squared-error loss over the 4 outputs: per-block FP64 partial sums of r^2 (partial), and
+// dz = 2 r / (4 N) for channels 0..3 of z4 [N][16] (zero for the padded 4..15, FP32 and BF16),
+// whose per-block sums part[block][0..3] are the last layer's bias gradient partials (in order:
+// thread c < 4 adds the block's nodes in order; channels 4..31 of the record are zero).
 __global__ void __launch_bounds__(256) loss_kernel(const float *__restrict__ z4, const float *__restrict__ t, int N,
                                                    float *__restrict__ dz, __nv_bfloat16 *__restrict__ dzb,
-                                                   double *__restrict__ partial)
+                                                   double *__restrict__ partial, float *__restrict__ part)
 {
     __shared__ double red[256];
+    __shared__ float gsh[256][5];
     const int n = blockIdx.x * blockDim.x + threadIdx.x;
     double s = 0.0;
+    float g[4] = {0.0f, 0.0f, 0.0f, 0.0f};
     if (n < N) {
         const float scale = 2.0f / (4.0f * (float)N);
+        const float4 zz = reinterpret_cast<const float4 *>(z4)[(size_t)n * 4];
+        const float zc[4] = {zz.x, zz.y, zz.z, zz.w};
 #pragma unroll
-        for (int c = 0; c < 16; ++c) {
-            float g = 0.0f;
-            if (c < 4) {
-                const float r = z4[(size_t)n * 16 + c] - t[(size_t)c * N + n];
-                s += (double)r * r;
-                g = scale * r;
-            }
-            dz[(size_t)n * 16 + c] = g;
-            dzb[(size_t)n * 16 + c] = __float2bfloat16_rn(g);
+        for (int c = 0; c < 4; ++c) {
+            const float r = zc[c] - t[(size_t)c * N + n];
+            s += (double)r * r;
+            g[c] = scale * r;
         }
+        float4 *d = reinterpret_cast<float4 *>(dz + (size_t)n * 16);
+        d[0] = make_float4(g[0], g[1], g[2], g[3]);
+        d[1] = d[2] = d[3] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        uint4 *db = reinterpret_cast<uint4 *>(dzb + (size_t)n * 16);
+        db[0] = make_uint4(pack_bf16(g[0], g[1]), pack_bf16(g[2], g[3]), 0u, 0u);
+        db[1] = make_uint4(0u, 0u, 0u, 0u);
     }
     red[threadIdx.x] = s;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) gsh[threadIdx.x][c] = g[c];
     __syncthreads();
+    if (threadIdx.x < 32) {
+        float tot = 0.0f;
+        if (threadIdx.x < 4)
+            for (int r = 0; r < 256; ++r) tot += gsh[r][threadIdx.x];
+        part[(size_t)blockIdx.x * 32 + threadIdx.x] = tot;
+    }
     for (int w = 128; w > 0; w >>= 1) {
         if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
         __syncthreads();
@@ -1008,43 +1048,28 @@ __global__ void __launch_bounds__(256) dweight_mma_kernel(int nx, int ny, int nz
 // dW[o][i][k] += sum over the nblk blocks of k's z offset group, in block order
 // xfold (the first layer): the gradient of tap k of input channel i is that of the folded input's
 // channel 5 dx' + i at the dx = 0 tap k - dx' + 1 (dx' = k % 3)
-__global__ void dw_reduce_kernel(const float *__restrict__ part, int nblk, int cout, int cin, bool xfold,
-                                 float *__restrict__ dW)
+// One warp per weight w: lane l adds the partials of blocks l, l + 32, ... in order, then a fixed
+// shuffle tree adds the lanes (deterministic; the blocks' loads are spread over the warp).
+__global__ void __launch_bounds__(256) dw_reduce_kernel(const float *__restrict__ part, int nblk, int cout, int cin,
+                                                        bool xfold, float *__restrict__ dW)
 {
-    const int w = blockIdx.x * blockDim.x + threadIdx.x;
+    const int w = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
     if (w >= cout * cin * 27) return;
     const int k = w % 27, oi = w / 27, o = oi / cin, i = oi - o * cin;
     const int ks = xfold ? k - k % 3 + 1 : k, is = xfold ? 5 * (k % 3) + i : i;
     const int gz = ks / 9, q = ks - 9 * gz;
     const float *pp = part + ((size_t)gz * nblk * 9 + q) * 1024 + o * 32 + is;
     float s = 0.0f;
-    for (int b = 0; b < nblk; ++b) s += pp[(size_t)b * 9 * 1024];
-    dW[w] += s;
+    for (int b = lane; b < nblk; b += 32) s += pp[(size_t)b * 9 * 1024];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
+    if (lane == 0) dW[w] += s;
 }
 
-// db[o] += sum over a node chunk of dz[n][o]
-// Bias gradient in two deterministic passes (no atomics, so training is reproducible run to run):
-// block b sums chunk b of the nodes into part[b][32]; dbias_reduce_kernel adds the chunks in order.
-__global__ void __launch_bounds__(256) dbias_kernel(const float *__restrict__ dz, int cop, int cout, int N, int chunk,
-                                                    float *__restrict__ part)
-{
-    __shared__ float red[8][33];
-    const int c = threadIdx.x & 31, row = threadIdx.x >> 5;
-    const int n0 = blockIdx.x * chunk, n1 = min(N, n0 + chunk);
-    float s = 0.0f;
-    if (c < cout)
-        for (int n = n0 + row; n < n1; n += 8) s += dz[(size_t)n * cop + c];
-    red[row][c] = s;
-    __syncthreads();
-    if (row == 0 && c < cout) {
-        float tot = 0.0f;
-        for (int r = 0; r < 8; ++r) tot += red[r][c];
-        part[(size_t)blockIdx.x * 32 + c] = tot;
-    }
-}
-
-// one block of 256 threads: row r = threadIdx.x / 32 adds chunks r, r + 8, ... of channel
-// threadIdx.x % 32 in order, then row 0 adds the 8 rows in order (a fixed order: deterministic)
+// db[o] += the sum of the per-block partials part[b][o] (written by the producers of dz: the loss
+// kernel and silu_back_kernel).  One block of 256 threads: row r = threadIdx.x / 32 adds blocks
+// r, r + 8, ... of channel threadIdx.x % 32 in order, then row 0 adds the 8 rows in order (a fixed
+// order: deterministic).
 __global__ void __launch_bounds__(256) dbias_reduce_kernel(const float *__restrict__ part, int nchunk, int cout,
                                                            float *__restrict__ db)
 {
@@ -1487,36 +1512,36 @@ cudaError_t launch_dweight(lbm_cnn *c, int layer, float *dW)
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const int nw = tslb::COUT[layer] * tslb::CIN[layer] * 27;
-    tslb::dw_reduce_kernel<<<(nw + 255) / 256, 256, 0, c->stream>>>(c->dwpart, tiles * nzc, tslb::COUT[layer],
-                                                                     tslb::CIN[layer], layer == 0, dW);
+    tslb::dw_reduce_kernel<<<(nw + 7) / 8, 256, 0, c->stream>>>(c->dwpart, tiles * nzc, tslb::COUT[layer],
+                                                                 tslb::CIN[layer], layer == 0, dW);
     return cudaGetLastError();
 }
 
 cudaError_t backward(lbm_cnn *c)
 {
     const int N = c->N;
-    const int chunk = tslb::kBiasChunk;
-    const int nchunk = (N + chunk - 1) / chunk;
     cudaError_t e;
     // dz of the last layer is in dz / dzb with 16 channels (written by the loss kernel)
     for (int l = tslb::NLAYER - 1; l >= 0; --l) {
-        const int cop = COUTP[l];
         float *dW = c->grad + c->pofs[l];
         float *db = dW + tslb::wcount(l);
         e = l == 0   ? launch_dweight<2, 1>(c, l, dW)
             : l == 3 ? launch_dweight<1, 2>(c, l, dW)
                      : launch_dweight<2, 2>(c, l, dW);
         if (e != cudaSuccess) return e;
-        tslb::dbias_kernel<<<nchunk, 256, 0, c->stream>>>(c->dz[l], cop, tslb::COUT[l], N, chunk, c->dbpart);
-        tslb::dbias_reduce_kernel<<<1, 256, 0, c->stream>>>(c->dbpart, nchunk, tslb::COUT[l], db);
+        // the bias gradient from the per-block partials of dz_l, written by its producer (the loss
+        // kernel for the last layer, silu_back_kernel for the others)
+        tslb::dbias_reduce_kernel<<<1, 256, 0, c->stream>>>(c->dbpart, l == tslb::NLAYER - 1 ? c->loss_blocks
+                                                                                             : tslb::kBackBlocks,
+                                                           tslb::COUT[l], db);
         if (l == 0) break;
         // da_{l-1}[n][i] = sum_{k,o} W_l[o][i][k] dz_l[n - off_k][o]
         e = l == 3 ? launch_conv<2, 1>(c, l, true, c->dzb, nullptr, c->da)
                    : launch_conv<2, 2>(c, l, true, c->dzb, nullptr, c->da);
         if (e != cudaSuccess) return e;
-        const size_t cnt = (size_t)N * 32;
-        tslb::silu_back_kernel<<<(unsigned)((cnt + 255) / 256), 256, 0, c->stream>>>(c->da, c->z[l - 1], cnt,
-                                                                                      c->dz[l - 1], c->dzb);
+        tslb::silu_back_kernel<<<tslb::kBackBlocks, 256, 0, c->stream>>>(
+            reinterpret_cast<const float4 *>(c->da), reinterpret_cast<const float4 *>(c->z[l - 1]), (size_t)N * 8,
+            reinterpret_cast<float4 *>(c->dz[l - 1]), reinterpret_cast<uint2 *>(c->dzb), c->dbpart);
     }
     return cudaGetLastError();
 }
@@ -1586,7 +1611,7 @@ lbm_status lbm_cnn_create(int nx, int ny, int nz, unsigned long long seed, void 
         {(void **)&c->ybuf, 4 * N * sizeof(float)},
         // loss partials, or the correction's 6 sums then its blocks' records at offset 8
         {(void **)&c->dsum, (size_t)(std::max(c->loss_blocks, tslb::kCorrBlocks * 6) + 8) * sizeof(double)},
-        {(void **)&c->dbpart, (size_t)((N + tslb::kBiasChunk - 1) / tslb::kBiasChunk) * 32 * sizeof(float)},
+        {(void **)&c->dbpart, (size_t)std::max(c->loss_blocks, tslb::kBackBlocks) * 32 * sizeof(float)},
         {(void **)&c->bpad, (size_t)tslb::NLAYER * 32 * sizeof(float)},
     };
     cudaError_t err = cudaSuccess;
@@ -1721,7 +1746,7 @@ lbm_status lbm_cnn_grad(lbm_cnn *cnn, const float *x, const float *t, int accumu
     if (!accumulate) CNN_TRY(cudaMemsetAsync(cnn->grad, 0, cnn->nparams * sizeof(float), cnn->stream));
     CNN_TRY(forward(cnn, x, true));
     tslb::loss_kernel<<<cnn->loss_blocks, 256, 0, cnn->stream>>>(cnn->z[3], t, cnn->N, cnn->dz[3], cnn->dzb,
-                                                                  cnn->dsum);
+                                                                  cnn->dsum, cnn->dbpart);
     CNN_TRY(cudaGetLastError());
     CNN_TRY(backward(cnn));
     // loss: sum of the per-block partials
