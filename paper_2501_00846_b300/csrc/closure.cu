@@ -420,7 +420,8 @@ __device__ __forceinline__ void um_load_plane(uint8_t *slot, const __nv_bfloat16
 
 // z[n][o] = bias[o] + sum_{k, i} W[o][i][k] in[n + off_k][i], CO = MT * 16 output channels (padded),
 // CB * 16 input channels (padded); wpack: [9][CB][2][3 CO][8] BF16 (pack_weights_umma_kernel).
-// z is written when keep_z != 0 or act is null; act (not null): the next layer's input silu(z).
+// z is written when keep_z != 0 or act is null; act (not null): the next layer's input silu(z);
+// ycf (not null, the last layer): also its first 4 channels channel-first, ycf[c][n].
 constexpr int UM_EPI_WARPS = 8;                          // load and epilogue warps
 constexpr int UM_MMA_WARPS = 2;                          // MMA warps: one per patch
 constexpr int UM_THREADS = 32 * (UM_EPI_WARPS + UM_MMA_WARPS);
@@ -430,8 +431,8 @@ template <int MT, int CB, bool XF>
 __global__ void __launch_bounds__(UM_THREADS, 1) conv_umma_kernel(int nx, int ny, int nz, const __nv_bfloat16 *__restrict__ wpack,
                                                            const __nv_bfloat16 *__restrict__ in,
                                                            const float *__restrict__ bias, float *__restrict__ z,
-                                                           __nv_bfloat16 *__restrict__ act, int zlen,
-                                                           int *__restrict__ err, int stall, int keep_z)
+                                                           __nv_bfloat16 *__restrict__ act, float *__restrict__ ycf,
+                                                           int zlen, int *__restrict__ err, int stall, int keep_z)
 {
     constexpr int CO = MT * 16;
     constexpr int ROWS = 3 * CO;                       // B rows (jb, o)
@@ -669,6 +670,11 @@ __global__ void __launch_bounds__(UM_THREADS, 1) conv_umma_kernel(int nx, int ny
                     float v[CH];
 #pragma unroll
                     for (int o = 0; o < CH; ++o) v[o] = __uint_as_float(r[pt][o]) + bv[o];
+                    if (ycf && h == 0) {   // the network's output, channel-first: y[c][node], c < 4
+                        const size_t nn = (size_t)nx * ny * nz;
+#pragma unroll
+                        for (int o = 0; o < 4; ++o) ycf[(size_t)o * nn + node] = v[o];
+                    }
                     if (keep_z || !act) {
                         float4 *dst = reinterpret_cast<float4 *>(z + node * CO + h * CH);
 #pragma unroll
@@ -1425,7 +1431,7 @@ cudaError_t launch_conv_mma(lbm_cnn *c, const uint4 *wfrag, const __nv_bfloat16 
 // next layer's input; fused into the tcgen05 kernel's epilogue, a separate pass for the others).
 template <int MT, int CB, bool XF = false>
 cudaError_t launch_conv(lbm_cnn *c, int layer, bool transpose, const __nv_bfloat16 *in, const float *bias, float *out,
-                        __nv_bfloat16 *act = nullptr, bool keep_z = true)
+                        __nv_bfloat16 *act = nullptr, bool keep_z = true, float *ycf = nullptr)
 {
     const uint4 *wfrag = transpose ? c->wt[layer] : c->wf[layer];
     const __nv_bfloat16 *wpack = transpose ? c->wut[layer] : c->wu[layer];
@@ -1450,8 +1456,8 @@ cudaError_t launch_conv(lbm_cnn *c, int layer, bool transpose, const __nv_bfloat
         // writes packed weights or biases may directly precede a convolution on the stream (repack
         // is always followed by pack_input_kernel or another ordinary launch).
         return tslb::launch_pdl(tslb::conv_umma_kernel<MT, CB, XF>, dim3(tiles, nzc), dim3(tslb::UM_THREADS), smem, c->stream,
-                                c->nx, c->ny, c->nz, wpack, in, bias, out, act, zlen, c->derr, c->test_expire,
-                                keep_z ? 1 : 0);
+                                c->nx, c->ny, c->nz, wpack, in, bias, out, act, ycf, zlen, c->derr,
+                                c->test_expire, keep_z ? 1 : 0);
     }
     cudaError_t e = launch_conv_mma<MT, CB>(c, wfrag, in, bias, out);
     if (e == cudaSuccess && act) {
@@ -1459,12 +1465,17 @@ cudaError_t launch_conv(lbm_cnn *c, int layer, bool transpose, const __nv_bfloat
         tslb::silu_kernel<<<(unsigned)((cnt + 255) / 256), 256, 0, c->stream>>>(out, cnt, act);
         e = cudaGetLastError();
     }
+    if (e == cudaSuccess && ycf) {
+        tslb::unpack_output_kernel<<<(c->N + 255) / 256, 256, 0, c->stream>>>(out, c->N, ycf);
+        e = cudaGetLastError();
+    }
     return e;
 }
 
 // train: keep every layer's pre-activation z (the backward pass needs it); otherwise only the last
-// layer's, the output (the tensor-core kernel then skips the other z stores)
-cudaError_t forward(lbm_cnn *c, const float *x, bool train)
+// layer's, the output (the tensor-core kernel then skips the other z stores).  y (not null): the
+// output also channel-first, y[c][n] (written by the last layer's epilogue).
+cudaError_t forward(lbm_cnn *c, const float *x, bool train, float *y = nullptr)
 {
     const int N = c->N;
     cudaError_t e;
@@ -1474,7 +1485,7 @@ cudaError_t forward(lbm_cnn *c, const float *x, bool train)
     for (int l = 1; l < tslb::NLAYER; ++l) {
         const float *bias = c->bpad + 32 * l;
         e = l < 3 ? launch_conv<2, 2>(c, l, false, c->a[l], bias, c->z[l], c->a[l + 1], train)
-                  : launch_conv<1, 2>(c, l, false, c->a[l], bias, c->z[l]);
+                  : launch_conv<1, 2>(c, l, false, c->a[l], bias, c->z[l], nullptr, true, y);
         if (e != cudaSuccess) return e;
     }
     return cudaGetLastError();
@@ -1734,8 +1745,7 @@ lbm_status lbm_cnn_test_expire_wait(lbm_cnn *cnn, int on)
 lbm_status lbm_cnn_forward(lbm_cnn *cnn, const float *x, float *y)
 {
     if (!cnn || !x || !y) return cnn_fail(LBM_ERR_ARG, "network, x and y are required");
-    CNN_TRY(forward(cnn, x, false));
-    tslb::unpack_output_kernel<<<(cnn->N + 255) / 256, 256, 0, cnn->stream>>>(cnn->z[3], cnn->N, y);
+    CNN_TRY(forward(cnn, x, false, y));
     CNN_TRY(cudaGetLastError());
     return check_timeout(cnn);
 }
@@ -1858,8 +1868,7 @@ lbm_status lbm_closure_apply(lbm_ctx *ctx, lbm_cnn *cnn, const lbm_closure_norm 
     const int N = v.G.N;
     tslb::features_kernel<<<(N + 255) / 256, 256, 0, v.stream>>>(v.G, v.P, v.g, v.phi, v.u, *norm, cnn->xbuf);
     CNN_TRY(cudaGetLastError());
-    CNN_TRY(forward(cnn, cnn->xbuf, false));
-    tslb::unpack_output_kernel<<<(N + 255) / 256, 256, 0, v.stream>>>(cnn->z[3], N, cnn->ybuf);
+    CNN_TRY(forward(cnn, cnn->xbuf, false, cnn->ybuf));
     tslb::corr_sums_kernel<<<tslb::kCorrBlocks, 256, 0, v.stream>>>(cnn->ybuf, v.phi, *norm, v.P.rho_g, v.P.drho, N,
                                                                      cnn->dsum + 8);
     tslb::corr_final_kernel<<<1, 192, 0, v.stream>>>(cnn->dsum + 8, tslb::kCorrBlocks, cnn->dsum);
