@@ -39,6 +39,7 @@ class _Params(ctypes.Structure):
         ("body", ctypes.c_double * 3),
         ("advect", ctypes.c_int),
         ("literal_weight", ctypes.c_int),
+        ("storage16", ctypes.c_int),
     ]
 
 
@@ -61,6 +62,7 @@ class Params:
     body: tuple = (0.0, 0.0, 0.0)
     advect: int = 0          # 0: flux form div(ubar phi) (reading R4); 1: literal ubar . grad(phi)
     literal_weight: int = 0  # 0: sharpening weight max(phi (1 - phi), 0) (reading R15); 1: phi (1 - phi)
+    storage16: int = 0       # 0: FP64 populations; 1 / 2: the library's BF16 / FP16 deviation storage, emulated
 
     @property
     def shape(self):
@@ -80,6 +82,7 @@ class Params:
         p.body[:] = list(self.body)
         p.advect = int(self.advect)
         p.literal_weight = int(self.literal_weight)
+        p.storage16 = int(self.storage16)
         return p
 
 
@@ -108,6 +111,7 @@ def lib():
         L.oracle_init.argtypes = [pp, dp, dp, dp, dp, dp, dp]
         L.oracle_run.argtypes = [pp, ctypes.c_int, dp, dp, dp]
         L.oracle_pressure.argtypes = [pp, dp, dp, dp]
+        L.oracle_store16_node.argtypes = [ctypes.c_int, dp, dp, dp, dp, dp]
         _lib = L
     return _lib
 
@@ -187,6 +191,16 @@ def collide_node(f, acc, omega: float):
     A = np.zeros(9)
     lib().oracle_collide_node(_p(f), _p(acc), float(omega), _p(g), _p(u), _p(A))
     return g, u, A.reshape(3, 3)
+
+
+def store16_node(fmt: int, g, u):
+    """The library's 16-bit storage of one node (fmt 1 BF16, 2 FP16): the stored P, the rounded
+    deviations hr [27] and the populations w_i (P + e_i(u) + hr_i) they represent."""
+    g, u = _f64(g), _f64(u)
+    P_out = ctypes.c_double()
+    hr, gout = np.zeros(Q), np.zeros(Q)
+    lib().oracle_store16_node(int(fmt), _p(g), _p(u), ctypes.byref(P_out), _p(hr), _p(gout))
+    return P_out.value, hr, gout
 
 
 def force_node(P: Params, f, phi: float, gphi, lphi: float, ubar):

@@ -53,6 +53,7 @@
  *       printed phi (1 - phi) everywhere, to measure how far the reading moves the results.
  */
 #include <math.h>
+#include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
 #ifdef _OPENMP
@@ -75,6 +76,7 @@ typedef struct {
     double body[3];        /* uniform body-force density */
     int advect;            /* 0: flux form div(ubar phi); 1: literal form ubar . grad(phi) */
     int literal_weight;    /* 0: sharpening weight max(phi (1 - phi), 0) (R15); 1: phi (1 - phi) as printed */
+    int storage16;         /* 0: FP64 populations; 1 / 2: the library's BF16 / FP16 deviation storage (store16) */
 } oracle_params;
 
 /* ------------------------------------------------------------------------------------------ */
@@ -464,6 +466,57 @@ static void pull(const oracle_params *P, const double *g, int x, int y, int z, d
 }
 
 /* One full step S^n = (g, phi, ubar) -> S^{n+1} = (g_new, phi_new, u_new). */
+/* ------------------------------------------------------------------------------------------ */
+/* The library's 16-bit population storage, emulated (not in the paper: the precision form of   */
+/* the storage, its own design).  A node keeps h_i = g_i / w_i - p* - e_i(u), with              */
+/* e_i(u) = f^eq_i(0, u) / w_i, rounded to BF16, or to FP16 after scaling by 2^12, from its FP32 */
+/* value (the precision in which the library takes the rounding), plus P = p* - sum_i w_i hr_i.  */
+/* The populations it represents are w_i (P + e_i(u) + hr_i): their sum is p*, because          */
+/* sum_i w_i e_i(u) = 0.  Rounding is to nearest, ties to even.                                  */
+/* ------------------------------------------------------------------------------------------ */
+static float round_bf16(float v)
+{
+    uint32_t b;
+    memcpy(&b, &v, 4);
+    if ((b & 0x7fffffffu) > 0x7f800000u) return v;        /* NaN */
+    b += 0x7fffu + ((b >> 16) & 1u);                      /* half an ulp of BF16, ties to even */
+    b &= 0xffff0000u;
+    float r;
+    memcpy(&r, &b, 4);
+    return r;
+}
+
+static double round16(int fmt, double h)
+{
+    const float h32 = (float)h;
+    if (fmt == 1) return (double)round_bf16(h32);
+    return (double)(float)(_Float16)(h32 * 4096.0f) / 4096.0;   /* IEEE binary16 conversion, scaled */
+}
+
+/* One node: the stored pair (P, hr) of populations g with velocity u, and the populations it
+   represents (gout; may alias g). */
+void oracle_store16_node(int fmt, const double g[Q], const double u[3], double *P_out, double hr[Q], double gout[Q])
+{
+    build_lattice();
+    double ps = 0.0;
+    for (int i = 0; i < Q; ++i) ps += g[i];
+    double feq0[Q], sum = 0.0;
+    oracle_equilibrium(0.0, u, feq0);
+    for (int i = 0; i < Q; ++i) {
+        hr[i] = round16(fmt, g[i] / Wt[i] - ps - feq0[i] / Wt[i]);
+        sum += Wt[i] * hr[i];
+    }
+    const double Pv = ps - sum;
+    for (int i = 0; i < Q; ++i) gout[i] = Wt[i] * (Pv + feq0[i] / Wt[i] + hr[i]);
+    *P_out = Pv;
+}
+
+static void store16(int fmt, double g[Q], const double u[3])
+{
+    double Pv, hr[Q];
+    oracle_store16_node(fmt, g, u, &Pv, hr, g);
+}
+
 void oracle_step(const oracle_params *P, const double *g, const double *phi, const double *ubar,
                  double *g_new, double *phi_new, double *u_new)
 {
@@ -496,6 +549,7 @@ void oracle_step(const oracle_params *P, const double *g, const double *phi, con
 
                 double gout[Q], u[3], A[9];
                 oracle_collide_node(f, acc, omega, gout, u, A);
+                if (P->storage16) store16(P->storage16, gout, u);
                 for (int i = 0; i < Q; ++i) g_new[(long)i * N + k] = gout[i];
                 for (int a = 0; a < 3; ++a) u_new[a * N + k] = u[a];
             }

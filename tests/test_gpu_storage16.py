@@ -1,19 +1,21 @@
 """16-bit population storage (LBM_BF16, LBM_FP16) against the FP64 oracle and the FP32 path.
 
 The 16-bit formats round only h_i = (g_i - f^eq_i(p*, u)) / w_i, the non-equilibrium part of each
-population, once per step; p*, u and phi stay FP32 and the arithmetic is FP32.  The error of a
-stored population is at most u16 |h_i| w_i per step (unit roundoff u16 = 2^-8 for BF16, 2^-11
-for FP16), which is what separates these tolerances from the FP32 ones (1e-5 / 1e-4 / 1e-4):
+population, once per step; p*, u and phi stay FP32 and the arithmetic is FP32.  The oracle
+emulates exactly that rounding (oracle.Params.storage16, pinned against the format's definition
+in test_oracle_storage16.py).  So each case's bar is derived, not fitted: the format's own effect
+on it, eps16 = |oracle with 16-bit storage - oracle| (max|d phi|, relative du, relative dp), is
+computed by the oracle at test time, and a GPU run must lie within
 
-                 max|d phi|   rel du    rel dp     (after the stated steps, vs the FP64 oracle)
-    BF16         2e-5         1e-3      5e-3
-    FP16         5e-6         2e-4      1e-3
+    FP32 bar (1e-5 / 1e-4 / 1e-4, the FP32 path's bars)  +  3 eps16
 
-Measured on B300 (droplet 48^3 with velocity noise, 100 steps / walled bubble at density ratio
-1000, 60 steps): BF16 9.3e-7 / 2.5e-4 / 6.6e-5 and 8.3e-6 / 2.8e-4 / 1.7e-3; FP16 1.8e-7 / 3.2e-5
-/ 9.5e-6 and 9.2e-7 / 5.6e-5 / 1.6e-4.  The bounds are those values times 3 to 8, rounded up.
-Integral observables (rise, bubble velocity, mass, sum phi) stay within the 0.5% bar of the FP32
-form on long runs.
+of the plain oracle.  The factor: a GPU run is another realisation of the same rounding (a
+last-bit difference in FP32 moves a value across a rounding boundary, and the runs' rounding
+errors decorrelate from there), so its distance from the plain oracle is of the size of eps16,
+not below it; measured on B300 within 1.5 eps16 on every case here (droplet 48^3 100 steps,
+ragged walled bubble at density ratio 1000 60 steps, ragged periodic droplet 80 steps; BF16 and
+FP16, both kernels).  Integral observables (rise, bubble velocity, mass, sum phi) stay within the
+0.5% bar of the FP32 form on long runs.
 """
 import math
 
@@ -27,7 +29,8 @@ pytestmark = pytest.mark.gpu
 
 STORAGES = [solver.LBM_BF16, solver.LBM_FP16]
 IDS = ["bf16", "fp16"]
-TOL = {solver.LBM_BF16: (2e-5, 1e-3, 5e-3), solver.LBM_FP16: (5e-6, 2e-4, 1e-3)}
+FP32_BAR = (1e-5, 1e-4, 1e-4)   # the FP32 path's bars against the oracle: max|d phi|, rel du, rel dp
+SPREAD = 3.0                    # an independent realisation of the rounding: measured within 1.5 eps16
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -59,29 +62,43 @@ def _run(wl, nsteps, storage, path=0):
     return phi, u, p, g, obs
 
 
-def _oracle(wl, nsteps):
-    P = oracle.Params(**wl.params())
+def _oracle(wl, nsteps, storage16=0):
+    P = oracle.Params(**wl.params(), storage16=storage16)
     ps = _pstar0(wl)
     st = oracle.run(P, oracle.init(P, _f32(wl.phi0()).astype(np.float64), _f32(wl.u0()).astype(np.float64),
                                    None if ps is None else ps.astype(np.float64)), nsteps)
     return P, st
 
 
-def _check(out, P, ref, storage, label, factor=1.0):
-    phi, u, p = out[:3]
+def _errs(fields, P, ref, u_scale=None):
+    """max|d phi|, max|d u| / (u_scale or max|u_ref|), max|d p| / max|p_ref| of fields (phi, u, p)."""
+    phi, u, p = fields[:3]
     pref = oracle.pressure(P, ref)
-    dphi = float(np.abs(phi - ref.phi).max())
-    du = float(np.abs(u - ref.u).max() / np.abs(ref.u).max())
-    dp = float(np.abs(p - pref).max() / np.abs(pref).max())
-    print(f"{label} storage={storage}: max|dphi| {dphi:.3e} rel du {du:.3e} rel dp {dp:.3e}")
-    tphi, tu, tp = (factor * t for t in TOL[storage])
-    assert dphi <= tphi and du <= tu and dp <= tp, (label, dphi, du, dp)
+    us = u_scale if u_scale else np.abs(ref.u).max()
+    return (float(np.abs(phi - ref.phi).max()), float(np.abs(u - ref.u).max() / us),
+            float(np.abs(p - pref).max() / np.abs(pref).max()))
+
+
+def _reference(wl, nsteps, storage, u_scale=None):
+    """(P, ref, bars): the plain oracle run and the derived bars FP32 bar + SPREAD eps16, eps16
+    the emulated 16-bit oracle's distance from it."""
+    P, ref = _oracle(wl, nsteps)
+    P16, ref16 = _oracle(wl, nsteps, storage)
+    eps = _errs((ref16.phi, ref16.u, oracle.pressure(P16, ref16)), P, ref, u_scale)
+    return P, ref, tuple(FP32_BAR[j] + SPREAD * eps[j] for j in range(3))
+
+
+def _check(out, P, ref, bars, label, u_scale=None):
+    d = _errs(out, P, ref, u_scale)
+    print(f"{label}: max|dphi| {d[0]:.3e} rel du {d[1]:.3e} rel dp {d[2]:.3e}; bars {bars[0]:.3e} {bars[1]:.3e} "
+          f"{bars[2]:.3e}")
+    assert all(d[j] <= bars[j] for j in range(3)), (label, d, bars)
 
 
 @pytest.fixture(scope="module")
 def droplet48():
     wl = inputs.static_droplet(L=48, radius=12.0, noise=0.01, seed=1234)
-    return (wl,) + _oracle(wl, 100)
+    return {st: (wl,) + _reference(wl, 100, st) for st in STORAGES}
 
 
 # path 0: tiled 16-bit kernel (shared-memory staging); path 1: the plain one-node-per-thread kernel
@@ -92,8 +109,8 @@ PATH_IDS = ["tiled", "plain"]
 @pytest.mark.parametrize("path", PATHS, ids=PATH_IDS)
 @pytest.mark.parametrize("storage", STORAGES, ids=IDS)
 def test_droplet48_100_steps(droplet48, storage, path):
-    wl, P, ref = droplet48
-    _check(_run(wl, 100, storage, path), P, ref, storage, f"droplet48 path={path}")
+    wl, P, ref, bars = droplet48[storage]
+    _check(_run(wl, 100, storage, path), P, ref, bars, f"droplet48 storage={storage} path={path}")
 
 
 @pytest.mark.parametrize("path", PATHS, ids=PATH_IDS)
@@ -101,8 +118,8 @@ def test_droplet48_100_steps(droplet48, storage, path):
 def test_ragged_walled_bubble_ratio1000(storage, path):
     wl = inputs.rising_bubble(nx=37, ny=21, nz=19, R=5.0, zc=8.0, sqrt_gR=0.04, mobility=0.1)
     wl.noise, wl.seed = 0.005, 99
-    P, ref = _oracle(wl, 60)
-    _check(_run(wl, 60, storage, path), P, ref, storage, f"ragged walled bubble path={path}")
+    P, ref, bars = _reference(wl, 60, storage)
+    _check(_run(wl, 60, storage, path), P, ref, bars, f"ragged walled bubble storage={storage} path={path}")
 
 
 @pytest.mark.parametrize("path", PATHS, ids=PATH_IDS)
@@ -111,22 +128,23 @@ def test_ragged_periodic_droplet_across_boundary(storage, path):
     wl = inputs.static_droplet(L=24, radius=6.0, noise=0.01, seed=5)
     wl.nx, wl.ny, wl.nz = 45, 29, 27
     wl.center = (2.0, 27.5, 25.0)
-    P, ref = _oracle(wl, 80)
-    _check(_run(wl, 80, storage, path), P, ref, storage, f"ragged periodic droplet path={path}")
+    P, ref, bars = _reference(wl, 80, storage)
+    _check(_run(wl, 80, storage, path), P, ref, bars, f"ragged periodic droplet storage={storage} path={path}")
 
 
 @pytest.mark.parametrize("storage", STORAGES, ids=IDS)
 def test_minimum_boxes(storage):
     """4^3 periodic and 4 x 5 x 4 walled: every tile is ragged and every halo wraps.  Every node
     of these boxes lies inside the interface of the R = 1.5, W = 4 droplet, where the
-    non-equilibrium part h is largest relative to u, so the bounds are 4 times the bulk ones."""
+    non-equilibrium part h is largest relative to u; the derived bars follow that."""
     for walled in (False, True):
         wl = inputs.static_droplet(L=4, radius=1.5, noise=0.01, seed=3)
         if walled:
             wl.ny, wl.wall_z, wl.gravity = 5, 1, (0.0, 0.0, -1e-5)
-        P, ref = _oracle(wl, 10)
+        P, ref, bars = _reference(wl, 10, storage)
         for path in PATHS:
-            _check(_run(wl, 10, storage, path), P, ref, storage, f"minimum box walled={walled} path={path}", 4.0)
+            _check(_run(wl, 10, storage, path), P, ref, bars,
+                   f"minimum box storage={storage} walled={walled} path={path}")
 
 
 @pytest.mark.parametrize("storage", STORAGES, ids=IDS)
@@ -134,13 +152,14 @@ def test_tiled_and_plain_kernels_agree(storage):
     """The tiled and the plain 16-bit kernels do the same arithmetic on the same values, but the
     compiler may order FP32 operations differently, and a last-bit difference can move a value
     across a 16-bit rounding boundary, after which the two runs carry independent rounding
-    errors.  So they agree to the oracle bounds, not bit for bit."""
+    errors.  So they agree as two realisations of the rounding, each within its derived bar of the
+    oracle: to twice that bar, not bit for bit."""
     wl = inputs.rising_bubble(nx=37, ny=21, nz=19, R=5.0, zc=8.0, sqrt_gR=0.04, mobility=0.1)
     wl.noise, wl.seed = 0.005, 99
     a, b = _run(wl, 20, storage, 0), _run(wl, 20, storage, 1)
-    tphi, tu, _ = TOL[storage]
-    assert np.abs(a[0] - b[0]).max() <= tphi
-    assert np.abs(a[1] - b[1]).max() <= tu * np.abs(b[1]).max()
+    _, ref, bars = _reference(wl, 20, storage)
+    assert np.abs(a[0] - b[0]).max() <= 2 * bars[0]
+    assert np.abs(a[1] - b[1]).max() <= 2 * bars[1] * np.abs(ref.u).max()
 
 
 @pytest.mark.parametrize("storage", STORAGES, ids=IDS)
@@ -233,16 +252,9 @@ def test_rising_bubble_full_size_two_steps(storage):
     """The benchmark workload (128 x 128 x 256, ratios 1000 / 100) in the benchmark's launch
     configuration, two steps against the oracle."""
     wl = inputs.rising_bubble()
-    P, ref = _oracle(wl, 2)
-    phi, u, p, _, _ = _run(wl, 2, storage)
-    pref = oracle.pressure(P, ref)
-    dphi = float(np.abs(phi - ref.phi).max())
-    dp = float(np.abs(p - pref).max() / np.abs(pref).max())
-    du = float(np.abs(u - ref.u).max())
-    print(f"bubble full size storage={storage}: {dphi:.3e} {du:.3e} {dp:.3e}")
-    tphi, tu, tp = TOL[storage]
-    assert dphi <= tphi and dp <= tp
-    assert du <= tu * 0.04          # velocities ~1e-6 after two steps: scale sqrt(gR) = 0.04
+    # velocities are ~1e-6 after two steps: measured against the velocity scale sqrt(gR) = 0.04
+    P, ref, bars = _reference(wl, 2, storage, u_scale=0.04)
+    _check(_run(wl, 2, storage), P, ref, bars, f"bubble full size storage={storage}", u_scale=0.04)
 
 
 @pytest.mark.parametrize("storage", STORAGES, ids=IDS)
