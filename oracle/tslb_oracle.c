@@ -51,6 +51,10 @@
  *       lives in [0, 1]; outside it the weight would turn the sharpening flux around exactly
  *       where phi has an extremum and the normal is undefined.  literal_weight = 1 takes the
  *       printed phi (1 - phi) everywhere, to measure how far the reading moves the results.
+ *
+ * Not from the paper: storage16 = 1 / 2 emulates the library's 16-bit population storage (its
+ * precision form, BF16 / FP16 deviations from equilibrium; store16 below), so that the tests know
+ * each case's 16-bit effect from the oracle alone.  storage16 = 0 (the default) is the method.
  */
 #include <math.h>
 #include <stdint.h>
