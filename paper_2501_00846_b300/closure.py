@@ -1,24 +1,27 @@
 """Learned closure: training data from the solver's own fine-grid runs, training with the library's
 network kernels, and evaluation against the fine solver.
 
-The closure corrects (phi, ubar) of a 2x-coarser grid after every coarse step.  Data: seeded
-head-on droplet collisions (inputs.collision_set) run on the fine grid (L^3) in batches through the
-ensemble; at each snapshot the fine state is restricted 2x into a coarse context (populations,
-phi and ubar averaged over the 8 fine nodes of a coarse cell), the coarse context takes one step
-(= 2 fine steps in acoustic scaling) while the fine batch takes two, and the pair
+The closure corrects (phi, ubar) of a 2x-coarser grid once every `every` coarse steps (default 8).
+Data: seeded head-on droplet collisions (inputs.collision_set) run on the fine grid (L^3) in
+batches through the ensemble; at each snapshot the fine state is restricted 2x into a coarse
+context (populations, phi and ubar averaged over the 8 fine nodes of a coarse cell), the coarse
+context takes `every` steps (= 2 x every fine steps in acoustic scaling) while the fine batch takes
+twice as many, and the pair
 
-    x = features(coarse state after the step),    t = (restricted fine (phi, u) - coarse (phi, ubar)) / out_scale
+    x = features(coarse state after those steps),    t = (restricted fine (phi, u) - coarse (phi, ubar)) / out_scale
 
 is stored on the device.  Training: Adam on the mean-squared error, minibatches accumulated in
 the network's gradient buffer.  Evaluation: a held-out collision run three ways from the same
 restricted initial state -- the fine solver (restricted 2x, the reference), the plain coarse solver,
-and the coarse solver corrected by the network after every step -- with RMS errors of phi and u
-against that reference and device times of each.
+and the coarse solver corrected by the network after every `every` steps -- with RMS errors of phi
+and u against that reference and device times of each.  Trained on one-step defects, the velocity
+correction drives the closed loop away from its data and is applied with a factor (--u-relax);
+trained on 8-step defects, the network's own velocity prediction lowers the u error.
 
 Everything numerical runs in the library's CUDA kernels; torch provides device memory and the
 stream.
 
-    python -m paper_2501_00846_b300.closure --traj 200 --epochs 4 --out closure_run.json
+    python -m paper_2501_00846_b300.closure --traj 200 --epochs 6 --out closure_run.json
 """
 import argparse
 import json
@@ -390,9 +393,11 @@ def main(argv=None):
     ap.add_argument("--weights", default=None, help="npz file for the trained parameters and normalisation")
     ap.add_argument("--load", default=None, help="evaluate parameters from an npz written by --weights (no training)")
     ap.add_argument("--phi-only", action="store_true", help="apply only the phi correction when evaluating")
-    ap.add_argument("--every", type=int, default=1, help="coarse steps per correction")
-    ap.add_argument("--u-relax", type=float, default=0.0,
-                    help="factor on the applied velocity correction (0: the phi correction alone)")
+    ap.add_argument("--every", type=int, default=8,
+                    help="coarse steps per correction (the network is trained on the defect of this many steps)")
+    ap.add_argument("--u-relax", type=float, default=1.0,
+                    help="factor on the applied velocity correction (1: the network's own prediction; "
+                         "0: the phi correction alone)")
     ap.add_argument("--time-network", type=int, default=0, metavar="L",
                     help="only time the network's forward pass and training step on an L^3 grid")
     ap.add_argument("--ladder", action="store_true",
@@ -419,11 +424,17 @@ def main(argv=None):
         norm = solver.LbmClosureNorm.make(z["in_shift"], z["in_scale"], out_scale)
         net = solver.Network(a.L // 2, a.L // 2, a.L // 2, seed=a.seed)
         net.set_params(z["params"])
-        evals = [evaluate(net, norm, c, coarse_steps=a.eval_steps, apply_every=a.every) for c in eval_cols]
-        print(json.dumps({"eval": evals}))
+        res = {"eval": [evaluate(net, norm, c, coarse_steps=a.eval_steps, apply_every=a.every) for c in eval_cols],
+               "every": a.every, "u_relax": a.u_relax}
+        if a.ladder:
+            res["ladder"] = accuracy_ladder(net, norm, eval_cols[0], coarse_steps=a.eval_steps,
+                                            resolutions=(a.L // 2, 3 * a.L // 4), compare=a.L // 4,
+                                            apply_every=a.every)
+            res["equal_accuracy"] = equal_accuracy(res["ladder"], coarse=a.L // 2, finer=3 * a.L // 4)
+        print(json.dumps(res))
         if a.out:
             with open(a.out, "w") as fh:
-                json.dump({"eval": evals}, fh, indent=1)
+                json.dump(res, fh, indent=1)
         net.close()
         return 0
     t0 = time.perf_counter()
