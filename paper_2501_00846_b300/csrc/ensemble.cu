@@ -50,7 +50,39 @@ struct EnsBox {
     int zlen;        // planes per Allen–Cahn task of the box
     int mtask0;      // first task of the box in the moment-storage lattice Boltzmann task list
     int mzlen;       // planes per moment-storage task of the box
+    float rnxy, rnx; // 1 / (nx ny) and 1 / nx, rounded: node coordinates without integer division
 };
+
+// q = n / d (integer division) for 0 <= n < 2^24 and d >= 1, with rd = 1/d rounded to FP32.  n is
+// exact in FP32 and the product is within one unit of n / d (relative error below 2^-23 on a
+// quotient below 2^23, or exact for d = 1), so its truncation is off by at most one either way,
+// which the integer remainder corrects.
+__device__ __forceinline__ int div_u24(int n, int d, float rd)
+{
+    int q = __float2int_rz(__fmul_rn(__int2float_rn(n), rd));
+    const int r = n - q * d;
+    if (r < 0)
+        --q;
+    else if (r >= d)
+        ++q;
+    return q;
+}
+
+// Coordinates of node `node` (flat index x + nx (y + ny z)) of box B.
+__device__ __forceinline__ void box_coords(const EnsBox &B, int node, int &x, int &y, int &z)
+{
+    if (B.G.N < (1 << 24)) {   // uniform across a block: every thread of a block is in one box
+        z = div_u24(node, B.G.nxy, B.rnxy);
+        const int rem = node - z * B.G.nxy;
+        y = div_u24(rem, B.G.nx, B.rnx);
+        x = rem - y * B.G.nx;
+    } else {
+        z = node / B.G.nxy;
+        const int rem = node - z * B.G.nxy;
+        y = rem / B.G.nx;
+        x = rem - y * B.G.nx;
+    }
+}
 
 constexpr int kEnsMomZlen = 32;   // planes per moment-storage task (2 partial halo planes each)
 
@@ -73,21 +105,20 @@ __device__ __forceinline__ int find_box(const EnsBox *__restrict__ boxes, int nb
     return lo;
 }
 
-__global__ void __launch_bounds__(256, 3) ens_lbm_kernel(const EnsBox *__restrict__ boxes, int nb,
+// blk_box[k]: the box of lattice Boltzmann block k (one table read instead of a search)
+__global__ void __launch_bounds__(256, 3) ens_lbm_kernel(const EnsBox *__restrict__ boxes, const int *__restrict__ blk_box,
                                                       const float *__restrict__ g_in, const float *__restrict__ phi_new,
                                                       const float *__restrict__ u_in, float *__restrict__ g_out,
                                                       float *__restrict__ u_out, float *__restrict__ w_out)
 {
-    const int b = find_box<0>(boxes, nb, blockIdx.x);
+    const int b = blk_box[blockIdx.x];
     const Grid G = boxes[b].G;
     const int node = (blockIdx.x - boxes[b].blk0) * blockDim.x + threadIdx.x;
     if (node >= G.N) return;
     const Phys P = boxes[b].P;
     const size_t o = (size_t)boxes[b].off;
-    const int z = node / G.nxy;
-    const int rem = node - z * G.nxy;
-    const int y = rem / G.nx;
-    const int x = rem - y * G.nx;
+    int x, y, z;
+    box_coords(boxes[b], node, x, y, z);
     lbm_node<StoreF32>(G, P, g_in + 27 * o, nullptr, phi_new + o, u_in + 3 * o, g_out + 27 * o, nullptr,
                        u_out + 3 * o, w_out + 3 * o, x, y, z);
 }
@@ -212,7 +243,8 @@ __device__ __forceinline__ bool ens_grid_barrier(EnsSync *sync, bool arrive)
 // STORE: LBM_FP32 or one of the moment storages (LBM_MOM, LBM_MOM_BF16, LBM_MOM_FP16)
 template <int RY, int STORE>
 __global__ void __launch_bounds__(256, 2)
-    ens_persistent_kernel(const EnsBox *__restrict__ boxes, int nb, int ac_tasks, int lbm_work, int lbm_block,
+    ens_persistent_kernel(const EnsBox *__restrict__ boxes, const int *__restrict__ blk_box, int nb, int ac_tasks,
+                          int lbm_work, int lbm_block,
                           int fpn, const float *__restrict__ phi, const float *__restrict__ w,
                           float *__restrict__ phi_new, const float *__restrict__ g_in, const float *__restrict__ u_in,
                           float *__restrict__ g_out, float *__restrict__ u_out, float *__restrict__ w_out,
@@ -245,20 +277,20 @@ __global__ void __launch_bounds__(256, 2)
     }
     // phase 2: lattice Boltzmann work
     if constexpr (STORE == LBM_FP32) {
-        const long long total = (long long)lbm_work * lbm_block;
+        // lbm_block is 64, 128 or 256: virtual block and lane by shift and mask
+        const int lg = __ffs(lbm_block) - 1;
+        const long long total = (long long)lbm_work << lg;
         for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < total;
              v += (long long)gridDim.x * blockDim.x) {
-            const int vblk = (int)(v / lbm_block);
-            const int b = find_box<0>(boxes, nb, vblk);
+            const int vblk = (int)(v >> lg);
+            const int b = blk_box[vblk];
             const Grid G = boxes[b].G;
-            const int node = (vblk - boxes[b].blk0) * lbm_block + (int)(v - (long long)vblk * lbm_block);
+            const int node = ((vblk - boxes[b].blk0) << lg) + (int)(v & (lbm_block - 1));
             if (node >= G.N) continue;
             const Phys P = boxes[b].P;
             const size_t o = (size_t)boxes[b].off;
-            const int z = node / G.nxy;
-            const int rem = node - z * G.nxy;
-            const int y = rem / G.nx;
-            const int x = rem - y * G.nx;
+            int x, y, z;
+            box_coords(boxes[b], node, x, y, z);
             lbm_node<StoreF32>(G, P, g_in + 27 * o, nullptr, phi_new + o, u_in + 3 * o, g_out + 27 * o, nullptr,
                                u_out + 3 * o, w_out + 3 * o, x, y, z);
         }
@@ -355,6 +387,8 @@ struct lbm_ens {
     std::vector<lbm_params> prm;
     std::vector<EnsBox> box;          // host copy of the box table
     EnsBox *box_d = nullptr;          // device copy
+    int *blk_box = nullptr;           // box of every lattice Boltzmann block (FP32 populations)
+    long long blk_box_cap = 0;        // entries allocated: the block count at the smallest lbm_block
     long long ntot = 0;
     float *g[2] = {nullptr, nullptr};  // FP32 populations, or the boxes' moment states
     int storage = LBM_FP32;
@@ -396,6 +430,7 @@ void free_ens(lbm_ens *e)
     cudaFree(e->w);
     cudaFree(e->sync);
     cudaFree(e->box_d);
+    cudaFree(e->blk_box);
     cudaFree(e->partials);
     cudaFree(e->result);
     if (e->h_result) cudaFreeHost(e->h_result);
@@ -437,7 +472,14 @@ lbm_status build_tables(lbm_ens *e)
     const long long warp_slots = (long long)e->sms * e->ac_bps[ry == 2 ? 0 : 1] * tslb::AC_WPB;
     const long long warps = task < warp_slots ? task : warp_slots;
     e->ac_ctas = (int)((warps + tslb::AC_WPB - 1) / tslb::AC_WPB);
+    if (blk > e->blk_box_cap) return ens_fail(LBM_ERR_ARG, "block table too small (%lld > %lld)", blk, e->blk_box_cap);
+    std::vector<int> bb((size_t)blk);
+    for (int b = 0; b < e->nb; ++b) {
+        const int end = b + 1 < e->nb ? e->box[b + 1].blk0 : (int)blk;
+        for (int k = e->box[b].blk0; k < end; ++k) bb[k] = b;
+    }
     ENS_TRY(cudaMemcpyAsync(e->box_d, e->box.data(), e->nb * sizeof(EnsBox), cudaMemcpyHostToDevice, e->stream));
+    ENS_TRY(cudaMemcpyAsync(e->blk_box, bb.data(), bb.size() * sizeof(int), cudaMemcpyHostToDevice, e->stream));
     ENS_TRY(cudaStreamSynchronize(e->stream));
     if (e->exec) {
         cudaGraphExecDestroy(e->exec);
@@ -473,7 +515,7 @@ cudaError_t ens_launch_lbm(lbm_ens *e, int a, cudaStream_t s)
     case LBM_MOM_FP16: return ens_launch_mom<tslb::StoreF16>(e, a, s);
     default: break;
     }
-    tslb::ens_lbm_kernel<<<e->lbm_blocks, e->tun.lbm_block, 0, s>>>(e->box_d, e->nb, e->g[a], e->phi[1 - a], e->u[a],
+    tslb::ens_lbm_kernel<<<e->lbm_blocks, e->tun.lbm_block, 0, s>>>(e->box_d, e->blk_box, e->g[a], e->phi[1 - a], e->u[a],
                                                                       e->g[1 - a], e->u[1 - a], e->w);
     return cudaGetLastError();
 }
@@ -501,10 +543,11 @@ cudaError_t ens_persistent_launch(lbm_ens *e, int a, cudaStream_t s)
     int ac_tasks = e->ac_tasks, lbm_work = STORE == LBM_FP32 ? e->lbm_blocks : e->mom_tasks, lbm_block = e->tun.lbm_block,
         fpn = e->fpn, nb = e->nb;
     const EnsBox *boxes = e->box_d;
+    const int *blk_box = e->blk_box;
     const float *phi = e->phi[a], *w = e->w, *g_in = e->g[a], *u_in = e->u[a];
     float *phi_new = e->phi[1 - a], *g_out = e->g[1 - a], *u_out = e->u[1 - a], *w_out = e->w;
     tslb::EnsSync *sync = e->sync;
-    void *args[] = {&boxes, &nb, &ac_tasks, &lbm_work, &lbm_block, &fpn, &phi, &w, &phi_new,
+    void *args[] = {&boxes, &blk_box, &nb, &ac_tasks, &lbm_work, &lbm_block, &fpn, &phi, &w, &phi_new,
                     &g_in, &u_in, &g_out, &u_out, &w_out, &sync};
     const size_t smem = STORE == LBM_FP32 ? 0 : tslb::momt::kMomSmem;
     return cudaLaunchCooperativeKernel((const void *)tslb::ens_persistent_kernel<RY, STORE>,
@@ -651,8 +694,11 @@ lbm_status lbm_ens_create(const lbm_params *params, int nboxes, void *stream, lb
         EnsBox &B = e->box[b];
         memset(&B, 0, sizeof B);
         tslb::params_to_consts(params[b], B.G, B.P);
+        B.rnxy = 1.0f / (float)B.G.nxy;
+        B.rnx = 1.0f / (float)B.G.nx;
         B.off = e->ntot;
         e->ntot += B.G.N;
+        e->blk_box_cap += (B.G.N + 63) / 64;
         const int ob = tslb::observables_blocks(B.G);
         if (ob > max_obs) max_obs = ob;
     }
@@ -669,6 +715,7 @@ lbm_status lbm_ens_create(const lbm_params *params, int nboxes, void *stream, lb
         {(void **)&e->phi[0], N * sizeof(float)},    {(void **)&e->phi[1], N * sizeof(float)},
         {(void **)&e->u[0], 3 * N * sizeof(float)},  {(void **)&e->u[1], 3 * N * sizeof(float)},
         {(void **)&e->w, 3 * N * sizeof(float)},     {(void **)&e->box_d, nboxes * sizeof(EnsBox)},
+        {(void **)&e->blk_box, (size_t)e->blk_box_cap * sizeof(int)},
         {(void **)&e->sync, sizeof(tslb::EnsSync)},
         {(void **)&e->partials, (size_t)max_obs * tslb::kObsFields * sizeof(double)},
         {(void **)&e->result, tslb::kObsFields * sizeof(double)},
