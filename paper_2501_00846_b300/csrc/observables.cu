@@ -1,6 +1,8 @@
 // FP64 conservation and interface diagnostics of the state (phi, ubar, p* = sum g).
-// Pass 1: a grid-stride loop accumulates per-thread FP64 records, reduced in each block with
-// warp shuffles and a shared-memory stage; each block writes one record of kObsFields doubles.
+// Pass 1: a grid-stride loop; each thread adds its nodes' terms exactly in FP32 pairs (TwoSum /
+// TwoProduct), moves them into FP64 accumulators every 16 nodes, and counts in 64-bit integers;
+// the per-thread FP64 records are reduced in each block with warp shuffles and a shared-memory
+// stage, and each block writes one record of kObsFields doubles.
 // Pass 2: one warp sums the block records in a fixed order (deterministic result).
 #include <float.h>
 
@@ -30,6 +32,47 @@ __device__ __forceinline__ double combine(int f, double a, double b)
 }
 
 constexpr int kThreads = 256;
+constexpr int kFlush = 16;   // nodes per thread between flushes of the FP32 pair sums into FP64
+
+// Error-free FP32 accumulation: hi + lo carries a running sum whose every addition to hi is
+// exact as hi + (rounding error), the error collected in lo (Knuth's TwoSum).  Over kFlush terms
+// the sum is within about kFlush * 2^-48 of sum |terms| (Neumaier's bound), then it is added to an
+// FP64 accumulator; the FP64 pipe, about 1/60 of the FP32 rate on this GPU, then does a few
+// operations per 16 nodes instead of some forty per node.
+struct Pair {
+    float hi, lo;
+};
+
+__device__ __forceinline__ void pair_add(Pair &a, float x)
+{
+    const float s = __fadd_rn(a.hi, x);
+    const float bp = __fsub_rn(s, a.hi);
+    a.lo = __fadd_rn(a.lo, __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bp)), __fsub_rn(x, bp)));
+    a.hi = s;
+}
+
+// adds the exact product x y = p + e (TwoProduct: e = fma(x, y, -p) is exact)
+__device__ __forceinline__ void pair_add_prod(Pair &a, float x, float y)
+{
+    const float p = __fmul_rn(x, y);
+    const float e = __fmaf_rn(x, y, -p);
+    pair_add(a, p);
+    a.lo = __fadd_rn(a.lo, e);
+}
+
+// adds x c exactly for an integer coordinate c: c is exact in FP32 below 2^24, larger values are
+// split into a multiple of 4096 and the remainder, each exact
+__device__ __forceinline__ void pair_add_coord(Pair &a, float x, int c, bool big)
+{
+    if (big) {
+        pair_add_prod(a, x, (float)(c & ~4095));
+        pair_add_prod(a, x, (float)(c & 4095));
+    } else {
+        pair_add_prod(a, x, (float)c);
+    }
+}
+
+__device__ __forceinline__ double pair_value(const Pair &a) { return (double)a.hi + (double)a.lo; }
 
 __global__ void __launch_bounds__(kThreads) obs_partial_kernel(Grid G, double rho_g, double drho,
                                                                const void *__restrict__ gv, int storage,
@@ -41,9 +84,34 @@ __global__ void __launch_bounds__(kThreads) obs_partial_kernel(Grid G, double rh
     double r[F_USED];
 #pragma unroll
     for (int f = 0; f < F_USED; ++f) r[f] = 0.0;
-    r[F_PHIMIN] = DBL_MAX;
-    r[F_PHIMAX] = -DBL_MAX;
     const size_t N = (size_t)G.N;
+    const bool big = G.nx > (1 << 24) || G.ny > (1 << 24) || G.nz > (1 << 24);
+    const float rho_g32 = (float)rho_g, drho32 = (float)drho;
+
+    // FP32 pair sums since the last flush: sum phi, p*, phi x (3), phi u (3), u (3), p in the
+    // liquid and in the gas; integer counts and coordinate sums are exact in 64-bit integers
+    Pair sphi{}, sps{}, sxphi[3]{}, suphi[3]{}, su[3]{}, spl{}, spg{};
+    long long cnt = 0, nvalid = 0, nliq = 0, ngas = 0, nbad = 0, sx[3] = {0, 0, 0};
+    float umax = 0.0f, phimin = FLT_MAX, phimax = -FLT_MAX;
+    auto flush = [&]() {
+        const double vphi = pair_value(sphi);
+        r[F_SUM_PHI] += vphi;
+        r[F_MASS] += fma(drho, vphi, rho_g * (double)cnt);   // sum (rho_g + phi drho) of the flushed nodes
+        r[F_SUM_PS] += pair_value(sps);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const double vu = pair_value(su[a]), vuphi = pair_value(suphi[a]);
+            r[F_MOM + a] += fma(drho, vuphi, rho_g * vu);    // sum (rho_g + phi drho) u
+            r[F_XPHI + a] += pair_value(sxphi[a]);
+            r[F_UPHI + a] += vuphi;
+            r[F_UGAS + a] += vu;
+            sxphi[a] = Pair{}, suphi[a] = Pair{}, su[a] = Pair{};
+        }
+        r[F_PLIQ] += pair_value(spl);
+        r[F_PGAS] += pair_value(spg);
+        sphi = Pair{}, sps = Pair{}, spl = Pair{}, spg = Pair{};
+        cnt = 0;
+    };
 
     // 64-bit node index: with N close to 2^31 an int index would wrap past INT_MAX on its last
     // stride.  Inside the loop k < N < 2^31, so the coordinates come from 32-bit divisions.
@@ -53,62 +121,68 @@ __global__ void __launch_bounds__(kThreads) obs_partial_kernel(Grid G, double rh
         const int rem = kk - z * G.nxy;
         const int y = rem / G.nx;
         const int x = rem - y * G.nx;
-        double ps = 0.0;
+        float ps_hi = 0.0f, ps_lo = 0.0f;
         if (storage >= LBM_MOM) {   // moment storages: p* is the first moment array
-            ps = ((const float *)gv)[k];
+            ps_hi = ((const float *)gv)[k];
         } else if (pst) {   // 16-bit formats: p* = P + sum_i w_i h_i
             float s = pst[k];
 #pragma unroll
             for (int i = 0; i < 27; ++i) s = fmaf(wgt(i), load_h16(gv, storage, i * N + k), s);
-            ps = s;
-        } else {   // FP32 populations: an error-free FP32 sum (TwoSum; hi + lo carries p* to ~2^-46), then FP64
+            ps_hi = s;
+        } else {   // FP32 populations: an error-free FP32 sum (TwoSum; hi + lo carries p* to ~2^-46)
             const float *g = (const float *)gv;
-            float hi = 0.0f, lo = 0.0f;
+            Pair a{};
 #pragma unroll
-            for (int i = 0; i < 27; ++i) {
-                const float a = g[i * N + k];
-                const float sum = __fadd_rn(hi, a);
-                const float bp = __fsub_rn(sum, hi);
-                lo = __fadd_rn(lo, __fadd_rn(__fsub_rn(hi, __fsub_rn(sum, bp)), __fsub_rn(a, bp)));
-                hi = sum;
-            }
-            ps = (double)hi + (double)lo;
+            for (int i = 0; i < 27; ++i) pair_add(a, g[i * N + k]);
+            ps_hi = a.hi, ps_lo = a.lo;
         }
-        const double ph = phi[k];
-        const double ux = u[k], uy = u[N + k], uz = u[2 * N + k];
-        if (!(isfinite(ph) && isfinite(ux) && isfinite(uy) && isfinite(uz) && isfinite(ps))) {
-            r[F_NONFIN] += 1.0;
+        const float ph = phi[k];
+        const float ux = u[k], uy = u[N + k], uz = u[2 * N + k];
+        if (!(isfinite(ph) && isfinite(ux) && isfinite(uy) && isfinite(uz) && isfinite(ps_hi) && isfinite(ps_lo))) {
+            ++nbad;
             continue;
         }
-        const double rho = rho_g + ph * drho;
         // the (1 - phi)-weighted sums are formed at the end as (count, sum x, sum u) minus the
         // phi-weighted ones (obs_final_kernel); here F_SUM_GAS, F_XGAS, F_UGAS hold the former
-        r[F_SUM_PHI] += ph;
-        r[F_SUM_GAS] += 1.0;
-        r[F_MASS] += rho;
-        r[F_SUM_PS] += ps;
-        r[F_MOM + 0] += rho * ux;
-        r[F_MOM + 1] += rho * uy;
-        r[F_MOM + 2] += rho * uz;
-        r[F_XPHI + 0] += ph * x;
-        r[F_XPHI + 1] += ph * y;
-        r[F_XPHI + 2] += ph * z;
-        r[F_XGAS + 0] += (double)x;
-        r[F_XGAS + 1] += (double)y;
-        r[F_XGAS + 2] += (double)z;
-        r[F_UPHI + 0] += ph * ux;
-        r[F_UPHI + 1] += ph * uy;
-        r[F_UPHI + 2] += ph * uz;
-        r[F_UGAS + 0] += ux;
-        r[F_UGAS + 1] += uy;
-        r[F_UGAS + 2] += uz;
-        const double p = ps * rho * (1.0 / 3.0);
-        if (ph > 0.999) { r[F_PLIQ] += p; r[F_NLIQ] += 1.0; }
-        if (ph < 0.001) { r[F_PGAS] += p; r[F_NGAS] += 1.0; }
-        r[F_UMAX] = fmax(r[F_UMAX], sqrt(ux * ux + uy * uy + uz * uz));
-        r[F_PHIMIN] = fmin(r[F_PHIMIN], ph);
-        r[F_PHIMAX] = fmax(r[F_PHIMAX], ph);
+        pair_add(sphi, ph);
+        pair_add(sps, ps_hi);
+        sps.lo = __fadd_rn(sps.lo, ps_lo);
+        pair_add_coord(sxphi[0], ph, x, big);
+        pair_add_coord(sxphi[1], ph, y, big);
+        pair_add_coord(sxphi[2], ph, z, big);
+        sx[0] += x, sx[1] += y, sx[2] += z;
+        pair_add_prod(suphi[0], ph, ux);
+        pair_add_prod(suphi[1], ph, uy);
+        pair_add_prod(suphi[2], ph, uz);
+        pair_add(su[0], ux);
+        pair_add(su[1], uy);
+        pair_add(su[2], uz);
+        // pressure p = p* rho cs^2 for the phase means (an FP32 product: a diagnostic of the bulk).
+        // The phases are phi > 0.999 and phi < 0.001: 0.999f is the least float above 0.999 and
+        // 0.001f the least float above 0.001, so these FP32 tests select the same nodes.
+        const bool liq = ph >= 0.999f, gas = ph < 0.001f;
+        if (liq || gas) {
+            const float p = __fadd_rn(ps_hi, ps_lo) * fmaf(ph, drho32, rho_g32) * (1.0f / 3.0f);
+            if (liq) pair_add(spl, p), ++nliq;
+            else pair_add(spg, p), ++ngas;
+        }
+        umax = fmaxf(umax, sqrtf(fmaf(ux, ux, fmaf(uy, uy, uz * uz))));
+        phimin = fminf(phimin, ph);
+        phimax = fmaxf(phimax, ph);
+        ++nvalid;
+        if (++cnt == kFlush) flush();
     }
+    flush();
+    r[F_SUM_GAS] = (double)nvalid;
+    r[F_XGAS + 0] = (double)sx[0];
+    r[F_XGAS + 1] = (double)sx[1];
+    r[F_XGAS + 2] = (double)sx[2];
+    r[F_NLIQ] = (double)nliq;
+    r[F_NGAS] = (double)ngas;
+    r[F_NONFIN] = (double)nbad;
+    r[F_UMAX] = umax;
+    r[F_PHIMIN] = nvalid ? (double)phimin : DBL_MAX;
+    r[F_PHIMAX] = nvalid ? (double)phimax : -DBL_MAX;
 
     // warp stage
 #pragma unroll
