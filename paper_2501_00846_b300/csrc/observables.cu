@@ -3,7 +3,7 @@
 // TwoProduct), moves them into FP64 accumulators every 16 nodes, and counts in 64-bit integers;
 // the per-thread FP64 records are reduced in each block with warp shuffles and a shared-memory
 // stage, and each block writes one record of kObsFields doubles.
-// Pass 2: one warp sums the block records in a fixed order (deterministic result).
+// Pass 2: one warp per field sums the block records in a fixed order (deterministic result).
 #include <float.h>
 
 #include "tslb_internal.h"
@@ -204,22 +204,27 @@ __global__ void __launch_bounds__(kThreads) obs_partial_kernel(Grid G, double rh
     }
 }
 
-__global__ void obs_final_kernel(const double *__restrict__ partials, int nblocks, double *__restrict__ out)
+// Pass 2: one warp per record field.  Lane l combines the records of blocks l, l + 32, l + 64, ...
+// in that order, then the 32 lane values meet in a fixed shuffle tree: the same order, and so the
+// same bits, for a given block count.
+__global__ void __launch_bounds__(F_USED * 32) obs_final_kernel(const double *__restrict__ partials, int nblocks,
+                                                               double *__restrict__ out)
 {
     __shared__ double tot[F_USED];
-    const int f = threadIdx.x;
-    if (f < F_USED) {
-        double acc = partials[f];
-        for (int b = 1; b < nblocks; ++b) acc = combine(f, acc, partials[(size_t)b * kObsFields + f]);
-        tot[f] = acc;
-    }
-    __syncwarp();
-    if (f >= F_USED) return;
-    double v = tot[f];   // (1 - phi)-weighted sums: (count, sum x, sum u) minus the phi-weighted ones
-    if (f == F_SUM_GAS) v -= tot[F_SUM_PHI];
-    if (f >= F_XGAS && f < F_XGAS + 3) v -= tot[F_XPHI + f - F_XGAS];
-    if (f >= F_UGAS && f < F_UGAS + 3) v -= tot[F_UPHI + f - F_UGAS];
-    out[f] = v;
+    const int f = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    double acc = f == F_PHIMIN ? DBL_MAX : (f == F_UMAX || f == F_PHIMAX) ? -DBL_MAX : 0.0;
+    for (int b = lane; b < nblocks; b += 32) acc = combine(f, acc, partials[(size_t)b * kObsFields + f]);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) acc = combine(f, acc, __shfl_down_sync(0xffffffffu, acc, off));
+    if (lane == 0) tot[f] = acc;
+    __syncthreads();
+    if (threadIdx.x >= F_USED) return;
+    const int g = threadIdx.x;
+    double v = tot[g];   // (1 - phi)-weighted sums: (count, sum x, sum u) minus the phi-weighted ones
+    if (g == F_SUM_GAS) v -= tot[F_SUM_PHI];
+    if (g >= F_XGAS && g < F_XGAS + 3) v -= tot[F_XPHI + g - F_XGAS];
+    if (g >= F_UGAS && g < F_UGAS + 3) v -= tot[F_UPHI + g - F_UGAS];
+    out[g] = v;
 }
 
 }  // namespace
@@ -235,7 +240,7 @@ cudaError_t launch_observables(const Grid &G, double rho_l, double rho_g, const 
                                int storage, const float *pst)
 {
     obs_partial_kernel<<<nblocks, kThreads, 0, s>>>(G, rho_g, rho_l - rho_g, g, storage, pst, phi, u, partials);
-    obs_final_kernel<<<1, 32, 0, s>>>(partials, nblocks, result);
+    obs_final_kernel<<<1, F_USED * 32, 0, s>>>(partials, nblocks, result);
     return cudaGetLastError();
 }
 
