@@ -427,6 +427,20 @@ lbm_status lbm_closure_target(lbm_ctx *ctx, const float *ref, const lbm_closure_
  * Asynchronous on the context's stream. */
 lbm_status lbm_closure_apply(lbm_ctx *ctx, lbm_cnn *cnn, const lbm_closure_norm *norm);
 
+/* Set the state of a fine context to the 2x prolongation of a coarse context's state: the
+ * fallback of a corrected coarse run to the fine solver (the library's own addition for the
+ * learned closure; the paper has no counterpart).  Both contexts: initialised, FP32 populations;
+ * the fine box is twice the coarse box in every direction with the same walls (its parameters,
+ * rescaled for the fine grid, are the caller's).  Cell-centred trilinear interpolation: fine node X
+ * of coarse cell X / 2 takes 3/4 of that cell and 1/4 of the neighbour it lies towards along each
+ * axis (periodic axes wrap; beyond a z wall the wall cell itself), applied to the 27 populations,
+ * phi and ubar alike: the fine sums of phi, ubar and every population (so of p* and of the
+ * populations' first moment) are 8 times the coarse ones.
+ * Enqueued on the fine context's stream after the coarse context's pending work; the fine
+ * context's step count is not changed.  LBM_ERR_ARG for mismatched boxes or storages,
+ * LBM_ERR_STATE for an uninitialised context. */
+lbm_status lbm_prolong2_state(lbm_ctx *coarse, lbm_ctx *fine);
+
 /* 2x restriction of a fine state to the coarse grid (device arrays, channel-first): phi and p
  * averaged over the 8 fine nodes of a coarse cell, u averaged with weight rho(phi), and
  * p* = 3 p / rho(phi).  phi, p: N floats; u: 3N; out: 6 N/8 floats (phi, u_x, u_y, u_z, p, p*).

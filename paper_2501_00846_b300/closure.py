@@ -229,6 +229,86 @@ def evaluate(net, norm, col, coarse_steps=240, every=24, stream=None, apply_ever
     return out
 
 
+# Checks of a corrected coarse state (coarse lattice units): no non-finite value, phi inside
+# [phi_min, phi_max], max |u| below umax (far below the lattice speed of sound), and sum phi within
+# a relative sum_phi_drift of the start (the correction conserves it; a drift means trouble).
+DEFAULT_LIMITS = {"phi_min": -0.1, "phi_max": 1.1, "umax": 0.2, "sum_phi_drift": 1e-3}
+
+
+def failed_checks(obs, obs0, limits=None):
+    """Reasons why the state with observables obs fails the checks (empty when it passes); obs0:
+    the observables of the run's first state."""
+    lim = dict(DEFAULT_LIMITS, **(limits or {}))
+    bad = []
+    if obs["n_nonfinite"] > 0:
+        bad.append(f"{obs['n_nonfinite']:.0f} non-finite nodes")
+        return bad
+    if obs["phi_min"] < lim["phi_min"] or obs["phi_max"] > lim["phi_max"]:
+        bad.append(f"phi in [{obs['phi_min']:.4f}, {obs['phi_max']:.4f}]")
+    if obs["umax"] > lim["umax"]:
+        bad.append(f"max |u| {obs['umax']:.4f}")
+    if abs(obs["sum_phi"] - obs0["sum_phi"]) > lim["sum_phi_drift"] * abs(obs0["sum_phi"]):
+        bad.append(f"sum phi drifted by {obs['sum_phi'] / obs0['sum_phi'] - 1:.2e}")
+    return bad
+
+
+def run_with_fallback(net, norm, col, coarse_steps=240, check_every=24, apply_every=8, limits=None, stream=None):
+    """The corrected coarse run of collision `col`, with the plain fine solver as its fallback.
+
+    The run starts from the collision's fine initial state restricted 2x and applies the network
+    after every `apply_every` coarse steps.  Every `check_every` coarse steps (and at the end) the
+    state is checked (failed_checks); a state that passes is kept on the device as the checkpoint.
+    When a check fails, the run returns to the last checkpoint, prolongs it 2x to the fine grid
+    (lbm_prolong2_state) and finishes the remaining time with the plain fine solver, two fine steps
+    per coarse step.  Returns (record, solver): the record holds every check and, after a
+    fallback, the step it was detected at and the step the fine run restarted from; the solver is
+    the context holding the final state (the coarse one, or the fine one after a fallback), owned
+    by the caller."""
+    import torch
+    stream = stream or torch.cuda.current_stream()
+    L = solver.load()
+    with torch.cuda.stream(stream):
+        ens = solver.Ensemble([col.params()], stream=stream)
+        phi, u, ps = col.fields()
+        ens.init_fields(0, _f32(phi), _f32(u), _f32(ps))
+        corr = _coarse_context(col, stream)
+        ens.restrict_state(0, corr)
+        ens.close()
+        n = corr.n
+        ck = (torch.empty(27 * n, device="cuda"), torch.empty(n, device="cuda"), torch.empty(3 * n, device="cuda"))
+
+        def checkpoint():
+            solver._check(L.lbm_get_state(corr._ctx, ck[0].data_ptr(), ck[1].data_ptr(), ck[2].data_ptr(), 1))
+
+        checkpoint()
+        ck_step = 0
+        obs0 = corr.observables(allow_nonfinite=True)
+        record = {"checks": [], "fallback": None, "final": "coarse", "coarse_steps": coarse_steps}
+        for k in range(1, coarse_steps + 1):
+            corr.step(1)
+            if k % apply_every == 0:
+                solver.closure_apply(corr, net, norm)
+            if k % check_every and k != coarse_steps:
+                continue
+            bad = failed_checks(corr.observables(allow_nonfinite=True), obs0, limits)
+            record["checks"].append({"step": k, "failed": bad})
+            if not bad:
+                checkpoint()
+                ck_step = k
+                continue
+            # fallback: the last checkpoint, prolonged to the fine grid, finishes the run
+            corr.set_state(*ck, step=ck_step)
+            fine = solver.Solver(stream=stream, **col.params())
+            fine.init_fields(np.zeros(fine.n, np.float32), np.zeros(3 * fine.n, np.float32))
+            solver.prolong2_state(corr, fine)
+            corr.close()
+            fine.step(2 * (coarse_steps - ck_step))
+            record["fallback"] = {"detected_at": k, "restart_from": ck_step, "fine_steps": 2 * (coarse_steps - ck_step)}
+            record["final"] = "fine"
+            return record, fine
+    return record, corr
+
+
 def _block_mean(a, f):
     """Mean over f x f x f blocks of the last three axes."""
     *lead, nz, ny, nx = a.shape

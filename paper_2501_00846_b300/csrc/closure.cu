@@ -1266,6 +1266,54 @@ __global__ void restrict2_kernel(int nx, int ny, int nz, const float *__restrict
     out[(size_t)5 * Nc + kc] = 3.0f * pc / fmaf(phc, drho, rho_g);
 }
 
+// Cell-centred 2x prolongation of a coarse state to the fine grid (the fallback from the corrected
+// coarse run to the fine solver).  Fine index X of coarse cell i = X / 2 lies a quarter of a coarse
+// cell from that cell's centre, towards the neighbour i - 1 (X even) or i + 1 (X odd), so along each
+// axis it takes 3/4 of cell i and 1/4 of that neighbour; the 8 products of the three axes' weights
+// (27/64, 9/64, 3/64, 1/64) are exact in FP32 and added in a fixed order.  Periodic axes wrap; at a
+// z wall the neighbour beyond the wall is the wall cell itself (the mirror image of cell-centred
+// values).  The sum over the fine nodes is 8 times the sum over the coarse cells for every field,
+// and every field is interpolated the same way: the 27 populations (so p* and their first moment
+// keep their sums too), phi and ubar.
+__device__ __forceinline__ int prolong_nbr(int X, int n, bool clamp)
+{
+    const int i = X >> 1, j = (X & 1) ? i + 1 : i - 1;
+    if (j < 0) return clamp ? 0 : n - 1;
+    if (j >= n) return clamp ? n - 1 : 0;
+    return j;
+}
+
+__global__ void prolong2_kernel(Grid C, const float *__restrict__ gc, const float *__restrict__ phic,
+                                const float *__restrict__ uc, Grid F, float *__restrict__ gf,
+                                float *__restrict__ phif, float *__restrict__ uf)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= F.N) return;
+    const int Z = k / F.nxy, rem = k - Z * F.nxy, Y = rem / F.nx, X = rem - Y * F.nx;
+    const int ix[2] = {X >> 1, prolong_nbr(X, C.nx, false)};
+    const int iy[2] = {Y >> 1, prolong_nbr(Y, C.ny, false)};
+    const int iz[2] = {Z >> 1, prolong_nbr(Z, C.nz, C.wall != 0)};
+    int off[8];
+    float wt[8];
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+        const int a = c & 1, b = (c >> 1) & 1, d = c >> 2;
+        off[c] = (iz[d] * C.ny + iy[b]) * C.nx + ix[a];
+        wt[c] = (a ? 0.25f : 0.75f) * (b ? 0.25f : 0.75f) * (d ? 0.25f : 0.75f);
+    }
+    const size_t NC = (size_t)C.N, NF = (size_t)F.N;
+    auto interp = [&](const float *src) {
+        float v = 0.0f;
+#pragma unroll
+        for (int c = 0; c < 8; ++c) v = fmaf(wt[c], src[off[c]], v);
+        return v;
+    };
+    for (int i = 0; i < 27; ++i) gf[i * NF + k] = interp(gc + i * NC);
+    phif[k] = interp(phic);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) uf[a * NF + k] = interp(uc + a * NC);
+}
+
 }  // namespace
 }  // namespace tslb
 
@@ -1875,6 +1923,30 @@ lbm_status lbm_closure_apply(lbm_ctx *ctx, lbm_cnn *cnn, const lbm_closure_norm 
     tslb::correct_kernel<<<(N + 255) / 256, 256, 0, v.stream>>>(v.G, cnn->ybuf, *norm, cnn->dsum, v.g, v.phi, v.u);
     CNN_TRY(cudaGetLastError());
     tslb::ctx_state_changed(ctx);
+    return LBM_OK;
+}
+
+lbm_status lbm_prolong2_state(lbm_ctx *coarse, lbm_ctx *fine)
+{
+    if (!coarse || !fine || coarse == fine) return cnn_fail(LBM_ERR_ARG, "two distinct contexts are required");
+    tslb::CtxView c, f;
+    lbm_status st = tslb::ctx_view(coarse, &c);
+    if (st != LBM_OK) return st;
+    if ((st = tslb::ctx_view(fine, &f)) != LBM_OK) return st;
+    if (c.storage != LBM_FP32 || f.storage != LBM_FP32) return cnn_fail(LBM_ERR_ARG, "both contexts need FP32 populations");
+    if (f.G.nx != 2 * c.G.nx || f.G.ny != 2 * c.G.ny || f.G.nz != 2 * c.G.nz || f.G.wall != c.G.wall)
+        return cnn_fail(LBM_ERR_ARG, "fine box %dx%dx%d must be twice the coarse box %dx%dx%d with the same walls",
+                        f.G.nx, f.G.ny, f.G.nz, c.G.nx, c.G.ny, c.G.nz);
+    // the fine stream waits for the coarse context's pending work
+    cudaEvent_t ev;
+    CNN_TRY(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    cudaError_t err = cudaEventRecord(ev, c.stream);
+    if (err == cudaSuccess) err = cudaStreamWaitEvent(f.stream, ev, 0);
+    cudaEventDestroy(ev);
+    if (err != cudaSuccess) return cnn_fail(LBM_ERR_CUDA, "stream ordering failed: %s", cudaGetErrorString(err));
+    tslb::prolong2_kernel<<<(f.G.N + 255) / 256, 256, 0, f.stream>>>(c.G, c.g, c.phi, c.u, f.G, f.g, f.phi, f.u);
+    CNN_TRY(cudaGetLastError());
+    tslb::ctx_state_changed(fine);
     return LBM_OK;
 }
 

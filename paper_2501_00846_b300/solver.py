@@ -155,6 +155,7 @@ def load(path: str = LIB_PATH):
         "lbm_closure_target": ([vp, fp, ctypes.POINTER(LbmClosureNorm), fp], i),
         "lbm_closure_apply": ([vp, vp, ctypes.POINTER(LbmClosureNorm)], i),
         "lbm_restrict2": ([fp, fp, fp, i, i, i, ctypes.c_double, ctypes.c_double, fp, vp], i),
+        "lbm_prolong2_state": ([vp, vp], i),
     }
     for name, (args, res) in sigs.items():
         fn = getattr(L, name)
@@ -566,3 +567,8 @@ def restrict2(phi, u, p, nx, ny, nz, rho_l, rho_g, out, stream=None):
     st = (stream or torch.cuda.current_stream()).cuda_stream
     _check(load().lbm_restrict2(_dev(phi, n), _dev(u, 3 * n), _dev(p, n), nx, ny, nz, float(rho_l), float(rho_g),
                                 _dev(out, 6 * (n // 8)), st))
+
+
+def prolong2_state(coarse: "Solver", fine: "Solver"):
+    """Set fine's state to the 2x cell-centred prolongation of coarse's (lbm_prolong2_state)."""
+    _check(load().lbm_prolong2_state(coarse._ctx, fine._ctx))
