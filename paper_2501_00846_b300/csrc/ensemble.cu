@@ -410,6 +410,7 @@ struct lbm_ens {
     int ac_bps[2] = {0, 0};           // resident Allen–Cahn CTAs per SM, ac_rows 2 and 4
     int lbm_blocks = 0, ac_tasks = 0, ac_ctas = 0;
     cudaGraphExec_t exec = nullptr;   // graph_steps steps from cur = 0
+    cudaGraphExec_t pexec = nullptr;  // graph_steps persistent launches from cur = 0
     int persistent = 0;               // 1: one cooperative launch per step (ens_persistent_kernel)
     int pers_ctas[2] = {0, 0};        // co-resident CTAs of the persistent kernel, ac_rows 2 and 4
     tslb::EnsSync *sync = nullptr;    // barrier state of the persistent kernel
@@ -422,6 +423,7 @@ void free_ens(lbm_ens *e)
 {
     if (!e) return;
     if (e->exec) cudaGraphExecDestroy(e->exec);
+    if (e->pexec) cudaGraphExecDestroy(e->pexec);
     for (int b = 0; b < 2; ++b) {
         cudaFree(e->g[b]);
         cudaFree(e->phi[b]);
@@ -484,6 +486,10 @@ lbm_status build_tables(lbm_ens *e)
     if (e->exec) {
         cudaGraphExecDestroy(e->exec);
         e->exec = nullptr;
+    }
+    if (e->pexec) {
+        cudaGraphExecDestroy(e->pexec);
+        e->pexec = nullptr;
     }
     return LBM_OK;
 }
@@ -588,11 +594,25 @@ cudaError_t ens_persistent_setup(lbm_ens *e)
 // Persistent steps: one cooperative launch each, then the barrier record is read.  Returns the
 // steps completed; *timed_out when a barrier wait expired (the state is that of the last
 // completed step, its flux W recomputed, and the record reset).
+lbm_status build_persistent_graph(lbm_ens *e);
+
 lbm_status ens_persistent_run(lbm_ens *e, int nsteps)
 {
-    for (int k = 0; k < nsteps; ++k) {
+    const int K = e->tun.graph_steps;
+    for (int k = 0; k < nsteps;) {
         const int a = e->cur ^ (k & 1);
-        ENS_TRY(e->tun.ac_rows == 2 ? ens_persistent_step<2>(e, a, e->stream) : ens_persistent_step<4>(e, a, e->stream));
+        if (K >= 2 && a == 0 && nsteps - k >= K) {   // K launches from buffers 0, replayed from a graph
+            if (!e->pexec) {
+                lbm_status st = build_persistent_graph(e);
+                if (st != LBM_OK) return st;
+            }
+            ENS_TRY(cudaGraphLaunch(e->pexec, e->stream));
+            k += K;
+        } else {
+            ENS_TRY(e->tun.ac_rows == 2 ? ens_persistent_step<2>(e, a, e->stream)
+                                        : ens_persistent_step<4>(e, a, e->stream));
+            ++k;
+        }
     }
     tslb::EnsSync h;
     ENS_TRY(cudaMemcpyAsync(&h, e->sync, sizeof h, cudaMemcpyDeviceToHost, e->stream));
@@ -634,6 +654,31 @@ lbm_status build_graph(lbm_ens *e)
     if (err != cudaSuccess) {
         e->exec = nullptr;
         return ens_fail(LBM_ERR_CUDA, "graph instantiation failed: %s", cudaGetErrorString(err));
+    }
+    return LBM_OK;
+}
+
+// Capture graph_steps persistent launches (one per step) starting from buffers 0 on the private
+// stream.  A launch that finds the barrier record set returns at once, so a replay after an
+// expired wait keeps the state of the last completed step, as direct launches do.
+lbm_status build_persistent_graph(lbm_ens *e)
+{
+    cudaGraph_t graph = nullptr;
+    ENS_TRY(cudaStreamBeginCapture(e->cap, cudaStreamCaptureModeThreadLocal));
+    cudaError_t err = cudaSuccess;
+    for (int k = 0; k < e->tun.graph_steps && err == cudaSuccess; ++k)
+        err = e->tun.ac_rows == 2 ? ens_persistent_step<2>(e, k & 1, e->cap) : ens_persistent_step<4>(e, k & 1, e->cap);
+    cudaError_t end = cudaStreamEndCapture(e->cap, &graph);
+    if (err != cudaSuccess || end != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        return ens_fail(LBM_ERR_CUDA, "persistent graph capture failed: %s",
+                        cudaGetErrorString(err != cudaSuccess ? err : end));
+    }
+    err = cudaGraphInstantiate(&e->pexec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (err != cudaSuccess) {
+        e->pexec = nullptr;
+        return ens_fail(LBM_ERR_CUDA, "persistent graph instantiation failed: %s", cudaGetErrorString(err));
     }
     return LBM_OK;
 }

@@ -221,7 +221,9 @@ def test_persistent_step_equals_boxes_run_alone(mixed, store):
             with solver.from_workload(wl, storage=store) as s:
                 s.step(21)
                 ref.append(s.read_fields())
-    for tuning in ({}, dict(lbm_block=64, ac_rows=2, ac_zlen=8)):
+    # the default tuning (13 and 8 steps: direct launches), another tuning, and 4-step graphs of
+    # persistent launches (replayed for steps 1-12 and 15-18)
+    for tuning in ({}, dict(lbm_block=64, ac_rows=2, ac_zlen=8), dict(graph_steps=4)):
         with solver.ensemble_from_workloads(wls, storage=store) as e:
             if tuning:
                 e.set_tuning(**tuning)
@@ -233,13 +235,17 @@ def test_persistent_step_equals_boxes_run_alone(mixed, store):
         _assert_same(got, ref, f"persistent {store} {tuning}")
 
 
-def test_persistent_barrier_expiry_is_reported_and_the_ensemble_recovers(mixed):
+@pytest.mark.parametrize("graph_steps", [16, 2], ids=["direct", "graph"])
+def test_persistent_barrier_expiry_is_reported_and_the_ensemble_recovers(mixed, graph_steps):
     """The grid barrier's waits are bounded.  The test hook keeps CTA 0 from arriving and cuts the
     limit to 2 ms: every wait expires, lbm_ens_step returns LBM_ERR_TIMEOUT, no step is counted and
     the fields are those of the last completed step; with the hook off the ensemble steps on and
-    ends exactly where an undisturbed run ends."""
+    ends exactly where an undisturbed run ends.  With graph_steps = 2 the persistent launches are
+    replayed from 2-step graphs, the stalled call's first two included."""
     wls, ref = mixed
     with solver.ensemble_from_workloads(wls) as e:
+        if graph_steps != 16:
+            e.set_tuning(graph_steps=graph_steps)
         e.set_persistent(True)
         e.step(10)
         before = [e.read_fields(b) for b in range(len(wls))]
