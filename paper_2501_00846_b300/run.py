@@ -2,10 +2,13 @@
 
     python -m paper_2501_00846_b300.run --workload rising_bubble --steps 2000 --every 500
     python -m paper_2501_00846_b300.run --workload droplet256 --storage bf16 --steps 100
+    python -m paper_2501_00846_b300.run --workload ensemble32 --steps 100
 
 Workloads: ``rising_bubble`` (128 x 128 x 256, walls on z, density ratio 1000, viscosity ratio
 100, Eo = 10, Mo = 1e-4), ``dropletL`` (static droplet in a periodic L^3 box, R = L/4, density
-and viscosity ratio 10, sigma = 0.01).  Everything runs on the current CUDA device through the
+and viscosity ratio 10, sigma = 0.01), ``ensembleN`` (the first N boxes of the batched ensemble of
+seeded uneven droplets, inputs.droplet_ensemble, advanced together with the default launch
+tuning; diagnostics of every box).  Everything runs on the current CUDA device through the
 C ABI; the process fails if the CUDA library is missing.  Also the launch driver of the
 committed ncu summaries (a fixed, small number of steps of one workload).
 """
@@ -44,6 +47,8 @@ def main(argv=None) -> int:
     if not torch.cuda.is_available():
         raise SystemExit("no CUDA device")
     torch.cuda.set_device(0)
+    if a.workload.startswith("ensemble"):
+        return run_ensemble(a)
     wl = workload(a.workload)
     s = solver.from_workload(wl, storage=STORAGE[a.storage])
     try:
@@ -63,6 +68,31 @@ def main(argv=None) -> int:
                 return 1
     finally:
         s.close()
+    return 0
+
+
+def run_ensemble(a) -> int:
+    """The first N boxes of inputs.droplet_ensemble() in one ensemble; diagnostics of every box."""
+    n = int(a.workload[len("ensemble"):])
+    wls = inputs.droplet_ensemble()[:n]
+    e = solver.ensemble_from_workloads(wls, storage=STORAGE[a.storage])
+    try:
+        every = a.every if a.every > 0 else max(a.steps, 1)
+        done = 0
+        while done < a.steps:
+            k = min(every, a.steps - done)
+            e.step(k)
+            done += k
+            bad = 0
+            for b in range(n):
+                o = e.observables(b, allow_nonfinite=True)
+                bad += o["n_nonfinite"] > 0
+            print(json.dumps({"workload": a.workload, "storage": a.storage, "step": done, "boxes": n,
+                              "nodes": int(e.n), "boxes_nonfinite": int(bad)}), flush=True)
+            if bad:
+                return 1
+    finally:
+        e.close()
     return 0
 
 
