@@ -62,7 +62,8 @@ class Params:
     body: tuple = (0.0, 0.0, 0.0)
     advect: int = 0          # 0: flux form div(ubar phi) (reading R4); 1: literal ubar . grad(phi)
     literal_weight: int = 0  # 0: sharpening weight max(phi (1 - phi), 0) (reading R15); 1: phi (1 - phi)
-    storage16: int = 0       # 0: FP64 populations; 1 / 2: the library's BF16 / FP16 deviation storage, emulated
+    storage16: int = 0       # 0: FP64 populations; 1 / 2: the library's BF16 / FP16 deviation storage, emulated;
+                             # 3 / 4: its BF16 / FP16 deviation-moment storage, emulated
 
     @property
     def shape(self):
@@ -112,6 +113,9 @@ def lib():
         L.oracle_run.argtypes = [pp, ctypes.c_int, dp, dp, dp]
         L.oracle_pressure.argtypes = [pp, dp, dp, dp]
         L.oracle_store16_node.argtypes = [ctypes.c_int, dp, dp, dp, dp, dp]
+        L.oracle_mom_extract.argtypes = [dp, dp, dp, dp, dp]
+        L.oracle_mom_rebuild.argtypes = [ctypes.c_double, dp, dp, dp, dp]
+        L.oracle_store_mom16_node.argtypes = [ctypes.c_int, dp, dp, dp, dp]
         _lib = L
     return _lib
 
@@ -201,6 +205,32 @@ def store16_node(fmt: int, g, u):
     hr, gout = np.zeros(Q), np.zeros(Q)
     lib().oracle_store16_node(int(fmt), _p(g), _p(u), ctypes.byref(P_out), _p(hr), _p(gout))
     return P_out.value, hr, gout
+
+
+def mom_extract(g, u):
+    """(p*, a[3], B[3,3]) of one node's populations g with velocity u (the moment storage's set)."""
+    g, u = _f64(g), _f64(u)
+    ps = ctypes.c_double()
+    a, B = np.zeros(3), np.zeros(9)
+    lib().oracle_mom_extract(_p(g), _p(u), ctypes.byref(ps), _p(a), _p(B))
+    return ps.value, a, B.reshape(3, 3)
+
+
+def mom_rebuild(ps: float, u, a, B):
+    """The populations [27] of the moment set (p*, u, a, B)."""
+    u, a, B = _f64(u), _f64(a), _f64(np.asarray(B).reshape(9))
+    g = np.zeros(Q)
+    lib().oracle_mom_rebuild(float(ps), _p(u), _p(a), _p(B), _p(g))
+    return g
+
+
+def store_mom16_node(fmt: int, g, u):
+    """The library's 16-bit moment storage of one node (fmt 1 BF16, 2 FP16): the rounded
+    (a_x, a_y, a_z, B_xx, B_yy, B_zz, B_xy, B_xz, B_yz) and the populations they represent."""
+    g, u = _f64(g), _f64(u)
+    ab, gout = np.zeros(9), np.zeros(Q)
+    lib().oracle_store_mom16_node(int(fmt), _p(g), _p(u), _p(ab), _p(gout))
+    return ab, gout
 
 
 def force_node(P: Params, f, phi: float, gphi, lphi: float, ubar):

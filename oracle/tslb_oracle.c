@@ -53,8 +53,10 @@
  *       printed phi (1 - phi) everywhere, to measure how far the reading moves the results.
  *
  * Not from the paper: storage16 = 1 / 2 emulates the library's 16-bit population storage (its
- * precision form, BF16 / FP16 deviations from equilibrium; store16 below), so that the tests know
- * each case's 16-bit effect from the oracle alone.  storage16 = 0 (the default) is the method.
+ * precision form, BF16 / FP16 deviations from equilibrium; store16 below), and storage16 = 3 / 4
+ * its 16-bit moment storage (BF16 / FP16 deviation moments a and B; store_mom16 below), so that
+ * the tests know each case's 16-bit effect from the oracle alone.  storage16 = 0 (the default) is
+ * the method.
  */
 #include <math.h>
 #include <stdint.h>
@@ -80,7 +82,8 @@ typedef struct {
     double body[3];        /* uniform body-force density */
     int advect;            /* 0: flux form div(ubar phi); 1: literal form ubar . grad(phi) */
     int literal_weight;    /* 0: sharpening weight max(phi (1 - phi), 0) (R15); 1: phi (1 - phi) as printed */
-    int storage16;         /* 0: FP64 populations; 1 / 2: the library's BF16 / FP16 deviation storage (store16) */
+    int storage16;         /* 0: FP64 populations; 1 / 2: the library's BF16 / FP16 deviation storage (store16);
+                              3 / 4: its BF16 / FP16 deviation moments (store_mom16) */
 } oracle_params;
 
 /* ------------------------------------------------------------------------------------------ */
@@ -521,6 +524,88 @@ static void store16(int fmt, double g[Q], const double u[3])
     oracle_store16_node(fmt, g, u, &Pv, hr, g);
 }
 
+/* ------------------------------------------------------------------------------------------ */
+/* The library's 16-bit moment storage, emulated (not in the paper: its moment-only storage with */
+/* a and B in BF16 / FP16).  After a collision a node's populations are a polynomial in c of its  */
+/* p*, u, the acceleration a they carry and the non-equilibrium second moment B; the storage      */
+/* keeps p* and u and rounds a and B.  The moments of the populations give the set back:          */
+/*   sum g = p*,   sum g c = u + a / 2,                                                           */
+/*   sum g c c = p* I / 3 + (2/9) (B + 4.5 u u + 4.5 sym(u a)),  sym(u a)_ab = (u_a a_b + u_b a_a)/2 */
+/* and the polynomial, per unit weight, with cu = c.u, ca = c.a, cBc = c B c, is                  */
+/*   g_i / w_i = K0 + 4.5 cu (cu + ca) + cBc + cu (K1 + 4.5 cu^2 + 3 cBc) + c.v,                  */
+/*   K0 = p* - 1.5 u^2 - 1.5 u.a - tr B / 3,  K1 = 3 - 4.5 u^2 - tr B,  v = 1.5 a - 2 B u,         */
+/* the third-order equilibrium of (p*, u), plus the Guo source for a, plus the regularised        */
+/* non-equilibrium of B (its Hermite-2 and Hermite-3 parts).  The tests pin both directions       */
+/* against the collision (mom_rebuild of mom_extract returns the collided populations).           */
+/* ------------------------------------------------------------------------------------------ */
+void oracle_mom_extract(const double g[Q], const double u[3], double *ps_out, double a[3], double B[9])
+{
+    build_lattice();
+    double ps = 0.0, j[3] = {0, 0, 0}, Pi[3][3] = {{0}};
+    for (int i = 0; i < Q; ++i) {
+        ps += g[i];
+        for (int x = 0; x < 3; ++x) {
+            j[x] += g[i] * C[i][x];
+            for (int y = 0; y < 3; ++y) Pi[x][y] += g[i] * C[i][x] * C[i][y];
+        }
+    }
+    for (int x = 0; x < 3; ++x) a[x] = 2.0 * (j[x] - u[x]);
+    for (int x = 0; x < 3; ++x)
+        for (int y = 0; y < 3; ++y) {
+            const double T = 4.5 * (Pi[x][y] - (x == y ? ps * CS2 : 0.0));
+            B[3 * x + y] = T - 4.5 * u[x] * u[y] - 2.25 * (u[x] * a[y] + u[y] * a[x]);
+        }
+    *ps_out = ps;
+}
+
+void oracle_mom_rebuild(double ps, const double u[3], const double a[3], const double B[9], double g[Q])
+{
+    build_lattice();
+    double u2 = 0.0, ua = 0.0, trB = 0.0, v[3];
+    for (int x = 0; x < 3; ++x) {
+        u2 += u[x] * u[x];
+        ua += u[x] * a[x];
+        trB += B[3 * x + x];
+    }
+    for (int x = 0; x < 3; ++x) {
+        double Bu = 0.0;
+        for (int y = 0; y < 3; ++y) Bu += B[3 * x + y] * u[y];
+        v[x] = 1.5 * a[x] - 2.0 * Bu;
+    }
+    const double K0 = ps - 1.5 * u2 - 1.5 * ua - trB / 3.0;
+    const double K1 = 3.0 - 4.5 * u2 - trB;
+    for (int i = 0; i < Q; ++i) {
+        double cu = 0.0, ca = 0.0, cv = 0.0, cBc = 0.0;
+        for (int x = 0; x < 3; ++x) {
+            cu += C[i][x] * u[x];
+            ca += C[i][x] * a[x];
+            cv += C[i][x] * v[x];
+            for (int y = 0; y < 3; ++y) cBc += C[i][x] * B[3 * x + y] * C[i][y];
+        }
+        const double E = K0 + 4.5 * cu * (cu + ca) + cBc;
+        const double O = cu * (K1 + 4.5 * cu * cu + 3.0 * cBc) + cv;
+        g[i] = Wt[i] * (E + O);
+    }
+}
+
+/* One node: the rounded deviation moments ab_out = (a_x, a_y, a_z, B_xx, B_yy, B_zz, B_xy, B_xz,
+   B_yz) that the 16-bit moment storage (fmt 1 BF16, 2 FP16) keeps for populations g with
+   velocity u, and the populations they represent (gout; may alias g). */
+void oracle_store_mom16_node(int fmt, const double g[Q], const double u[3], double ab_out[9], double gout[Q])
+{
+    double ps, a[3], B[9];
+    oracle_mom_extract(g, u, &ps, a, B);
+    for (int x = 0; x < 3; ++x) a[x] = round16(fmt, a[x]);
+    static const int pair[6][2] = {{0, 0}, {1, 1}, {2, 2}, {0, 1}, {0, 2}, {1, 2}};
+    for (int m = 0; m < 6; ++m) {
+        const double r = round16(fmt, B[3 * pair[m][0] + pair[m][1]]);
+        B[3 * pair[m][0] + pair[m][1]] = B[3 * pair[m][1] + pair[m][0]] = r;
+    }
+    for (int x = 0; x < 3; ++x) ab_out[x] = a[x];
+    for (int m = 0; m < 6; ++m) ab_out[3 + m] = B[3 * pair[m][0] + pair[m][1]];
+    oracle_mom_rebuild(ps, u, a, B, gout);
+}
+
 void oracle_step(const oracle_params *P, const double *g, const double *phi, const double *ubar,
                  double *g_new, double *phi_new, double *u_new)
 {
@@ -553,7 +638,11 @@ void oracle_step(const oracle_params *P, const double *g, const double *phi, con
 
                 double gout[Q], u[3], A[9];
                 oracle_collide_node(f, acc, omega, gout, u, A);
-                if (P->storage16) store16(P->storage16, gout, u);
+                if (P->storage16 == 1 || P->storage16 == 2) store16(P->storage16, gout, u);
+                if (P->storage16 == 3 || P->storage16 == 4) {
+                    double ab[9];
+                    oracle_store_mom16_node(P->storage16 - 2, gout, u, ab, gout);
+                }
                 for (int i = 0; i < Q; ++i) g_new[(long)i * N + k] = gout[i];
                 for (int a = 0; a < 3; ++a) u_new[a * N + k] = u[a];
             }

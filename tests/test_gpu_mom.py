@@ -9,6 +9,14 @@ for every z split (each chunk rebuilds its halo planes' populations with the sam
 their owners).  It and the one-node-per-thread kernel (path 1) rebuild identical populations, but
 the compiler may contract the collision's FP32 products differently in the two kernels, so they
 agree to FP32 rounding, not bit for bit.
+
+The 16-bit moment stores round a and B (the non-equilibrium part of the state) once per step.
+The oracle emulates exactly that rounding (oracle.Params storage16 = 3 BF16, 4 FP16, pinned against
+the representation's moment identities and independent rounding routines in
+test_oracle_storage16.py), so each case's bar is derived, as for the 16-bit population stores:
+eps16 = |oracle with 16-bit moments - oracle| (max|d phi|, relative du, relative dp), and a GPU run
+must lie within FP32 bar + 3 eps16 of the plain oracle (a GPU run is another realisation of the
+rounding, so its distance from the plain oracle is of the size of eps16, not below it).
 """
 import math
 
@@ -23,16 +31,9 @@ pytestmark = pytest.mark.gpu
 MOM = solver.LBM_MOM
 STORES = [solver.LBM_MOM, solver.LBM_MOM_BF16, solver.LBM_MOM_FP16]
 STORE_IDS = ["f32", "bf16", "fp16"]
-# FP32 moments: the FP32 bars.  16-bit a and B round the non-equilibrium part of the state, as
-# the 16-bit population formats do, but a (the forcing) and B are rounded on their own and the
-# measured errors are 1.5-3 times those of the 16-bit populations: bars (phi / u / p) = measured
-# maxima times 2-4, rounded up.  Measured on B300 (droplet 48^3 with velocity noise, 100 steps;
-# ragged walled bubble at density ratio 1000, 60 steps; ragged periodic droplet, 80 steps):
-#   BF16  phi 2.3e-6 / 1.1e-5 / 3.1e-6,  u 4.0e-4 / 7.7e-4 / 7.5e-4,  p 7.0e-5 / 2.0e-3 / 5.9e-5
-#   FP16  phi 3.5e-7 / 2.5e-6 / 3.8e-7,  u 5.7e-5 / 8.9e-5 / 1.0e-4,  p 9.9e-6 / 2.0e-4 / 7.8e-6
-TOLS = {solver.LBM_MOM: (1e-5, 1e-4, 1e-4), solver.LBM_MOM_BF16: (4e-5, 3e-3, 6e-3),
-        solver.LBM_MOM_FP16: (1e-5, 4e-4, 1e-3)}
-TOL = TOLS[MOM]
+FP32_BAR = (1e-5, 1e-4, 1e-4)   # the FP32 bars against the oracle: max|d phi|, rel du, rel dp
+SPREAD = 3.0                    # 16-bit stores: bar = FP32 bar + SPREAD eps16
+EMULATION = {solver.LBM_MOM_BF16: 3, solver.LBM_MOM_FP16: 4}   # oracle.Params.storage16 of each store
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -65,23 +66,42 @@ def _run(wl, nsteps, storage=MOM, path=0, split=0):
     return phi, u, p, g, obs
 
 
-def _oracle(wl, nsteps):
-    P = oracle.Params(**wl.params())
+def _oracle(wl, nsteps, storage16=0):
+    P = oracle.Params(**wl.params(), storage16=storage16)
     ps = _pstar0(wl)
     st = oracle.run(P, oracle.init(P, _f32(wl.phi0()).astype(np.float64), _f32(wl.u0()).astype(np.float64),
                                    None if ps is None else ps.astype(np.float64)), nsteps)
     return P, st
 
 
-def _check(out, P, ref, label, factor=1.0, store=MOM):
-    phi, u, p = out[:3]
+def _errs(fields, P, ref, u_scale=None):
+    """max|d phi|, max|d u| / (u_scale or max|u_ref|), max|d p| / max|p_ref| of fields (phi, u, p)."""
+    phi, u, p = fields[:3]
     pref = oracle.pressure(P, ref)
-    dphi = float(np.abs(phi - ref.phi).max())
-    du = float(np.abs(u - ref.u).max() / np.abs(ref.u).max())
-    dp = float(np.abs(p - pref).max() / np.abs(pref).max())
-    print(f"{label} store={store}: max|dphi| {dphi:.3e} rel du {du:.3e} rel dp {dp:.3e}")
-    tphi, tu, tp = (factor * t for t in TOLS[store])
-    assert dphi <= tphi and du <= tu and dp <= tp, (label, dphi, du, dp)
+    us = u_scale if u_scale else np.abs(ref.u).max()
+    return (float(np.abs(phi - ref.phi).max()), float(np.abs(u - ref.u).max() / us),
+            float(np.abs(p - pref).max() / np.abs(pref).max()))
+
+
+def _eps16(wl, nsteps, store, P, ref, u_scale=None):
+    """The 16-bit moment store's own effect on this case: the emulating oracle's distance from the
+    plain one (zero for FP32 moments)."""
+    if store not in EMULATION:
+        return (0.0, 0.0, 0.0)
+    P16, ref16 = _oracle(wl, nsteps, EMULATION[store])
+    return _errs((ref16.phi, ref16.u, oracle.pressure(P16, ref16)), P, ref, u_scale)
+
+
+def _bars(wl, nsteps, store, P, ref, factor=1.0, u_scale=None):
+    eps = _eps16(wl, nsteps, store, P, ref, u_scale)
+    return tuple(factor * FP32_BAR[j] + SPREAD * eps[j] for j in range(3))
+
+
+def _check(out, P, ref, bars, label, store=MOM, u_scale=None):
+    d = _errs(out, P, ref, u_scale)
+    print(f"{label} store={store}: max|dphi| {d[0]:.3e} rel du {d[1]:.3e} rel dp {d[2]:.3e}; bars {bars[0]:.3e} "
+          f"{bars[1]:.3e} {bars[2]:.3e}")
+    assert all(d[j] <= bars[j] for j in range(3)), (label, d, bars)
 
 
 def _same(a, b):
@@ -92,7 +112,8 @@ def _same(a, b):
 @pytest.fixture(scope="module")
 def droplet48():
     wl = inputs.static_droplet(L=48, radius=12.0, noise=0.01, seed=1234)
-    return (wl,) + _oracle(wl, 100)
+    P, ref = _oracle(wl, 100)
+    return wl, P, ref, {st: _bars(wl, 100, st, P, ref) for st in STORES}
 
 
 PATHS = [0, 1]
@@ -102,8 +123,8 @@ PATH_IDS = ["tiled", "plain"]
 @pytest.mark.parametrize("store", STORES, ids=STORE_IDS)
 @pytest.mark.parametrize("path", PATHS, ids=PATH_IDS)
 def test_droplet48_100_steps(droplet48, path, store):
-    wl, P, ref = droplet48
-    _check(_run(wl, 100, storage=store, path=path), P, ref, f"droplet48 path={path}", store=store)
+    wl, P, ref, bars = droplet48
+    _check(_run(wl, 100, storage=store, path=path), P, ref, bars[store], f"droplet48 path={path}", store=store)
 
 
 @pytest.mark.parametrize("store", STORES, ids=STORE_IDS)
@@ -112,7 +133,8 @@ def test_ragged_walled_bubble_ratio1000(path, store):
     wl = inputs.rising_bubble(nx=37, ny=21, nz=19, R=5.0, zc=8.0, sqrt_gR=0.04, mobility=0.1)
     wl.noise, wl.seed = 0.005, 99
     P, ref = _oracle(wl, 60)
-    _check(_run(wl, 60, storage=store, path=path), P, ref, f"ragged walled bubble path={path}", store=store)
+    _check(_run(wl, 60, storage=store, path=path), P, ref, _bars(wl, 60, store, P, ref),
+           f"ragged walled bubble path={path}", store=store)
 
 
 @pytest.mark.parametrize("store", STORES, ids=STORE_IDS)
@@ -122,22 +144,24 @@ def test_ragged_periodic_droplet_across_boundary(path, store):
     wl.nx, wl.ny, wl.nz = 45, 29, 27
     wl.center = (2.0, 27.5, 25.0)
     P, ref = _oracle(wl, 80)
-    _check(_run(wl, 80, storage=store, path=path), P, ref, f"ragged periodic droplet path={path}", store=store)
+    _check(_run(wl, 80, storage=store, path=path), P, ref, _bars(wl, 80, store, P, ref),
+           f"ragged periodic droplet path={path}", store=store)
 
 
 @pytest.mark.parametrize("store", STORES, ids=STORE_IDS)
 def test_minimum_boxes(store):
     """4^3 periodic and 4 x 5 x 4 walled: every tile is ragged, every halo wraps, and a tile's
-    lanes hold several copies of the same node (every node lies in the interface, so the 16-bit
-    stores take 4 times their bulk bounds, as the 16-bit population stores do)."""
+    lanes hold several copies of the same node (every node lies in the interface: 4 times the
+    FP32 bars, plus the 16-bit stores' own derived term)."""
     for walled in (False, True):
         wl = inputs.static_droplet(L=4, radius=1.5, noise=0.01, seed=3)
         if walled:
             wl.ny, wl.wall_z, wl.gravity = 5, 1, (0.0, 0.0, -1e-5)
         P, ref = _oracle(wl, 10)
+        bars = _bars(wl, 10, store, P, ref, factor=4.0)
         for path in PATHS:
-            _check(_run(wl, 10, storage=store, path=path), P, ref, f"minimum box walled={walled} path={path}",
-                   4.0, store=store)
+            _check(_run(wl, 10, storage=store, path=path), P, ref, bars, f"minimum box walled={walled} path={path}",
+                   store=store)
 
 
 @pytest.mark.parametrize("store", STORES, ids=STORE_IDS)
@@ -145,13 +169,16 @@ def test_tiled_and_plain_kernels_agree(store):
     """FP32 moments, measured after 20 steps: max|d phi| ~ 2e-7, relative du and dp ~ 5e-7 (a halo
     or bounce-back error would show at 1e-3 or more).  16-bit moments: a last-bit difference of
     the collision can move a stored value across a 16-bit rounding boundary, so the two kernels
-    agree to the store's oracle bounds."""
+    are two realisations of the rounding: they agree to the FP32 bound plus 2 x SPREAD eps16 of
+    the case."""
     walled = inputs.rising_bubble(nx=37, ny=21, nz=19, R=5.0, zc=8.0, sqrt_gR=0.04, mobility=0.1)
     walled.noise, walled.seed = 0.005, 99
     periodic = inputs.static_droplet(L=24, radius=6.0, noise=0.01, seed=5)
     periodic.nx, periodic.ny, periodic.nz = 45, 29, 27
-    bars = (2e-6, 5e-6, 5e-6) if store == MOM else TOLS[store]
     for wl in (walled, periodic):
+        P, ref = _oracle(wl, 20)
+        eps = _eps16(wl, 20, store, P, ref)
+        bars = tuple(t + 2 * SPREAD * e for t, e in zip((2e-6, 5e-6, 5e-6), eps))
         a, b = _run(wl, 20, storage=store, path=0), _run(wl, 20, storage=store, path=1)
         dphi = np.abs(a[0] - b[0]).max()
         du = np.abs(a[1] - b[1]).max() / np.abs(b[1]).max()
@@ -296,15 +323,9 @@ def test_rising_bubble_full_size_two_steps(store):
     configuration, two steps against the oracle."""
     wl = inputs.rising_bubble()
     P, ref = _oracle(wl, 2)
-    phi, u, p, _, _ = _run(wl, 2, storage=store)
-    TOL = TOLS[store]
-    pref = oracle.pressure(P, ref)
-    dphi = float(np.abs(phi - ref.phi).max())
-    dp = float(np.abs(p - pref).max() / np.abs(pref).max())
-    du = float(np.abs(u - ref.u).max())
-    print(f"bubble full size: {dphi:.3e} {du:.3e} {dp:.3e}")
-    assert dphi <= TOL[0] and dp <= TOL[2]
-    assert du <= TOL[1] * 0.04      # velocities ~1e-6 after two steps: scale sqrt(gR) = 0.04
+    # velocities are ~1e-6 after two steps: measured against the velocity scale sqrt(gR) = 0.04
+    bars = _bars(wl, 2, store, P, ref, u_scale=0.04)
+    _check(_run(wl, 2, storage=store), P, ref, bars, "bubble full size", store=store, u_scale=0.04)
 
 
 @pytest.mark.parametrize("store", STORES, ids=STORE_IDS)

@@ -90,3 +90,68 @@ def test_rounding_keeps_pstar_and_moves_populations_within_the_bound(fmt):
     assert err.max() > 0.05 * bound.max()                # the rounding is seen
     # the state apart from the populations is the unrounded step's
     assert np.array_equal(s16.phi, s.phi) and np.array_equal(s16.u, s.u)
+
+
+# -- the 16-bit moment storage (storage16 = 3 BF16, 4 FP16) -------------------------------------
+
+def _round_like_library(fmt, v):
+    """FP32 value of v rounded to the format (torch's BF16 conversion; numpy's float16 of 2^12 v)."""
+    import torch
+    v32 = np.asarray(v, np.float32)
+    if fmt == 1:
+        return torch.from_numpy(v32).to(torch.bfloat16).to(torch.float32).numpy().astype(np.float64)
+    return ((v32 * np.float32(4096.0)).astype(np.float16).astype(np.float32) / np.float32(4096.0)).astype(np.float64)
+
+
+def test_moment_set_rebuilds_the_collided_populations():
+    """The moment storage's set of a collided node, extracted by the moment identities (sum g = p*,
+    sum g c = u + a/2, sum g c c = p* I/3 + (2/9)(B + 4.5 u u + 4.5 sym(u a))), is a = F / rho and
+    B = 4.5 (1 - omega) A of the collision, and its polynomial gives back the collided populations:
+    random pre-collision states, accelerations and relaxation rates, 200 nodes."""
+    rng = np.random.default_rng(17)
+    for _ in range(200):
+        f = 1.0 / 27.0 + 0.02 * rng.standard_normal(27)
+        acc = 0.002 * rng.standard_normal(3)
+        omega = rng.uniform(0.5, 1.95)
+        g, u, A = oracle.collide_node(f, acc, omega)
+        ps, a, B = oracle.mom_extract(g, u)
+        assert abs(ps - g.sum()) <= 1e-15
+        assert np.abs(a - acc).max() <= 1e-14
+        assert np.abs(B - 4.5 * (1.0 - omega) * A).max() <= 1e-14
+        assert np.abs(oracle.mom_rebuild(ps, u, a, B) - g).max() <= 1e-15
+
+
+@pytest.mark.parametrize("fmt", [1, 2], ids=["bf16", "fp16"])
+def test_moment_storage_rounds_a_and_b_and_keeps_the_other_moments(fmt):
+    """Per node of a stepped noisy droplet (oracle.store_mom16_node): the kept a and B are their
+    FP32 values rounded by an independent routine; the represented populations keep p* and carry
+    u + a_r / 2 as first moment, with a_r the rounded a."""
+    _, _, s = _one_step(0)
+    c, w = oracle.lattice()
+    rng = np.random.default_rng(5)
+    seen = 0
+    for _ in range(40):
+        z, y, x = (int(rng.integers(0, n)) for n in s.phi.shape)
+        g, u = s.g[:, z, y, x], s.u[:, z, y, x]
+        ps, a, B = oracle.mom_extract(g, u)
+        ab, gout = oracle.store_mom16_node(fmt, g, u)
+        want = np.concatenate([a, [B[0, 0], B[1, 1], B[2, 2], B[0, 1], B[0, 2], B[1, 2]]])
+        assert np.array_equal(ab, _round_like_library(fmt, want))
+        assert abs(gout.sum() - ps) <= 1e-15 * max(abs(ps), 1.0)
+        assert np.abs(gout @ c.astype(np.float64) - (u + 0.5 * ab[:3])).max() <= 1e-15
+        seen += np.count_nonzero(ab != want)
+    assert seen > 100                                     # real moments were rounded
+
+
+@pytest.mark.parametrize("fmt", [1, 2], ids=["bf16", "fp16"])
+def test_moment_storage_step_keeps_pstar_and_fields(fmt):
+    """One oracle step with the emulated moment storage: every node keeps the unrounded step's p*;
+    phi and u are the unrounded step's; the populations differ, by about the format's rounding."""
+    P, s0, s16 = _one_step(fmt + 2)
+    P0 = oracle.Params(**{k: getattr(P, k) for k in P.__dataclass_fields__ if k != "storage16"})
+    s = oracle.step(P0, s0)
+    ps, ps16 = s.g.sum(axis=0), s16.g.sum(axis=0)
+    assert np.abs(ps16 - ps).max() <= 1e-13 * max(np.abs(ps).max(), 1.0)
+    assert np.array_equal(s16.phi, s.phi) and np.array_equal(s16.u, s.u)
+    err = np.abs(s16.g - s.g).max()
+    assert 0 < err <= 50 * UNIT[fmt] * np.abs(s.g - s.g.mean(axis=(1, 2, 3), keepdims=True)).max()
