@@ -488,6 +488,9 @@ def main(argv=None):
                          "the pairs, retrain")
     ap.add_argument("--rollout", type=int, default=6, help="legs of each on-policy rollout")
     ap.add_argument("--reps", type=int, default=50)
+    ap.add_argument("--fallback", action="store_true",
+                    help="also run each held-out collision with the fine solver as fallback (run_with_fallback) "
+                         "and report its checks")
     a = ap.parse_args(argv)
     import torch
     torch.cuda.set_device(0)
@@ -506,6 +509,12 @@ def main(argv=None):
         net.set_params(z["params"])
         res = {"eval": [evaluate(net, norm, c, coarse_steps=a.eval_steps, apply_every=a.every) for c in eval_cols],
                "every": a.every, "u_relax": a.u_relax}
+        if a.fallback:
+            res["fallback"] = []
+            for c in eval_cols:
+                record, final = run_with_fallback(net, norm, c, coarse_steps=a.eval_steps, apply_every=a.every)
+                final.close()
+                res["fallback"].append(record)
         if a.ladder:
             res["ladder"] = accuracy_ladder(net, norm, eval_cols[0], coarse_steps=a.eval_steps,
                                             resolutions=(a.L // 2, 3 * a.L // 4), compare=a.L // 4,
