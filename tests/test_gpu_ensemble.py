@@ -193,6 +193,24 @@ def test_moment_storage_ensemble_equals_boxes_run_alone(mixed, store):
     assert obs["sum_pstar"] == o1["sum_pstar"] and obs["sum_phi"] == o1["sum_phi"]
 
 
+@pytest.mark.parametrize("n_boxes", [2, 64], ids=["chunked", "whole_boxes"])
+def test_moment_storage_task_length_does_not_change_the_result(n_boxes):
+    """The moment storages' tasks are as long as the task count allows: 2 boxes of 40^3 (too few
+    columns: 32-plane chunks) and 64 of them (enough columns for one task per column of a whole
+    box).  Either way every box matches its run alone bit for bit (boxes 0 and the last checked)."""
+    store = solver.LBM_MOM_BF16
+    wls = inputs.droplet_ensemble(n=n_boxes, seed=11, L_min=40, L_max=40)
+    with solver.ensemble_from_workloads(wls, storage=store) as e:
+        e.step(7)
+        got = [e.read_fields(b) for b in (0, n_boxes - 1)]
+    ref = []
+    for wl in (wls[0], wls[-1]):
+        with solver.from_workload(wl, storage=store) as s:
+            s.step(7)
+            ref.append(s.read_fields())
+    _assert_same(got, ref, f"{n_boxes} boxes")
+
+
 def test_moment_storage_ensemble_rules():
     """Every box of an ensemble has the same storage; the 2x restriction (closure data) needs FP32
     populations."""
