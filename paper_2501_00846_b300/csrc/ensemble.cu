@@ -94,15 +94,16 @@ constexpr int kEnsMomCtasPerSm = 2;   // the tiled kernel's 95 KB of shared memo
 
 constexpr int AC_WPB = 4;   // warps per Allen–Cahn CTA
 
-// The last box whose first block (FIELD 0), first task (FIELD 1) or first moment-storage task
-// (FIELD 2) is <= v; box 0 starts at 0.
+// The last box whose first Allen–Cahn task (FIELD 1) or first moment-storage task (FIELD 2) is
+// <= v; box 0 starts at 0.  (The lattice Boltzmann node blocks find their box in a table.)
 template <int FIELD>
 __device__ __forceinline__ int find_box(const EnsBox *__restrict__ boxes, int nb, int v)
 {
+    static_assert(FIELD == 1 || FIELD == 2, "FIELD selects the task list");
     int lo = 0, hi = nb - 1;
     while (lo < hi) {
         const int mid = (lo + hi + 1) >> 1;
-        const int start = FIELD == 0 ? boxes[mid].blk0 : FIELD == 1 ? boxes[mid].task0 : boxes[mid].mtask0;
+        const int start = FIELD == 1 ? boxes[mid].task0 : boxes[mid].mtask0;
         if (start <= v)
             lo = mid;
         else
