@@ -280,32 +280,40 @@ def run_with_fallback(net, norm, col, coarse_steps=240, check_every=24, apply_ev
         def checkpoint():
             solver._check(L.lbm_get_state(corr._ctx, ck[0].data_ptr(), ck[1].data_ptr(), ck[2].data_ptr(), 1))
 
-        checkpoint()
-        ck_step = 0
-        obs0 = corr.observables(allow_nonfinite=True)
         record = {"checks": [], "fallback": None, "final": "coarse", "coarse_steps": coarse_steps}
-        for k in range(1, coarse_steps + 1):
-            corr.step(1)
-            if k % apply_every == 0:
-                solver.closure_apply(corr, net, norm)
-            if k % check_every and k != coarse_steps:
-                continue
-            bad = failed_checks(corr.observables(allow_nonfinite=True), obs0, limits)
-            record["checks"].append({"step": k, "failed": bad})
-            if not bad:
-                checkpoint()
-                ck_step = k
-                continue
-            # fallback: the last checkpoint, prolonged to the fine grid, finishes the run
-            corr.set_state(*ck, step=ck_step)
-            fine = solver.Solver(stream=stream, **col.params())
-            fine.init_fields(np.zeros(fine.n, np.float32), np.zeros(3 * fine.n, np.float32))
-            solver.prolong2_state(corr, fine)
+        fine = None
+        try:
+            checkpoint()
+            ck_step = 0
+            obs0 = corr.observables(allow_nonfinite=True)
+            for k in range(1, coarse_steps + 1):
+                corr.step(1)
+                if k % apply_every == 0:
+                    solver.closure_apply(corr, net, norm)
+                if k % check_every and k != coarse_steps:
+                    continue
+                bad = failed_checks(corr.observables(allow_nonfinite=True), obs0, limits)
+                record["checks"].append({"step": k, "failed": bad})
+                if not bad:
+                    checkpoint()
+                    ck_step = k
+                    continue
+                # fallback: the last checkpoint, prolonged to the fine grid, finishes the run
+                corr.set_state(*ck, step=ck_step)
+                fine = solver.Solver(stream=stream, **col.params())
+                fine.init_fields(np.zeros(fine.n, np.float32), np.zeros(3 * fine.n, np.float32))
+                solver.prolong2_state(corr, fine)
+                fine.step(2 * (coarse_steps - ck_step))
+                record["fallback"] = {"detected_at": k, "restart_from": ck_step,
+                                      "fine_steps": 2 * (coarse_steps - ck_step)}
+                record["final"] = "fine"
+                corr.close()
+                return record, fine
+        except BaseException:
             corr.close()
-            fine.step(2 * (coarse_steps - ck_step))
-            record["fallback"] = {"detected_at": k, "restart_from": ck_step, "fine_steps": 2 * (coarse_steps - ck_step)}
-            record["final"] = "fine"
-            return record, fine
+            if fine is not None:
+                fine.close()
+            raise
     return record, corr
 
 
