@@ -211,6 +211,25 @@ def test_moment_storage_task_length_does_not_change_the_result(n_boxes):
     _assert_same(got, ref, f"{n_boxes} boxes")
 
 
+@pytest.mark.parametrize("store", [solver.LBM_FP32, solver.LBM_MOM_BF16], ids=["fp32", "mom_bf16"])
+def test_benchmark_ensemble_sampled_boxes_equal_boxes_run_alone(store):
+    """The benchmark's ensemble (256 seeded droplets, 80.9M nodes) in the benchmark's launch
+    configuration (autotuned, steps replayed from 16-step graphs): sampled boxes (the first, the
+    largest, the last) match their runs alone bit for bit after 20 steps."""
+    wls = inputs.droplet_ensemble()
+    picks = sorted({0, int(np.argmax([wl.n for wl in wls])), len(wls) - 1})
+    with solver.ensemble_from_workloads(wls, storage=store) as e:
+        e.autotune(reps=1)
+        e.step(20)
+        got = [e.read_fields(b) for b in picks]
+    ref = []
+    for b in picks:
+        with solver.from_workload(wls[b], storage=store) as s:
+            s.step(20)
+            ref.append(s.read_fields())
+    _assert_same(got, ref, f"benchmark ensemble {store}")
+
+
 def test_moment_storage_ensemble_rules():
     """Every box of an ensemble has the same storage; the 2x restriction (closure data) needs FP32
     populations."""
