@@ -103,14 +103,16 @@ def droplet512():
     return inputs.static_droplet(L=512)
 
 
-@pytest.mark.parametrize("store", [solver.LBM_FP32, solver.LBM_BF16, solver.LBM_MOM, solver.LBM_MOM_BF16],
-                         ids=["fp32", "bf16", "mom", "mom_bf16"])
+@pytest.mark.parametrize("store", [solver.LBM_FP32, solver.LBM_BF16, solver.LBM_FP16, solver.LBM_MOM,
+                                   solver.LBM_MOM_BF16, solver.LBM_MOM_FP16],
+                         ids=["fp32", "bf16", "fp16", "mom", "mom_bf16", "mom_fp16"])
 def test_droplet_512_sampled_step(droplet512, store):
     """The 512^3 static droplet of the sweep and of the precision study, 20 steps in."""
     _check_sampled(droplet512, store, 20, 0)
 
 
-@pytest.mark.parametrize("store", [solver.LBM_FP32, solver.LBM_MOM_BF16], ids=["fp32", "mom_bf16"])
+@pytest.mark.parametrize("store", [solver.LBM_FP32, solver.LBM_BF16, solver.LBM_MOM_BF16],
+                         ids=["fp32", "bf16", "mom_bf16"])
 def test_rising_bubble_sampled_step(store):
     """The 128 x 128 x 256 benchmark bubble (walls on z, ratios 1000 / 100), 60 steps in, when the
     flow has developed from rest."""
