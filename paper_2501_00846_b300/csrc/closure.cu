@@ -1051,25 +1051,46 @@ __global__ void __launch_bounds__(256) dweight_mma_kernel(int nx, int ny, int nz
         }
 }
 
-// dW[o][i][k] += sum over the nblk blocks of k's z offset group, in block order
-// xfold (the first layer): the gradient of tap k of input channel i is that of the folded input's
-// channel 5 dx' + i at the dx = 0 tap k - dx' + 1 (dx' = k % 3)
-// One warp per weight w: lane l adds the partials of blocks l, l + 32, ... in order, then a fixed
-// shuffle tree adds the lanes (deterministic; the blocks' loads are spread over the warp).
+// dW[o][i][k] += sum over the nblk blocks of k's z offset group.  A block of 256 threads takes 32
+// consecutive partial columns (gz, q, o, is) -- consecutive in memory, so every load is coalesced
+// -- and splits the blocks into 8 consecutive segments, one warp each; the 8 segment sums are then
+// added in segment order.  The order is fixed, so the gradient is reproducible bit for bit, and no
+// sum is longer than nblk terms.  A column maps back to its weight: k = 9 gz + q and i = is, or for
+// the first layer (xfold) the folded layout's ks = k - k % 3 + 1, is = 5 (k % 3) + i.
+constexpr int kDwSegs = 8;
+
 __global__ void __launch_bounds__(256) dw_reduce_kernel(const float *__restrict__ part, int nblk, int cout, int cin,
                                                         bool xfold, float *__restrict__ dW)
 {
-    const int w = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
-    if (w >= cout * cin * 27) return;
-    const int k = w % 27, oi = w / 27, o = oi / cin, i = oi - o * cin;
-    const int ks = xfold ? k - k % 3 + 1 : k, is = xfold ? 5 * (k % 3) + i : i;
-    const int gz = ks / 9, q = ks - 9 * gz;
-    const float *pp = part + ((size_t)gz * nblk * 9 + q) * 1024 + o * 32 + is;
+    __shared__ float seg_sum[kDwSegs][32];
+    const int lane = threadIdx.x & 31, seg = threadIdx.x >> 5;
+    const int col_all = blockIdx.x * 32 + lane;           // (gz, q) * 1024 + o * 32 + is, < 27 * 1024
+    const int gq = col_all >> 10, col = col_all & 1023;
+    const int gz = gq / 9, q = gq - 9 * gz;
+    const float *pp = part + ((size_t)gz * nblk * 9 + q) * 1024 + col;
+    const int b0 = (int)((long long)nblk * seg / kDwSegs), b1 = (int)((long long)nblk * (seg + 1) / kDwSegs);
     float s = 0.0f;
-    for (int b = lane; b < nblk; b += 32) s += pp[(size_t)b * 9 * 1024];
+    for (int b = b0; b < b1; ++b) s += pp[(size_t)b * 9 * 1024];
+    seg_sum[seg][lane] = s;
+    __syncthreads();
+    if (seg != 0) return;
+    float tot = seg_sum[0][lane];
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
-    if (lane == 0) dW[w] += s;
+    for (int g = 1; g < kDwSegs; ++g) tot += seg_sum[g][lane];
+    const int o = col >> 5, is = col & 31, ks = 9 * gz + q;
+    if (o >= cout) return;
+    int k, i;
+    if (xfold) {
+        if (ks % 3 != 1 || is >= 15) return;
+        const int r = is / 5;
+        i = is - 5 * r;
+        k = ks - 1 + r;
+    } else {
+        k = ks;
+        i = is;
+    }
+    if (i >= cin) return;
+    dW[(o * cin + i) * 27 + k] += tot;
 }
 
 // db[o] += the sum of the per-block partials part[b][o] (written by the producers of dz: the loss
@@ -1570,8 +1591,7 @@ cudaError_t launch_dweight(lbm_cnn *c, int layer, float *dW)
                                                                                    c->a[layer], zlen, c->dwpart);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    const int nw = tslb::COUT[layer] * tslb::CIN[layer] * 27;
-    tslb::dw_reduce_kernel<<<(nw + 7) / 8, 256, 0, c->stream>>>(c->dwpart, tiles * nzc, tslb::COUT[layer],
+    tslb::dw_reduce_kernel<<<27 * 1024 / 32, 256, 0, c->stream>>>(c->dwpart, tiles * nzc, tslb::COUT[layer],
                                                                  tslb::CIN[layer], layer == 0, dW);
     return cudaGetLastError();
 }
