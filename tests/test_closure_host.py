@@ -40,3 +40,18 @@ def test_limits_can_be_overridden():
     assert closure.failed_checks(o, _obs())
     assert closure.failed_checks(o, _obs(), {"umax": 0.3}) == []
     assert closure.failed_checks(_obs(sum_phi=1002.0), _obs(), {"sum_phi_drift": 1e-2}) == []
+
+
+def test_equal_accuracy_fit_recovers_power_laws():
+    """closure.equal_accuracy on a ladder made from exact power laws: e(L) = 3 L^-2 and
+    t(L) = 1e-6 L^4 (cost per unit physical time under acoustic scaling) recover p = 2 and q = 4, and
+    a corrected run with the error of the plain 128^3 grid is priced at t(128)."""
+    def plain(L):
+        return {"phi_rms_mean": 3.0 * L ** -2.0, "ms_per_coarse_step": 1e-6 * L ** 4.0}
+    ladder = {"runs": {"plain_64": plain(64), "plain_96": plain(96),
+                       "closure_64": {"phi_rms_mean": 3.0 * 128 ** -2.0, "ms_per_coarse_step": 0.5}}}
+    r = closure.equal_accuracy(ladder, coarse=64, finer=96)
+    assert abs(r["error_exponent"] - 2.0) < 1e-12 and abs(r["cost_exponent"] - 4.0) < 1e-12
+    assert abs(r["equal_accuracy_grid"] - 128.0) < 1e-9
+    assert abs(r["plain_ms_at_equal_accuracy"] - 1e-6 * 128 ** 4) < 1e-9
+    assert abs(r["speedup"] - 1e-6 * 128 ** 4 / 0.5) < 1e-9
