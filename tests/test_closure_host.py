@@ -1,7 +1,9 @@
-"""Host logic of the closure's fine-solver fallback (no GPU): closure.failed_checks decides when a
-corrected coarse run is handed to the fine solver.  A healthy state passes; each limit (non-finite
-nodes, phi range, max |u|, sum phi drift) fails on its own, with a reason that names it; limits can
-be overridden one at a time."""
+"""Host logic of the learned closure (no GPU).
+
+closure.failed_checks decides when a corrected coarse run is handed to the fine solver: a healthy
+state passes; each limit (non-finite nodes, phi range, max |u|, sum phi drift) fails on its own,
+with a reason that names it; limits can be overridden one at a time.  closure.equal_accuracy prices
+the plain grid of the corrected run's accuracy from two plain grids."""
 from paper_2501_00846_b300 import closure
 
 
